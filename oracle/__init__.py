@@ -1,0 +1,242 @@
+"""FP64 CPU oracle for the random batch Ewald k-space path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference legs of
+``bench.py`` may import this package.  It wraps ``rbe_oracle.c`` (plain C, FP64,
+index-order loops) through ctypes and never touches the CUDA library.
+
+Functions follow the paper's Sec. 4.1 (Ewald sum), Sec. 4.2 (RBE estimators, the
+normaliser S and the importance distribution), Sec. 4.3 (sampling) and App. C (the
+pressure tensor); each C function states the equation it restates.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rbe_oracle.c")
+_SRC_NPT = os.path.join(_HERE, "npt_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+_c_int32_p = ctypes.POINTER(ctypes.c_int32)
+_c_uint32_p = ctypes.POINTER(ctypes.c_uint32)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc into ``oracle/_build/liboracle.so`` and return its path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    srcs = [s for s in (_SRC, _SRC_NPT) if os.path.exists(s)]
+    newest = max(os.path.getmtime(s) for s in srcs)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", "-o", tmp] + srcs + ["-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.orc_philox4x32_10.argtypes = [_c_uint32_p, _c_uint32_p, _c_uint32_p]
+            lib.orc_philox4x32_10.restype = None
+            lib.orc_uniform53.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
+            lib.orc_uniform53.restype = ctypes.c_double
+            lib.orc_exp.argtypes = [ctypes.c_double]
+            lib.orc_exp.restype = ctypes.c_double
+            lib.orc_axis_M.argtypes = [ctypes.c_double, ctypes.c_double]
+            lib.orc_axis_M.restype = ctypes.c_int32
+            lib.orc_axis_table.argtypes = [ctypes.c_double, ctypes.c_double, _c_double_p, _c_double_p]
+            lib.orc_axis_table.restype = ctypes.c_double
+            lib.orc_sample_k.argtypes = [_c_double_p, ctypes.c_double, ctypes.c_int32, ctypes.c_uint64,
+                                         ctypes.c_uint64, _c_int32_p, _c_double_p]
+            lib.orc_sample_k.restype = ctypes.c_int
+            lib.orc_ewald_kspace.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p,
+                                             ctypes.c_double, ctypes.c_int32, _c_double_p, _c_double_p,
+                                             _c_double_p]
+            lib.orc_ewald_kspace.restype = ctypes.c_int
+            lib.orc_rbe_kspace.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p,
+                                           ctypes.c_double, ctypes.c_int32, _c_int32_p, _c_double_p,
+                                           _c_double_p, _c_double_p, _c_double_p, _c_double_p]
+            lib.orc_rbe_kspace.restype = ctypes.c_int
+            lib.orc_rbe_snapshot.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p,
+                                             ctypes.c_double, ctypes.c_int32, ctypes.c_uint64,
+                                             ctypes.c_uint64, _c_double_p, _c_double_p, _c_double_p,
+                                             _c_int32_p, _c_double_p]
+            lib.orc_rbe_snapshot.restype = ctypes.c_int
+            lib.orc_ewald_real.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p,
+                                           ctypes.c_double, ctypes.c_double, _c_double_p, _c_double_p,
+                                           _c_double_p]
+            lib.orc_ewald_real.restype = ctypes.c_int
+            lib.orc_direct_sum.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p,
+                                           ctypes.c_int32]
+            lib.orc_direct_sum.restype = ctypes.c_double
+            if hasattr(lib, "orc_npt_step"):
+                _bind_npt(lib)
+            _lib = lib
+    return _lib
+
+
+def _bind_npt(lib):
+    lib.orc_npt_step.restype = ctypes.c_int
+
+
+def _dp(a):
+    return a.ctypes.data_as(_c_double_p)
+
+
+def _ip(a):
+    return a.ctypes.data_as(_c_int32_p)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _check(st, what):
+    if st != 0:
+        raise OracleError(f"{what} failed with status {st}")
+
+
+# ---------------------------------------------------------------------------------
+def philox4x32_10(ctr, key):
+    """Philox-4x32-10 words for one counter (4 uint32) and key (2 uint32)."""
+    lib = _load()
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib.orc_philox4x32_10(c.ctypes.data_as(_c_uint32_p), k.ctypes.data_as(_c_uint32_p),
+                          out.ctypes.data_as(_c_uint32_p))
+    return out
+
+
+def uniform53(a, b):
+    return _load().orc_uniform53(int(a), int(b))
+
+
+def exp_table(x: float) -> float:
+    """The sampler's own exponential (Cody--Waite + Taylor), for x in [-700, 0]."""
+    return _load().orc_exp(float(x))
+
+
+def axis_table(alpha: float, ell: float):
+    """(w, cdf, M, H) of the per-axis discrete Gaussian for box length ell."""
+    lib = _load()
+    M = lib.orc_axis_M(alpha, ell)
+    w = np.zeros(2 * M + 1)
+    cdf = np.zeros(2 * M + 1)
+    H = lib.orc_axis_table(alpha, ell, _dp(w), _dp(cdf))
+    return w, cdf, M, H
+
+
+def sample_k(box, alpha: float, P: int, seed: int, step: int):
+    """m[P,3] (int32) and S for one step of the k-sampling stream."""
+    lib = _load()
+    b = _f64(box, (3,))
+    m = np.zeros((P, 3), dtype=np.int32)
+    S = ctypes.c_double(0.0)
+    _check(lib.orc_sample_k(_dp(b), alpha, P, seed, step, _ip(m), ctypes.byref(S)), "sample_k")
+    return m, S.value
+
+
+def ewald_kspace(pos, q, box, alpha: float, kmax: int):
+    """Full Ewald k-space sum: (F[N,3], W[3,3], E_k, E_self)."""
+    lib = _load()
+    pos = _f64(pos)
+    q = _f64(q)
+    N = q.shape[0]
+    b = _f64(box, (3,))
+    F = np.zeros((N, 3))
+    W = np.zeros((3, 3))
+    E = np.zeros(2)
+    _check(lib.orc_ewald_kspace(N, _dp(pos), _dp(q), _dp(b), alpha, kmax, _dp(F), _dp(W), _dp(E)),
+           "ewald_kspace")
+    return F, W, E[0], E[1]
+
+
+def rbe_kspace(pos, q, box, alpha: float, m, weights):
+    """RBE estimators on a given batch: (F[N,3], W[3,3], E_k, E_self, rho[P] complex)."""
+    lib = _load()
+    pos = _f64(pos)
+    q = _f64(q)
+    N = q.shape[0]
+    m = np.ascontiguousarray(m, dtype=np.int32).reshape(-1, 3)
+    P = m.shape[0]
+    wl = np.asarray(weights, dtype=np.float64)
+    wl = np.full(P, float(wl)) if wl.ndim == 0 else np.ascontiguousarray(wl)
+    if wl.shape != (P,):
+        raise ValueError("weights must be a scalar or have one entry per frequency")
+    b = _f64(box, (3,))
+    F = np.zeros((N, 3))
+    W = np.zeros((3, 3))
+    E = np.zeros(2)
+    rho = np.zeros(2 * P)
+    _check(lib.orc_rbe_kspace(N, _dp(pos), _dp(q), _dp(b), alpha, P, _ip(m), _dp(wl), _dp(F), _dp(W),
+                              _dp(E), _dp(rho)), "rbe_kspace")
+    return F, W, E[0], E[1], rho[0::2] + 1j * rho[1::2]
+
+
+def rbe_snapshot(pos, q, box, alpha: float, P: int, seed: int, step: int):
+    """Sample and evaluate: (F, W, E_k, E_self, m, S)."""
+    lib = _load()
+    pos = _f64(pos)
+    q = _f64(q)
+    N = q.shape[0]
+    b = _f64(box, (3,))
+    F = np.zeros((N, 3))
+    W = np.zeros((3, 3))
+    E = np.zeros(2)
+    m = np.zeros((P, 3), dtype=np.int32)
+    S = ctypes.c_double(0.0)
+    _check(lib.orc_rbe_snapshot(N, _dp(pos), _dp(q), _dp(b), alpha, P, seed, step, _dp(F), _dp(W),
+                                _dp(E), _ip(m), ctypes.byref(S)), "rbe_snapshot")
+    return F, W, E[0], E[1], m, S.value
+
+
+def ewald_real(pos, q, box, alpha: float, rc: float):
+    """Nearest-image erfc real-space part: (F[N,3], W[3,3], E_r)."""
+    lib = _load()
+    pos = _f64(pos)
+    q = _f64(q)
+    N = q.shape[0]
+    b = _f64(box, (3,))
+    F = np.zeros((N, 3))
+    W = np.zeros((3, 3))
+    E = ctypes.c_double(0.0)
+    _check(lib.orc_ewald_real(N, _dp(pos), _dp(q), _dp(b), alpha, rc, _dp(F), _dp(W), ctypes.byref(E)),
+           "ewald_real")
+    return F, W, E.value
+
+
+def direct_sum(pos, q, box, R: int) -> float:
+    """Brute-force image sum over whole cells with |n| <= R."""
+    lib = _load()
+    pos = _f64(pos)
+    q = _f64(q)
+    b = _f64(box, (3,))
+    return lib.orc_direct_sum(q.shape[0], _dp(pos), _dp(q), _dp(b), R)
+
+
+def ewald_total(pos, q, box, alpha: float, rc: float, kmax: int):
+    """Total Ewald energy, force and virial (k-space + self + real space)."""
+    Fk, Wk, Ek, Es = ewald_kspace(pos, q, box, alpha, kmax)
+    Fr, Wr, Er = ewald_real(pos, q, box, alpha, rc)
+    return Fk + Fr, Wk + Wr, Ek + Es + Er

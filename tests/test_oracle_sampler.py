@@ -1,0 +1,150 @@
+"""Pins of the oracle's counter-based generator and frequency sampler (Sec. 4.2 Eqs. (S),
+(psf), (probexpression); Sec. 4.3; App. C item 1)."""
+import json
+import math
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+
+_TRITON_SCRIPT = r"""
+import os, sys, json
+os.environ["TRITON_INTERPRET"] = "1"
+import torch, triton, triton.language as tl
+
+@triton.jit
+def _philox_kernel(ctr_ptr, key_ptr, out_ptr):
+    i = tl.program_id(0)
+    c0 = tl.load(ctr_ptr + 4 * i + 0).to(tl.uint32)
+    c1 = tl.load(ctr_ptr + 4 * i + 1).to(tl.uint32)
+    c2 = tl.load(ctr_ptr + 4 * i + 2).to(tl.uint32)
+    c3 = tl.load(ctr_ptr + 4 * i + 3).to(tl.uint32)
+    seed = tl.load(key_ptr + i).to(tl.uint64)
+    a, b, c, d = tl.philox(seed, c0, c1, c2, c3, 10)
+    tl.store(out_ptr + 4 * i + 0, a.to(tl.int64, bitcast=False))
+    tl.store(out_ptr + 4 * i + 1, b.to(tl.int64, bitcast=False))
+    tl.store(out_ptr + 4 * i + 2, c.to(tl.int64, bitcast=False))
+    tl.store(out_ptr + 4 * i + 3, d.to(tl.int64, bitcast=False))
+
+data = json.loads(sys.stdin.read())
+ctr = torch.tensor(data["ctr"], dtype=torch.int64)
+key = torch.tensor(data["key"], dtype=torch.int64)
+n = key.shape[0]
+out = torch.zeros(4 * n, dtype=torch.int64)
+_philox_kernel[(n,)](ctr, key, out)
+print(json.dumps([int(x) & 0xFFFFFFFF for x in out.tolist()]))
+"""
+
+
+def test_philox_matches_independent_library():
+    """Philox-4x32-10 words against Triton's own implementation, run by its CPU interpreter."""
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(7)
+    n = 48
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64)
+    ctr[0] = 0
+    ctr[1] = [0xFFFFFFFF] * 4
+    keys = rng.integers(0, 2**63, size=n, dtype=np.uint64)
+    keys[0] = 0
+    payload = json.dumps({"ctr": ctr.reshape(-1).astype(np.int64).tolist(),
+                          "key": keys.astype(np.int64).tolist()})
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    res = subprocess.run([sys.executable, "-c", _TRITON_SCRIPT], input=payload, capture_output=True,
+                         text=True, env=env, timeout=600)
+    if res.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + res.stderr[-300:])
+    ref = np.array(json.loads(res.stdout.strip().splitlines()[-1]), dtype=np.uint64).reshape(n, 4)
+    for i in range(n):
+        k = int(keys[i])
+        got = oracle.philox4x32_10(ctr[i].astype(np.uint32), [k & 0xFFFFFFFF, k >> 32])
+        assert np.array_equal(got.astype(np.uint64), ref[i]), i
+
+
+def test_uniform53_range_and_law():
+    rng = np.random.default_rng(1)
+    words = rng.integers(0, 2**32, size=(20000, 2), dtype=np.uint64)
+    u = np.array([oracle.uniform53(a, b) for a, b in words])
+    assert u.min() >= 0.0 and u.max() < 1.0
+    assert oracle.uniform53(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - 2.0 ** -53
+    assert oracle.uniform53(0, 0) == 0.0
+    assert stats.kstest(u, "uniform").pvalue > 1e-3
+
+
+def test_own_exp_against_libm():
+    xs = np.concatenate([-np.linspace(0, 700, 20001), -np.geomspace(1e-12, 700, 5000), [0.0, -1e-300]])
+    for x in xs:
+        got = oracle.exp_table(float(x))
+        ref = math.exp(float(x))
+        assert abs(got - ref) <= 2 * math.ulp(ref), x
+
+
+@pytest.mark.parametrize("alpha,ell", [(1.0, 10.0), (0.2, 80.0), (0.2, 120.0), (0.2, 342.0), (0.25, 44.78),
+                                       (5.0, 1.3)])
+def test_axis_table_poisson_identity(alpha, ell):
+    """H = sum_m exp(-pi^2 m^2/(alpha l^2)) = sqrt(alpha l^2/pi) sum_n exp(-alpha n^2 l^2) (Eq. (psf))."""
+    w, cdf, M, H = oracle.axis_table(alpha, ell)
+    assert np.array_equal(w, w[::-1])                  # exactly symmetric
+    assert w[M] == 1.0
+    assert np.all(np.diff(cdf) >= 0) and cdf[-1] == H   # tail terms below 1 ulp of H are absorbed
+    n = np.arange(-50, 51)
+    dual = math.sqrt(alpha * ell * ell / math.pi) * np.sum(np.exp(-alpha * n * n * ell * ell))
+    assert abs(H / dual - 1.0) < 1e-14
+    # truncation: w_M is the first term at or below 2^-60 of the peak
+    c = math.pi ** 2 / (alpha * ell * ell)
+    assert math.exp(-c * M * M) <= 2.0 ** -60 * (1 + 1e-12)
+    assert M == 1 or math.exp(-c * (M - 1) ** 2) > 2.0 ** -60
+
+
+def test_sampler_marginals_chi_square():
+    """Per-axis marginals of the rejection sampler: P(m_x = a) = w_a (H_y H_z - [a == 0]) / S."""
+    box = np.array([3.0, 4.0, 5.0])
+    alpha = 1.0
+    P = 200_000
+    m, S = oracle.sample_k(box, alpha, P, seed=2024, step=3)
+    assert not np.any(np.all(m == 0, axis=1))
+    tabs = [oracle.axis_table(alpha, b) for b in box]
+    Hs = [t[3] for t in tabs]
+    assert abs(S - (Hs[0] * Hs[1] * Hs[2] - 1.0)) < 1e-15 * S
+    for ax in range(3):
+        w, _, M, H = tabs[ax]
+        others = np.prod([Hs[j] for j in range(3) if j != ax])
+        vals = np.arange(-M, M + 1)
+        p = w * (others - (vals == 0)) / S
+        counts = np.array([(m[:, ax] == v).sum() for v in vals])
+        keep = p * P >= 5
+        obs = np.append(counts[keep], counts[~keep].sum())
+        exp = np.append(p[keep] * P, p[~keep].sum() * P)
+        if exp[-1] < 5:
+            obs[-2] += obs[-1]; exp[-2] += exp[-1]
+            obs, exp = obs[:-1], exp[:-1]
+        chi2 = ((obs - exp) ** 2 / exp).sum()
+        pval = stats.chi2.sf(chi2, len(obs) - 1)
+        assert pval > 1e-4, (ax, chi2, len(obs))
+    # joint: m_x = m_y = 0 has probability (H_z - 1)/S
+    both0 = np.mean((m[:, 0] == 0) & (m[:, 1] == 0))
+    pz = (Hs[2] - 1.0) / S
+    assert abs(both0 - pz) < 5 * math.sqrt(pz * (1 - pz) / P)
+
+
+def test_sampler_counter_semantics():
+    box = np.array([10.0, 10.0, 10.0])
+    a, S1 = oracle.sample_k(box, 1.0, 64, seed=5, step=9)
+    b, S2 = oracle.sample_k(box, 1.0, 64, seed=5, step=9)
+    c, _ = oracle.sample_k(box, 1.0, 64, seed=5, step=10)
+    d, _ = oracle.sample_k(box, 1.0, 64, seed=6, step=9)
+    e, _ = oracle.sample_k(box, 1.0, 128, seed=5, step=9)
+    assert np.array_equal(a, b) and S1 == S2
+    assert not np.array_equal(a, c) and not np.array_equal(a, d)
+    assert np.array_equal(e[:64], a)                 # sample l depends only on (seed, step, l)
+
+
+def test_sampler_tiny_box_rejects_often():
+    """With alpha l^2 small almost every draw is m = 0; the redraw still returns nonzero m."""
+    box = np.array([1.0, 1.0, 1.0])
+    m, S = oracle.sample_k(box, 1.5, 32, seed=1, step=0)
+    assert S < 0.01 and not np.any(np.all(m == 0, axis=1))
