@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Benchmark of the RBE k-space hot path on GB300: one JSON line on rank 0.
+
+A step is one RBE k-space evaluation of the whole workload through the C ABI:
+sample P frequencies, reduce rho(k) over all N particles, gather the N forces, and
+reduce the energy and the 3x3 virial (``rbe_kspace_forces_virial``).  The metric is
+N*P pair evaluations per second (one evaluation = both passes over a (particle,
+frequency) pair).  Inputs sit in HBM before the timed region; the L2 is flushed
+(a 256 MB write) between timed steps, outside the per-step CUDA events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload slab|uniform1e6|...]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+Under torchrun each rank runs its own replica of the workload (independent systems,
+no collective on the data path); rank 0 prints the max-over-ranks timing.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2110_14362_gb300 import inputs  # noqa: E402
+
+METRIC = "RBE k-space N*P pair evaluations/s (FP32-phase; FP64 alongside)"
+UNIT = "pair-evals/s"
+SEED = 12345
+
+# MUFU sine/cosine operations per pair evaluation in the two-pass schedule
+# (one __sincosf = MUFU.SIN + MUFU.COS in the rho pass and again in the force pass).
+MUFU_OPS_PER_PAIR_PASS = 2.0
+
+# DRAM bytes per launch of the dominant kernel measured by ncu on this workload
+# (dram__bytes_read.sum + dram__bytes_write.sum), or None when not captured for the
+# current kernel version.  Source: profiles/ summaries.
+NCU_TRAFFIC = {}
+
+
+def workload(name: str):
+    if name == "slab":
+        return inputs.slab()
+    if name == "snapshot":
+        return inputs.small_snapshot()
+    if name.startswith("uniform"):
+        # uniform<N>[-P<P>], e.g. uniform1e6-P500
+        spec = name[len("uniform"):]
+        P = 100
+        if "-P" in spec:
+            spec, p = spec.split("-P")
+            P = int(p)
+        return inputs.uniform_density(int(float(spec)), P=P)
+    if name == "water":
+        return inputs.water()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() in ("active", "1"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_2110_14362_gb300 as rbe
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    s = workload(args.workload)
+    precision = rbe.RBE_FP32_PHASE if args.precision == "fp32" else rbe.RBE_FP64
+    pos = torch.as_tensor(s.pos).to(dev).contiguous()
+    q = torch.as_tensor(s.q).to(dev).contiguous()
+    F = torch.empty((s.N, 3), dtype=torch.float64, device=dev)
+    W = torch.empty(9, dtype=torch.float64, device=dev)
+    E = torch.empty(2, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    seed = SEED + rank
+
+    def timed_loop(ctx, steps, warmup, first_step):
+        ctx.set_stream(stream.cuda_stream)
+        for w in range(warmup):
+            ctx.forces_virial(pos, q, first_step + w, F, W, E)
+        ctx.sync()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            ctx.forces_virial(pos, q, first_step + warmup + k, F, W, E)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        wall = time.perf_counter() - t0
+        ctx.sync()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        return ms, wall
+
+    ctx = rbe.Context(s.box, s.alpha, s.P, seed, precision)
+    with ClockSampler(local) as clk:
+        ms, wall = timed_loop(ctx, args.steps, args.warmup, 0)
+    clocks = clk.summary()
+    dev_s = sum(ms) / 1e3
+    dev_s_max = max_over_ranks(world, dev_s)
+    pairs = float(s.N) * s.P
+    value = world * args.steps * pairs / dev_s_max
+
+    # per-kernel durations (live, CUDA events recorded by the library on its stream)
+    ctx.set_kernel_timing(True)
+    kt = []
+    for k in range(max(3, min(args.steps, 20))):
+        flush.fill_(float(k))
+        ctx.forces_virial(pos, q, 10_000 + k, F, W, E)
+        kt.append(ctx.kernel_times())
+    ctx.set_kernel_timing(False)
+    kmean = np.mean(np.array(kt), axis=0)  # sample, rho, reduce, force
+    names = ["k_sample", "k_rho", "k_reduce", "k_force"]
+    dom = int(np.argmax(kmean))
+
+    # FP64 on the same workload, a few steps (the plain single-system FP64 path)
+    other = None
+    if args.precision == "fp32" and not args.skip_fp64:
+        ctx64 = rbe.Context(s.box, s.alpha, s.P, seed, rbe.RBE_FP64)
+        ms64, _ = timed_loop(ctx64, max(2, min(args.steps, 5)), 2, 50_000)
+        other = {"precision": "fp64", "value": pairs / (sum(ms64) / len(ms64) / 1e3), "unit": UNIT,
+                 "ms_per_step": sum(ms64) / len(ms64)}
+        ctx64.close()
+
+    # end to end through the public host-buffer call: pinned host inputs in, forces out
+    pos_h = torch.empty((s.N, 3), dtype=torch.float64, pin_memory=True)
+    q_h = torch.empty((s.N,), dtype=torch.float64, pin_memory=True)
+    F_h = torch.empty((s.N, 3), dtype=torch.float64, pin_memory=True)
+    pos_h.copy_(torch.as_tensor(s.pos))
+    q_h.copy_(torch.as_tensor(s.q))
+    pn, qn, Fn = pos_h.numpy(), q_h.numpy(), F_h.numpy()
+    for w in range(2):
+        rbe.rbe_kspace_forces_virial_host(ctx.h, pn, qn, 20_000 + w, Fn)
+    barrier(world)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        rbe.rbe_kspace_forces_virial_host(ctx.h, pn, qn, 30_000 + k, Fn)
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+    e2e = {"value": world * args.steps * pairs / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(pn.nbytes + qn.nbytes),
+           "d2h_bytes_per_step": int(Fn.nbytes + 11 * 8)}
+
+    # roofline of the dominant kernel against the measured MUFU throughput
+    peak_mufu = rbe.rbe_measure_pipe(0, 4096)
+    dom_ms = float(kmean[dom])
+    if args.precision == "fp32" and names[dom] in ("k_rho", "k_force"):
+        achieved = MUFU_OPS_PER_PAIR_PASS * pairs / (dom_ms * 1e-3)
+        roof = {"bound": "alu", "pipe": "MUFU (sin/cos)", "kernel": names[dom], "achieved": achieved / 1e9,
+                "peak": peak_mufu / 1e9, "unit": "Gop/s", "frac": achieved / peak_mufu,
+                "peak_source": "measured on this GPU by rbe_measure_pipe(MUFU sin.approx)",
+                "traffic": NCU_TRAFFIC.get((names[dom], args.workload))}
+    else:
+        peak_dfma = rbe.rbe_measure_pipe(2, 1024)
+        roof = {"bound": "alu", "pipe": "FP64 FMA", "kernel": names[dom], "achieved": None,
+                "peak": peak_dfma / 1e9, "unit": "GDFMA/s", "frac": None, "traffic": None}
+    ctx.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        cpu = cpu_baseline(s, budget_s=args.cpu_seconds)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_s_max * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32-phase/f64-accum" if args.precision == "fp32" else "f64",
+        "data": "synthetic (seeded NumPy; shapes of the paper's workloads)",
+        "config": {"workload": s.name, "N": s.N, "P": s.P, "alpha": s.alpha, "box": [float(b) for b in s.box],
+                   "precision": args.precision, "rho_accum": "fp32-tile/fp64", "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world} (independent systems, no collective)"},
+        "kernel_ms": {n: float(v) for n, v in zip(names, kmean)},
+        "wall_s_timed_region": wall,
+        "gpu_launches": 4 * args.steps,
+        "e2e": e2e,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    if other:
+        line["fp64_same_workload"] = other
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(s, budget_s: float = 15.0):
+    """The FP64 oracle, as it stands, on a bounded sample: the same P frequencies against
+    the first n particles, n sized so the run takes about budget_s seconds."""
+    import oracle
+    m, S = oracle.sample_k(s.box, s.alpha, s.P, SEED, 0)
+    n = min(s.N, 256)
+    t0 = time.perf_counter()
+    oracle.rbe_kspace(s.pos[:n], s.q[:n], s.box, s.alpha, m, S / s.P)
+    dt = time.perf_counter() - t0
+    n2 = int(min(s.N, max(n, n * budget_s / max(dt, 1e-6) * 0.8)))
+    t0 = time.perf_counter()
+    oracle.rbe_kspace(s.pos[:n2], s.q[:n2], s.box, s.alpha, m, S / s.P)
+    dt = time.perf_counter() - t0
+    return {"value": n2 * s.P / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n2} of {s.N} particles x all P={s.P} frequencies (rho pass + force pass, FP64, "
+                      f"single thread), {dt:.1f} s"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    s = workload(args.workload)
+    import oracle
+    m, S = oracle.sample_k(s.box, s.alpha, s.P, SEED, 0)
+    # each step: the oracle on a bounded sample sized so that the whole run takes minutes
+    n = min(s.N, 256)
+    t0 = time.perf_counter()
+    oracle.rbe_kspace(s.pos[:n], s.q[:n], s.box, s.alpha, m, S / s.P)
+    dt = time.perf_counter() - t0
+    per_step = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    n = int(min(s.N, max(n, n * per_step / max(dt, 1e-6))))
+    for w in range(args.warmup):
+        oracle.rbe_kspace(s.pos[:n], s.q[:n], s.box, s.alpha, m, S / s.P)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.rbe_kspace(s.pos[:n], s.q[:n], s.box, s.alpha, m, S / s.P)
+    dt = time.perf_counter() - t0
+    value = args.steps * n * s.P / dt
+    sample = f"first {n} of {s.N} particles x all P={s.P} frequencies per step (FP64 oracle, single thread)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded NumPy)",
+        "config": {"workload": s.name, "N": s.N, "P": s.P, "precision": "fp64 (oracle)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="slab")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,163 @@
+/*
+ * librbe -- random batch Ewald (RBE) k-space forces, energy and virial on one GB300 GPU.
+ *
+ * The method (Liang, Tan, Hong, Jin, Xu, Li, "A random batch Ewald method for charged
+ * particles in the isothermal-isobaric ensemble"): N charges q_i at r_i in a periodic
+ * rectangular box h = diag(l_x, l_y, l_z) (Sec. 4.1, App. C).  Each evaluation draws P
+ * frequencies k = 2 pi m / l (m in Z^3 \ {0}) i.i.d. from the discrete Gaussian
+ * P(k) = exp(-|k|^2/4a) / S, S = H_x H_y H_z - 1 (Sec. 4.2 Eqs. (S), (psf),
+ * (probexpression); App. C item 1), forms rho(k) = sum_i q_i e^{i k.r_i}, and returns
+ *   forces   F_i = -sum_l (S/P) (4 pi q_i k_l / (V |k_l|^2)) Im(e^{-i k_l.r_i} rho(k_l))
+ *                                                                  Sec. 4.2 Eq. (appforce)
+ *   virial   W = (2 pi / V) sum_l (S/P) |rho_l|^2/|k_l|^2 [I - 2 (1/|k_l|^2 + 1/4a) k_l k_l]
+ *            (energy units: the k-space pressure tensor is W / V)   App. C Eq. (pressuretensorflexible);
+ *            tr(W)/(3V) is P_2* of Sec. 4.2 Eq. (apppress)
+ *   energy   E_k = (2 pi / V) sum_l (S/P) |rho_l|^2/|k_l|^2 and E_self = -sqrt(a/pi) sum_i q_i^2
+ *            (importance-weighted form of Sec. 4.1 Eq. (U1fourier))
+ * Units are Gaussian (U = 1/2 sum q_i q_j / r): multiply by the caller's Coulomb constant.
+ *
+ * Conventions for every call:
+ *  - Ownership: the caller owns every buffer it passes; nothing is freed across the
+ *    boundary.  The context owns only its scratch and tables.
+ *  - Device pointers must be CUDA device (or managed) memory of the current device,
+ *    8-byte aligned; host pointers are ordinary host memory.
+ *  - Device outputs are written asynchronously on the context's stream (rbe_set_stream);
+ *    calls taking host buffers synchronise that stream before returning.
+ *  - Every call validates all arguments before any launch and returns without side
+ *    effects on RBE_EINVAL.  rbe_last_error() gives a message for the last failure.
+ *  - Errors detected on the device (a sample that stayed at m = 0 for 2^20 redraws, a
+ *    non-finite rho) are latched in a device status word and returned by the next
+ *    synchronising call (rbe_sync, rbe_sample_k, the *_host calls).
+ *  - One context per host thread; calls on one context are not thread-safe.
+ */
+#ifndef RBE_H
+#define RBE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rbe_ctx_s* rbe_ctx;
+
+typedef enum {
+    RBE_OK = 0,
+    RBE_EINVAL = 1,      /* bad argument: null/misaligned pointer, N < 0, P < 1, alpha <= 0, box <= 0 ... */
+    RBE_ENOMEM = 2,      /* device or host allocation failed */
+    RBE_ECUDA = 3,       /* a CUDA runtime call or launch failed (message in rbe_last_error) */
+    RBE_ETIMEOUT = 4,    /* a bounded device-side wait gave up */
+    RBE_ENONFINITE = 5,  /* rho(k) or an output became NaN/Inf (non-finite inputs) */
+    RBE_ESAMPLE = 6,     /* a frequency stayed m = 0 after 2^20 redraws (alpha l^2 far too small) */
+    RBE_ESTATE = 7       /* call not valid in the context's current state */
+} rbe_status;
+
+typedef enum {
+    RBE_FP64 = 0,        /* phases, sincos and accumulation in FP64 */
+    RBE_FP32_PHASE = 1   /* exact 32-bit fixed-point phase m.s mod 1, FP32 sincos, FP64 across tiles */
+} rbe_precision;
+
+typedef enum {
+    RBE_RHO_FP64 = 0,    /* FP32-phase path: rho accumulated per pair in FP64 */
+    RBE_RHO_COMP32 = 1,  /* FP32-phase path: compensated (Kahan) FP32 within a staged tile, FP64 across */
+    RBE_RHO_FP32 = 2     /* FP32-phase path: plain FP32 within a staged tile, FP64 across (default) */
+} rbe_rho_accum;
+
+/* Create a context for box lengths box[3] (> 0), splitting parameter alpha (> 0, Sec. 4.1),
+ * batch size P (1 <= P <= 65536, Sec. 4.2) and the Philox key seed.  Allocates the
+ * context's device scratch on the current CUDA device.  *out is set only on RBE_OK.
+ * The box must satisfy pi^2 / (alpha l^2) <= 600 on every axis (otherwise S underflows
+ * and the frequency distribution is degenerate): RBE_EINVAL. */
+rbe_status rbe_create(const double box[3], double alpha, int32_t P, uint64_t seed, rbe_ctx* out);
+
+/* Free the context and its device scratch (synchronises its stream first).  NULL is a no-op. */
+rbe_status rbe_destroy(rbe_ctx ctx);
+
+/* Set the CUDA stream (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream)
+ * on which all later device work of this context runs.  NULL = the legacy default stream. */
+rbe_status rbe_set_stream(rbe_ctx ctx, void* stream);
+
+/* Select the arithmetic: precision in rbe_precision, rho_accum in rbe_rho_accum
+ * (rho_accum is ignored on the FP64 path). */
+rbe_status rbe_set_precision(rbe_ctx ctx, int32_t precision, int32_t rho_accum);
+
+/* Replace the box lengths (same validity rule as rbe_create).  The per-axis sampling
+ * tables are rebuilt on the device at the next evaluation. */
+rbe_status rbe_set_box(rbe_ctx ctx, const double box[3]);
+
+/* Draw the batch of one step (Sec. 4.2-4.3; App. C item 1) into HOST memory:
+ * m_out[P][3] int32 row-major (may be NULL) and S (may be NULL).  Sample l depends only
+ * on (seed, step, l): Philox-4x32-10 with key (seed_lo, seed_hi) and counter
+ * (l, 2*attempt + half, step_lo32, step_hi24); three 53-bit uniforms; per-axis inverse
+ * CDF of exp(-c m^2), c = pi^2/(alpha l^2), truncated at |m| <= ceil(sqrt(60 ln2 / c));
+ * redraw (attempt + 1) while m = 0.  step < 2^56.  Synchronous. */
+rbe_status rbe_sample_k(rbe_ctx ctx, uint64_t step, int32_t* m_out, double* S_out);
+
+/* One RBE k-space evaluation on DEVICE buffers (Sec. 4.2 Eqs. (appforce), (apppress);
+ * App. C Eq. (pressuretensorflexible)).
+ *   N           number of particles, N >= 0 (N = 0 gives zero outputs)
+ *   positions   device, N*3 double, row-major (x, y, z); need not be wrapped into the box
+ *   charges     device, N double
+ *   step        Philox counter of the batch: the same step gives the same m as rbe_sample_k
+ *   forces_out  device, N*3 double, overwritten with the k-space force only
+ *   virial_out  device, 9 double, row-major 3x3 W in energy units (may be NULL)
+ *   energy_out  device, 2 double {E_k, E_self} (may be NULL)
+ * Asynchronous on the context's stream. */
+rbe_status rbe_kspace_forces_virial(rbe_ctx ctx, int64_t N, const double* positions,
+                                    const double* charges, uint64_t step, double* forces_out,
+                                    double* virial_out, double* energy_out);
+
+/* The same evaluation on HOST buffers: copies positions and charges to context-owned
+ * device buffers, evaluates, copies forces, virial and energy back, synchronises the
+ * stream and returns any latched device error.  forces_out may be NULL. */
+rbe_status rbe_kspace_forces_virial_host(rbe_ctx ctx, int64_t N, const double* positions,
+                                         const double* charges, uint64_t step, double* forces_out,
+                                         double* virial_out, double* energy_out);
+
+/* Weighted evaluation on a caller-given frequency list (no sampling): the estimator of
+ * rbe_kspace_forces_virial with S/P replaced by weights[l] for frequency m[l].  With
+ * every m of a cube |m_theta| <= kmax and weights exp(-|k|^2/4a) this is the plain
+ * Ewald k-space sum of Sec. 4.1 Eqs. (U1fourier), (force).
+ *   K          number of frequencies, 1 <= K <= 2^24
+ *   m          device, K*3 int32 (no all-zero row: RBE_EINVAL is not checked on the
+ *              device; a zero row yields a non-finite result latched as RBE_ENONFINITE)
+ *   weights    device, K double
+ * Other arguments as rbe_kspace_forces_virial.  Asynchronous. */
+rbe_status rbe_kspace_weighted(rbe_ctx ctx, int64_t N, const double* positions, const double* charges,
+                               int32_t K, const int32_t* m, const double* weights, double* forces_out,
+                               double* virial_out, double* energy_out);
+
+/* Copy the last evaluation's rho(k_l) (interleaved re, im; 2*P doubles, or 2*K after a
+ * weighted call) into HOST memory.  Synchronous. */
+rbe_status rbe_get_rho(rbe_ctx ctx, double* rho_out, int32_t capacity);
+
+/* Measurement support (no counterpart in the paper).  With timing enabled the context
+ * records CUDA events on its stream around the kernels of each evaluation;
+ * rbe_get_kernel_times waits for the last evaluation and returns the durations in ms of
+ * {sampling, rho pass, rho reduction + energy/virial, force pass}. */
+rbe_status rbe_set_kernel_timing(rbe_ctx ctx, int32_t enable);
+rbe_status rbe_get_kernel_times(rbe_ctx ctx, float ms_out[4]);
+
+/* Throughput probe of one GPU pipe on the current device, in operations per second:
+ * kind 0 = MUFU sine (sin.approx.f32), 1 = FP32 FMA, 2 = FP64 FMA; `iters` rounds of 8
+ * independent operations per thread over 8 x 256-thread blocks per SM, best of three.
+ * Synchronous, legacy default stream.  The measured denominators of the roofline. */
+rbe_status rbe_measure_pipe(int32_t kind, int32_t iters, double* ops_per_s);
+
+/* Synchronise the context's stream and return (and clear) any latched device error. */
+rbe_status rbe_sync(rbe_ctx ctx);
+
+/* Static description of a status code. */
+const char* rbe_status_string(rbe_status status);
+
+/* Message for the last non-OK status returned on ctx (or by rbe_create when ctx is NULL). */
+const char* rbe_last_error(rbe_ctx ctx);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t rbe_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBE_H */

@@ -1,0 +1,15 @@
+"""GB300-native random batch Ewald (RBE) k-space path.
+
+The computation lives in ``librbe.so`` (CUDA for sm_103a, C ABI in ``include/rbe.h``);
+this package holds its build step and a ctypes binding.  ``inputs`` holds the seeded
+synthetic workloads.  Importing the package does not load the library; the first call
+does, and raises if it cannot be built or loaded.
+"""
+from ._binding import (  # noqa: F401
+    RBE_OK, RBE_EINVAL, RBE_ENOMEM, RBE_ECUDA, RBE_ETIMEOUT, RBE_ENONFINITE, RBE_ESAMPLE, RBE_ESTATE,
+    RBE_FP64, RBE_FP32_PHASE, RBE_RHO_FP64, RBE_RHO_COMP32, RBE_RHO_FP32,
+    RBEError, Context, load, library_path,
+    rbe_create, rbe_destroy, rbe_set_stream, rbe_set_precision, rbe_set_box, rbe_sample_k,
+    rbe_kspace_forces_virial, rbe_kspace_forces_virial_host, rbe_kspace_weighted, rbe_get_rho, rbe_sync,
+    rbe_version, rbe_set_kernel_timing, rbe_get_kernel_times, rbe_measure_pipe,
+)

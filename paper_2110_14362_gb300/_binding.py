@@ -1,0 +1,256 @@
+"""ctypes binding of librbe.so (the C ABI in include/rbe.h).
+
+Argument marshalling only: every step of the computation runs in the library's CUDA
+kernels.  Functions carry the C names; ``Context`` wraps a handle for convenience.
+Device buffers are passed as torch CUDA tensors (their data pointers); host buffers as
+NumPy arrays.  If the library is missing or fails to load, every call raises -- there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+RBE_OK, RBE_EINVAL, RBE_ENOMEM, RBE_ECUDA, RBE_ETIMEOUT, RBE_ENONFINITE, RBE_ESAMPLE, RBE_ESTATE = range(8)
+RBE_FP64, RBE_FP32_PHASE = 0, 1
+RBE_RHO_FP64, RBE_RHO_COMP32, RBE_RHO_FP32 = 0, 1, 2
+
+_lock = threading.Lock()
+_lib = None
+
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+
+# (name, restype, argtypes) of every exported symbol
+SIGNATURES = [
+    ("rbe_create", ctypes.c_int, [_dp, ctypes.c_double, ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(_vp)]),
+    ("rbe_destroy", ctypes.c_int, [_vp]),
+    ("rbe_set_stream", ctypes.c_int, [_vp, _vp]),
+    ("rbe_set_precision", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
+    ("rbe_set_box", ctypes.c_int, [_vp, _dp]),
+    ("rbe_sample_k", ctypes.c_int, [_vp, ctypes.c_uint64, _ip, _dp]),
+    ("rbe_kspace_forces_virial", ctypes.c_int, [_vp, ctypes.c_int64, _vp, _vp, ctypes.c_uint64, _vp, _vp, _vp]),
+    ("rbe_kspace_forces_virial_host", ctypes.c_int,
+     [_vp, ctypes.c_int64, _dp, _dp, ctypes.c_uint64, _dp, _dp, _dp]),
+    ("rbe_kspace_weighted", ctypes.c_int,
+     [_vp, ctypes.c_int64, _vp, _vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]),
+    ("rbe_get_rho", ctypes.c_int, [_vp, _dp, ctypes.c_int32]),
+    ("rbe_sync", ctypes.c_int, [_vp]),
+    ("rbe_set_kernel_timing", ctypes.c_int, [_vp, ctypes.c_int32]),
+    ("rbe_get_kernel_times", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float)]),
+    ("rbe_measure_pipe", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _dp]),
+    ("rbe_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("rbe_last_error", ctypes.c_char_p, [_vp]),
+    ("rbe_version", ctypes.c_int32, []),
+]
+
+
+class RBEError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(message)
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load librbe.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"librbe.so not found at {path}: build it with __graft_entry__.build()")
+            lib = ctypes.CDLL(path)
+            for name, res, args in SIGNATURES:
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(st: int, ctx=None):
+    if st != RBE_OK:
+        lib = load()
+        msg = lib.rbe_last_error(ctx).decode() if lib.rbe_last_error(ctx) else ""
+        raise RBEError(st, f"{lib.rbe_status_string(st).decode()}: {msg}")
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a
+
+
+# ---------------------------------------------------------------------------------
+# Functions with the C names.
+
+def rbe_create(box, alpha: float, P: int, seed: int):
+    lib = load()
+    b = _host(box, np.float64).reshape(3)
+    h = ctypes.c_void_p()
+    _check(lib.rbe_create(b.ctypes.data_as(_dp), float(alpha), int(P), int(seed), ctypes.byref(h)))
+    return h
+
+
+def rbe_destroy(h):
+    load().rbe_destroy(h)
+
+
+def rbe_set_stream(h, stream_handle: int):
+    _check(load().rbe_set_stream(h, ctypes.c_void_p(stream_handle)), h)
+
+
+def rbe_set_precision(h, precision: int, rho_accum: int = RBE_RHO_FP32):
+    _check(load().rbe_set_precision(h, int(precision), int(rho_accum)), h)
+
+
+def rbe_set_box(h, box):
+    b = _host(box, np.float64).reshape(3)
+    _check(load().rbe_set_box(h, b.ctypes.data_as(_dp)), h)
+
+
+def rbe_sample_k(h, step: int, P: int):
+    m = np.zeros((P, 3), dtype=np.int32)
+    S = ctypes.c_double(0.0)
+    _check(load().rbe_sample_k(h, int(step), m.ctypes.data_as(_ip), ctypes.byref(S)), h)
+    return m, S.value
+
+
+def rbe_kspace_forces_virial(h, positions, charges, step: int, forces_out, virial_out=None, energy_out=None):
+    N = int(charges.shape[0])
+    _check(load().rbe_kspace_forces_virial(h, N, _ptr(positions), _ptr(charges), int(step), _ptr(forces_out),
+                                           _ptr(virial_out), _ptr(energy_out)), h)
+
+
+def rbe_kspace_forces_virial_host(h, positions, charges, step: int, forces_out=None):
+    pos = _host(positions, np.float64)
+    q = _host(charges, np.float64)
+    N = int(q.shape[0])
+    F = np.zeros((N, 3)) if forces_out is None else forces_out
+    W = np.zeros(9)
+    E = np.zeros(2)
+    _check(load().rbe_kspace_forces_virial_host(h, N, pos.ctypes.data_as(_dp), q.ctypes.data_as(_dp), int(step),
+                                                F.ctypes.data_as(_dp), W.ctypes.data_as(_dp),
+                                                E.ctypes.data_as(_dp)), h)
+    return F, W.reshape(3, 3), E
+
+
+def rbe_kspace_weighted(h, positions, charges, m, weights, forces_out, virial_out=None, energy_out=None):
+    N = int(charges.shape[0])
+    K = int(weights.shape[0])
+    _check(load().rbe_kspace_weighted(h, N, _ptr(positions), _ptr(charges), K, _ptr(m), _ptr(weights),
+                                      _ptr(forces_out), _ptr(virial_out), _ptr(energy_out)), h)
+
+
+def rbe_get_rho(h, K: int):
+    out = np.zeros(2 * K)
+    _check(load().rbe_get_rho(h, out.ctypes.data_as(_dp), 2 * K), h)
+    return out[0::2] + 1j * out[1::2]
+
+
+def rbe_sync(h):
+    _check(load().rbe_sync(h), h)
+
+
+def rbe_set_kernel_timing(h, enable: bool):
+    _check(load().rbe_set_kernel_timing(h, int(bool(enable))), h)
+
+
+def rbe_get_kernel_times(h):
+    out = (ctypes.c_float * 4)()
+    _check(load().rbe_get_kernel_times(h, out), h)
+    return list(out)
+
+
+def rbe_measure_pipe(kind: int, iters: int = 4096) -> float:
+    v = ctypes.c_double(0.0)
+    _check(load().rbe_measure_pipe(int(kind), int(iters), ctypes.byref(v)))
+    return v.value
+
+
+def rbe_version() -> int:
+    return int(load().rbe_version())
+
+
+# ---------------------------------------------------------------------------------
+class Context:
+    """Owns one librbe context: box, alpha, batch size P and Philox seed."""
+
+    def __init__(self, box, alpha: float, P: int, seed: int, precision: int = RBE_FP64,
+                 rho_accum: int = RBE_RHO_FP32, stream=None):
+        self.P = int(P)
+        self.alpha = float(alpha)
+        self.h = rbe_create(box, alpha, P, seed)
+        rbe_set_precision(self.h, precision, rho_accum)
+        if stream is not None:
+            rbe_set_stream(self.h, stream)
+
+    def close(self):
+        if self.h is not None:
+            rbe_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_stream(self, stream_handle: int):
+        rbe_set_stream(self.h, stream_handle)
+
+    def set_precision(self, precision: int, rho_accum: int = RBE_RHO_FP32):
+        rbe_set_precision(self.h, precision, rho_accum)
+
+    def set_box(self, box):
+        rbe_set_box(self.h, box)
+
+    def sample_k(self, step: int):
+        return rbe_sample_k(self.h, step, self.P)
+
+    def forces_virial(self, positions, charges, step: int, forces_out, virial_out=None, energy_out=None):
+        rbe_kspace_forces_virial(self.h, positions, charges, step, forces_out, virial_out, energy_out)
+
+    def forces_virial_host(self, positions, charges, step: int):
+        return rbe_kspace_forces_virial_host(self.h, positions, charges, step)
+
+    def weighted(self, positions, charges, m, weights, forces_out, virial_out=None, energy_out=None):
+        rbe_kspace_weighted(self.h, positions, charges, m, weights, forces_out, virial_out, energy_out)
+
+    def rho(self, K: int | None = None):
+        return rbe_get_rho(self.h, self.P if K is None else K)
+
+    def sync(self):
+        rbe_sync(self.h)
+
+    def set_kernel_timing(self, enable: bool = True):
+        rbe_set_kernel_timing(self.h, enable)
+
+    def kernel_times(self):
+        return rbe_get_kernel_times(self.h)

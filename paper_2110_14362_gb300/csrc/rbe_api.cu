@@ -1,0 +1,395 @@
+// The C ABI of librbe (declared in include/rbe.h): argument validation, context
+// lifetime, device scratch, and the host-buffer variants.  The arithmetic lives in
+// rbe_kspace.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "rbe_context.h"
+#include "rbe_device.cuh"
+
+namespace rbe {
+
+static thread_local std::string g_create_error;
+
+rbe_status fail(rbe_ctx ctx, rbe_status st, const std::string& msg)
+{
+    if (ctx) ctx->last_error = msg;
+    else g_create_error = msg;
+    return st;
+}
+
+rbe_status cuda_fail(rbe_ctx ctx, cudaError_t err, const char* what)
+{
+    std::string msg = std::string(what) + ": " + cudaGetErrorName(err) + " (" + cudaGetErrorString(err) + ")";
+    return fail(ctx, err == cudaErrorMemoryAllocation ? RBE_ENOMEM : RBE_ECUDA, msg);
+}
+
+int host_axis_M(double alpha, double ell)
+{
+    const double c = (kPi * kPi) / (alpha * (ell * ell));
+    return (int)std::ceil(std::sqrt((60.0 * kLn2) / c));
+}
+
+// Makes ctx->device current for the duration of a call and restores the caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+static rbe_status check_box(rbe_ctx ctx, const double box[3], double alpha)
+{
+    if (!box) return fail(ctx, RBE_EINVAL, "box is NULL");
+    for (int t = 0; t < 3; ++t) {
+        if (!std::isfinite(box[t]) || !(box[t] > 0.0)) return fail(ctx, RBE_EINVAL, "box lengths must be finite and > 0");
+        const double c = (kPi * kPi) / (alpha * (box[t] * box[t]));
+        if (!(c <= 600.0))
+            return fail(ctx, RBE_EINVAL, "pi^2/(alpha l^2) > 600 on some axis: the frequency distribution is degenerate");
+        if (host_axis_M(alpha, box[t]) > (1 << 20))
+            return fail(ctx, RBE_EINVAL, "alpha l^2 too large: per-axis table would exceed 2^21 entries");
+    }
+    return RBE_OK;
+}
+
+// A pointer the current device can read: device or managed memory.
+static bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+static rbe_status check_dev(rbe_ctx ctx, const void* p, const char* name, bool required)
+{
+    if (!p) return required ? fail(ctx, RBE_EINVAL, std::string(name) + " is NULL") : RBE_OK;
+    if (reinterpret_cast<uintptr_t>(p) % 8 != 0) return fail(ctx, RBE_EINVAL, std::string(name) + " is not 8-byte aligned");
+    if (!is_device_ptr(p)) return fail(ctx, RBE_EINVAL, std::string(name) + " is not device memory");
+    return RBE_OK;
+}
+
+constexpr int64_t kMaxN = (int64_t(1) << 31) - 256;
+
+static rbe_status status_from_bits(rbe_ctx ctx, unsigned bits)
+{
+    if (bits & kStatusSample) return fail(ctx, RBE_ESAMPLE, "a frequency stayed m = 0 after 2^20 redraws");
+    if (bits & kStatusTable) return fail(ctx, RBE_ESTATE, "sampling table capacity exceeded on the device");
+    if (bits & kStatusTimeout) return fail(ctx, RBE_ETIMEOUT, "a bounded device wait gave up");
+    if (bits & kStatusNonFinite) return fail(ctx, RBE_ENONFINITE, "rho(k) or an output is not finite");
+    return RBE_OK;
+}
+
+static rbe_status sync_and_status(rbe_ctx ctx)
+{
+    cudaError_t err = cudaStreamSynchronize(ctx->stream);
+    if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaStreamSynchronize");
+    unsigned bits = 0;
+    err = cudaMemcpy(&bits, ctx->d.status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaMemcpy(status)");
+    if (bits) {
+        err = cudaMemset(ctx->d.status, 0, sizeof(unsigned));
+        if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaMemset(status)");
+    }
+    return status_from_bits(ctx, bits);
+}
+
+static void free_buffers(DeviceBuffers& d)
+{
+    cudaFree(d.cdf); cudaFree(d.hdr); cudaFree(d.m); cudaFree(d.w); cudaFree(d.rho); cudaFree(d.terms);
+    cudaFree(d.coef_m); cudaFree(d.coef_f); cudaFree(d.coef_d); cudaFree(d.partials); cudaFree(d.counter);
+    cudaFree(d.status); cudaFree(d.pos); cudaFree(d.q); cudaFree(d.F); cudaFree(d.WE);
+    d = DeviceBuffers{};
+}
+
+}  // namespace rbe
+
+using namespace rbe;
+
+extern "C" {
+
+rbe_status rbe_create(const double box[3], double alpha, int32_t P, uint64_t seed, rbe_ctx* out)
+{
+    if (!out) return fail(nullptr, RBE_EINVAL, "out is NULL");
+    if (!std::isfinite(alpha) || !(alpha > 0.0)) return fail(nullptr, RBE_EINVAL, "alpha must be finite and > 0");
+    if (P < 1 || P > 65536) return fail(nullptr, RBE_EINVAL, "P must be in [1, 65536]");
+    rbe_status st = check_box(nullptr, box, alpha);
+    if (st != RBE_OK) return st;
+    rbe_ctx ctx = new (std::nothrow) rbe_ctx_s();
+    if (!ctx) return fail(nullptr, RBE_ENOMEM, "host allocation failed");
+    cudaError_t err = cudaGetDevice(&ctx->device);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (err != cudaSuccess) {
+        std::string msg = std::string("no usable CUDA device: ") + cudaGetErrorString(err);
+        delete ctx;
+        return fail(nullptr, RBE_ECUDA, msg);
+    }
+    for (int t = 0; t < 3; ++t) ctx->box[t] = box[t];
+    ctx->alpha = alpha;
+    ctx->P = P;
+    ctx->seed = seed;
+    DeviceBuffers& d = ctx->d;
+    if ((err = cudaMalloc(&d.hdr, sizeof(TableHeader))) != cudaSuccess ||
+        (err = cudaMalloc(&d.counter, sizeof(unsigned))) != cudaSuccess ||
+        (err = cudaMalloc(&d.status, sizeof(unsigned))) != cudaSuccess ||
+        (err = cudaMemset(d.counter, 0, sizeof(unsigned))) != cudaSuccess ||
+        (err = cudaMemset(d.status, 0, sizeof(unsigned))) != cudaSuccess) {
+        std::string msg = std::string("device allocation failed: ") + cudaGetErrorString(err);
+        free_buffers(d);
+        delete ctx;
+        return fail(nullptr, err == cudaErrorMemoryAllocation ? RBE_ENOMEM : RBE_ECUDA, msg);
+    }
+    st = ensure_k_capacity(ctx, P);
+    if (st == RBE_OK) st = ensure_tables(ctx);
+    if (st == RBE_OK && (err = cudaDeviceSynchronize()) != cudaSuccess) st = cuda_fail(ctx, err, "rbe_create");
+    if (st != RBE_OK) {
+        std::string msg = ctx->last_error;
+        free_buffers(d);
+        delete ctx;
+        return fail(nullptr, st, msg);
+    }
+    *out = ctx;
+    return RBE_OK;
+}
+
+rbe_status rbe_destroy(rbe_ctx ctx)
+{
+    if (!ctx) return RBE_OK;
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    free_buffers(ctx->d);
+    delete ctx;
+    return RBE_OK;
+}
+
+rbe_status rbe_set_stream(rbe_ctx ctx, void* stream)
+{
+    if (!ctx) return RBE_EINVAL;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    return RBE_OK;
+}
+
+rbe_status rbe_set_precision(rbe_ctx ctx, int32_t precision, int32_t rho_accum)
+{
+    if (!ctx) return RBE_EINVAL;
+    if (precision != RBE_FP64 && precision != RBE_FP32_PHASE) return fail(ctx, RBE_EINVAL, "unknown precision");
+    if (rho_accum != RBE_RHO_FP64 && rho_accum != RBE_RHO_COMP32 && rho_accum != RBE_RHO_FP32)
+        return fail(ctx, RBE_EINVAL, "unknown rho accumulation");
+    ctx->precision = precision;
+    ctx->rho_accum = rho_accum;
+    return RBE_OK;
+}
+
+rbe_status rbe_set_box(rbe_ctx ctx, const double box[3])
+{
+    if (!ctx) return RBE_EINVAL;
+    rbe_status st = check_box(ctx, box, ctx->alpha);
+    if (st != RBE_OK) return st;
+    for (int t = 0; t < 3; ++t) {
+        if (ctx->box[t] != box[t]) ctx->tables_dirty = true;
+        ctx->box[t] = box[t];
+    }
+    return RBE_OK;
+}
+
+rbe_status rbe_sample_k(rbe_ctx ctx, uint64_t step, int32_t* m_out, double* S_out)
+{
+    if (!ctx) return RBE_EINVAL;
+    if ((step >> 56) != 0) return fail(ctx, RBE_EINVAL, "step must be < 2^56");
+    DeviceGuard g(ctx->device);
+    rbe_status st = launch_sample(ctx, step, ctx->P);
+    if (st != RBE_OK) return st;
+    std::vector<int4> m(ctx->P);
+    TableHeader h;
+    cudaError_t err = cudaMemcpyAsync(m.data(), ctx->d.m, sizeof(int4) * ctx->P, cudaMemcpyDeviceToHost, ctx->stream);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(&h, ctx->d.hdr, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
+    if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaMemcpyAsync(sample)");
+    st = sync_and_status(ctx);
+    if (st != RBE_OK) return st;
+    if (m_out)
+        for (int l = 0; l < ctx->P; ++l) {
+            m_out[3 * l] = m[l].x;
+            m_out[3 * l + 1] = m[l].y;
+            m_out[3 * l + 2] = m[l].z;
+        }
+    if (S_out) *S_out = h.S;
+    return RBE_OK;
+}
+
+rbe_status rbe_kspace_forces_virial(rbe_ctx ctx, int64_t N, const double* positions, const double* charges,
+                                    uint64_t step, double* forces_out, double* virial_out, double* energy_out)
+{
+    if (!ctx) return RBE_EINVAL;
+    if (N < 0 || N > kMaxN) return fail(ctx, RBE_EINVAL, "N out of range [0, 2^31 - 256]");
+    if ((step >> 56) != 0) return fail(ctx, RBE_EINVAL, "step must be < 2^56");
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(ctx, RBE_ECUDA, "cannot select the context's device");
+    rbe_status st;
+    if ((st = check_dev(ctx, positions, "positions", N > 0)) != RBE_OK) return st;
+    if ((st = check_dev(ctx, charges, "charges", N > 0)) != RBE_OK) return st;
+    if ((st = check_dev(ctx, forces_out, "forces_out", N > 0)) != RBE_OK) return st;
+    if ((st = check_dev(ctx, virial_out, "virial_out", false)) != RBE_OK) return st;
+    if ((st = check_dev(ctx, energy_out, "energy_out", false)) != RBE_OK) return st;
+    st = launch_sample(ctx, step, ctx->P);
+    if (st != RBE_OK) return st;
+    return launch_evaluate(ctx, N, positions, charges, ctx->P, true, forces_out, virial_out, energy_out);
+}
+
+rbe_status rbe_kspace_forces_virial_host(rbe_ctx ctx, int64_t N, const double* positions, const double* charges,
+                                         uint64_t step, double* forces_out, double* virial_out,
+                                         double* energy_out)
+{
+    if (!ctx) return RBE_EINVAL;
+    if (N < 0 || N > kMaxN) return fail(ctx, RBE_EINVAL, "N out of range [0, 2^31 - 256]");
+    if ((step >> 56) != 0) return fail(ctx, RBE_EINVAL, "step must be < 2^56");
+    if (N > 0 && (!positions || !charges)) return fail(ctx, RBE_EINVAL, "positions/charges are NULL");
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(ctx, RBE_ECUDA, "cannot select the context's device");
+    DeviceBuffers& d = ctx->d;
+    cudaError_t err;
+    if (!d.WE && (err = cudaMalloc(&d.WE, 11 * sizeof(double))) != cudaSuccess)
+        return cuda_fail(ctx, err, "cudaMalloc(host-call outputs)");
+    if (N > d.ncap) {
+        cudaFree(d.pos); cudaFree(d.q); cudaFree(d.F);
+        d.pos = d.q = d.F = nullptr;
+        d.ncap = 0;
+        if ((err = cudaMalloc(&d.pos, sizeof(double) * 3 * N)) != cudaSuccess ||
+            (err = cudaMalloc(&d.q, sizeof(double) * N)) != cudaSuccess ||
+            (err = cudaMalloc(&d.F, sizeof(double) * 3 * N)) != cudaSuccess)
+            return cuda_fail(ctx, err, "cudaMalloc(host-call staging)");
+        d.ncap = N;
+    }
+    cudaStream_t s = ctx->stream;
+    if (N > 0) {
+        if ((err = cudaMemcpyAsync(d.pos, positions, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+            (err = cudaMemcpyAsync(d.q, charges, sizeof(double) * N, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return cuda_fail(ctx, err, "cudaMemcpyAsync(H2D)");
+    }
+    rbe_status st = launch_sample(ctx, step, ctx->P);
+    if (st != RBE_OK) return st;
+    st = launch_evaluate(ctx, N, d.pos, d.q, ctx->P, true, d.F, d.WE, d.WE + 9);
+    if (st != RBE_OK) return st;
+    if (forces_out && N > 0 &&
+        (err = cudaMemcpyAsync(forces_out, d.F, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(ctx, err, "cudaMemcpyAsync(D2H forces)");
+    double we[11];
+    if ((err = cudaMemcpyAsync(we, d.WE, sizeof(we), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(ctx, err, "cudaMemcpyAsync(D2H virial)");
+    st = sync_and_status(ctx);
+    if (st != RBE_OK) return st;
+    if (virial_out) std::memcpy(virial_out, we, 9 * sizeof(double));
+    if (energy_out) std::memcpy(energy_out, we + 9, 2 * sizeof(double));
+    return RBE_OK;
+}
+
+rbe_status rbe_kspace_weighted(rbe_ctx ctx, int64_t N, const double* positions, const double* charges, int32_t K,
+                               const int32_t* m, const double* weights, double* forces_out, double* virial_out,
+                               double* energy_out)
+{
+    if (!ctx) return RBE_EINVAL;
+    if (N < 0 || N > kMaxN) return fail(ctx, RBE_EINVAL, "N out of range [0, 2^31 - 256]");
+    if (K < 1 || K > (1 << 24)) return fail(ctx, RBE_EINVAL, "K must be in [1, 2^24]");
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(ctx, RBE_ECUDA, "cannot select the context's device");
+    rbe_status st;
+    if ((st = check_dev(ctx, positions, "positions", N > 0)) != RBE_OK) return st;
+    if ((st = check_dev(ctx, charges, "charges", N > 0)) != RBE_OK) return st;
+    if ((st = check_dev(ctx, forces_out, "forces_out", N > 0)) != RBE_OK) return st;
+    if ((st = check_dev(ctx, virial_out, "virial_out", false)) != RBE_OK) return st;
+    if ((st = check_dev(ctx, energy_out, "energy_out", false)) != RBE_OK) return st;
+    if (!m || (reinterpret_cast<uintptr_t>(m) % 4) != 0 || !is_device_ptr(m))
+        return fail(ctx, RBE_EINVAL, "m must be 4-byte aligned device memory");
+    if ((st = check_dev(ctx, weights, "weights", true)) != RBE_OK) return st;
+    st = launch_weights_from_list(ctx, K, m, weights);
+    if (st != RBE_OK) return st;
+    return launch_evaluate(ctx, N, positions, charges, K, false, forces_out, virial_out, energy_out);
+}
+
+rbe_status rbe_get_rho(rbe_ctx ctx, double* rho_out, int32_t capacity)
+{
+    if (!ctx) return RBE_EINVAL;
+    if (!rho_out) return fail(ctx, RBE_EINVAL, "rho_out is NULL");
+    if (ctx->last_K <= 0) return fail(ctx, RBE_ESTATE, "no evaluation has run on this context");
+    if (capacity < 2 * ctx->last_K) return fail(ctx, RBE_EINVAL, "capacity < 2 * K");
+    DeviceGuard g(ctx->device);
+    cudaError_t err = cudaMemcpyAsync(rho_out, ctx->d.rho, sizeof(double2) * ctx->last_K, cudaMemcpyDeviceToHost,
+                                      ctx->stream);
+    if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaMemcpyAsync(rho)");
+    return sync_and_status(ctx);
+}
+
+rbe_status rbe_set_kernel_timing(rbe_ctx ctx, int32_t enable)
+{
+    if (!ctx) return RBE_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (enable && !ctx->ev[0])
+        for (auto& e : ctx->ev) {
+            cudaError_t err = cudaEventCreate(&e);
+            if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaEventCreate");
+        }
+    ctx->timing = enable != 0;
+    return RBE_OK;
+}
+
+rbe_status rbe_get_kernel_times(rbe_ctx ctx, float ms_out[4])
+{
+    if (!ctx || !ms_out) return RBE_EINVAL;
+    if (!ctx->timing || ctx->last_K <= 0) return fail(ctx, RBE_ESTATE, "kernel timing is off or nothing ran");
+    DeviceGuard g(ctx->device);
+    cudaError_t err = cudaEventSynchronize(ctx->ev[4]);
+    if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaEventSynchronize");
+    for (int j = 0; j < 4; ++j) {
+        err = cudaEventElapsedTime(&ms_out[j], ctx->ev[j], ctx->ev[j + 1]);
+        if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaEventElapsedTime");
+    }
+    return RBE_OK;
+}
+
+rbe_status rbe_sync(rbe_ctx ctx)
+{
+    if (!ctx) return RBE_EINVAL;
+    DeviceGuard g(ctx->device);
+    return sync_and_status(ctx);
+}
+
+const char* rbe_status_string(rbe_status status)
+{
+    switch (status) {
+    case RBE_OK: return "RBE_OK";
+    case RBE_EINVAL: return "RBE_EINVAL: invalid argument";
+    case RBE_ENOMEM: return "RBE_ENOMEM: allocation failed";
+    case RBE_ECUDA: return "RBE_ECUDA: CUDA runtime error";
+    case RBE_ETIMEOUT: return "RBE_ETIMEOUT: bounded device wait gave up";
+    case RBE_ENONFINITE: return "RBE_ENONFINITE: non-finite rho or output";
+    case RBE_ESAMPLE: return "RBE_ESAMPLE: frequency sampling did not find m != 0";
+    case RBE_ESTATE: return "RBE_ESTATE: call not valid in this state";
+    }
+    return "unknown rbe_status";
+}
+
+const char* rbe_last_error(rbe_ctx ctx)
+{
+    return ctx ? ctx->last_error.c_str() : g_create_error.c_str();
+}
+
+int32_t rbe_version(void) { return 100; }
+
+}  // extern "C"

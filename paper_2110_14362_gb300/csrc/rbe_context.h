@@ -1,0 +1,93 @@
+// Host-side state of an RBE context and the launchers shared by the library's
+// translation units.  Not part of the public ABI (include/rbe.h is).
+#pragma once
+
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/rbe.h"
+
+namespace rbe {
+
+// Per-axis sampling tables: M, H and S, written on the device.
+struct TableHeader {
+    int M[3];
+    int pad;
+    double H[3];
+    double S;
+};
+
+// Launch plan of the N x K pair kernels (chosen by plan_* in rbe_kspace.cu).
+struct Plan {
+    int kpt;        // frequencies per thread in the rho pass
+    int ktiles;     // frequency tiles in the rho pass
+    int nchunks;    // particle chunks in the rho pass
+    int chunk_len;  // particles per chunk (a multiple of the staging tile)
+    int ppt;        // particles per thread in the force pass
+    int fblocks;    // blocks of the force pass
+};
+
+struct DeviceBuffers {
+    double* cdf = nullptr;            // [3][tab_cap] cumulative weights
+    int tab_cap = 0;                  // entries per axis (>= 2M+1)
+    TableHeader* hdr = nullptr;
+    int4* m = nullptr;                // [kcap] (mx, my, mz, 0)
+    double* w = nullptr;              // [kcap] per-frequency weight (S/P for RBE)
+    double2* rho = nullptr;           // [kcap]
+    double* terms = nullptr;          // [kcap + 1][8] per-frequency energy/virial terms
+    int4* coef_m = nullptr;           // [kcap] FP32 force data (mx, my, mz, bits of A)
+    float4* coef_f = nullptr;         // [kcap] FP32 force data (B, mx, my, mz)
+    double2* coef_d = nullptr;        // [kcap] FP64 force data (A, B)
+    int kcap = 0;
+    double2* partials = nullptr;      // [(K + 1) * nchunks]
+    size_t part_cap = 0;              // in double2
+    unsigned* counter = nullptr;      // last-block counter of the reduction
+    unsigned* status = nullptr;       // latched device status bits
+    double* pos = nullptr;            // host-API staging
+    double* q = nullptr;
+    double* F = nullptr;
+    double* WE = nullptr;             // 11 doubles: virial (9) + energy (2)
+    int64_t ncap = 0;
+};
+
+}  // namespace rbe
+
+struct rbe_ctx_s {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    double box[3] = {0, 0, 0};
+    double alpha = 0;
+    int32_t P = 0;
+    uint64_t seed = 0;
+    int32_t precision = RBE_FP64;
+    int32_t rho_accum = RBE_RHO_FP32;
+    bool tables_dirty = true;
+    int32_t last_K = 0;
+    bool timing = false;             // record CUDA events around each evaluation kernel
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    rbe::DeviceBuffers d;
+    std::string last_error;
+};
+
+namespace rbe {
+
+// Device validation helpers (rbe_api.cu).
+rbe_status fail(rbe_ctx ctx, rbe_status st, const std::string& msg);
+rbe_status cuda_fail(rbe_ctx ctx, cudaError_t err, const char* what);
+
+// Host-side rule shared by create/set_box: the per-axis table size for (alpha, l).
+int host_axis_M(double alpha, double ell);
+
+// Launchers (rbe_kspace.cu).  All asynchronous on ctx->stream.
+rbe_status ensure_tables(rbe_ctx ctx);
+rbe_status ensure_k_capacity(rbe_ctx ctx, int K);
+rbe_status launch_sample(rbe_ctx ctx, uint64_t step, int P);
+rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int K,
+                           bool uniform_weight, double* F, double* W, double* E);
+void record_event(rbe_ctx ctx, int idx);
+rbe_status launch_weights_from_list(rbe_ctx ctx, int K, const int32_t* m, const double* w);
+
+}  // namespace rbe

@@ -1,0 +1,106 @@
+// Device-side building blocks of the RBE k-space path (sm_103a).
+//
+//  * Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) for the counter-based sampler.
+//  * A Cody--Waite + Taylor exponential for the sampler's weight table, written with
+//    explicitly rounded double operations so that no multiply-add is contracted.
+//  * Fixed-point scaled coordinates: s = r / l mod 1 as a 32-bit fraction, so that the
+//    phase m.s mod 1 is exact in wrapping 32-bit integer arithmetic.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rbe {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kLn2 = 0.69314718055994530942;
+constexpr uint32_t kMaxAttempts = 1u << 20;
+
+// Status bits latched on the device.
+constexpr unsigned kStatusSample = 1u;     // a sample stayed at m = 0 for kMaxAttempts redraws
+constexpr unsigned kStatusNonFinite = 2u;  // rho or an output is NaN/Inf
+constexpr unsigned kStatusTable = 4u;      // the sampling table did not fit its capacity
+constexpr unsigned kStatusTimeout = 8u;    // a bounded wait gave up
+
+// ---------------------------------------------------------------------------------
+// Philox-4x32-10: ten rounds; each multiplies words 0 and 2 by 0xD2511F53 and
+// 0xCD9E8D57 (32x32 -> 64 bits), xors the high halves with words 1 and 3 and the round
+// key, and permutes; the key advances by 0x9E3779B9 and 0xBB67AE85 between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// 53-bit uniform in [0, 1): all of a and the top 21 bits of b.
+__device__ __forceinline__ double uniform53(uint32_t a, uint32_t b)
+{
+    const unsigned long long bits = ((unsigned long long)a << 21) | (unsigned long long)(b >> 11);
+    return __dmul_rn((double)bits, 0x1.0p-53);
+}
+
+// ---------------------------------------------------------------------------------
+// exp(x) for x in [-700, 0]: n = rint(x / ln2), r = (x - n ln2_hi) - n ln2_lo with a
+// 32-significant-bit head of ln2 (n * head exact), e^r by its Taylor series to degree 13
+// in Horner form, times 2^n.  Every step is a separately rounded IEEE operation.
+__device__ __forceinline__ double table_exp(double x)
+{
+    const double inv_ln2 = 0x1.71547652b82fep+0;
+    const double ln2_hi = 0x1.62e42fee00000p-1;
+    const double ln2_lo = 0x1.a39ef35793c76p-33;
+    const double c[14] = {0x1.0000000000000p+0, 0x1.0000000000000p+0, 0x1.0000000000000p-1,
+                          0x1.5555555555555p-3, 0x1.5555555555555p-5, 0x1.1111111111111p-7,
+                          0x1.6c16c16c16c17p-10, 0x1.a01a01a01a01ap-13, 0x1.a01a01a01a01ap-16,
+                          0x1.71de3a556c734p-19, 0x1.27e4fb7789f5cp-22, 0x1.ae64567f544e4p-26,
+                          0x1.1eed8eff8d898p-29, 0x1.6124613a86d09p-33};
+    const double n = rint(__dmul_rn(x, inv_ln2));
+    const double r = __dsub_rn(__dsub_rn(x, __dmul_rn(n, ln2_hi)), __dmul_rn(n, ln2_lo));
+    double p = c[13];
+#pragma unroll
+    for (int j = 12; j >= 0; --j) p = __dadd_rn(__dmul_rn(p, r), c[j]);
+    return ldexp(p, (int)n);
+}
+
+// c = pi^2 / (alpha l^2), the per-axis exponent of exp(-|k|^2 / 4 alpha) in m.
+__device__ __forceinline__ double axis_c(double alpha, double ell)
+{
+    return __ddiv_rn(__dmul_rn(kPi, kPi), __dmul_rn(alpha, __dmul_rn(ell, ell)));
+}
+
+// Truncation |m| <= M = ceil(sqrt(60 ln2 / c)): drops weights below 2^-60 of the peak.
+__device__ __forceinline__ int axis_M(double c)
+{
+    return (int)ceil(__dsqrt_rn(__ddiv_rn(__dmul_rn(60.0, kLn2), c)));
+}
+
+// ---------------------------------------------------------------------------------
+// 32-bit fixed-point fraction of r / l (wrapping: any real r maps into [0, 2^32)).
+__device__ __forceinline__ uint32_t fixed_frac(double r, double inv_l)
+{
+    return (uint32_t)(unsigned long long)__double2ll_rn(__dmul_rn(r, inv_l) * 4294967296.0);
+}
+
+// Phase of m.s for 32-bit fixed-point s, as an angle in [-pi, pi) (FP32).
+// t = m.s + 2^8 (mod 2^32) is exact; the top 23 bits of t + 2^31 become the mantissa of
+// a float in [1, 2) that encodes (t / 2^32 + 1/2) mod 1 rounded to 2^-23 revolutions.
+__device__ __forceinline__ float fixed_phase(int mx, int my, int mz, uint32_t sx, uint32_t sy, uint32_t sz)
+{
+    uint32_t t = (uint32_t)mx * sx + 256u;
+    t += (uint32_t)my * sy;
+    t += (uint32_t)mz * sz;
+    const uint32_t bits = ((t >> 9) ^ 0x00400000u) | 0x3f800000u;
+    return (__uint_as_float(bits) - 1.5f) * 6.28318530717958647692f;
+}
+
+}  // namespace rbe
