@@ -21,12 +21,13 @@ struct TableHeader {
 
 // Launch plan of the N x K pair kernels (chosen by plan_* in rbe_kspace.cu).
 struct Plan {
-    int kpt;        // frequencies per thread in the rho pass
-    int ktiles;     // frequency tiles in the rho pass
-    int nchunks;    // particle chunks in the rho pass
-    int chunk_len;  // particles per chunk (a multiple of the staging tile)
-    int ppt;        // particles per thread in the force pass
-    int fblocks;    // blocks of the force pass
+    int ktiles;         // frequency tiles in the rho pass (one thread per frequency)
+    int kthreads;       // threads per rho block: whole warps, <= 256
+    int nchunks;        // particle chunks in the rho pass
+    int64_t chunk_len;  // particles per chunk
+    int ppt;            // particles per thread in the force pass
+    int fblocks;        // blocks of the force pass
+    int64_t per_block;  // particles per force block
 };
 
 struct DeviceBuffers {

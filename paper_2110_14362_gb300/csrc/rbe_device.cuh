@@ -92,15 +92,21 @@ __device__ __forceinline__ uint32_t fixed_frac(double r, double inv_l)
 }
 
 // Phase of m.s for 32-bit fixed-point s, as an angle in [-pi, pi) (FP32).
-// t = m.s + 2^8 (mod 2^32) is exact; the top 23 bits of t + 2^31 become the mantissa of
-// a float in [1, 2) that encodes (t / 2^32 + 1/2) mod 1 rounded to 2^-23 revolutions.
-__device__ __forceinline__ float fixed_phase(int mx, int my, int mz, uint32_t sx, uint32_t sy, uint32_t sz)
+// t = m.s + 2^31 + 2^8 (mod 2^32) is exact; one IMAD.HI by mul23 = 2^23 (passed at run
+// time so that it stays a multiply) adds 0x3f800000 to the top 23 bits of t, giving a
+// float f in [1, 2) with f - 1 = (m.s + 1/2) mod 1 rounded to 2^-23 revolutions; one FFMA
+// maps it to 2 pi (f - 1.5).  The FP32 constants 2 pi and 3 pi shift every angle by the
+// same ~2.4e-7 rad (plus a relative 3e-8 scale error); a common shift of all phases
+// multiplies rho(k) by a unit phase factor that cancels in |rho|^2 and in
+// Im(e^{-ik.r} rho(k)), so it leaves forces, energy and virial unchanged.
+__device__ __forceinline__ float fixed_phase(int mx, int my, int mz, uint32_t sx, uint32_t sy, uint32_t sz,
+                                             uint32_t mul23)
 {
-    uint32_t t = (uint32_t)mx * sx + 256u;
+    uint32_t t = (uint32_t)mx * sx + 0x80000100u;
     t += (uint32_t)my * sy;
     t += (uint32_t)mz * sz;
-    const uint32_t bits = ((t >> 9) ^ 0x00400000u) | 0x3f800000u;
-    return (__uint_as_float(bits) - 1.5f) * 6.28318530717958647692f;
+    const uint32_t bits = __umulhi(t, mul23) + 0x3f800000u;
+    return fmaf(__uint_as_float(bits), 6.28318530717958647692f, -9.42477796076937971538f);
 }
 
 }  // namespace rbe
