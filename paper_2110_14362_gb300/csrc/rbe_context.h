@@ -17,6 +17,7 @@ struct TableHeader {
     int pad;
     double H[3];
     double S;
+    double wP;  // S / P
 };
 
 // Launch plan of the N x K pair kernels (chosen by plan_* in rbe_kspace.cu).
@@ -42,8 +43,8 @@ struct DeviceBuffers {
     float4* coef_f = nullptr;         // [kcap] FP32 force data (B, mx, my, mz)
     double2* coef_d = nullptr;        // [kcap] FP64 force data (A, B)
     int kcap = 0;
-    double2* partials = nullptr;      // [(K + 1) * nchunks]
-    size_t part_cap = 0;              // in double2
+    void* partials = nullptr;         // [(K + 1) * nchunks] double2 (FP64) or float4 (FP32-phase)
+    size_t part_cap = 0;              // in 16-byte entries
     unsigned* counter = nullptr;      // last-block counter of the reduction
     unsigned* status = nullptr;       // latched device status bits
     double* pos = nullptr;            // host-API staging

@@ -23,6 +23,16 @@ constexpr unsigned kStatusTable = 4u;      // the sampling table did not fit its
 constexpr unsigned kStatusTimeout = 8u;    // a bounded wait gave up
 
 // ---------------------------------------------------------------------------------
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while its predecessor in the stream is still running;
+// pdl_wait() blocks until the predecessor grid has completed and its writes are visible
+// (it returns at once for a normal launch).  pdl_trigger() lets the successor launch.
+// Every kernel here reads its predecessor's outputs, and writes global memory, only
+// after pdl_wait().
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------------
 // Philox-4x32-10: ten rounds; each multiplies words 0 and 2 by 0xD2511F53 and
 // 0xCD9E8D57 (32x32 -> 64 bits), xors the high halves with words 1 and 3 and the round
 // key, and permutes; the key advances by 0x9E3779B9 and 0xBB67AE85 between rounds.
@@ -92,21 +102,152 @@ __device__ __forceinline__ uint32_t fixed_frac(double r, double inv_l)
 }
 
 // Phase of m.s for 32-bit fixed-point s, as an angle in [-pi, pi) (FP32).
-// t = m.s + 2^31 + 2^8 (mod 2^32) is exact; one IMAD.HI by mul23 = 2^23 (passed at run
-// time so that it stays a multiply) adds 0x3f800000 to the top 23 bits of t, giving a
-// float f in [1, 2) with f - 1 = (m.s + 1/2) mod 1 rounded to 2^-23 revolutions; one FFMA
-// maps it to 2 pi (f - 1.5).  The FP32 constants 2 pi and 3 pi shift every angle by the
-// same ~2.4e-7 rad (plus a relative 3e-8 scale error); a common shift of all phases
-// multiplies rho(k) by a unit phase factor that cancels in |rho|^2 and in
-// Im(e^{-ik.r} rho(k)), so it leaves forces, energy and virial unchanged.
-__device__ __forceinline__ float fixed_phase(int mx, int my, int mz, uint32_t sx, uint32_t sy, uint32_t sz,
-                                             uint32_t mul23)
+// t = m.s + 2^31 + 2^8 (mod 2^32) is exact; its top 23 bits under the exponent bits of
+// 1.0f give a float f in [1, 2) with f - 1 = (m.s + 1/2) mod 1 rounded to 2^-23
+// revolutions, and one FFMA maps it to 2 pi (f - 1.5).  The FP32 constants 2 pi and
+// 3 pi shift every angle by the same ~2.4e-7 rad (plus a relative 3e-8 scale error); a
+// common shift of all phases multiplies rho(k) by a unit phase factor that cancels in
+// |rho|^2 and in Im(e^{-ik.r} rho(k)), so it leaves forces, energy and virial unchanged.
+__device__ __forceinline__ float fixed_phase(int mx, int my, int mz, uint32_t sx, uint32_t sy, uint32_t sz)
 {
     uint32_t t = (uint32_t)mx * sx + 0x80000100u;
     t += (uint32_t)my * sy;
     t += (uint32_t)mz * sz;
-    const uint32_t bits = __umulhi(t, mul23) + 0x3f800000u;
-    return fmaf(__uint_as_float(bits), 6.28318530717958647692f, -9.42477796076937971538f);
+    return fmaf(__uint_as_float((t >> 9) | 0x3f800000u), 6.28318530717958647692f, -9.42477796076937971538f);
+}
+
+// ---------------------------------------------------------------------------------
+// Integer-only conversions.  GB300 executes FP64 instructions on a narrow pipe (about
+// 1.7 FP64 FMA per clock per SM), so the FP32-phase path converts its FP64 inputs with
+// 32/64-bit integer operations on the IEEE bit patterns instead.
+
+// 1/l as a 64-bit mantissa and a power of two: 1/l = q * 2^e, q in [2^63, 2^64).
+struct FixScale {
+    unsigned long long q;
+    int e;
+};
+
+// round(r / l * 2^32) mod 2^32 for a finite double r (zero/subnormal r -> 0): the
+// 117-bit product of r's 53-bit mantissa and q, shifted and rounded to nearest.
+__host__ __device__ inline uint32_t fixed_frac_int(unsigned long long rb, FixScale sc)
+{
+    const unsigned er = (unsigned)(rb >> 52) & 0x7ffu;
+    if (er == 0u || er == 0x7ffu) return 0u;
+    const unsigned long long mr = (rb & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = (int)er - 1075 + sc.e + 32;  // r / l * 2^32 = mr * q * 2^sh
+#ifdef __CUDA_ARCH__
+    const unsigned long long hi = __umul64hi(mr, sc.q);
+#else
+    const unsigned long long hi = (unsigned long long)(((unsigned __int128)mr * sc.q) >> 64);
+#endif
+    const unsigned long long lo = mr * sc.q;
+    uint32_t res;
+    if (sh >= 0) {
+        res = sh >= 32 ? 0u : (uint32_t)(lo << sh);
+    } else {
+        const int d = -sh;
+        unsigned long long lo2 = lo, hi2 = hi;
+        if (d <= 64) {
+            lo2 = lo + (1ull << (d - 1));
+            hi2 = hi + (lo2 < lo ? 1ull : 0ull);
+        } else if (d < 128) {
+            hi2 = hi + (1ull << (d - 65));
+        }
+        if (d < 64) res = (uint32_t)((lo2 >> d) | (hi2 << (64 - d)));
+        else if (d < 128) res = (uint32_t)(hi2 >> (d - 64));
+        else res = 0u;
+    }
+    return (rb >> 63) ? 0u - res : res;
+}
+
+// Nearest float to a double (round half to even); zero/subnormal -> signed zero,
+// overflow -> infinity, NaN stays NaN.  Integer operations only.
+__host__ __device__ inline float double_to_float_int(unsigned long long b)
+{
+    const uint32_t sign = (uint32_t)(b >> 63) << 31;
+    const int e = (int)((b >> 52) & 0x7ff);
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    uint32_t out;
+    if (e == 0x7ff) {
+        out = sign | 0x7f800000u | (m ? 0x400000u : 0u);
+    } else {
+        int fe = e - 1023 + 127;
+        if (e == 0 || fe <= 0) {
+            out = sign;
+        } else {
+            uint32_t mant = (uint32_t)(m >> 29);
+            const uint32_t rem = (uint32_t)(m & 0x1FFFFFFFu);
+            if (rem > 0x10000000u || (rem == 0x10000000u && (mant & 1u))) {
+                if (++mant == 0x800000u) {
+                    mant = 0u;
+                    ++fe;
+                }
+            }
+            out = fe >= 255 ? (sign | 0x7f800000u) : (sign | ((uint32_t)fe << 23) | mant);
+        }
+    }
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(out);
+#else
+    float f;
+    __builtin_memcpy(&f, &out, 4);
+    return f;
+#endif
+}
+
+// The double equal to a float (exact), with integer operations only.
+__host__ __device__ inline unsigned long long float_to_double_bits(uint32_t b)
+{
+    const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+    int e = (int)((b >> 23) & 0xff);
+    uint32_t m = b & 0x7fffffu;
+    if (e == 0xff) return sign | (0x7ffull << 52) | ((unsigned long long)m << 29);
+    if (e == 0) {
+        if (m == 0u) return sign;
+        int lz = 0;  // subnormal float: normalise
+        while (!(m & 0x800000u)) {
+            m <<= 1;
+            ++lz;
+        }
+        m &= 0x7fffffu;
+        e = 1 - lz;
+    }
+    return sign | ((unsigned long long)(e - 127 + 1023) << 52) | ((unsigned long long)m << 29);
+}
+
+// Exponent field == 0x7ff: infinity or NaN.
+__host__ __device__ inline bool nonfinite_bits(unsigned long long b)
+{
+    return ((b >> 52) & 0x7ffull) == 0x7ffull;
+}
+
+// Float-float accumulation (Knuth's TwoSum): (hi, lo) += x with the rounding error of
+// the FP32 addition carried in lo; about 48 significant bits from FP32 operations.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float x)
+{
+    const float s = hi + x;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (x - bb);
+    hi = s;
+    lo += err;
+}
+
+// (hi, lo) += (xh, xl)
+__device__ __forceinline__ void ff_add2(float& hi, float& lo, float xh, float xl)
+{
+    ff_add(hi, lo, xh);
+    lo += xl;
+}
+
+// 53-bit uniform u = (a << 21 | b >> 11) * 2^-53 as the bit pattern of a double, built
+// with integer operations (exact, the same value as the FP64 conversion).
+__device__ __forceinline__ unsigned long long uniform53_bits(uint32_t a, uint32_t b)
+{
+    const unsigned long long v = ((unsigned long long)a << 21) | (unsigned long long)(b >> 11);
+    if (v == 0ull) return 0ull;
+    const int shift = __clzll(v) - 11;
+    const unsigned long long mant = v << shift;
+    return ((unsigned long long)(1022 - shift) << 52) | (mant & 0xFFFFFFFFFFFFFull);
 }
 
 }  // namespace rbe

@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 
 #include "rbe_context.h"
 #include "rbe_device.cuh"
@@ -28,7 +29,7 @@ constexpr int kForceKT = 256;  // frequencies staged per tile in the force pass
 // =================================================================================
 // Sampling tables (Sec. 4.2 Eqs. (S), (psf); App. C item 1).
 __global__ void k_tables(double bx, double by, double bz, const double* __restrict__ box_dev, double alpha,
-                         double* __restrict__ cdf, int cap, TableHeader* __restrict__ hdr,
+                         int P, double* __restrict__ cdf, int cap, TableHeader* __restrict__ hdr,
                          unsigned* __restrict__ status)
 {
     __shared__ int sM[3];
@@ -69,13 +70,19 @@ __global__ void k_tables(double bx, double by, double bz, const double* __restri
         hdr->H[tid] = acc;
     }
     __syncthreads();
-    if (tid == 0) hdr->S = __dsub_rn(__dmul_rn(__dmul_rn(hdr->H[0], hdr->H[1]), hdr->H[2]), 1.0);
+    if (tid == 0) {
+        const double S = __dsub_rn(__dmul_rn(__dmul_rn(hdr->H[0], hdr->H[1]), hdr->H[2]), 1.0);
+        hdr->S = S;
+        hdr->wP = S / (double)P;  // the importance weight S/P of every sampled frequency
+    }
 }
 
-// Smallest j in [0, 2M] with target < cdf[j] (cdf is non-decreasing), minus M.
-__device__ __forceinline__ int inverse_cdf(const double* __restrict__ row, int M, double u)
+// Smallest j in [0, 2M] with target < cdf[j], minus M.  cdf is non-decreasing and
+// non-negative, and for non-negative doubles the order of the values is the order of
+// their bit patterns, so the search compares 64-bit integers (no FP64 instructions).
+__device__ __forceinline__ int inverse_cdf_bits(const unsigned long long* __restrict__ row, int M,
+                                                unsigned long long target)
 {
-    const double target = __dmul_rn(u, row[2 * M]);
     int lo = 0, hi = 2 * M;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
@@ -87,22 +94,26 @@ __device__ __forceinline__ int inverse_cdf(const double* __restrict__ row, int M
 
 // =================================================================================
 // Frequency sampling (Sec. 4.2-4.3): sample l uses Philox key (seed_lo, seed_hi) and
-// counters (l, 2 attempt + half, step_lo, step_hi24); redraw while m = 0.  When the three
-// cumulative tables fit (smem_entries > 0) the block first copies them to shared memory,
-// so that the binary searches do not wait on global memory.
+// counters (l, 2 attempt + half, step_lo, step_hi24); redraw while m = 0.  The block
+// first copies the three cumulative tables to shared memory when they fit
+// (smem_cap > 0).  Per axis the only FP64 instruction is target = u * H; u is built from
+// its bits and the search compares bit patterns.
 __global__ void k_sample(uint64_t seed, uint64_t step, int P, const double* __restrict__ cdf, int cap,
                          int smem_cap, const TableHeader* __restrict__ hdr, int4* __restrict__ m_out,
                          double* __restrict__ w_out, unsigned* __restrict__ status)
 {
-    extern __shared__ double s_cdf[];
+    extern __shared__ unsigned long long s_cdf[];
+    pdl_trigger();  // the rho pass may start staging its particles meanwhile
+    const double wP = hdr->wP;
+    const unsigned long long* gx = reinterpret_cast<const unsigned long long*>(cdf);
+    const unsigned long long* tx = gx;
+    const unsigned long long* ty = gx + cap;
+    const unsigned long long* tz = gx + 2 * (size_t)cap;
+    if (smem_cap > 0) {  // smem_cap == cap: copy the three rows whole, without waiting for M
+        for (int j = threadIdx.x; j < 3 * smem_cap; j += blockDim.x) s_cdf[j] = gx[j];
+    }
     const int Mx = hdr->M[0], My = hdr->M[1], Mz = hdr->M[2];
-    const double* tx = cdf;
-    const double* ty = cdf + cap;
-    const double* tz = cdf + 2 * (size_t)cap;
     if (smem_cap > 0) {
-        for (int j = threadIdx.x; j <= 2 * Mx; j += blockDim.x) s_cdf[j] = tx[j];
-        for (int j = threadIdx.x; j <= 2 * My; j += blockDim.x) s_cdf[smem_cap + j] = ty[j];
-        for (int j = threadIdx.x; j <= 2 * Mz; j += blockDim.x) s_cdf[2 * smem_cap + j] = tz[j];
         __syncthreads();
         tx = s_cdf;
         ty = s_cdf + smem_cap;
@@ -110,6 +121,9 @@ __global__ void k_sample(uint64_t seed, uint64_t step, int P, const double* __re
     }
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= P) return;
+    const double Hx = __longlong_as_double((long long)tx[2 * Mx]);
+    const double Hy = __longlong_as_double((long long)ty[2 * My]);
+    const double Hz = __longlong_as_double((long long)tz[2 * Mz]);
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     const uint32_t c2 = (uint32_t)step, c3 = (uint32_t)((step >> 32) & 0xFFFFFFu);
     int4 m = make_int4(0, 0, 0, 0);
@@ -117,9 +131,12 @@ __global__ void k_sample(uint64_t seed, uint64_t step, int P, const double* __re
     for (uint32_t attempt = 0; attempt < kMaxAttempts; ++attempt) {
         const uint4 w0 = philox4x32_10(make_uint4((uint32_t)l, 2u * attempt, c2, c3), k0, k1);
         const uint4 w1 = philox4x32_10(make_uint4((uint32_t)l, 2u * attempt + 1u, c2, c3), k0, k1);
-        m.x = inverse_cdf(tx, Mx, uniform53(w0.x, w0.y));
-        m.y = inverse_cdf(ty, My, uniform53(w0.z, w0.w));
-        m.z = inverse_cdf(tz, Mz, uniform53(w1.x, w1.y));
+        const double ux = __longlong_as_double((long long)uniform53_bits(w0.x, w0.y));
+        const double uy = __longlong_as_double((long long)uniform53_bits(w0.z, w0.w));
+        const double uz = __longlong_as_double((long long)uniform53_bits(w1.x, w1.y));
+        m.x = inverse_cdf_bits(tx, Mx, (unsigned long long)__double_as_longlong(__dmul_rn(ux, Hx)));
+        m.y = inverse_cdf_bits(ty, My, (unsigned long long)__double_as_longlong(__dmul_rn(uy, Hy)));
+        m.z = inverse_cdf_bits(tz, Mz, (unsigned long long)__double_as_longlong(__dmul_rn(uz, Hz)));
         if (m.x != 0 || m.y != 0 || m.z != 0) {
             found = true;
             break;
@@ -130,7 +147,7 @@ __global__ void k_sample(uint64_t seed, uint64_t step, int P, const double* __re
         m = make_int4(1, 0, 0, 0);  // keeps the evaluation finite; the call reports RBE_ESAMPLE
     }
     m_out[l] = m;
-    w_out[l] = hdr->S / (double)P;
+    w_out[l] = wP;
 }
 
 // Caller-given frequencies and weights (weighted mode).
@@ -161,39 +178,101 @@ __device__ __forceinline__ double block_sum(double v, double* scratch32)
     return v;
 }
 
+// Fixed-order block sum of a float-float value per thread; valid in thread 0.
+__device__ __forceinline__ void block_sum_ff(float& hi, float& lo, float (*scratch)[32])
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, hi, off);
+        const float ol = __shfl_xor_sync(0xffffffffu, lo, off);
+        ff_add2(hi, lo, oh, ol);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) {
+        scratch[0][warp] = hi;
+        scratch[1][warp] = lo;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const bool on = lane < (int)(blockDim.x >> 5);
+        hi = on ? scratch[0][lane] : 0.f;
+        lo = on ? scratch[1][lane] : 0.f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, hi, off);
+            const float ol = __shfl_xor_sync(0xffffffffu, lo, off);
+            ff_add2(hi, lo, oh, ol);
+        }
+    }
+}
+
+// Loads particle i as (s_x, s_y, s_z) 32-bit fixed point and q as float, with integer
+// operations only; flags non-finite inputs.
+__device__ __forceinline__ uint4 load_fixed(const double* __restrict__ pos, const double* __restrict__ q,
+                                            int64_t i, FixScale scx, FixScale scy, FixScale scz,
+                                            unsigned* __restrict__ status)
+{
+    const unsigned long long bx = (unsigned long long)__double_as_longlong(pos[3 * i]);
+    const unsigned long long by = (unsigned long long)__double_as_longlong(pos[3 * i + 1]);
+    const unsigned long long bz = (unsigned long long)__double_as_longlong(pos[3 * i + 2]);
+    const unsigned long long bq = (unsigned long long)__double_as_longlong(q[i]);
+    if (nonfinite_bits(bx) || nonfinite_bits(by) || nonfinite_bits(bz) || nonfinite_bits(bq))
+        atomicOr(status, kStatusNonFinite);  // status may be a shared-memory flag (before pdl_wait)
+    return make_uint4(fixed_frac_int(bx, scx), fixed_frac_int(by, scy), fixed_frac_int(bz, scz),
+                      __float_as_uint(double_to_float_int(bq)));
+}
+
 // =================================================================================
 // rho pass, FP32-phase path.  Block (kt, c) has blockDim.x (a multiple of 32, <= 256)
 // threads; thread j owns frequency kt * blockDim.x + j and runs over the particles
 // [c * chunk_len, (c + 1) * chunk_len), staged in shared memory blockDim.x at a time as
-// 32-bit fixed-point (s_x, s_y, s_z) plus q as float and read as broadcasts.
-// ACC: RBE_RHO_FP32 (plain FP32 within a staged tile, FP64 across tiles),
-//      RBE_RHO_COMP32 (Kahan-compensated FP32 within a tile), RBE_RHO_FP64 (per pair).
+// 32-bit fixed-point (s_x, s_y, s_z) plus q as float and read as broadcasts.  No FP64
+// instruction runs per particle or per pair: sums across staged tiles are float-float.
+// ACC: RBE_RHO_FP32 (plain FP32 within a staged tile), RBE_RHO_COMP32 (Kahan-compensated
+//      FP32 within a tile), RBE_RHO_FP64 (FP64 per pair; slow on GB300, for reference).
+// Partials: float4 (Re hi, Re lo, Im hi, Im lo) at [l * nchunks + c]; row K holds the
+// chunk's sum of q^2 (hi, lo).
 constexpr int kMaxRhoThreads = 256;
 
 template <int ACC>
 __global__ void __launch_bounds__(kMaxRhoThreads)
-k_rho_f32(const double* __restrict__ pos, const double* __restrict__ q, int64_t N, double ilx, double ily,
-          double ilz, const int4* __restrict__ m, int K, int64_t chunk_len, int nchunks,
-          double2* __restrict__ partials, unsigned* __restrict__ status, uint32_t mul23)
+k_rho_f32(const double* __restrict__ pos, const double* __restrict__ q, int64_t N, FixScale scx, FixScale scy,
+          FixScale scz, const int4* __restrict__ m, int K, int64_t chunk_len, int nchunks,
+          float4* __restrict__ partials, unsigned* __restrict__ status)
 {
     __shared__ uint4 sp[kMaxRhoThreads];
-    __shared__ double red[32];
+    __shared__ float red[2][32];
+    __shared__ unsigned bad;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int l = blockIdx.x * nt + tid;
     const int c = blockIdx.y;
-    const int4 mv = l < K ? m[l] : make_int4(0, 0, 0, 0);
-    double are = 0.0, aim = 0.0, q2 = 0.0;
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f, q2h = 0.f, q2l = 0.f;
+    double are = 0.0, aim = 0.0;
     const int64_t start = (int64_t)c * chunk_len;
     const int64_t end = min(N, start + chunk_len);
+    if (tid == 0) bad = 0u;
+    __syncthreads();
+    // the first tile is staged before waiting for the sampler (inputs only)
+    uint4 rec0 = make_uint4(0u, 0u, 0u, 0u);
+    if (start + tid < end) {
+        rec0 = load_fixed(pos, q, start + tid, scx, scy, scz, &bad);
+        const float qf = __uint_as_float(rec0.w);
+        ff_add(q2h, q2l, qf * qf);
+    }
+    pdl_wait();
+    pdl_trigger();
+    const int4 mv = l < K ? m[l] : make_int4(0, 0, 0, 0);
     for (int64_t base = start; base < end; base += nt) {
         const int64_t i = base + tid;
-        uint4 rec = make_uint4(0u, 0u, 0u, 0u);
-        if (i < end) {
-            const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
-            const double qi = q[i];
-            if (!isfinite(x + y + z + qi)) atomicOr(status, kStatusNonFinite);
-            q2 += qi * qi;
-            rec = make_uint4(fixed_frac(x, ilx), fixed_frac(y, ily), fixed_frac(z, ilz), __float_as_uint((float)qi));
+        uint4 rec = rec0;
+        if (base != start) {
+            rec = make_uint4(0u, 0u, 0u, 0u);
+            if (i < end) {
+                rec = load_fixed(pos, q, i, scx, scy, scz, status);
+                const float qf = __uint_as_float(rec.w);
+                ff_add(q2h, q2l, qf * qf);
+            }
         }
         sp[tid] = rec;
         __syncthreads();
@@ -203,7 +282,7 @@ k_rho_f32(const double* __restrict__ pos, const double* __restrict__ q, int64_t 
         for (int p = 0; p < n_here; ++p) {
             const uint4 r = sp[p];
             const float qp = __uint_as_float(r.w);
-            const float th = fixed_phase(mv.x, mv.y, mv.z, r.x, r.y, r.z, mul23);
+            const float th = fixed_phase(mv.x, mv.y, mv.z, r.x, r.y, r.z);
             float sn, cs;
             __sincosf(th, &sn, &cs);
             if (ACC == RBE_RHO_FP32) {
@@ -224,15 +303,22 @@ k_rho_f32(const double* __restrict__ pos, const double* __restrict__ q, int64_t 
             }
         }
         if (ACC != RBE_RHO_FP64) {
-            are += (double)re - (double)cre;
-            aim += (double)im - (double)cim;
+            ff_add(rh, rl, re);
+            rl -= cre;
+            ff_add(ih, il, im);
+            il -= cim;
         }
         __syncthreads();
     }
-    if (l < K) partials[(size_t)l * nchunks + c] = make_double2(are, aim);
+    if (ACC == RBE_RHO_FP64) {
+        rh = (float)are; rl = (float)(are - (double)rh);
+        ih = (float)aim; il = (float)(aim - (double)ih);
+    }
+    if (tid == 0 && bad) atomicOr(status, kStatusNonFinite);  // flagged while staging the first tile
+    if (l < K) partials[(size_t)l * nchunks + c] = make_float4(rh, rl, ih, il);
     if (blockIdx.x == 0) {
-        const double s = block_sum(q2, red);  // sum of q^2 over the chunk, for E_self
-        if (tid == 0) partials[(size_t)K * nchunks + c] = make_double2(s, 0.0);
+        block_sum_ff(q2h, q2l, red);  // sum of q^2 over the chunk, for E_self
+        if (tid == 0) partials[(size_t)K * nchunks + c] = make_float4(q2h, q2l, 0.f, 0.f);
     }
 }
 
@@ -388,88 +474,244 @@ k_reduce(const double2* __restrict__ partials, int nchunks, int K, const int4* _
 }
 
 // =================================================================================
-// Force pass, FP32-phase path.  Block b owns particles [b * per_block, (b+1) * per_block),
-// processed kT * PPT at a time (PPT per thread).  Frequencies are staged in shared memory
-// kForceKT at a time as (mx, my, mz, A) and (B, mx, my, mz) and read as broadcasts; when
-// K <= kForceKT they are staged once per block.
-// F_i,theta = q_i (2 pi / l_theta) sum_l m_l,theta (sin B_l - cos A_l): FP32 within a
-// staged frequency tile, FP64 across tiles.
-template <int PPT>
-__global__ void __launch_bounds__(kT) k_force_f32(const double* __restrict__ pos, const double* __restrict__ q,
-                                                  int64_t N, int64_t per_block, double ilx, double ily,
-                                                  double ilz, const int4* __restrict__ coef_m,
-                                                  const float4* __restrict__ coef_f, int K,
-                                                  double* __restrict__ F, uint32_t mul23)
+// Reduction for the FP32-phase path.  Block l (of K + 1) sums row l of the partials over
+// the chunks as float-float in a fixed order, then forms the per-frequency terms in FP32
+// (the path's stated accuracy is 1e-5 relative):
+//   e_l = (2 pi / V) w_l |rho_l|^2 / |k_l|^2,  W_l = e_l [I - 2 (1/|k_l|^2 + 1/4a) k_l k_l],
+//   A_l = beta_l Im rho_l, B_l = beta_l Re rho_l with beta_l = w_l 4 pi / (V |k_l|^2).
+// Row K carries the sum of q^2.  The sums over l run in the force launch (k_force_f32's
+// extra block), concurrently with the force pass.  Constants come from the host:
+//   cx, cy, cz = 2 pi / l,  ce = 2 pi / V,  cb = 4 pi / V,  inv4a = 1 / (4 alpha),
+//   cself = -sqrt(alpha / pi).
+struct ReduceConsts32 {
+    float cx, cy, cz, ce, cb, inv4a, cself;
+};
+
+__device__ __forceinline__ double ff_to_double(float hi, float lo)
 {
-    __shared__ int4 sm[kForceKT];
-    __shared__ float4 sf[kForceKT];
-    const int tid = threadIdx.x;
-    const bool one_tile = K <= kForceKT;
-    if (one_tile) {
-        for (int j = tid; j < K; j += kT) {
-            sm[j] = coef_m[j];
-            sf[j] = coef_f[j];
-        }
-        __syncthreads();
+    return __longlong_as_double((long long)float_to_double_bits(__float_as_uint(hi))) +
+           __longlong_as_double((long long)float_to_double_bits(__float_as_uint(lo)));
+}
+
+__global__ void __launch_bounds__(kReduceThreads)
+k_reduce_f32(const float4* __restrict__ partials, int nchunks, int K, const int4* __restrict__ m,
+             const double* __restrict__ w, ReduceConsts32 cst, double2* __restrict__ rho,
+             float* __restrict__ terms, int4* __restrict__ coef_m, float4* __restrict__ coef_f,
+             unsigned* __restrict__ status)
+{
+    __shared__ float red[2][32];
+    const int l = blockIdx.x;
+    // the sampler completed before the rho pass passed its wait, and the rho pass lets this
+    // launch start only after that wait: m and w are final here
+    int4 mi = make_int4(0, 0, 0, 0);
+    double wd = 0.0;
+    if (threadIdx.x == 0 && l < K) {
+        mi = m[l];
+        wd = w[l];
     }
+    pdl_wait();
+    pdl_trigger();
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    const float4* row = partials + (size_t)l * nchunks;
+    for (int j = threadIdx.x; j < nchunks; j += kReduceThreads) {
+        const float4 v = row[j];
+        ff_add2(rh, rl, v.x, v.y);
+        ff_add2(ih, il, v.z, v.w);
+    }
+    block_sum_ff(rh, rl, red);
+    block_sum_ff(ih, il, red);
+    if (threadIdx.x != 0) return;
+    float* t = terms + (size_t)l * 8;
+    if (l == K) {
+        t[0] = rh;  // sum of q^2 as float-float
+        t[1] = rl;
+        return;
+    }
+    const float re = rh + rl, im = ih + il;
+    const float wl = double_to_float_int((unsigned long long)__double_as_longlong(wd));
+    const float kx = cst.cx * (float)mi.x, ky = cst.cy * (float)mi.y, kz = cst.cz * (float)mi.z;
+    const float kk = kx * kx + ky * ky + kz * kz;
+    const float ikk = 1.0f / kk;
+    const float rho2 = re * re + im * im;
+    const float e = cst.ce * wl * rho2 * ikk;
+    const float b = 2.0f * (ikk + cst.inv4a);
+    t[0] = e;
+    t[1] = e * (1.0f - b * kx * kx);
+    t[2] = e * (1.0f - b * ky * ky);
+    t[3] = e * (1.0f - b * kz * kz);
+    t[4] = -e * b * kx * ky;
+    t[5] = -e * b * kx * kz;
+    t[6] = -e * b * ky * kz;
+    t[7] = 0.f;
+    const float beta = cst.cb * wl * ikk;
+    const float A = beta * im, B = beta * re;
+    rho[l] = make_double2(ff_to_double(rh, rl), ff_to_double(ih, il));
+    coef_m[l] = make_int4(mi.x, mi.y, mi.z, __float_as_int(A));
+    coef_f[l] = make_float4(B, (float)mi.x, (float)mi.y, (float)mi.z);
+    if (!isfinite(re) || !isfinite(im)) atomicOr(status, kStatusNonFinite);
+}
+
+// Energy and virial: fixed-order float-float sums of the per-frequency terms over l,
+// by one block of kForceThreads threads.
+constexpr int kForceWarps = 8;
+constexpr int kForceThreads = 32 * kForceWarps;
+
+__device__ void final_sums_f32(const float* __restrict__ terms, int K, float cself, double* __restrict__ W_out,
+                               double* __restrict__ E_out, unsigned* __restrict__ status)
+{
+    __shared__ float fin[kForceWarps][14];
+    float ah[7] = {0, 0, 0, 0, 0, 0, 0}, al[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+        const float* t = terms + (size_t)j * 8;
+#pragma unroll
+        for (int a = 0; a < 7; ++a) ff_add(ah[a], al[a], t[a]);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int a = 0; a < 7; ++a) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, ah[a], off);
+            const float ol = __shfl_xor_sync(0xffffffffu, al[a], off);
+            ff_add2(ah[a], al[a], oh, ol);
+        }
+        if (lane == 0) {
+            fin[warp][2 * a] = ah[a];
+            fin[warp][2 * a + 1] = al[a];
+        }
+    }
+    __syncthreads();
+    // thread a (< 7) finishes term a; thread 7 the self energy
+    if (threadIdx.x < 8) {
+        const int a = threadIdx.x;
+        float th = 0.f, tl = 0.f;
+        if (a < 7) {
+            for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) ff_add2(th, tl, fin[wv][2 * a], fin[wv][2 * a + 1]);
+        } else {
+            const float q2h = terms[(size_t)K * 8], q2l = terms[(size_t)K * 8 + 1];
+            ff_add(th, tl, cself * q2h);
+            tl += cself * q2l;
+        }
+        const double v = ff_to_double(th, tl);
+        if (!isfinite(th)) atomicOr(status, kStatusNonFinite);
+        if (a == 0 && E_out) E_out[0] = v;
+        if (a == 7 && E_out) E_out[1] = v;
+        if (W_out) {
+            if (a == 1) W_out[0] = v;
+            if (a == 2) W_out[4] = v;
+            if (a == 3) W_out[8] = v;
+            if (a == 4) { W_out[1] = v; W_out[3] = v; }
+            if (a == 5) { W_out[2] = v; W_out[6] = v; }
+            if (a == 6) { W_out[5] = v; W_out[7] = v; }
+        }
+    }
+}
+
+// =================================================================================
+// Force pass, FP32-phase path.  Blocks of kForceWarps warps; block b owns particles
+// [b * per_block, (b+1) * per_block).  The frequencies are staged in shared memory (as
+// (mx, my, mz, A) and (B, mx, my, mz)) and split into kForceWarps contiguous slices, one
+// per warp.  Particles are converted once per block into shared memory, kForceThreads at
+// a time; each round of kForceRound particles is processed by every warp against its
+// slice (kForcePPT particles per lane), and the warps' partial forces are summed in
+// shared memory in a fixed order.  No FP64 instruction runs:
+//   F_i,theta = q_i (2 pi / l_theta) sum_l m_l,theta (sin B_l - cos A_l)
+// is formed in FP32 and widened to double exactly.  The launch carries one extra block
+// that computes the energy and virial sums (final_sums_f32) meanwhile.
+constexpr int kForcePPT = 4;
+constexpr int kForceRound = 32 * kForcePPT;  // particles per round
+constexpr int kForceStageK = 2048;           // frequencies staged at once (dynamic shared memory)
+
+__global__ void __launch_bounds__(kForceThreads)
+k_force_f32(const double* __restrict__ pos, const double* __restrict__ q, int64_t N, int64_t per_block,
+            FixScale scx, FixScale scy, FixScale scz, float cx, float cy, float cz,
+            const int4* __restrict__ coef_m, const float4* __restrict__ coef_f, int K, double* __restrict__ F,
+            unsigned* __restrict__ status, const float* __restrict__ terms, float cself,
+            double* __restrict__ W_out, double* __restrict__ E_out)
+{
+    extern __shared__ int4 s_dyn[];
+    __shared__ uint4 sp[kForceThreads];
+    __shared__ float part[kForceWarps][3][kForceRound];
+    if (blockIdx.x == gridDim.x - 1) {
+        pdl_wait();
+        final_sums_f32(terms, K, cself, W_out, E_out, status);
+        return;
+    }
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int kstage = min(K, kForceStageK);
+    int4* sm = s_dyn;
+    float4* sf = reinterpret_cast<float4*>(s_dyn + kstage);
+    unsigned long long* Fb = reinterpret_cast<unsigned long long*>(F);
     const int64_t b0 = (int64_t)blockIdx.x * per_block;
     const int64_t b1 = min(N, b0 + per_block);
-    const double cx = 2.0 * kPi * ilx, cy = 2.0 * kPi * ily, cz = 2.0 * kPi * ilz;
-    for (int64_t base = b0; base < b1; base += (int64_t)kT * PPT) {
-        uint32_t sx[PPT], sy[PPT], sz[PPT];
-        double fx[PPT], fy[PPT], fz[PPT];
+    const bool multi = K > kstage;  // frequency tiles must be restaged for every round
+    bool staged = false;
+    // the first particle tile is converted before waiting for the reduction (inputs only)
+    __shared__ unsigned bad;
+    if (tid == 0) bad = 0u;
+    __syncthreads();
+    const uint4 first = b0 + tid < b1 ? load_fixed(pos, q, b0 + tid, scx, scy, scz, &bad) : make_uint4(0u, 0u, 0u, 0u);
+    pdl_wait();
+    for (int64_t sbase = b0; sbase < b1; sbase += kForceThreads) {
+        // convert up to kForceThreads particles into shared memory
+        const int64_t i = sbase + tid;
+        __syncthreads();
+        sp[tid] = sbase == b0 ? first
+                              : (i < b1 ? load_fixed(pos, q, i, scx, scy, scz, status) : make_uint4(0u, 0u, 0u, 0u));
+        if (sbase == b0 && tid == 0 && bad) atomicOr(status, kStatusNonFinite);
+        const int nstaged = (int)min((int64_t)kForceThreads, b1 - sbase);
+        for (int r0 = 0; r0 < nstaged; r0 += kForceRound) {
+            float gx[kForcePPT], gy[kForcePPT], gz[kForcePPT];
 #pragma unroll
-        for (int p = 0; p < PPT; ++p) {
-            const int64_t i = base + (int64_t)p * kT + tid;
-            if (i < b1) {
-                sx[p] = fixed_frac(pos[3 * i], ilx);
-                sy[p] = fixed_frac(pos[3 * i + 1], ily);
-                sz[p] = fixed_frac(pos[3 * i + 2], ilz);
-            } else {
-                sx[p] = sy[p] = sz[p] = 0u;
-            }
-            fx[p] = fy[p] = fz[p] = 0.0;
-        }
-        for (int k0 = 0; k0 < K; k0 += kForceKT) {
-            const int nk = min(kForceKT, K - k0);
-            if (!one_tile) {
-                __syncthreads();
-                for (int j = tid; j < nk; j += kT) {
-                    sm[j] = coef_m[k0 + j];
-                    sf[j] = coef_f[k0 + j];
+            for (int p = 0; p < kForcePPT; ++p) gx[p] = gy[p] = gz[p] = 0.f;
+            for (int k0 = 0; k0 < K; k0 += kstage) {
+                const int nk = min(kstage, K - k0);
+                if (multi || !staged) {
+                    __syncthreads();
+                    for (int j = tid; j < nk; j += kForceThreads) {
+                        sm[j] = coef_m[k0 + j];
+                        sf[j] = coef_f[k0 + j];
+                    }
+                    staged = true;
                 }
                 __syncthreads();
-            }
-            float gx[PPT], gy[PPT], gz[PPT];
+                uint4 pr[kForcePPT];
 #pragma unroll
-            for (int p = 0; p < PPT; ++p) gx[p] = gy[p] = gz[p] = 0.f;
+                for (int p = 0; p < kForcePPT; ++p) pr[p] = sp[(r0 + 32 * p + lane) % kForceThreads];
+                const int l0 = (warp * nk) / kForceWarps, l1 = ((warp + 1) * nk) / kForceWarps;
 #pragma unroll 2
-            for (int l = 0; l < nk; ++l) {
-                const int4 a = sm[l];
-                const float4 b = sf[l];
-                const float A = __int_as_float(a.w);
+                for (int l = l0; l < l1; ++l) {
+                    const int4 a = sm[l];
+                    const float4 b = sf[l];
+                    const float A = __int_as_float(a.w);
 #pragma unroll
-                for (int p = 0; p < PPT; ++p) {
-                    const float th = fixed_phase(a.x, a.y, a.z, sx[p], sy[p], sz[p], mul23);
-                    float sn, cs;
-                    __sincosf(th, &sn, &cs);
-                    const float g = fmaf(sn, b.x, -cs * A);
-                    gx[p] = fmaf(g, b.y, gx[p]);
-                    gy[p] = fmaf(g, b.z, gy[p]);
-                    gz[p] = fmaf(g, b.w, gz[p]);
+                    for (int p = 0; p < kForcePPT; ++p) {
+                        float sn, cs;
+                        __sincosf(fixed_phase(a.x, a.y, a.z, pr[p].x, pr[p].y, pr[p].z), &sn, &cs);
+                        const float g = fmaf(sn, b.x, -cs * A);
+                        gx[p] = fmaf(g, b.y, gx[p]);
+                        gy[p] = fmaf(g, b.z, gy[p]);
+                        gz[p] = fmaf(g, b.w, gz[p]);
+                    }
                 }
             }
 #pragma unroll
-            for (int p = 0; p < PPT; ++p) { fx[p] += gx[p]; fy[p] += gy[p]; fz[p] += gz[p]; }
-        }
+            for (int p = 0; p < kForcePPT; ++p) {
+                part[warp][0][32 * p + lane] = gx[p];
+                part[warp][1][32 * p + lane] = gy[p];
+                part[warp][2][32 * p + lane] = gz[p];
+            }
+            __syncthreads();
+            for (int t = tid; t < 3 * kForceRound; t += kForceThreads) {
+                const int c = t / kForceRound, j = t % kForceRound;
+                if (r0 + j < nstaged) {
+                    float acc = part[0][c][j];
 #pragma unroll
-        for (int p = 0; p < PPT; ++p) {
-            const int64_t i = base + (int64_t)p * kT + tid;
-            if (i < b1) {
-                const double qi = q[i];
-                F[3 * i] = qi * cx * fx[p];
-                F[3 * i + 1] = qi * cy * fy[p];
-                F[3 * i + 2] = qi * cz * fz[p];
+                    for (int wv = 1; wv < kForceWarps; ++wv) acc += part[wv][c][j];
+                    const float qf = __uint_as_float(sp[r0 + j].w);
+                    const float sc = c == 0 ? cx : (c == 1 ? cy : cz);
+                    Fb[3 * (sbase + r0 + j) + c] = float_to_double_bits(__float_as_uint(qf * sc * acc));
+                }
             }
         }
     }
@@ -582,7 +824,7 @@ rbe_status ensure_tables(rbe_ctx ctx)
         if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaMalloc(tables)");
         ctx->d.tab_cap = cap;
     }
-    k_tables<<<1, 256, 0, ctx->stream>>>(ctx->box[0], ctx->box[1], ctx->box[2], nullptr, ctx->alpha,
+    k_tables<<<1, 256, 0, ctx->stream>>>(ctx->box[0], ctx->box[1], ctx->box[2], nullptr, ctx->alpha, ctx->P,
                                          ctx->d.cdf, ctx->d.tab_cap, ctx->d.hdr, ctx->d.status);
     rbe_status st = check_launch(ctx, "k_tables");
     if (st == RBE_OK) ctx->tables_dirty = false;
@@ -640,10 +882,10 @@ rbe_status launch_weights_from_list(rbe_ctx ctx, int K, const int32_t* m, const 
 
 // Resident blocks per SM of a kernel at a block size (cached per process).
 template <typename Kern>
-static int blocks_per_sm(Kern kern, int threads)
+static int blocks_per_sm(Kern kern, int threads, size_t dyn_smem = 0)
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, dyn_smem) != cudaSuccess) {
         cudaGetLastError();
         n = 1;
     }
@@ -652,9 +894,9 @@ static int blocks_per_sm(Kern kern, int threads)
 
 // Launch plan.  rho pass: frequency tiles of at most 256 threads, sized in whole warps
 // so that few lanes idle; particle chunks so that the grid is one full wave of resident
-// blocks with equal particle counts.  Force pass: a grid that is a multiple of the SM
-// count, equal particle ranges per block.
-static Plan make_plan(rbe_ctx ctx, int64_t N, int K, int rho_bps, int force_bps)
+// blocks with equal particle counts.  Force pass: one wave of resident blocks with equal
+// particle ranges.
+static Plan make_plan(rbe_ctx ctx, int64_t N, int K, int rho_bps, int force_bps, int force_unit)
 {
     Plan p{};
     p.ktiles = (K + kMaxRhoThreads - 1) / kMaxRhoThreads;
@@ -667,80 +909,128 @@ static Plan make_plan(rbe_ctx ctx, int64_t N, int K, int rho_bps, int force_bps)
     p.nchunks = (int)std::max<int64_t>(1, (N + p.chunk_len - 1) / p.chunk_len);
     p.ppt = 2;
     const int64_t fwant = (int64_t)ctx->num_sms * force_bps;
-    const int64_t fmax = (N + kT * p.ppt - 1) / (kT * p.ppt);
+    const int64_t fmax = (N + force_unit - 1) / force_unit;
     p.fblocks = (int)std::min<int64_t>(fwant, fmax);
     p.per_block = p.fblocks > 0 ? (N + p.fblocks - 1) / p.fblocks : 0;
     if (p.per_block > 0) p.fblocks = (int)((N + p.per_block - 1) / p.per_block);
     return p;
 }
 
+// Launch with programmatic stream serialization (the kernel calls pdl_wait()).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+// 1/l as (64-bit mantissa, power of two), from the double 1/l.
+static FixScale fix_scale(double ell)
+{
+    const double inv = 1.0 / ell;
+    unsigned long long b;
+    std::memcpy(&b, &inv, 8);
+    const int e = (int)((b >> 52) & 0x7ff) - 1075;
+    const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    return FixScale{mant << 11, e - 11};
+}
+
 rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int K,
                            bool /*uniform_weight*/, double* F, double* W, double* E)
 {
     DeviceBuffers& d = ctx->d;
-    static int bps_rho32 = 0, bps_rho64 = 0, bps_f32 = 0, bps_f64 = 0;
-    if (!bps_rho32) {
-        bps_rho32 = blocks_per_sm(k_rho_f32<RBE_RHO_FP32>, kMaxRhoThreads) * kMaxRhoThreads;
-        bps_rho64 = blocks_per_sm(k_rho_f64, kMaxRhoThreads) * kMaxRhoThreads;
-        bps_f32 = blocks_per_sm(k_force_f32<2>, kT);
-        bps_f64 = blocks_per_sm(k_force_f64<2>, kT);
-    }
     const bool fp64 = ctx->precision == RBE_FP64;
+    static int rho32_threads = 0, rho64_threads = 0, bps_f64 = 0;
+    if (!rho32_threads) {
+        rho32_threads = blocks_per_sm(k_rho_f32<RBE_RHO_FP32>, kMaxRhoThreads) * kMaxRhoThreads;
+        rho64_threads = blocks_per_sm(k_rho_f64, kMaxRhoThreads) * kMaxRhoThreads;
+        bps_f64 = blocks_per_sm(k_force_f64<2>, kT);
+        cudaFuncSetAttribute(k_force_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(32 * kForceStageK));
+    }
+    const int kstage = std::min(K, kForceStageK);
+    const size_t force_smem = fp64 ? 0 : (size_t)32 * kstage;
+    const int bps_force = fp64 ? bps_f64 : blocks_per_sm(k_force_f32, kForceThreads, force_smem);
     // resident rho blocks per SM at the tile's block size (threads per SM / block size)
     const int ktiles = (K + kMaxRhoThreads - 1) / kMaxRhoThreads;
     const int kthreads = std::min(kMaxRhoThreads, 32 * (((K + ktiles - 1) / ktiles + 31) / 32));
-    const int rho_bps = std::max(1, std::min(32, (fp64 ? bps_rho64 : bps_rho32) / kthreads));
-    const Plan p = make_plan(ctx, N, K, rho_bps, fp64 ? bps_f64 : bps_f32);
+    const int rho_bps = std::max(1, std::min(32, (fp64 ? rho64_threads : rho32_threads) / kthreads));
+    const Plan p = make_plan(ctx, N, K, rho_bps, bps_force, fp64 ? kT * 2 : kForceRound);
     const size_t need = (size_t)(K + 1) * p.nchunks;
     if (need > d.part_cap) {
         cudaFree(d.partials);
         d.partials = nullptr;
         d.part_cap = 0;
-        cudaError_t err = cudaMalloc(&d.partials, sizeof(double2) * need);
+        cudaError_t err = cudaMalloc(&d.partials, 16 * need);
         if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaMalloc(partials)");
         d.part_cap = need;
     }
     const double ilx = 1.0 / ctx->box[0], ily = 1.0 / ctx->box[1], ilz = 1.0 / ctx->box[2];
+    const FixScale scx = fix_scale(ctx->box[0]), scy = fix_scale(ctx->box[1]), scz = fix_scale(ctx->box[2]);
     const dim3 grid(p.ktiles, p.nchunks);
-    const uint32_t mul23 = 1u << 23;
     cudaStream_t s = ctx->stream;
+    double2* part64 = static_cast<double2*>(d.partials);
+    float4* part32 = static_cast<float4*>(d.partials);
     if (fp64) {
-        k_rho_f64<<<grid, p.kthreads, 0, s>>>(pos, q, N, ilx, ily, ilz, d.m, K, p.chunk_len, p.nchunks, d.partials,
+        k_rho_f64<<<grid, p.kthreads, 0, s>>>(pos, q, N, ilx, ily, ilz, d.m, K, p.chunk_len, p.nchunks, part64,
                                               d.status);
     } else {
-        switch (ctx->rho_accum) {
-        case RBE_RHO_FP64:
-            k_rho_f32<RBE_RHO_FP64><<<grid, p.kthreads, 0, s>>>(pos, q, N, ilx, ily, ilz, d.m, K, p.chunk_len,
-                                                                 p.nchunks, d.partials, d.status, mul23);
-            break;
-        case RBE_RHO_COMP32:
-            k_rho_f32<RBE_RHO_COMP32><<<grid, p.kthreads, 0, s>>>(pos, q, N, ilx, ily, ilz, d.m, K, p.chunk_len,
-                                                                   p.nchunks, d.partials, d.status, mul23);
-            break;
-        default:
-            k_rho_f32<RBE_RHO_FP32><<<grid, p.kthreads, 0, s>>>(pos, q, N, ilx, ily, ilz, d.m, K, p.chunk_len,
-                                                                 p.nchunks, d.partials, d.status, mul23);
-            break;
-        }
+        auto kern = ctx->rho_accum == RBE_RHO_FP64     ? k_rho_f32<RBE_RHO_FP64>
+                    : ctx->rho_accum == RBE_RHO_COMP32 ? k_rho_f32<RBE_RHO_COMP32>
+                                                       : k_rho_f32<RBE_RHO_FP32>;
+        cudaError_t err = launch_pdl(kern, grid, dim3(p.kthreads), 0, s, pos, q, N, scx, scy, scz,
+                                     (const int4*)d.m, K, p.chunk_len, p.nchunks, part32, d.status);
+        if (err != cudaSuccess) return cuda_fail(ctx, err, "launch k_rho_f32");
     }
     rbe_status st = check_launch(ctx, "k_rho");
     if (st != RBE_OK) return st;
     record_event(ctx, 2);
-    k_reduce<<<K + 1, kReduceThreads, 0, s>>>(d.partials, p.nchunks, K, d.m, d.w, ctx->box[0], ctx->box[1],
-                                               ctx->box[2], ctx->alpha, d.rho, d.terms, d.coef_m, d.coef_f,
-                                               d.coef_d, d.counter, d.status, W, E);
+    const double V = ctx->box[0] * ctx->box[1] * ctx->box[2];
+    ReduceConsts32 c;
+    c.cx = (float)(2.0 * kPi / ctx->box[0]);
+    c.cy = (float)(2.0 * kPi / ctx->box[1]);
+    c.cz = (float)(2.0 * kPi / ctx->box[2]);
+    c.ce = (float)(2.0 * kPi / V);
+    c.cb = (float)(4.0 * kPi / V);
+    c.inv4a = (float)(1.0 / (4.0 * ctx->alpha));
+    c.cself = (float)(-std::sqrt(ctx->alpha / kPi));
+    if (fp64) {
+        k_reduce<<<K + 1, kReduceThreads, 0, s>>>(part64, p.nchunks, K, d.m, d.w, ctx->box[0], ctx->box[1],
+                                                   ctx->box[2], ctx->alpha, d.rho, d.terms, d.coef_m, d.coef_f,
+                                                   d.coef_d, d.counter, d.status, W, E);
+    } else {
+        cudaError_t err = launch_pdl(k_reduce_f32, dim3(K + 1), dim3(kReduceThreads), 0, s, (const float4*)part32,
+                                     p.nchunks, K, (const int4*)d.m, (const double*)d.w, c, d.rho,
+                                     reinterpret_cast<float*>(d.terms), d.coef_m, d.coef_f, d.status);
+        if (err != cudaSuccess) return cuda_fail(ctx, err, "launch k_reduce_f32");
+    }
     st = check_launch(ctx, "k_reduce");
     if (st != RBE_OK) return st;
     record_event(ctx, 3);
-    if (p.fblocks > 0) {
-        if (fp64)
+    if (fp64) {
+        if (p.fblocks > 0) {
             k_force_f64<2><<<p.fblocks, kT, 0, s>>>(pos, q, N, p.per_block, ilx, ily, ilz, d.m, d.coef_d, K, F);
-        else
-            k_force_f32<2><<<p.fblocks, kT, 0, s>>>(pos, q, N, p.per_block, ilx, ily, ilz, d.coef_m, d.coef_f, K, F,
-                                                    mul23);
-        st = check_launch(ctx, "k_force");
-        if (st != RBE_OK) return st;
+            st = check_launch(ctx, "k_force");
+        }
+    } else {
+        // one extra block computes the energy and virial sums
+        cudaError_t err = launch_pdl(k_force_f32, dim3(p.fblocks + 1), dim3(kForceThreads), force_smem, s, pos, q,
+                                     N, p.per_block, scx, scy, scz, c.cx, c.cy, c.cz, (const int4*)d.coef_m,
+                                     (const float4*)d.coef_f, K, F, d.status,
+                                     reinterpret_cast<const float*>(d.terms), c.cself, W, E);
+        st = err == cudaSuccess ? RBE_OK : cuda_fail(ctx, err, "launch k_force_f32");
     }
+    if (st != RBE_OK) return st;
     record_event(ctx, 4);
     ctx->last_K = K;
     return RBE_OK;
