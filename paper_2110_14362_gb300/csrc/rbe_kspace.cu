@@ -236,7 +236,7 @@ __device__ __forceinline__ uint4 load_fixed(const double* __restrict__ pos, cons
 constexpr int kMaxRhoThreads = 256;
 
 template <int ACC>
-__global__ void __launch_bounds__(kMaxRhoThreads)
+__global__ void __launch_bounds__(kMaxRhoThreads, 8)
 k_rho_f32(const double* __restrict__ pos, const double* __restrict__ q, int64_t N, FixScale scx, FixScale scy,
           FixScale scz, const int4* __restrict__ m, int K, int64_t chunk_len, int nchunks,
           float4* __restrict__ partials, unsigned* __restrict__ status)
@@ -622,7 +622,7 @@ constexpr int kForcePPT = 4;
 constexpr int kForceRound = 32 * kForcePPT;  // particles per round
 constexpr int kForceStageK = 2048;           // frequencies staged at once (dynamic shared memory)
 
-__global__ void __launch_bounds__(kForceThreads)
+__global__ void __launch_bounds__(kForceThreads, 5)
 k_force_f32(const double* __restrict__ pos, const double* __restrict__ q, int64_t N, int64_t per_block,
             FixScale scx, FixScale scy, FixScale scz, float cx, float cy, float cz,
             const int4* __restrict__ coef_m, const float4* __restrict__ coef_f, int K, double* __restrict__ F,
@@ -881,6 +881,9 @@ rbe_status launch_weights_from_list(rbe_ctx ctx, int K, const int32_t* m, const 
 }
 
 // Resident blocks per SM of a kernel at a block size (cached per process).
+// Resident blocks per SM of a kernel at a block size: the occupancy API's answer, capped
+// by a count from the kernel's own register and shared-memory use (registers are
+// allocated per warp in units of 256).
 template <typename Kern>
 static int blocks_per_sm(Kern kern, int threads, size_t dyn_smem = 0)
 {
@@ -888,6 +891,23 @@ static int blocks_per_sm(Kern kern, int threads, size_t dyn_smem = 0)
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, dyn_smem) != cudaSuccess) {
         cudaGetLastError();
         n = 1;
+    }
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kern) == cudaSuccess) {
+        int dev = 0, regs_sm = 65536, smem_sm = 228 * 1024, thr_sm = 2048;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+        const int warps = (threads + 31) / 32;
+        const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+        int lim = regs_warp > 0 ? regs_sm / (regs_warp * warps) : n;
+        const size_t smem_blk = fa.sharedSizeBytes + dyn_smem + 1024;  // 1 KB reserved per block
+        lim = std::min<int>(lim, (int)(smem_sm / std::max<size_t>(smem_blk, 1)));
+        lim = std::min(lim, thr_sm / (warps * 32));
+        n = std::min(n, lim);
+    } else {
+        cudaGetLastError();
     }
     return std::max(1, n);
 }
@@ -908,11 +928,12 @@ static Plan make_plan(rbe_ctx ctx, int64_t N, int K, int rho_bps, int force_bps,
     p.chunk_len = std::max<int64_t>(1, (N + p.nchunks - 1) / p.nchunks);
     p.nchunks = (int)std::max<int64_t>(1, (N + p.chunk_len - 1) / p.chunk_len);
     p.ppt = 2;
-    const int64_t fwant = (int64_t)ctx->num_sms * force_bps;
-    const int64_t fmax = (N + force_unit - 1) / force_unit;
-    p.fblocks = (int)std::min<int64_t>(fwant, fmax);
-    p.per_block = p.fblocks > 0 ? (N + p.fblocks - 1) / p.fblocks : 0;
-    if (p.per_block > 0) p.fblocks = (int)((N + p.per_block - 1) / p.per_block);
+    // force pass: whole rounds of force_unit particles per block, at most one resident wave
+    const int64_t resident = std::max<int64_t>(1, (int64_t)ctx->num_sms * force_bps);
+    const int64_t rounds = (N + force_unit - 1) / force_unit;
+    const int64_t per = rounds > 0 ? (rounds + resident - 1) / resident : 0;  // rounds per block
+    p.per_block = per * force_unit;
+    p.fblocks = per > 0 ? (int)((rounds + per - 1) / per) : 0;
     return p;
 }
 
@@ -960,7 +981,12 @@ rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const doub
     }
     const int kstage = std::min(K, kForceStageK);
     const size_t force_smem = fp64 ? 0 : (size_t)32 * kstage;
-    const int bps_force = fp64 ? bps_f64 : blocks_per_sm(k_force_f32, kForceThreads, force_smem);
+    static int cached_kstage = -1, cached_bps_force = 1;
+    if (!fp64 && kstage != cached_kstage) {
+        cached_bps_force = blocks_per_sm(k_force_f32, kForceThreads, force_smem);
+        cached_kstage = kstage;
+    }
+    const int bps_force = fp64 ? bps_f64 : cached_bps_force;
     // resident rho blocks per SM at the tile's block size (threads per SM / block size)
     const int ktiles = (K + kMaxRhoThreads - 1) / kMaxRhoThreads;
     const int kthreads = std::min(kMaxRhoThreads, 32 * (((K + ktiles - 1) / ktiles + 31) / 32));
