@@ -144,6 +144,31 @@ rbe_status rbe_get_kernel_times(rbe_ctx ctx, float ms_out[4]);
  * Synchronous, legacy default stream.  The measured denominators of the roofline. */
 rbe_status rbe_measure_pipe(int32_t kind, int32_t iters, double* ops_per_s);
 
+/* Allocation-free sampling (the paper has no counterpart: this serves callers that cannot
+ * allocate device memory when they need a batch -- an MD engine that sized one device pool at
+ * start-up and allows no allocation afterwards, a plugin inside an application that owns all
+ * device memory, or a loop that must not call cudaMalloc because a device allocation can
+ * synchronise the whole device).  Draws the same batch as rbe_sample_k for (box, alpha, P,
+ * seed, step) without a context and without allocating: no cudaMalloc, no cudaFree, no
+ * allocating library routine.
+ *   box, alpha, P, seed, step  as rbe_create / rbe_sample_k
+ *   m_out    device, P*3 int32 row-major (4-byte aligned), written
+ *   S_out    device, 1 double (8-byte aligned), written with S = H_x H_y H_z - 1
+ *   stream   cudaStream_t to run on (NULL = legacy default stream)
+ * Scratch: a fixed file-scope device array of 192 KB (three tables of up to 8191 entries and a
+ * status word) that every GPU which loads the library holds until the process exits.  Boxes
+ * that need more than 4094 frequencies per axis (2 sqrt(alpha) l > ~4094) are rejected with
+ * RBE_EINVAL ("too large for the fixed scratch"); use rbe_sample_k for those.
+ * Every call shares the array, which keeps the last call's contents (the status word is
+ * cleared at the start of each call); calls that overlap on the GPU -- on different streams
+ * or from different host threads -- race on it and must be serialised by the caller.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  Synchronises `stream`
+ * before returning; a frequency that stayed m = 0 after 2^20 redraws returns RBE_ESAMPLE.
+ * Messages for failures are returned by rbe_last_error(NULL). */
+rbe_status rbe_sample_k_noalloc(const double box[3], double alpha, int32_t P, uint64_t seed, uint64_t step,
+                                int32_t* m_out, double* S_out, void* stream);
+
 /* Synchronise the context's stream and return (and clear) any latched device error. */
 rbe_status rbe_sync(rbe_ctx ctx);
 

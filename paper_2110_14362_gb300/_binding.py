@@ -45,6 +45,8 @@ SIGNATURES = [
     ("rbe_set_kernel_timing", ctypes.c_int, [_vp, ctypes.c_int32]),
     ("rbe_get_kernel_times", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float)]),
     ("rbe_measure_pipe", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _dp]),
+    ("rbe_sample_k_noalloc", ctypes.c_int,
+     [_dp, ctypes.c_double, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, _vp, _vp, _vp]),
     ("rbe_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("rbe_last_error", ctypes.c_char_p, [_vp]),
     ("rbe_version", ctypes.c_int32, []),
@@ -186,6 +188,13 @@ def rbe_measure_pipe(kind: int, iters: int = 4096) -> float:
     v = ctypes.c_double(0.0)
     _check(load().rbe_measure_pipe(int(kind), int(iters), ctypes.byref(v)))
     return v.value
+
+
+def rbe_sample_k_noalloc(box, alpha: float, P: int, seed: int, step: int, m_out, S_out, stream_handle: int = 0):
+    """Allocation-free sampling into caller device buffers (torch int32 (P, 3), float64 (1,))."""
+    b = _host(box, np.float64).reshape(3)
+    _check(load().rbe_sample_k_noalloc(b.ctypes.data_as(_dp), float(alpha), int(P), int(seed), int(step),
+                                       _ptr(m_out), _ptr(S_out), ctypes.c_void_p(stream_handle)))
 
 
 def rbe_version() -> int:
