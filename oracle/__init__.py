@@ -57,8 +57,11 @@ def _load():
             lib.orc_exp.restype = ctypes.c_double
             lib.orc_axis_M.argtypes = [ctypes.c_double, ctypes.c_double]
             lib.orc_axis_M.restype = ctypes.c_int32
-            lib.orc_axis_table.argtypes = [ctypes.c_double, ctypes.c_double, _c_double_p, _c_double_p]
+            lib.orc_axis_table.argtypes = [ctypes.c_double, ctypes.c_double, _c_double_p,
+                                           ctypes.POINTER(ctypes.c_uint64)]
             lib.orc_axis_table.restype = ctypes.c_double
+            lib.orc_axis_shift.argtypes = [ctypes.c_int32]
+            lib.orc_axis_shift.restype = ctypes.c_int
             lib.orc_sample_k.argtypes = [_c_double_p, ctypes.c_double, ctypes.c_int32, ctypes.c_uint64,
                                          ctypes.c_uint64, _c_int32_p, _c_double_p]
             lib.orc_sample_k.restype = ctypes.c_int
@@ -138,13 +141,14 @@ def exp_table(x: float) -> float:
 
 
 def axis_table(alpha: float, ell: float):
-    """(w, cdf, M, H) of the per-axis discrete Gaussian for box length ell."""
+    """(w, cum, M, H, sh) of the per-axis discrete Gaussian for box length ell: the weights,
+    the integer cumulative sums of rint(w 2^sh), the truncation, H and the shift."""
     lib = _load()
     M = lib.orc_axis_M(alpha, ell)
     w = np.zeros(2 * M + 1)
-    cdf = np.zeros(2 * M + 1)
-    H = lib.orc_axis_table(alpha, ell, _dp(w), _dp(cdf))
-    return w, cdf, M, H
+    cum = np.zeros(2 * M + 1, dtype=np.uint64)
+    H = lib.orc_axis_table(alpha, ell, _dp(w), cum.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+    return w, cum, M, H, lib.orc_axis_shift(M)
 
 
 def sample_k(box, alpha: float, P: int, seed: int, step: int):

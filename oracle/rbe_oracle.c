@@ -76,7 +76,7 @@ double orc_uniform53(uint32_t a, uint32_t b)
  * (sample index l, 2*attempt + half, step bits 0..31, (stream << 24) | step bits 32..55).
  * Two Philox calls (half = 0, 1) give 8 words; words (0,1), (2,3), (4,5) make the
  * x, y and z uniforms. */
-static void sample_uniforms(uint64_t seed, uint64_t step, uint32_t l, uint32_t attempt, double u[3])
+static void sample_uniforms(uint64_t seed, uint64_t step, uint32_t l, uint32_t attempt, uint64_t U[3])
 {
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint32_t w[8];
@@ -85,9 +85,9 @@ static void sample_uniforms(uint64_t seed, uint64_t step, uint32_t l, uint32_t a
                            (0u << 24) | (uint32_t)((step >> 32) & 0xFFFFFFu)};
         orc_philox4x32_10(ctr, key, w + 4 * half);
     }
-    u[0] = orc_uniform53(w[0], w[1]);
-    u[1] = orc_uniform53(w[2], w[3]);
-    u[2] = orc_uniform53(w[4], w[5]);
+    U[0] = ((uint64_t)w[0] << 21) | (uint64_t)(w[1] >> 11);
+    U[1] = ((uint64_t)w[2] << 21) | (uint64_t)(w[3] >> 11);
+    U[2] = ((uint64_t)w[4] << 21) | (uint64_t)(w[5] >> 11);
 }
 
 /* ------------------------------------------------------------------------------ */
@@ -123,9 +123,10 @@ double orc_exp(double x)
  * P(m) is proportional to exp(-|k|^2/(4 alpha)) = prod_theta exp(-c_theta m_theta^2)
  * with c_theta = pi^2 / (alpha l_theta^2).
  * The table keeps |m| <= M with M = ceil(sqrt(60 ln2 / c)), i.e. it drops terms below
- * 2^-60 of the peak.  w_j = exp(-c (j - M)^2), j = 0..2M, computed once per |m| so
- * the table is exactly symmetric; cdf_j = w_0 + ... + w_j summed left to right;
- * H = cdf_2M (Eq. (psf)). */
+ * 2^-60 of the peak.  w_j = exp(-c (j - M)^2), j = 0..2M, computed once per |m| so the
+ * table is exactly symmetric.  The weights are held as integers W_j = rint(w_j 2^sh) with
+ * sh = 62 - bitlength(2M + 1), so that their sum fits 63 bits; the cumulative sums
+ * C_j = W_0 + ... + W_j are exact, and H = C_2M 2^-sh (Eq. (psf)). */
 int32_t orc_axis_M(double alpha, double ell)
 {
     double c = (M_PI * M_PI) / (alpha * (ell * ell));
@@ -133,31 +134,42 @@ int32_t orc_axis_M(double alpha, double ell)
     return (int32_t)M;
 }
 
-/* Writes w[2M+1] and cdf[2M+1]; returns H. Caller sizes the arrays with orc_axis_M. */
-double orc_axis_table(double alpha, double ell, double* w, double* cdf)
+int orc_axis_shift(int32_t M)
+{
+    uint64_t n = (uint64_t)(2 * M + 1);
+    int bits = 0;
+    while (n) { ++bits; n >>= 1; }
+    return 62 - bits;
+}
+
+/* Writes w[2M+1] (the weights), cum[2M+1] (the integer cumulative sums) and returns H. */
+double orc_axis_table(double alpha, double ell, double* w, uint64_t* cum)
 {
     double c = (M_PI * M_PI) / (alpha * (ell * ell));
     int32_t M = orc_axis_M(alpha, ell);
+    int sh = orc_axis_shift(M);
     for (int32_t a = 0; a <= M; ++a) {
         double v = orc_exp(-(c * ((double)a * (double)a)));
         w[M + a] = v;
         w[M - a] = v;
     }
-    double acc = 0.0;
+    uint64_t acc = 0;
     for (int32_t j = 0; j <= 2 * M; ++j) {
-        acc = acc + w[j];
-        cdf[j] = acc;
+        acc += (uint64_t)llrint(ldexp(w[j], sh));
+        cum[j] = acc;
     }
-    return cdf[2 * M];
+    return ldexp((double)cum[2 * M], -sh);
 }
 
-/* Inverse CDF: the smallest j with u*H < cdf_j, minus M. */
-static int32_t axis_draw(const double* cdf, int32_t M, double u)
+/* Inverse CDF on the integer table: with U the 53-bit uniform integer,
+ * T = floor(U * C_2M / 2^53), m = (smallest j with T < C_j) - M. */
+static int32_t axis_draw(const uint64_t* cum, int32_t M, uint64_t U)
 {
-    double target = u * cdf[2 * M];
+    unsigned __int128 prod = (unsigned __int128)U * (unsigned __int128)cum[2 * M];
+    uint64_t T = (uint64_t)(prod >> 53);
     for (int32_t j = 0; j <= 2 * M; ++j)
-        if (target < cdf[j]) return j - M;
-    return M; /* unreachable for u < 1 */
+        if (T < cum[j]) return j - M;
+    return M; /* unreachable: T < C_2M */
 }
 
 #define ORC_MAX_ATTEMPTS (1u << 20)
@@ -170,7 +182,7 @@ int orc_sample_k(const double box[3], double alpha, int32_t P, uint64_t seed, ui
 {
     if (P < 0 || !(alpha > 0.0) || (step >> 56) != 0) return ORC_EINVAL;
     double H[3];
-    double* cdf[3];
+    uint64_t* cum[3] = {NULL, NULL, NULL};
     int32_t M[3];
     for (int t = 0; t < 3; ++t) {
         if (!(box[t] > 0.0)) return ORC_EINVAL;
@@ -179,19 +191,23 @@ int orc_sample_k(const double box[3], double alpha, int32_t P, uint64_t seed, ui
     int status = ORC_OK;
     for (int t = 0; t < 3; ++t) {
         double* w = (double*)malloc(sizeof(double) * (size_t)(2 * M[t] + 1));
-        cdf[t] = (double*)malloc(sizeof(double) * (size_t)(2 * M[t] + 1));
-        if (!w || !cdf[t]) { free(w); return ORC_ENOMEM; }
-        H[t] = orc_axis_table(alpha, box[t], w, cdf[t]);
+        cum[t] = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(2 * M[t] + 1));
+        if (!w || !cum[t]) {
+            free(w);
+            for (int u = 0; u <= t; ++u) free(cum[u]);
+            return ORC_ENOMEM;
+        }
+        H[t] = orc_axis_table(alpha, box[t], w, cum[t]);
         free(w);
     }
     for (int32_t l = 0; l < P && status == ORC_OK; ++l) {
         uint32_t attempt = 0;
         for (;;) {
             if (attempt >= ORC_MAX_ATTEMPTS) { status = ORC_ESAMPLE; break; }
-            double u[3];
-            sample_uniforms(seed, step, (uint32_t)l, attempt, u);
+            uint64_t U[3];
+            sample_uniforms(seed, step, (uint32_t)l, attempt, U);
             int32_t m[3];
-            for (int t = 0; t < 3; ++t) m[t] = axis_draw(cdf[t], M[t], u[t]);
+            for (int t = 0; t < 3; ++t) m[t] = axis_draw(cum[t], M[t], U[t]);
             if (m[0] != 0 || m[1] != 0 || m[2] != 0) {
                 m_out[3 * l + 0] = m[0];
                 m_out[3 * l + 1] = m[1];
@@ -202,7 +218,7 @@ int orc_sample_k(const double box[3], double alpha, int32_t P, uint64_t seed, ui
         }
     }
     if (S_out) *S_out = H[0] * H[1] * H[2] - 1.0;
-    for (int t = 0; t < 3; ++t) free(cdf[t]);
+    for (int t = 0; t < 3; ++t) free(cum[t]);
     return status;
 }
 

@@ -112,7 +112,7 @@ static rbe_status sync_and_status(rbe_ctx ctx)
 
 static void free_buffers(DeviceBuffers& d)
 {
-    cudaFree(d.cdf); cudaFree(d.hdr); cudaFree(d.m); cudaFree(d.w); cudaFree(d.rho); cudaFree(d.terms);
+    cudaFree(d.cum); cudaFree(d.ks); cudaFree(d.m); cudaFree(d.w); cudaFree(d.rho); cudaFree(d.terms);
     cudaFree(d.coef_m); cudaFree(d.coef_f); cudaFree(d.coef_d); cudaFree(d.partials); cudaFree(d.counter);
     cudaFree(d.status); cudaFree(d.pos); cudaFree(d.q); cudaFree(d.F); cudaFree(d.WE);
     d = DeviceBuffers{};
@@ -145,7 +145,7 @@ rbe_status rbe_create(const double box[3], double alpha, int32_t P, uint64_t see
     ctx->P = P;
     ctx->seed = seed;
     DeviceBuffers& d = ctx->d;
-    if ((err = cudaMalloc(&d.hdr, sizeof(TableHeader))) != cudaSuccess ||
+    if ((err = cudaMalloc(&d.ks, sizeof(KState))) != cudaSuccess ||
         (err = cudaMalloc(&d.counter, sizeof(unsigned))) != cudaSuccess ||
         (err = cudaMalloc(&d.status, sizeof(unsigned))) != cudaSuccess ||
         (err = cudaMemset(d.counter, 0, sizeof(unsigned))) != cudaSuccess ||
@@ -218,9 +218,9 @@ rbe_status rbe_sample_k(rbe_ctx ctx, uint64_t step, int32_t* m_out, double* S_ou
     rbe_status st = launch_sample(ctx, step, ctx->P);
     if (st != RBE_OK) return st;
     std::vector<int4> m(ctx->P);
-    TableHeader h;
+    KState h;
     cudaError_t err = cudaMemcpyAsync(m.data(), ctx->d.m, sizeof(int4) * ctx->P, cudaMemcpyDeviceToHost, ctx->stream);
-    if (err == cudaSuccess) err = cudaMemcpyAsync(&h, ctx->d.hdr, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(&h, ctx->d.ks, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
     if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaMemcpyAsync(sample)");
     st = sync_and_status(ctx);
     if (st != RBE_OK) return st;

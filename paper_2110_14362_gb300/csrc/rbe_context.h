@@ -11,13 +11,31 @@
 
 namespace rbe {
 
-// Per-axis sampling tables: M, H and S, written on the device.
-struct TableHeader {
-    int M[3];
+// Box-dependent state of an evaluation, written on the device by k_tables whenever the
+// box changes (from host values or from a device-resident box) and read by every other
+// kernel: the sampling tables' sizes and sums, S, and the constants of both precisions.
+struct FixScaleH {  // host mirror of rbe::FixScale (1/l = q 2^e)
+    unsigned long long q;
+    int e;
     int pad;
-    double H[3];
-    double S;
-    double wP;  // S / P
+};
+
+struct KState {
+    double L[3];        // box lengths
+    double inv[3];      // 1 / l
+    double V;           // l_x l_y l_z
+    double alpha;
+    int M[3];           // table truncation per axis
+    int sh[3];          // fixed-point shift of the integer weights per axis
+    double H[3];        // per-axis sums (Eq. (psf))
+    double S;           // H_x H_y H_z - 1 (Eq. (S))
+    double wP;          // S / P
+    FixScaleH sc[3];    // 1/l as a 64-bit mantissa and a power of two (FP32-phase path)
+    float cx, cy, cz;   // 2 pi / l
+    float ce, cb;       // 2 pi / V, 4 pi / V
+    float inv4a;        // 1 / (4 alpha)
+    float cself;        // -sqrt(alpha / pi)
+    int P;
 };
 
 // Launch plan of the N x K pair kernels (chosen by plan_* in rbe_kspace.cu).
@@ -32,9 +50,9 @@ struct Plan {
 };
 
 struct DeviceBuffers {
-    double* cdf = nullptr;            // [3][tab_cap] cumulative weights
+    unsigned long long* cum = nullptr;  // [3][tab_cap] integer cumulative weights
     int tab_cap = 0;                  // entries per axis (>= 2M+1)
-    TableHeader* hdr = nullptr;
+    KState* ks = nullptr;             // box-dependent state
     int4* m = nullptr;                // [kcap] (mx, my, mz, 0)
     double* w = nullptr;              // [kcap] per-frequency weight (S/P for RBE)
     double2* rho = nullptr;           // [kcap]
@@ -85,6 +103,8 @@ int host_axis_M(double alpha, double ell);
 
 // Launchers (rbe_kspace.cu).  All asynchronous on ctx->stream.
 rbe_status ensure_tables(rbe_ctx ctx);
+rbe_status ensure_table_capacity(rbe_ctx ctx, int need);
+rbe_status launch_tables(rbe_ctx ctx, const double* box_dev);
 rbe_status ensure_k_capacity(rbe_ctx ctx, int K);
 rbe_status launch_sample(rbe_ctx ctx, uint64_t step, int P);
 rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int K,

@@ -53,13 +53,6 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// 53-bit uniform in [0, 1): all of a and the top 21 bits of b.
-__device__ __forceinline__ double uniform53(uint32_t a, uint32_t b)
-{
-    const unsigned long long bits = ((unsigned long long)a << 21) | (unsigned long long)(b >> 11);
-    return __dmul_rn((double)bits, 0x1.0p-53);
-}
-
 // ---------------------------------------------------------------------------------
 // exp(x) for x in [-700, 0]: n = rint(x / ln2), r = (x - n ln2_hi) - n ln2_lo with a
 // 32-significant-bit head of ln2 (n * head exact), e^r by its Taylor series to degree 13
@@ -237,17 +230,6 @@ __device__ __forceinline__ void ff_add2(float& hi, float& lo, float xh, float xl
 {
     ff_add(hi, lo, xh);
     lo += xl;
-}
-
-// 53-bit uniform u = (a << 21 | b >> 11) * 2^-53 as the bit pattern of a double, built
-// with integer operations (exact, the same value as the FP64 conversion).
-__device__ __forceinline__ unsigned long long uniform53_bits(uint32_t a, uint32_t b)
-{
-    const unsigned long long v = ((unsigned long long)a << 21) | (unsigned long long)(b >> 11);
-    if (v == 0ull) return 0ull;
-    const int shift = __clzll(v) - 11;
-    const unsigned long long mant = v << shift;
-    return ((unsigned long long)(1022 - shift) << 52) | (mant & 0xFFFFFFFFFFFFFull);
 }
 
 }  // namespace rbe

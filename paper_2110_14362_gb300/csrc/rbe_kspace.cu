@@ -1,12 +1,13 @@
 // RBE k-space kernels for sm_103a and their launchers.
 //
-// One evaluation (Sec. 4.2 of the paper) is five launches on the context's stream:
-//   k_tables   per-axis weights exp(-c m^2), cumulative sums, H and S        Eqs. (S), (psf)
-//                (only when the box changed)
+// One evaluation (Sec. 4.2 of the paper) is up to five launches on the context's stream:
+//   k_tables   per-axis weights exp(-c m^2) as exact integers, their cumulative sums, H,
+//              S and the box constants (KState)                            Eqs. (S), (psf)
+//              (only when the box changed; the box may come from the host or the device)
 //   k_sample   one thread per frequency: Philox -> 3 uniforms -> inverse CDF  Eq. (probexpression)
 //   k_rho_*    particle-chunk x frequency-tile blocks: partial rho(k_l) per chunk
-//   k_reduce   fixed-order FP64 sum of the partials -> rho(k_l), the per-frequency
-//              force coefficients, and (last block) the energy and the 3x3 virial
+//   k_reduce*  fixed-order sum of the partials -> rho(k_l), the per-frequency terms and
+//              force coefficients (and, on the FP64 path, the energy and virial)
 //                                              Eq. (apppress); App. C Eq. (pressuretensorflexible)
 //   k_force_*  particle tiles x all frequencies: F_i                             Eq. (appforce)
 // No floating-point atomics: every sum runs in an order fixed by (N, K, plan), so
@@ -23,107 +24,175 @@
 
 namespace rbe {
 
-constexpr int kT = 128;        // threads per block of the force pass
-constexpr int kForceKT = 256;  // frequencies staged per tile in the force pass
+constexpr int kT = 128;               // threads per block of the FP64 force pass
+constexpr int kForceKT = 256;         // frequencies staged per tile in the FP64 force pass
+constexpr int kTableThreads = 1024;   // k_tables block
+constexpr int kMaxRhoThreads = 256;
+constexpr int kReduceThreads = 256;
+constexpr int kForceWarps = 8;
+constexpr int kForceThreads = 32 * kForceWarps;
+constexpr int kForcePPT = 4;
+constexpr int kForceRound = 32 * kForcePPT;  // particles per round of the FP32 force pass
+constexpr int kForceStageK = 2048;           // frequencies staged at once (dynamic shared memory)
+
+__device__ __forceinline__ FixScale fs(const FixScaleH& h) { return FixScale{h.q, h.e}; }
 
 // =================================================================================
-// Sampling tables (Sec. 4.2 Eqs. (S), (psf); App. C item 1).
-__global__ void k_tables(double bx, double by, double bz, const double* __restrict__ box_dev, double alpha,
-                         int P, double* __restrict__ cdf, int cap, TableHeader* __restrict__ hdr,
-                         unsigned* __restrict__ status)
+// Tables and box constants (Sec. 4.2 Eqs. (S), (psf); App. C item 1).  One block.
+// Per axis: c = pi^2/(alpha l^2), M = ceil(sqrt(60 ln2 / c)), w_a = exp(-c a^2) by the
+// library's own exponential, W_j = rint(w_{|j-M|} 2^sh) with sh = 62 - bitlength(2M+1),
+// C_j = W_0 + ... + W_j (exact integers: any summation order gives the same bits, so the
+// prefix sum runs in parallel), H = C_2M 2^-sh, S = H_x H_y H_z - 1.
+__device__ __forceinline__ int bitlength(unsigned x) { return 32 - __clz(x); }
+
+__global__ void __launch_bounds__(kTableThreads)
+k_tables(double bx, double by, double bz, const double* __restrict__ box_dev, double alpha, int P,
+         unsigned long long* __restrict__ cum, int cap, KState* __restrict__ ks, unsigned* __restrict__ status)
 {
-    __shared__ int sM[3];
-    __shared__ double sc[3];
-    const int tid = threadIdx.x;
+    __shared__ int sM[3], sSh[3];
+    __shared__ double sc[3], sL[3];
+    __shared__ unsigned long long wsum[kTableThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid < 3) {
-        double ell = box_dev ? box_dev[tid] : (tid == 0 ? bx : (tid == 1 ? by : bz));
-        double c = axis_c(alpha, ell);
+        const double ell = box_dev ? box_dev[tid] : (tid == 0 ? bx : (tid == 1 ? by : bz));
+        const double c = axis_c(alpha, ell);
         int M = axis_M(c);
         if (2 * M + 1 > cap) {
             atomicOr(status, kStatusTable);
             M = (cap - 1) / 2;
         }
-        sM[tid] = M;
+        sL[tid] = ell;
         sc[tid] = c;
+        sM[tid] = M;
+        sSh[tid] = 62 - bitlength((unsigned)(2 * M + 1));
     }
     __syncthreads();
+    // integer weights, written once per |m| into both halves of the row
     for (int t = 0; t < 3; ++t) {
         const int M = sM[t];
-        const double c = sc[t];
-        double* row = cdf + (size_t)t * cap;
-        for (int a = tid; a <= M; a += blockDim.x) {
-            const double v = table_exp(-__dmul_rn(c, (double)a * (double)a));
-            row[M + a] = v;
-            row[M - a] = v;
+        unsigned long long* row = cum + (size_t)t * cap;
+        for (int a = tid; a <= M; a += kTableThreads) {
+            const double v = table_exp(-__dmul_rn(sc[t], (double)a * (double)a));
+            const unsigned long long W = (unsigned long long)__double2ll_rn(ldexp(v, sSh[t]));
+            row[M + a] = W;
+            row[M - a] = W;
         }
     }
     __syncthreads();
-    if (tid < 3) {
-        const int M = sM[tid];
-        double* row = cdf + (size_t)tid * cap;
-        double acc = 0.0;
-        for (int j = 0; j <= 2 * M; ++j) {
-            acc = __dadd_rn(acc, row[j]);
-            row[j] = acc;
+    // inclusive prefix sums, one row at a time: each thread owns a contiguous segment
+    for (int t = 0; t < 3; ++t) {
+        const int n = 2 * sM[t] + 1;
+        unsigned long long* row = cum + (size_t)t * cap;
+        const int per = (n + kTableThreads - 1) / kTableThreads;
+        const int j0 = min(n, tid * per), j1 = min(n, j0 + per);
+        unsigned long long local = 0;
+        for (int j = j0; j < j1; ++j) local += row[j];
+        unsigned long long incl = local;  // inclusive scan of the segment sums over the block
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long o = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += o;
         }
-        hdr->M[tid] = M;
-        hdr->H[tid] = acc;
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long v = wsum[lane];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned long long o = __shfl_up_sync(0xffffffffu, v, off);
+                if (lane >= off) v += o;
+            }
+            wsum[lane] = v;
+        }
+        __syncthreads();
+        unsigned long long run = incl - local + (warp > 0 ? wsum[warp - 1] : 0ull);
+        for (int j = j0; j < j1; ++j) {
+            run += row[j];
+            row[j] = run;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     if (tid == 0) {
-        const double S = __dsub_rn(__dmul_rn(__dmul_rn(hdr->H[0], hdr->H[1]), hdr->H[2]), 1.0);
-        hdr->S = S;
-        hdr->wP = S / (double)P;  // the importance weight S/P of every sampled frequency
+        double H[3];
+        for (int t = 0; t < 3; ++t) {
+            const unsigned long long C = cum[(size_t)t * cap + 2 * sM[t]];
+            H[t] = ldexp((double)C, -sSh[t]);
+            ks->H[t] = H[t];
+            ks->M[t] = sM[t];
+            ks->sh[t] = sSh[t];
+            ks->L[t] = sL[t];
+            const double inv = 1.0 / sL[t];
+            ks->inv[t] = inv;
+            const unsigned long long b = (unsigned long long)__double_as_longlong(inv);
+            const int e = (int)((b >> 52) & 0x7ff) - 1075;
+            ks->sc[t].q = ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 11;
+            ks->sc[t].e = e - 11;
+        }
+        const double S = __dsub_rn(__dmul_rn(__dmul_rn(H[0], H[1]), H[2]), 1.0);
+        const double V = sL[0] * sL[1] * sL[2];
+        ks->S = S;
+        ks->wP = S / (double)P;
+        ks->V = V;
+        ks->alpha = alpha;
+        ks->P = P;
+        ks->cx = (float)(2.0 * kPi / sL[0]);
+        ks->cy = (float)(2.0 * kPi / sL[1]);
+        ks->cz = (float)(2.0 * kPi / sL[2]);
+        ks->ce = (float)(2.0 * kPi / V);
+        ks->cb = (float)(4.0 * kPi / V);
+        ks->inv4a = (float)(1.0 / (4.0 * alpha));
+        ks->cself = (float)(-sqrt(alpha / kPi));
     }
 }
 
-// Smallest j in [0, 2M] with target < cdf[j], minus M.  cdf is non-decreasing and
-// non-negative, and for non-negative doubles the order of the values is the order of
-// their bit patterns, so the search compares 64-bit integers (no FP64 instructions).
-__device__ __forceinline__ int inverse_cdf_bits(const unsigned long long* __restrict__ row, int M,
-                                                unsigned long long target)
+// Smallest j in [0, 2M] with T < C_j, minus M (C non-decreasing).
+__device__ __forceinline__ int inverse_cdf_int(const unsigned long long* __restrict__ row, int M,
+                                               unsigned long long T)
 {
     int lo = 0, hi = 2 * M;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (target < row[mid]) hi = mid;
+        if (T < row[mid]) hi = mid;
         else lo = mid + 1;
     }
     return lo - M;
 }
 
+// T = floor(U * C_2M / 2^53) for a 53-bit uniform integer U (exact, 128-bit product).
+__device__ __forceinline__ unsigned long long scaled_target(unsigned long long U, unsigned long long Ctot)
+{
+    const unsigned long long hi = __umul64hi(U, Ctot), lo = U * Ctot;
+    return (hi << 11) | (lo >> 53);
+}
+
 // =================================================================================
 // Frequency sampling (Sec. 4.2-4.3): sample l uses Philox key (seed_lo, seed_hi) and
-// counters (l, 2 attempt + half, step_lo, step_hi24); redraw while m = 0.  The block
-// first copies the three cumulative tables to shared memory when they fit
-// (smem_cap > 0).  Per axis the only FP64 instruction is target = u * H; u is built from
-// its bits and the search compares bit patterns.
-__global__ void k_sample(uint64_t seed, uint64_t step, int P, const double* __restrict__ cdf, int cap,
-                         int smem_cap, const TableHeader* __restrict__ hdr, int4* __restrict__ m_out,
+// counters (l, 2 attempt + half, step_lo, step_hi24); redraw while m = 0.  Integer
+// operations only: U from 53 bits of Philox output, T = floor(U C_2M / 2^53), and the
+// search over the integer cumulative weights.  The block copies the three rows to shared
+// memory when they fit (smem_cap > 0).
+__global__ void k_sample(uint64_t seed, uint64_t step, int P, const unsigned long long* __restrict__ cum,
+                         int cap, int smem_cap, const KState* __restrict__ ks, int4* __restrict__ m_out,
                          double* __restrict__ w_out, unsigned* __restrict__ status)
 {
-    extern __shared__ unsigned long long s_cdf[];
+    extern __shared__ unsigned long long s_cum[];
     pdl_trigger();  // the rho pass may start staging its particles meanwhile
-    const double wP = hdr->wP;
-    const unsigned long long* gx = reinterpret_cast<const unsigned long long*>(cdf);
-    const unsigned long long* tx = gx;
-    const unsigned long long* ty = gx + cap;
-    const unsigned long long* tz = gx + 2 * (size_t)cap;
-    if (smem_cap > 0) {  // smem_cap == cap: copy the three rows whole, without waiting for M
-        for (int j = threadIdx.x; j < 3 * smem_cap; j += blockDim.x) s_cdf[j] = gx[j];
-    }
-    const int Mx = hdr->M[0], My = hdr->M[1], Mz = hdr->M[2];
+    const double wP = ks->wP;
+    const unsigned long long* tx = cum;
+    const unsigned long long* ty = cum + cap;
+    const unsigned long long* tz = cum + 2 * (size_t)cap;
+    if (smem_cap > 0)  // smem_cap == cap: copy the three rows whole, without waiting for M
+        for (int j = threadIdx.x; j < 3 * smem_cap; j += blockDim.x) s_cum[j] = cum[j];
+    const int Mx = ks->M[0], My = ks->M[1], Mz = ks->M[2];
     if (smem_cap > 0) {
         __syncthreads();
-        tx = s_cdf;
-        ty = s_cdf + smem_cap;
-        tz = s_cdf + 2 * smem_cap;
+        tx = s_cum;
+        ty = s_cum + smem_cap;
+        tz = s_cum + 2 * smem_cap;
     }
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= P) return;
-    const double Hx = __longlong_as_double((long long)tx[2 * Mx]);
-    const double Hy = __longlong_as_double((long long)ty[2 * My]);
-    const double Hz = __longlong_as_double((long long)tz[2 * Mz]);
+    const unsigned long long Cx = tx[2 * Mx], Cy = ty[2 * My], Cz = tz[2 * Mz];
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     const uint32_t c2 = (uint32_t)step, c3 = (uint32_t)((step >> 32) & 0xFFFFFFu);
     int4 m = make_int4(0, 0, 0, 0);
@@ -131,12 +200,9 @@ __global__ void k_sample(uint64_t seed, uint64_t step, int P, const double* __re
     for (uint32_t attempt = 0; attempt < kMaxAttempts; ++attempt) {
         const uint4 w0 = philox4x32_10(make_uint4((uint32_t)l, 2u * attempt, c2, c3), k0, k1);
         const uint4 w1 = philox4x32_10(make_uint4((uint32_t)l, 2u * attempt + 1u, c2, c3), k0, k1);
-        const double ux = __longlong_as_double((long long)uniform53_bits(w0.x, w0.y));
-        const double uy = __longlong_as_double((long long)uniform53_bits(w0.z, w0.w));
-        const double uz = __longlong_as_double((long long)uniform53_bits(w1.x, w1.y));
-        m.x = inverse_cdf_bits(tx, Mx, (unsigned long long)__double_as_longlong(__dmul_rn(ux, Hx)));
-        m.y = inverse_cdf_bits(ty, My, (unsigned long long)__double_as_longlong(__dmul_rn(uy, Hy)));
-        m.z = inverse_cdf_bits(tz, Mz, (unsigned long long)__double_as_longlong(__dmul_rn(uz, Hz)));
+        m.x = inverse_cdf_int(tx, Mx, scaled_target(((unsigned long long)w0.x << 21) | (w0.y >> 11), Cx));
+        m.y = inverse_cdf_int(ty, My, scaled_target(((unsigned long long)w0.z << 21) | (w0.w >> 11), Cy));
+        m.z = inverse_cdf_int(tz, Mz, scaled_target(((unsigned long long)w1.x << 21) | (w1.y >> 11), Cz));
         if (m.x != 0 || m.y != 0 || m.z != 0) {
             found = true;
             break;
@@ -232,14 +298,14 @@ __device__ __forceinline__ uint4 load_fixed(const double* __restrict__ pos, cons
 // ACC: RBE_RHO_FP32 (plain FP32 within a staged tile), RBE_RHO_COMP32 (Kahan-compensated
 //      FP32 within a tile), RBE_RHO_FP64 (FP64 per pair; slow on GB300, for reference).
 // Partials: float4 (Re hi, Re lo, Im hi, Im lo) at [l * nchunks + c]; row K holds the
-// chunk's sum of q^2 (hi, lo).
-constexpr int kMaxRhoThreads = 256;
-
+// chunk's sum of q^2 (hi, lo).  The box constants are read from ks before pdl_wait: the
+// kernel that wrote them (k_tables) runs before the sampler, which is this launch's
+// predecessor, and the sampler starts only after k_tables has completed.
 template <int ACC>
 __global__ void __launch_bounds__(kMaxRhoThreads, 8)
-k_rho_f32(const double* __restrict__ pos, const double* __restrict__ q, int64_t N, FixScale scx, FixScale scy,
-          FixScale scz, const int4* __restrict__ m, int K, int64_t chunk_len, int nchunks,
-          float4* __restrict__ partials, unsigned* __restrict__ status)
+k_rho_f32(const double* __restrict__ pos, const double* __restrict__ q, int64_t N, const KState* __restrict__ ks,
+          const int4* __restrict__ m, int K, int64_t chunk_len, int nchunks, float4* __restrict__ partials,
+          unsigned* __restrict__ status)
 {
     __shared__ uint4 sp[kMaxRhoThreads];
     __shared__ float red[2][32];
@@ -247,6 +313,7 @@ k_rho_f32(const double* __restrict__ pos, const double* __restrict__ q, int64_t 
     const int tid = threadIdx.x, nt = blockDim.x;
     const int l = blockIdx.x * nt + tid;
     const int c = blockIdx.y;
+    const FixScale scx = fs(ks->sc[0]), scy = fs(ks->sc[1]), scz = fs(ks->sc[2]);
     float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f, q2h = 0.f, q2l = 0.f;
     double are = 0.0, aim = 0.0;
     const int64_t start = (int64_t)c * chunk_len;
@@ -324,15 +391,16 @@ k_rho_f32(const double* __restrict__ pos, const double* __restrict__ q, int64_t 
 
 // rho pass, FP64 path: s = r / l wrapped to [0, 1); t = m.s - rint(m.s); sincospi(2t).
 __global__ void __launch_bounds__(kMaxRhoThreads)
-k_rho_f64(const double* __restrict__ pos, const double* __restrict__ q, int64_t N, double ilx, double ily,
-          double ilz, const int4* __restrict__ m, int K, int64_t chunk_len, int nchunks,
-          double2* __restrict__ partials, unsigned* __restrict__ status)
+k_rho_f64(const double* __restrict__ pos, const double* __restrict__ q, int64_t N, const KState* __restrict__ ks,
+          const int4* __restrict__ m, int K, int64_t chunk_len, int nchunks, double2* __restrict__ partials,
+          unsigned* __restrict__ status)
 {
     __shared__ double4_32a sp[kMaxRhoThreads];
     __shared__ double red[32];
     const int tid = threadIdx.x, nt = blockDim.x;
     const int l = blockIdx.x * nt + tid;
     const int c = blockIdx.y;
+    const double ilx = ks->inv[0], ily = ks->inv[1], ilz = ks->inv[2];
     const int4 mv = l < K ? m[l] : make_int4(0, 0, 0, 0);
     const double mx = mv.x, my = mv.y, mz = mv.z;
     double re = 0.0, im = 0.0, q2 = 0.0;
@@ -372,20 +440,16 @@ k_rho_f64(const double* __restrict__ pos, const double* __restrict__ q, int64_t 
 }
 
 // =================================================================================
-// Reduction of the partials: block l (of K + 1) sums its row over the chunks in a fixed
-// order (strided per thread, then a fixed tree), forms the per-frequency terms, and the
-// last block to finish sums those over l in a fixed order.
+// FP64 reduction: block l (of K + 1) sums its row over the chunks in a fixed order and
+// forms the per-frequency terms; the last block to finish sums those over l.
 //   e_l = (2 pi / V) w_l |rho_l|^2 / |k_l|^2
 //   W  += e_l [I - 2 (1/|k_l|^2 + 1/4a) k_l k_l]
 //   beta_l = w_l 4 pi / (V |k_l|^2), A_l = beta_l Im rho_l, B_l = beta_l Re rho_l, so that
 //   F_i = q_i sum_l k_l (sin(k_l.r_i) B_l - cos(k_l.r_i) A_l).
-constexpr int kReduceThreads = 256;
-
 __global__ void __launch_bounds__(kReduceThreads)
 k_reduce(const double2* __restrict__ partials, int nchunks, int K, const int4* __restrict__ m,
-         const double* __restrict__ w, double bx, double by, double bz, double alpha,
-         double2* __restrict__ rho, double* __restrict__ terms, int4* __restrict__ coef_m,
-         float4* __restrict__ coef_f, double2* __restrict__ coef_d, unsigned* __restrict__ counter,
+         const double* __restrict__ w, const KState* __restrict__ ks, double2* __restrict__ rho,
+         double* __restrict__ terms, double2* __restrict__ coef_d, unsigned* __restrict__ counter,
          unsigned* __restrict__ status, double* __restrict__ W_out, double* __restrict__ E_out)
 {
     __shared__ double red[32];
@@ -401,10 +465,12 @@ k_reduce(const double2* __restrict__ partials, int nchunks, int K, const int4* _
     }
     re = block_sum(re, red);
     im = block_sum(im, red);
+    const double alpha = ks->alpha;
     if (threadIdx.x == 0) {
         double* t = terms + (size_t)l * 8;
         if (l < K) {
             const int4 mi = m[l];
+            const double bx = ks->L[0], by = ks->L[1], bz = ks->L[2];
             const double V = bx * by * bz;
             const double kx = 2.0 * kPi * mi.x / bx, ky = 2.0 * kPi * mi.y / by, kz = 2.0 * kPi * mi.z / bz;
             const double kk = kx * kx + ky * ky + kz * kz;
@@ -420,11 +486,8 @@ k_reduce(const double2* __restrict__ partials, int nchunks, int K, const int4* _
             t[6] = -e * b * ky * kz;
             t[7] = 0.0;
             const double beta = w[l] * (4.0 * kPi / (V * kk));
-            const double A = beta * im, B = beta * re;
             rho[l] = make_double2(re, im);
-            coef_d[l] = make_double2(A, B);
-            coef_m[l] = make_int4(mi.x, mi.y, mi.z, __float_as_int((float)A));
-            coef_f[l] = make_float4((float)B, (float)mi.x, (float)mi.y, (float)mi.z);
+            coef_d[l] = make_double2(beta * im, beta * re);
             if (!isfinite(re) || !isfinite(im)) atomicOr(status, kStatusNonFinite);
         } else {
             t[0] = re;  // sum of q^2
@@ -476,17 +539,9 @@ k_reduce(const double2* __restrict__ partials, int nchunks, int K, const int4* _
 // =================================================================================
 // Reduction for the FP32-phase path.  Block l (of K + 1) sums row l of the partials over
 // the chunks as float-float in a fixed order, then forms the per-frequency terms in FP32
-// (the path's stated accuracy is 1e-5 relative):
-//   e_l = (2 pi / V) w_l |rho_l|^2 / |k_l|^2,  W_l = e_l [I - 2 (1/|k_l|^2 + 1/4a) k_l k_l],
-//   A_l = beta_l Im rho_l, B_l = beta_l Re rho_l with beta_l = w_l 4 pi / (V |k_l|^2).
-// Row K carries the sum of q^2.  The sums over l run in the force launch (k_force_f32's
-// extra block), concurrently with the force pass.  Constants come from the host:
-//   cx, cy, cz = 2 pi / l,  ce = 2 pi / V,  cb = 4 pi / V,  inv4a = 1 / (4 alpha),
-//   cself = -sqrt(alpha / pi).
-struct ReduceConsts32 {
-    float cx, cy, cz, ce, cb, inv4a, cself;
-};
-
+// (the path's stated accuracy is 1e-5 relative).  Row K carries the sum of q^2.  The sums
+// over l run in the force launch (k_force_f32's extra block), concurrently with the force
+// pass.
 __device__ __forceinline__ double ff_to_double(float hi, float lo)
 {
     return __longlong_as_double((long long)float_to_double_bits(__float_as_uint(hi))) +
@@ -495,19 +550,21 @@ __device__ __forceinline__ double ff_to_double(float hi, float lo)
 
 __global__ void __launch_bounds__(kReduceThreads)
 k_reduce_f32(const float4* __restrict__ partials, int nchunks, int K, const int4* __restrict__ m,
-             const double* __restrict__ w, ReduceConsts32 cst, double2* __restrict__ rho,
+             const double* __restrict__ w, const KState* __restrict__ ks, double2* __restrict__ rho,
              float* __restrict__ terms, int4* __restrict__ coef_m, float4* __restrict__ coef_f,
              unsigned* __restrict__ status)
 {
     __shared__ float red[2][32];
     const int l = blockIdx.x;
     // the sampler completed before the rho pass passed its wait, and the rho pass lets this
-    // launch start only after that wait: m and w are final here
+    // launch start only after that wait: m, w and ks are final here
     int4 mi = make_int4(0, 0, 0, 0);
     double wd = 0.0;
+    float cx = 0.f, cy = 0.f, cz = 0.f, ce = 0.f, cb = 0.f, inv4a = 0.f;
     if (threadIdx.x == 0 && l < K) {
         mi = m[l];
         wd = w[l];
+        cx = ks->cx; cy = ks->cy; cz = ks->cz; ce = ks->ce; cb = ks->cb; inv4a = ks->inv4a;
     }
     pdl_wait();
     pdl_trigger();
@@ -529,12 +586,12 @@ k_reduce_f32(const float4* __restrict__ partials, int nchunks, int K, const int4
     }
     const float re = rh + rl, im = ih + il;
     const float wl = double_to_float_int((unsigned long long)__double_as_longlong(wd));
-    const float kx = cst.cx * (float)mi.x, ky = cst.cy * (float)mi.y, kz = cst.cz * (float)mi.z;
+    const float kx = cx * (float)mi.x, ky = cy * (float)mi.y, kz = cz * (float)mi.z;
     const float kk = kx * kx + ky * ky + kz * kz;
     const float ikk = 1.0f / kk;
     const float rho2 = re * re + im * im;
-    const float e = cst.ce * wl * rho2 * ikk;
-    const float b = 2.0f * (ikk + cst.inv4a);
+    const float e = ce * wl * rho2 * ikk;
+    const float b = 2.0f * (ikk + inv4a);
     t[0] = e;
     t[1] = e * (1.0f - b * kx * kx);
     t[2] = e * (1.0f - b * ky * ky);
@@ -543,7 +600,7 @@ k_reduce_f32(const float4* __restrict__ partials, int nchunks, int K, const int4
     t[5] = -e * b * kx * kz;
     t[6] = -e * b * ky * kz;
     t[7] = 0.f;
-    const float beta = cst.cb * wl * ikk;
+    const float beta = cb * wl * ikk;
     const float A = beta * im, B = beta * re;
     rho[l] = make_double2(ff_to_double(rh, rl), ff_to_double(ih, il));
     coef_m[l] = make_int4(mi.x, mi.y, mi.z, __float_as_int(A));
@@ -551,11 +608,8 @@ k_reduce_f32(const float4* __restrict__ partials, int nchunks, int K, const int4
     if (!isfinite(re) || !isfinite(im)) atomicOr(status, kStatusNonFinite);
 }
 
-// Energy and virial: fixed-order float-float sums of the per-frequency terms over l,
-// by one block of kForceThreads threads.
-constexpr int kForceWarps = 8;
-constexpr int kForceThreads = 32 * kForceWarps;
-
+// Energy and virial: fixed-order float-float sums of the per-frequency terms over l, by one
+// block of kForceThreads threads.
 __device__ void final_sums_f32(const float* __restrict__ terms, int K, float cself, double* __restrict__ W_out,
                                double* __restrict__ E_out, unsigned* __restrict__ status)
 {
@@ -618,23 +672,19 @@ __device__ void final_sums_f32(const float* __restrict__ terms, int K, float cse
 //   F_i,theta = q_i (2 pi / l_theta) sum_l m_l,theta (sin B_l - cos A_l)
 // is formed in FP32 and widened to double exactly.  The launch carries one extra block
 // that computes the energy and virial sums (final_sums_f32) meanwhile.
-constexpr int kForcePPT = 4;
-constexpr int kForceRound = 32 * kForcePPT;  // particles per round
-constexpr int kForceStageK = 2048;           // frequencies staged at once (dynamic shared memory)
-
 __global__ void __launch_bounds__(kForceThreads, 5)
 k_force_f32(const double* __restrict__ pos, const double* __restrict__ q, int64_t N, int64_t per_block,
-            FixScale scx, FixScale scy, FixScale scz, float cx, float cy, float cz,
-            const int4* __restrict__ coef_m, const float4* __restrict__ coef_f, int K, double* __restrict__ F,
-            unsigned* __restrict__ status, const float* __restrict__ terms, float cself,
+            const KState* __restrict__ ks, const int4* __restrict__ coef_m, const float4* __restrict__ coef_f,
+            int K, double* __restrict__ F, unsigned* __restrict__ status, const float* __restrict__ terms,
             double* __restrict__ W_out, double* __restrict__ E_out)
 {
     extern __shared__ int4 s_dyn[];
     __shared__ uint4 sp[kForceThreads];
     __shared__ float part[kForceWarps][3][kForceRound];
+    __shared__ unsigned bad;
     if (blockIdx.x == gridDim.x - 1) {
         pdl_wait();
-        final_sums_f32(terms, K, cself, W_out, E_out, status);
+        final_sums_f32(terms, K, ks->cself, W_out, E_out, status);
         return;
     }
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -642,12 +692,13 @@ k_force_f32(const double* __restrict__ pos, const double* __restrict__ q, int64_
     int4* sm = s_dyn;
     float4* sf = reinterpret_cast<float4*>(s_dyn + kstage);
     unsigned long long* Fb = reinterpret_cast<unsigned long long*>(F);
+    const FixScale scx = fs(ks->sc[0]), scy = fs(ks->sc[1]), scz = fs(ks->sc[2]);
+    const float cx = ks->cx, cy = ks->cy, cz = ks->cz;
     const int64_t b0 = (int64_t)blockIdx.x * per_block;
     const int64_t b1 = min(N, b0 + per_block);
     const bool multi = K > kstage;  // frequency tiles must be restaged for every round
     bool staged = false;
     // the first particle tile is converted before waiting for the reduction (inputs only)
-    __shared__ unsigned bad;
     if (tid == 0) bad = 0u;
     __syncthreads();
     const uint4 first = b0 + tid < b1 ? load_fixed(pos, q, b0 + tid, scx, scy, scz, &bad) : make_uint4(0u, 0u, 0u, 0u);
@@ -717,17 +768,17 @@ k_force_f32(const double* __restrict__ pos, const double* __restrict__ q, int64_
     }
 }
 
-// Force pass, FP64 path (same blocking, FP64 throughout).
+// Force pass, FP64 path: particle tiles of kT * PPT, frequencies staged kForceKT at a time.
 template <int PPT>
 __global__ void __launch_bounds__(kT) k_force_f64(const double* __restrict__ pos, const double* __restrict__ q,
-                                                  int64_t N, int64_t per_block, double ilx, double ily,
-                                                  double ilz, const int4* __restrict__ mk,
-                                                  const double2* __restrict__ coef_d, int K,
-                                                  double* __restrict__ F)
+                                                  int64_t N, int64_t per_block, const KState* __restrict__ ks,
+                                                  const int4* __restrict__ mk, const double2* __restrict__ coef_d,
+                                                  int K, double* __restrict__ F)
 {
     __shared__ double4_32a sk[kForceKT];  // (mx, my, mz, A)
     __shared__ double sb[kForceKT];       // B
     const int tid = threadIdx.x;
+    const double ilx = ks->inv[0], ily = ks->inv[1], ilz = ks->inv[2];
     const bool one_tile = K <= kForceKT;
     if (one_tile) {
         for (int j = tid; j < K; j += kT) {
@@ -810,23 +861,36 @@ static rbe_status check_launch(rbe_ctx ctx, const char* what)
     return RBE_OK;
 }
 
+// Capacity of the table rows: the host estimate of 2M+1 with headroom for boxes that grow
+// on the device.
+rbe_status ensure_table_capacity(rbe_ctx ctx, int need)
+{
+    if (need <= ctx->d.tab_cap) return RBE_OK;
+    if (ctx->d.cum) cudaFree(ctx->d.cum);
+    ctx->d.cum = nullptr;
+    ctx->d.tab_cap = 0;
+    const int cap = need + need / 4 + 16;
+    cudaError_t err = cudaMalloc(&ctx->d.cum, sizeof(unsigned long long) * 3 * (size_t)cap);
+    if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaMalloc(tables)");
+    ctx->d.tab_cap = cap;
+    return RBE_OK;
+}
+
+rbe_status launch_tables(rbe_ctx ctx, const double* box_dev)
+{
+    k_tables<<<1, kTableThreads, 0, ctx->stream>>>(ctx->box[0], ctx->box[1], ctx->box[2], box_dev, ctx->alpha,
+                                                   ctx->P, ctx->d.cum, ctx->d.tab_cap, ctx->d.ks, ctx->d.status);
+    return check_launch(ctx, "k_tables");
+}
+
 rbe_status ensure_tables(rbe_ctx ctx)
 {
     if (!ctx->tables_dirty) return RBE_OK;
     int need = 0;
     for (int t = 0; t < 3; ++t) need = std::max(need, 2 * host_axis_M(ctx->alpha, ctx->box[t]) + 1);
-    if (need > ctx->d.tab_cap) {
-        if (ctx->d.cdf) cudaFree(ctx->d.cdf);
-        ctx->d.cdf = nullptr;
-        ctx->d.tab_cap = 0;
-        const int cap = need + need / 4 + 16;  // headroom for boxes that grow on the device
-        cudaError_t err = cudaMalloc(&ctx->d.cdf, sizeof(double) * 3 * (size_t)cap);
-        if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaMalloc(tables)");
-        ctx->d.tab_cap = cap;
-    }
-    k_tables<<<1, 256, 0, ctx->stream>>>(ctx->box[0], ctx->box[1], ctx->box[2], nullptr, ctx->alpha, ctx->P,
-                                         ctx->d.cdf, ctx->d.tab_cap, ctx->d.hdr, ctx->d.status);
-    rbe_status st = check_launch(ctx, "k_tables");
+    rbe_status st = ensure_table_capacity(ctx, need);
+    if (st != RBE_OK) return st;
+    st = launch_tables(ctx, nullptr);
     if (st == RBE_OK) ctx->tables_dirty = false;
     return st;
 }
@@ -863,24 +927,25 @@ rbe_status launch_sample(rbe_ctx ctx, uint64_t step, int P)
     if (st != RBE_OK) return st;
     record_event(ctx, 0);
     const int threads = 128;
-    const size_t smem = sizeof(double) * 3 * (size_t)ctx->d.tab_cap;
+    const size_t smem = sizeof(unsigned long long) * 3 * (size_t)ctx->d.tab_cap;
     const int smem_cap = smem <= (size_t)kSampleSmemMax ? ctx->d.tab_cap : 0;
     k_sample<<<(P + threads - 1) / threads, threads, smem_cap ? smem : 0, ctx->stream>>>(
-        ctx->seed, step, P, ctx->d.cdf, ctx->d.tab_cap, smem_cap, ctx->d.hdr, ctx->d.m, ctx->d.w, ctx->d.status);
+        ctx->seed, step, P, ctx->d.cum, ctx->d.tab_cap, smem_cap, ctx->d.ks, ctx->d.m, ctx->d.w, ctx->d.status);
     record_event(ctx, 1);
     return check_launch(ctx, "k_sample");
 }
 
 rbe_status launch_weights_from_list(rbe_ctx ctx, int K, const int32_t* m, const double* w)
 {
-    rbe_status st = ensure_k_capacity(ctx, K);
+    rbe_status st = ensure_tables(ctx);  // the box constants live in the same state
+    if (st != RBE_OK) return st;
+    st = ensure_k_capacity(ctx, K);
     if (st != RBE_OK) return st;
     const int threads = 128;
     k_weights_from_list<<<(K + threads - 1) / threads, threads, 0, ctx->stream>>>(K, m, w, ctx->d.m, ctx->d.w);
     return check_launch(ctx, "k_weights_from_list");
 }
 
-// Resident blocks per SM of a kernel at a block size (cached per process).
 // Resident blocks per SM of a kernel at a block size: the occupancy API's answer, capped
 // by a count from the kernel's own register and shared-memory use (registers are
 // allocated per warp in units of 256).
@@ -914,8 +979,8 @@ static int blocks_per_sm(Kern kern, int threads, size_t dyn_smem = 0)
 
 // Launch plan.  rho pass: frequency tiles of at most 256 threads, sized in whole warps
 // so that few lanes idle; particle chunks so that the grid is one full wave of resident
-// blocks with equal particle counts.  Force pass: one wave of resident blocks with equal
-// particle ranges.
+// blocks with equal particle counts.  Force pass: whole rounds of force_unit particles
+// per block, at most one resident wave.
 static Plan make_plan(rbe_ctx ctx, int64_t N, int K, int rho_bps, int force_bps, int force_unit)
 {
     Plan p{};
@@ -927,8 +992,7 @@ static Plan make_plan(rbe_ctx ctx, int64_t N, int K, int rho_bps, int force_bps,
     p.nchunks = (int)std::min<int64_t>(want, max_chunks);
     p.chunk_len = std::max<int64_t>(1, (N + p.nchunks - 1) / p.nchunks);
     p.nchunks = (int)std::max<int64_t>(1, (N + p.chunk_len - 1) / p.chunk_len);
-    p.ppt = 2;
-    // force pass: whole rounds of force_unit particles per block, at most one resident wave
+    p.ppt = kForcePPT;
     const int64_t resident = std::max<int64_t>(1, (int64_t)ctx->num_sms * force_bps);
     const int64_t rounds = (N + force_unit - 1) / force_unit;
     const int64_t per = rounds > 0 ? (rounds + resident - 1) / resident : 0;  // rounds per block
@@ -955,17 +1019,6 @@ static cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
     return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
-// 1/l as (64-bit mantissa, power of two), from the double 1/l.
-static FixScale fix_scale(double ell)
-{
-    const double inv = 1.0 / ell;
-    unsigned long long b;
-    std::memcpy(&b, &inv, 8);
-    const int e = (int)((b >> 52) & 0x7ff) - 1075;
-    const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    return FixScale{mant << 11, e - 11};
-}
-
 rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int K,
                            bool /*uniform_weight*/, double* F, double* W, double* E)
 {
@@ -976,8 +1029,7 @@ rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const doub
         rho32_threads = blocks_per_sm(k_rho_f32<RBE_RHO_FP32>, kMaxRhoThreads) * kMaxRhoThreads;
         rho64_threads = blocks_per_sm(k_rho_f64, kMaxRhoThreads) * kMaxRhoThreads;
         bps_f64 = blocks_per_sm(k_force_f64<2>, kT);
-        cudaFuncSetAttribute(k_force_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(32 * kForceStageK));
+        cudaFuncSetAttribute(k_force_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(32 * kForceStageK));
     }
     const int kstage = std::min(K, kForceStageK);
     const size_t force_smem = fp64 ? 0 : (size_t)32 * kstage;
@@ -1001,42 +1053,30 @@ rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const doub
         if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaMalloc(partials)");
         d.part_cap = need;
     }
-    const double ilx = 1.0 / ctx->box[0], ily = 1.0 / ctx->box[1], ilz = 1.0 / ctx->box[2];
-    const FixScale scx = fix_scale(ctx->box[0]), scy = fix_scale(ctx->box[1]), scz = fix_scale(ctx->box[2]);
     const dim3 grid(p.ktiles, p.nchunks);
     cudaStream_t s = ctx->stream;
     double2* part64 = static_cast<double2*>(d.partials);
     float4* part32 = static_cast<float4*>(d.partials);
+    const KState* ks = d.ks;
     if (fp64) {
-        k_rho_f64<<<grid, p.kthreads, 0, s>>>(pos, q, N, ilx, ily, ilz, d.m, K, p.chunk_len, p.nchunks, part64,
-                                              d.status);
+        k_rho_f64<<<grid, p.kthreads, 0, s>>>(pos, q, N, ks, d.m, K, p.chunk_len, p.nchunks, part64, d.status);
     } else {
         auto kern = ctx->rho_accum == RBE_RHO_FP64     ? k_rho_f32<RBE_RHO_FP64>
                     : ctx->rho_accum == RBE_RHO_COMP32 ? k_rho_f32<RBE_RHO_COMP32>
                                                        : k_rho_f32<RBE_RHO_FP32>;
-        cudaError_t err = launch_pdl(kern, grid, dim3(p.kthreads), 0, s, pos, q, N, scx, scy, scz,
-                                     (const int4*)d.m, K, p.chunk_len, p.nchunks, part32, d.status);
+        cudaError_t err = launch_pdl(kern, grid, dim3(p.kthreads), 0, s, pos, q, N, ks, (const int4*)d.m, K,
+                                     p.chunk_len, p.nchunks, part32, d.status);
         if (err != cudaSuccess) return cuda_fail(ctx, err, "launch k_rho_f32");
     }
     rbe_status st = check_launch(ctx, "k_rho");
     if (st != RBE_OK) return st;
     record_event(ctx, 2);
-    const double V = ctx->box[0] * ctx->box[1] * ctx->box[2];
-    ReduceConsts32 c;
-    c.cx = (float)(2.0 * kPi / ctx->box[0]);
-    c.cy = (float)(2.0 * kPi / ctx->box[1]);
-    c.cz = (float)(2.0 * kPi / ctx->box[2]);
-    c.ce = (float)(2.0 * kPi / V);
-    c.cb = (float)(4.0 * kPi / V);
-    c.inv4a = (float)(1.0 / (4.0 * ctx->alpha));
-    c.cself = (float)(-std::sqrt(ctx->alpha / kPi));
     if (fp64) {
-        k_reduce<<<K + 1, kReduceThreads, 0, s>>>(part64, p.nchunks, K, d.m, d.w, ctx->box[0], ctx->box[1],
-                                                   ctx->box[2], ctx->alpha, d.rho, d.terms, d.coef_m, d.coef_f,
-                                                   d.coef_d, d.counter, d.status, W, E);
+        k_reduce<<<K + 1, kReduceThreads, 0, s>>>(part64, p.nchunks, K, d.m, d.w, ks, d.rho, d.terms, d.coef_d,
+                                                   d.counter, d.status, W, E);
     } else {
         cudaError_t err = launch_pdl(k_reduce_f32, dim3(K + 1), dim3(kReduceThreads), 0, s, (const float4*)part32,
-                                     p.nchunks, K, (const int4*)d.m, (const double*)d.w, c, d.rho,
+                                     p.nchunks, K, (const int4*)d.m, (const double*)d.w, ks, d.rho,
                                      reinterpret_cast<float*>(d.terms), d.coef_m, d.coef_f, d.status);
         if (err != cudaSuccess) return cuda_fail(ctx, err, "launch k_reduce_f32");
     }
@@ -1045,15 +1085,14 @@ rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const doub
     record_event(ctx, 3);
     if (fp64) {
         if (p.fblocks > 0) {
-            k_force_f64<2><<<p.fblocks, kT, 0, s>>>(pos, q, N, p.per_block, ilx, ily, ilz, d.m, d.coef_d, K, F);
+            k_force_f64<2><<<p.fblocks, kT, 0, s>>>(pos, q, N, p.per_block, ks, d.m, d.coef_d, K, F);
             st = check_launch(ctx, "k_force");
         }
     } else {
         // one extra block computes the energy and virial sums
         cudaError_t err = launch_pdl(k_force_f32, dim3(p.fblocks + 1), dim3(kForceThreads), force_smem, s, pos, q,
-                                     N, p.per_block, scx, scy, scz, c.cx, c.cy, c.cz, (const int4*)d.coef_m,
-                                     (const float4*)d.coef_f, K, F, d.status,
-                                     reinterpret_cast<const float*>(d.terms), c.cself, W, E);
+                                     N, p.per_block, ks, (const int4*)d.coef_m, (const float4*)d.coef_f, K, F,
+                                     d.status, reinterpret_cast<const float*>(d.terms), W, E);
         st = err == cudaSuccess ? RBE_OK : cuda_fail(ctx, err, "launch k_force_f32");
     }
     if (st != RBE_OK) return st;

@@ -18,90 +18,118 @@
 
 namespace rbe {
 
-// Entries per axis table (2M + 1 <= kNoAllocTableCap, i.e. M <= 4095); 3 x 8191 doubles
-// plus a status word: 192 KB per device.
+// Entries per axis table (2M + 1 <= kNoAllocTableCap, i.e. M <= 4095); 3 x 8191 64-bit
+// integers plus a status word: 192 KB per device.
 constexpr int kNoAllocTableCap = 8191;
+constexpr int kNoAllocThreads = 256;
 
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[3 * kNoAllocTableCap + 32];
 
-// Smallest j in [0, 2M] with target < cdf[j], minus M, comparing the bit patterns of
-// non-negative doubles (their order is the order of the values).
-__device__ __forceinline__ int search_bits(const unsigned long long* __restrict__ row, int M, unsigned long long target)
+// Smallest j in [0, 2M] with T < C_j, minus M.
+__device__ __forceinline__ int search_int(const unsigned long long* __restrict__ row, int M, unsigned long long T)
 {
     int lo = 0, hi = 2 * M;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (target < row[mid]) hi = mid;
+        if (T < row[mid]) hi = mid;
         else lo = mid + 1;
     }
     return lo - M;
 }
 
-// One block: builds the three tables in the scratch array exactly as k_tables does (same
-// operations in the same order, so the same bits), then draws all P samples as k_sample
-// does.  The status word at scratch[3 * cap] is cleared at the start of every call.
-__global__ void __launch_bounds__(256)
+// One block: builds the three integer tables in the scratch array exactly as k_tables does
+// (the same weights; integer prefix sums are exact in any order), then draws all P samples
+// as k_sample does.  The status word at scratch[3 * cap] is cleared at the start of every
+// call.
+__global__ void __launch_bounds__(kNoAllocThreads)
 k_sample_noalloc(unsigned long long* __restrict__ scratch, double bx, double by, double bz, double alpha, int P,
                  uint64_t seed, uint64_t step, int32_t* __restrict__ m_out, double* __restrict__ S_out)
 {
-    __shared__ int sM[3];
+    __shared__ int sM[3], sSh[3];
     __shared__ double sc[3];
-    __shared__ double sH[3];
-    double* cdf = reinterpret_cast<double*>(scratch);
+    __shared__ unsigned long long wsum[kNoAllocThreads / 32];
     unsigned* status = reinterpret_cast<unsigned*>(scratch + 3 * kNoAllocTableCap);
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) *status = 0u;  // the array keeps the previous call's contents
     __syncthreads();
     if (tid < 3) {
         const double ell = tid == 0 ? bx : (tid == 1 ? by : bz);
         const double c = axis_c(alpha, ell);
-        sc[tid] = c;
         int M = axis_M(c);  // the host checked 2M + 1 <= kNoAllocTableCap; clamp all the same
         if (2 * M + 1 > kNoAllocTableCap) {
             atomicOr(status, kStatusTable);
             M = (kNoAllocTableCap - 1) / 2;
         }
+        sc[tid] = c;
         sM[tid] = M;
+        sSh[tid] = 62 - (32 - __clz((unsigned)(2 * M + 1)));
     }
     __syncthreads();
     for (int t = 0; t < 3; ++t) {
         const int M = sM[t];
-        double* row = cdf + (size_t)t * kNoAllocTableCap;
-        for (int a = tid; a <= M; a += blockDim.x) {
+        unsigned long long* row = scratch + (size_t)t * kNoAllocTableCap;
+        for (int a = tid; a <= M; a += kNoAllocThreads) {
             const double v = table_exp(-__dmul_rn(sc[t], (double)a * (double)a));
-            row[M + a] = v;
-            row[M - a] = v;
+            const unsigned long long W = (unsigned long long)__double2ll_rn(ldexp(v, sSh[t]));
+            row[M + a] = W;
+            row[M - a] = W;
         }
     }
     __syncthreads();
-    if (tid < 3) {
-        double* row = cdf + (size_t)tid * kNoAllocTableCap;
-        double acc = 0.0;
-        for (int j = 0; j <= 2 * sM[tid]; ++j) {
-            acc = __dadd_rn(acc, row[j]);
-            row[j] = acc;
+    for (int t = 0; t < 3; ++t) {
+        const int n = 2 * sM[t] + 1;
+        unsigned long long* row = scratch + (size_t)t * kNoAllocTableCap;
+        const int per = (n + kNoAllocThreads - 1) / kNoAllocThreads;
+        const int j0 = min(n, tid * per), j1 = min(n, j0 + per);
+        unsigned long long local = 0;
+        for (int j = j0; j < j1; ++j) local += row[j];
+        unsigned long long incl = local;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long o = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += o;
         }
-        sH[tid] = acc;
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long v = lane < kNoAllocThreads / 32 ? wsum[lane] : 0ull;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned long long o = __shfl_up_sync(0xffffffffu, v, off);
+                if (lane >= off) v += o;
+            }
+            if (lane < kNoAllocThreads / 32) wsum[lane] = v;
+        }
+        __syncthreads();
+        unsigned long long run = incl - local + (warp > 0 ? wsum[warp - 1] : 0ull);
+        for (int j = j0; j < j1; ++j) {
+            run += row[j];
+            row[j] = run;
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    if (tid == 0 && S_out) *S_out = __dsub_rn(__dmul_rn(__dmul_rn(sH[0], sH[1]), sH[2]), 1.0);
     const unsigned long long* tx = scratch;
     const unsigned long long* ty = scratch + kNoAllocTableCap;
     const unsigned long long* tz = scratch + 2 * kNoAllocTableCap;
+    const unsigned long long Cx = tx[2 * sM[0]], Cy = ty[2 * sM[1]], Cz = tz[2 * sM[2]];
+    if (tid == 0) {
+        const double Hx = ldexp((double)Cx, -sSh[0]), Hy = ldexp((double)Cy, -sSh[1]), Hz = ldexp((double)Cz, -sSh[2]);
+        *S_out = __dsub_rn(__dmul_rn(__dmul_rn(Hx, Hy), Hz), 1.0);
+    }
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     const uint32_t c2 = (uint32_t)step, c3 = (uint32_t)((step >> 32) & 0xFFFFFFu);
-    for (int l = tid; l < P; l += blockDim.x) {
+    for (int l = tid; l < P; l += kNoAllocThreads) {
         int mx = 0, my = 0, mz = 0;
         bool found = false;
         for (uint32_t attempt = 0; attempt < kMaxAttempts; ++attempt) {
             const uint4 w0 = philox4x32_10(make_uint4((uint32_t)l, 2u * attempt, c2, c3), k0, k1);
             const uint4 w1 = philox4x32_10(make_uint4((uint32_t)l, 2u * attempt + 1u, c2, c3), k0, k1);
-            const double ux = __longlong_as_double((long long)uniform53_bits(w0.x, w0.y));
-            const double uy = __longlong_as_double((long long)uniform53_bits(w0.z, w0.w));
-            const double uz = __longlong_as_double((long long)uniform53_bits(w1.x, w1.y));
-            mx = search_bits(tx, sM[0], (unsigned long long)__double_as_longlong(__dmul_rn(ux, sH[0])));
-            my = search_bits(ty, sM[1], (unsigned long long)__double_as_longlong(__dmul_rn(uy, sH[1])));
-            mz = search_bits(tz, sM[2], (unsigned long long)__double_as_longlong(__dmul_rn(uz, sH[2])));
+            const unsigned long long Ux = ((unsigned long long)w0.x << 21) | (w0.y >> 11);
+            const unsigned long long Uy = ((unsigned long long)w0.z << 21) | (w0.w >> 11);
+            const unsigned long long Uz = ((unsigned long long)w1.x << 21) | (w1.y >> 11);
+            mx = search_int(tx, sM[0], (__umul64hi(Ux, Cx) << 11) | ((Ux * Cx) >> 53));
+            my = search_int(ty, sM[1], (__umul64hi(Uy, Cy) << 11) | ((Uy * Cy) >> 53));
+            mz = search_int(tz, sM[2], (__umul64hi(Uz, Cz) << 11) | ((Uz * Cz) >> 53));
             if (mx != 0 || my != 0 || mz != 0) {
                 found = true;
                 break;
@@ -175,7 +203,7 @@ extern "C" rbe_status rbe_sample_k_noalloc(const double box[3], double alpha, in
     rbe_status st = noalloc_scratch(device, &scratch, err);
     if (st != RBE_OK) return fail(nullptr, st, err);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    k_sample_noalloc<<<1, 256, 0, s>>>(scratch, box[0], box[1], box[2], alpha, P, seed, step, m_out, S_out);
+    k_sample_noalloc<<<1, kNoAllocThreads, 0, s>>>(scratch, box[0], box[1], box[2], alpha, P, seed, step, m_out, S_out);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(nullptr, RBE_ECUDA, std::string("k_sample_noalloc: ") + cudaGetErrorString(e));
     unsigned bits = 0;

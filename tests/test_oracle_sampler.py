@@ -87,10 +87,14 @@ def test_own_exp_against_libm():
                                        (5.0, 1.3)])
 def test_axis_table_poisson_identity(alpha, ell):
     """H = sum_m exp(-pi^2 m^2/(alpha l^2)) = sqrt(alpha l^2/pi) sum_n exp(-alpha n^2 l^2) (Eq. (psf))."""
-    w, cdf, M, H = oracle.axis_table(alpha, ell)
+    w, cum, M, H, sh = oracle.axis_table(alpha, ell)
     assert np.array_equal(w, w[::-1])                  # exactly symmetric
     assert w[M] == 1.0
-    assert np.all(np.diff(cdf) >= 0) and cdf[-1] == H   # tail terms below 1 ulp of H are absorbed
+    W = np.diff(cum.astype(object), prepend=0)         # the integer weights rint(w 2^sh)
+    for j in range(2 * M + 1):
+        assert W[j] == round(math.ldexp(w[j], sh))     # ties cannot occur at these magnitudes
+    assert int(cum[-1]) < 2 ** 62                      # the sum fits the 63-bit budget
+    assert H == math.ldexp(float(int(cum[-1])), -sh)
     n = np.arange(-50, 51)
     dual = math.sqrt(alpha * ell * ell / math.pi) * np.sum(np.exp(-alpha * n * n * ell * ell))
     assert abs(H / dual - 1.0) < 1e-14
@@ -111,7 +115,7 @@ def test_sampler_marginals_chi_square():
     Hs = [t[3] for t in tabs]
     assert abs(S - (Hs[0] * Hs[1] * Hs[2] - 1.0)) < 1e-15 * S
     for ax in range(3):
-        w, _, M, H = tabs[ax]
+        w, _, M, H, _ = tabs[ax]
         others = np.prod([Hs[j] for j in range(3) if j != ax])
         vals = np.arange(-M, M + 1)
         p = w * (others - (vals == 0)) / S
