@@ -67,11 +67,15 @@ k_tables(double bx, double by, double bz, const double* __restrict__ box_dev, do
         sSh[tid] = 62 - bitlength((unsigned)(2 * M + 1));
     }
     __syncthreads();
-    // integer weights, written once per |m| into both halves of the row
-    for (int t = 0; t < 3; ++t) {
-        const int M = sM[t];
-        unsigned long long* row = cum + (size_t)t * cap;
-        for (int a = tid; a <= M; a += kTableThreads) {
+    // integer weights, written once per |m| into both halves of the row; the (axis, a)
+    // entries of the three rows are spread over all threads
+    {
+        const int n0 = sM[0] + 1, n1 = sM[1] + 1, n2 = sM[2] + 1;
+        for (int e = tid; e < n0 + n1 + n2; e += kTableThreads) {
+            const int t = e < n0 ? 0 : (e < n0 + n1 ? 1 : 2);
+            const int a = e - (t == 0 ? 0 : (t == 1 ? n0 : n0 + n1));
+            const int M = sM[t];
+            unsigned long long* row = cum + (size_t)t * cap;
             const double v = table_exp(-__dmul_rn(sc[t], (double)a * (double)a));
             const unsigned long long W = (unsigned long long)__double2ll_rn(ldexp(v, sSh[t]));
             row[M + a] = W;
@@ -112,36 +116,46 @@ k_tables(double bx, double by, double bz, const double* __restrict__ box_dev, do
         }
         __syncthreads();
     }
-    if (tid == 0) {
-        double H[3];
-        for (int t = 0; t < 3; ++t) {
-            const unsigned long long C = cum[(size_t)t * cap + 2 * sM[t]];
-            H[t] = ldexp((double)C, -sSh[t]);
-            ks->H[t] = H[t];
-            ks->M[t] = sM[t];
-            ks->sh[t] = sSh[t];
-            ks->L[t] = sL[t];
-            const double inv = 1.0 / sL[t];
-            ks->inv[t] = inv;
-            const unsigned long long b = (unsigned long long)__double_as_longlong(inv);
-            const int e = (int)((b >> 52) & 0x7ff) - 1075;
-            ks->sc[t].q = ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 11;
-            ks->sc[t].e = e - 11;
-        }
-        const double S = __dsub_rn(__dmul_rn(__dmul_rn(H[0], H[1]), H[2]), 1.0);
+    // box constants: independent FP64 chains on separate threads (GB300 runs FP64 at a low
+    // rate, so a single thread computing all of them would serialise their latency)
+    __shared__ double sH[3];
+    if (tid < 3) {
+        const unsigned long long C = cum[(size_t)tid * cap + 2 * sM[tid]];
+        sH[tid] = ldexp((double)C, -sSh[tid]);
+        ks->H[tid] = sH[tid];
+        ks->M[tid] = sM[tid];
+        ks->sh[tid] = sSh[tid];
+        ks->L[tid] = sL[tid];
+    } else if (tid >= 32 && tid < 35) {
+        const int t = tid - 32;
+        const double inv = 1.0 / sL[t];
+        ks->inv[t] = inv;
+        const unsigned long long b = (unsigned long long)__double_as_longlong(inv);
+        const int e = (int)((b >> 52) & 0x7ff) - 1075;
+        ks->sc[t].q = ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 11;
+        ks->sc[t].e = e - 11;
+    } else if (tid >= 64 && tid < 67) {
+        const int t = tid - 64;
+        const float c = (float)(2.0 * kPi / sL[t]);
+        if (t == 0) ks->cx = c;
+        else if (t == 1) ks->cy = c;
+        else ks->cz = c;
+    } else if (tid == 96) {
         const double V = sL[0] * sL[1] * sL[2];
-        ks->S = S;
-        ks->wP = S / (double)P;
         ks->V = V;
-        ks->alpha = alpha;
-        ks->P = P;
-        ks->cx = (float)(2.0 * kPi / sL[0]);
-        ks->cy = (float)(2.0 * kPi / sL[1]);
-        ks->cz = (float)(2.0 * kPi / sL[2]);
         ks->ce = (float)(2.0 * kPi / V);
         ks->cb = (float)(4.0 * kPi / V);
+    } else if (tid == 128) {
+        ks->alpha = alpha;
+        ks->P = P;
         ks->inv4a = (float)(1.0 / (4.0 * alpha));
         ks->cself = (float)(-sqrt(alpha / kPi));
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const double S = __dsub_rn(__dmul_rn(__dmul_rn(sH[0], sH[1]), sH[2]), 1.0);
+        ks->S = S;
+        ks->wP = S / (double)P;
     }
 }
 
