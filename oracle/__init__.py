@@ -91,8 +91,35 @@ def _load():
     return _lib
 
 
+class NptParams(ctypes.Structure):
+    """Parameters of the Langevin NPT step (mirrors orc_npt_params in npt_oracle.c)."""
+    _fields_ = [("dt", ctypes.c_double), ("kT", ctypes.c_double), ("P_ext", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("gamma_V", ctypes.c_double), ("M_V", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("rc", ctypes.c_double), ("qqr2e", ctypes.c_double),
+                ("lj_sigma", ctypes.c_double), ("lj_eps", ctypes.c_double), ("max_disp", ctypes.c_double),
+                ("P", ctypes.c_int32), ("kspace", ctypes.c_int32), ("real", ctypes.c_int32),
+                ("noise", ctypes.c_int32), ("barostat", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
 def _bind_npt(lib):
+    P = ctypes.POINTER(NptParams)
+    lib.orc_npt_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, _c_double_p]
+    lib.orc_npt_normals.restype = None
+    lib.orc_pair_real.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _c_double_p,
+                                  _c_double_p, _c_double_p]
+    lib.orc_pair_real.restype = ctypes.c_int
+    lib.orc_npt_forces.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p, ctypes.c_uint64, P,
+                                   _c_double_p, _c_double_p, _c_double_p]
+    lib.orc_npt_forces.restype = ctypes.c_int
+    lib.orc_npt_step.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p, _c_double_p, _c_double_p,
+                                 _c_double_p, _c_double_p, _c_double_p, ctypes.c_uint64, P, _c_double_p]
     lib.orc_npt_step.restype = ctypes.c_int
+    lib.orc_npt_run.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p, _c_double_p, _c_double_p,
+                                _c_double_p, _c_double_p, _c_double_p, ctypes.c_uint64, ctypes.c_int32, P,
+                                _c_double_p, _c_double_p, _c_double_p]
+    lib.orc_npt_run.restype = ctypes.c_int
 
 
 def _dp(a):
@@ -237,6 +264,94 @@ def direct_sum(pos, q, box, R: int) -> float:
     q = _f64(q)
     b = _f64(box, (3,))
     return lib.orc_direct_sum(q.shape[0], _dp(pos), _dp(q), _dp(b), R)
+
+
+# ---------------------------------------------------------------------------------
+# Langevin NPT (npt_oracle.c)
+
+KB = 0.00831446261815324        # kJ/mol/K
+BAR = 6.02214076e-5              # kJ/mol/A^3 per bar
+QQR2E = 1389.35457644382         # kJ/mol A / e^2
+
+
+def npt_params(**kw) -> NptParams:
+    """NptParams with the defaults of the point-charge NPT system (reading 17): 300 K,
+    1 bar, dt = 1 fs, gamma = 10/ps, gamma_V = 2/ps, alpha = 0.2, rc = 7, LJ 2 A / 0.5 kJ/mol."""
+    d = dict(dt=0.001, kT=KB * 300.0, P_ext=1.0 * BAR, gamma=10.0, gamma_V=2.0, M_V=1.0, alpha=0.2, rc=7.0,
+             qqr2e=QQR2E, lj_sigma=2.0, lj_eps=0.5, max_disp=0.0, P=100, kspace=1, real=1, noise=1,
+             barostat=1, pad=0, seed=1)
+    d.update(kw)
+    return NptParams(**d)
+
+
+def piston_mass(tau_p: float, beta_T: float, V0: float) -> float:
+    """M = tau_P^2 / (4 pi^2 beta_T V0): a harmonic volume oscillation of period tau_P (reading 13)."""
+    return tau_p ** 2 / (4.0 * np.pi ** 2 * beta_T * V0)
+
+
+def npt_normals(seed: int, stream: int, step: int, index: int):
+    z = np.zeros(4)
+    _load().orc_npt_normals(seed, stream, step, index, _dp(z))
+    return z
+
+
+def pair_real(pos, q, box, alpha, rc, qqr2e, lj_sigma, lj_eps):
+    """Nearest-image erfc Coulomb + LJ: (F[N,3], W[3,3], E_coul, E_lj)."""
+    lib = _load()
+    pos = _f64(pos)
+    q = _f64(q)
+    N = q.shape[0]
+    b = _f64(box, (3,))
+    F = np.zeros((N, 3))
+    W = np.zeros((3, 3))
+    E = np.zeros(2)
+    _check(lib.orc_pair_real(N, _dp(pos), _dp(q), _dp(b), alpha, rc, qqr2e, lj_sigma, lj_eps, _dp(F), _dp(W),
+                             _dp(E)), "pair_real")
+    return F, W, E[0], E[1]
+
+
+class NptState:
+    """Device-free NPT state for the oracle: positions, momenta, forces, box, p_V, virial trace."""
+
+    def __init__(self, r, p, q, m, L, pV=0.0):
+        self.r = _f64(r).copy()
+        self.p = _f64(p).copy()
+        self.q = _f64(q)
+        self.m = _f64(m)
+        self.L = _f64(L, (3,)).copy()
+        self.F = np.zeros_like(self.r)
+        self.pV = ctypes.c_double(pV)
+        self.W = ctypes.c_double(0.0)
+
+    @property
+    def N(self):
+        return self.q.shape[0]
+
+
+def npt_forces(st: NptState, step: int, prm: NptParams):
+    E = np.zeros(3)
+    _check(_load().orc_npt_forces(st.N, _dp(st.r), _dp(st.q), _dp(st.L), step, ctypes.byref(prm), _dp(st.F),
+                                  ctypes.byref(st.W), _dp(E)), "npt_forces")
+    return E
+
+
+def npt_step(st: NptState, step: int, prm: NptParams):
+    E = np.zeros(3)
+    _check(_load().orc_npt_step(st.N, _dp(st.r), _dp(st.p), _dp(st.F), _dp(st.q), _dp(st.m), _dp(st.L),
+                                ctypes.byref(st.pV), ctypes.byref(st.W), step, ctypes.byref(prm), _dp(E)),
+           "npt_step")
+    return E
+
+
+def npt_run(st: NptState, step0: int, nsteps: int, prm: NptParams):
+    """nsteps steps; returns (V, P_ins, extended energy) per step."""
+    V = np.zeros(nsteps)
+    Pi = np.zeros(nsteps)
+    H = np.zeros(nsteps)
+    _check(_load().orc_npt_run(st.N, _dp(st.r), _dp(st.p), _dp(st.F), _dp(st.q), _dp(st.m), _dp(st.L),
+                               ctypes.byref(st.pV), ctypes.byref(st.W), step0, nsteps, ctypes.byref(prm), _dp(V),
+                               _dp(Pi), _dp(H)), "npt_run")
+    return V, Pi, H
 
 
 def ewald_total(pos, q, box, alpha: float, rc: float, kmax: int):
