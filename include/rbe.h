@@ -172,6 +172,66 @@ rbe_status rbe_sample_k_noalloc(const double box[3], double alpha, int32_t P, ui
 /* Synchronise the context's stream and return (and clear) any latched device error. */
 rbe_status rbe_sync(rbe_ctx ctx);
 
+/* ---------------------------------------------------------------------------------
+ * Isotropic Langevin NPT (Sec. 3.2 Eq. (24); Sec. 3.3 splitting
+ *   V^p/2, R^p/2, V/2, R/2, O^p, O, R/2, V/2, [forces, P_ins], R^p/2, V^p/2
+ * with the R and R^p flows solved exactly for frozen eps = p_V / (3 M V) and exact
+ * Ornstein--Uhlenbeck steps O, O^p).  Forces: the context's RBE k-space estimator (batch of
+ * the step index, Sec. 4.2) times qqr2e, plus the nearest-image real space within rc:
+ * qqr2e q_i q_j erfc(sqrt(alpha) r)/r + 4 eps ((sigma/r)^12 - (sigma/r)^6) (Sec. 4.1-4.2).
+ * P_ins = (sum p^2/m + W_k + W_r) / (3V) (Sec. 4.1 Eq. (pressurecubic)).
+ * Units: A, ps, g/mol, kJ/mol, e; momenta in g/mol A/ps (dp/dt = 100 F for F in kJ/mol/A);
+ * pressure in kJ/mol/A^3; p_V in kJ/mol ps/A^3; M in kJ/mol ps^2/A^6.  The box scales
+ * isotropically.  Noise: Philox-4x32-10 with the context's seed, counters
+ * (i, 0, step_lo, (1 << 24) | step_hi24) for particle i and (0, 0, step_lo, (2 << 24) |
+ * step_hi24) for the cell, 32-bit uniforms (w + 1/2) 2^-32 and Box--Muller. */
+typedef struct {
+    double dt;        /* time step, ps */
+    double kT;        /* k_B T, kJ/mol */
+    double P_ext;     /* external pressure, kJ/mol/A^3 */
+    double gamma;     /* particle friction, 1/ps */
+    double gamma_V;   /* cell friction, 1/ps */
+    double M_V;       /* piston mass, kJ/mol ps^2/A^6 (> 0 when barostat != 0) */
+    double rc;        /* real-space cutoff, A (rc <= box/2 on every axis) */
+    double qqr2e;     /* Coulomb constant, kJ/mol A/e^2 */
+    double lj_sigma;  /* A */
+    double lj_eps;    /* kJ/mol; 0 disables the Lennard-Jones term */
+    double max_disp;  /* cap on |dr| per step in A, split over the two R/2 sub-steps; 0 = none */
+    int32_t kspace;   /* 1: RBE k-space forces and virial */
+    int32_t real;     /* 1: real-space forces and virial */
+    int32_t noise;    /* 1: Langevin noise in O and O^p */
+    int32_t barostat; /* 1: the cell moves; 0: V fixed and p_V = 0 */
+} rbe_npt_params;
+
+/* Number of doubles of the device cell-state block: {l_x, l_y, l_z, p_V, W (virial trace at
+ * the current positions), sum p^2/m /100 (= 2K), P_ins, E_k (k-space incl. self, x qqr2e),
+ * E_coul (real space), E_lj, V, reserved...}. */
+#define RBE_CELL_DOUBLES 16
+
+/* One replica; every buffer is the caller's device memory.  `step` is the next step index
+ * (the Philox counter of its RBE batch and noise); rbe_npt_step advances it. */
+typedef struct {
+    int64_t N;
+    double* pos;          /* device N*3, wrapped into [0, l) after every step */
+    double* mom;          /* device N*3 */
+    double* force;        /* device N*3: forces at pos, kJ/mol/A (kept between steps) */
+    const double* charge; /* device N, e */
+    const double* mass;   /* device N, g/mol */
+    double* cell;         /* device RBE_CELL_DOUBLES (box in cell[0..2] must be set by the caller) */
+    uint64_t step;        /* host */
+    rbe_npt_params params;
+} rbe_system;
+
+/* Forces, virial trace and energies at the current state, with the RBE batch of index
+ * `batch`; fills sys->force and cell[3..10] (p_V is kept).  Call once before the first step.
+ * Asynchronous on the context's stream.  RBE_EINVAL for bad pointers or parameters. */
+rbe_status rbe_npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch);
+
+/* Advance nsteps >= 1 steps (Sec. 3.3); asynchronous on the context's stream; sys->step
+ * advances by nsteps.  The context's box is not used: each step rebuilds the sampling tables
+ * from the device box in sys->cell. */
+rbe_status rbe_npt_step(rbe_ctx ctx, rbe_system* sys, int32_t nsteps);
+
 /* Static description of a status code. */
 const char* rbe_status_string(rbe_status status);
 

@@ -27,6 +27,25 @@ _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int32)
 
+class NptParams(ctypes.Structure):
+    """rbe_npt_params (include/rbe.h)."""
+    _fields_ = [("dt", ctypes.c_double), ("kT", ctypes.c_double), ("P_ext", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("gamma_V", ctypes.c_double), ("M_V", ctypes.c_double),
+                ("rc", ctypes.c_double), ("qqr2e", ctypes.c_double), ("lj_sigma", ctypes.c_double),
+                ("lj_eps", ctypes.c_double), ("max_disp", ctypes.c_double), ("kspace", ctypes.c_int32),
+                ("real", ctypes.c_int32), ("noise", ctypes.c_int32), ("barostat", ctypes.c_int32)]
+
+
+class System(ctypes.Structure):
+    """rbe_system (include/rbe.h): device pointers of one replica, the next step index and
+    the NPT parameters."""
+    _fields_ = [("N", ctypes.c_int64), ("pos", ctypes.c_void_p), ("mom", ctypes.c_void_p),
+                ("force", ctypes.c_void_p), ("charge", ctypes.c_void_p), ("mass", ctypes.c_void_p),
+                ("cell", ctypes.c_void_p), ("step", ctypes.c_uint64), ("params", NptParams)]
+
+
+RBE_CELL_DOUBLES = 16
+
 # (name, restype, argtypes) of every exported symbol
 SIGNATURES = [
     ("rbe_create", ctypes.c_int, [_dp, ctypes.c_double, ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(_vp)]),
@@ -47,6 +66,8 @@ SIGNATURES = [
     ("rbe_measure_pipe", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _dp]),
     ("rbe_sample_k_noalloc", ctypes.c_int,
      [_dp, ctypes.c_double, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, _vp, _vp, _vp]),
+    ("rbe_npt_init", ctypes.c_int, [_vp, ctypes.POINTER(System), ctypes.c_uint64]),
+    ("rbe_npt_step", ctypes.c_int, [_vp, ctypes.POINTER(System), ctypes.c_int32]),
     ("rbe_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("rbe_last_error", ctypes.c_char_p, [_vp]),
     ("rbe_version", ctypes.c_int32, []),
@@ -195,6 +216,46 @@ def rbe_sample_k_noalloc(box, alpha: float, P: int, seed: int, step: int, m_out,
     b = _host(box, np.float64).reshape(3)
     _check(load().rbe_sample_k_noalloc(b.ctypes.data_as(_dp), float(alpha), int(P), int(seed), int(step),
                                        _ptr(m_out), _ptr(S_out), ctypes.c_void_p(stream_handle)))
+
+
+def rbe_npt_init(h, sys_: "System", batch: int):
+    _check(load().rbe_npt_init(h, ctypes.byref(sys_), int(batch)), h)
+
+
+def rbe_npt_step(h, sys_: "System", nsteps: int):
+    _check(load().rbe_npt_step(h, ctypes.byref(sys_), int(nsteps)), h)
+
+
+class NptReplica:
+    """One device-resident NPT replica: torch CUDA tensors for r, p, F, q, m and the cell
+    block, and the rbe_system that points at them."""
+
+    def __init__(self, pos, mom, charge, mass, box, params: NptParams, device, step: int = 0, pV: float = 0.0):
+        import torch
+        f64 = torch.float64
+        self.pos = torch.as_tensor(np.ascontiguousarray(pos), dtype=f64).to(device).contiguous()
+        self.mom = torch.as_tensor(np.ascontiguousarray(mom), dtype=f64).to(device).contiguous()
+        self.force = torch.zeros_like(self.pos)
+        self.charge = torch.as_tensor(np.ascontiguousarray(charge), dtype=f64).to(device).contiguous()
+        self.mass = torch.as_tensor(np.ascontiguousarray(mass), dtype=f64).to(device).contiguous()
+        cell = np.zeros(RBE_CELL_DOUBLES)
+        cell[:3] = np.asarray(box, dtype=np.float64).reshape(3)
+        cell[3] = pV
+        self.cell = torch.as_tensor(cell).to(device).contiguous()
+        self.sys = System(N=int(self.charge.shape[0]), pos=self.pos.data_ptr(), mom=self.mom.data_ptr(),
+                          force=self.force.data_ptr(), charge=self.charge.data_ptr(), mass=self.mass.data_ptr(),
+                          cell=self.cell.data_ptr(), step=int(step), params=params)
+
+    def init(self, ctx: "Context", batch: int | None = None):
+        rbe_npt_init(ctx.h, self.sys, self.sys.step if batch is None else batch)
+
+    def step(self, ctx: "Context", nsteps: int = 1):
+        rbe_npt_step(ctx.h, self.sys, nsteps)
+
+    def state(self):
+        """(pos, mom, force, box, cell block) as NumPy arrays (synchronises)."""
+        c = self.cell.cpu().numpy()
+        return (self.pos.cpu().numpy(), self.mom.cpu().numpy(), self.force.cpu().numpy(), c[:3].copy(), c)
 
 
 def rbe_version() -> int:

@@ -110,6 +110,14 @@ static rbe_status sync_and_status(rbe_ctx ctx)
     return status_from_bits(ctx, bits);
 }
 
+static void free_npt(NptBuffers& b)
+{
+    cudaFree(b.Fk); cudaFree(b.Fr); cudaFree(b.WEk); cudaFree(b.coef); cudaFree(b.cid); cudaFree(b.sorted);
+    cudaFree(b.spos); cudaFree(b.cnt); cudaFree(b.start); cudaFree(b.cursor); cudaFree(b.partials);
+    cudaFree(b.counter);
+    b = NptBuffers{};
+}
+
 static void free_buffers(DeviceBuffers& d)
 {
     cudaFree(d.cum); cudaFree(d.ks); cudaFree(d.m); cudaFree(d.w); cudaFree(d.rho); cudaFree(d.terms);
@@ -175,6 +183,7 @@ rbe_status rbe_destroy(rbe_ctx ctx)
     cudaStreamSynchronize(ctx->stream);
     for (auto& e : ctx->ev)
         if (e) cudaEventDestroy(e);
+    free_npt(ctx->npt);
     free_buffers(ctx->d);
     delete ctx;
     return RBE_OK;
@@ -334,6 +343,32 @@ rbe_status rbe_get_rho(rbe_ctx ctx, double* rho_out, int32_t capacity)
                                       ctx->stream);
     if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaMemcpyAsync(rho)");
     return sync_and_status(ctx);
+}
+
+rbe_status rbe_npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch)
+{
+    if (!ctx) return RBE_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(ctx, RBE_ECUDA, "cannot select the context's device");
+    if (sys) {
+        rbe_status st;
+        const int64_t N = sys->N;
+        if ((st = check_dev(ctx, sys->pos, "pos", N > 0)) != RBE_OK) return st;
+        if ((st = check_dev(ctx, sys->mom, "mom", N > 0)) != RBE_OK) return st;
+        if ((st = check_dev(ctx, sys->force, "force", N > 0)) != RBE_OK) return st;
+        if ((st = check_dev(ctx, sys->charge, "charge", N > 0)) != RBE_OK) return st;
+        if ((st = check_dev(ctx, sys->mass, "mass", N > 0)) != RBE_OK) return st;
+        if ((st = check_dev(ctx, sys->cell, "cell", true)) != RBE_OK) return st;
+    }
+    return npt_init(ctx, sys, batch);
+}
+
+rbe_status rbe_npt_step(rbe_ctx ctx, rbe_system* sys, int32_t nsteps)
+{
+    if (!ctx) return RBE_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(ctx, RBE_ECUDA, "cannot select the context's device");
+    return npt_run(ctx, sys, nsteps);
 }
 
 rbe_status rbe_set_kernel_timing(rbe_ctx ctx, int32_t enable)

@@ -49,6 +49,25 @@ struct Plan {
     int64_t per_block;  // particles per force block
 };
 
+// Scratch of the NPT step (grown on demand).
+struct NptBuffers {
+    double* Fk = nullptr;          // N*3 k-space forces (Gaussian units)
+    double* Fr = nullptr;          // N*3 real-space forces (kJ/mol/A)
+    double* WEk = nullptr;         // 11: k-space virial (9) + energy (2)
+    double* coef = nullptr;        // per-step coefficients (NptCoef)
+    int* cid = nullptr;            // N cell index per particle
+    int* sorted = nullptr;         // N particle indices grouped by cell
+    void* spos = nullptr;          // N packed positions+charge in cell order (float4 or double4)
+    int* cnt = nullptr;            // cells: counts
+    int* start = nullptr;          // cells: exclusive prefix sums
+    int* cursor = nullptr;         // cells: fill cursors
+    double* partials = nullptr;    // per-block partial sums (K2, W_r, E_coul, E_lj)
+    unsigned* counter = nullptr;   // last-block counter of the finishing kernel
+    int64_t ncap = 0;
+    int cellcap = 0;
+    int partcap = 0;
+};
+
 struct DeviceBuffers {
     unsigned long long* cum = nullptr;  // [3][tab_cap] integer cumulative weights
     int tab_cap = 0;                  // entries per axis (>= 2M+1)
@@ -86,6 +105,8 @@ struct rbe_ctx_s {
     int32_t rho_accum = RBE_RHO_FP32;
     bool tables_dirty = true;
     int32_t last_K = 0;
+    rbe::NptBuffers npt;
+    int64_t npt_ready_N = -1;        // N of the system rbe_npt_init prepared the scratch for
     bool timing = false;             // record CUDA events around each evaluation kernel
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     rbe::DeviceBuffers d;
@@ -107,6 +128,9 @@ rbe_status ensure_table_capacity(rbe_ctx ctx, int need);
 rbe_status launch_tables(rbe_ctx ctx, const double* box_dev);
 rbe_status ensure_k_capacity(rbe_ctx ctx, int K);
 rbe_status launch_sample(rbe_ctx ctx, uint64_t step, int P);
+rbe_status launch_sample_device_box(rbe_ctx ctx, uint64_t step, int P);
+rbe_status npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch);
+rbe_status npt_run(rbe_ctx ctx, rbe_system* sys, int32_t nsteps);
 rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int K,
                            bool uniform_weight, double* F, double* W, double* E);
 void record_event(rbe_ctx ctx, int idx);

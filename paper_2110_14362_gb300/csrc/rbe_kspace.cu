@@ -937,7 +937,13 @@ rbe_status launch_sample(rbe_ctx ctx, uint64_t step, int P)
 {
     rbe_status st = ensure_tables(ctx);
     if (st != RBE_OK) return st;
-    st = ensure_k_capacity(ctx, P);
+    return launch_sample_device_box(ctx, step, P);
+}
+
+// The sampler on the tables already on the device (built by launch_tables from any box).
+rbe_status launch_sample_device_box(rbe_ctx ctx, uint64_t step, int P)
+{
+    rbe_status st = ensure_k_capacity(ctx, P);
     if (st != RBE_OK) return st;
     record_event(ctx, 0);
     const int threads = 128;

@@ -1,0 +1,621 @@
+// Isotropic Langevin NPT step on the device (Sec. 3.2-3.3 of the paper) with RBE k-space
+// forces (rbe_kspace.cu) and a nearest-image real space on a deterministic cell list.
+//
+// One step is a fixed sequence of launches on the context's stream:
+//   k_npt_cell_a   one thread: V^p/2, the sub-step coefficients, V/2, O^p, V/2 (new box)
+//   k_npt_drift    particles: R^p/2, R/2, O, R/2, wrap into the new box
+//   k-space        tables for the new box, sampler, rho, reduction, force pass
+//   cell list      count, scan, fill, per-cell sort (deterministic order), packed positions
+//   k_pair_*       real-space forces, virial trace and energies (one thread per particle)
+//   k_npt_finish   F = qqr2e F_k + F_r, R^p/2, kinetic sum; last block: P_ins and V^p/2
+// Nothing leaves the device between steps; the step index drives the RBE batch and noise.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+
+#include "rbe_context.h"
+#include "rbe_device.cuh"
+
+namespace rbe {
+
+constexpr double kFConv = 100.0;  // kJ/mol/A per g/mol -> A/ps^2
+constexpr int kNptThreads = 256;
+constexpr int kScanThreads = 1024;
+
+struct NptCoef {
+    double a1, b1;      // R^p/2 before the forces: p <- a1 p + 100 F b1
+    double a2m1, b2;    // first R/2: r <- r + r (a2 - 1) + (p/m) b2
+    double g, og;       // O: p <- g p + sqrt(og m) z, og = 100 kT (1 - g^2)
+    double a3m1, b3;    // second R/2
+    double a4, b4;      // R^p/2 after the forces
+    double L[3];        // box after the second V/2
+    double half_cap;    // displacement cap per R/2
+    double V;
+    int noise;
+    int pad;
+};
+
+// (e^x - 1)/x * t with x = eps t; the series for tiny x.
+__device__ __forceinline__ double expm1_over(double x, double t)
+{
+    if (fabs(x) < 1e-8) return t * (1.0 + x * (0.5 + x * (1.0 / 6.0 + x / 24.0)));
+    return t * expm1(x) / x;
+}
+
+// Four standard normals from one Philox call: u = (w + 1/2) 2^-32, Box--Muller.
+__device__ __forceinline__ void npt_normals(uint64_t seed, uint32_t stream, uint64_t step, uint32_t index,
+                                            double z[4])
+{
+    const uint4 w = philox4x32_10(make_uint4(index, 0u, (uint32_t)step,
+                                             (stream << 24) | (uint32_t)((step >> 32) & 0xFFFFFFu)),
+                                  (uint32_t)seed, (uint32_t)(seed >> 32));
+    const double u0 = ((double)w.x + 0.5) * 0x1.0p-32, u1 = ((double)w.y + 0.5) * 0x1.0p-32;
+    const double u2 = ((double)w.z + 0.5) * 0x1.0p-32, u3 = ((double)w.w + 0.5) * 0x1.0p-32;
+    double s, c;
+    const double r0 = sqrt(-2.0 * log(u0));
+    sincospi(2.0 * u1, &s, &c);
+    z[0] = r0 * c;
+    z[1] = r0 * s;
+    const double r1 = sqrt(-2.0 * log(u2));
+    sincospi(2.0 * u3, &s, &c);
+    z[2] = r1 * c;
+    z[3] = r1 * s;
+}
+
+// ---------------------------------------------------------------------------------
+// Cell-variable part of the step (Sec. 3.3): V^p/2, R^p/2 coefficient, V/2, R/2
+// coefficient, O^p, R/2 coefficient, V/2, R^p/2 coefficient.  cell = {l, p_V, W, 2K, ...}.
+__global__ void k_npt_cell_a(double* __restrict__ cell, NptCoef* __restrict__ cf, rbe_npt_params prm,
+                             uint64_t seed, uint64_t step)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double h = 0.5 * prm.dt;
+    double L[3] = {cell[0], cell[1], cell[2]};
+    double V = L[0] * L[1] * L[2];
+    double pV = prm.barostat ? cell[3] : 0.0;
+    const double W = cell[4], K2 = cell[5];
+    if (prm.barostat) pV += h * ((K2 + W) / (3.0 * V) - prm.P_ext);
+    double eps = prm.barostat ? pV / (3.0 * prm.M_V * V) : 0.0;
+    NptCoef c;
+    c.a1 = exp(-eps * h);
+    c.b1 = expm1_over(-eps * h, h);
+    if (prm.barostat) {
+        const double Vn = V + h * pV / prm.M_V;
+        const double f = cbrt(Vn / V);
+        for (int t = 0; t < 3; ++t) L[t] *= f;
+        V = L[0] * L[1] * L[2];
+    }
+    eps = prm.barostat ? pV / (3.0 * prm.M_V * V) : 0.0;
+    c.a2m1 = exp(eps * h) - 1.0;
+    c.b2 = expm1_over(eps * h, h);
+    if (prm.barostat) {
+        const double g = exp(-prm.gamma_V * prm.dt);
+        pV *= g;
+        if (prm.noise) {
+            double z[4];
+            npt_normals(seed, 2u, step, 0u, z);
+            pV += sqrt(prm.kT * prm.M_V * (1.0 - g * g)) * z[0];
+        }
+    }
+    c.g = exp(-prm.gamma * prm.dt);
+    c.og = prm.kT * kFConv * (1.0 - c.g * c.g);
+    eps = prm.barostat ? pV / (3.0 * prm.M_V * V) : 0.0;
+    c.a3m1 = exp(eps * h) - 1.0;
+    c.b3 = expm1_over(eps * h, h);
+    if (prm.barostat) {
+        const double Vn = V + h * pV / prm.M_V;
+        const double f = cbrt(Vn / V);
+        for (int t = 0; t < 3; ++t) L[t] *= f;
+        V = L[0] * L[1] * L[2];
+    }
+    eps = prm.barostat ? pV / (3.0 * prm.M_V * V) : 0.0;
+    c.a4 = exp(-eps * h);
+    c.b4 = expm1_over(-eps * h, h);
+    for (int t = 0; t < 3; ++t) c.L[t] = L[t];
+    c.half_cap = 0.5 * prm.max_disp;
+    c.V = V;
+    c.noise = prm.noise;
+    c.pad = 0;
+    *cf = c;
+    cell[0] = L[0];
+    cell[1] = L[1];
+    cell[2] = L[2];
+    cell[3] = pV;
+    cell[10] = V;
+}
+
+__device__ __forceinline__ void capped_add(double r[3], double d[3], double cap)
+{
+    if (cap > 0.0) {
+        const double len = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        if (len > cap) {
+            const double s = cap / len;
+            d[0] *= s; d[1] *= s; d[2] *= s;
+        }
+    }
+    r[0] += d[0]; r[1] += d[1]; r[2] += d[2];
+}
+
+// Particle part before the forces: R^p/2, R/2, O, R/2, wrap into the new box.
+__global__ void __launch_bounds__(kNptThreads)
+k_npt_drift(int64_t N, double* __restrict__ pos, double* __restrict__ mom, const double* __restrict__ force,
+            const double* __restrict__ mass, const NptCoef* __restrict__ cfp, uint64_t seed, uint64_t step)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const NptCoef c = *cfp;
+    const double m = mass[i];
+    double r[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+    double p[3] = {mom[3 * i], mom[3 * i + 1], mom[3 * i + 2]};
+    for (int t = 0; t < 3; ++t) p[t] = p[t] * c.a1 + kFConv * force[3 * i + t] * c.b1;
+    double d[3];
+    for (int t = 0; t < 3; ++t) d[t] = r[t] * c.a2m1 + (p[t] / m) * c.b2;
+    capped_add(r, d, c.half_cap);
+    double z[4] = {0.0, 0.0, 0.0, 0.0};
+    if (c.noise) npt_normals(seed, 1u, step, (uint32_t)i, z);
+    const double s = sqrt(c.og * m);
+    for (int t = 0; t < 3; ++t) p[t] = p[t] * c.g + s * z[t];
+    for (int t = 0; t < 3; ++t) d[t] = r[t] * c.a3m1 + (p[t] / m) * c.b3;
+    capped_add(r, d, c.half_cap);
+    for (int t = 0; t < 3; ++t) {
+        r[t] -= c.L[t] * floor(r[t] / c.L[t]);
+        pos[3 * i + t] = r[t];
+        mom[3 * i + t] = p[t];
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Cell list.  Cells per axis nc = floor(l / rc) (>= 3, checked by the host with headroom and
+// here), cell of a wrapped position s = r / l: floor(s nc).
+__device__ __forceinline__ void cell_dims(const double* cell, double rc, int nc[3])
+{
+    for (int t = 0; t < 3; ++t) nc[t] = max(1, (int)floor(cell[t] / rc));
+}
+
+__device__ __forceinline__ int cell_of(const double r[3], const double* L, const int nc[3])
+{
+    int c[3];
+    for (int t = 0; t < 3; ++t) {
+        const double s = r[t] / L[t];
+        c[t] = min(nc[t] - 1, max(0, (int)floor((s - floor(s)) * nc[t])));
+    }
+    return (c[2] * nc[1] + c[1]) * nc[0] + c[0];
+}
+
+__global__ void k_cl_count(int64_t N, const double* __restrict__ pos, const double* __restrict__ cell, double rc,
+                           int cellcap, int* __restrict__ cid, int* __restrict__ cnt, unsigned* __restrict__ status)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int nc[3];
+    cell_dims(cell, rc, nc);
+    if ((int64_t)nc[0] * nc[1] * nc[2] > cellcap) {
+        atomicOr(status, kStatusTable);
+        cid[i] = 0;
+        return;
+    }
+    const double r[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+    const int c = cell_of(r, cell, nc);
+    cid[i] = c;
+    atomicAdd(&cnt[c], 1);
+}
+
+// Exclusive scan of the counts (one block); cursor = start.
+__global__ void __launch_bounds__(kScanThreads)
+k_cl_scan(const double* __restrict__ cell, double rc, int cellcap, const int* __restrict__ cnt,
+          int* __restrict__ start, int* __restrict__ cursor)
+{
+    __shared__ int wsum[kScanThreads / 32];
+    int nc[3];
+    cell_dims(cell, rc, nc);
+    const int n = (int)min((int64_t)cellcap, (int64_t)nc[0] * nc[1] * nc[2]);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int per = (n + kScanThreads - 1) / kScanThreads;
+    const int j0 = min(n, tid * per), j1 = min(n, j0 + per);
+    int local = 0;
+    for (int j = j0; j < j1; ++j) local += cnt[j];
+    int incl = local;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int o = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += o;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int v = wsum[lane];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, v, off);
+            if (lane >= off) v += o;
+        }
+        wsum[lane] = v;
+    }
+    __syncthreads();
+    int run = incl - local + (warp > 0 ? wsum[warp - 1] : 0);
+    for (int j = j0; j < j1; ++j) {
+        start[j] = run;
+        cursor[j] = run;
+        run += cnt[j];
+    }
+}
+
+__global__ void k_cl_fill(int64_t N, const int* __restrict__ cid, int* __restrict__ cursor, int* __restrict__ sorted)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int slot = atomicAdd(&cursor[cid[i]], 1);
+    sorted[slot] = (int)i;
+}
+
+// Per cell: sort the members by particle index (a fixed order for every run), then pack
+// their positions and charges (FP32 or FP64) in that order.
+template <typename T4>
+__global__ void k_cl_sort(const double* __restrict__ cell, double rc, int cellcap, const int* __restrict__ cnt,
+                          const int* __restrict__ start, int* __restrict__ sorted, const double* __restrict__ pos,
+                          const double* __restrict__ q, T4* __restrict__ spos)
+{
+    int nc[3];
+    cell_dims(cell, rc, nc);
+    const int n = (int)min((int64_t)cellcap, (int64_t)nc[0] * nc[1] * nc[2]);
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const int s0 = start[c], k = cnt[c];
+    int* a = sorted + s0;
+    for (int x = 1; x < k; ++x) {
+        const int v = a[x];
+        int y = x - 1;
+        while (y >= 0 && a[y] > v) {
+            a[y + 1] = a[y];
+            --y;
+        }
+        a[y + 1] = v;
+    }
+    for (int x = 0; x < k; ++x) {
+        const int i = a[x];
+        T4 v;
+        v.x = pos[3 * i];
+        v.y = pos[3 * i + 1];
+        v.z = pos[3 * i + 2];
+        v.w = q[i];
+        spos[s0 + x] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Real-space forces (Sec. 4.1 Eqs. (U2), (force)): one thread per particle i loops over the
+// neighbour cells (27 when every axis has >= 3 cells of size >= rc) and their members in a
+// fixed order; nearest image within rc <= l/2;
+// f = -(dU/dr)/r for U = qqr2e q_i q_j erfc(sqrt(a) r)/r + 4 eps ((s/r)^12 - (s/r)^6).
+// Each pair is visited from both ends: energies and the virial trace take half.
+// Per-block partials: {W_r, E_coul, E_lj}.
+template <typename R, typename T4>
+__global__ void __launch_bounds__(kNptThreads)
+k_pair(int64_t N, const double* __restrict__ pos, const double* __restrict__ q, const double* __restrict__ cell,
+       double rc, double alpha, double qqr2e, double lj_sigma, double lj_eps, const int* __restrict__ cid,
+       const int* __restrict__ cnt, const int* __restrict__ start, const int* __restrict__ sorted,
+       const T4* __restrict__ spos, double* __restrict__ Fr, double* __restrict__ partials)
+{
+    __shared__ double red[3][kNptThreads / 32];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const R L[3] = {(R)cell[0], (R)cell[1], (R)cell[2]};
+    int nc[3];
+    cell_dims(cell, rc, nc);
+    const R rc2 = (R)(rc * rc), sa = (R)sqrt(alpha), two_sa_pi = (R)(2.0 * sqrt(alpha / 3.14159265358979323846));
+    const R qk = (R)qqr2e, s2 = (R)(lj_sigma * lj_sigma), e4 = (R)(4.0 * lj_eps), e24 = (R)(24.0 * lj_eps);
+    R fx = 0, fy = 0, fz = 0, w = 0, ec = 0, el = 0;
+    if (i < N) {
+        const R xi = (R)pos[3 * i], yi = (R)pos[3 * i + 1], zi = (R)pos[3 * i + 2], qi = (R)q[i];
+        const int c = cid[i];
+        const int cx = c % nc[0], cy = (c / nc[0]) % nc[1], cz = c / (nc[0] * nc[1]);
+        // neighbour offsets per axis: {-1, 0, 1} with 3 or more cells, {0, 1} with 2, {0} with 1,
+        // so that every distinct cell is visited once
+        const int lo0 = nc[0] >= 3 ? -1 : 0, hi0 = nc[0] >= 2 ? 1 : 0;
+        const int lo1 = nc[1] >= 3 ? -1 : 0, hi1 = nc[1] >= 2 ? 1 : 0;
+        const int lo2 = nc[2] >= 3 ? -1 : 0, hi2 = nc[2] >= 2 ? 1 : 0;
+        for (int dz = lo2; dz <= hi2; ++dz)
+            for (int dy = lo1; dy <= hi1; ++dy)
+                for (int dx = lo0; dx <= hi0; ++dx) {
+                    const int nx = (cx + dx + nc[0]) % nc[0], ny = (cy + dy + nc[1]) % nc[1], nz = (cz + dz + nc[2]) % nc[2];
+                    const int cc = (nz * nc[1] + ny) * nc[0] + nx;
+                    const int s0 = start[cc], s1 = s0 + cnt[cc];
+                    for (int s = s0; s < s1; ++s) {
+                        if (sorted[s] == (int)i) continue;
+                        const T4 o = spos[s];
+                        R ddx = (R)o.x - xi, ddy = (R)o.y - yi, ddz = (R)o.z - zi;
+                        ddx -= L[0] * rint(ddx / L[0]);
+                        ddy -= L[1] * rint(ddy / L[1]);
+                        ddz -= L[2] * rint(ddz / L[2]);
+                        const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                        if (!(r2 < rc2)) continue;
+                        const R r = sqrt(r2);
+                        const R qq = qk * qi * (R)o.w;
+                        const R er = erfc(sa * r);
+                        R f = qq * (er / r2 + two_sa_pi * exp(-(R)alpha * r2) / r) / r;
+                        ec += qq * er / r;
+                        if (lj_eps != 0.0) {
+                            const R sr2 = s2 / r2;
+                            const R sr6 = sr2 * sr2 * sr2;
+                            el += e4 * (sr6 * sr6 - sr6);
+                            f += e24 * (2 * sr6 * sr6 - sr6) / r2;
+                        }
+                        // force on i is -f d (d points from i to the neighbour)
+                        fx -= f * ddx;
+                        fy -= f * ddy;
+                        fz -= f * ddz;
+                        w += f * r2;
+                    }
+                }
+        Fr[3 * i] = (double)fx;
+        Fr[3 * i + 1] = (double)fy;
+        Fr[3 * i + 2] = (double)fz;
+    }
+    // fixed-order block sums of the halves
+    double v[3] = {0.5 * (double)w, 0.5 * (double)ec, 0.5 * (double)el};
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[a] += __shfl_xor_sync(0xffffffffu, v[a], off);
+        if (lane == 0) red[a][warp] = v[a];
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double s = 0.0;
+        for (int wv = 0; wv < kNptThreads / 32; ++wv) s += red[threadIdx.x][wv];
+        partials[4 * blockIdx.x + 1 + threadIdx.x] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Forces F = qqr2e F_k + F_r; with do_kick, R^p/2 with (a4, b4); the kinetic sum 2K per
+// block; the last block sums the partials in a fixed order and finishes the pressure:
+// W = qqr2e tr(W_k) + W_r, P_ins = (2K + W)/(3V), and with do_kick V^p/2.
+__global__ void __launch_bounds__(kNptThreads)
+k_npt_finish(int64_t N, double* __restrict__ mom, double* __restrict__ force, const double* __restrict__ mass,
+             const double* __restrict__ Fk, const double* __restrict__ Fr, const double* __restrict__ WEk,
+             const NptCoef* __restrict__ cfp, double* __restrict__ partials, int nblocks_pair,
+             unsigned* __restrict__ counter, double* __restrict__ cell, rbe_npt_params prm, int do_kick,
+             unsigned* __restrict__ status)
+{
+    __shared__ double red[kNptThreads / 32];
+    __shared__ bool is_last;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double k2 = 0.0;
+    if (i < N) {
+        const double m = mass[i];
+        double a = 1.0, b = 0.0;
+        if (do_kick) {
+            a = cfp->a4;
+            b = cfp->b4;
+        }
+        for (int t = 0; t < 3; ++t) {
+            const double F = (prm.kspace ? prm.qqr2e * Fk[3 * i + t] : 0.0) + (prm.real ? Fr[3 * i + t] : 0.0);
+            force[3 * i + t] = F;
+            double p = mom[3 * i + t];
+            if (do_kick) {
+                p = p * a + kFConv * F * b;
+                mom[3 * i + t] = p;
+            }
+            k2 += p * p / m;
+        }
+        k2 /= kFConv;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) k2 += __shfl_xor_sync(0xffffffffu, k2, off);
+    if (lane == 0) red[warp] = k2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int wv = 0; wv < kNptThreads / 32; ++wv) s += red[wv];
+        partials[4 * (size_t)(nblocks_pair + blockIdx.x)] = s;
+        __threadfence();
+        is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last || threadIdx.x != 0) return;
+    __threadfence();
+    double K2 = 0.0, Wr = 0.0, Ec = 0.0, El = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) K2 += __ldcg(partials + 4 * (size_t)(nblocks_pair + b));
+    if (prm.real)
+        for (int b = 0; b < nblocks_pair; ++b) {
+            Wr += __ldcg(partials + 4 * (size_t)b + 1);
+            Ec += __ldcg(partials + 4 * (size_t)b + 2);
+            El += __ldcg(partials + 4 * (size_t)b + 3);
+        }
+    double Wk = 0.0, Ek = 0.0;
+    if (prm.kspace) {
+        Wk = prm.qqr2e * (__ldcg(WEk + 0) + __ldcg(WEk + 4) + __ldcg(WEk + 8));
+        Ek = prm.qqr2e * (__ldcg(WEk + 9) + __ldcg(WEk + 10));
+    }
+    const double W = Wk + Wr;
+    const double V = cell[0] * cell[1] * cell[2];
+    const double Pins = (K2 + W) / (3.0 * V);
+    double pV = prm.barostat ? cell[3] : 0.0;
+    if (do_kick && prm.barostat) pV += 0.5 * prm.dt * (Pins - prm.P_ext);
+    cell[3] = pV;
+    cell[4] = W;
+    cell[5] = K2;
+    cell[6] = Pins;
+    cell[7] = Ek;
+    cell[8] = Ec;
+    cell[9] = El;
+    cell[10] = V;
+    if (!isfinite(Pins) || !isfinite(pV)) atomicOr(status, kStatusNonFinite);
+    *counter = 0u;
+}
+
+// ---------------------------------------------------------------------------------
+// Host side.
+
+static rbe_status npt_fail(rbe_ctx ctx, cudaError_t e, const char* what) { return cuda_fail(ctx, e, what); }
+
+static rbe_status npt_check(rbe_ctx ctx, const char* what)
+{
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? RBE_OK : npt_fail(ctx, e, what);
+}
+
+// Grow the NPT scratch for N particles and a box that may grow by 30 %.
+static rbe_status npt_ensure(rbe_ctx ctx, int64_t N, const double box[3], double rc)
+{
+    NptBuffers& b = ctx->npt;
+    cudaError_t e;
+    if (!b.WEk) {
+        if ((e = cudaMalloc(&b.WEk, 16 * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc(&b.coef, sizeof(NptCoef))) != cudaSuccess ||
+            (e = cudaMalloc(&b.counter, sizeof(unsigned))) != cudaSuccess ||
+            (e = cudaMemset(b.counter, 0, sizeof(unsigned))) != cudaSuccess)
+            return npt_fail(ctx, e, "cudaMalloc(npt)");
+    }
+    if (N > b.ncap) {
+        cudaFree(b.Fk); cudaFree(b.Fr); cudaFree(b.cid); cudaFree(b.sorted); cudaFree(b.spos);
+        b.Fk = b.Fr = nullptr; b.cid = b.sorted = nullptr; b.spos = nullptr; b.ncap = 0;
+        if ((e = cudaMalloc(&b.Fk, 3 * sizeof(double) * N)) != cudaSuccess ||
+            (e = cudaMalloc(&b.Fr, 3 * sizeof(double) * N)) != cudaSuccess ||
+            (e = cudaMalloc(&b.cid, sizeof(int) * N)) != cudaSuccess ||
+            (e = cudaMalloc(&b.sorted, sizeof(int) * N)) != cudaSuccess ||
+            (e = cudaMalloc(&b.spos, 32 * N)) != cudaSuccess)
+            return npt_fail(ctx, e, "cudaMalloc(npt particles)");
+        b.ncap = N;
+    }
+    int64_t cells = 1;
+    for (int t = 0; t < 3; ++t) cells *= std::max<int64_t>(1, (int64_t)std::floor(1.3 * box[t] / rc));
+    if (cells > b.cellcap) {
+        cudaFree(b.cnt); cudaFree(b.start); cudaFree(b.cursor);
+        b.cnt = b.start = b.cursor = nullptr;
+        b.cellcap = 0;
+        if ((e = cudaMalloc(&b.cnt, sizeof(int) * cells)) != cudaSuccess ||
+            (e = cudaMalloc(&b.start, sizeof(int) * cells)) != cudaSuccess ||
+            (e = cudaMalloc(&b.cursor, sizeof(int) * cells)) != cudaSuccess)
+            return npt_fail(ctx, e, "cudaMalloc(cells)");
+        b.cellcap = (int)cells;
+    }
+    const int nb = (int)((N + kNptThreads - 1) / kNptThreads);
+    if (2 * nb > b.partcap) {
+        cudaFree(b.partials);
+        b.partials = nullptr;
+        b.partcap = 0;
+        if ((e = cudaMalloc(&b.partials, sizeof(double) * 4 * 2 * (size_t)nb)) != cudaSuccess)
+            return npt_fail(ctx, e, "cudaMalloc(npt partials)");
+        b.partcap = 2 * nb;
+    }
+    return RBE_OK;
+}
+
+// Forces, virial and energies at the current state (k-space batch `batch`), then the
+// finishing kernel (with or without the R^p/2 and V^p/2 of the step's end).
+static rbe_status npt_forces(rbe_ctx ctx, rbe_system* sys, uint64_t batch, int do_kick)
+{
+    NptBuffers& b = ctx->npt;
+    const rbe_npt_params& prm = sys->params;
+    cudaStream_t s = ctx->stream;
+    const int64_t N = sys->N;
+    const int nb = (int)((N + kNptThreads - 1) / kNptThreads);
+    rbe_status st;
+    if (prm.kspace) {
+        // tables from the device box, then the evaluation
+        if ((st = launch_tables(ctx, sys->cell)) != RBE_OK) return st;
+        ctx->tables_dirty = true;  // the snapshot API must rebuild from its own box
+        if ((st = ensure_k_capacity(ctx, ctx->P)) != RBE_OK) return st;
+        if ((st = launch_sample_device_box(ctx, batch, ctx->P)) != RBE_OK) return st;
+        if ((st = launch_evaluate(ctx, N, sys->pos, sys->charge, ctx->P, true, b.Fk, b.WEk, b.WEk + 9)) != RBE_OK)
+            return st;
+    }
+    if (prm.real && N > 0) {
+        cudaError_t e = cudaMemsetAsync(b.cnt, 0, sizeof(int) * b.cellcap, s);
+        if (e != cudaSuccess) return npt_fail(ctx, e, "cudaMemsetAsync(cells)");
+        k_cl_count<<<nb, kNptThreads, 0, s>>>(N, sys->pos, sys->cell, prm.rc, b.cellcap, b.cid, b.cnt, ctx->d.status);
+        k_cl_scan<<<1, kScanThreads, 0, s>>>(sys->cell, prm.rc, b.cellcap, b.cnt, b.start, b.cursor);
+        k_cl_fill<<<nb, kNptThreads, 0, s>>>(N, b.cid, b.cursor, b.sorted);
+        const int cb = (b.cellcap + 127) / 128;
+        const bool fp64 = ctx->precision == RBE_FP64;
+        if (fp64) {
+            k_cl_sort<double4_32a><<<cb, 128, 0, s>>>(sys->cell, prm.rc, b.cellcap, b.cnt, b.start, b.sorted, sys->pos,
+                                                      sys->charge, static_cast<double4_32a*>(b.spos));
+            k_pair<double, double4_32a><<<nb, kNptThreads, 0, s>>>(
+                N, sys->pos, sys->charge, sys->cell, prm.rc, ctx->alpha, prm.qqr2e, prm.lj_sigma, prm.lj_eps, b.cid,
+                b.cnt, b.start, b.sorted, static_cast<const double4_32a*>(b.spos), b.Fr, b.partials);
+        } else {
+            k_cl_sort<float4><<<cb, 128, 0, s>>>(sys->cell, prm.rc, b.cellcap, b.cnt, b.start, b.sorted, sys->pos,
+                                                 sys->charge, static_cast<float4*>(b.spos));
+            k_pair<float, float4><<<nb, kNptThreads, 0, s>>>(
+                N, sys->pos, sys->charge, sys->cell, prm.rc, ctx->alpha, prm.qqr2e, prm.lj_sigma, prm.lj_eps, b.cid,
+                b.cnt, b.start, b.sorted, static_cast<const float4*>(b.spos), b.Fr, b.partials);
+        }
+        if ((st = npt_check(ctx, "real-space kernels")) != RBE_OK) return st;
+    }
+    k_npt_finish<<<std::max(1, nb), kNptThreads, 0, s>>>(N, sys->mom, sys->force, sys->mass, b.Fk, b.Fr, b.WEk,
+                                                         reinterpret_cast<const NptCoef*>(b.coef), b.partials, nb,
+                                                         b.counter, sys->cell, prm, do_kick, ctx->d.status);
+    return npt_check(ctx, "k_npt_finish");
+}
+
+static rbe_status npt_validate(rbe_ctx ctx, const rbe_system* sys)
+{
+    if (!sys) return fail(ctx, RBE_EINVAL, "system is NULL");
+    const rbe_npt_params& p = sys->params;
+    if (sys->N < 1 || sys->N > ((int64_t)1 << 31) - 256) return fail(ctx, RBE_EINVAL, "N out of range");
+    if (!sys->pos || !sys->mom || !sys->force || !sys->charge || !sys->mass || !sys->cell)
+        return fail(ctx, RBE_EINVAL, "system buffers must not be NULL");
+    if (!(p.dt > 0.0) || !(p.kT >= 0.0) || !(p.gamma >= 0.0) || !(p.gamma_V >= 0.0) || !(p.rc > 0.0) ||
+        !(p.max_disp >= 0.0) || (p.barostat && !(p.M_V > 0.0)))
+        return fail(ctx, RBE_EINVAL, "invalid NPT parameters");
+    if ((sys->step >> 56) != 0) return fail(ctx, RBE_EINVAL, "step must be < 2^56");
+    return RBE_OK;
+}
+
+// The nearest-image real space needs rc <= l/2.  The host checks the box it is given (the
+// caller's initial box, read back once by rbe_npt_init).
+static rbe_status npt_box_check(rbe_ctx ctx, const rbe_system* sys, double box[3])
+{
+    cudaError_t e = cudaMemcpyAsync(box, sys->cell, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return npt_fail(ctx, e, "read box");
+    for (int t = 0; t < 3; ++t) {
+        if (!(box[t] > 0.0) || !std::isfinite(box[t])) return fail(ctx, RBE_EINVAL, "cell box must be > 0");
+        if (sys->params.real && box[t] < 2.0 * sys->params.rc)
+            return fail(ctx, RBE_EINVAL, "real space needs rc <= l/2 on every axis");
+    }
+    return RBE_OK;
+}
+
+rbe_status npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch)
+{
+    rbe_status st = npt_validate(ctx, sys);
+    if (st != RBE_OK) return st;
+    double box[3];
+    if ((st = npt_box_check(ctx, sys, box)) != RBE_OK) return st;
+    if ((st = npt_ensure(ctx, sys->N, box, sys->params.rc)) != RBE_OK) return st;
+    // tables for boxes up to 30 % longer than the initial one
+    int need = 0;
+    for (int t = 0; t < 3; ++t) need = std::max(need, 2 * host_axis_M(ctx->alpha, 1.3 * box[t]) + 1);
+    if ((st = ensure_table_capacity(ctx, need)) != RBE_OK) return st;
+    ctx->npt_ready_N = sys->N;
+    return npt_forces(ctx, sys, batch, 0);
+}
+
+rbe_status npt_run(rbe_ctx ctx, rbe_system* sys, int32_t nsteps)
+{
+    if (nsteps < 1) return fail(ctx, RBE_EINVAL, "nsteps must be >= 1");
+    rbe_status st = npt_validate(ctx, sys);
+    if (st != RBE_OK) return st;
+    if (ctx->npt_ready_N != sys->N) return fail(ctx, RBE_ESTATE, "call rbe_npt_init for this system first");
+    cudaStream_t s = ctx->stream;
+    const int64_t N = sys->N;
+    const int nb = (int)((N + kNptThreads - 1) / kNptThreads);
+    NptCoef* cf = reinterpret_cast<NptCoef*>(ctx->npt.coef);
+    for (int32_t k = 0; k < nsteps; ++k) {
+        const uint64_t step = sys->step;
+        k_npt_cell_a<<<1, 32, 0, s>>>(sys->cell, cf, sys->params, ctx->seed, step);
+        k_npt_drift<<<nb, kNptThreads, 0, s>>>(N, sys->pos, sys->mom, sys->force, sys->mass, cf, ctx->seed, step);
+        if ((st = npt_check(ctx, "k_npt_cell_a/k_npt_drift")) != RBE_OK) return st;
+        if ((st = npt_forces(ctx, sys, step, 1)) != RBE_OK) return st;
+        sys->step = step + 1;
+    }
+    return RBE_OK;
+}
+
+}  // namespace rbe
