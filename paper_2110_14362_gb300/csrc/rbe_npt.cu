@@ -294,7 +294,7 @@ __global__ void k_cl_sort(const double* __restrict__ cell, double rc, int cellca
 template <typename R, typename T4>
 __global__ void __launch_bounds__(kNptThreads)
 k_pair(int64_t N, const double* __restrict__ pos, const double* __restrict__ q, const double* __restrict__ cell,
-       double rc, double alpha, double qqr2e, double lj_sigma, double lj_eps, const int* __restrict__ cid,
+       int cellcap, double rc, double alpha, double qqr2e, double lj_sigma, double lj_eps, const int* __restrict__ cid,
        const int* __restrict__ cnt, const int* __restrict__ start, const int* __restrict__ sorted,
        const T4* __restrict__ spos, double* __restrict__ Fr, double* __restrict__ partials)
 {
@@ -306,7 +306,9 @@ k_pair(int64_t N, const double* __restrict__ pos, const double* __restrict__ q, 
     const R rc2 = (R)(rc * rc), sa = (R)sqrt(alpha), two_sa_pi = (R)(2.0 * sqrt(alpha / 3.14159265358979323846));
     const R qk = (R)qqr2e, s2 = (R)(lj_sigma * lj_sigma), e4 = (R)(4.0 * lj_eps), e24 = (R)(24.0 * lj_eps);
     R fx = 0, fy = 0, fz = 0, w = 0, ec = 0, el = 0;
-    if (i < N) {
+    // a box that outgrew the cell arrays was flagged by k_cl_count: no neighbour search then
+    const bool cells_ok = (int64_t)nc[0] * nc[1] * nc[2] <= (int64_t)cellcap;
+    if (i < N && cells_ok) {
         const R xi = (R)pos[3 * i], yi = (R)pos[3 * i + 1], zi = (R)pos[3 * i + 2], qi = (R)q[i];
         const int c = cid[i];
         const int cx = c % nc[0], cy = (c / nc[0]) % nc[1], cz = c / (nc[0] * nc[1]);
@@ -348,6 +350,8 @@ k_pair(int64_t N, const double* __restrict__ pos, const double* __restrict__ q, 
                         w += f * r2;
                     }
                 }
+    }
+    if (i < N) {
         Fr[3 * i] = (double)fx;
         Fr[3 * i + 1] = (double)fy;
         Fr[3 * i + 2] = (double)fz;
@@ -536,14 +540,14 @@ static rbe_status npt_forces(rbe_ctx ctx, rbe_system* sys, uint64_t batch, int d
             k_cl_sort<double4_32a><<<cb, 128, 0, s>>>(sys->cell, prm.rc, b.cellcap, b.cnt, b.start, b.sorted, sys->pos,
                                                       sys->charge, static_cast<double4_32a*>(b.spos));
             k_pair<double, double4_32a><<<nb, kNptThreads, 0, s>>>(
-                N, sys->pos, sys->charge, sys->cell, prm.rc, ctx->alpha, prm.qqr2e, prm.lj_sigma, prm.lj_eps, b.cid,
-                b.cnt, b.start, b.sorted, static_cast<const double4_32a*>(b.spos), b.Fr, b.partials);
+                N, sys->pos, sys->charge, sys->cell, b.cellcap, prm.rc, ctx->alpha, prm.qqr2e, prm.lj_sigma, prm.lj_eps,
+                b.cid, b.cnt, b.start, b.sorted, static_cast<const double4_32a*>(b.spos), b.Fr, b.partials);
         } else {
             k_cl_sort<float4><<<cb, 128, 0, s>>>(sys->cell, prm.rc, b.cellcap, b.cnt, b.start, b.sorted, sys->pos,
                                                  sys->charge, static_cast<float4*>(b.spos));
             k_pair<float, float4><<<nb, kNptThreads, 0, s>>>(
-                N, sys->pos, sys->charge, sys->cell, prm.rc, ctx->alpha, prm.qqr2e, prm.lj_sigma, prm.lj_eps, b.cid,
-                b.cnt, b.start, b.sorted, static_cast<const float4*>(b.spos), b.Fr, b.partials);
+                N, sys->pos, sys->charge, sys->cell, b.cellcap, prm.rc, ctx->alpha, prm.qqr2e, prm.lj_sigma, prm.lj_eps,
+                b.cid, b.cnt, b.start, b.sorted, static_cast<const float4*>(b.spos), b.Fr, b.partials);
         }
         if ((st = npt_check(ctx, "real-space kernels")) != RBE_OK) return st;
     }
