@@ -74,8 +74,13 @@ rbe_status rbe_create(const double box[3], double alpha, int32_t P, uint64_t see
 rbe_status rbe_destroy(rbe_ctx ctx);
 
 /* Set the CUDA stream (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream)
- * on which all later device work of this context runs.  NULL = the legacy default stream. */
+ * on which all later device work of this context runs.  NULL = the legacy default stream.
+ * The context's scratch is allocated in stream order; switching streams first waits for the
+ * old stream. */
 rbe_status rbe_set_stream(rbe_ctx ctx, void* stream);
+
+/* Replace the Philox key used by later calls (sampling and NPT noise). */
+rbe_status rbe_set_seed(rbe_ctx ctx, uint64_t seed);
 
 /* Select the arithmetic: precision in rbe_precision, rho_accum in rbe_rho_accum
  * (rho_accum is ignored on the FP64 path). */
@@ -229,8 +234,74 @@ rbe_status rbe_npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch);
 
 /* Advance nsteps >= 1 steps (Sec. 3.3); asynchronous on the context's stream; sys->step
  * advances by nsteps.  The context's box is not used: each step rebuilds the sampling tables
- * from the device box in sys->cell. */
+ * from the device box in sys->cell.  The step index also lives on the device (cell[11], as
+ * 64-bit integer bits, set by rbe_npt_init and advanced by every step), so the launches of
+ * one call may be captured once in a CUDA graph and replayed for later steps. */
 rbe_status rbe_npt_step(rbe_ctx ctx, rbe_system* sys, int32_t nsteps);
+
+/* ---------------------------------------------------------------------------------
+ * Serving loop for independent NPT replicas (continuous batching on one GPU; no counterpart
+ * in the paper, whose runs are single systems).  Requests queue on the host; a request is
+ * admitted when a slot is free and its device memory fits the budget, and its state stays
+ * resident in HBM until it finishes.  Each resident replica runs on its own non-blocking
+ * stream and context, in chunks of chunk_steps NPT steps (rbe_npt_step), captured once per
+ * replica as a CUDA graph when use_graphs != 0; chunks of different replicas run
+ * concurrently, and requests are admitted while others run.  A replica's result does not
+ * depend on what else is resident (no shared state; fixed-order reductions). */
+typedef struct rbe_server_s* rbe_server;
+
+typedef struct {
+    double alpha;        /* Ewald splitting of every replica */
+    int32_t P;           /* RBE batch size */
+    int32_t precision;   /* rbe_precision */
+    int32_t max_slots;   /* replicas resident at once, 1..4096 */
+    int32_t chunk_steps; /* NPT steps per chunk, >= 1 */
+    int64_t mem_budget;  /* device bytes the resident replicas may use; a replica of N particles
+                            counts N*176 + (P+1)*32768 + 4 MiB bytes (state, NPT scratch, tables) */
+    int32_t use_graphs;  /* 1: replay a captured graph per chunk; 0: launch the steps directly */
+    int32_t pad;
+} rbe_server_config;
+
+typedef struct {
+    int64_t N;
+    const double* pos;     /* host N*3 (copied at submission) */
+    const double* mom;     /* host N*3 */
+    const double* charge;  /* host N */
+    const double* mass;    /* host N */
+    double box[3];
+    double pV;             /* initial piston momentum */
+    uint64_t seed;         /* Philox key of this replica (RBE batches and noise) */
+    int32_t nsteps;        /* steps to run, >= 1 */
+    int32_t pad;
+    rbe_npt_params params;
+} rbe_request;
+
+rbe_status rbe_server_create(const rbe_server_config* cfg, rbe_server* out);
+rbe_status rbe_server_destroy(rbe_server s);
+
+/* Enqueue a request (inputs are copied, the caller may reuse its buffers); *id counts from 0.
+ * RBE_ENOMEM if the request alone exceeds the memory budget. */
+rbe_status rbe_server_submit(rbe_server s, const rbe_request* req, int64_t* id);
+
+/* One round of the loop: observe finished chunks (non-blocking event queries), retire
+ * finished requests (their results are copied to host memory), admit queued requests in
+ * arrival order while a slot is free and the budget allows, and launch the next chunk of
+ * every idle resident replica.  With wait != 0 it repeats until at least one chunk has
+ * finished (or nothing is left).  Outputs (may be NULL): queued, resident, finished counts. */
+rbe_status rbe_server_progress(rbe_server s, int32_t wait, int32_t* n_queued, int32_t* n_active, int64_t* n_done);
+
+/* Final state of a finished request into host memory (any pointer may be NULL): pos, mom
+ * N*3 and the cell block (RBE_CELL_DOUBLES).  RBE_ESTATE while it runs. */
+rbe_status rbe_server_result(rbe_server s, int64_t id, double* pos, double* mom, double* cell);
+
+/* Per-chunk latencies in seconds (launch to observed completion), up to `capacity` of them;
+ * the number of chunks and steps finished; the span from the first admission to the last
+ * retirement. */
+rbe_status rbe_server_stats(rbe_server s, double* chunk_latency, int64_t capacity, int64_t* n_chunks,
+                            int64_t* steps_done, double* span_seconds);
+
+/* Message for the server's last failure. */
+const char* rbe_server_last_error(rbe_server s);
 
 /* Static description of a status code. */
 const char* rbe_status_string(rbe_status status);

@@ -46,12 +46,26 @@ class System(ctypes.Structure):
 
 RBE_CELL_DOUBLES = 16
 
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("P", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("max_slots", ctypes.c_int32), ("chunk_steps", ctypes.c_int32), ("mem_budget", ctypes.c_int64),
+                ("use_graphs", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("pos", ctypes.c_void_p), ("mom", ctypes.c_void_p),
+                ("charge", ctypes.c_void_p), ("mass", ctypes.c_void_p), ("box", ctypes.c_double * 3),
+                ("pV", ctypes.c_double), ("seed", ctypes.c_uint64), ("nsteps", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("params", NptParams)]
+
 # (name, restype, argtypes) of every exported symbol
 SIGNATURES = [
     ("rbe_create", ctypes.c_int, [_dp, ctypes.c_double, ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(_vp)]),
     ("rbe_destroy", ctypes.c_int, [_vp]),
     ("rbe_set_stream", ctypes.c_int, [_vp, _vp]),
     ("rbe_set_precision", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
+    ("rbe_set_seed", ctypes.c_int, [_vp, ctypes.c_uint64]),
     ("rbe_set_box", ctypes.c_int, [_vp, _dp]),
     ("rbe_sample_k", ctypes.c_int, [_vp, ctypes.c_uint64, _ip, _dp]),
     ("rbe_kspace_forces_virial", ctypes.c_int, [_vp, ctypes.c_int64, _vp, _vp, ctypes.c_uint64, _vp, _vp, _vp]),
@@ -68,6 +82,15 @@ SIGNATURES = [
      [_dp, ctypes.c_double, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, _vp, _vp, _vp]),
     ("rbe_npt_init", ctypes.c_int, [_vp, ctypes.POINTER(System), ctypes.c_uint64]),
     ("rbe_npt_step", ctypes.c_int, [_vp, ctypes.POINTER(System), ctypes.c_int32]),
+    ("rbe_server_create", ctypes.c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_vp)]),
+    ("rbe_server_destroy", ctypes.c_int, [_vp]),
+    ("rbe_server_submit", ctypes.c_int, [_vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_int64)]),
+    ("rbe_server_progress", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]),
+    ("rbe_server_result", ctypes.c_int, [_vp, ctypes.c_int64, _dp, _dp, _dp]),
+    ("rbe_server_stats", ctypes.c_int, [_vp, _dp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_int64), _dp]),
+    ("rbe_server_last_error", ctypes.c_char_p, [_vp]),
     ("rbe_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("rbe_last_error", ctypes.c_char_p, [_vp]),
     ("rbe_version", ctypes.c_int32, []),
@@ -145,6 +168,10 @@ def rbe_set_stream(h, stream_handle: int):
 
 def rbe_set_precision(h, precision: int, rho_accum: int = RBE_RHO_FP32):
     _check(load().rbe_set_precision(h, int(precision), int(rho_accum)), h)
+
+
+def rbe_set_seed(h, seed: int):
+    _check(load().rbe_set_seed(h, int(seed)), h)
 
 
 def rbe_set_box(h, box):
@@ -256,6 +283,73 @@ class NptReplica:
         """(pos, mom, force, box, cell block) as NumPy arrays (synchronises)."""
         c = self.cell.cpu().numpy()
         return (self.pos.cpu().numpy(), self.mom.cpu().numpy(), self.force.cpu().numpy(), c[:3].copy(), c)
+
+
+class Server:
+    """The C++ serving loop (rbe_server_*): submit requests, call progress() until all are
+    done, read results and chunk-latency statistics."""
+
+    def __init__(self, alpha, P, precision=RBE_FP32_PHASE, max_slots=32, chunk_steps=10,
+                 mem_budget=8 << 30, use_graphs=True):
+        cfg = ServerConfig(alpha=float(alpha), P=int(P), precision=int(precision), max_slots=int(max_slots),
+                           chunk_steps=int(chunk_steps), mem_budget=int(mem_budget),
+                           use_graphs=int(bool(use_graphs)), pad=0)
+        self.h = ctypes.c_void_p()
+        lib = load()
+        st = lib.rbe_server_create(ctypes.byref(cfg), ctypes.byref(self.h))
+        if st != RBE_OK:
+            raise RBEError(st, lib.rbe_last_error(None).decode())
+        self._n = {}
+
+    def _check(self, st):
+        if st != RBE_OK:
+            lib = load()
+            raise RBEError(st, f"{lib.rbe_status_string(st).decode()}: {lib.rbe_server_last_error(self.h).decode()}")
+
+    def close(self):
+        if self.h:
+            load().rbe_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, pos, mom, charge, mass, box, params: NptParams, seed: int, nsteps: int, pV: float = 0.0):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (pos, mom, charge, mass)]
+        req = Request(N=int(arrs[2].shape[0]), pos=arrs[0].ctypes.data, mom=arrs[1].ctypes.data,
+                      charge=arrs[2].ctypes.data, mass=arrs[3].ctypes.data,
+                      box=(ctypes.c_double * 3)(*[float(b) for b in box]), pV=float(pV), seed=int(seed),
+                      nsteps=int(nsteps), pad=0, params=params)
+        rid = ctypes.c_int64()
+        self._check(load().rbe_server_submit(self.h, ctypes.byref(req), ctypes.byref(rid)))
+        self._n[rid.value] = req.N
+        return rid.value
+
+    def progress(self, wait: bool = False):
+        q, a, d = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        self._check(load().rbe_server_progress(self.h, int(bool(wait)), ctypes.byref(q), ctypes.byref(a),
+                                               ctypes.byref(d)))
+        return q.value, a.value, d.value
+
+    def result(self, rid: int):
+        N = self._n[rid]
+        pos = np.zeros((N, 3))
+        mom = np.zeros((N, 3))
+        cell = np.zeros(RBE_CELL_DOUBLES)
+        self._check(load().rbe_server_result(self.h, rid, pos.ctypes.data_as(_dp), mom.ctypes.data_as(_dp),
+                                             cell.ctypes.data_as(_dp)))
+        return pos, mom, cell
+
+    def stats(self):
+        n, steps, span = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+        load().rbe_server_stats(self.h, None, 0, ctypes.byref(n), ctypes.byref(steps), ctypes.byref(span))
+        lat = np.zeros(max(n.value, 1))
+        load().rbe_server_stats(self.h, lat.ctypes.data_as(_dp), n.value, ctypes.byref(n), ctypes.byref(steps),
+                                ctypes.byref(span))
+        return lat[:n.value], steps.value, span.value
 
 
 def rbe_version() -> int:

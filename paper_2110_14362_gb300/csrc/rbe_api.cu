@@ -163,9 +163,10 @@ rbe_status rbe_create(const double box[3], double alpha, int32_t P, uint64_t see
         delete ctx;
         return fail(nullptr, err == cudaErrorMemoryAllocation ? RBE_ENOMEM : RBE_ECUDA, msg);
     }
+    // frequency buffers now; the tables are built by the first evaluation (tables_dirty), on
+    // whatever stream the context uses by then.  Only the legacy default stream is waited for.
     st = ensure_k_capacity(ctx, P);
-    if (st == RBE_OK) st = ensure_tables(ctx);
-    if (st == RBE_OK && (err = cudaDeviceSynchronize()) != cudaSuccess) st = cuda_fail(ctx, err, "rbe_create");
+    if (st == RBE_OK && (err = cudaStreamSynchronize(nullptr)) != cudaSuccess) st = cuda_fail(ctx, err, "rbe_create");
     if (st != RBE_OK) {
         std::string msg = ctx->last_error;
         free_buffers(d);
@@ -192,7 +193,20 @@ rbe_status rbe_destroy(rbe_ctx ctx)
 rbe_status rbe_set_stream(rbe_ctx ctx, void* stream)
 {
     if (!ctx) return RBE_EINVAL;
+    if (static_cast<cudaStream_t>(stream) != ctx->stream) {
+        // scratch was allocated in the old stream's order: finish it before switching
+        DeviceGuard g(ctx->device);
+        cudaError_t err = cudaStreamSynchronize(ctx->stream);
+        if (err != cudaSuccess) return cuda_fail(ctx, err, "rbe_set_stream");
+    }
     ctx->stream = static_cast<cudaStream_t>(stream);
+    return RBE_OK;
+}
+
+rbe_status rbe_set_seed(rbe_ctx ctx, uint64_t seed)
+{
+    if (!ctx) return RBE_EINVAL;
+    ctx->seed = seed;
     return RBE_OK;
 }
 
@@ -274,15 +288,15 @@ rbe_status rbe_kspace_forces_virial_host(rbe_ctx ctx, int64_t N, const double* p
     if (!g.ok) return fail(ctx, RBE_ECUDA, "cannot select the context's device");
     DeviceBuffers& d = ctx->d;
     cudaError_t err;
-    if (!d.WE && (err = cudaMalloc(&d.WE, 11 * sizeof(double))) != cudaSuccess)
+    if (!d.WE && (err = ctx_alloc(ctx, &d.WE, 11 * sizeof(double))) != cudaSuccess)
         return cuda_fail(ctx, err, "cudaMalloc(host-call outputs)");
     if (N > d.ncap) {
-        cudaFree(d.pos); cudaFree(d.q); cudaFree(d.F);
+        ctx_free(ctx, d.pos); ctx_free(ctx, d.q); ctx_free(ctx, d.F);
         d.pos = d.q = d.F = nullptr;
         d.ncap = 0;
-        if ((err = cudaMalloc(&d.pos, sizeof(double) * 3 * N)) != cudaSuccess ||
-            (err = cudaMalloc(&d.q, sizeof(double) * N)) != cudaSuccess ||
-            (err = cudaMalloc(&d.F, sizeof(double) * 3 * N)) != cudaSuccess)
+        if ((err = ctx_alloc(ctx, &d.pos, sizeof(double) * 3 * N)) != cudaSuccess ||
+            (err = ctx_alloc(ctx, &d.q, sizeof(double) * N)) != cudaSuccess ||
+            (err = ctx_alloc(ctx, &d.F, sizeof(double) * 3 * N)) != cudaSuccess)
             return cuda_fail(ctx, err, "cudaMalloc(host-call staging)");
         d.ncap = N;
     }

@@ -115,6 +115,19 @@ struct rbe_ctx_s {
 
 namespace rbe {
 
+// Stream-ordered (re)allocation of context scratch: it never synchronises the device, so
+// contexts on other streams keep running while one grows its buffers.
+template <typename T>
+inline cudaError_t ctx_alloc(rbe_ctx ctx, T** p, size_t bytes)
+{
+    return cudaMallocAsync(reinterpret_cast<void**>(p), bytes, ctx->stream);
+}
+
+inline void ctx_free(rbe_ctx ctx, void* p)
+{
+    if (p) cudaFreeAsync(p, ctx->stream);
+}
+
 // Device validation helpers (rbe_api.cu).
 rbe_status fail(rbe_ctx ctx, rbe_status st, const std::string& msg);
 rbe_status cuda_fail(rbe_ctx ctx, cudaError_t err, const char* what);
@@ -128,7 +141,7 @@ rbe_status ensure_table_capacity(rbe_ctx ctx, int need);
 rbe_status launch_tables(rbe_ctx ctx, const double* box_dev);
 rbe_status ensure_k_capacity(rbe_ctx ctx, int K);
 rbe_status launch_sample(rbe_ctx ctx, uint64_t step, int P);
-rbe_status launch_sample_device_box(rbe_ctx ctx, uint64_t step, int P);
+rbe_status launch_sample_device_box(rbe_ctx ctx, uint64_t step, int P, const unsigned long long* step_dev);
 rbe_status npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch);
 rbe_status npt_run(rbe_ctx ctx, rbe_system* sys, int32_t nsteps);
 rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int K,

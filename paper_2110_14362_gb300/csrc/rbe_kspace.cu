@@ -185,12 +185,14 @@ __device__ __forceinline__ unsigned long long scaled_target(unsigned long long U
 // operations only: U from 53 bits of Philox output, T = floor(U C_2M / 2^53), and the
 // search over the integer cumulative weights.  The block copies the three rows to shared
 // memory when they fit (smem_cap > 0).
-__global__ void k_sample(uint64_t seed, uint64_t step, int P, const unsigned long long* __restrict__ cum,
-                         int cap, int smem_cap, const KState* __restrict__ ks, int4* __restrict__ m_out,
-                         double* __restrict__ w_out, unsigned* __restrict__ status)
+__global__ void k_sample(uint64_t seed, uint64_t step_arg, const unsigned long long* __restrict__ step_dev, int P,
+                         const unsigned long long* __restrict__ cum, int cap, int smem_cap,
+                         const KState* __restrict__ ks, int4* __restrict__ m_out, double* __restrict__ w_out,
+                         unsigned* __restrict__ status)
 {
     extern __shared__ unsigned long long s_cum[];
     pdl_trigger();  // the rho pass may start staging its particles meanwhile
+    const uint64_t step = step_dev ? *step_dev : step_arg;  // a device-resident step index when given
     const double wP = ks->wP;
     const unsigned long long* tx = cum;
     const unsigned long long* ty = cum + cap;
@@ -880,11 +882,11 @@ static rbe_status check_launch(rbe_ctx ctx, const char* what)
 rbe_status ensure_table_capacity(rbe_ctx ctx, int need)
 {
     if (need <= ctx->d.tab_cap) return RBE_OK;
-    if (ctx->d.cum) cudaFree(ctx->d.cum);
+    if (ctx->d.cum) ctx_free(ctx, ctx->d.cum);
     ctx->d.cum = nullptr;
     ctx->d.tab_cap = 0;
     const int cap = need + need / 4 + 16;
-    cudaError_t err = cudaMalloc(&ctx->d.cum, sizeof(unsigned long long) * 3 * (size_t)cap);
+    cudaError_t err = ctx_alloc(ctx, &ctx->d.cum, sizeof(unsigned long long) * 3 * (size_t)cap);
     if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaMalloc(tables)");
     ctx->d.tab_cap = cap;
     return RBE_OK;
@@ -913,19 +915,19 @@ rbe_status ensure_k_capacity(rbe_ctx ctx, int K)
 {
     if (K <= ctx->d.kcap) return RBE_OK;
     DeviceBuffers& d = ctx->d;
-    cudaFree(d.m); cudaFree(d.w); cudaFree(d.rho); cudaFree(d.terms);
-    cudaFree(d.coef_m); cudaFree(d.coef_f); cudaFree(d.coef_d);
+    ctx_free(ctx, d.m); ctx_free(ctx, d.w); ctx_free(ctx, d.rho); ctx_free(ctx, d.terms);
+    ctx_free(ctx, d.coef_m); ctx_free(ctx, d.coef_f); ctx_free(ctx, d.coef_d);
     d.m = nullptr; d.w = nullptr; d.rho = nullptr; d.terms = nullptr;
     d.coef_m = nullptr; d.coef_f = nullptr; d.coef_d = nullptr;
     d.kcap = 0;
     cudaError_t err = cudaSuccess;
-    if ((err = cudaMalloc(&d.m, sizeof(int4) * K)) != cudaSuccess ||
-        (err = cudaMalloc(&d.w, sizeof(double) * K)) != cudaSuccess ||
-        (err = cudaMalloc(&d.rho, sizeof(double2) * K)) != cudaSuccess ||
-        (err = cudaMalloc(&d.terms, sizeof(double) * 8 * (size_t)(K + 1))) != cudaSuccess ||
-        (err = cudaMalloc(&d.coef_m, sizeof(int4) * K)) != cudaSuccess ||
-        (err = cudaMalloc(&d.coef_f, sizeof(float4) * K)) != cudaSuccess ||
-        (err = cudaMalloc(&d.coef_d, sizeof(double2) * K)) != cudaSuccess)
+    if ((err = ctx_alloc(ctx, &d.m, sizeof(int4) * K)) != cudaSuccess ||
+        (err = ctx_alloc(ctx, &d.w, sizeof(double) * K)) != cudaSuccess ||
+        (err = ctx_alloc(ctx, &d.rho, sizeof(double2) * K)) != cudaSuccess ||
+        (err = ctx_alloc(ctx, &d.terms, sizeof(double) * 8 * (size_t)(K + 1))) != cudaSuccess ||
+        (err = ctx_alloc(ctx, &d.coef_m, sizeof(int4) * K)) != cudaSuccess ||
+        (err = ctx_alloc(ctx, &d.coef_f, sizeof(float4) * K)) != cudaSuccess ||
+        (err = ctx_alloc(ctx, &d.coef_d, sizeof(double2) * K)) != cudaSuccess)
         return cuda_fail(ctx, err, "cudaMalloc(frequency buffers)");
     d.kcap = K;
     return RBE_OK;
@@ -937,11 +939,12 @@ rbe_status launch_sample(rbe_ctx ctx, uint64_t step, int P)
 {
     rbe_status st = ensure_tables(ctx);
     if (st != RBE_OK) return st;
-    return launch_sample_device_box(ctx, step, P);
+    return launch_sample_device_box(ctx, step, P, nullptr);
 }
 
-// The sampler on the tables already on the device (built by launch_tables from any box).
-rbe_status launch_sample_device_box(rbe_ctx ctx, uint64_t step, int P)
+// The sampler on the tables already on the device (built by launch_tables from any box);
+// step_dev, when not NULL, points at a device-resident step index used instead of step.
+rbe_status launch_sample_device_box(rbe_ctx ctx, uint64_t step, int P, const unsigned long long* step_dev)
 {
     rbe_status st = ensure_k_capacity(ctx, P);
     if (st != RBE_OK) return st;
@@ -950,7 +953,8 @@ rbe_status launch_sample_device_box(rbe_ctx ctx, uint64_t step, int P)
     const size_t smem = sizeof(unsigned long long) * 3 * (size_t)ctx->d.tab_cap;
     const int smem_cap = smem <= (size_t)kSampleSmemMax ? ctx->d.tab_cap : 0;
     k_sample<<<(P + threads - 1) / threads, threads, smem_cap ? smem : 0, ctx->stream>>>(
-        ctx->seed, step, P, ctx->d.cum, ctx->d.tab_cap, smem_cap, ctx->d.ks, ctx->d.m, ctx->d.w, ctx->d.status);
+        ctx->seed, step, step_dev, P, ctx->d.cum, ctx->d.tab_cap, smem_cap, ctx->d.ks, ctx->d.m, ctx->d.w,
+        ctx->d.status);
     record_event(ctx, 1);
     return check_launch(ctx, "k_sample");
 }
@@ -1066,10 +1070,10 @@ rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const doub
     const Plan p = make_plan(ctx, N, K, rho_bps, bps_force, fp64 ? kT * 2 : kForceRound);
     const size_t need = (size_t)(K + 1) * p.nchunks;
     if (need > d.part_cap) {
-        cudaFree(d.partials);
+        ctx_free(ctx, d.partials);
         d.partials = nullptr;
         d.part_cap = 0;
-        cudaError_t err = cudaMalloc(&d.partials, 16 * need);
+        cudaError_t err = ctx_alloc(ctx, &d.partials, 16 * need);
         if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaMalloc(partials)");
         d.part_cap = need;
     }

@@ -67,10 +67,25 @@ __device__ __forceinline__ void npt_normals(uint64_t seed, uint32_t stream, uint
 // ---------------------------------------------------------------------------------
 // Cell-variable part of the step (Sec. 3.3): V^p/2, R^p/2 coefficient, V/2, R/2
 // coefficient, O^p, R/2 coefficient, V/2, R^p/2 coefficient.  cell = {l, p_V, W, 2K, ...}.
+// The step index lives on the device (cell[kCellStep] as 64-bit integer bits), so that a
+// captured sequence of steps can be replayed: every kernel reads it, k_npt_finish advances it.
+constexpr int kCellStep = 11;
+
+__device__ __forceinline__ uint64_t cell_step(const double* cell)
+{
+    return (uint64_t)__double_as_longlong(cell[kCellStep]);
+}
+
+__global__ void k_npt_set_step(double* __restrict__ cell, uint64_t step)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) cell[kCellStep] = __longlong_as_double((long long)step);
+}
+
 __global__ void k_npt_cell_a(double* __restrict__ cell, NptCoef* __restrict__ cf, rbe_npt_params prm,
-                             uint64_t seed, uint64_t step)
+                             uint64_t seed)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const uint64_t step = cell_step(cell);
     const double h = 0.5 * prm.dt;
     double L[3] = {cell[0], cell[1], cell[2]};
     double V = L[0] * L[1] * L[2];
@@ -141,10 +156,12 @@ __device__ __forceinline__ void capped_add(double r[3], double d[3], double cap)
 // Particle part before the forces: R^p/2, R/2, O, R/2, wrap into the new box.
 __global__ void __launch_bounds__(kNptThreads)
 k_npt_drift(int64_t N, double* __restrict__ pos, double* __restrict__ mom, const double* __restrict__ force,
-            const double* __restrict__ mass, const NptCoef* __restrict__ cfp, uint64_t seed, uint64_t step)
+            const double* __restrict__ mass, const NptCoef* __restrict__ cfp, uint64_t seed,
+            const double* __restrict__ cell)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    const uint64_t step = cell_step(cell);
     const NptCoef c = *cfp;
     const double m = mass[i];
     double r[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
@@ -447,6 +464,7 @@ k_npt_finish(int64_t N, double* __restrict__ mom, double* __restrict__ force, co
     cell[8] = Ec;
     cell[9] = El;
     cell[10] = V;
+    if (do_kick) cell[kCellStep] = __longlong_as_double((long long)(cell_step(cell) + 1));
     if (!isfinite(Pins) || !isfinite(pV)) atomicOr(status, kStatusNonFinite);
     *counter = 0u;
 }
@@ -468,41 +486,41 @@ static rbe_status npt_ensure(rbe_ctx ctx, int64_t N, const double box[3], double
     NptBuffers& b = ctx->npt;
     cudaError_t e;
     if (!b.WEk) {
-        if ((e = cudaMalloc(&b.WEk, 16 * sizeof(double))) != cudaSuccess ||
-            (e = cudaMalloc(&b.coef, sizeof(NptCoef))) != cudaSuccess ||
-            (e = cudaMalloc(&b.counter, sizeof(unsigned))) != cudaSuccess ||
-            (e = cudaMemset(b.counter, 0, sizeof(unsigned))) != cudaSuccess)
+        if ((e = ctx_alloc(ctx, &b.WEk, 16 * sizeof(double))) != cudaSuccess ||
+            (e = ctx_alloc(ctx, &b.coef, sizeof(NptCoef))) != cudaSuccess ||
+            (e = ctx_alloc(ctx, &b.counter, sizeof(unsigned))) != cudaSuccess ||
+            (e = cudaMemsetAsync(b.counter, 0, sizeof(unsigned), ctx->stream)) != cudaSuccess)
             return npt_fail(ctx, e, "cudaMalloc(npt)");
     }
     if (N > b.ncap) {
-        cudaFree(b.Fk); cudaFree(b.Fr); cudaFree(b.cid); cudaFree(b.sorted); cudaFree(b.spos);
+        ctx_free(ctx, b.Fk); ctx_free(ctx, b.Fr); ctx_free(ctx, b.cid); ctx_free(ctx, b.sorted); ctx_free(ctx, b.spos);
         b.Fk = b.Fr = nullptr; b.cid = b.sorted = nullptr; b.spos = nullptr; b.ncap = 0;
-        if ((e = cudaMalloc(&b.Fk, 3 * sizeof(double) * N)) != cudaSuccess ||
-            (e = cudaMalloc(&b.Fr, 3 * sizeof(double) * N)) != cudaSuccess ||
-            (e = cudaMalloc(&b.cid, sizeof(int) * N)) != cudaSuccess ||
-            (e = cudaMalloc(&b.sorted, sizeof(int) * N)) != cudaSuccess ||
-            (e = cudaMalloc(&b.spos, 32 * N)) != cudaSuccess)
+        if ((e = ctx_alloc(ctx, &b.Fk, 3 * sizeof(double) * N)) != cudaSuccess ||
+            (e = ctx_alloc(ctx, &b.Fr, 3 * sizeof(double) * N)) != cudaSuccess ||
+            (e = ctx_alloc(ctx, &b.cid, sizeof(int) * N)) != cudaSuccess ||
+            (e = ctx_alloc(ctx, &b.sorted, sizeof(int) * N)) != cudaSuccess ||
+            (e = ctx_alloc(ctx, &b.spos, 32 * N)) != cudaSuccess)
             return npt_fail(ctx, e, "cudaMalloc(npt particles)");
         b.ncap = N;
     }
     int64_t cells = 1;
     for (int t = 0; t < 3; ++t) cells *= std::max<int64_t>(1, (int64_t)std::floor(1.3 * box[t] / rc));
     if (cells > b.cellcap) {
-        cudaFree(b.cnt); cudaFree(b.start); cudaFree(b.cursor);
+        ctx_free(ctx, b.cnt); ctx_free(ctx, b.start); ctx_free(ctx, b.cursor);
         b.cnt = b.start = b.cursor = nullptr;
         b.cellcap = 0;
-        if ((e = cudaMalloc(&b.cnt, sizeof(int) * cells)) != cudaSuccess ||
-            (e = cudaMalloc(&b.start, sizeof(int) * cells)) != cudaSuccess ||
-            (e = cudaMalloc(&b.cursor, sizeof(int) * cells)) != cudaSuccess)
+        if ((e = ctx_alloc(ctx, &b.cnt, sizeof(int) * cells)) != cudaSuccess ||
+            (e = ctx_alloc(ctx, &b.start, sizeof(int) * cells)) != cudaSuccess ||
+            (e = ctx_alloc(ctx, &b.cursor, sizeof(int) * cells)) != cudaSuccess)
             return npt_fail(ctx, e, "cudaMalloc(cells)");
         b.cellcap = (int)cells;
     }
     const int nb = (int)((N + kNptThreads - 1) / kNptThreads);
     if (2 * nb > b.partcap) {
-        cudaFree(b.partials);
+        ctx_free(ctx, b.partials);
         b.partials = nullptr;
         b.partcap = 0;
-        if ((e = cudaMalloc(&b.partials, sizeof(double) * 4 * 2 * (size_t)nb)) != cudaSuccess)
+        if ((e = ctx_alloc(ctx, &b.partials, sizeof(double) * 4 * 2 * (size_t)nb)) != cudaSuccess)
             return npt_fail(ctx, e, "cudaMalloc(npt partials)");
         b.partcap = 2 * nb;
     }
@@ -524,7 +542,9 @@ static rbe_status npt_forces(rbe_ctx ctx, rbe_system* sys, uint64_t batch, int d
         if ((st = launch_tables(ctx, sys->cell)) != RBE_OK) return st;
         ctx->tables_dirty = true;  // the snapshot API must rebuild from its own box
         if ((st = ensure_k_capacity(ctx, ctx->P)) != RBE_OK) return st;
-        if ((st = launch_sample_device_box(ctx, batch, ctx->P)) != RBE_OK) return st;
+        if ((st = launch_sample_device_box(ctx, batch, ctx->P,
+                                           reinterpret_cast<const unsigned long long*>(sys->cell + kCellStep))) != RBE_OK)
+            return st;
         if ((st = launch_evaluate(ctx, N, sys->pos, sys->charge, ctx->P, true, b.Fk, b.WEk, b.WEk + 9)) != RBE_OK)
             return st;
     }
@@ -598,7 +618,12 @@ rbe_status npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch)
     for (int t = 0; t < 3; ++t) need = std::max(need, 2 * host_axis_M(ctx->alpha, 1.3 * box[t]) + 1);
     if ((st = ensure_table_capacity(ctx, need)) != RBE_OK) return st;
     ctx->npt_ready_N = sys->N;
-    return npt_forces(ctx, sys, batch, 0);
+    k_npt_set_step<<<1, 32, 0, ctx->stream>>>(sys->cell, batch);
+    if ((st = npt_check(ctx, "k_npt_set_step")) != RBE_OK) return st;
+    st = npt_forces(ctx, sys, batch, 0);
+    if (st != RBE_OK) return st;
+    k_npt_set_step<<<1, 32, 0, ctx->stream>>>(sys->cell, sys->step);
+    return npt_check(ctx, "k_npt_set_step");
 }
 
 rbe_status npt_run(rbe_ctx ctx, rbe_system* sys, int32_t nsteps)
@@ -613,8 +638,8 @@ rbe_status npt_run(rbe_ctx ctx, rbe_system* sys, int32_t nsteps)
     NptCoef* cf = reinterpret_cast<NptCoef*>(ctx->npt.coef);
     for (int32_t k = 0; k < nsteps; ++k) {
         const uint64_t step = sys->step;
-        k_npt_cell_a<<<1, 32, 0, s>>>(sys->cell, cf, sys->params, ctx->seed, step);
-        k_npt_drift<<<nb, kNptThreads, 0, s>>>(N, sys->pos, sys->mom, sys->force, sys->mass, cf, ctx->seed, step);
+        k_npt_cell_a<<<1, 32, 0, s>>>(sys->cell, cf, sys->params, ctx->seed);
+        k_npt_drift<<<nb, kNptThreads, 0, s>>>(N, sys->pos, sys->mom, sys->force, sys->mass, cf, ctx->seed, sys->cell);
         if ((st = npt_check(ctx, "k_npt_cell_a/k_npt_drift")) != RBE_OK) return st;
         if ((st = npt_forces(ctx, sys, step, 1)) != RBE_OK) return st;
         sys->step = step + 1;

@@ -1,0 +1,403 @@
+// Serving loop for independent NPT replicas (continuous batching on one GPU).
+//
+// Requests (N charges, initial state, NPT parameters, number of steps) queue on the host.
+// A request is admitted when a slot is free and its device memory fits the budget; its
+// state then stays resident in HBM until it finishes.  Every resident replica runs on its
+// own non-blocking stream with its own context, in chunks of `chunk_steps` steps; a chunk is
+// the library's NPT step launches captured once per replica as a CUDA graph (the step index
+// is device-resident, so one graph serves every chunk).  Chunks of different replicas run
+// concurrently on the GPU and new requests are admitted while others run.  Latency of a
+// chunk = host time from its launch to the observation of its completion event.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "rbe_context.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    rbe_request r;
+    std::vector<double> pos, mom, q, m;  // copies of the caller's host inputs
+    std::vector<double> out_pos, out_mom, out_cell;
+    int state = 0;  // 0 queued, 1 resident, 2 done, 3 failed
+    rbe_status error = RBE_OK;
+    double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
+};
+
+struct Slot {
+    bool busy = false;
+    int64_t req = -1;
+    rbe_ctx ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    double *pos = nullptr, *mom = nullptr, *force = nullptr, *charge = nullptr, *mass = nullptr, *cell = nullptr;
+    int64_t ncap = 0;
+    rbe_system sys{};
+    int32_t steps_left = 0;
+    bool in_flight = false;
+    int32_t chunk_in_flight = 0;
+    double t_launch = 0.0;
+    cudaGraphExec_t graph = nullptr;
+    int32_t graph_steps = 0;
+    int64_t bytes = 0;
+};
+
+}  // namespace
+
+struct rbe_server_s {
+    rbe_server_config cfg;
+    std::vector<std::unique_ptr<Request>> reqs;
+    std::deque<int64_t> queue;
+    std::vector<Slot> slots;
+    int64_t mem_used = 0;
+    std::vector<double> latencies;
+    int64_t steps_done = 0;
+    int64_t n_done = 0;
+    Clock::time_point t0;
+    double t_first_admit = -1.0, t_last_done = 0.0;
+    std::string last_error;
+    int device = 0;
+};
+
+namespace rbe {
+
+static double now_s(const rbe_server_s* s)
+{
+    return std::chrono::duration<double>(Clock::now() - s->t0).count();
+}
+
+static rbe_status sfail(rbe_server_s* s, rbe_status st, const std::string& msg)
+{
+    if (s) s->last_error = msg;
+    return fail(nullptr, st, msg);
+}
+
+// Device bytes a replica of N particles holds while resident: its state (r, p, F: 72 B;
+// q, m: 16 B), the context's NPT scratch (k-space and real-space forces 48 B, cell list
+// 8 B + 32 B packed positions) and a fixed allowance for tables, frequency buffers and
+// partial sums.
+static int64_t replica_bytes(int64_t N, int P)
+{
+    return N * (72 + 16 + 48 + 8 + 32) + (int64_t)(P + 1) * 16 * 2048 + (4 << 20);
+}
+
+static void release_slot(rbe_server_s* s, Slot& sl)
+{
+    if (sl.graph) {
+        cudaGraphExecDestroy(sl.graph);
+        sl.graph = nullptr;
+        sl.graph_steps = 0;
+    }
+    s->mem_used -= sl.bytes;
+    sl.bytes = 0;
+    sl.busy = false;
+    sl.req = -1;
+    sl.in_flight = false;
+}
+
+static rbe_status ensure_slot_buffers(rbe_server_s* s, Slot& sl, int64_t N)
+{
+    if (!sl.stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        if (e != cudaSuccess) return sfail(s, RBE_ECUDA, std::string("slot stream: ") + cudaGetErrorString(e));
+    }
+    if (N > sl.ncap) {
+        for (double** p : {&sl.pos, &sl.mom, &sl.force, &sl.charge, &sl.mass}) {
+            if (*p) cudaFreeAsync(*p, sl.stream);
+            *p = nullptr;
+        }
+        cudaError_t e = cudaSuccess;
+        if ((e = cudaMallocAsync(&sl.pos, sizeof(double) * 3 * N, sl.stream)) != cudaSuccess ||
+            (e = cudaMallocAsync(&sl.mom, sizeof(double) * 3 * N, sl.stream)) != cudaSuccess ||
+            (e = cudaMallocAsync(&sl.force, sizeof(double) * 3 * N, sl.stream)) != cudaSuccess ||
+            (e = cudaMallocAsync(&sl.charge, sizeof(double) * N, sl.stream)) != cudaSuccess ||
+            (e = cudaMallocAsync(&sl.mass, sizeof(double) * N, sl.stream)) != cudaSuccess)
+            return sfail(s, RBE_ENOMEM, std::string("slot buffers: ") + cudaGetErrorString(e));
+        sl.ncap = N;
+    }
+    if (!sl.cell) {
+        cudaError_t e = cudaMallocAsync(&sl.cell, sizeof(double) * RBE_CELL_DOUBLES, sl.stream);
+        if (e != cudaSuccess) return sfail(s, RBE_ENOMEM, std::string("slot cell: ") + cudaGetErrorString(e));
+    }
+    return RBE_OK;
+}
+
+// Admit request `id` into slot `sl`: upload its state, initialise the forces, capture the
+// chunk graph.  Everything runs on the slot's stream; no device-wide synchronisation.
+static rbe_status admit(rbe_server_s* s, Slot& sl, int64_t id)
+{
+    Request& rq = *s->reqs[id];
+    const int64_t N = rq.r.N;
+    rbe_status st = ensure_slot_buffers(s, sl, N);
+    if (st != RBE_OK) return st;
+    if (!sl.ctx) {
+        st = rbe_create(rq.r.box, s->cfg.alpha, s->cfg.P, rq.r.seed, &sl.ctx);
+        if (st != RBE_OK) return sfail(s, st, std::string("slot context: ") + rbe_last_error(nullptr));
+        rbe_set_precision(sl.ctx, s->cfg.precision, RBE_RHO_FP32);
+        if ((st = rbe_set_stream(sl.ctx, sl.stream)) != RBE_OK) return st;
+    }
+    rbe_set_seed(sl.ctx, rq.r.seed);
+    if ((st = rbe_set_box(sl.ctx, rq.r.box)) != RBE_OK) return sfail(s, st, rbe_last_error(sl.ctx));
+    double cell[RBE_CELL_DOUBLES] = {0};
+    for (int t = 0; t < 3; ++t) cell[t] = rq.r.box[t];
+    cell[3] = rq.r.pV;
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaMemcpyAsync(sl.pos, rq.pos.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice, sl.stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(sl.mom, rq.mom.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice, sl.stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(sl.charge, rq.q.data(), sizeof(double) * N, cudaMemcpyHostToDevice, sl.stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(sl.mass, rq.m.data(), sizeof(double) * N, cudaMemcpyHostToDevice, sl.stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(sl.cell, cell, sizeof(cell), cudaMemcpyHostToDevice, sl.stream)) != cudaSuccess)
+        return sfail(s, RBE_ECUDA, std::string("upload: ") + cudaGetErrorString(e));
+    sl.sys = rbe_system{N, sl.pos, sl.mom, sl.force, sl.charge, sl.mass, sl.cell, 0, rq.r.params};
+    if ((st = rbe_npt_init(sl.ctx, &sl.sys, 0)) != RBE_OK) return sfail(s, st, rbe_last_error(sl.ctx));
+    if (sl.graph) {
+        cudaGraphExecDestroy(sl.graph);
+        sl.graph = nullptr;
+    }
+    sl.graph_steps = 0;
+    if (s->cfg.use_graphs && rq.r.nsteps >= s->cfg.chunk_steps) {
+        // one chunk of launches, captured; the device step index makes it replayable
+        cudaGraph_t g = nullptr;
+        rbe_system probe = sl.sys;
+        e = cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            st = rbe_npt_step(sl.ctx, &probe, s->cfg.chunk_steps);
+            e = cudaStreamEndCapture(sl.stream, &g);
+            if (st != RBE_OK) {
+                if (g) cudaGraphDestroy(g);
+                return sfail(s, st, std::string("capture: ") + rbe_last_error(sl.ctx));
+            }
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&sl.graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) return sfail(s, RBE_ECUDA, std::string("graph: ") + cudaGetErrorString(e));
+        sl.graph_steps = s->cfg.chunk_steps;
+    }
+    sl.busy = true;
+    sl.req = id;
+    sl.steps_left = rq.r.nsteps;
+    sl.in_flight = false;
+    sl.bytes = replica_bytes(N, s->cfg.P);
+    s->mem_used += sl.bytes;
+    rq.state = 1;
+    rq.t_admit = now_s(s);
+    if (s->t_first_admit < 0.0) s->t_first_admit = rq.t_admit;
+    return RBE_OK;
+}
+
+static rbe_status launch_chunk(rbe_server_s* s, Slot& sl)
+{
+    const int32_t n = std::min(sl.steps_left, s->cfg.chunk_steps);
+    rbe_status st = RBE_OK;
+    if (sl.graph && n == sl.graph_steps) {
+        cudaError_t e = cudaGraphLaunch(sl.graph, sl.stream);
+        if (e != cudaSuccess) return sfail(s, RBE_ECUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+        sl.sys.step += (uint64_t)n;
+    } else {
+        st = rbe_npt_step(sl.ctx, &sl.sys, n);
+        if (st != RBE_OK) return sfail(s, st, rbe_last_error(sl.ctx));
+    }
+    cudaError_t e = cudaEventRecord(sl.done, sl.stream);
+    if (e != cudaSuccess) return sfail(s, RBE_ECUDA, std::string("cudaEventRecord: ") + cudaGetErrorString(e));
+    sl.in_flight = true;
+    sl.chunk_in_flight = n;
+    sl.t_launch = now_s(s);
+    return RBE_OK;
+}
+
+static rbe_status retire(rbe_server_s* s, Slot& sl)
+{
+    Request& rq = *s->reqs[sl.req];
+    const int64_t N = rq.r.N;
+    rq.out_pos.resize(3 * N);
+    rq.out_mom.resize(3 * N);
+    rq.out_cell.resize(RBE_CELL_DOUBLES);
+    cudaError_t e = cudaMemcpyAsync(rq.out_pos.data(), sl.pos, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, sl.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(rq.out_mom.data(), sl.mom, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, sl.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(rq.out_cell.data(), sl.cell, sizeof(double) * RBE_CELL_DOUBLES, cudaMemcpyDeviceToHost,
+                            sl.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sl.stream);
+    rbe_status st = e == cudaSuccess ? rbe_sync(sl.ctx) : RBE_ECUDA;
+    rq.state = st == RBE_OK ? 2 : 3;
+    rq.error = st;
+    rq.t_done = now_s(s);
+    s->t_last_done = rq.t_done;
+    ++s->n_done;
+    release_slot(s, sl);
+    return RBE_OK;  // a failed request is reported through rbe_server_result, not here
+}
+
+}  // namespace rbe
+
+using namespace rbe;
+
+extern "C" {
+
+rbe_status rbe_server_create(const rbe_server_config* cfg, rbe_server* out)
+{
+    if (!cfg || !out) return fail(nullptr, RBE_EINVAL, "cfg and out must not be NULL");
+    if (!(cfg->alpha > 0.0) || cfg->P < 1 || cfg->P > 65536 || cfg->max_slots < 1 || cfg->max_slots > 4096 ||
+        cfg->chunk_steps < 1 || cfg->mem_budget <= 0 ||
+        (cfg->precision != RBE_FP64 && cfg->precision != RBE_FP32_PHASE))
+        return fail(nullptr, RBE_EINVAL, "invalid server configuration");
+    rbe_server s = new (std::nothrow) rbe_server_s();
+    if (!s) return fail(nullptr, RBE_ENOMEM, "host allocation failed");
+    s->cfg = *cfg;
+    s->slots.resize(cfg->max_slots);
+    s->t0 = Clock::now();
+    cudaGetDevice(&s->device);
+    *out = s;
+    return RBE_OK;
+}
+
+rbe_status rbe_server_destroy(rbe_server s)
+{
+    if (!s) return RBE_OK;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != s->device) cudaSetDevice(s->device);
+    for (Slot& sl : s->slots) {
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.graph) cudaGraphExecDestroy(sl.graph);
+        if (sl.ctx) rbe_destroy(sl.ctx);  // frees its scratch on the slot's stream
+        for (double* p : {sl.pos, sl.mom, sl.force, sl.charge, sl.mass, sl.cell})
+            if (p) cudaFreeAsync(p, sl.stream);
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+    }
+    if (cur >= 0 && cur != s->device) cudaSetDevice(cur);
+    delete s;
+    return RBE_OK;
+}
+
+rbe_status rbe_server_submit(rbe_server s, const rbe_request* req, int64_t* id)
+{
+    if (!s || !req || !id) return fail(nullptr, RBE_EINVAL, "NULL argument");
+    const int64_t N = req->N;
+    if (N < 1 || N > ((int64_t)1 << 31) - 256 || req->nsteps < 1 || !req->pos || !req->mom || !req->charge ||
+        !req->mass)
+        return sfail(s, RBE_EINVAL, "invalid request");
+    for (int t = 0; t < 3; ++t)
+        if (!(req->box[t] > 0.0)) return sfail(s, RBE_EINVAL, "box lengths must be > 0");
+    if (replica_bytes(N, s->cfg.P) > s->cfg.mem_budget)
+        return sfail(s, RBE_ENOMEM, "request larger than the whole memory budget");
+    auto rq = std::make_unique<Request>();
+    rq->r = *req;
+    rq->pos.assign(req->pos, req->pos + 3 * N);
+    rq->mom.assign(req->mom, req->mom + 3 * N);
+    rq->q.assign(req->charge, req->charge + N);
+    rq->m.assign(req->mass, req->mass + N);
+    rq->r.pos = rq->pos.data();
+    rq->r.mom = rq->mom.data();
+    rq->r.charge = rq->q.data();
+    rq->r.mass = rq->m.data();
+    rq->t_submit = now_s(s);
+    *id = (int64_t)s->reqs.size();
+    s->reqs.push_back(std::move(rq));
+    s->queue.push_back(*id);
+    return RBE_OK;
+}
+
+rbe_status rbe_server_progress(rbe_server s, int32_t wait, int32_t* n_queued, int32_t* n_active, int64_t* n_done)
+{
+    if (!s) return RBE_EINVAL;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != s->device) cudaSetDevice(s->device);
+    bool any_done = false;
+    for (;;) {
+        // 1. observe finished chunks
+        for (Slot& sl : s->slots) {
+            if (!sl.busy || !sl.in_flight) continue;
+            const cudaError_t q = cudaEventQuery(sl.done);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) return sfail(s, RBE_ECUDA, std::string("cudaEventQuery: ") + cudaGetErrorString(q));
+            s->latencies.push_back(now_s(s) - sl.t_launch);
+            sl.in_flight = false;
+            sl.steps_left -= sl.chunk_in_flight;
+            s->steps_done += sl.chunk_in_flight;
+            any_done = true;
+            if (sl.steps_left <= 0) retire(s, sl);
+        }
+        // 2. admit while a slot is free and the budget allows (first come, first served)
+        while (!s->queue.empty()) {
+            const int64_t id = s->queue.front();
+            const int64_t need = replica_bytes(s->reqs[id]->r.N, s->cfg.P);
+            if (s->mem_used + need > s->cfg.mem_budget) break;
+            Slot* free_slot = nullptr;
+            for (Slot& sl : s->slots)
+                if (!sl.busy) {
+                    free_slot = &sl;
+                    break;
+                }
+            if (!free_slot) break;
+            s->queue.pop_front();
+            const rbe_status st = admit(s, *free_slot, id);
+            if (st != RBE_OK) {
+                s->reqs[id]->state = 3;
+                s->reqs[id]->error = st;
+                ++s->n_done;
+                return st;
+            }
+        }
+        // 3. next chunk of every resident replica that is idle
+        for (Slot& sl : s->slots)
+            if (sl.busy && !sl.in_flight && sl.steps_left > 0) {
+                const rbe_status st = launch_chunk(s, sl);
+                if (st != RBE_OK) return st;
+            }
+        bool active = false;
+        for (const Slot& sl : s->slots) active = active || sl.busy;
+        if (!wait || any_done || (!active && s->queue.empty())) break;
+    }
+    int32_t na = 0;
+    for (const Slot& sl : s->slots) na += sl.busy ? 1 : 0;
+    if (n_queued) *n_queued = (int32_t)s->queue.size();
+    if (n_active) *n_active = na;
+    if (n_done) *n_done = s->n_done;
+    return RBE_OK;
+}
+
+rbe_status rbe_server_result(rbe_server s, int64_t id, double* pos, double* mom, double* cell)
+{
+    if (!s || id < 0 || id >= (int64_t)s->reqs.size()) return RBE_EINVAL;
+    const Request& rq = *s->reqs[id];
+    if (rq.state == 3) return sfail(s, rq.error, "request failed");
+    if (rq.state != 2) return sfail(s, RBE_ESTATE, "request not finished");
+    const int64_t N = rq.r.N;
+    if (pos) std::memcpy(pos, rq.out_pos.data(), sizeof(double) * 3 * N);
+    if (mom) std::memcpy(mom, rq.out_mom.data(), sizeof(double) * 3 * N);
+    if (cell) std::memcpy(cell, rq.out_cell.data(), sizeof(double) * RBE_CELL_DOUBLES);
+    return RBE_OK;
+}
+
+rbe_status rbe_server_stats(rbe_server s, double* chunk_latency, int64_t capacity, int64_t* n_chunks,
+                            int64_t* steps_done, double* span_seconds)
+{
+    if (!s) return RBE_EINVAL;
+    const int64_t n = (int64_t)s->latencies.size();
+    if (chunk_latency)
+        std::memcpy(chunk_latency, s->latencies.data(), sizeof(double) * (size_t)std::min(n, std::max<int64_t>(capacity, 0)));
+    if (n_chunks) *n_chunks = n;
+    if (steps_done) *steps_done = s->steps_done;
+    if (span_seconds) *span_seconds = s->t_first_admit >= 0.0 ? s->t_last_done - s->t_first_admit : 0.0;
+    return RBE_OK;
+}
+
+const char* rbe_server_last_error(rbe_server s) { return s ? s->last_error.c_str() : ""; }
+
+}  // extern "C"

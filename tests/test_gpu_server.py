@@ -1,0 +1,146 @@
+"""GPU tests of the serving loop (rbe_server_*): a replica's result does not depend on what
+else is resident, graph replay equals direct launches, admission respects the memory budget,
+and the served FP64 trajectory matches the oracle's NPT step (Sec. 3.2-3.3)."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2110_14362_gb300 as rbe
+
+from gpu_util import cuda_device
+
+pytestmark = pytest.mark.gpu
+
+ALPHA = 0.2
+P = 100
+DEADLINE_S = 300.0
+
+
+def _system(n_side, seed, density=0.1):
+    N = n_side ** 3
+    L = (N / density) ** (1 / 3)
+    rng = np.random.default_rng(seed)
+    g = (np.arange(n_side) + 0.5) * (L / n_side)
+    pos = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    pos = np.mod(pos + rng.uniform(-0.3, 0.3, pos.shape), L)
+    q = np.where(np.arange(N) % 2 == 0, 1.0, -1.0)
+    m = np.full(N, 20.0)
+    mom = rng.normal(size=(N, 3)) * np.sqrt(oracle.KB * 300 * 100 * m)[:, None]
+    return pos, mom, q, m, np.array([L, L, L])
+
+
+def _base(box, rc=6.0):
+    V0 = float(np.prod(box))
+    return dict(dt=0.001, kT=oracle.KB * 300.0, P_ext=1.0 * oracle.BAR, gamma=10.0, gamma_V=2.0,
+                M_V=oracle.piston_mass(0.5, 4.5e-5 / oracle.BAR, V0), rc=rc, qqr2e=oracle.QQR2E, lj_sigma=2.0,
+                lj_eps=0.5, max_disp=0.05, kspace=1, real=1, noise=1, barostat=1)
+
+
+REQS = [  # (n_side, seed of the system, Philox seed, steps)
+    (6, 1, 11, 9),
+    (10, 2, 22, 14),
+    (8, 3, 33, 7),
+    (7, 4, 44, 12),
+]
+
+
+def _serve(reqs, precision, max_slots, chunk_steps=4, use_graphs=True, mem_budget=8 << 30, order=None):
+    """Run `reqs` through one server; returns {index: (pos, mom, cell)} and the largest number
+    of replicas seen resident at once."""
+    cuda_device()
+    srv = rbe.Server(ALPHA, P, precision, max_slots=max_slots, chunk_steps=chunk_steps,
+                     mem_budget=mem_budget, use_graphs=use_graphs)
+    try:
+        ids = {}
+        for i in (order if order is not None else range(len(reqs))):
+            n_side, sseed, pseed, nsteps = reqs[i]
+            pos, mom, q, m, box = _system(n_side, sseed)
+            ids[i] = srv.submit(pos, mom, q, m, box, rbe.NptParams(**_base(box)), pseed, nsteps)
+        t_end = time.monotonic() + DEADLINE_S
+        peak = 0
+        while True:
+            nq, na, nd = srv.progress(wait=True)
+            peak = max(peak, na)
+            if nd == len(ids):
+                break
+            assert time.monotonic() < t_end, "serving loop did not finish"
+        lat, steps, span = srv.stats()
+        assert steps == sum(reqs[i][3] for i in ids)
+        assert len(lat) == sum(-(-reqs[i][3] // chunk_steps) for i in ids)
+        assert np.all(lat > 0) and span > 0
+        return {i: srv.result(r) for i, r in ids.items()}, peak
+    finally:
+        srv.close()
+
+
+def _direct(req, precision):
+    n_side, sseed, pseed, nsteps = req
+    pos, mom, q, m, box = _system(n_side, sseed)
+    with rbe.Context(box, ALPHA, P, pseed, precision) as ctx:
+        rep = rbe.NptReplica(pos, mom, q, m, box, rbe.NptParams(**_base(box)), cuda_device(), step=0)
+        rep.init(ctx, batch=0)
+        rep.step(ctx, nsteps)
+        ctx.sync()
+        r, p, F, L, cell = rep.state()
+    return r, p, cell
+
+
+def _same(a, b):
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("precision", [rbe.RBE_FP64, rbe.RBE_FP32_PHASE])
+def test_served_equals_direct_steps(precision):
+    # chunks of 4 steps: graph replays for the whole chunks, direct launches for the tail
+    out, _ = _serve(REQS[:2], precision, max_slots=2)
+    for i in range(2):
+        _same(out[i], _direct(REQS[i], precision))
+
+
+@pytest.mark.parametrize("precision", [rbe.RBE_FP64, rbe.RBE_FP32_PHASE])
+def test_alone_equals_mixed(precision):
+    alone = {i: _serve([REQS[i]], precision, max_slots=1)[0][0] for i in (0, 2)}
+    mixed, peak = _serve(REQS, precision, max_slots=4, order=[3, 0, 1, 2])
+    assert peak >= 2
+    for i in (0, 2):
+        _same(mixed[i], alone[i])
+
+
+def test_graphs_equal_direct_launches():
+    a, _ = _serve(REQS, rbe.RBE_FP32_PHASE, max_slots=4, use_graphs=True)
+    b, _ = _serve(REQS, rbe.RBE_FP32_PHASE, max_slots=4, use_graphs=False)
+    for i in a:
+        _same(a[i], b[i])
+
+
+def test_budget_limits_residency():
+    # the budget fits one replica of the largest request, not two
+    big = max(r[0] ** 3 for r in REQS)
+    one = big * 176 + (P + 1) * 32768 + (4 << 20)
+    tight, peak = _serve(REQS, rbe.RBE_FP32_PHASE, max_slots=4, mem_budget=one + one // 2)
+    assert peak == 1
+    free, peak_free = _serve(REQS, rbe.RBE_FP32_PHASE, max_slots=4)
+    assert peak_free >= 2
+    for i in free:
+        _same(tight[i], free[i])
+
+
+def test_served_fp64_matches_oracle():
+    req = REQS[0]
+    out, _ = _serve([req], rbe.RBE_FP64, max_slots=1)
+    r, p, cell = out[0]
+    n_side, sseed, pseed, nsteps = req
+    pos, mom, q, m, box = _system(n_side, sseed)
+    prm = oracle.npt_params(alpha=ALPHA, P=P, seed=pseed, **_base(box))
+    st = oracle.NptState(pos, mom, q, m, box)
+    oracle.npt_forces(st, 0, prm)
+    for s in range(nsteps):
+        oracle.npt_step(st, s, prm)
+    assert np.allclose(cell[:3], st.L, rtol=1e-12, atol=0)
+    d = r - st.r
+    d -= st.L * np.round(d / st.L)
+    assert np.abs(d).max() < 1e-10 * st.L[0]
+    assert np.abs(p - st.p).max() < 1e-10 * np.abs(st.p).max()
