@@ -248,6 +248,8 @@ def run_ours(args, world, rank, local):
                 "peak": peak_dfma / 1e9, "unit": "GDFMA/s", "frac": None, "traffic": None}
     ctx.close()
 
+    serving = None if args.skip_serving else run_serving(args, world, rank)
+
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         cpu = cpu_baseline(s, budget_s=args.cpu_seconds)
@@ -270,8 +272,89 @@ def run_ours(args, world, rank, local):
     }
     if other:
         line["fp64_same_workload"] = other
+    if serving:
+        line["serving"] = serving
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+# Serving workload: Langevin NPT replicas with RBE k-space, erfc real space and LJ 12-6
+# (300 K, 1 bar, dt = 1 fs, gamma = 10/ps, gamma_V = 2/ps, tau_P = 0.5 ps, beta_T = 4.5e-5/bar),
+# charges screened by the relative permittivity of water (primitive electrolyte model),
+# starting from jittered-lattice positions.
+SERVE_ALPHA, SERVE_P, SERVE_RC, SERVE_EPS_R = 0.2, 100, 7.0, 78.5
+KB = 0.00831446261815324
+BAR = 6.02214076e-5
+
+
+def serve_params(rbe, box):
+    V0 = float(np.prod(box))
+    return rbe.NptParams(dt=0.001, kT=KB * 300.0, P_ext=1.0 * BAR, gamma=10.0, gamma_V=2.0,
+                         M_V=rbe.piston_mass(0.5, 4.5e-5 / BAR, V0), rc=SERVE_RC, qqr2e=1389.35457644382 / SERVE_EPS_R,
+                         lj_sigma=2.0, lj_eps=0.5, max_disp=0.05, kspace=1, real=1, noise=1, barostat=1)
+
+
+def serve(rbe, reqs, states, precision, max_slots, chunk, nsteps, use_graphs=True, open_loop=False,
+          budget=32 << 30, deadline_s=600.0):
+    """Drive the C++ serving loop: submit every request at t = 0 (closed loop) or at its
+    Poisson arrival time (open loop), poll until all are done.  Returns the metrics."""
+    srv = rbe.Server(SERVE_ALPHA, SERVE_P, precision, max_slots=max_slots, chunk_steps=chunk,
+                     mem_budget=budget, use_graphs=use_graphs)
+    try:
+        t0 = time.perf_counter()
+        nxt = 0
+        order = sorted(range(len(reqs)), key=lambda i: reqs[i].arrival_s)
+        done = 0
+        while done < len(reqs):
+            now = time.perf_counter() - t0
+            while nxt < len(order) and (not open_loop or reqs[order[nxt]].arrival_s <= now):
+                i = order[nxt]
+                pos, mom, q, m, box = states[i]
+                srv.submit(pos, mom, q, m, box, serve_params(rbe, box), 1000 + reqs[i].rid, nsteps)
+                nxt += 1
+            nq, na, done = srv.progress(wait=not open_loop or nxt == len(order))
+            if open_loop and na == 0 and nq == 0 and nxt < len(order):
+                time.sleep(max(0.0, reqs[order[nxt]].arrival_s - (time.perf_counter() - t0)))
+            if time.perf_counter() - t0 > deadline_s:
+                raise RuntimeError("serving loop exceeded its deadline")
+        wall = time.perf_counter() - t0
+        lat, steps, span = srv.stats()
+    finally:
+        srv.close()
+    return {"requests": len(reqs), "replica_steps": int(steps), "wall_s": wall,
+            "replica_steps_per_s": steps / wall,
+            "pair_evals_per_s": sum(r.N for r in reqs) * SERVE_P * nsteps / wall,
+            "chunk_latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
+                                 "max": float(lat.max() * 1e3), "chunks": int(lat.size)}}
+
+
+def run_serving(args, world, rank):
+    """Requests of Poisson arrivals at 20/s, N log-uniform in [1e3, 1e5] at 0.1 per A^3,
+    P = 100, 100 NPT steps each, chunks of 10 steps: closed-loop capacity and open-loop
+    latency of the FP32-phase server, against FP64 one request at a time on a sample."""
+    import paper_2110_14362_gb300 as rbe
+    reqs = inputs.request_stream(args.serve_requests, 20.0, seed=0)
+    states = [inputs.npt_replica(r.N, r.seed) for r in reqs]
+    steps, chunk = args.serve_steps, 10
+    # warm-up: a few requests through a server (module load, pools, first graph)
+    serve(rbe, reqs[:4], states[:4], rbe.RBE_FP32_PHASE, args.serve_slots, chunk, chunk)
+    closed = serve(rbe, reqs, states, rbe.RBE_FP32_PHASE, args.serve_slots, chunk, steps)
+    wall = max_over_ranks(world, closed["wall_s"])
+    closed["replica_steps_per_s_all_ranks"] = world * closed["replica_steps"] / wall
+    out = {"workload": f"{len(reqs)} NPT replica requests, Poisson 20/s, N log-uniform [1e3, 1e5] at 0.1/A^3, "
+                       f"P={SERVE_P}, {steps} steps, chunk {chunk} steps, FP32-phase",
+           "slots": args.serve_slots, "closed_loop": closed}
+    if not args.skip_open_loop:
+        out["open_loop_20_per_s"] = serve(rbe, reqs, states, rbe.RBE_FP32_PHASE, args.serve_slots, chunk, steps,
+                                          open_loop=True)
+    k = min(args.serve_fp64_sample, len(reqs))
+    if k > 0:
+        fp64 = serve(rbe, reqs[:k], states[:k], rbe.RBE_FP64, 1, chunk, steps, use_graphs=False)
+        same = serve(rbe, reqs[:k], states[:k], rbe.RBE_FP32_PHASE, args.serve_slots, chunk, steps)
+        out["fp64_one_at_a_time"] = dict(fp64, sample=f"first {k} requests")
+        out["fp32_served_same_sample"] = dict(same, sample=f"first {k} requests")
+        out["served_fp32_over_fp64_one_at_a_time"] = same["replica_steps_per_s"] / fp64["replica_steps_per_s"]
+    return out
 
 
 def cpu_baseline(s, budget_s: float = 15.0):
@@ -334,6 +417,12 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--skip-open-loop", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--serve-steps", type=int, default=100)
+    ap.add_argument("--serve-slots", type=int, default=64)
+    ap.add_argument("--serve-fp64-sample", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -229,7 +229,11 @@ typedef struct {
 
 /* Forces, virial trace and energies at the current state, with the RBE batch of index
  * `batch`; fills sys->force and cell[3..10] (p_V is kept).  Call once before the first step.
- * Asynchronous on the context's stream.  RBE_EINVAL for bad pointers or parameters. */
+ * Reads the initial box back (synchronises the context's stream) and sizes the per-axis
+ * tables and the cell list for box edges up to twice the initial ones; a step whose box
+ * leaves that range, or breaks rc <= l/2 with real space on, is flagged on the device and
+ * reported as RBE_ESTATE by the next rbe_sync.  Asynchronous otherwise.  RBE_EINVAL for bad
+ * pointers or parameters. */
 rbe_status rbe_npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch);
 
 /* Advance nsteps >= 1 steps (Sec. 3.3); asynchronous on the context's stream; sys->step
@@ -257,7 +261,8 @@ typedef struct {
     int32_t max_slots;   /* replicas resident at once, 1..4096 */
     int32_t chunk_steps; /* NPT steps per chunk, >= 1 */
     int64_t mem_budget;  /* device bytes the resident replicas may use; a replica of N particles
-                            counts N*176 + (P+1)*32768 + 4 MiB bytes (state, NPT scratch, tables) */
+                            counts N*176 + 12*C + (P+1)*32768 + 4 MiB bytes (state, NPT scratch,
+                            C = prod_t floor(2 l_t / rc) cells, tables) */
     int32_t use_graphs;  /* 1: replay a captured graph per chunk; 0: launch the steps directly */
     int32_t pad;
 } rbe_server_config;

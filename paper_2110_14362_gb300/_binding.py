@@ -9,6 +9,7 @@ is no CPU fallback.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import threading
 
@@ -283,6 +284,13 @@ class NptReplica:
         """(pos, mom, force, box, cell block) as NumPy arrays (synchronises)."""
         c = self.cell.cpu().numpy()
         return (self.pos.cpu().numpy(), self.mom.cpu().numpy(), self.force.cpu().numpy(), c[:3].copy(), c)
+
+
+def piston_mass(tau_P: float, beta_T: float, V0: float) -> float:
+    """Barostat mass giving a harmonic volume oscillation of period tau_P (ps) for an
+    isothermal compressibility beta_T (per kJ/mol/A^3) about V0 (A^3): M = tau_P^2 / (4 pi^2
+    beta_T V0), in the units of the Langevin NPT equations of Sec. 3.2."""
+    return tau_P * tau_P / (4.0 * math.pi * math.pi * beta_T * V0)
 
 
 class Server:

@@ -33,7 +33,8 @@ rbe_status cuda_fail(rbe_ctx ctx, cudaError_t err, const char* what)
 int host_axis_M(double alpha, double ell)
 {
     const double c = (kPi * kPi) / (alpha * (ell * ell));
-    return (int)std::ceil(std::sqrt((60.0 * kLn2) / c));
+    const double M = std::ceil(std::sqrt((60.0 * kLn2) / c));
+    return M <= 1073741824.0 ? (int)M : 1073741824;  // clamped (also NaN) before the conversion
 }
 
 // Makes ctx->device current for the duration of a call and restores the caller's device.
@@ -91,6 +92,9 @@ static rbe_status status_from_bits(rbe_ctx ctx, unsigned bits)
 {
     if (bits & kStatusSample) return fail(ctx, RBE_ESAMPLE, "a frequency stayed m = 0 after 2^20 redraws");
     if (bits & kStatusTable) return fail(ctx, RBE_ESTATE, "sampling table capacity exceeded on the device");
+    if (bits & kStatusBox)
+        return fail(ctx, RBE_ESTATE,
+                    "the box left the range rbe_npt_init prepared (cell list capacity, or rc > l/2 on some axis)");
     if (bits & kStatusTimeout) return fail(ctx, RBE_ETIMEOUT, "a bounded device wait gave up");
     if (bits & kStatusNonFinite) return fail(ctx, RBE_ENONFINITE, "rho(k) or an output is not finite");
     return RBE_OK;

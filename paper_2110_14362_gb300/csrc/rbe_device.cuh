@@ -21,6 +21,7 @@ constexpr unsigned kStatusSample = 1u;     // a sample stayed at m = 0 for kMaxA
 constexpr unsigned kStatusNonFinite = 2u;  // rho or an output is NaN/Inf
 constexpr unsigned kStatusTable = 4u;      // the sampling table did not fit its capacity
 constexpr unsigned kStatusTimeout = 8u;    // a bounded wait gave up
+constexpr unsigned kStatusBox = 16u;       // NPT: the box outgrew the cell list or broke rc <= l/2
 
 // ---------------------------------------------------------------------------------
 // Programmatic dependent launch: a kernel launched with programmatic stream
@@ -82,9 +83,19 @@ __device__ __forceinline__ double axis_c(double alpha, double ell)
 }
 
 // Truncation |m| <= M = ceil(sqrt(60 ln2 / c)): drops weights below 2^-60 of the peak.
-__device__ __forceinline__ int axis_M(double c)
+// M is formed in FP64 and compared with the table's room before any integer conversion,
+// so that no box length (huge, infinite, NaN) can overflow the index arithmetic: beyond
+// the room, or for a box that is not finite and positive, *bad is set and M is clamped.
+__device__ __forceinline__ int axis_M_capped(double ell, double c, int cap, bool* bad)
 {
-    return (int)ceil(__dsqrt_rn(__ddiv_rn(__dmul_rn(60.0, kLn2), c)));
+    const double Md = ceil(__dsqrt_rn(__ddiv_rn(__dmul_rn(60.0, kLn2), c)));
+    const int Mmax = (cap - 1) / 2;
+    if (!(ell > 0.0) || !isfinite(ell) || !(Md <= (double)Mmax)) {
+        *bad = true;
+        return Mmax;
+    }
+    *bad = false;
+    return (int)Md;
 }
 
 // ---------------------------------------------------------------------------------

@@ -56,11 +56,9 @@ k_tables(double bx, double by, double bz, const double* __restrict__ box_dev, do
     if (tid < 3) {
         const double ell = box_dev ? box_dev[tid] : (tid == 0 ? bx : (tid == 1 ? by : bz));
         const double c = axis_c(alpha, ell);
-        int M = axis_M(c);
-        if (2 * M + 1 > cap) {
-            atomicOr(status, kStatusTable);
-            M = (cap - 1) / 2;
-        }
+        bool bad;
+        const int M = axis_M_capped(ell, c, cap, &bad);
+        if (bad) atomicOr(status, kStatusTable);
         sL[tid] = ell;
         sc[tid] = c;
         sM[tid] = M;

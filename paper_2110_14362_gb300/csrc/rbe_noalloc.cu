@@ -55,11 +55,9 @@ k_sample_noalloc(unsigned long long* __restrict__ scratch, double bx, double by,
     if (tid < 3) {
         const double ell = tid == 0 ? bx : (tid == 1 ? by : bz);
         const double c = axis_c(alpha, ell);
-        int M = axis_M(c);  // the host checked 2M + 1 <= kNoAllocTableCap; clamp all the same
-        if (2 * M + 1 > kNoAllocTableCap) {
-            atomicOr(status, kStatusTable);
-            M = (kNoAllocTableCap - 1) / 2;
-        }
+        bool bad;  // the host checked 2M + 1 <= kNoAllocTableCap; clamp all the same
+        const int M = axis_M_capped(ell, c, kNoAllocTableCap, &bad);
+        if (bad) atomicOr(status, kStatusTable);
         sc[tid] = c;
         sM[tid] = M;
         sSh[tid] = 62 - (32 - __clz((unsigned)(2 * M + 1)));

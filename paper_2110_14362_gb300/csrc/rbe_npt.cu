@@ -23,6 +23,9 @@ namespace rbe {
 constexpr double kFConv = 100.0;  // kJ/mol/A per g/mol -> A/ps^2
 constexpr int kNptThreads = 256;
 constexpr int kScanThreads = 1024;
+// rbe_npt_init sizes the per-axis tables and the cell list for box edges up to this many
+// times the initial ones; a box beyond it is flagged (RBE_ESTATE) by the step.
+constexpr double kBoxHeadroom = 2.0;
 
 struct NptCoef {
     double a1, b1;      // R^p/2 before the forces: p <- a1 p + 100 F b1
@@ -188,7 +191,12 @@ k_npt_drift(int64_t N, double* __restrict__ pos, double* __restrict__ mom, const
 // here), cell of a wrapped position s = r / l: floor(s nc).
 __device__ __forceinline__ void cell_dims(const double* cell, double rc, int nc[3])
 {
-    for (int t = 0; t < 3; ++t) nc[t] = max(1, (int)floor(cell[t] / rc));
+    // clamped in FP64 before the conversion: any box (huge, infinite, NaN) gives 1..2^20
+    // cells per axis, whose product cannot overflow and is checked against the capacity
+    for (int t = 0; t < 3; ++t) {
+        const double f = floor(cell[t] / rc);
+        nc[t] = f >= 1.0 ? (f <= 1048576.0 ? (int)f : 1048576) : 1;
+    }
 }
 
 __device__ __forceinline__ int cell_of(const double r[3], const double* L, const int nc[3])
@@ -209,10 +217,12 @@ __global__ void k_cl_count(int64_t N, const double* __restrict__ pos, const doub
     int nc[3];
     cell_dims(cell, rc, nc);
     if ((int64_t)nc[0] * nc[1] * nc[2] > cellcap) {
-        atomicOr(status, kStatusTable);
+        atomicOr(status, kStatusBox);
         cid[i] = 0;
         return;
     }
+    // nearest image needs rc <= l/2 (NaN fails too)
+    if (i == 0 && !(2.0 * rc <= cell[0] && 2.0 * rc <= cell[1] && 2.0 * rc <= cell[2])) atomicOr(status, kStatusBox);
     const double r[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
     const int c = cell_of(r, cell, nc);
     cid[i] = c;
@@ -480,7 +490,7 @@ static rbe_status npt_check(rbe_ctx ctx, const char* what)
     return e == cudaSuccess ? RBE_OK : npt_fail(ctx, e, what);
 }
 
-// Grow the NPT scratch for N particles and a box that may grow by 30 %.
+// Grow the NPT scratch for N particles and a box whose edges may double.
 static rbe_status npt_ensure(rbe_ctx ctx, int64_t N, const double box[3], double rc)
 {
     NptBuffers& b = ctx->npt;
@@ -504,7 +514,11 @@ static rbe_status npt_ensure(rbe_ctx ctx, int64_t N, const double box[3], double
         b.ncap = N;
     }
     int64_t cells = 1;
-    for (int t = 0; t < 3; ++t) cells *= std::max<int64_t>(1, (int64_t)std::floor(1.3 * box[t] / rc));
+    for (int t = 0; t < 3; ++t) {
+        const double f = std::floor(kBoxHeadroom * box[t] / rc);
+        if (!(f <= 4096.0)) return fail(ctx, RBE_EINVAL, "box / rc too large for the cell list (> 2048 cells per axis)");
+        cells *= std::max<int64_t>(1, (int64_t)f);
+    }
     if (cells > b.cellcap) {
         ctx_free(ctx, b.cnt); ctx_free(ctx, b.start); ctx_free(ctx, b.cursor);
         b.cnt = b.start = b.cursor = nullptr;
@@ -613,9 +627,13 @@ rbe_status npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch)
     double box[3];
     if ((st = npt_box_check(ctx, sys, box)) != RBE_OK) return st;
     if ((st = npt_ensure(ctx, sys->N, box, sys->params.rc)) != RBE_OK) return st;
-    // tables for boxes up to 30 % longer than the initial one
+    // tables for boxes up to twice as long as the initial one
     int need = 0;
-    for (int t = 0; t < 3; ++t) need = std::max(need, 2 * host_axis_M(ctx->alpha, 1.3 * box[t]) + 1);
+    for (int t = 0; t < 3; ++t) {
+        const int M = host_axis_M(ctx->alpha, kBoxHeadroom * box[t]);
+        if (M > (1 << 20)) return fail(ctx, RBE_EINVAL, "alpha l^2 too large for the per-axis tables");
+        need = std::max(need, 2 * M + 1);
+    }
     if ((st = ensure_table_capacity(ctx, need)) != RBE_OK) return st;
     ctx->npt_ready_N = sys->N;
     k_npt_set_step<<<1, 32, 0, ctx->stream>>>(sys->cell, batch);

@@ -84,11 +84,16 @@ static rbe_status sfail(rbe_server_s* s, rbe_status st, const std::string& msg)
 
 // Device bytes a replica of N particles holds while resident: its state (r, p, F: 72 B;
 // q, m: 16 B), the context's NPT scratch (k-space and real-space forces 48 B, cell list
-// 8 B + 32 B packed positions) and a fixed allowance for tables, frequency buffers and
-// partial sums.
-static int64_t replica_bytes(int64_t N, int P)
+// 8 B + 32 B packed positions), the cell arrays (12 B per cell for edges up to twice the
+// initial box) and a fixed allowance for tables, frequency buffers and partial sums.
+static int64_t replica_bytes(const rbe_request& r, int P)
 {
-    return N * (72 + 16 + 48 + 8 + 32) + (int64_t)(P + 1) * 16 * 2048 + (4 << 20);
+    int64_t cells = 1;
+    for (int t = 0; t < 3; ++t) {
+        const double f = std::floor(2.0 * r.box[t] / r.params.rc);
+        cells *= f >= 1.0 ? (f <= 4096.0 ? (int64_t)f : 4096) : 1;
+    }
+    return r.N * (72 + 16 + 48 + 8 + 32) + 12 * cells + (int64_t)(P + 1) * 16 * 2048 + (4 << 20);
 }
 
 static void release_slot(rbe_server_s* s, Slot& sl)
@@ -188,7 +193,7 @@ static rbe_status admit(rbe_server_s* s, Slot& sl, int64_t id)
     sl.req = id;
     sl.steps_left = rq.r.nsteps;
     sl.in_flight = false;
-    sl.bytes = replica_bytes(N, s->cfg.P);
+    sl.bytes = replica_bytes(rq.r, s->cfg.P);
     s->mem_used += sl.bytes;
     rq.state = 1;
     rq.t_admit = now_s(s);
@@ -293,7 +298,7 @@ rbe_status rbe_server_submit(rbe_server s, const rbe_request* req, int64_t* id)
         return sfail(s, RBE_EINVAL, "invalid request");
     for (int t = 0; t < 3; ++t)
         if (!(req->box[t] > 0.0)) return sfail(s, RBE_EINVAL, "box lengths must be > 0");
-    if (replica_bytes(N, s->cfg.P) > s->cfg.mem_budget)
+    if (replica_bytes(*req, s->cfg.P) > s->cfg.mem_budget)
         return sfail(s, RBE_ENOMEM, "request larger than the whole memory budget");
     auto rq = std::make_unique<Request>();
     rq->r = *req;
@@ -336,7 +341,7 @@ rbe_status rbe_server_progress(rbe_server s, int32_t wait, int32_t* n_queued, in
         // 2. admit while a slot is free and the budget allows (first come, first served)
         while (!s->queue.empty()) {
             const int64_t id = s->queue.front();
-            const int64_t need = replica_bytes(s->reqs[id]->r.N, s->cfg.P);
+            const int64_t need = replica_bytes(s->reqs[id]->r, s->cfg.P);
             if (s->mem_used + need > s->cfg.mem_budget) break;
             Slot* free_slot = nullptr;
             for (Slot& sl : s->slots)

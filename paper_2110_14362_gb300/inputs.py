@@ -153,6 +153,33 @@ class Request:
     seed: int
 
 
+K_B_KJ_MOL_K = 0.00831446261815324  # Boltzmann constant, kJ/mol/K
+
+
+def npt_replica(N: int, seed: int, density: float = 0.1, T: float = 300.0, mass: float = 20.0,
+                jitter: float = 0.1):
+    """Initial state of one NPT replica: N +-1 charges at `density` per A^3 in a cube, on the
+    sites of a jittered cubic lattice (the smallest n^3 >= N grid of spacing a = L/n; N sites
+    drawn without replacement; each displaced uniformly by up to +-jitter*a per axis), so
+    that no two particles overlap; +1 on the first half of the drawn sites, -1 on the rest;
+    masses `mass` g/mol and Maxwell-Boltzmann momenta at T (units g/mol A/ps, so that
+    p^2/m/100 is in kJ/mol).  Returns pos, mom, q, m, box."""
+    L = (N / density) ** (1.0 / 3.0)
+    box = np.array([L, L, L])
+    n = int(math.ceil(N ** (1.0 / 3.0) - 1e-9))
+    a = L / n
+    rng = np.random.default_rng(seed)
+    grid = np.stack(np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij"), -1).reshape(-1, 3)
+    sites = grid[rng.permutation(n ** 3)[:N]].astype(np.float64)
+    pos = np.mod((sites + 0.5 + rng.uniform(-jitter, jitter, (N, 3))) * a, L)
+    q = np.where(np.arange(N) < N // 2, 1.0, -1.0)
+    if N % 2:
+        q[-1] = 0.0
+    m = np.full(N, float(mass))
+    mom = rng.standard_normal((N, 3)) * np.sqrt(K_B_KJ_MOL_K * T * 100.0 * m)[:, None]
+    return pos, mom, q, m, box
+
+
 def request_stream(n_req: int = 256, rate_per_s: float = 20.0, seed: int = 0,
                    n_lo: float = 1e3, n_hi: float = 1e5) -> list[Request]:
     """Poisson arrivals (exponential gaps) and per-request N = 2 floor(exp(U(ln lo, ln hi))/2)."""

@@ -115,3 +115,28 @@ def test_npt_energy_conservation_device():
             H.append(0.5 * c[5] + c[8] + c[9] + prm_d.P_ext * V + c[3] ** 2 / (2 * prm_d.M_V))
     H = np.array(H)
     assert np.abs(H - H[0]).max() < 1e-5
+
+
+@pytest.mark.parametrize("scale", [2.5, 0.7, float("inf"), float("nan")])
+def test_npt_box_out_of_range_is_reported(scale):
+    """A device box beyond the range rbe_npt_init prepared (edges above twice the initial
+    ones, rc > l/2, or not finite) is flagged by the step and reported as an error status by
+    the next synchronisation; the context stays usable."""
+    pos, mom, q, m, box = _system(6)  # l = 12.9, rc = 6
+    prm_d, _ = _params(box, 6.0)
+    dev = cuda_device()
+    with rbe.Context(box, ALPHA, P, SEED, rbe.RBE_FP32_PHASE) as ctx:
+        rep = rbe.NptReplica(pos, mom, q, m, box, prm_d, dev)
+        rep.init(ctx, batch=0)
+        ctx.sync()
+        rep.cell[:3] = float(box[0]) * scale
+        rep.step(ctx, 1)
+        with pytest.raises(rbe.RBEError) as e:
+            ctx.sync()
+        assert e.value.status in (rbe.RBE_ESTATE, rbe.RBE_ENONFINITE)
+        # the context still works on a sane box
+        rep2 = rbe.NptReplica(pos, mom, q, m, box, prm_d, dev)
+        rep2.init(ctx, batch=0)
+        rep2.step(ctx, 2)
+        ctx.sync()
+        assert np.isfinite(rep2.cell.cpu().numpy()[:11]).all()
