@@ -261,7 +261,7 @@ typedef struct {
     int32_t max_slots;   /* replicas resident at once, 1..4096 */
     int32_t chunk_steps; /* NPT steps per chunk, >= 1 */
     int64_t mem_budget;  /* device bytes the resident replicas may use; a replica of N particles
-                            counts N*176 + 12*C + (P+1)*32768 + 4 MiB bytes (state, NPT scratch,
+                            counts N*196 + 12*C + (P+1)*32768 + 4 MiB bytes (state, NPT scratch,
                             C = prod_t floor(2 l_t / rc) cells, tables) */
     int32_t use_graphs;  /* 1: replay a captured graph per chunk; 0: launch the steps directly */
     int32_t pad;

@@ -56,14 +56,17 @@ struct NptBuffers {
     double* WEk = nullptr;         // 11: k-space virial (9) + energy (2)
     double* coef = nullptr;        // per-step coefficients (NptCoef)
     int* cid = nullptr;            // N cell index per particle
-    int* sorted = nullptr;         // N particle indices grouped by cell
-    void* spos = nullptr;          // N packed positions+charge in cell order (float4 or double4)
+    int* fill = nullptr;           // N particle indices grouped by cell (atomic fill order)
+    int* sorted = nullptr;         // N particle indices grouped by cell, by index within a cell
+    float4* spos32 = nullptr;      // N packed FP32 positions+charge in sorted order
+    double4_32a* spos64 = nullptr; // N packed FP64 positions+charge (FP64 path)
     int* cnt = nullptr;            // cells: counts
     int* start = nullptr;          // cells: exclusive prefix sums
     int* cursor = nullptr;         // cells: fill cursors
     double* partials = nullptr;    // per-block partial sums (K2, W_r, E_coul, E_lj)
     unsigned* counter = nullptr;   // last-block counter of the finishing kernel
     int64_t ncap = 0;
+    int64_t n64 = 0;
     int cellcap = 0;
     int partcap = 0;
 };

@@ -6,12 +6,14 @@
 //   k_npt_drift    particles: R^p/2, R/2, O, R/2, wrap into the new box
 //   k-space        tables for the new box, sampler, rho, reduction, force pass
 //   cell list      count, scan, fill, per-cell sort (deterministic order), packed positions
-//   k_pair_*       real-space forces, virial trace and energies (one thread per particle)
+//   k_pair         real-space forces, virial trace and energies (one warp per particle)
 //   k_npt_finish   F = qqr2e F_k + F_r, R^p/2, kinetic sum; last block: P_ins and V^p/2
 // Nothing leaves the device between steps; the step index drives the RBE batch and noise.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
+#include <type_traits>
 #include <cmath>
 #include <string>
 
@@ -23,6 +25,11 @@ namespace rbe {
 constexpr double kFConv = 100.0;  // kJ/mol/A per g/mol -> A/ps^2
 constexpr int kNptThreads = 256;
 constexpr int kScanThreads = 1024;
+constexpr int kSortWarps = 8;        // k_cl_sort: warps (cells) per block
+constexpr int kPairWarps = 8;        // k_pair: warps (particles in flight) per block
+constexpr int kPairBlocksPerSM = 4;  // k_pair (FP32): resident blocks per SM the grid is sized for
+constexpr int kPairBlocksPerSM64 = 2;  // k_pair (FP64): more registers per thread
+constexpr int kHitCap = 64;          // k_pair: buffered candidates per warp (< 32 + 32)
 // rbe_npt_init sizes the per-axis tables and the cell list for box edges up to this many
 // times the initial ones; a box beyond it is flagged (RBE_ESTATE) by the step.
 constexpr double kBoxHeadroom = 2.0;
@@ -269,133 +276,260 @@ k_cl_scan(const double* __restrict__ cell, double rc, int cellcap, const int* __
     }
 }
 
-__global__ void k_cl_fill(int64_t N, const int* __restrict__ cid, int* __restrict__ cursor, int* __restrict__ sorted)
+__global__ void k_cl_fill(int64_t N, const int* __restrict__ cid, int* __restrict__ cursor, int* __restrict__ fill)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int slot = atomicAdd(&cursor[cid[i]], 1);
-    sorted[slot] = (int)i;
+    fill[slot] = (int)i;
 }
 
-// Per cell: sort the members by particle index (a fixed order for every run), then pack
-// their positions and charges (FP32 or FP64) in that order.
-template <typename T4>
-__global__ void k_cl_sort(const double* __restrict__ cell, double rc, int cellcap, const int* __restrict__ cnt,
-                          const int* __restrict__ start, int* __restrict__ sorted, const double* __restrict__ pos,
-                          const double* __restrict__ q, T4* __restrict__ spos)
+// Per cell, one warp: order the members by particle index (a fixed order for every run,
+// whatever order the fill's atomics gave): the member with index i goes to rank = number of
+// members with a smaller index.  Then pack positions and charges in that order: FP32 xyzq
+// always (the pair search runs on it), FP64 as well when spos64 is given.
+__global__ void __launch_bounds__(kSortWarps * 32)
+k_cl_sort(const double* __restrict__ cell, double rc, int cellcap, const int* __restrict__ cnt,
+          const int* __restrict__ start, const int* __restrict__ fill, int* __restrict__ sorted,
+          const double* __restrict__ pos, const double* __restrict__ q, float4* __restrict__ spos32,
+          double4_32a* __restrict__ spos64)
 {
     int nc[3];
     cell_dims(cell, rc, nc);
-    const int n = (int)min((int64_t)cellcap, (int64_t)nc[0] * nc[1] * nc[2]);
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
+    const int64_t ncell = min((int64_t)cellcap, (int64_t)nc[0] * nc[1] * nc[2]);
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= ncell) return;  // c is the same for the whole warp
     const int s0 = start[c], k = cnt[c];
-    int* a = sorted + s0;
-    for (int x = 1; x < k; ++x) {
-        const int v = a[x];
-        int y = x - 1;
-        while (y >= 0 && a[y] > v) {
-            a[y + 1] = a[y];
-            --y;
+    for (int a0 = 0; a0 < k; a0 += 32) {
+        const int a = a0 + lane;
+        const int ia = a < k ? fill[s0 + a] : INT_MAX;
+        int rank = 0;
+        for (int b0 = 0; b0 < k; b0 += 32) {
+            const int b = b0 + lane;
+            const int ib = b < k ? fill[s0 + b] : INT_MAX;
+#pragma unroll 8
+            for (int t = 0; t < 32; ++t) rank += __shfl_sync(0xffffffffu, ib, t) < ia ? 1 : 0;
         }
-        a[y + 1] = v;
-    }
-    for (int x = 0; x < k; ++x) {
-        const int i = a[x];
-        T4 v;
-        v.x = pos[3 * i];
-        v.y = pos[3 * i + 1];
-        v.z = pos[3 * i + 2];
-        v.w = q[i];
-        spos[s0 + x] = v;
+        if (a < k) {
+            const double x = pos[3 * (int64_t)ia], y = pos[3 * (int64_t)ia + 1], z = pos[3 * (int64_t)ia + 2];
+            const double qq = q[ia];
+            sorted[s0 + rank] = ia;
+            spos32[s0 + rank] = make_float4((float)x, (float)y, (float)z, (float)qq);
+            if (spos64) {
+                double4_32a v;
+                v.x = x;
+                v.y = y;
+                v.z = z;
+                v.w = qq;
+                spos64[s0 + rank] = v;
+            }
+        }
     }
 }
 
 // ---------------------------------------------------------------------------------
-// Real-space forces (Sec. 4.1 Eqs. (U2), (force)): one thread per particle i loops over the
-// neighbour cells (27 when every axis has >= 3 cells of size >= rc) and their members in a
-// fixed order; nearest image within rc <= l/2;
-// f = -(dU/dr)/r for U = qqr2e q_i q_j erfc(sqrt(a) r)/r + 4 eps ((s/r)^12 - (s/r)^6).
-// Each pair is visited from both ends: energies and the virial trace take half.
-// Per-block partials: {W_r, E_coul, E_lj}.
-template <typename R, typename T4>
-__global__ void __launch_bounds__(kNptThreads)
-k_pair(int64_t N, const double* __restrict__ pos, const double* __restrict__ q, const double* __restrict__ cell,
-       int cellcap, double rc, double alpha, double qqr2e, double lj_sigma, double lj_eps, const int* __restrict__ cid,
-       const int* __restrict__ cnt, const int* __restrict__ start, const int* __restrict__ sorted,
-       const T4* __restrict__ spos, double* __restrict__ Fr, double* __restrict__ partials)
+// Real-space forces (Sec. 4.1 Eqs. (U2), (force)) on the cell list: one warp per particle
+// i, taken in cell order (slot u of the sorted array), so that neighbouring warps search
+// the same cells.  For each of the 3 x 3 rows (dy, dz) of neighbour cells the cells
+// cx-1..cx+1 are contiguous slots (split in two where the row wraps); the lanes stride over
+// them.  With 3 or more cells on an axis the periodic image of a neighbour cell is fixed
+// (shift -l, 0 or +l where the row or column wraps); with fewer, each pair takes the nearest
+// image.  Every distinct cell is visited once, and rc <= l/2 makes the image within rc the
+// nearest one.
+//   Search: FP32 positions; a candidate within the cutoff (FP64 path: within rc plus a
+//   margin above the FP32 rounding of the distance) is appended to the warp's buffer in
+//   shared memory (ballot order, so the order is fixed).
+//   Evaluation: every 32 buffered candidates, one per lane; the FP64 path recomputes the
+//   distance from the FP64 positions and applies the exact cutoff.
+//   f = -(dU/dr)/r for U = qqr2e q_i q_j erfc(sqrt(a) r)/r + 4 eps ((s/r)^12 - (s/r)^6); the
+//   lane sums go through a fixed shuffle tree, so the result does not depend on timing.
+// Each pair is visited from both ends: energies and the virial trace take half.  The warps
+// stride over the slots (grid-stride); per-block partials {W_r, E_coul, E_lj}.  A box that
+// outgrew the cell arrays (flagged by k_cl_count) leaves F_r = 0.
+template <bool kF64>
+__global__ void __launch_bounds__(kPairWarps * 32, kF64 ? kPairBlocksPerSM64 : kPairBlocksPerSM)
+k_pair(int64_t N, const double* __restrict__ cell, int cellcap, double rc, double alpha, double qqr2e,
+       double lj_sigma, double lj_eps, const int* __restrict__ cid, const int* __restrict__ cnt,
+       const int* __restrict__ start, const int* __restrict__ sorted, const float4* __restrict__ spos32,
+       const double4_32a* __restrict__ spos64, double* __restrict__ Fr, double* __restrict__ partials)
 {
-    __shared__ double red[3][kNptThreads / 32];
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const R L[3] = {(R)cell[0], (R)cell[1], (R)cell[2]};
+    using R = typename std::conditional<kF64, double, float>::type;
+    using Hit = typename std::conditional<kF64, int2, float4>::type;  // FP64: (slot, image code)
+    __shared__ Hit hits[kPairWarps][kHitCap];
+    __shared__ double red[3][kPairWarps];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const double L[3] = {cell[0], cell[1], cell[2]};
     int nc[3];
     cell_dims(cell, rc, nc);
-    const R rc2 = (R)(rc * rc), sa = (R)sqrt(alpha), two_sa_pi = (R)(2.0 * sqrt(alpha / 3.14159265358979323846));
-    const R qk = (R)qqr2e, s2 = (R)(lj_sigma * lj_sigma), e4 = (R)(4.0 * lj_eps), e24 = (R)(24.0 * lj_eps);
-    R fx = 0, fy = 0, fz = 0, w = 0, ec = 0, el = 0;
-    // a box that outgrew the cell arrays was flagged by k_cl_count: no neighbour search then
+    double wsum = 0.0, ecsum = 0.0, elsum = 0.0;  // this warp's particles (lane 0)
     const bool cells_ok = (int64_t)nc[0] * nc[1] * nc[2] <= (int64_t)cellcap;
-    if (i < N && cells_ok) {
-        const R xi = (R)pos[3 * i], yi = (R)pos[3 * i + 1], zi = (R)pos[3 * i + 2], qi = (R)q[i];
-        const int c = cid[i];
-        const int cx = c % nc[0], cy = (c / nc[0]) % nc[1], cz = c / (nc[0] * nc[1]);
-        // neighbour offsets per axis: {-1, 0, 1} with 3 or more cells, {0, 1} with 2, {0} with 1,
-        // so that every distinct cell is visited once
-        const int lo0 = nc[0] >= 3 ? -1 : 0, hi0 = nc[0] >= 2 ? 1 : 0;
+    if (!cells_ok) {
+        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < 3 * N; j += (int64_t)gridDim.x * blockDim.x)
+            Fr[j] = 0.0;
+    } else {
+        const float Lf[3] = {(float)L[0], (float)L[1], (float)L[2]};
+        const float invLf[3] = {(float)(1.0 / L[0]), (float)(1.0 / L[1]), (float)(1.0 / L[2])};
+        const double invL[3] = {1.0 / L[0], 1.0 / L[1], 1.0 / L[2]};
+        const bool mi[3] = {nc[0] < 3, nc[1] < 3, nc[2] < 3};
+        const double Lmax = fmax(L[0], fmax(L[1], L[2]));
+        const float rc2_pass = kF64 ? (float)((rc + Lmax * 0x1.0p-16) * (rc + Lmax * 0x1.0p-16)) : (float)(rc * rc);
+        const R rc2 = (R)(rc * rc), sa = (R)sqrt(alpha), aR = (R)alpha;
+        const R two_sa_pi = (R)(2.0 * sqrt(alpha / 3.14159265358979323846));
+        const R qk = (R)qqr2e, s2 = (R)(lj_sigma * lj_sigma), e4 = (R)(4.0 * lj_eps), e24 = (R)(24.0 * lj_eps);
+        const bool lj = lj_eps != 0.0;
         const int lo1 = nc[1] >= 3 ? -1 : 0, hi1 = nc[1] >= 2 ? 1 : 0;
         const int lo2 = nc[2] >= 3 ? -1 : 0, hi2 = nc[2] >= 2 ? 1 : 0;
-        for (int dz = lo2; dz <= hi2; ++dz)
-            for (int dy = lo1; dy <= hi1; ++dy)
-                for (int dx = lo0; dx <= hi0; ++dx) {
-                    const int nx = (cx + dx + nc[0]) % nc[0], ny = (cy + dy + nc[1]) % nc[1], nz = (cz + dz + nc[2]) % nc[2];
-                    const int cc = (nz * nc[1] + ny) * nc[0] + nx;
-                    const int s0 = start[cc], s1 = s0 + cnt[cc];
-                    for (int s = s0; s < s1; ++s) {
-                        if (sorted[s] == (int)i) continue;
-                        const T4 o = spos[s];
-                        R ddx = (R)o.x - xi, ddy = (R)o.y - yi, ddz = (R)o.z - zi;
-                        ddx -= L[0] * rint(ddx / L[0]);
-                        ddy -= L[1] * rint(ddy / L[1]);
-                        ddz -= L[2] * rint(ddz / L[2]);
-                        const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                        if (!(r2 < rc2)) continue;
-                        const R r = sqrt(r2);
-                        const R qq = qk * qi * (R)o.w;
-                        const R er = erfc(sa * r);
-                        R f = qq * (er / r2 + two_sa_pi * exp(-(R)alpha * r2) / r) / r;
-                        ec += qq * er / r;
-                        if (lj_eps != 0.0) {
-                            const R sr2 = s2 / r2;
-                            const R sr6 = sr2 * sr2 * sr2;
-                            el += e4 * (sr6 * sr6 - sr6);
-                            f += e24 * (2 * sr6 * sr6 - sr6) / r2;
-                        }
-                        // force on i is -f d (d points from i to the neighbour)
-                        fx -= f * ddx;
-                        fy -= f * ddy;
-                        fz -= f * ddz;
-                        w += f * r2;
+        const int64_t nwarps = (int64_t)gridDim.x * kPairWarps;
+        for (int64_t u = (int64_t)blockIdx.x * kPairWarps + wib; u < N; u += nwarps) {
+            const int i = sorted[u];
+            const float4 me = spos32[u];
+            R xi, yi, zi, qi;
+            if constexpr (kF64) {
+                const double4_32a m64 = spos64[u];
+                xi = m64.x;
+                yi = m64.y;
+                zi = m64.z;
+                qi = m64.w;
+            } else {
+                xi = me.x;
+                yi = me.y;
+                zi = me.z;
+                qi = me.w;
+            }
+            const int c = cid[i];
+            const int cx = c % nc[0], cy = (c / nc[0]) % nc[1], cz = c / (nc[0] * nc[1]);
+            R fx = 0, fy = 0, fz = 0, w = 0, ec = 0, el = 0;
+            int nh = 0;
+            // one buffered candidate per lane (lanes >= count idle)
+            auto evaluate = [&](int count) {
+                if (lane >= count) return;
+                const Hit h = hits[wib][lane];
+                R dx, dy, dz, qj;
+                if constexpr (kF64) {
+                    const double4_32a o = spos64[h.x];
+                    const int code = h.y;
+                    dx = (o.x - xi) + (double)((code & 3) - 1) * L[0];
+                    dy = (o.y - yi) + (double)(((code >> 2) & 3) - 1) * L[1];
+                    dz = (o.z - zi) + (double)(((code >> 4) & 3) - 1) * L[2];
+                    if (mi[0]) dx -= L[0] * rint(dx * invL[0]);
+                    if (mi[1]) dy -= L[1] * rint(dy * invL[1]);
+                    if (mi[2]) dz -= L[2] * rint(dz * invL[2]);
+                    qj = o.w;
+                } else {
+                    dx = h.x;
+                    dy = h.y;
+                    dz = h.z;
+                    qj = h.w;
+                }
+                const R r2 = dx * dx + dy * dy + dz * dz;
+                if (!(r2 < rc2)) return;
+                const R r = sqrt(r2);
+                const R qq = qk * qi * qj;
+                const R er = erfc(sa * r);
+                R f = qq * (er / r2 + two_sa_pi * exp(-aR * r2) / r) / r;
+                ec += qq * er / r;
+                if (lj) {
+                    const R sr2 = s2 / r2;
+                    const R sr6 = sr2 * sr2 * sr2;
+                    el += e4 * (sr6 * sr6 - sr6);
+                    f += e24 * (2 * sr6 * sr6 - sr6) / r2;
+                }
+                // force on i is -f d (d points from i to the neighbour)
+                fx -= f * dx;
+                fy -= f * dy;
+                fz -= f * dz;
+                w += f * r2;
+            };
+            // lanes stride over slots [lo, hi) of one image (sx, sy, sz in {-1, 0, 1})
+            auto search = [&](int lo, int hi, int sx, int sy, int sz) {
+                const float shx = (float)sx * Lf[0], shy = (float)sy * Lf[1], shz = (float)sz * Lf[2];
+                const int code = (sx + 1) | ((sy + 1) << 2) | ((sz + 1) << 4);
+                for (int s0 = lo; s0 < hi; s0 += 32) {
+                    const int s = s0 + lane;
+                    bool hit = false;
+                    float dx = 0.f, dy = 0.f, dz = 0.f, qj = 0.f;
+                    if (s < hi && (int64_t)s != u) {
+                        const float4 o = spos32[s];
+                        dx = (o.x - me.x) + shx;
+                        dy = (o.y - me.y) + shy;
+                        dz = (o.z - me.z) + shz;
+                        if (mi[0]) dx -= Lf[0] * rintf(dx * invLf[0]);
+                        if (mi[1]) dy -= Lf[1] * rintf(dy * invLf[1]);
+                        if (mi[2]) dz -= Lf[2] * rintf(dz * invLf[2]);
+                        qj = o.w;
+                        hit = dx * dx + dy * dy + dz * dz < rc2_pass;
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, hit);
+                    if (hit) {
+                        const int p = nh + __popc(m & ((1u << lane) - 1u));
+                        if constexpr (kF64) hits[wib][p] = make_int2(s, code);
+                        else hits[wib][p] = make_float4(dx, dy, dz, qj);
+                    }
+                    nh += __popc(m);
+                    if (nh >= 32) {
+                        __syncwarp();
+                        evaluate(32);
+                        __syncwarp();
+                        if (lane < nh - 32) hits[wib][lane] = hits[wib][32 + lane];
+                        __syncwarp();
+                        nh -= 32;
                     }
                 }
-    }
-    if (i < N) {
-        Fr[3 * i] = (double)fx;
-        Fr[3 * i + 1] = (double)fy;
-        Fr[3 * i + 2] = (double)fz;
-    }
-    // fixed-order block sums of the halves
-    double v[3] = {0.5 * (double)w, 0.5 * (double)ec, 0.5 * (double)el};
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int a = 0; a < 3; ++a) {
+            };
+            for (int dz = lo2; dz <= hi2; ++dz)
+                for (int dy = lo1; dy <= hi1; ++dy) {
+                    const int uy = cy + dy, uz = cz + dz;
+                    const int yy = (uy + nc[1]) % nc[1], zz = (uz + nc[2]) % nc[2];
+                    const int sy = mi[1] ? 0 : (uy < 0 ? -1 : (uy >= nc[1] ? 1 : 0));
+                    const int sz = mi[2] ? 0 : (uz < 0 ? -1 : (uz >= nc[2] ? 1 : 0));
+                    const int row = (zz * nc[1] + yy) * nc[0];
+                    const int nx = nc[0];
+                    if (mi[0]) {
+                        search(start[row], start[row + nx - 1] + cnt[row + nx - 1], 0, sy, sz);
+                    } else if (cx == 0) {
+                        search(start[row], start[row + 1] + cnt[row + 1], 0, sy, sz);
+                        search(start[row + nx - 1], start[row + nx - 1] + cnt[row + nx - 1], -1, sy, sz);
+                    } else if (cx == nx - 1) {
+                        search(start[row + nx - 2], start[row + nx - 1] + cnt[row + nx - 1], 0, sy, sz);
+                        search(start[row], start[row] + cnt[row], 1, sy, sz);
+                    } else {
+                        search(start[row + cx - 1], start[row + cx + 1] + cnt[row + cx + 1], 0, sy, sz);
+                    }
+                }
+            __syncwarp();
+            evaluate(nh);
+            __syncwarp();
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v[a] += __shfl_xor_sync(0xffffffffu, v[a], off);
-        if (lane == 0) red[a][warp] = v[a];
+            for (int off = 16; off > 0; off >>= 1) {
+                fx += __shfl_xor_sync(0xffffffffu, fx, off);
+                fy += __shfl_xor_sync(0xffffffffu, fy, off);
+                fz += __shfl_xor_sync(0xffffffffu, fz, off);
+                w += __shfl_xor_sync(0xffffffffu, w, off);
+                ec += __shfl_xor_sync(0xffffffffu, ec, off);
+                el += __shfl_xor_sync(0xffffffffu, el, off);
+            }
+            if (lane == 0) {
+                Fr[3 * (int64_t)i] = (double)fx;
+                Fr[3 * (int64_t)i + 1] = (double)fy;
+                Fr[3 * (int64_t)i + 2] = (double)fz;
+                wsum += 0.5 * (double)w;
+                ecsum += 0.5 * (double)ec;
+                elsum += 0.5 * (double)el;
+            }
+        }
+    }
+    // fixed-order block sums
+    if (lane == 0) {
+        red[0][wib] = wsum;
+        red[1][wib] = ecsum;
+        red[2][wib] = elsum;
     }
     __syncthreads();
     if (threadIdx.x < 3) {
-        double s = 0.0;
-        for (int wv = 0; wv < kNptThreads / 32; ++wv) s += red[threadIdx.x][wv];
-        partials[4 * blockIdx.x + 1 + threadIdx.x] = s;
+        double t = 0.0;
+        for (int wv = 0; wv < kPairWarps; ++wv) t += red[threadIdx.x][wv];
+        partials[4 * (size_t)blockIdx.x + 1 + threadIdx.x] = t;
     }
 }
 
@@ -446,16 +580,31 @@ k_npt_finish(int64_t N, double* __restrict__ mom, double* __restrict__ force, co
         is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
     }
     __syncthreads();
-    if (!is_last || threadIdx.x != 0) return;
+    if (!is_last) return;
     __threadfence();
-    double K2 = 0.0, Wr = 0.0, Ec = 0.0, El = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) K2 += __ldcg(partials + 4 * (size_t)(nblocks_pair + b));
-    if (prm.real)
-        for (int b = 0; b < nblocks_pair; ++b) {
-            Wr += __ldcg(partials + 4 * (size_t)b + 1);
-            Ec += __ldcg(partials + 4 * (size_t)b + 2);
-            El += __ldcg(partials + 4 * (size_t)b + 3);
-        }
+    // the last block: thread t sums the partials t, t + 256, ... and a fixed shared-memory
+    // tree combines the threads, so the sums do not depend on which block came last
+    __shared__ double fin[4][kNptThreads];
+    {
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += kNptThreads)
+            v[0] += __ldcg(partials + 4 * (size_t)(nblocks_pair + b));
+        if (prm.real)
+            for (int b = threadIdx.x; b < nblocks_pair; b += kNptThreads) {
+                v[1] += __ldcg(partials + 4 * (size_t)b + 1);
+                v[2] += __ldcg(partials + 4 * (size_t)b + 2);
+                v[3] += __ldcg(partials + 4 * (size_t)b + 3);
+            }
+        for (int a = 0; a < 4; ++a) fin[a][threadIdx.x] = v[a];
+    }
+    __syncthreads();
+    for (int half = kNptThreads / 2; half > 0; half >>= 1) {
+        if (threadIdx.x < half)
+            for (int a = 0; a < 4; ++a) fin[a][threadIdx.x] += fin[a][threadIdx.x + half];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    const double K2 = fin[0][0], Wr = fin[1][0], Ec = fin[2][0], El = fin[3][0];
     double Wk = 0.0, Ek = 0.0;
     if (prm.kspace) {
         Wk = prm.qqr2e * (__ldcg(WEk + 0) + __ldcg(WEk + 4) + __ldcg(WEk + 8));
@@ -490,6 +639,15 @@ static rbe_status npt_check(rbe_ctx ctx, const char* what)
     return e == cudaSuccess ? RBE_OK : npt_fail(ctx, e, what);
 }
 
+// Blocks of the pair kernel: one warp per particle, at most one resident wave (the warps
+// stride over the rest).  The FP32 count is the larger one and sizes the partials.
+static int pair_blocks(rbe_ctx ctx, int64_t N, bool fp64)
+{
+    const int64_t want = (N + kPairWarps - 1) / kPairWarps;
+    const int per_sm = fp64 ? kPairBlocksPerSM64 : kPairBlocksPerSM;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->num_sms * per_sm));
+}
+
 // Grow the NPT scratch for N particles and a box whose edges may double.
 static rbe_status npt_ensure(rbe_ctx ctx, int64_t N, const double box[3], double rc)
 {
@@ -503,15 +661,27 @@ static rbe_status npt_ensure(rbe_ctx ctx, int64_t N, const double box[3], double
             return npt_fail(ctx, e, "cudaMalloc(npt)");
     }
     if (N > b.ncap) {
-        ctx_free(ctx, b.Fk); ctx_free(ctx, b.Fr); ctx_free(ctx, b.cid); ctx_free(ctx, b.sorted); ctx_free(ctx, b.spos);
-        b.Fk = b.Fr = nullptr; b.cid = b.sorted = nullptr; b.spos = nullptr; b.ncap = 0;
+        ctx_free(ctx, b.Fk); ctx_free(ctx, b.Fr); ctx_free(ctx, b.cid); ctx_free(ctx, b.fill); ctx_free(ctx, b.sorted);
+        ctx_free(ctx, b.spos32); ctx_free(ctx, b.spos64);
+        b.Fk = b.Fr = nullptr; b.cid = b.fill = b.sorted = nullptr; b.spos32 = nullptr; b.spos64 = nullptr; b.ncap = 0;
+        b.n64 = 0;
         if ((e = ctx_alloc(ctx, &b.Fk, 3 * sizeof(double) * N)) != cudaSuccess ||
             (e = ctx_alloc(ctx, &b.Fr, 3 * sizeof(double) * N)) != cudaSuccess ||
             (e = ctx_alloc(ctx, &b.cid, sizeof(int) * N)) != cudaSuccess ||
+            (e = ctx_alloc(ctx, &b.fill, sizeof(int) * N)) != cudaSuccess ||
             (e = ctx_alloc(ctx, &b.sorted, sizeof(int) * N)) != cudaSuccess ||
-            (e = ctx_alloc(ctx, &b.spos, 32 * N)) != cudaSuccess)
+            (e = ctx_alloc(ctx, &b.spos32, sizeof(float4) * N)) != cudaSuccess)
             return npt_fail(ctx, e, "cudaMalloc(npt particles)");
         b.ncap = N;
+    }
+    // FP64 packed positions only for the FP64 path
+    if (ctx->precision == RBE_FP64 && N > b.n64) {
+        ctx_free(ctx, b.spos64);
+        b.spos64 = nullptr;
+        b.n64 = 0;
+        if ((e = ctx_alloc(ctx, &b.spos64, sizeof(double4_32a) * N)) != cudaSuccess)
+            return npt_fail(ctx, e, "cudaMalloc(npt FP64 positions)");
+        b.n64 = N;
     }
     int64_t cells = 1;
     for (int t = 0; t < 3; ++t) {
@@ -529,14 +699,14 @@ static rbe_status npt_ensure(rbe_ctx ctx, int64_t N, const double box[3], double
             return npt_fail(ctx, e, "cudaMalloc(cells)");
         b.cellcap = (int)cells;
     }
-    const int nb = (int)((N + kNptThreads - 1) / kNptThreads);
-    if (2 * nb > b.partcap) {
+    const int need = pair_blocks(ctx, N, false) + (int)((N + kNptThreads - 1) / kNptThreads);
+    if (need > b.partcap) {
         ctx_free(ctx, b.partials);
         b.partials = nullptr;
         b.partcap = 0;
-        if ((e = ctx_alloc(ctx, &b.partials, sizeof(double) * 4 * 2 * (size_t)nb)) != cudaSuccess)
+        if ((e = ctx_alloc(ctx, &b.partials, sizeof(double) * 4 * (size_t)need)) != cudaSuccess)
             return npt_fail(ctx, e, "cudaMalloc(npt partials)");
-        b.partcap = 2 * nb;
+        b.partcap = need;
     }
     return RBE_OK;
 }
@@ -550,6 +720,7 @@ static rbe_status npt_forces(rbe_ctx ctx, rbe_system* sys, uint64_t batch, int d
     cudaStream_t s = ctx->stream;
     const int64_t N = sys->N;
     const int nb = (int)((N + kNptThreads - 1) / kNptThreads);
+    const int nbp = pair_blocks(ctx, N, ctx->precision == RBE_FP64);
     rbe_status st;
     if (prm.kspace) {
         // tables from the device box, then the evaluation
@@ -567,26 +738,25 @@ static rbe_status npt_forces(rbe_ctx ctx, rbe_system* sys, uint64_t batch, int d
         if (e != cudaSuccess) return npt_fail(ctx, e, "cudaMemsetAsync(cells)");
         k_cl_count<<<nb, kNptThreads, 0, s>>>(N, sys->pos, sys->cell, prm.rc, b.cellcap, b.cid, b.cnt, ctx->d.status);
         k_cl_scan<<<1, kScanThreads, 0, s>>>(sys->cell, prm.rc, b.cellcap, b.cnt, b.start, b.cursor);
-        k_cl_fill<<<nb, kNptThreads, 0, s>>>(N, b.cid, b.cursor, b.sorted);
-        const int cb = (b.cellcap + 127) / 128;
+        k_cl_fill<<<nb, kNptThreads, 0, s>>>(N, b.cid, b.cursor, b.fill);
         const bool fp64 = ctx->precision == RBE_FP64;
-        if (fp64) {
-            k_cl_sort<double4_32a><<<cb, 128, 0, s>>>(sys->cell, prm.rc, b.cellcap, b.cnt, b.start, b.sorted, sys->pos,
-                                                      sys->charge, static_cast<double4_32a*>(b.spos));
-            k_pair<double, double4_32a><<<nb, kNptThreads, 0, s>>>(
-                N, sys->pos, sys->charge, sys->cell, b.cellcap, prm.rc, ctx->alpha, prm.qqr2e, prm.lj_sigma, prm.lj_eps,
-                b.cid, b.cnt, b.start, b.sorted, static_cast<const double4_32a*>(b.spos), b.Fr, b.partials);
-        } else {
-            k_cl_sort<float4><<<cb, 128, 0, s>>>(sys->cell, prm.rc, b.cellcap, b.cnt, b.start, b.sorted, sys->pos,
-                                                 sys->charge, static_cast<float4*>(b.spos));
-            k_pair<float, float4><<<nb, kNptThreads, 0, s>>>(
-                N, sys->pos, sys->charge, sys->cell, b.cellcap, prm.rc, ctx->alpha, prm.qqr2e, prm.lj_sigma, prm.lj_eps,
-                b.cid, b.cnt, b.start, b.sorted, static_cast<const float4*>(b.spos), b.Fr, b.partials);
-        }
+        if (fp64 && b.n64 < N) return fail(ctx, RBE_ESTATE, "precision changed to FP64 after rbe_npt_init: call it again");
+        const int64_t sort_blocks = ((int64_t)b.cellcap + kSortWarps - 1) / kSortWarps;
+        k_cl_sort<<<(unsigned)sort_blocks, kSortWarps * 32, 0, s>>>(sys->cell, prm.rc, b.cellcap, b.cnt, b.start, b.fill,
+                                                                  b.sorted, sys->pos, sys->charge, b.spos32,
+                                                                  fp64 ? b.spos64 : nullptr);
+        if (fp64)
+            k_pair<true><<<nbp, kPairWarps * 32, 0, s>>>(N, sys->cell, b.cellcap, prm.rc, ctx->alpha, prm.qqr2e,
+                                                         prm.lj_sigma, prm.lj_eps, b.cid, b.cnt, b.start, b.sorted,
+                                                         b.spos32, b.spos64, b.Fr, b.partials);
+        else
+            k_pair<false><<<nbp, kPairWarps * 32, 0, s>>>(N, sys->cell, b.cellcap, prm.rc, ctx->alpha, prm.qqr2e,
+                                                          prm.lj_sigma, prm.lj_eps, b.cid, b.cnt, b.start, b.sorted,
+                                                          b.spos32, nullptr, b.Fr, b.partials);
         if ((st = npt_check(ctx, "real-space kernels")) != RBE_OK) return st;
     }
     k_npt_finish<<<std::max(1, nb), kNptThreads, 0, s>>>(N, sys->mom, sys->force, sys->mass, b.Fk, b.Fr, b.WEk,
-                                                         reinterpret_cast<const NptCoef*>(b.coef), b.partials, nb,
+                                                         reinterpret_cast<const NptCoef*>(b.coef), b.partials, nbp,
                                                          b.counter, sys->cell, prm, do_kick, ctx->d.status);
     return npt_check(ctx, "k_npt_finish");
 }

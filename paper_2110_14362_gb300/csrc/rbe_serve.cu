@@ -84,7 +84,7 @@ static rbe_status sfail(rbe_server_s* s, rbe_status st, const std::string& msg)
 
 // Device bytes a replica of N particles holds while resident: its state (r, p, F: 72 B;
 // q, m: 16 B), the context's NPT scratch (k-space and real-space forces 48 B, cell list
-// 8 B + 32 B packed positions), the cell arrays (12 B per cell for edges up to twice the
+// 12 B, packed positions 16 B FP32 + 32 B FP64), the cell arrays (12 B per cell for edges up to twice the
 // initial box) and a fixed allowance for tables, frequency buffers and partial sums.
 static int64_t replica_bytes(const rbe_request& r, int P)
 {
@@ -93,7 +93,7 @@ static int64_t replica_bytes(const rbe_request& r, int P)
         const double f = std::floor(2.0 * r.box[t] / r.params.rc);
         cells *= f >= 1.0 ? (f <= 4096.0 ? (int64_t)f : 4096) : 1;
     }
-    return r.N * (72 + 16 + 48 + 8 + 32) + 12 * cells + (int64_t)(P + 1) * 16 * 2048 + (4 << 20);
+    return r.N * (72 + 16 + 48 + 12 + 48) + 12 * cells + (int64_t)(P + 1) * 16 * 2048 + (4 << 20);
 }
 
 static void release_slot(rbe_server_s* s, Slot& sl)

@@ -119,7 +119,7 @@ def test_graphs_equal_direct_launches():
 def test_budget_limits_residency():
     # the budget fits one replica of the largest request, not two
     big = max(r[0] ** 3 for r in REQS)
-    one = big * 176 + (P + 1) * 32768 + (4 << 20)
+    one = big * 196 + (P + 1) * 32768 + (4 << 20)
     tight, peak = _serve(REQS, rbe.RBE_FP32_PHASE, max_slots=4, mem_budget=one + one // 2)
     assert peak == 1
     free, peak_free = _serve(REQS, rbe.RBE_FP32_PHASE, max_slots=4)
