@@ -249,6 +249,7 @@ def run_ours(args, world, rank, local):
     ctx.close()
 
     serving = None if args.skip_serving else run_serving(args, world, rank)
+    npt1 = None if args.skip_serving else run_npt_single(rbe, [1000, 10000, 100000], 20)
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
@@ -274,6 +275,9 @@ def run_ours(args, world, rank, local):
         line["fp64_same_workload"] = other
     if serving:
         line["serving"] = serving
+    if npt1:
+        line["npt_one_replica"] = {"system": "jittered-lattice +-1 charges at 0.1/A^3, P=100, rc=7, Langevin NPT",
+                                   "launch": "direct, one stream", "by_N": npt1}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -326,6 +330,35 @@ def serve(rbe, reqs, states, precision, max_slots, chunk, nsteps, use_graphs=Tru
             "pair_evals_per_s": sum(r.N for r in reqs) * SERVE_P * nsteps / wall,
             "chunk_latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
                                  "max": float(lat.max() * 1e3), "chunks": int(lat.size)}}
+
+
+def npt_single(rbe, N, precision, steps, warmup=3):
+    """ms per NPT step of one replica of N particles (the serving system), launched directly
+    on one stream, timed with CUDA events after `warmup` steps."""
+    import torch
+    pos, mom, q, m, box = inputs.npt_replica(N, 3)
+    prm = serve_params(rbe, box)
+    stream = torch.cuda.current_stream()
+    with rbe.Context(box, SERVE_ALPHA, SERVE_P, 1003, precision, stream=stream.cuda_stream) as ctx:
+        rep = rbe.NptReplica(pos, mom, q, m, box, prm, torch.device("cuda", torch.cuda.current_device()))
+        rep.init(ctx, batch=0)
+        rep.step(ctx, warmup)
+        ctx.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep.step(ctx, steps)
+        e1.record(stream)
+        ctx.sync()
+        return e0.elapsed_time(e1) / steps
+
+
+def run_npt_single(rbe, sizes, steps):
+    out = {}
+    for N in sizes:
+        f32 = npt_single(rbe, N, rbe.RBE_FP32_PHASE, steps)
+        f64 = npt_single(rbe, N, rbe.RBE_FP64, max(2, steps // 4))
+        out[str(N)] = {"fp32_ms_per_step": f32, "fp64_ms_per_step": f64, "fp32_over_fp64": f64 / f32}
+    return out
 
 
 def run_serving(args, world, rank):
@@ -423,10 +456,21 @@ def main():
     ap.add_argument("--serve-steps", type=int, default=100)
     ap.add_argument("--serve-slots", type=int, default=64)
     ap.add_argument("--serve-fp64-sample", type=int, default=16)
+    ap.add_argument("--profile-npt", type=int, default=0, help="time only NPT steps of one replica of this N")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_init()
+    if args.profile_npt:
+        # profiling aid: only the NPT steps of one replica of this many particles
+        import torch
+        import paper_2110_14362_gb300 as rbe
+        torch.cuda.set_device(local)
+        prec = rbe.RBE_FP32_PHASE if args.precision == "fp32" else rbe.RBE_FP64
+        ms = npt_single(rbe, args.profile_npt, prec, args.steps, args.warmup)
+        print(json.dumps({"metric": "NPT steps of one replica", "value": 1e3 / ms, "unit": "replica-steps/s",
+                          "ms_per_step": ms, "N": args.profile_npt, "precision": args.precision}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:

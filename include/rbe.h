@@ -189,7 +189,8 @@ rbe_status rbe_sync(rbe_ctx ctx);
  * pressure in kJ/mol/A^3; p_V in kJ/mol ps/A^3; M in kJ/mol ps^2/A^6.  The box scales
  * isotropically.  Noise: Philox-4x32-10 with the context's seed, counters
  * (i, 0, step_lo, (1 << 24) | step_hi24) for particle i and (0, 0, step_lo, (2 << 24) |
- * step_hi24) for the cell, 32-bit uniforms (w + 1/2) 2^-32 and Box--Muller. */
+ * step_hi24) for the cell, 32-bit uniforms (w + 1/2) 2^-32 and Box--Muller (the particle
+ * normals in FP32 arithmetic on the FP32-phase path, FP64 otherwise). */
 typedef struct {
     double dt;        /* time step, ps */
     double kT;        /* k_B T, kJ/mol */

@@ -117,7 +117,7 @@ static rbe_status sync_and_status(rbe_ctx ctx)
 static void free_npt(NptBuffers& b)
 {
     cudaFree(b.Fk); cudaFree(b.Fr); cudaFree(b.WEk); cudaFree(b.coef); cudaFree(b.cid); cudaFree(b.fill);
-    cudaFree(b.sorted); cudaFree(b.spos32); cudaFree(b.spos64); cudaFree(b.cnt); cudaFree(b.start); cudaFree(b.cursor); cudaFree(b.partials);
+    cudaFree(b.sorted); cudaFree(b.spos32); cudaFree(b.spos64); cudaFree(b.mprop); cudaFree(b.cellc); cudaFree(b.cnt); cudaFree(b.start); cudaFree(b.cursor); cudaFree(b.partials);
     cudaFree(b.counter);
     b = NptBuffers{};
 }

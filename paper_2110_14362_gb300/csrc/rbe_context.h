@@ -60,6 +60,8 @@ struct NptBuffers {
     int* sorted = nullptr;         // N particle indices grouped by cell, by index within a cell
     float4* spos32 = nullptr;      // N packed FP32 positions+charge in sorted order
     double4_32a* spos64 = nullptr; // N packed FP64 positions+charge (FP64 path)
+    double2* mprop = nullptr;      // N (1/m, sqrt(m)), set by rbe_npt_init
+    void* cellc = nullptr;         // cell-list constants of the current box (rbe_npt.cu)
     int* cnt = nullptr;            // cells: counts
     int* start = nullptr;          // cells: exclusive prefix sums
     int* cursor = nullptr;         // cells: fill cursors

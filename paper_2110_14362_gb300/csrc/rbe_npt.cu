@@ -2,7 +2,8 @@
 // forces (rbe_kspace.cu) and a nearest-image real space on a deterministic cell list.
 //
 // One step is a fixed sequence of launches on the context's stream:
-//   k_npt_cell_a   one thread: V^p/2, the sub-step coefficients, V/2, O^p, V/2 (new box)
+//   k_npt_cell_a   one warp: V^p/2, the sub-step coefficients, V/2, O^p, V/2 (new box),
+//                  and the cell-list constants of the new box
 //   k_npt_drift    particles: R^p/2, R/2, O, R/2, wrap into the new box
 //   k-space        tables for the new box, sampler, rho, reduction, force pass
 //   cell list      count, scan, fill, per-cell sort (deterministic order), packed positions
@@ -38,9 +39,11 @@ struct NptCoef {
     double a1, b1;      // R^p/2 before the forces: p <- a1 p + 100 F b1
     double a2m1, b2;    // first R/2: r <- r + r (a2 - 1) + (p/m) b2
     double g, og;       // O: p <- g p + sqrt(og m) z, og = 100 kT (1 - g^2)
+    double sog;         // sqrt(og): the O noise amplitude is sog sqrt(m)
     double a3m1, b3;    // second R/2
     double a4, b4;      // R^p/2 after the forces
     double L[3];        // box after the second V/2
+    double invL[3];     // 1 / L
     double half_cap;    // displacement cap per R/2
     double V;
     int noise;
@@ -86,108 +89,256 @@ __device__ __forceinline__ uint64_t cell_step(const double* cell)
     return (uint64_t)__double_as_longlong(cell[kCellStep]);
 }
 
+// Constants of the cell list for the current box, written once per step (by the cell
+// update, or k_cell_consts before the first forces), so that no kernel of the step divides
+// by the box or by rc itself (FP64 divisions are slow on this GPU).
+struct CellConsts {
+    double L[3], invL[3];
+    float Lf[3], invLf[3];
+    float pass64;  // FP64 path: squared FP32 search radius (rc plus 2^-16 l_max)
+    int nc[3];     // cells per axis, floor(l / rc) clamped to 1..2^20
+    int ncell;     // nc0 nc1 nc2, or -1 when that exceeds the cell arrays
+    int ok;        // ncell >= 0 and rc <= l/2 on every axis
+};
+
+__device__ __forceinline__ int cell_dim(double l, double rc)
+{
+    // clamped in FP64 before the conversion: any box (huge, infinite, NaN) gives 1..2^20
+    // cells per axis, whose product cannot overflow and is checked against the capacity
+    const double f = floor(l / rc);
+    return f >= 1.0 ? (f <= 1048576.0 ? (int)f : 1048576) : 1;
+}
+
+// Lanes 0..2 of one warp: axis `lane` of the box L; then lane 0 the totals.
+__device__ __forceinline__ void write_cell_consts(int lane, const double* L, double rc, int cellcap,
+                                                  CellConsts* __restrict__ cc)
+{
+    if (lane < 3) {
+        const double l = L[lane];
+        cc->L[lane] = l;
+        cc->invL[lane] = 1.0 / l;
+        cc->Lf[lane] = (float)l;
+        cc->invLf[lane] = (float)(1.0 / l);
+        cc->nc[lane] = cell_dim(l, rc);
+    }
+    __syncwarp();
+    if (lane == 0) {
+        const int64_t n = (int64_t)cc->nc[0] * cc->nc[1] * cc->nc[2];
+        cc->ncell = n <= (int64_t)cellcap ? (int)n : -1;
+        cc->ok = cc->ncell >= 0 && 2.0 * rc <= L[0] && 2.0 * rc <= L[1] && 2.0 * rc <= L[2];
+        const double lmax = fmax(L[0], fmax(L[1], L[2]));
+        const double rp = rc + lmax * 0x1.0p-16;
+        cc->pass64 = (float)(rp * rp);
+    }
+}
+
+__global__ void k_cell_consts(const double* __restrict__ cell, double rc, int cellcap, CellConsts* __restrict__ cc)
+{
+    write_cell_consts(threadIdx.x, cell, rc, cellcap, cc);
+}
+
+// 1/m and sqrt(m) per particle, once per rbe_npt_init.
+__global__ void k_mass_props(int64_t N, const double* __restrict__ mass, double2* __restrict__ mprop)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) mprop[i] = make_double2(1.0 / mass[i], sqrt(mass[i]));
+}
+
 __global__ void k_npt_set_step(double* __restrict__ cell, uint64_t step)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) cell[kCellStep] = __longlong_as_double((long long)step);
 }
 
-__global__ void k_npt_cell_a(double* __restrict__ cell, NptCoef* __restrict__ cf, rbe_npt_params prm,
-                             uint64_t seed)
+__global__ void __launch_bounds__(32)
+k_npt_cell_a(double* __restrict__ cell, NptCoef* __restrict__ cf, rbe_npt_params prm, uint64_t seed, int cellcap,
+             CellConsts* __restrict__ cc)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    // One warp.  The chain p_V -> box -> p_V -> box runs on lane 0; the exponentials of the
+    // sub-step coefficients and the cell noise, independent of one another, run on other
+    // lanes (single FP64 chains are slow on this GPU, parallel ones are not).
+    __shared__ double sh[24];
+    const int lane = threadIdx.x;
     const uint64_t step = cell_step(cell);
     const double h = 0.5 * prm.dt;
-    double L[3] = {cell[0], cell[1], cell[2]};
-    double V = L[0] * L[1] * L[2];
-    double pV = prm.barostat ? cell[3] : 0.0;
-    const double W = cell[4], K2 = cell[5];
-    if (prm.barostat) pV += h * ((K2 + W) / (3.0 * V) - prm.P_ext);
-    double eps = prm.barostat ? pV / (3.0 * prm.M_V * V) : 0.0;
-    NptCoef c;
-    c.a1 = exp(-eps * h);
-    c.b1 = expm1_over(-eps * h, h);
-    if (prm.barostat) {
-        const double Vn = V + h * pV / prm.M_V;
-        const double f = cbrt(Vn / V);
-        for (int t = 0; t < 3; ++t) L[t] *= f;
-        V = L[0] * L[1] * L[2];
-    }
-    eps = prm.barostat ? pV / (3.0 * prm.M_V * V) : 0.0;
-    c.a2m1 = exp(eps * h) - 1.0;
-    c.b2 = expm1_over(eps * h, h);
-    if (prm.barostat) {
-        const double g = exp(-prm.gamma_V * prm.dt);
-        pV *= g;
-        if (prm.noise) {
-            double z[4];
-            npt_normals(seed, 2u, step, 0u, z);
-            pV += sqrt(prm.kT * prm.M_V * (1.0 - g * g)) * z[0];
+    const double MV = prm.M_V;
+    if (lane == 0) {
+        double L[3] = {cell[0], cell[1], cell[2]};
+        double V = L[0] * L[1] * L[2];
+        double pV = prm.barostat ? cell[3] : 0.0;
+        const double W = cell[4], K2 = cell[5];
+        if (prm.barostat) pV += h * ((K2 + W) / (3.0 * V) - prm.P_ext);
+        sh[0] = prm.barostat ? pV / (3.0 * MV * V) : 0.0;  // eps for the first R^p/2
+        if (prm.barostat) {
+            const double Vn = V + h * pV / MV;
+            const double f = cbrt(Vn / V);
+            for (int t = 0; t < 3; ++t) L[t] *= f;
+            V = L[0] * L[1] * L[2];
         }
+        sh[1] = prm.barostat ? pV / (3.0 * MV * V) : 0.0;  // eps for the first R/2
+        sh[2] = pV;
+        sh[3] = L[0];
+        sh[4] = L[1];
+        sh[5] = L[2];
+        sh[6] = V;
+    } else if (lane == 1) {
+        // O^p: friction factor and the noise term of the cell
+        double gV = 1.0, nz = 0.0;
+        if (prm.barostat) {
+            gV = exp(-prm.gamma_V * prm.dt);
+            if (prm.noise) {
+                double z[4];
+                npt_normals(seed, 2u, step, 0u, z);
+                nz = sqrt(prm.kT * MV * (1.0 - gV * gV)) * z[0];
+            }
+        }
+        sh[7] = gV;
+        sh[8] = nz;
+    } else if (lane == 2) {
+        const double g = exp(-prm.gamma * prm.dt);
+        const double og = prm.kT * kFConv * (1.0 - g * g);
+        sh[9] = g;
+        sh[10] = og;
+        sh[11] = sqrt(og);
     }
-    c.g = exp(-prm.gamma * prm.dt);
-    c.og = prm.kT * kFConv * (1.0 - c.g * c.g);
-    eps = prm.barostat ? pV / (3.0 * prm.M_V * V) : 0.0;
-    c.a3m1 = exp(eps * h) - 1.0;
-    c.b3 = expm1_over(eps * h, h);
-    if (prm.barostat) {
-        const double Vn = V + h * pV / prm.M_V;
-        const double f = cbrt(Vn / V);
-        for (int t = 0; t < 3; ++t) L[t] *= f;
-        V = L[0] * L[1] * L[2];
+    __syncwarp();
+    if (lane == 0) {
+        double L[3] = {sh[3], sh[4], sh[5]};
+        double V = sh[6], pV = sh[2];
+        if (prm.barostat) {
+            pV *= sh[7];
+            if (prm.noise) pV += sh[8];
+        }
+        sh[12] = prm.barostat ? pV / (3.0 * MV * V) : 0.0;  // eps for the second R/2
+        if (prm.barostat) {
+            const double Vn = V + h * pV / MV;
+            const double f = cbrt(Vn / V);
+            for (int t = 0; t < 3; ++t) L[t] *= f;
+            V = L[0] * L[1] * L[2];
+        }
+        sh[13] = prm.barostat ? pV / (3.0 * MV * V) : 0.0;  // eps for the second R^p/2
+        sh[2] = pV;
+        sh[3] = L[0];
+        sh[4] = L[1];
+        sh[5] = L[2];
+        sh[6] = V;
+    } else if (lane == 1) {
+        sh[14] = exp(-sh[0] * h);
+    } else if (lane == 2) {
+        sh[15] = expm1_over(-sh[0] * h, h);
+    } else if (lane == 3) {
+        sh[16] = exp(sh[1] * h) - 1.0;
+    } else if (lane == 4) {
+        sh[17] = expm1_over(sh[1] * h, h);
     }
-    eps = prm.barostat ? pV / (3.0 * prm.M_V * V) : 0.0;
-    c.a4 = exp(-eps * h);
-    c.b4 = expm1_over(-eps * h, h);
-    for (int t = 0; t < 3; ++t) c.L[t] = L[t];
-    c.half_cap = 0.5 * prm.max_disp;
-    c.V = V;
-    c.noise = prm.noise;
-    c.pad = 0;
-    *cf = c;
-    cell[0] = L[0];
-    cell[1] = L[1];
-    cell[2] = L[2];
-    cell[3] = pV;
-    cell[10] = V;
+    __syncwarp();
+    if (lane == 1) {
+        sh[18] = exp(sh[12] * h) - 1.0;
+    } else if (lane == 2) {
+        sh[19] = expm1_over(sh[12] * h, h);
+    } else if (lane == 3) {
+        sh[20] = exp(-sh[13] * h);
+    } else if (lane == 4) {
+        sh[21] = expm1_over(-sh[13] * h, h);
+    }
+    write_cell_consts(lane, sh + 3, prm.rc, cellcap, cc);  // syncs the warp
+    __syncwarp();
+    if (lane == 0) {
+        NptCoef c;
+        c.a1 = sh[14];
+        c.b1 = sh[15];
+        c.a2m1 = sh[16];
+        c.b2 = sh[17];
+        c.g = sh[9];
+        c.og = sh[10];
+        c.sog = sh[11];
+        c.a3m1 = sh[18];
+        c.b3 = sh[19];
+        c.a4 = sh[20];
+        c.b4 = sh[21];
+        for (int t = 0; t < 3; ++t) {
+            c.L[t] = sh[3 + t];
+            c.invL[t] = cc->invL[t];
+        }
+        c.half_cap = 0.5 * prm.max_disp;
+        c.V = sh[6];
+        c.noise = prm.noise;
+        c.pad = 0;
+        *cf = c;
+        cell[0] = sh[3];
+        cell[1] = sh[4];
+        cell[2] = sh[5];
+        cell[3] = sh[2];
+        cell[10] = sh[6];
+    }
 }
 
+// r += d with |d| capped at cap (cap > 0); the square root only for a step that is capped.
 __device__ __forceinline__ void capped_add(double r[3], double d[3], double cap)
 {
     if (cap > 0.0) {
-        const double len = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        if (len > cap) {
-            const double s = cap / len;
+        const double l2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (l2 > cap * cap) {
+            const double s = cap / sqrt(l2);
             d[0] *= s; d[1] *= s; d[2] *= s;
         }
     }
     r[0] += d[0]; r[1] += d[1]; r[2] += d[2];
 }
 
-// Particle part before the forces: R^p/2, R/2, O, R/2, wrap into the new box.
+// The same four normals in FP32 (FP32-phase path): Box--Muller with the fast logarithm and
+// sine/cosine; the angle 2 pi u is taken as 2 pi (u - 1/2) + pi, so that the argument of the
+// fast sine/cosine stays in [-pi, pi).
+__device__ __forceinline__ void npt_normals_f32(uint64_t seed, uint32_t stream, uint64_t step, uint32_t index,
+                                                double z[4])
+{
+    const uint4 w = philox4x32_10(make_uint4(index, 0u, (uint32_t)step,
+                                             (stream << 24) | (uint32_t)((step >> 32) & 0xFFFFFFu)),
+                                  (uint32_t)seed, (uint32_t)(seed >> 32));
+    const float k = 0x1.0p-32f, two_pi = 6.28318530717958647692f;
+    const float u0 = ((float)w.x + 0.5f) * k, u1 = ((float)w.y + 0.5f) * k;
+    const float u2 = ((float)w.z + 0.5f) * k, u3 = ((float)w.w + 0.5f) * k;
+    float s, c;
+    const float r0 = sqrtf(-2.0f * __logf(u0));
+    __sincosf(two_pi * (u1 - 0.5f), &s, &c);
+    z[0] = -(double)(r0 * c);
+    z[1] = -(double)(r0 * s);
+    const float r1 = sqrtf(-2.0f * __logf(u2));
+    __sincosf(two_pi * (u3 - 0.5f), &s, &c);
+    z[2] = -(double)(r1 * c);
+    z[3] = -(double)(r1 * s);
+}
+
+// Particle part before the forces: R^p/2, R/2, O, R/2, wrap into the new box.  kF32Noise:
+// the Langevin normals in FP32 (FP32-phase path); the state stays FP64 either way.
+template <bool kF32Noise>
 __global__ void __launch_bounds__(kNptThreads)
 k_npt_drift(int64_t N, double* __restrict__ pos, double* __restrict__ mom, const double* __restrict__ force,
-            const double* __restrict__ mass, const NptCoef* __restrict__ cfp, uint64_t seed,
+            const double2* __restrict__ mprop, const NptCoef* __restrict__ cfp, uint64_t seed,
             const double* __restrict__ cell)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const uint64_t step = cell_step(cell);
     const NptCoef c = *cfp;
-    const double m = mass[i];
+    const double2 mp = mprop[i];  // (1/m, sqrt(m))
+    const double inv_m = mp.x;
     double r[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
     double p[3] = {mom[3 * i], mom[3 * i + 1], mom[3 * i + 2]};
     for (int t = 0; t < 3; ++t) p[t] = p[t] * c.a1 + kFConv * force[3 * i + t] * c.b1;
     double d[3];
-    for (int t = 0; t < 3; ++t) d[t] = r[t] * c.a2m1 + (p[t] / m) * c.b2;
+    for (int t = 0; t < 3; ++t) d[t] = r[t] * c.a2m1 + (p[t] * inv_m) * c.b2;
     capped_add(r, d, c.half_cap);
     double z[4] = {0.0, 0.0, 0.0, 0.0};
-    if (c.noise) npt_normals(seed, 1u, step, (uint32_t)i, z);
-    const double s = sqrt(c.og * m);
+    if (c.noise) {
+        if (kF32Noise) npt_normals_f32(seed, 1u, step, (uint32_t)i, z);
+        else npt_normals(seed, 1u, step, (uint32_t)i, z);
+    }
+    const double s = c.sog * mp.y;
     for (int t = 0; t < 3; ++t) p[t] = p[t] * c.g + s * z[t];
-    for (int t = 0; t < 3; ++t) d[t] = r[t] * c.a3m1 + (p[t] / m) * c.b3;
+    for (int t = 0; t < 3; ++t) d[t] = r[t] * c.a3m1 + (p[t] * inv_m) * c.b3;
     capped_add(r, d, c.half_cap);
     for (int t = 0; t < 3; ++t) {
-        r[t] -= c.L[t] * floor(r[t] / c.L[t]);
+        r[t] -= c.L[t] * floor(r[t] * c.invL[t]);
         pos[3 * i + t] = r[t];
         mom[3 * i + t] = p[t];
     }
@@ -196,55 +347,46 @@ k_npt_drift(int64_t N, double* __restrict__ pos, double* __restrict__ mom, const
 // ---------------------------------------------------------------------------------
 // Cell list.  Cells per axis nc = floor(l / rc) (>= 3, checked by the host with headroom and
 // here), cell of a wrapped position s = r / l: floor(s nc).
-__device__ __forceinline__ void cell_dims(const double* cell, double rc, int nc[3])
-{
-    // clamped in FP64 before the conversion: any box (huge, infinite, NaN) gives 1..2^20
-    // cells per axis, whose product cannot overflow and is checked against the capacity
-    for (int t = 0; t < 3; ++t) {
-        const double f = floor(cell[t] / rc);
-        nc[t] = f >= 1.0 ? (f <= 1048576.0 ? (int)f : 1048576) : 1;
-    }
-}
-
-__device__ __forceinline__ int cell_of(const double r[3], const double* L, const int nc[3])
+// Cell of a position: s = r / l (as r times 1/l), wrapped into [0, 1), times nc, clamped.
+__device__ __forceinline__ int cell_of(const double r[3], const double* inv_l, const int nc[3])
 {
     int c[3];
     for (int t = 0; t < 3; ++t) {
-        const double s = r[t] / L[t];
+        const double s = r[t] * inv_l[t];
         c[t] = min(nc[t] - 1, max(0, (int)floor((s - floor(s)) * nc[t])));
     }
     return (c[2] * nc[1] + c[1]) * nc[0] + c[0];
 }
 
-__global__ void k_cl_count(int64_t N, const double* __restrict__ pos, const double* __restrict__ cell, double rc,
-                           int cellcap, int* __restrict__ cid, int* __restrict__ cnt, unsigned* __restrict__ status)
+__global__ void __launch_bounds__(kNptThreads)
+k_cl_count(int64_t N, const double* __restrict__ pos, const CellConsts* __restrict__ cc, int* __restrict__ cid,
+           int* __restrict__ cnt, unsigned* __restrict__ status)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    int nc[3];
-    cell_dims(cell, rc, nc);
-    if ((int64_t)nc[0] * nc[1] * nc[2] > cellcap) {
-        atomicOr(status, kStatusBox);
+    // a box that outgrew the cell arrays, or broke rc <= l/2, is reported once
+    if (i == 0 && !cc->ok) atomicOr(status, kStatusBox);
+    if (cc->ncell < 0) {
         cid[i] = 0;
         return;
     }
-    // nearest image needs rc <= l/2 (NaN fails too)
-    if (i == 0 && !(2.0 * rc <= cell[0] && 2.0 * rc <= cell[1] && 2.0 * rc <= cell[2])) atomicOr(status, kStatusBox);
+    const int nc[3] = {cc->nc[0], cc->nc[1], cc->nc[2]};
+    const double inv[3] = {cc->invL[0], cc->invL[1], cc->invL[2]};
     const double r[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
-    const int c = cell_of(r, cell, nc);
+    const int c = cell_of(r, inv, nc);
     cid[i] = c;
     atomicAdd(&cnt[c], 1);
 }
 
 // Exclusive scan of the counts (one block); cursor = start.
 __global__ void __launch_bounds__(kScanThreads)
-k_cl_scan(const double* __restrict__ cell, double rc, int cellcap, const int* __restrict__ cnt,
-          int* __restrict__ start, int* __restrict__ cursor)
+k_cl_scan(const CellConsts* __restrict__ cc, const int* __restrict__ cnt, int* __restrict__ start,
+          int* __restrict__ cursor)
 {
     __shared__ int wsum[kScanThreads / 32];
-    int nc[3];
-    cell_dims(cell, rc, nc);
-    const int n = (int)min((int64_t)cellcap, (int64_t)nc[0] * nc[1] * nc[2]);
+    // a box beyond the cell arrays put every particle in cell 0 with a count of 0: start and
+    // cursor of cell 0 are still written (0), so the fill stays in bounds
+    const int n = cc->ncell < 0 ? 1 : cc->ncell;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int per = (n + kScanThreads - 1) / kScanThreads;
     const int j0 = min(n, tid * per), j1 = min(n, j0 + per);
@@ -289,14 +431,11 @@ __global__ void k_cl_fill(int64_t N, const int* __restrict__ cid, int* __restric
 // members with a smaller index.  Then pack positions and charges in that order: FP32 xyzq
 // always (the pair search runs on it), FP64 as well when spos64 is given.
 __global__ void __launch_bounds__(kSortWarps * 32)
-k_cl_sort(const double* __restrict__ cell, double rc, int cellcap, const int* __restrict__ cnt,
-          const int* __restrict__ start, const int* __restrict__ fill, int* __restrict__ sorted,
-          const double* __restrict__ pos, const double* __restrict__ q, float4* __restrict__ spos32,
-          double4_32a* __restrict__ spos64)
+k_cl_sort(const CellConsts* __restrict__ cc, const int* __restrict__ cnt, const int* __restrict__ start,
+          const int* __restrict__ fill, int* __restrict__ sorted, const double* __restrict__ pos,
+          const double* __restrict__ q, float4* __restrict__ spos32, double4_32a* __restrict__ spos64)
 {
-    int nc[3];
-    cell_dims(cell, rc, nc);
-    const int64_t ncell = min((int64_t)cellcap, (int64_t)nc[0] * nc[1] * nc[2]);
+    const int64_t ncell = cc->ncell;  // -1: nothing to sort
     const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (c >= ncell) return;  // c is the same for the whole warp
@@ -347,10 +486,43 @@ k_cl_sort(const double* __restrict__ cell, double rc, int cellcap, const int* __
 // Each pair is visited from both ends: energies and the virial trace take half.  The warps
 // stride over the slots (grid-stride); per-block partials {W_r, E_coul, E_lj}.  A box that
 // outgrew the cell arrays (flagged by k_cl_count) leaves F_r = 0.
+// Pair constants, formed on the host in FP64 and rounded once: the kernel never derives
+// them itself (the FP32 kernel would otherwise recompute FP64 products in its loops).
+struct PairConst {
+    double rc, rc2, sa, a, two_sa_pi, qk, s2, e4, e24;
+    float rcf, rc2f, saf, af, two_sa_pif, qkf, s2f, e4f, e24f;
+    int lj;
+};
+
+static PairConst make_pair_const(double rc, double alpha, double qqr2e, double lj_sigma, double lj_eps)
+{
+    PairConst c;
+    c.rc = rc;
+    c.rc2 = rc * rc;
+    c.sa = std::sqrt(alpha);
+    c.a = alpha;
+    c.two_sa_pi = 2.0 * std::sqrt(alpha / 3.14159265358979323846);
+    c.qk = qqr2e;
+    c.s2 = lj_sigma * lj_sigma;
+    c.e4 = 4.0 * lj_eps;
+    c.e24 = 24.0 * lj_eps;
+    c.rcf = (float)c.rc;
+    c.rc2f = (float)c.rc2;
+    c.saf = (float)c.sa;
+    c.af = (float)c.a;
+    c.two_sa_pif = (float)c.two_sa_pi;
+    c.qkf = (float)c.qk;
+    c.s2f = (float)c.s2;
+    c.e4f = (float)c.e4;
+    c.e24f = (float)c.e24;
+    c.lj = lj_eps != 0.0;
+    return c;
+}
+
 template <bool kF64>
 __global__ void __launch_bounds__(kPairWarps * 32, kF64 ? kPairBlocksPerSM64 : kPairBlocksPerSM)
-k_pair(int64_t N, const double* __restrict__ cell, int cellcap, double rc, double alpha, double qqr2e,
-       double lj_sigma, double lj_eps, const int* __restrict__ cid, const int* __restrict__ cnt,
+k_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, const int* __restrict__ cid,
+       const int* __restrict__ cnt,
        const int* __restrict__ start, const int* __restrict__ sorted, const float4* __restrict__ spos32,
        const double4_32a* __restrict__ spos64, double* __restrict__ Fr, double* __restrict__ partials)
 {
@@ -358,30 +530,45 @@ k_pair(int64_t N, const double* __restrict__ cell, int cellcap, double rc, doubl
     using Hit = typename std::conditional<kF64, int2, float4>::type;  // FP64: (slot, image code)
     __shared__ Hit hits[kPairWarps][kHitCap];
     __shared__ double red[3][kPairWarps];
+    __shared__ double sL[3], sInvL[3];
+    __shared__ float sLf[3], sInvLf[3], sPass;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const double L[3] = {cell[0], cell[1], cell[2]};
-    int nc[3];
-    cell_dims(cell, rc, nc);
+    // box constants once per block (shared memory)
+    if (threadIdx.x < 3) {
+        sL[threadIdx.x] = cc->L[threadIdx.x];
+        sInvL[threadIdx.x] = cc->invL[threadIdx.x];
+        sLf[threadIdx.x] = cc->Lf[threadIdx.x];
+        sInvLf[threadIdx.x] = cc->invLf[threadIdx.x];
+    } else if (threadIdx.x == 32) {
+        // FP64 path: the FP32 search keeps candidates within rc plus 2^-16 l_max, far above
+        // the FP32 rounding of a distance, and the exact cutoff is applied in FP64
+        sPass = kF64 ? cc->pass64 : pc.rc2f;
+    }
+    __syncthreads();
+    const int nc[3] = {cc->nc[0], cc->nc[1], cc->nc[2]};
     double wsum = 0.0, ecsum = 0.0, elsum = 0.0;  // this warp's particles (lane 0)
-    const bool cells_ok = (int64_t)nc[0] * nc[1] * nc[2] <= (int64_t)cellcap;
+    const bool cells_ok = cc->ncell >= 0;
     if (!cells_ok) {
         for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < 3 * N; j += (int64_t)gridDim.x * blockDim.x)
             Fr[j] = 0.0;
     } else {
-        const float Lf[3] = {(float)L[0], (float)L[1], (float)L[2]};
-        const float invLf[3] = {(float)(1.0 / L[0]), (float)(1.0 / L[1]), (float)(1.0 / L[2])};
-        const double invL[3] = {1.0 / L[0], 1.0 / L[1], 1.0 / L[2]};
+        const double* L = sL;
+        const double* invL = sInvL;
+        const float* Lf = sLf;
+        const float* invLf = sInvLf;
         const bool mi[3] = {nc[0] < 3, nc[1] < 3, nc[2] < 3};
-        const double Lmax = fmax(L[0], fmax(L[1], L[2]));
-        const float rc2_pass = kF64 ? (float)((rc + Lmax * 0x1.0p-16) * (rc + Lmax * 0x1.0p-16)) : (float)(rc * rc);
-        const R rc2 = (R)(rc * rc), sa = (R)sqrt(alpha), aR = (R)alpha;
-        const R two_sa_pi = (R)(2.0 * sqrt(alpha / 3.14159265358979323846));
-        const R qk = (R)qqr2e, s2 = (R)(lj_sigma * lj_sigma), e4 = (R)(4.0 * lj_eps), e24 = (R)(24.0 * lj_eps);
-        const bool lj = lj_eps != 0.0;
-        const int lo1 = nc[1] >= 3 ? -1 : 0, hi1 = nc[1] >= 2 ? 1 : 0;
-        const int lo2 = nc[2] >= 3 ? -1 : 0, hi2 = nc[2] >= 2 ? 1 : 0;
-        const int64_t nwarps = (int64_t)gridDim.x * kPairWarps;
-        for (int64_t u = (int64_t)blockIdx.x * kPairWarps + wib; u < N; u += nwarps) {
+        const float rc2_pass = sPass;
+        R rc2, sa, aR, two_sa_pi, qk, s2, e4, e24;
+        if constexpr (kF64) {
+            rc2 = pc.rc2, sa = pc.sa, aR = pc.a, two_sa_pi = pc.two_sa_pi;
+            qk = pc.qk, s2 = pc.s2, e4 = pc.e4, e24 = pc.e24;
+        } else {
+            rc2 = pc.rc2f, sa = pc.saf, aR = pc.af, two_sa_pi = pc.two_sa_pif;
+            qk = pc.qkf, s2 = pc.s2f, e4 = pc.e4f, e24 = pc.e24f;
+        }
+        const bool lj = pc.lj != 0;
+        const int nwarps = gridDim.x * kPairWarps;
+        for (int u = blockIdx.x * kPairWarps + wib; u < (int)N; u += nwarps) {
             const int i = sorted[u];
             const float4 me = spos32[u];
             R xi, yi, zi, qi;
@@ -397,8 +584,48 @@ k_pair(int64_t N, const double* __restrict__ cell, int cellcap, double rc, doubl
                 zi = me.z;
                 qi = me.w;
             }
-            const int c = cid[i];
-            const int cx = c % nc[0], cy = (c / nc[0]) % nc[1], cz = c / (nc[0] * nc[1]);
+            // Segments, one per lane (lanes 0..17): row r = lane / 2 of the 3 x 3 rows (dy, dz),
+            // part lane % 2 (a row that wraps in x has two parts).  Each lane finds its slot
+            // range [lo, hi), its image (sx, sy, sz) and the search centre me - shift.
+            int lo = 0, hi = 0, code = 0;
+            float ctx = 0.f, cty = 0.f, ctz = 0.f;
+            {
+                const int c = cid[i];
+                const int cxy = nc[0] * nc[1];
+                const int cz = c / cxy, cy = (c - cz * cxy) / nc[0], cx = c - cz * cxy - cy * nc[0];
+                const int r = lane >> 1, part = lane & 1;
+                const int dy = r % 3 - 1, dz = r / 3 - 1;
+                const bool row_ok = r < 9 && (dy >= (nc[1] >= 3 ? -1 : 0)) && (dy <= (nc[1] >= 2 ? 1 : 0)) &&
+                                    (dz >= (nc[2] >= 3 ? -1 : 0)) && (dz <= (nc[2] >= 2 ? 1 : 0));
+                if (row_ok) {
+                    const int uy = cy + dy, uz = cz + dz;
+                    const int yy = uy < 0 ? uy + nc[1] : (uy >= nc[1] ? uy - nc[1] : uy);
+                    const int zz = uz < 0 ? uz + nc[2] : (uz >= nc[2] ? uz - nc[2] : uz);
+                    const int sy = mi[1] ? 0 : (uy < 0 ? -1 : (uy >= nc[1] ? 1 : 0));
+                    const int sz = mi[2] ? 0 : (uz < 0 ? -1 : (uz >= nc[2] ? 1 : 0));
+                    const int row = (zz * nc[1] + yy) * nc[0], nx = nc[0];
+                    int a = -1, e = -1, sx = 0;  // cells a..e of the row, image sx
+                    if (mi[0]) {
+                        if (part == 0) a = 0, e = nx - 1;
+                    } else if (cx == 0) {
+                        if (part == 0) a = 0, e = 1;
+                        else a = e = nx - 1, sx = -1;
+                    } else if (cx == nx - 1) {
+                        if (part == 0) a = nx - 2, e = nx - 1;
+                        else a = e = 0, sx = 1;
+                    } else if (part == 0) {
+                        a = cx - 1, e = cx + 1;
+                    }
+                    if (a >= 0) {
+                        lo = start[row + a];
+                        hi = start[row + e] + cnt[row + e];
+                        code = (sx + 1) | ((sy + 1) << 2) | ((sz + 1) << 4);
+                        ctx = me.x - (float)sx * Lf[0];
+                        cty = me.y - (float)sy * Lf[1];
+                        ctz = me.z - (float)sz * Lf[2];
+                    }
+                }
+            }
             R fx = 0, fy = 0, fz = 0, w = 0, ec = 0, el = 0;
             int nh = 0;
             // one buffered candidate per lane (lanes >= count idle)
@@ -408,10 +635,10 @@ k_pair(int64_t N, const double* __restrict__ cell, int cellcap, double rc, doubl
                 R dx, dy, dz, qj;
                 if constexpr (kF64) {
                     const double4_32a o = spos64[h.x];
-                    const int code = h.y;
-                    dx = (o.x - xi) + (double)((code & 3) - 1) * L[0];
-                    dy = (o.y - yi) + (double)(((code >> 2) & 3) - 1) * L[1];
-                    dz = (o.z - zi) + (double)(((code >> 4) & 3) - 1) * L[2];
+                    const int cd = h.y;
+                    dx = (o.x - xi) + (double)((cd & 3) - 1) * L[0];
+                    dy = (o.y - yi) + (double)(((cd >> 2) & 3) - 1) * L[1];
+                    dz = (o.z - zi) + (double)(((cd >> 4) & 3) - 1) * L[2];
                     if (mi[0]) dx -= L[0] * rint(dx * invL[0]);
                     if (mi[1]) dy -= L[1] * rint(dy * invL[1]);
                     if (mi[2]) dz -= L[2] * rint(dz * invL[2]);
@@ -424,16 +651,26 @@ k_pair(int64_t N, const double* __restrict__ cell, int cellcap, double rc, doubl
                 }
                 const R r2 = dx * dx + dy * dy + dz * dz;
                 if (!(r2 < rc2)) return;
-                const R r = sqrt(r2);
-                const R qq = qk * qi * qj;
+                R inv_r, r, ex;
+                if constexpr (kF64) {
+                    r = sqrt(r2);
+                    inv_r = 1.0 / r;
+                    ex = exp(-aR * r2);
+                } else {
+                    inv_r = rsqrtf(r2);
+                    r = r2 * inv_r;
+                    ex = __expf(-aR * r2);
+                }
+                const R inv_r2 = inv_r * inv_r;
+                const R coul = qk * qi * qj * inv_r;  // qqr2e q_i q_j / r
                 const R er = erfc(sa * r);
-                R f = qq * (er / r2 + two_sa_pi * exp(-aR * r2) / r) / r;
-                ec += qq * er / r;
+                ec += coul * er;
+                R f = coul * (er + two_sa_pi * r * ex) * inv_r2;
                 if (lj) {
-                    const R sr2 = s2 / r2;
+                    const R sr2 = s2 * inv_r2;
                     const R sr6 = sr2 * sr2 * sr2;
                     el += e4 * (sr6 * sr6 - sr6);
-                    f += e24 * (2 * sr6 * sr6 - sr6) / r2;
+                    f += e24 * (2 * sr6 * sr6 - sr6) * inv_r2;
                 }
                 // force on i is -f d (d points from i to the neighbour)
                 fx -= f * dx;
@@ -441,30 +678,27 @@ k_pair(int64_t N, const double* __restrict__ cell, int cellcap, double rc, doubl
                 fz -= f * dz;
                 w += f * r2;
             };
-            // lanes stride over slots [lo, hi) of one image (sx, sy, sz in {-1, 0, 1})
-            auto search = [&](int lo, int hi, int sx, int sy, int sz) {
-                const float shx = (float)sx * Lf[0], shy = (float)sy * Lf[1], shz = (float)sz * Lf[2];
-                const int code = (sx + 1) | ((sy + 1) << 2) | ((sz + 1) << 4);
-                for (int s0 = lo; s0 < hi; s0 += 32) {
+            // the search over one segment; MI: some axis has fewer than 3 cells (nearest image
+            // per candidate there).  The loop body has no divergent branch: out-of-range lanes
+            // load an in-range slot and are masked out of the hit.
+            auto search = [&](auto mi_tag, int glo, int ghi, int gcode, float gx, float gy, float gz) {
+                constexpr bool MI = decltype(mi_tag)::value;
+                for (int s0 = glo; s0 < ghi; s0 += 32) {
                     const int s = s0 + lane;
-                    bool hit = false;
-                    float dx = 0.f, dy = 0.f, dz = 0.f, qj = 0.f;
-                    if (s < hi && (int64_t)s != u) {
-                        const float4 o = spos32[s];
-                        dx = (o.x - me.x) + shx;
-                        dy = (o.y - me.y) + shy;
-                        dz = (o.z - me.z) + shz;
+                    const bool valid = s < ghi && s != u;
+                    const float4 o = spos32[s < ghi ? s : glo];
+                    float dx = o.x - gx, dy = o.y - gy, dz = o.z - gz;
+                    if constexpr (MI) {
                         if (mi[0]) dx -= Lf[0] * rintf(dx * invLf[0]);
                         if (mi[1]) dy -= Lf[1] * rintf(dy * invLf[1]);
                         if (mi[2]) dz -= Lf[2] * rintf(dz * invLf[2]);
-                        qj = o.w;
-                        hit = dx * dx + dy * dy + dz * dz < rc2_pass;
                     }
+                    const bool hit = valid && dx * dx + dy * dy + dz * dz < rc2_pass;
                     const unsigned m = __ballot_sync(0xffffffffu, hit);
                     if (hit) {
                         const int p = nh + __popc(m & ((1u << lane) - 1u));
-                        if constexpr (kF64) hits[wib][p] = make_int2(s, code);
-                        else hits[wib][p] = make_float4(dx, dy, dz, qj);
+                        if constexpr (kF64) hits[wib][p] = make_int2(s, gcode);
+                        else hits[wib][p] = make_float4(dx, dy, dz, o.w);
                     }
                     nh += __popc(m);
                     if (nh >= 32) {
@@ -477,26 +711,16 @@ k_pair(int64_t N, const double* __restrict__ cell, int cellcap, double rc, doubl
                     }
                 }
             };
-            for (int dz = lo2; dz <= hi2; ++dz)
-                for (int dy = lo1; dy <= hi1; ++dy) {
-                    const int uy = cy + dy, uz = cz + dz;
-                    const int yy = (uy + nc[1]) % nc[1], zz = (uz + nc[2]) % nc[2];
-                    const int sy = mi[1] ? 0 : (uy < 0 ? -1 : (uy >= nc[1] ? 1 : 0));
-                    const int sz = mi[2] ? 0 : (uz < 0 ? -1 : (uz >= nc[2] ? 1 : 0));
-                    const int row = (zz * nc[1] + yy) * nc[0];
-                    const int nx = nc[0];
-                    if (mi[0]) {
-                        search(start[row], start[row + nx - 1] + cnt[row + nx - 1], 0, sy, sz);
-                    } else if (cx == 0) {
-                        search(start[row], start[row + 1] + cnt[row + 1], 0, sy, sz);
-                        search(start[row + nx - 1], start[row + nx - 1] + cnt[row + nx - 1], -1, sy, sz);
-                    } else if (cx == nx - 1) {
-                        search(start[row + nx - 2], start[row + nx - 1] + cnt[row + nx - 1], 0, sy, sz);
-                        search(start[row], start[row] + cnt[row], 1, sy, sz);
-                    } else {
-                        search(start[row + cx - 1], start[row + cx + 1] + cnt[row + cx + 1], 0, sy, sz);
-                    }
-                }
+            const bool any_mi = mi[0] || mi[1] || mi[2];
+            for (int g = 0; g < 18; ++g) {
+                const int glo = __shfl_sync(0xffffffffu, lo, g), ghi = __shfl_sync(0xffffffffu, hi, g);
+                if (glo >= ghi) continue;  // the same for every lane
+                const int gcode = __shfl_sync(0xffffffffu, code, g);
+                const float gx = __shfl_sync(0xffffffffu, ctx, g), gy = __shfl_sync(0xffffffffu, cty, g),
+                            gz = __shfl_sync(0xffffffffu, ctz, g);
+                if (any_mi) search(std::true_type{}, glo, ghi, gcode, gx, gy, gz);
+                else search(std::false_type{}, glo, ghi, gcode, gx, gy, gz);
+            }
             __syncwarp();
             evaluate(nh);
             __syncwarp();
@@ -538,7 +762,7 @@ k_pair(int64_t N, const double* __restrict__ cell, int cellcap, double rc, doubl
 // block; the last block sums the partials in a fixed order and finishes the pressure:
 // W = qqr2e tr(W_k) + W_r, P_ins = (2K + W)/(3V), and with do_kick V^p/2.
 __global__ void __launch_bounds__(kNptThreads)
-k_npt_finish(int64_t N, double* __restrict__ mom, double* __restrict__ force, const double* __restrict__ mass,
+k_npt_finish(int64_t N, double* __restrict__ mom, double* __restrict__ force, const double2* __restrict__ mprop,
              const double* __restrict__ Fk, const double* __restrict__ Fr, const double* __restrict__ WEk,
              const NptCoef* __restrict__ cfp, double* __restrict__ partials, int nblocks_pair,
              unsigned* __restrict__ counter, double* __restrict__ cell, rbe_npt_params prm, int do_kick,
@@ -549,7 +773,7 @@ k_npt_finish(int64_t N, double* __restrict__ mom, double* __restrict__ force, co
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double k2 = 0.0;
     if (i < N) {
-        const double m = mass[i];
+        const double inv_m = mprop[i].x;
         double a = 1.0, b = 0.0;
         if (do_kick) {
             a = cfp->a4;
@@ -563,9 +787,9 @@ k_npt_finish(int64_t N, double* __restrict__ mom, double* __restrict__ force, co
                 p = p * a + kFConv * F * b;
                 mom[3 * i + t] = p;
             }
-            k2 += p * p / m;
+            k2 += p * p * inv_m;
         }
-        k2 /= kFConv;
+        k2 *= 1.0 / kFConv;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -655,6 +879,7 @@ static rbe_status npt_ensure(rbe_ctx ctx, int64_t N, const double box[3], double
     cudaError_t e;
     if (!b.WEk) {
         if ((e = ctx_alloc(ctx, &b.WEk, 16 * sizeof(double))) != cudaSuccess ||
+            (e = ctx_alloc(ctx, &b.cellc, sizeof(CellConsts))) != cudaSuccess ||
             (e = ctx_alloc(ctx, &b.coef, sizeof(NptCoef))) != cudaSuccess ||
             (e = ctx_alloc(ctx, &b.counter, sizeof(unsigned))) != cudaSuccess ||
             (e = cudaMemsetAsync(b.counter, 0, sizeof(unsigned), ctx->stream)) != cudaSuccess)
@@ -662,15 +887,17 @@ static rbe_status npt_ensure(rbe_ctx ctx, int64_t N, const double box[3], double
     }
     if (N > b.ncap) {
         ctx_free(ctx, b.Fk); ctx_free(ctx, b.Fr); ctx_free(ctx, b.cid); ctx_free(ctx, b.fill); ctx_free(ctx, b.sorted);
-        ctx_free(ctx, b.spos32); ctx_free(ctx, b.spos64);
+        ctx_free(ctx, b.spos32); ctx_free(ctx, b.spos64); ctx_free(ctx, b.mprop);
         b.Fk = b.Fr = nullptr; b.cid = b.fill = b.sorted = nullptr; b.spos32 = nullptr; b.spos64 = nullptr; b.ncap = 0;
+        b.mprop = nullptr;
         b.n64 = 0;
         if ((e = ctx_alloc(ctx, &b.Fk, 3 * sizeof(double) * N)) != cudaSuccess ||
             (e = ctx_alloc(ctx, &b.Fr, 3 * sizeof(double) * N)) != cudaSuccess ||
             (e = ctx_alloc(ctx, &b.cid, sizeof(int) * N)) != cudaSuccess ||
             (e = ctx_alloc(ctx, &b.fill, sizeof(int) * N)) != cudaSuccess ||
             (e = ctx_alloc(ctx, &b.sorted, sizeof(int) * N)) != cudaSuccess ||
-            (e = ctx_alloc(ctx, &b.spos32, sizeof(float4) * N)) != cudaSuccess)
+            (e = ctx_alloc(ctx, &b.spos32, sizeof(float4) * N)) != cudaSuccess ||
+            (e = ctx_alloc(ctx, &b.mprop, sizeof(double2) * N)) != cudaSuccess)
             return npt_fail(ctx, e, "cudaMalloc(npt particles)");
         b.ncap = N;
     }
@@ -736,26 +963,26 @@ static rbe_status npt_forces(rbe_ctx ctx, rbe_system* sys, uint64_t batch, int d
     if (prm.real && N > 0) {
         cudaError_t e = cudaMemsetAsync(b.cnt, 0, sizeof(int) * b.cellcap, s);
         if (e != cudaSuccess) return npt_fail(ctx, e, "cudaMemsetAsync(cells)");
-        k_cl_count<<<nb, kNptThreads, 0, s>>>(N, sys->pos, sys->cell, prm.rc, b.cellcap, b.cid, b.cnt, ctx->d.status);
-        k_cl_scan<<<1, kScanThreads, 0, s>>>(sys->cell, prm.rc, b.cellcap, b.cnt, b.start, b.cursor);
+        const CellConsts* cc = static_cast<const CellConsts*>(b.cellc);
+        k_cl_count<<<nb, kNptThreads, 0, s>>>(N, sys->pos, cc, b.cid, b.cnt, ctx->d.status);
+        k_cl_scan<<<1, kScanThreads, 0, s>>>(cc, b.cnt, b.start, b.cursor);
         k_cl_fill<<<nb, kNptThreads, 0, s>>>(N, b.cid, b.cursor, b.fill);
         const bool fp64 = ctx->precision == RBE_FP64;
         if (fp64 && b.n64 < N) return fail(ctx, RBE_ESTATE, "precision changed to FP64 after rbe_npt_init: call it again");
         const int64_t sort_blocks = ((int64_t)b.cellcap + kSortWarps - 1) / kSortWarps;
-        k_cl_sort<<<(unsigned)sort_blocks, kSortWarps * 32, 0, s>>>(sys->cell, prm.rc, b.cellcap, b.cnt, b.start, b.fill,
+        k_cl_sort<<<(unsigned)sort_blocks, kSortWarps * 32, 0, s>>>(cc, b.cnt, b.start, b.fill,
                                                                   b.sorted, sys->pos, sys->charge, b.spos32,
                                                                   fp64 ? b.spos64 : nullptr);
+        const PairConst pc = make_pair_const(prm.rc, ctx->alpha, prm.qqr2e, prm.lj_sigma, prm.lj_eps);
         if (fp64)
-            k_pair<true><<<nbp, kPairWarps * 32, 0, s>>>(N, sys->cell, b.cellcap, prm.rc, ctx->alpha, prm.qqr2e,
-                                                         prm.lj_sigma, prm.lj_eps, b.cid, b.cnt, b.start, b.sorted,
+            k_pair<true><<<nbp, kPairWarps * 32, 0, s>>>(N, cc, pc, b.cid, b.cnt, b.start, b.sorted,
                                                          b.spos32, b.spos64, b.Fr, b.partials);
         else
-            k_pair<false><<<nbp, kPairWarps * 32, 0, s>>>(N, sys->cell, b.cellcap, prm.rc, ctx->alpha, prm.qqr2e,
-                                                          prm.lj_sigma, prm.lj_eps, b.cid, b.cnt, b.start, b.sorted,
+            k_pair<false><<<nbp, kPairWarps * 32, 0, s>>>(N, cc, pc, b.cid, b.cnt, b.start, b.sorted,
                                                           b.spos32, nullptr, b.Fr, b.partials);
         if ((st = npt_check(ctx, "real-space kernels")) != RBE_OK) return st;
     }
-    k_npt_finish<<<std::max(1, nb), kNptThreads, 0, s>>>(N, sys->mom, sys->force, sys->mass, b.Fk, b.Fr, b.WEk,
+    k_npt_finish<<<std::max(1, nb), kNptThreads, 0, s>>>(N, sys->mom, sys->force, b.mprop, b.Fk, b.Fr, b.WEk,
                                                          reinterpret_cast<const NptCoef*>(b.coef), b.partials, nbp,
                                                          b.counter, sys->cell, prm, do_kick, ctx->d.status);
     return npt_check(ctx, "k_npt_finish");
@@ -806,6 +1033,11 @@ rbe_status npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch)
     }
     if ((st = ensure_table_capacity(ctx, need)) != RBE_OK) return st;
     ctx->npt_ready_N = sys->N;
+    // per-particle 1/m and sqrt(m), and the cell-list constants of the initial box
+    NptBuffers& b = ctx->npt;
+    k_mass_props<<<(unsigned)((sys->N + kNptThreads - 1) / kNptThreads), kNptThreads, 0, ctx->stream>>>(
+        sys->N, sys->mass, b.mprop);
+    k_cell_consts<<<1, 32, 0, ctx->stream>>>(sys->cell, sys->params.rc, b.cellcap, static_cast<CellConsts*>(b.cellc));
     k_npt_set_step<<<1, 32, 0, ctx->stream>>>(sys->cell, batch);
     if ((st = npt_check(ctx, "k_npt_set_step")) != RBE_OK) return st;
     st = npt_forces(ctx, sys, batch, 0);
@@ -824,10 +1056,17 @@ rbe_status npt_run(rbe_ctx ctx, rbe_system* sys, int32_t nsteps)
     const int64_t N = sys->N;
     const int nb = (int)((N + kNptThreads - 1) / kNptThreads);
     NptCoef* cf = reinterpret_cast<NptCoef*>(ctx->npt.coef);
+    const NptBuffers& b = ctx->npt;
     for (int32_t k = 0; k < nsteps; ++k) {
         const uint64_t step = sys->step;
-        k_npt_cell_a<<<1, 32, 0, s>>>(sys->cell, cf, sys->params, ctx->seed);
-        k_npt_drift<<<nb, kNptThreads, 0, s>>>(N, sys->pos, sys->mom, sys->force, sys->mass, cf, ctx->seed, sys->cell);
+        k_npt_cell_a<<<1, 32, 0, s>>>(sys->cell, cf, sys->params, ctx->seed, b.cellcap,
+                                      static_cast<CellConsts*>(b.cellc));
+        if (ctx->precision == RBE_FP64)
+            k_npt_drift<false><<<nb, kNptThreads, 0, s>>>(N, sys->pos, sys->mom, sys->force, b.mprop, cf, ctx->seed,
+                                                          sys->cell);
+        else
+            k_npt_drift<true><<<nb, kNptThreads, 0, s>>>(N, sys->pos, sys->mom, sys->force, b.mprop, cf, ctx->seed,
+                                                         sys->cell);
         if ((st = npt_check(ctx, "k_npt_cell_a/k_npt_drift")) != RBE_OK) return st;
         if ((st = npt_forces(ctx, sys, step, 1)) != RBE_OK) return st;
         sys->step = step + 1;
