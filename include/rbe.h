@@ -245,6 +245,60 @@ rbe_status rbe_npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch);
 rbe_status rbe_npt_step(rbe_ctx ctx, rbe_system* sys, int32_t nsteps);
 
 /* ---------------------------------------------------------------------------------
+ * Batched k-space evaluation: many systems of uneven N (the RBE force, energy and virial of
+ * Sec. 4.2 for each) in five launches per evaluation, FP32-phase path with plain FP32
+ * accumulation inside a staged tile.  The batch fixes alpha and P; every item brings its own
+ * positions, charges, box, Philox key and batch index, and gets the same frequencies m as
+ * rbe_sample_k with that key and index.  Work runs as persistent grids over a work list of
+ * (item, tile) pairs; the tile shapes are the batch's (rbe_batch_set_tiles, or chosen by
+ * rbe_batch_autotune).  An item's outputs depend only on its own inputs and the tile shapes,
+ * not on the other items.  No counterpart in the paper (its runs are single systems). */
+typedef struct rbe_batch_s* rbe_batch;
+
+typedef struct {
+    int64_t N;             /* >= 1 */
+    const double* pos;     /* device N*3 (8-byte aligned), any real positions */
+    const double* charge;  /* device N */
+    double* forces;        /* device N*3, overwritten with the k-space force */
+    double* virial;        /* device 9, row-major, energy units */
+    double* energy;        /* device 2 {E_k, E_self}, or NULL */
+    double box[3];         /* rectangular box of this item */
+    uint64_t seed;         /* Philox key of this item */
+    uint64_t step;         /* batch index (< 2^56) */
+} rbe_batch_item;
+
+/* A batch for up to max_items items with boxes no longer than max_box on any axis (sizes the
+ * per-item sampling tables).  RBE_EINVAL for bad parameters; allocates its buffers now. */
+rbe_status rbe_batch_create(double alpha, int32_t P, int32_t max_items, double max_box, rbe_batch* out);
+rbe_status rbe_batch_destroy(rbe_batch b);
+/* Stream of later evaluations (a cudaStream_t; NULL = legacy default); synchronises the old one. */
+rbe_status rbe_batch_set_stream(rbe_batch b, void* stream);
+/* Tile shapes: rho_k frequencies per rho tile (a multiple of 32 in [32, 256]), rho_chunk
+ * particles per rho chunk (>= 32), force_block particles per force tile (a positive multiple of
+ * 128).  All three 0 restores the defaults. */
+rbe_status rbe_batch_set_tiles(rbe_batch b, int32_t rho_k, int32_t rho_chunk, int32_t force_block);
+rbe_status rbe_batch_get_tiles(rbe_batch b, int32_t* rho_k, int32_t* rho_chunk, int32_t* force_block);
+
+/* Evaluate items[0..n) (host array of descriptors, read during the call).  Asynchronous on the
+ * batch's stream; validation errors (RBE_EINVAL) leave no side effects.  The work lists are
+ * rebuilt (with a synchronisation of the stream) only when some item's N or a tile shape
+ * changed.  Graph capture: evaluate the same items once outside capture first (RBE_ESTATE
+ * otherwise); a captured evaluation reads the descriptors as they are at replay, so make no
+ * other call on the batch between capture and replay.  Device errors (m = 0 after 2^20
+ * redraws, non-finite values) are reported by rbe_batch_sync. */
+rbe_status rbe_kspace_forces_virial_batched(rbe_batch b, const rbe_batch_item* items, int32_t n);
+
+/* Times candidate tile shapes on these items (frequencies per rho tile x particles per chunk,
+ * then particles per force tile; reps evaluations of each pass) and keeps the fastest; the
+ * items' outputs are overwritten.  *best_ms (may be NULL): mean time of one evaluation with
+ * the chosen shapes.  Synchronous. */
+rbe_status rbe_batch_autotune(rbe_batch b, const rbe_batch_item* items, int32_t n, int32_t reps, double* best_ms);
+
+/* Waits for the batch's stream and reports device-side errors of earlier evaluations. */
+rbe_status rbe_batch_sync(rbe_batch b);
+const char* rbe_batch_last_error(rbe_batch b);
+
+/* ---------------------------------------------------------------------------------
  * Serving loop for independent NPT replicas (continuous batching on one GPU; no counterpart
  * in the paper, whose runs are single systems).  Requests queue on the host; a request is
  * admitted when a slot is free and its device memory fits the budget, and its state stays

@@ -48,6 +48,12 @@ class System(ctypes.Structure):
 RBE_CELL_DOUBLES = 16
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("pos", ctypes.c_void_p), ("charge", ctypes.c_void_p),
+                ("forces", ctypes.c_void_p), ("virial", ctypes.c_void_p), ("energy", ctypes.c_void_p),
+                ("box", ctypes.c_double * 3), ("seed", ctypes.c_uint64), ("step", ctypes.c_uint64)]
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("P", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("max_slots", ctypes.c_int32), ("chunk_steps", ctypes.c_int32), ("mem_budget", ctypes.c_int64),
@@ -83,6 +89,17 @@ SIGNATURES = [
      [_dp, ctypes.c_double, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, _vp, _vp, _vp]),
     ("rbe_npt_init", ctypes.c_int, [_vp, ctypes.POINTER(System), ctypes.c_uint64]),
     ("rbe_npt_step", ctypes.c_int, [_vp, ctypes.POINTER(System), ctypes.c_int32]),
+    ("rbe_batch_create", ctypes.c_int, [ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                        ctypes.POINTER(_vp)]),
+    ("rbe_batch_destroy", ctypes.c_int, [_vp]),
+    ("rbe_batch_set_stream", ctypes.c_int, [_vp, _vp]),
+    ("rbe_batch_set_tiles", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    ("rbe_batch_get_tiles", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_int32)]),
+    ("rbe_kspace_forces_virial_batched", ctypes.c_int, [_vp, ctypes.POINTER(BatchItem), ctypes.c_int32]),
+    ("rbe_batch_autotune", ctypes.c_int, [_vp, ctypes.POINTER(BatchItem), ctypes.c_int32, ctypes.c_int32, _dp]),
+    ("rbe_batch_sync", ctypes.c_int, [_vp]),
+    ("rbe_batch_last_error", ctypes.c_char_p, [_vp]),
     ("rbe_server_create", ctypes.c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_vp)]),
     ("rbe_server_destroy", ctypes.c_int, [_vp]),
     ("rbe_server_submit", ctypes.c_int, [_vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_int64)]),
@@ -284,6 +301,81 @@ class NptReplica:
         """(pos, mom, force, box, cell block) as NumPy arrays (synchronises)."""
         c = self.cell.cpu().numpy()
         return (self.pos.cpu().numpy(), self.mom.cpu().numpy(), self.force.cpu().numpy(), c[:3].copy(), c)
+
+
+class Batch:
+    """Batched k-space evaluation of many systems (rbe_batch_*): FP32-phase path, persistent
+    work-list kernels, tile shapes set by hand or by the autotuner."""
+
+    def __init__(self, alpha: float, P: int, max_items: int, max_box: float, stream=None):
+        lib = load()
+        self.h = ctypes.c_void_p()
+        st = lib.rbe_batch_create(float(alpha), int(P), int(max_items), float(max_box), ctypes.byref(self.h))
+        if st != RBE_OK:
+            raise RBEError(st, lib.rbe_last_error(None).decode())
+        self.P = int(P)
+        if stream is not None:
+            self._check(lib.rbe_batch_set_stream(self.h, stream))
+
+    def _check(self, st):
+        if st != RBE_OK:
+            lib = load()
+            raise RBEError(st, f"{lib.rbe_status_string(st).decode()}: {lib.rbe_batch_last_error(self.h).decode()}")
+
+    def close(self):
+        if self.h:
+            load().rbe_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @staticmethod
+    def items(systems):
+        """ctypes array of BatchItem from dicts with torch CUDA tensors pos (N x 3), q (N),
+        F (N x 3), W (9), optional E (2), and box, seed, step."""
+        arr = (BatchItem * len(systems))()
+        for k, sy in enumerate(systems):
+            E = sy.get("E")
+            arr[k] = BatchItem(N=int(sy["q"].shape[0]), pos=sy["pos"].data_ptr(), charge=sy["q"].data_ptr(),
+                               forces=sy["F"].data_ptr(), virial=sy["W"].data_ptr(),
+                               energy=E.data_ptr() if E is not None else None,
+                               box=(ctypes.c_double * 3)(*[float(b) for b in sy["box"]]), seed=int(sy["seed"]),
+                               step=int(sy["step"]))
+        return arr
+
+    def evaluate(self, items):
+        arr = items if isinstance(items, ctypes.Array) else self.items(items)
+        self._check(load().rbe_kspace_forces_virial_batched(self.h, arr, len(arr)))
+
+    def autotune(self, items, reps: int = 5) -> float:
+        arr = items if isinstance(items, ctypes.Array) else self.items(items)
+        ms = ctypes.c_double()
+        self._check(load().rbe_batch_autotune(self.h, arr, len(arr), int(reps), ctypes.byref(ms)))
+        return ms.value
+
+    def set_tiles(self, rho_k: int, rho_chunk: int, force_block: int):
+        self._check(load().rbe_batch_set_tiles(self.h, int(rho_k), int(rho_chunk), int(force_block)))
+
+    def tiles(self):
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self._check(load().rbe_batch_get_tiles(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def set_stream(self, stream_handle: int):
+        self._check(load().rbe_batch_set_stream(self.h, stream_handle))
+
+    def sync(self):
+        self._check(load().rbe_batch_sync(self.h))
 
 
 def piston_mass(tau_P: float, beta_T: float, V0: float) -> float:

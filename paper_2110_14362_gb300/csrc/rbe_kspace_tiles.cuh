@@ -1,0 +1,590 @@
+// Tile bodies of the RBE k-space FP32-phase path and the table/sampler kernels, as device
+// functions with explicit tile indices.  The single-system kernels (rbe_kspace.cu) call them
+// with their block indices; the batched kernels (rbe_batch.cu) with the tiles of a work list
+// over many systems.  See rbe_kspace.cu for the pass structure (Sec. 4.2 of the paper).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "rbe_context.h"
+#include "rbe_device.cuh"
+
+namespace rbe {
+
+constexpr int kTableThreads = 1024;   // k_tables block
+constexpr int kMaxRhoThreads = 256;
+constexpr int kReduceThreads = 256;
+constexpr int kForceWarps = 8;
+constexpr int kForceThreads = 32 * kForceWarps;
+constexpr int kForcePPT = 4;
+constexpr int kForceRound = 32 * kForcePPT;  // particles per round of the FP32 force pass
+constexpr int kForceStageK = 2048;           // frequencies staged at once (dynamic shared memory)
+
+__device__ __forceinline__ FixScale fs(const FixScaleH& h) { return FixScale{h.q, h.e}; }
+
+// =================================================================================
+// Tables and box constants (Sec. 4.2 Eqs. (S), (psf); App. C item 1).  One block.
+// Per axis: c = pi^2/(alpha l^2), M = ceil(sqrt(60 ln2 / c)), w_a = exp(-c a^2) by the
+// library's own exponential, W_j = rint(w_{|j-M|} 2^sh) with sh = 62 - bitlength(2M+1),
+// C_j = W_0 + ... + W_j (exact integers: any summation order gives the same bits, so the
+// prefix sum runs in parallel), H = C_2M 2^-sh, S = H_x H_y H_z - 1.
+__device__ __forceinline__ int bitlength(unsigned x) { return 32 - __clz(x); }
+
+__device__ __forceinline__ void tables_body(double bx, double by, double bz, const double* __restrict__ box_dev,
+                                            double alpha, int P,
+         unsigned long long* __restrict__ cum, int cap, KState* __restrict__ ks, unsigned* __restrict__ status)
+{
+    __shared__ int sM[3], sSh[3];
+    __shared__ double sc[3], sL[3];
+    __shared__ unsigned long long wsum[kTableThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < 3) {
+        const double ell = box_dev ? box_dev[tid] : (tid == 0 ? bx : (tid == 1 ? by : bz));
+        const double c = axis_c(alpha, ell);
+        bool bad;
+        const int M = axis_M_capped(ell, c, cap, &bad);
+        if (bad) atomicOr(status, kStatusTable);
+        sL[tid] = ell;
+        sc[tid] = c;
+        sM[tid] = M;
+        sSh[tid] = 62 - bitlength((unsigned)(2 * M + 1));
+    }
+    __syncthreads();
+    // integer weights, written once per |m| into both halves of the row; the (axis, a)
+    // entries of the three rows are spread over all threads
+    {
+        const int n0 = sM[0] + 1, n1 = sM[1] + 1, n2 = sM[2] + 1;
+        for (int e = tid; e < n0 + n1 + n2; e += kTableThreads) {
+            const int t = e < n0 ? 0 : (e < n0 + n1 ? 1 : 2);
+            const int a = e - (t == 0 ? 0 : (t == 1 ? n0 : n0 + n1));
+            const int M = sM[t];
+            unsigned long long* row = cum + (size_t)t * cap;
+            const double v = table_exp(-__dmul_rn(sc[t], (double)a * (double)a));
+            const unsigned long long W = (unsigned long long)__double2ll_rn(ldexp(v, sSh[t]));
+            row[M + a] = W;
+            row[M - a] = W;
+        }
+    }
+    __syncthreads();
+    // inclusive prefix sums, one row at a time: each thread owns a contiguous segment
+    for (int t = 0; t < 3; ++t) {
+        const int n = 2 * sM[t] + 1;
+        unsigned long long* row = cum + (size_t)t * cap;
+        const int per = (n + kTableThreads - 1) / kTableThreads;
+        const int j0 = min(n, tid * per), j1 = min(n, j0 + per);
+        unsigned long long local = 0;
+        for (int j = j0; j < j1; ++j) local += row[j];
+        unsigned long long incl = local;  // inclusive scan of the segment sums over the block
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long o = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += o;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long v = wsum[lane];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned long long o = __shfl_up_sync(0xffffffffu, v, off);
+                if (lane >= off) v += o;
+            }
+            wsum[lane] = v;
+        }
+        __syncthreads();
+        unsigned long long run = incl - local + (warp > 0 ? wsum[warp - 1] : 0ull);
+        for (int j = j0; j < j1; ++j) {
+            run += row[j];
+            row[j] = run;
+        }
+        __syncthreads();
+    }
+    // box constants: independent FP64 chains on separate threads (GB300 runs FP64 at a low
+    // rate, so a single thread computing all of them would serialise their latency)
+    __shared__ double sH[3];
+    if (tid < 3) {
+        const unsigned long long C = cum[(size_t)tid * cap + 2 * sM[tid]];
+        sH[tid] = ldexp((double)C, -sSh[tid]);
+        ks->H[tid] = sH[tid];
+        ks->M[tid] = sM[tid];
+        ks->sh[tid] = sSh[tid];
+        ks->L[tid] = sL[tid];
+    } else if (tid >= 32 && tid < 35) {
+        const int t = tid - 32;
+        const double inv = 1.0 / sL[t];
+        ks->inv[t] = inv;
+        const unsigned long long b = (unsigned long long)__double_as_longlong(inv);
+        const int e = (int)((b >> 52) & 0x7ff) - 1075;
+        ks->sc[t].q = ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 11;
+        ks->sc[t].e = e - 11;
+    } else if (tid >= 64 && tid < 67) {
+        const int t = tid - 64;
+        const float c = (float)(2.0 * kPi / sL[t]);
+        if (t == 0) ks->cx = c;
+        else if (t == 1) ks->cy = c;
+        else ks->cz = c;
+    } else if (tid == 96) {
+        const double V = sL[0] * sL[1] * sL[2];
+        ks->V = V;
+        ks->ce = (float)(2.0 * kPi / V);
+        ks->cb = (float)(4.0 * kPi / V);
+    } else if (tid == 128) {
+        ks->alpha = alpha;
+        ks->P = P;
+        ks->inv4a = (float)(1.0 / (4.0 * alpha));
+        ks->cself = (float)(-sqrt(alpha / kPi));
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const double S = __dsub_rn(__dmul_rn(__dmul_rn(sH[0], sH[1]), sH[2]), 1.0);
+        ks->S = S;
+        ks->wP = S / (double)P;
+    }
+}
+
+// Smallest j in [0, 2M] with T < C_j, minus M (C non-decreasing).
+__device__ __forceinline__ int inverse_cdf_int(const unsigned long long* __restrict__ row, int M,
+                                               unsigned long long T)
+{
+    int lo = 0, hi = 2 * M;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (T < row[mid]) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo - M;
+}
+
+// T = floor(U * C_2M / 2^53) for a 53-bit uniform integer U (exact, 128-bit product).
+__device__ __forceinline__ unsigned long long scaled_target(unsigned long long U, unsigned long long Ctot)
+{
+    const unsigned long long hi = __umul64hi(U, Ctot), lo = U * Ctot;
+    return (hi << 11) | (lo >> 53);
+}
+
+// =================================================================================
+// Frequency sampling (Sec. 4.2-4.3): sample l uses Philox key (seed_lo, seed_hi) and
+// counters (l, 2 attempt + half, step_lo, step_hi24); redraw while m = 0.  Integer
+// operations only: U from 53 bits of Philox output, T = floor(U C_2M / 2^53), and the
+// search over the integer cumulative weights.  The block copies the three rows to shared
+// memory when they fit (smem_cap > 0).
+__device__ __forceinline__ void sample_body(int lbase, uint64_t seed, uint64_t step_arg,
+                                            const unsigned long long* __restrict__ step_dev, int P,
+                         const unsigned long long* __restrict__ cum, int cap, int smem_cap,
+                         const KState* __restrict__ ks, int4* __restrict__ m_out, double* __restrict__ w_out,
+                         unsigned* __restrict__ status)
+{
+    extern __shared__ unsigned long long s_cum[];
+    pdl_trigger();  // the rho pass may start staging its particles meanwhile
+    const uint64_t step = step_dev ? *step_dev : step_arg;  // a device-resident step index when given
+    const double wP = ks->wP;
+    const unsigned long long* tx = cum;
+    const unsigned long long* ty = cum + cap;
+    const unsigned long long* tz = cum + 2 * (size_t)cap;
+    if (smem_cap > 0)  // smem_cap == cap: copy the three rows whole, without waiting for M
+        for (int j = threadIdx.x; j < 3 * smem_cap; j += blockDim.x) s_cum[j] = cum[j];
+    const int Mx = ks->M[0], My = ks->M[1], Mz = ks->M[2];
+    if (smem_cap > 0) {
+        __syncthreads();
+        tx = s_cum;
+        ty = s_cum + smem_cap;
+        tz = s_cum + 2 * smem_cap;
+    }
+    const int l = lbase + (int)threadIdx.x;
+    if (l >= P) return;
+    const unsigned long long Cx = tx[2 * Mx], Cy = ty[2 * My], Cz = tz[2 * Mz];
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const uint32_t c2 = (uint32_t)step, c3 = (uint32_t)((step >> 32) & 0xFFFFFFu);
+    int4 m = make_int4(0, 0, 0, 0);
+    bool found = false;
+    for (uint32_t attempt = 0; attempt < kMaxAttempts; ++attempt) {
+        const uint4 w0 = philox4x32_10(make_uint4((uint32_t)l, 2u * attempt, c2, c3), k0, k1);
+        const uint4 w1 = philox4x32_10(make_uint4((uint32_t)l, 2u * attempt + 1u, c2, c3), k0, k1);
+        m.x = inverse_cdf_int(tx, Mx, scaled_target(((unsigned long long)w0.x << 21) | (w0.y >> 11), Cx));
+        m.y = inverse_cdf_int(ty, My, scaled_target(((unsigned long long)w0.z << 21) | (w0.w >> 11), Cy));
+        m.z = inverse_cdf_int(tz, Mz, scaled_target(((unsigned long long)w1.x << 21) | (w1.y >> 11), Cz));
+        if (m.x != 0 || m.y != 0 || m.z != 0) {
+            found = true;
+            break;
+        }
+    }
+    if (!found) {
+        atomicOr(status, kStatusSample);
+        m = make_int4(1, 0, 0, 0);  // keeps the evaluation finite; the call reports RBE_ESAMPLE
+    }
+    m_out[l] = m;
+    w_out[l] = wP;
+}
+
+// Fixed-order block sum of a float-float value per thread; valid in thread 0.
+__device__ __forceinline__ void block_sum_ff(float& hi, float& lo, float (*scratch)[32])
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, hi, off);
+        const float ol = __shfl_xor_sync(0xffffffffu, lo, off);
+        ff_add2(hi, lo, oh, ol);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) {
+        scratch[0][warp] = hi;
+        scratch[1][warp] = lo;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const bool on = lane < (int)(blockDim.x >> 5);
+        hi = on ? scratch[0][lane] : 0.f;
+        lo = on ? scratch[1][lane] : 0.f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, hi, off);
+            const float ol = __shfl_xor_sync(0xffffffffu, lo, off);
+            ff_add2(hi, lo, oh, ol);
+        }
+    }
+}
+
+// Loads particle i as (s_x, s_y, s_z) 32-bit fixed point and q as float, with integer
+// operations only; flags non-finite inputs.
+__device__ __forceinline__ uint4 load_fixed(const double* __restrict__ pos, const double* __restrict__ q,
+                                            int64_t i, FixScale scx, FixScale scy, FixScale scz,
+                                            unsigned* __restrict__ status)
+{
+    const unsigned long long bx = (unsigned long long)__double_as_longlong(pos[3 * i]);
+    const unsigned long long by = (unsigned long long)__double_as_longlong(pos[3 * i + 1]);
+    const unsigned long long bz = (unsigned long long)__double_as_longlong(pos[3 * i + 2]);
+    const unsigned long long bq = (unsigned long long)__double_as_longlong(q[i]);
+    if (nonfinite_bits(bx) || nonfinite_bits(by) || nonfinite_bits(bz) || nonfinite_bits(bq))
+        atomicOr(status, kStatusNonFinite);  // status may be a shared-memory flag (before pdl_wait)
+    return make_uint4(fixed_frac_int(bx, scx), fixed_frac_int(by, scy), fixed_frac_int(bz, scz),
+                      __float_as_uint(double_to_float_int(bq)));
+}
+
+// =================================================================================
+// rho pass, FP32-phase path.  Block (kt, c) has blockDim.x (a multiple of 32, <= 256)
+// threads; thread j owns frequency kt * blockDim.x + j and runs over the particles
+// [c * chunk_len, (c + 1) * chunk_len), staged in shared memory blockDim.x at a time as
+// 32-bit fixed-point (s_x, s_y, s_z) plus q as float and read as broadcasts.  No FP64
+// instruction runs per particle or per pair: sums across staged tiles are float-float.
+// ACC: RBE_RHO_FP32 (plain FP32 within a staged tile), RBE_RHO_COMP32 (Kahan-compensated
+//      FP32 within a tile), RBE_RHO_FP64 (FP64 per pair; slow on GB300, for reference).
+// Partials: float4 (Re hi, Re lo, Im hi, Im lo) at [l * nchunks + c]; row K holds the
+// chunk's sum of q^2 (hi, lo).  The box constants are read from ks before pdl_wait: the
+// kernel that wrote them (k_tables) runs before the sampler, which is this launch's
+// predecessor, and the sampler starts only after k_tables has completed.
+template <int ACC>
+__device__ __forceinline__ void rho_f32_tile(int kt, int c, const double* __restrict__ pos,
+                                             const double* __restrict__ q, int64_t N, const KState* __restrict__ ks,
+          const int4* __restrict__ m, int K, int64_t chunk_len, int nchunks, float4* __restrict__ partials,
+          unsigned* __restrict__ status)
+{
+    __shared__ uint4 sp[kMaxRhoThreads];
+    __shared__ float red[2][32];
+    __shared__ unsigned bad;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int l = kt * nt + tid;
+    const FixScale scx = fs(ks->sc[0]), scy = fs(ks->sc[1]), scz = fs(ks->sc[2]);
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f, q2h = 0.f, q2l = 0.f;
+    double are = 0.0, aim = 0.0;
+    const int64_t start = (int64_t)c * chunk_len;
+    const int64_t end = min(N, start + chunk_len);
+    if (tid == 0) bad = 0u;
+    __syncthreads();
+    // the first tile is staged before waiting for the sampler (inputs only)
+    uint4 rec0 = make_uint4(0u, 0u, 0u, 0u);
+    if (start + tid < end) {
+        rec0 = load_fixed(pos, q, start + tid, scx, scy, scz, &bad);
+        const float qf = __uint_as_float(rec0.w);
+        ff_add(q2h, q2l, qf * qf);
+    }
+    pdl_wait();
+    pdl_trigger();
+    const int4 mv = l < K ? m[l] : make_int4(0, 0, 0, 0);
+    for (int64_t base = start; base < end; base += nt) {
+        const int64_t i = base + tid;
+        uint4 rec = rec0;
+        if (base != start) {
+            rec = make_uint4(0u, 0u, 0u, 0u);
+            if (i < end) {
+                rec = load_fixed(pos, q, i, scx, scy, scz, status);
+                const float qf = __uint_as_float(rec.w);
+                ff_add(q2h, q2l, qf * qf);
+            }
+        }
+        sp[tid] = rec;
+        __syncthreads();
+        const int n_here = (int)min((int64_t)nt, end - base);
+        float re = 0.f, im = 0.f, cre = 0.f, cim = 0.f;
+#pragma unroll 4
+        for (int p = 0; p < n_here; ++p) {
+            const uint4 r = sp[p];
+            const float qp = __uint_as_float(r.w);
+            const float th = fixed_phase(mv.x, mv.y, mv.z, r.x, r.y, r.z);
+            float sn, cs;
+            __sincosf(th, &sn, &cs);
+            if (ACC == RBE_RHO_FP32) {
+                re = fmaf(qp, cs, re);
+                im = fmaf(qp, sn, im);
+            } else if (ACC == RBE_RHO_COMP32) {
+                const float yr = qp * cs - cre;
+                const float tr = re + yr;
+                cre = (tr - re) - yr;
+                re = tr;
+                const float yi = qp * sn - cim;
+                const float ti = im + yi;
+                cim = (ti - im) - yi;
+                im = ti;
+            } else {
+                are = fma((double)qp, (double)cs, are);
+                aim = fma((double)qp, (double)sn, aim);
+            }
+        }
+        if (ACC != RBE_RHO_FP64) {
+            ff_add(rh, rl, re);
+            rl -= cre;
+            ff_add(ih, il, im);
+            il -= cim;
+        }
+        __syncthreads();
+    }
+    if (ACC == RBE_RHO_FP64) {
+        rh = (float)are; rl = (float)(are - (double)rh);
+        ih = (float)aim; il = (float)(aim - (double)ih);
+    }
+    if (tid == 0 && bad) atomicOr(status, kStatusNonFinite);  // flagged while staging the first tile
+    if (l < K) partials[(size_t)l * nchunks + c] = make_float4(rh, rl, ih, il);
+    if (kt == 0) {
+        block_sum_ff(q2h, q2l, red);  // sum of q^2 over the chunk, for E_self
+        if (tid == 0) partials[(size_t)K * nchunks + c] = make_float4(q2h, q2l, 0.f, 0.f);
+    }
+}
+
+// =================================================================================
+// Reduction for the FP32-phase path.  Block l (of K + 1) sums row l of the partials over
+// the chunks as float-float in a fixed order, then forms the per-frequency terms in FP32
+// (the path's stated accuracy is 1e-5 relative).  Row K carries the sum of q^2.  The sums
+// over l run in the force launch (k_force_f32's extra block), concurrently with the force
+// pass.
+__device__ __forceinline__ double ff_to_double(float hi, float lo)
+{
+    return __longlong_as_double((long long)float_to_double_bits(__float_as_uint(hi))) +
+           __longlong_as_double((long long)float_to_double_bits(__float_as_uint(lo)));
+}
+
+__device__ __forceinline__ void reduce_f32_row(int l, const float4* __restrict__ partials, int nchunks, int K,
+                                               const int4* __restrict__ m,
+             const double* __restrict__ w, const KState* __restrict__ ks, double2* __restrict__ rho,
+             float* __restrict__ terms, int4* __restrict__ coef_m, float4* __restrict__ coef_f,
+             unsigned* __restrict__ status)
+{
+    __shared__ float red[2][32];
+    // the sampler completed before the rho pass passed its wait, and the rho pass lets this
+    // launch start only after that wait: m, w and ks are final here
+    int4 mi = make_int4(0, 0, 0, 0);
+    double wd = 0.0;
+    float cx = 0.f, cy = 0.f, cz = 0.f, ce = 0.f, cb = 0.f, inv4a = 0.f;
+    if (threadIdx.x == 0 && l < K) {
+        mi = m[l];
+        wd = w[l];
+        cx = ks->cx; cy = ks->cy; cz = ks->cz; ce = ks->ce; cb = ks->cb; inv4a = ks->inv4a;
+    }
+    pdl_wait();
+    pdl_trigger();
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    const float4* row = partials + (size_t)l * nchunks;
+    for (int j = threadIdx.x; j < nchunks; j += kReduceThreads) {
+        const float4 v = row[j];
+        ff_add2(rh, rl, v.x, v.y);
+        ff_add2(ih, il, v.z, v.w);
+    }
+    block_sum_ff(rh, rl, red);
+    block_sum_ff(ih, il, red);
+    if (threadIdx.x != 0) return;
+    float* t = terms + (size_t)l * 8;
+    if (l == K) {
+        t[0] = rh;  // sum of q^2 as float-float
+        t[1] = rl;
+        return;
+    }
+    const float re = rh + rl, im = ih + il;
+    const float wl = double_to_float_int((unsigned long long)__double_as_longlong(wd));
+    const float kx = cx * (float)mi.x, ky = cy * (float)mi.y, kz = cz * (float)mi.z;
+    const float kk = kx * kx + ky * ky + kz * kz;
+    const float ikk = 1.0f / kk;
+    const float rho2 = re * re + im * im;
+    const float e = ce * wl * rho2 * ikk;
+    const float b = 2.0f * (ikk + inv4a);
+    t[0] = e;
+    t[1] = e * (1.0f - b * kx * kx);
+    t[2] = e * (1.0f - b * ky * ky);
+    t[3] = e * (1.0f - b * kz * kz);
+    t[4] = -e * b * kx * ky;
+    t[5] = -e * b * kx * kz;
+    t[6] = -e * b * ky * kz;
+    t[7] = 0.f;
+    const float beta = cb * wl * ikk;
+    const float A = beta * im, B = beta * re;
+    rho[l] = make_double2(ff_to_double(rh, rl), ff_to_double(ih, il));
+    coef_m[l] = make_int4(mi.x, mi.y, mi.z, __float_as_int(A));
+    coef_f[l] = make_float4(B, (float)mi.x, (float)mi.y, (float)mi.z);
+    if (!isfinite(re) || !isfinite(im)) atomicOr(status, kStatusNonFinite);
+}
+
+// Energy and virial: fixed-order float-float sums of the per-frequency terms over l, by one
+// block of kForceThreads threads.
+__device__ __forceinline__ void final_sums_f32(const float* __restrict__ terms, int K, float cself,
+                                               double* __restrict__ W_out, double* __restrict__ E_out,
+                                               unsigned* __restrict__ status)
+{
+    __shared__ float fin[kForceWarps][14];
+    float ah[7] = {0, 0, 0, 0, 0, 0, 0}, al[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+        const float* t = terms + (size_t)j * 8;
+#pragma unroll
+        for (int a = 0; a < 7; ++a) ff_add(ah[a], al[a], t[a]);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int a = 0; a < 7; ++a) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, ah[a], off);
+            const float ol = __shfl_xor_sync(0xffffffffu, al[a], off);
+            ff_add2(ah[a], al[a], oh, ol);
+        }
+        if (lane == 0) {
+            fin[warp][2 * a] = ah[a];
+            fin[warp][2 * a + 1] = al[a];
+        }
+    }
+    __syncthreads();
+    // thread a (< 7) finishes term a; thread 7 the self energy
+    if (threadIdx.x < 8) {
+        const int a = threadIdx.x;
+        float th = 0.f, tl = 0.f;
+        if (a < 7) {
+            for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) ff_add2(th, tl, fin[wv][2 * a], fin[wv][2 * a + 1]);
+        } else {
+            const float q2h = terms[(size_t)K * 8], q2l = terms[(size_t)K * 8 + 1];
+            ff_add(th, tl, cself * q2h);
+            tl += cself * q2l;
+        }
+        const double v = ff_to_double(th, tl);
+        if (!isfinite(th)) atomicOr(status, kStatusNonFinite);
+        if (a == 0 && E_out) E_out[0] = v;
+        if (a == 7 && E_out) E_out[1] = v;
+        if (W_out) {
+            if (a == 1) W_out[0] = v;
+            if (a == 2) W_out[4] = v;
+            if (a == 3) W_out[8] = v;
+            if (a == 4) { W_out[1] = v; W_out[3] = v; }
+            if (a == 5) { W_out[2] = v; W_out[6] = v; }
+            if (a == 6) { W_out[5] = v; W_out[7] = v; }
+        }
+    }
+}
+
+// =================================================================================
+// Force pass, FP32-phase path.  Blocks of kForceWarps warps; block b owns particles
+// [b * per_block, (b+1) * per_block).  The frequencies are staged in shared memory (as
+// (mx, my, mz, A) and (B, mx, my, mz)) and split into kForceWarps contiguous slices, one
+// per warp.  Particles are converted once per block into shared memory, kForceThreads at
+// a time; each round of kForceRound particles is processed by every warp against its
+// slice (kForcePPT particles per lane), and the warps' partial forces are summed in
+// shared memory in a fixed order.  No FP64 instruction runs:
+//   F_i,theta = q_i (2 pi / l_theta) sum_l m_l,theta (sin B_l - cos A_l)
+// is formed in FP32 and widened to double exactly.  The launch carries one extra block
+// that computes the energy and virial sums (final_sums_f32) meanwhile.
+__device__ __forceinline__ void force_f32_block(int64_t blk, const double* __restrict__ pos,
+                                                const double* __restrict__ q, int64_t N, int64_t per_block,
+                                                const KState* __restrict__ ks, const int4* __restrict__ coef_m,
+                                                const float4* __restrict__ coef_f, int K, double* __restrict__ F,
+                                                unsigned* __restrict__ status)
+{
+    extern __shared__ int4 s_dyn[];
+    __shared__ uint4 sp[kForceThreads];
+    __shared__ float part[kForceWarps][3][kForceRound];
+    __shared__ unsigned bad;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int kstage = min(K, kForceStageK);
+    int4* sm = s_dyn;
+    float4* sf = reinterpret_cast<float4*>(s_dyn + kstage);
+    unsigned long long* Fb = reinterpret_cast<unsigned long long*>(F);
+    const FixScale scx = fs(ks->sc[0]), scy = fs(ks->sc[1]), scz = fs(ks->sc[2]);
+    const float cx = ks->cx, cy = ks->cy, cz = ks->cz;
+    const int64_t b0 = blk * per_block;
+    const int64_t b1 = min(N, b0 + per_block);
+    const bool multi = K > kstage;  // frequency tiles must be restaged for every round
+    bool staged = false;
+    // the first particle tile is converted before waiting for the reduction (inputs only)
+    if (tid == 0) bad = 0u;
+    __syncthreads();
+    const uint4 first = b0 + tid < b1 ? load_fixed(pos, q, b0 + tid, scx, scy, scz, &bad) : make_uint4(0u, 0u, 0u, 0u);
+    pdl_wait();
+    for (int64_t sbase = b0; sbase < b1; sbase += kForceThreads) {
+        // convert up to kForceThreads particles into shared memory
+        const int64_t i = sbase + tid;
+        __syncthreads();
+        sp[tid] = sbase == b0 ? first
+                              : (i < b1 ? load_fixed(pos, q, i, scx, scy, scz, status) : make_uint4(0u, 0u, 0u, 0u));
+        if (sbase == b0 && tid == 0 && bad) atomicOr(status, kStatusNonFinite);
+        const int nstaged = (int)min((int64_t)kForceThreads, b1 - sbase);
+        for (int r0 = 0; r0 < nstaged; r0 += kForceRound) {
+            float gx[kForcePPT], gy[kForcePPT], gz[kForcePPT];
+#pragma unroll
+            for (int p = 0; p < kForcePPT; ++p) gx[p] = gy[p] = gz[p] = 0.f;
+            for (int k0 = 0; k0 < K; k0 += kstage) {
+                const int nk = min(kstage, K - k0);
+                if (multi || !staged) {
+                    __syncthreads();
+                    for (int j = tid; j < nk; j += kForceThreads) {
+                        sm[j] = coef_m[k0 + j];
+                        sf[j] = coef_f[k0 + j];
+                    }
+                    staged = true;
+                }
+                __syncthreads();
+                uint4 pr[kForcePPT];
+#pragma unroll
+                for (int p = 0; p < kForcePPT; ++p) pr[p] = sp[(r0 + 32 * p + lane) % kForceThreads];
+                const int l0 = (warp * nk) / kForceWarps, l1 = ((warp + 1) * nk) / kForceWarps;
+#pragma unroll 2
+                for (int l = l0; l < l1; ++l) {
+                    const int4 a = sm[l];
+                    const float4 b = sf[l];
+                    const float A = __int_as_float(a.w);
+#pragma unroll
+                    for (int p = 0; p < kForcePPT; ++p) {
+                        float sn, cs;
+                        __sincosf(fixed_phase(a.x, a.y, a.z, pr[p].x, pr[p].y, pr[p].z), &sn, &cs);
+                        const float g = fmaf(sn, b.x, -cs * A);
+                        gx[p] = fmaf(g, b.y, gx[p]);
+                        gy[p] = fmaf(g, b.z, gy[p]);
+                        gz[p] = fmaf(g, b.w, gz[p]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < kForcePPT; ++p) {
+                part[warp][0][32 * p + lane] = gx[p];
+                part[warp][1][32 * p + lane] = gy[p];
+                part[warp][2][32 * p + lane] = gz[p];
+            }
+            __syncthreads();
+            for (int t = tid; t < 3 * kForceRound; t += kForceThreads) {
+                const int c = t / kForceRound, j = t % kForceRound;
+                if (r0 + j < nstaged) {
+                    float acc = part[0][c][j];
+#pragma unroll
+                    for (int wv = 1; wv < kForceWarps; ++wv) acc += part[wv][c][j];
+                    const float qf = __uint_as_float(sp[r0 + j].w);
+                    const float sc = c == 0 ? cx : (c == 1 ? cy : cz);
+                    Fb[3 * (sbase + r0 + j) + c] = float_to_double_bits(__float_as_uint(qf * sc * acc));
+                }
+            }
+        }
+    }
+}
+
+}  // namespace rbe
