@@ -250,6 +250,7 @@ def run_ours(args, world, rank, local):
 
     serving = None if args.skip_serving else run_serving(args, world, rank)
     npt1 = None if args.skip_serving else run_npt_single(rbe, [1000, 10000, 100000], 20)
+    batched = None if args.skip_serving else run_batched(rbe)
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
@@ -275,6 +276,8 @@ def run_ours(args, world, rank, local):
         line["fp64_same_workload"] = other
     if serving:
         line["serving"] = serving
+    if batched:
+        line["batched_kspace"] = batched
     if npt1:
         line["npt_one_replica"] = {"system": "jittered-lattice +-1 charges at 0.1/A^3, P=100, rc=7, Langevin NPT",
                                    "launch": "direct, one stream", "by_N": npt1}
@@ -358,6 +361,65 @@ def run_npt_single(rbe, sizes, steps):
         f32 = npt_single(rbe, N, rbe.RBE_FP32_PHASE, steps)
         f64 = npt_single(rbe, N, rbe.RBE_FP64, max(2, steps // 4))
         out[str(N)] = {"fp32_ms_per_step": f32, "fp64_ms_per_step": f64, "fp32_over_fp64": f64 / f32}
+    return out
+
+
+def run_batched(rbe, n_items=64, P=100, iters=20):
+    """Batched k-space (one evaluation of n_items uneven systems in five launches, autotuned
+    tiles) against a loop of single-system evaluations of the same systems on one stream:
+    the first n_items request sizes of the serving stream, +-1 charges at 0.1 per A^3."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    reqs = inputs.request_stream(n_items, 20.0, seed=0)
+    items, ctxs = [], []
+    stream = torch.cuda.current_stream()
+    for r in reqs:
+        pos, _, q, _, box = inputs.npt_replica(r.N, r.seed)
+        it = dict(pos=torch.as_tensor(pos).to(dev), q=torch.as_tensor(q).to(dev),
+                  F=torch.empty((r.N, 3), dtype=torch.float64, device=dev),
+                  W=torch.empty(9, dtype=torch.float64, device=dev), E=torch.empty(2, dtype=torch.float64, device=dev),
+                  box=box, seed=1000 + r.rid, step=0)
+        items.append(it)
+        ctxs.append(rbe.Context(box, SERVE_ALPHA, P, 1000 + r.rid, rbe.RBE_FP32_PHASE, stream=stream.cuda_stream))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    max_box = max(float(np.max(it["box"])) for it in items) * 1.01
+    out = {"items": n_items, "N_total": int(sum(r.N for r in reqs)), "P": P,
+           "N_range": [int(min(r.N for r in reqs)), int(max(r.N for r in reqs))]}
+    with rbe.Batch(SERVE_ALPHA, P, n_items, max_box, stream=stream.cuda_stream) as b:
+        arr = b.items(items)
+        out["autotune_ms"] = b.autotune(arr, reps=3)
+        out["tiles"] = {"rho_k": b.tiles()[0], "rho_chunk": b.tiles()[1], "force_block": b.tiles()[2]}
+
+        def timed(fn):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            ms = []
+            for k in range(iters):
+                flush.fill_(float(k))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                ms.append((e0, e1))
+            torch.cuda.synchronize()
+            return float(np.mean([a.elapsed_time(c) for a, c in ms]))
+
+        def loop():
+            for c, it in zip(ctxs, items):
+                c.forces_virial(it["pos"], it["q"], 0, it["F"], it["W"], it["E"])
+
+        out["batched_ms"] = timed(lambda: b.evaluate(arr))
+        b.sync()
+        out["loop_ms"] = timed(loop)
+        for c in ctxs:
+            c.sync()
+            c.close()
+    pairs = out["N_total"] * P
+    out["pair_evals_per_s_batched"] = pairs / (out["batched_ms"] * 1e-3)
+    out["pair_evals_per_s_loop"] = pairs / (out["loop_ms"] * 1e-3)
+    out["batched_over_loop"] = out["loop_ms"] / out["batched_ms"]
+    out["launches"] = {"batched": 5, "loop": 4 * n_items}
     return out
 
 
@@ -457,6 +519,7 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=64)
     ap.add_argument("--serve-fp64-sample", type=int, default=16)
     ap.add_argument("--profile-npt", type=int, default=0, help="time only NPT steps of one replica of this N")
+    ap.add_argument("--profile-batched", action="store_true", help="time only the batched k-space evaluation")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -470,6 +533,14 @@ def main():
         ms = npt_single(rbe, args.profile_npt, prec, args.steps, args.warmup)
         print(json.dumps({"metric": "NPT steps of one replica", "value": 1e3 / ms, "unit": "replica-steps/s",
                           "ms_per_step": ms, "N": args.profile_npt, "precision": args.precision}), flush=True)
+        return
+    if args.profile_batched:
+        # profiling aid: only the batched-versus-loop k-space measurement
+        import torch
+        import paper_2110_14362_gb300 as rbe
+        torch.cuda.set_device(local)
+        print(json.dumps({"metric": "batched k-space", "batched_kspace": run_batched(rbe, iters=args.steps)}),
+              flush=True)
         return
     if args.impl == "reference":
         run_reference(args, world, rank)
