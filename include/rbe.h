@@ -114,7 +114,13 @@ rbe_status rbe_kspace_forces_virial(rbe_ctx ctx, int64_t N, const double* positi
 
 /* The same evaluation on HOST buffers: copies positions and charges to context-owned
  * device buffers, evaluates, copies forces, virial and energy back, synchronises the
- * stream and returns any latched device error.  forces_out may be NULL. */
+ * stream and returns any latched device error.  forces_out may be NULL.  On the FP32-phase
+ * path with N >= 2^17 the copies are pipelined with the passes: the particles go in two
+ * groups, each evaluated by full-GPU passes of its own, so that a group's copy in overlaps the
+ * previous group's rho pass and its forces' copy out overlaps the next group's force pass.
+ * The sums then run over a different chunk partition: the results agree with
+ * rbe_kspace_forces_virial to FP32 rounding and are reproducible run to run.  Page-locked
+ * host buffers let the copies overlap fully. */
 rbe_status rbe_kspace_forces_virial_host(rbe_ctx ctx, int64_t N, const double* positions,
                                          const double* charges, uint64_t step, double* forces_out,
                                          double* virial_out, double* energy_out);

@@ -188,6 +188,13 @@ rbe_status rbe_destroy(rbe_ctx ctx)
     cudaStreamSynchronize(ctx->stream);
     for (auto& e : ctx->ev)
         if (e) cudaEventDestroy(e);
+    if (ctx->copy_stream) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaStreamDestroy(ctx->copy_stream);
+    }
+    for (auto& e : ctx->pev)
+        if (e) cudaEventDestroy(e);
+    if (ctx->h_out) cudaFreeHost(ctx->h_out);
     free_npt(ctx->npt);
     free_buffers(ctx->d);
     delete ctx;
@@ -280,6 +287,25 @@ rbe_status rbe_kspace_forces_virial(rbe_ctx ctx, int64_t N, const double* positi
     return launch_evaluate(ctx, N, positions, charges, ctx->P, true, forces_out, virial_out, energy_out);
 }
 
+// The copy stream and events of the pipelined host-buffer call (created on first use).
+static rbe_status ensure_copy_stream(rbe_ctx ctx)
+{
+    if (ctx->copy_stream) return RBE_OK;
+    cudaError_t err = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+    for (auto& e : ctx->pev)
+        if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    return err == cudaSuccess ? RBE_OK : cuda_fail(ctx, err, "copy stream");
+}
+
+// Pinned host words for the small outputs of the host-buffer call: virial (9), energy (2),
+// status (in the 12th slot).
+static rbe_status ensure_host_out(rbe_ctx ctx)
+{
+    if (ctx->h_out) return RBE_OK;
+    cudaError_t err = cudaMallocHost(reinterpret_cast<void**>(&ctx->h_out), 16 * sizeof(double));
+    return err == cudaSuccess ? RBE_OK : cuda_fail(ctx, err, "cudaMallocHost(outputs)");
+}
+
 rbe_status rbe_kspace_forces_virial_host(rbe_ctx ctx, int64_t N, const double* positions, const double* charges,
                                          uint64_t step, double* forces_out, double* virial_out,
                                          double* energy_out)
@@ -305,25 +331,55 @@ rbe_status rbe_kspace_forces_virial_host(rbe_ctx ctx, int64_t N, const double* p
         d.ncap = N;
     }
     cudaStream_t s = ctx->stream;
-    if (N > 0) {
-        if ((err = cudaMemcpyAsync(d.pos, positions, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-            (err = cudaMemcpyAsync(d.q, charges, sizeof(double) * N, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-            return cuda_fail(ctx, err, "cudaMemcpyAsync(H2D)");
+    // pipelined on the FP32-phase path for systems large enough to split; plain copies else
+    const int pieces = N >= (1 << 17) ? 2 : 1;
+    const bool piped = ctx->precision == RBE_FP32_PHASE && pieces > 1;
+    rbe_status st;
+    if (piped) {
+        // the copy stream starts after the main stream's earlier work (the staging buffers
+        // may have been in use) and runs beside the sampler
+        if ((st = ensure_copy_stream(ctx)) != RBE_OK) return st;
+        if ((err = cudaEventRecord(ctx->pev[0], s)) != cudaSuccess ||
+            (err = cudaStreamWaitEvent(ctx->copy_stream, ctx->pev[0], 0)) != cudaSuccess)
+            return cuda_fail(ctx, err, "order the copy stream");
     }
-    rbe_status st = launch_sample(ctx, step, ctx->P);
-    if (st != RBE_OK) return st;
-    st = launch_evaluate(ctx, N, d.pos, d.q, ctx->P, true, d.F, d.WE, d.WE + 9);
-    if (st != RBE_OK) return st;
-    if (forces_out && N > 0 &&
-        (err = cudaMemcpyAsync(forces_out, d.F, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-        return cuda_fail(ctx, err, "cudaMemcpyAsync(D2H forces)");
-    double we[11];
-    if ((err = cudaMemcpyAsync(we, d.WE, sizeof(we), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    if ((st = launch_sample(ctx, step, ctx->P)) != RBE_OK) return st;
+    if (piped) {
+        st = launch_evaluate_staged(ctx, N, positions, charges, forces_out, d.pos, d.q, d.F, ctx->P, d.WE, d.WE + 9,
+                                    pieces);
+        if (st != RBE_OK) return st;
+    } else {
+        if (N > 0) {
+            if ((err = cudaMemcpyAsync(d.pos, positions, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s)) !=
+                    cudaSuccess ||
+                (err = cudaMemcpyAsync(d.q, charges, sizeof(double) * N, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+                return cuda_fail(ctx, err, "cudaMemcpyAsync(H2D)");
+        }
+        st = launch_evaluate(ctx, N, d.pos, d.q, ctx->P, true, d.F, d.WE, d.WE + 9);
+        if (st != RBE_OK) return st;
+        if (forces_out && N > 0 &&
+            (err = cudaMemcpyAsync(forces_out, d.F, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return cuda_fail(ctx, err, "cudaMemcpyAsync(D2H forces)");
+    }
+    // virial, energy and the status word into pinned host memory, then one wait
+    if ((st = ensure_host_out(ctx)) != RBE_OK) return st;
+    double* ho = ctx->h_out;
+    if ((err = cudaMemcpyAsync(ho, d.WE, 11 * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (err = cudaMemcpyAsync(ho + 11, d.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_fail(ctx, err, "cudaMemcpyAsync(D2H virial)");
-    st = sync_and_status(ctx);
-    if (st != RBE_OK) return st;
-    if (virial_out) std::memcpy(virial_out, we, 9 * sizeof(double));
-    if (energy_out) std::memcpy(energy_out, we + 9, 2 * sizeof(double));
+    if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(ctx, err, "cudaStreamSynchronize");
+    if (ctx->copy_stream && (err = cudaStreamSynchronize(ctx->copy_stream)) != cudaSuccess)
+        return cuda_fail(ctx, err, "cudaStreamSynchronize(copy)");
+    unsigned bits;
+    std::memcpy(&bits, ho + 11, sizeof(unsigned));
+    if (bits) {
+        if ((err = cudaMemsetAsync(d.status, 0, sizeof(unsigned), s)) != cudaSuccess ||
+            (err = cudaStreamSynchronize(s)) != cudaSuccess)
+            return cuda_fail(ctx, err, "reset status");
+        return status_from_bits(ctx, bits);
+    }
+    if (virial_out) std::memcpy(virial_out, ho, 9 * sizeof(double));
+    if (energy_out) std::memcpy(energy_out, ho + 9, 2 * sizeof(double));
     return RBE_OK;
 }
 

@@ -114,6 +114,11 @@ struct rbe_ctx_s {
     int64_t npt_ready_N = -1;        // N of the system rbe_npt_init prepared the scratch for
     bool timing = false;             // record CUDA events around each evaluation kernel
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    // pipelined host-buffer calls: a copy stream, its events, pinned outputs (virial, energy,
+    // status word)
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t pev[17] = {};  // 1 + 2 kMaxPieces
+    double* h_out = nullptr;
     rbe::DeviceBuffers d;
     std::string last_error;
 };
@@ -151,6 +156,11 @@ rbe_status npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch);
 rbe_status npt_run(rbe_ctx ctx, rbe_system* sys, int32_t nsteps);
 rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int K,
                            bool uniform_weight, double* F, double* W, double* E);
+// Pieces of the pipelined host-buffer evaluation (copy stream events: 1 + 2 kMaxPieces).
+constexpr int kMaxPieces = 8;
+rbe_status launch_evaluate_staged(rbe_ctx ctx, int64_t N, const double* h_pos, const double* h_q, double* h_F,
+                                  double* d_pos, double* d_q, double* d_F, int K, double* W, double* E,
+                                  int pieces);
 void record_event(rbe_ctx ctx, int idx);
 rbe_status launch_weights_from_list(rbe_ctx ctx, int K, const int32_t* m, const double* w);
 

@@ -73,13 +73,16 @@ __device__ __forceinline__ double block_sum(double v, double* scratch32)
     return v;
 }
 
+// Block (kt, c) handles frequency tile kt and particle chunk c_off + c (c_off: the first chunk
+// of a piece when the staged host call feeds the pass piece by piece).
 template <int ACC>
 __global__ void __launch_bounds__(kMaxRhoThreads, 8)
 k_rho_f32(const double* __restrict__ pos, const double* __restrict__ q, int64_t N, const KState* __restrict__ ks,
           const int4* __restrict__ m, int K, int64_t chunk_len, int nchunks, float4* __restrict__ partials,
-          unsigned* __restrict__ status)
+          unsigned* __restrict__ status, int c_off)
 {
-    rho_f32_tile<ACC>((int)blockIdx.x, (int)blockIdx.y, pos, q, N, ks, m, K, chunk_len, nchunks, partials, status);
+    rho_f32_tile<ACC>((int)blockIdx.x, c_off + (int)blockIdx.y, pos, q, N, ks, m, K, chunk_len, nchunks, partials,
+                      status);
 }
 
 // rho pass, FP64 path: s = r / l wrapped to [0, 1); t = m.s - rint(m.s); sincospi(2t).
@@ -240,18 +243,20 @@ k_reduce_f32(const float4* __restrict__ partials, int nchunks, int K, const int4
 
 // Force pass, FP32-phase path (body in rbe_kspace_tiles.cuh); the launch carries one extra
 // block that computes the energy and virial sums (final_sums_f32) meanwhile.
+// Blocks [0, gridDim.x - final) take particle blocks b_off + blockIdx.x; with final = 1 the
+// last block computes the energy and virial sums.
 __global__ void __launch_bounds__(kForceThreads, 5)
 k_force_f32(const double* __restrict__ pos, const double* __restrict__ q, int64_t N, int64_t per_block,
             const KState* __restrict__ ks, const int4* __restrict__ coef_m, const float4* __restrict__ coef_f,
             int K, double* __restrict__ F, unsigned* __restrict__ status, const float* __restrict__ terms,
-            double* __restrict__ W_out, double* __restrict__ E_out)
+            double* __restrict__ W_out, double* __restrict__ E_out, int64_t b_off, int final)
 {
-    if (blockIdx.x == gridDim.x - 1) {
+    if (final && blockIdx.x == gridDim.x - 1) {
         pdl_wait();
         final_sums_f32(terms, K, ks->cself, W_out, E_out, status);
         return;
     }
-    force_f32_block((int64_t)blockIdx.x, pos, q, N, per_block, ks, coef_m, coef_f, K, F, status);
+    force_f32_block(b_off + (int64_t)blockIdx.x, pos, q, N, per_block, ks, coef_m, coef_f, K, F, status);
 }
 
 // Force pass, FP64 path: particle tiles of kT * PPT, frequencies staged kForceKT at a time.
@@ -513,8 +518,14 @@ static cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
     return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
-rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int K,
-                           bool /*uniform_weight*/, double* F, double* W, double* E)
+// Launch plan and partials capacity of one evaluation of N particles and K frequencies.
+struct EvalShape {
+    Plan p;
+    size_t force_smem;
+    bool fp64;
+};
+
+static rbe_status evaluate_shape(rbe_ctx ctx, int64_t N, int K, EvalShape* out)
 {
     DeviceBuffers& d = ctx->d;
     const bool fp64 = ctx->precision == RBE_FP64;
@@ -547,6 +558,20 @@ rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const doub
         if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaMalloc(partials)");
         d.part_cap = need;
     }
+    *out = EvalShape{p, force_smem, fp64};
+    return RBE_OK;
+}
+
+rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int K,
+                           bool /*uniform_weight*/, double* F, double* W, double* E)
+{
+    DeviceBuffers& d = ctx->d;
+    EvalShape sh;
+    rbe_status st0 = evaluate_shape(ctx, N, K, &sh);
+    if (st0 != RBE_OK) return st0;
+    const Plan& p = sh.p;
+    const bool fp64 = sh.fp64;
+    const size_t force_smem = sh.force_smem;
     const dim3 grid(p.ktiles, p.nchunks);
     cudaStream_t s = ctx->stream;
     double2* part64 = static_cast<double2*>(d.partials);
@@ -559,7 +584,7 @@ rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const doub
                     : ctx->rho_accum == RBE_RHO_COMP32 ? k_rho_f32<RBE_RHO_COMP32>
                                                        : k_rho_f32<RBE_RHO_FP32>;
         cudaError_t err = launch_pdl(kern, grid, dim3(p.kthreads), 0, s, pos, q, N, ks, (const int4*)d.m, K,
-                                     p.chunk_len, p.nchunks, part32, d.status);
+                                     p.chunk_len, p.nchunks, part32, d.status, 0);
         if (err != cudaSuccess) return cuda_fail(ctx, err, "launch k_rho_f32");
     }
     rbe_status st = check_launch(ctx, "k_rho");
@@ -586,11 +611,96 @@ rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const doub
         // one extra block computes the energy and virial sums
         cudaError_t err = launch_pdl(k_force_f32, dim3(p.fblocks + 1), dim3(kForceThreads), force_smem, s, pos, q,
                                      N, p.per_block, ks, (const int4*)d.coef_m, (const float4*)d.coef_f, K, F,
-                                     d.status, reinterpret_cast<const float*>(d.terms), W, E);
+                                     d.status, reinterpret_cast<const float*>(d.terms), W, E, (int64_t)0, 1);
         st = err == cudaSuccess ? RBE_OK : cuda_fail(ctx, err, "launch k_force_f32");
     }
     if (st != RBE_OK) return st;
     record_event(ctx, 4);
+    ctx->last_K = K;
+    return RBE_OK;
+}
+
+// The host-buffer evaluation on the FP32-phase path, pipelined in quarters: the particles
+// are split into `pieces` contiguous groups, each evaluated by full-GPU passes of its own
+// plan.  Group g's positions and charges go to the device on the context's copy stream while
+// the rho pass of group g - 1 runs; after the reduction (over the chunks of all groups), group
+// g's forces come back on the copy stream while group g + 1's force pass runs.  The chunk
+// partition differs from a single evaluation's, so the results agree with
+// rbe_kspace_forces_virial to FP32 rounding (not bit for bit) and are reproducible run to run.
+// d_pos, d_q, d_F: device staging of at least N particles; W, E: device outputs.
+rbe_status launch_evaluate_staged(rbe_ctx ctx, int64_t N, const double* h_pos, const double* h_q, double* h_F,
+                                  double* d_pos, double* d_q, double* d_F, int K, double* W, double* E,
+                                  int pieces)
+{
+    DeviceBuffers& d = ctx->d;
+    pieces = std::max(1, std::min(pieces, kMaxPieces));
+    if (N < pieces) pieces = 1;
+    EvalShape whole;
+    rbe_status st = evaluate_shape(ctx, N, K, &whole);  // occupancy caches, frequency tile shape
+    if (st != RBE_OK) return st;
+    Plan pl[kMaxPieces];
+    int64_t i0[kMaxPieces + 1];
+    int coff[kMaxPieces + 1];
+    coff[0] = 0;
+    for (int g = 0; g <= pieces; ++g) i0[g] = N * g / pieces;
+    for (int g = 0; g < pieces; ++g) {
+        EvalShape sg;
+        if ((st = evaluate_shape(ctx, i0[g + 1] - i0[g], K, &sg)) != RBE_OK) return st;
+        pl[g] = sg.p;
+        coff[g + 1] = coff[g] + pl[g].nchunks;
+    }
+    const int nchunks = coff[pieces];
+    const size_t need = (size_t)(K + 1) * nchunks;
+    if (need > d.part_cap) {
+        ctx_free(ctx, d.partials);
+        d.partials = nullptr;
+        d.part_cap = 0;
+        cudaError_t e = ctx_alloc(ctx, &d.partials, 16 * need);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(partials)");
+        d.part_cap = need;
+    }
+    cudaStream_t s = ctx->stream, cs = ctx->copy_stream;
+    const KState* ks = d.ks;
+    float4* part32 = static_cast<float4*>(d.partials);
+    auto kern = ctx->rho_accum == RBE_RHO_FP64     ? k_rho_f32<RBE_RHO_FP64>
+                : ctx->rho_accum == RBE_RHO_COMP32 ? k_rho_f32<RBE_RHO_COMP32>
+                                                   : k_rho_f32<RBE_RHO_FP32>;
+    cudaError_t err;
+    // (the caller has ordered the copy stream after the main stream's earlier work)
+    for (int g = 0; g < pieces; ++g) {
+        const int64_t a = i0[g], n = i0[g + 1] - i0[g];
+        if ((err = cudaMemcpyAsync(d_pos + 3 * a, h_pos + 3 * a, sizeof(double) * 3 * n, cudaMemcpyHostToDevice,
+                                   cs)) != cudaSuccess ||
+            (err = cudaMemcpyAsync(d_q + a, h_q + a, sizeof(double) * n, cudaMemcpyHostToDevice, cs)) != cudaSuccess)
+            return cuda_fail(ctx, err, "staged: H2D");
+        if ((err = cudaEventRecord(ctx->pev[1 + g], cs)) != cudaSuccess ||
+            (err = cudaStreamWaitEvent(s, ctx->pev[1 + g], 0)) != cudaSuccess)
+            return cuda_fail(ctx, err, "staged: input event");
+        // group g: rows of stride nchunks, its columns from coff[g]
+        err = launch_pdl(kern, dim3(pl[g].ktiles, pl[g].nchunks), dim3(pl[g].kthreads), 0, s,
+                         (const double*)(d_pos + 3 * a), (const double*)(d_q + a), n, ks, (const int4*)d.m, K,
+                         pl[g].chunk_len, nchunks, part32 + coff[g], d.status, 0);
+        if (err != cudaSuccess) return cuda_fail(ctx, err, "staged: k_rho_f32");
+    }
+    err = launch_pdl(k_reduce_f32, dim3(K + 1), dim3(kReduceThreads), 0, s, (const float4*)part32, nchunks, K,
+                     (const int4*)d.m, (const double*)d.w, ks, d.rho, reinterpret_cast<float*>(d.terms), d.coef_m,
+                     d.coef_f, d.status);
+    if (err != cudaSuccess) return cuda_fail(ctx, err, "staged: k_reduce_f32");
+    for (int g = 0; g < pieces; ++g) {
+        const int64_t a = i0[g], n = i0[g + 1] - i0[g];
+        const int final_block = g == pieces - 1 ? 1 : 0;
+        err = launch_pdl(k_force_f32, dim3(pl[g].fblocks + final_block), dim3(kForceThreads), whole.force_smem, s,
+                         (const double*)(d_pos + 3 * a), (const double*)(d_q + a), n, pl[g].per_block, ks,
+                         (const int4*)d.coef_m, (const float4*)d.coef_f, K, d_F + 3 * a, d.status,
+                         reinterpret_cast<const float*>(d.terms), W, E, (int64_t)0, final_block);
+        if (err != cudaSuccess) return cuda_fail(ctx, err, "staged: k_force_f32");
+        if ((err = cudaEventRecord(ctx->pev[1 + kMaxPieces + g], s)) != cudaSuccess ||
+            (err = cudaStreamWaitEvent(cs, ctx->pev[1 + kMaxPieces + g], 0)) != cudaSuccess)
+            return cuda_fail(ctx, err, "staged: force event");
+        if (h_F && (err = cudaMemcpyAsync(h_F + 3 * a, d_F + 3 * a, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost,
+                                          cs)) != cudaSuccess)
+            return cuda_fail(ctx, err, "staged: D2H forces");
+    }
     ctx->last_K = K;
     return RBE_OK;
 }

@@ -164,6 +164,45 @@ def test_host_api_matches_device_api():
     assert np.array_equal(F, Fh) and np.array_equal(W, Wh) and np.array_equal(E, Eh)
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_api_pipelined(pinned):
+    """The host-buffer call on the full slab (N = 300000: copies pipelined with two groups of
+    full-GPU passes), with page-locked or pageable buffers: the device API's result to FP32
+    rounding (a different chunk partition), the oracle's within the path's 1e-5, and the same
+    bits on every call."""
+    import torch
+    s = inputs.slab()
+    F, W, E, _ = _run(s, s.P, 3, rbe.RBE_FP32_PHASE)
+    if pinned:
+        pos = torch.empty((s.N, 3), dtype=torch.float64, pin_memory=True)
+        q = torch.empty((s.N,), dtype=torch.float64, pin_memory=True)
+        pos.copy_(torch.as_tensor(s.pos))
+        q.copy_(torch.as_tensor(s.q))
+        pos_h, q_h = pos.numpy(), q.numpy()
+        Fout = torch.zeros((s.N, 3), dtype=torch.float64, pin_memory=True).numpy()
+    else:
+        pos_h, q_h, Fout = s.pos, s.q, np.zeros((s.N, 3))
+    first = None
+    with rbe.Context(s.box, s.alpha, s.P, SEED, rbe.RBE_FP32_PHASE) as ctx:
+        for _ in range(2):  # the second call reuses the staging and the copy stream
+            Fout[:] = np.nan
+            Fh, Wh, Eh = rbe.rbe_kspace_forces_virial_host(ctx.h, pos_h, q_h, 3, Fout)
+            out = (Fh.copy(), Wh.copy(), Eh.copy())
+            if first is None:
+                first = out
+            for a, b in zip(first, out):
+                assert np.array_equal(a, b)
+    Fh, Wh, Eh = first
+    assert rel_rms_force(Fh, F) < 2e-6
+    assert rel_frob(Wh, W) < 2e-6
+    assert abs(Eh[0] - E[0]) < 2e-6 * abs(E[0]) and abs(Eh[1] - E[1]) < 2e-6 * abs(E[1])
+    m, S = oracle.sample_k(s.box, s.alpha, s.P, SEED, 3)
+    Fo, Wo, Eko, Eso, _ = oracle.rbe_kspace(s.pos, s.q, s.box, s.alpha, m, S / s.P)
+    assert rel_rms_force(Fh, Fo) < 1e-5
+    for a in range(3):
+        assert abs(Wh[a, a] - Wo[a, a]) <= 1e-5 * np.abs(np.diag(Wo)).max()
+
+
 @pytest.mark.parametrize("precision", [rbe.RBE_FP64, rbe.RBE_FP32_PHASE])
 def test_bitwise_reproducible(precision):
     s = inputs.uniform_density(30000, P=300)
