@@ -289,7 +289,7 @@ def run_ours(args, world, rank, local):
 # (300 K, 1 bar, dt = 1 fs, gamma = 10/ps, gamma_V = 2/ps, tau_P = 0.5 ps, beta_T = 4.5e-5/bar),
 # charges screened by the relative permittivity of water (primitive electrolyte model),
 # starting from jittered-lattice positions.
-SERVE_ALPHA, SERVE_P, SERVE_RC, SERVE_EPS_R = 0.2, 100, 7.0, 78.5
+SERVE_ALPHA, SERVE_P, SERVE_RC, SERVE_EPS_R, SERVE_SKIN = 0.2, 100, 7.0, 78.5, 1.0
 KB = 0.00831446261815324
 BAR = 6.02214076e-5
 
@@ -298,7 +298,7 @@ def serve_params(rbe, box):
     V0 = float(np.prod(box))
     return rbe.NptParams(dt=0.001, kT=KB * 300.0, P_ext=1.0 * BAR, gamma=10.0, gamma_V=2.0,
                          M_V=rbe.piston_mass(0.5, 4.5e-5 / BAR, V0), rc=SERVE_RC, qqr2e=1389.35457644382 / SERVE_EPS_R,
-                         lj_sigma=2.0, lj_eps=0.5, max_disp=0.05, kspace=1, real=1, noise=1, barostat=1)
+                         lj_sigma=2.0, lj_eps=0.5, max_disp=0.05, kspace=1, real=1, noise=1, barostat=1, skin=SERVE_SKIN)
 
 
 def serve(rbe, reqs, states, precision, max_slots, chunk, nsteps, use_graphs=True, open_loop=False,

@@ -213,6 +213,10 @@ typedef struct {
     int32_t real;     /* 1: real-space forces and virial */
     int32_t noise;    /* 1: Langevin noise in O and O^p */
     int32_t barostat; /* 1: the cell moves; 0: V fixed and p_V = 0 */
+    double skin;      /* A.  0: the real-space pairs come from a cell search every step.  > 0: from
+                         a neighbour list of radius rc + skin, rebuilt on the device when the largest
+                         displacement since the last build and the box change could have brought an
+                         unlisted pair within rc (the same pairs either way) */
 } rbe_npt_params;
 
 /* Number of doubles of the device cell-state block: {l_x, l_y, l_z, p_V, W (virial trace at
@@ -323,7 +327,9 @@ typedef struct {
     int32_t chunk_steps; /* NPT steps per chunk, >= 1 */
     int64_t mem_budget;  /* device bytes the resident replicas may use; a replica of N particles
                             counts N*196 + 12*C + (P+1)*32768 + 4 MiB bytes (state, NPT scratch,
-                            C = prod_t floor(2 l_t / rc) cells, tables) */
+                            C = prod_t floor(2 l_t / rc) cells, tables), plus N*(4*cap + 20) with a
+                            neighbour list (cap = 2 x the expected neighbours within rc + skin, + 64,
+                            rounded up to 32) */
     int32_t use_graphs;  /* 1: replay a captured graph per chunk; 0: launch the steps directly */
     int32_t pad;
 } rbe_server_config;

@@ -34,7 +34,8 @@ class NptParams(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("gamma_V", ctypes.c_double), ("M_V", ctypes.c_double),
                 ("rc", ctypes.c_double), ("qqr2e", ctypes.c_double), ("lj_sigma", ctypes.c_double),
                 ("lj_eps", ctypes.c_double), ("max_disp", ctypes.c_double), ("kspace", ctypes.c_int32),
-                ("real", ctypes.c_int32), ("noise", ctypes.c_int32), ("barostat", ctypes.c_int32)]
+                ("real", ctypes.c_int32), ("noise", ctypes.c_int32), ("barostat", ctypes.c_int32),
+                ("skin", ctypes.c_double)]
 
 
 class System(ctypes.Structure):

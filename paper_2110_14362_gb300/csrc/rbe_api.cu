@@ -92,6 +92,8 @@ static rbe_status status_from_bits(rbe_ctx ctx, unsigned bits)
 {
     if (bits & kStatusSample) return fail(ctx, RBE_ESAMPLE, "a frequency stayed m = 0 after 2^20 redraws");
     if (bits & kStatusTable) return fail(ctx, RBE_ESTATE, "sampling table capacity exceeded on the device");
+    if (bits & kStatusList)
+        return fail(ctx, RBE_ESTATE, "neighbour list capacity exceeded (the density rose far above its initial value)");
     if (bits & kStatusBox)
         return fail(ctx, RBE_ESTATE,
                     "the box left the range rbe_npt_init prepared (cell list capacity, or rc > l/2 on some axis)");
@@ -117,7 +119,8 @@ static rbe_status sync_and_status(rbe_ctx ctx)
 static void free_npt(NptBuffers& b)
 {
     cudaFree(b.Fk); cudaFree(b.Fr); cudaFree(b.WEk); cudaFree(b.coef); cudaFree(b.cid); cudaFree(b.fill);
-    cudaFree(b.sorted); cudaFree(b.spos32); cudaFree(b.spos64); cudaFree(b.mprop); cudaFree(b.cellc); cudaFree(b.cnt); cudaFree(b.start); cudaFree(b.cursor); cudaFree(b.partials);
+    cudaFree(b.sorted); cudaFree(b.spos32); cudaFree(b.spos64); cudaFree(b.mprop); cudaFree(b.cellc); cudaFree(b.cnt);
+    cudaFree(b.nbr); cudaFree(b.nnb); cudaFree(b.sref); cudaFree(b.nls); cudaFree(b.start); cudaFree(b.cursor); cudaFree(b.partials);
     cudaFree(b.counter);
     b = NptBuffers{};
 }

@@ -62,6 +62,13 @@ struct NptBuffers {
     double4_32a* spos64 = nullptr; // N packed FP64 positions+charge (FP64 path)
     double2* mprop = nullptr;      // N (1/m, sqrt(m)), set by rbe_npt_init
     void* cellc = nullptr;         // cell-list constants of the current box (rbe_npt.cu)
+    int* nbr = nullptr;            // neighbour list: slots of the neighbours of slot u at [u * nbr_cap, ...)
+    int* nnb = nullptr;            // neighbours per slot
+    float4* sref = nullptr;        // per slot: scaled position s = r / l at the last build
+    void* nls = nullptr;           // neighbour-list state (rbe_npt.cu)
+    int64_t nl_entries = 0;        // allocated list entries
+    int64_t ncap_list = 0;         // slots of nnb and sref
+    int nbr_cap = 0;               // list entries per slot
     int* cnt = nullptr;            // cells: counts
     int* start = nullptr;          // cells: exclusive prefix sums
     int* cursor = nullptr;         // cells: fill cursors

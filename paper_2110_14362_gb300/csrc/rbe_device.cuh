@@ -22,6 +22,7 @@ constexpr unsigned kStatusNonFinite = 2u;  // rho or an output is NaN/Inf
 constexpr unsigned kStatusTable = 4u;      // the sampling table did not fit its capacity
 constexpr unsigned kStatusTimeout = 8u;    // a bounded wait gave up
 constexpr unsigned kStatusBox = 16u;       // NPT: the box outgrew the cell list or broke rc <= l/2
+constexpr unsigned kStatusList = 32u;      // NPT: a particle had more neighbours than the list holds
 
 // ---------------------------------------------------------------------------------
 // Programmatic dependent launch: a kernel launched with programmatic stream

@@ -30,7 +30,8 @@ constexpr int kSortWarps = 8;        // k_cl_sort: warps (cells) per block
 constexpr int kPairWarps = 8;        // k_pair: warps (particles in flight) per block
 constexpr int kPairBlocksPerSM = 4;  // k_pair (FP32): resident blocks per SM the grid is sized for
 constexpr int kPairBlocksPerSM64 = 2;  // k_pair (FP64): more registers per thread
-constexpr int kHitCap = 64;          // k_pair: buffered candidates per warp (< 32 + 32)
+constexpr int kListBatch = 4;        // k_pair (list): list entries per lane loaded together
+constexpr int kHitCap = 32 * (kListBatch + 1);  // k_pair: buffered candidates per warp (< 32 + 32 kListBatch)
 // rbe_npt_init sizes the per-axis tables and the cell list for box edges up to this many
 // times the initial ones; a box beyond it is flagged (RBE_ESTATE) by the step.
 constexpr double kBoxHeadroom = 2.0;
@@ -109,8 +110,9 @@ __device__ __forceinline__ int cell_dim(double l, double rc)
     return f >= 1.0 ? (f <= 1048576.0 ? (int)f : 1048576) : 1;
 }
 
-// Lanes 0..2 of one warp: axis `lane` of the box L; then lane 0 the totals.
-__device__ __forceinline__ void write_cell_consts(int lane, const double* L, double rc, int cellcap,
+// Lanes 0..2 of one warp: axis `lane` of the box L; then lane 0 the totals.  Cells of at
+// least rcell (rc, or rc + skin when a neighbour list is built from them).
+__device__ __forceinline__ void write_cell_consts(int lane, const double* L, double rc, double rcell, int cellcap,
                                                   CellConsts* __restrict__ cc)
 {
     if (lane < 3) {
@@ -119,7 +121,7 @@ __device__ __forceinline__ void write_cell_consts(int lane, const double* L, dou
         cc->invL[lane] = 1.0 / l;
         cc->Lf[lane] = (float)l;
         cc->invLf[lane] = (float)(1.0 / l);
-        cc->nc[lane] = cell_dim(l, rc);
+        cc->nc[lane] = cell_dim(l, rcell);
     }
     __syncwarp();
     if (lane == 0) {
@@ -132,9 +134,98 @@ __device__ __forceinline__ void write_cell_consts(int lane, const double* L, dou
     }
 }
 
-__global__ void k_cell_consts(const double* __restrict__ cell, double rc, int cellcap, CellConsts* __restrict__ cc)
+__global__ void k_cell_consts(const double* __restrict__ cell, double rc, double rcell, int cellcap,
+                              CellConsts* __restrict__ cc)
 {
-    write_cell_consts(threadIdx.x, cell, rc, cellcap, cc);
+    write_cell_consts(threadIdx.x, cell, rc, rcell, cellcap, cc);
+}
+
+// Neighbour-list state of a replica.  The list holds, for every slot of the cell order of its
+// build, the slots within rl = rc + skin (by the nearest image) at the build.  With D the
+// largest displacement since then (in units of the build's box) and f the smallest ratio of
+// the box edges to the build's, every unlisted pair is now at least f (rl - 2 D) apart: the
+// list stands while that is at least rc.
+struct NListState {
+    double Lref[3];    // box at the last build
+    float rl, rc;
+    unsigned maxd2;    // bits of the largest squared displacement of this step (non-negative float)
+    unsigned counter;  // last-block counter of the check
+    int rebuild;       // 1: this step rebuilds the list
+    int force;         // 1: build at the next step (set by rbe_npt_init)
+};
+
+// Per step, before the cell list: refresh the packed positions in the list's slot order and
+// decide whether the list must be rebuilt.  Until the first build there is no slot order:
+// the kernel then only asks for a build.
+template <bool kF64>
+__global__ void __launch_bounds__(kNptThreads)
+k_nl_check(int64_t N, const double* __restrict__ pos, const double* __restrict__ q, const int* __restrict__ sorted,
+           float4* __restrict__ spos32, double4_32a* __restrict__ spos64, const float4* __restrict__ sref,
+           const CellConsts* __restrict__ cc, NListState* __restrict__ nls)
+{
+    __shared__ float smax[kNptThreads / 32];
+    __shared__ bool last;
+    const bool force = nls->force != 0;
+    float d2max = 0.f;
+    if (!force) {
+        const float Lr[3] = {(float)nls->Lref[0], (float)nls->Lref[1], (float)nls->Lref[2]};
+        const double inv[3] = {cc->invL[0], cc->invL[1], cc->invL[2]};
+        for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < N; u += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t i = sorted[u];
+            const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2], qq = q[i];
+            spos32[u] = make_float4((float)x, (float)y, (float)z, (float)qq);
+            if (kF64) {
+                double4_32a v;
+                v.x = x;
+                v.y = y;
+                v.z = z;
+                v.w = qq;
+                spos64[u] = v;
+            }
+            const float4 r0 = sref[u];
+            float dx = (float)(x * inv[0]) - r0.x, dy = (float)(y * inv[1]) - r0.y, dz = (float)(z * inv[2]) - r0.z;
+            dx = (dx - rintf(dx)) * Lr[0];
+            dy = (dy - rintf(dy)) * Lr[1];
+            dz = (dz - rintf(dz)) * Lr[2];
+            const float d2 = dx * dx + dy * dy + dz * dz;
+            d2max = d2 > d2max ? d2 : d2max;  // NaN compares false: caught by the box checks
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) d2max = fmaxf(d2max, __shfl_xor_sync(0xffffffffu, d2max, off));
+    if (lane == 0) smax[warp] = d2max;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < kNptThreads / 32; ++w) m = fmaxf(m, smax[w]);
+        atomicMax(&nls->maxd2, __float_as_uint(m));
+        __threadfence();
+        last = atomicAdd(&nls->counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    const float D = sqrtf(__uint_as_float(atomicAdd(&nls->maxd2, 0u)));
+    double f = 1e300;
+    for (int t = 0; t < 3; ++t) f = fmin(f, cc->L[t] / nls->Lref[t]);
+    // a margin of 1e-3 A covers the FP32 rounding of the displacements
+    const bool stands = !force && f * ((double)nls->rl - 2.0 * (double)D - 1e-3) >= (double)nls->rc;
+    nls->rebuild = stands ? 0 : 1;
+    nls->maxd2 = 0u;
+    nls->counter = 0u;
+}
+
+__global__ void k_nl_init(NListState* __restrict__ nls, float rl, float rc)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    nls->Lref[0] = nls->Lref[1] = nls->Lref[2] = 1.0;
+    nls->rl = rl;
+    nls->rc = rc;
+    nls->maxd2 = 0u;
+    nls->counter = 0u;
+    nls->rebuild = 1;
+    nls->force = 1;
 }
 
 // 1/m and sqrt(m) per particle, once per rbe_npt_init.
@@ -240,7 +331,7 @@ k_npt_cell_a(double* __restrict__ cell, NptCoef* __restrict__ cf, rbe_npt_params
     } else if (lane == 4) {
         sh[21] = expm1_over(-sh[13] * h, h);
     }
-    write_cell_consts(lane, sh + 3, prm.rc, cellcap, cc);  // syncs the warp
+    write_cell_consts(lane, sh + 3, prm.rc, prm.rc + (prm.skin > 0.0 ? prm.skin : 0.0), cellcap, cc);  // syncs
     __syncwarp();
     if (lane == 0) {
         NptCoef c;
@@ -360,12 +451,13 @@ __device__ __forceinline__ int cell_of(const double r[3], const double* inv_l, c
 
 __global__ void __launch_bounds__(kNptThreads)
 k_cl_count(int64_t N, const double* __restrict__ pos, const CellConsts* __restrict__ cc, int* __restrict__ cid,
-           int* __restrict__ cnt, unsigned* __restrict__ status)
+           int* __restrict__ cnt, unsigned* __restrict__ status, const NListState* __restrict__ nls)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    // a box that outgrew the cell arrays, or broke rc <= l/2, is reported once
     if (i == 0 && !cc->ok) atomicOr(status, kStatusBox);
+    if (nls && !nls->rebuild) return;  // the neighbour list stands: no cell list this step
+    // (a box that outgrew the cell arrays, or broke rc <= l/2, was reported above)
     if (cc->ncell < 0) {
         cid[i] = 0;
         return;
@@ -381,9 +473,10 @@ k_cl_count(int64_t N, const double* __restrict__ pos, const CellConsts* __restri
 // Exclusive scan of the counts (one block); cursor = start.
 __global__ void __launch_bounds__(kScanThreads)
 k_cl_scan(const CellConsts* __restrict__ cc, const int* __restrict__ cnt, int* __restrict__ start,
-          int* __restrict__ cursor)
+          int* __restrict__ cursor, const NListState* __restrict__ nls)
 {
     __shared__ int wsum[kScanThreads / 32];
+    if (nls && !nls->rebuild) return;
     // a box beyond the cell arrays put every particle in cell 0 with a count of 0: start and
     // cursor of cell 0 are still written (0), so the fill stays in bounds
     const int n = cc->ncell < 0 ? 1 : cc->ncell;
@@ -418,10 +511,12 @@ k_cl_scan(const CellConsts* __restrict__ cc, const int* __restrict__ cnt, int* _
     }
 }
 
-__global__ void k_cl_fill(int64_t N, const int* __restrict__ cid, int* __restrict__ cursor, int* __restrict__ fill)
+__global__ void k_cl_fill(int64_t N, const int* __restrict__ cid, int* __restrict__ cursor, int* __restrict__ fill,
+                          const NListState* __restrict__ nls)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    if (nls && !nls->rebuild) return;
     const int slot = atomicAdd(&cursor[cid[i]], 1);
     fill[slot] = (int)i;
 }
@@ -433,8 +528,10 @@ __global__ void k_cl_fill(int64_t N, const int* __restrict__ cid, int* __restric
 __global__ void __launch_bounds__(kSortWarps * 32)
 k_cl_sort(const CellConsts* __restrict__ cc, const int* __restrict__ cnt, const int* __restrict__ start,
           const int* __restrict__ fill, int* __restrict__ sorted, const double* __restrict__ pos,
-          const double* __restrict__ q, float4* __restrict__ spos32, double4_32a* __restrict__ spos64)
+          const double* __restrict__ q, float4* __restrict__ spos32, double4_32a* __restrict__ spos64,
+          const NListState* __restrict__ nls)
 {
+    if (nls && !nls->rebuild) return;
     const int64_t ncell = cc->ncell;  // -1: nothing to sort
     const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -519,15 +616,32 @@ static PairConst make_pair_const(double rc, double alpha, double qqr2e, double l
     return c;
 }
 
-template <bool kF64>
+// Modes of the pair kernel: search the cells and evaluate (no list), search the cells within
+// the list radius and write the list (only on a rebuild step), evaluate the listed pairs.
+enum PairMode { kPairCells = 0, kPairBuild = 1, kPairList = 2 };
+
+// Neighbour-list arguments of the pair kernel (unused without a list).
+struct ListArgs {
+    NListState* nls;
+    int* nbr;          // [slot * cap + k]
+    int* nnb;          // per slot
+    float4* sref;      // per slot: scaled position at the build
+    unsigned* status;  // kStatusList on overflow
+    int cap;
+};
+
+template <bool kF64, int kMode>
 __global__ void __launch_bounds__(kPairWarps * 32, kF64 ? kPairBlocksPerSM64 : kPairBlocksPerSM)
 k_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, const int* __restrict__ cid,
        const int* __restrict__ cnt,
        const int* __restrict__ start, const int* __restrict__ sorted, const float4* __restrict__ spos32,
-       const double4_32a* __restrict__ spos64, double* __restrict__ Fr, double* __restrict__ partials)
+       const double4_32a* __restrict__ spos64, double* __restrict__ Fr, double* __restrict__ partials,
+       const ListArgs la)
 {
     using R = typename std::conditional<kF64, double, float>::type;
     using Hit = typename std::conditional<kF64, int2, float4>::type;  // FP64: (slot, image code)
+    constexpr bool kBuild = kMode == kPairBuild, kList = kMode == kPairList;
+    if (kBuild && !la.nls->rebuild) return;  // the list stands (the same for every thread)
     __shared__ Hit hits[kPairWarps][kHitCap];
     __shared__ double red[3][kPairWarps];
     __shared__ double sL[3], sInvL[3];
@@ -541,22 +655,38 @@ k_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, const i
         sInvLf[threadIdx.x] = cc->invLf[threadIdx.x];
     } else if (threadIdx.x == 32) {
         // FP64 path: the FP32 search keeps candidates within rc plus 2^-16 l_max, far above
-        // the FP32 rounding of a distance, and the exact cutoff is applied in FP64
-        sPass = kF64 ? cc->pass64 : pc.rc2f;
+        // the FP32 rounding of a distance, and the exact cutoff is applied in FP64.  A build
+        // keeps every candidate within rl plus the same margin (a superset is harmless).
+        if (kBuild) {
+            const double lmax = fmax(cc->L[0], fmax(cc->L[1], cc->L[2]));
+            const double rp = (double)la.nls->rl + lmax * 0x1.0p-16;
+            sPass = (float)(rp * rp);
+        } else {
+            sPass = kF64 ? cc->pass64 : pc.rc2f;
+        }
     }
     __syncthreads();
     const int nc[3] = {cc->nc[0], cc->nc[1], cc->nc[2]};
-    double wsum = 0.0, ecsum = 0.0, elsum = 0.0;  // this warp's particles (lane 0)
-    const bool cells_ok = cc->ncell >= 0;
+    // this warp's particles (lane 0): FP64 sums on the FP64 path; float-float sums on the FP32
+    // path, where no per-particle FP64 instruction runs (each costs a whole warp issue slot on
+    // GB300's narrow FP64 pipe)
+    double wsum = 0.0, ecsum = 0.0, elsum = 0.0;
+    float wh = 0.f, wl = 0.f, ech = 0.f, ecl = 0.f, elh = 0.f, ell = 0.f;
+    // no cell list this step (box beyond the cell arrays, flagged), or no list built yet
+    const bool cells_ok = kList ? la.nls->force == 0 : cc->ncell >= 0;
     if (!cells_ok) {
-        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < 3 * N; j += (int64_t)gridDim.x * blockDim.x)
-            Fr[j] = 0.0;
+        if (!kBuild)
+            for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < 3 * N;
+                 j += (int64_t)gridDim.x * blockDim.x)
+                Fr[j] = 0.0;
     } else {
         const double* L = sL;
         const double* invL = sInvL;
         const float* Lf = sLf;
         const float* invLf = sInvLf;
-        const bool mi[3] = {nc[0] < 3, nc[1] < 3, nc[2] < 3};
+        // nearest image per pair on the axes with fewer than 3 cells, and on all axes for the
+        // listed pairs (the list keeps slots, not images)
+        const bool mi[3] = {kList || nc[0] < 3, kList || nc[1] < 3, kList || nc[2] < 3};
         const float rc2_pass = sPass;
         R rc2, sa, aR, two_sa_pi, qk, s2, e4, e24;
         if constexpr (kF64) {
@@ -589,7 +719,7 @@ k_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, const i
             // range [lo, hi), its image (sx, sy, sz) and the search centre me - shift.
             int lo = 0, hi = 0, code = 0;
             float ctx = 0.f, cty = 0.f, ctz = 0.f;
-            {
+            if (!kList) {
                 const int c = cid[i];
                 const int cxy = nc[0] * nc[1];
                 const int cz = c / cxy, cy = (c - cz * cxy) / nc[0], cx = c - cz * cxy - cy * nc[0];
@@ -629,9 +759,9 @@ k_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, const i
             R fx = 0, fy = 0, fz = 0, w = 0, ec = 0, el = 0;
             int nh = 0;
             // one buffered candidate per lane (lanes >= count idle)
-            auto evaluate = [&](int count) {
+            auto evaluate = [&](int count, int base = 0) {
                 if (lane >= count) return;
-                const Hit h = hits[wib][lane];
+                const Hit h = hits[wib][base + lane];
                 R dx, dy, dz, qj;
                 if constexpr (kF64) {
                     const double4_32a o = spos64[h.x];
@@ -695,6 +825,14 @@ k_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, const i
                     }
                     const bool hit = valid && dx * dx + dy * dy + dz * dz < rc2_pass;
                     const unsigned m = __ballot_sync(0xffffffffu, hit);
+                    if constexpr (kBuild) {
+                        if (hit) {
+                            const int p = nh + __popc(m & ((1u << lane) - 1u));
+                            if (p < la.cap) la.nbr[(int64_t)u * la.cap + p] = s;
+                        }
+                        nh += __popc(m);
+                        continue;
+                    }
                     if (hit) {
                         const int p = nh + __popc(m & ((1u << lane) - 1u));
                         if constexpr (kF64) hits[wib][p] = make_int2(s, gcode);
@@ -711,15 +849,67 @@ k_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, const i
                     }
                 }
             };
-            const bool any_mi = mi[0] || mi[1] || mi[2];
-            for (int g = 0; g < 18; ++g) {
-                const int glo = __shfl_sync(0xffffffffu, lo, g), ghi = __shfl_sync(0xffffffffu, hi, g);
-                if (glo >= ghi) continue;  // the same for every lane
-                const int gcode = __shfl_sync(0xffffffffu, code, g);
-                const float gx = __shfl_sync(0xffffffffu, ctx, g), gy = __shfl_sync(0xffffffffu, cty, g),
-                            gz = __shfl_sync(0xffffffffu, ctz, g);
-                if (any_mi) search(std::true_type{}, glo, ghi, gcode, gx, gy, gz);
-                else search(std::false_type{}, glo, ghi, gcode, gx, gy, gz);
+            if constexpr (kList) {
+                // the listed slots, kListBatch x 32 at a time: all their list entries are loaded,
+                // then all their positions, so that the loads overlap; nearest image by compare
+                // and select (positions lie in [0, l)); then the same compaction and evaluation
+                const int nn = la.nnb[u];
+                const int* row = la.nbr + (int64_t)u * la.cap;
+                const float hx = 0.5f * Lf[0], hy = 0.5f * Lf[1], hz = 0.5f * Lf[2];
+                for (int k0 = 0; k0 < nn; k0 += 32 * kListBatch) {
+                    int sj[kListBatch];
+                    float4 o[kListBatch];
+#pragma unroll
+                    for (int a = 0; a < kListBatch; ++a) {
+                        const int k = k0 + 32 * a + lane;
+                        sj[a] = row[k < nn ? k : nn - 1];
+                    }
+#pragma unroll
+                    for (int a = 0; a < kListBatch; ++a) o[a] = spos32[sj[a]];
+#pragma unroll
+                    for (int a = 0; a < kListBatch; ++a) {
+                        const int k = k0 + 32 * a + lane;
+                        float dx = o[a].x - me.x, dy = o[a].y - me.y, dz = o[a].z - me.z;
+                        dx = dx > hx ? dx - Lf[0] : (dx < -hx ? dx + Lf[0] : dx);
+                        dy = dy > hy ? dy - Lf[1] : (dy < -hy ? dy + Lf[1] : dy);
+                        dz = dz > hz ? dz - Lf[2] : (dz < -hz ? dz + Lf[2] : dz);
+                        const bool hit = k < nn && dx * dx + dy * dy + dz * dz < rc2_pass;
+                        const unsigned m = __ballot_sync(0xffffffffu, hit);
+                        if (hit) {
+                            const int p = nh + __popc(m & ((1u << lane) - 1u));
+                            if constexpr (kF64) hits[wib][p] = make_int2(sj[a], 1 | (1 << 2) | (1 << 4));  // no shift
+                            else hits[wib][p] = make_float4(dx, dy, dz, o[a].w);
+                        }
+                        nh += __popc(m);
+                    }
+                    // evaluate whole groups of 32 and keep the rest at the front
+                    __syncwarp();
+                    int b0 = 0;
+                    for (; b0 + 32 <= nh; b0 += 32) evaluate(32, b0);
+                    __syncwarp();
+                    if (b0 > 0 && lane < nh - b0) hits[wib][lane] = hits[wib][b0 + lane];
+                    __syncwarp();
+                    nh -= b0;
+                }
+            } else {
+                const bool any_mi = mi[0] || mi[1] || mi[2];
+                for (int g = 0; g < 18; ++g) {
+                    const int glo = __shfl_sync(0xffffffffu, lo, g), ghi = __shfl_sync(0xffffffffu, hi, g);
+                    if (glo >= ghi) continue;  // the same for every lane
+                    const int gcode = __shfl_sync(0xffffffffu, code, g);
+                    const float gx = __shfl_sync(0xffffffffu, ctx, g), gy = __shfl_sync(0xffffffffu, cty, g),
+                                gz = __shfl_sync(0xffffffffu, ctz, g);
+                    if (any_mi) search(std::true_type{}, glo, ghi, gcode, gx, gy, gz);
+                    else search(std::false_type{}, glo, ghi, gcode, gx, gy, gz);
+                }
+            }
+            if constexpr (kBuild) {
+                if (lane == 0) {
+                    la.nnb[u] = nh < la.cap ? nh : la.cap;
+                    la.sref[u] = make_float4(me.x * invLf[0], me.y * invLf[1], me.z * invLf[2], 0.f);
+                    if (nh > la.cap) atomicOr(la.status, kStatusList);
+                }
+                continue;
             }
             __syncwarp();
             evaluate(nh);
@@ -734,17 +924,42 @@ k_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, const i
                 el += __shfl_xor_sync(0xffffffffu, el, off);
             }
             if (lane == 0) {
-                Fr[3 * (int64_t)i] = (double)fx;
-                Fr[3 * (int64_t)i + 1] = (double)fy;
-                Fr[3 * (int64_t)i + 2] = (double)fz;
-                wsum += 0.5 * (double)w;
-                ecsum += 0.5 * (double)ec;
-                elsum += 0.5 * (double)el;
+                if constexpr (kF64) {
+                    Fr[3 * (int64_t)i] = fx;
+                    Fr[3 * (int64_t)i + 1] = fy;
+                    Fr[3 * (int64_t)i + 2] = fz;
+                    wsum += 0.5 * w;
+                    ecsum += 0.5 * ec;
+                    elsum += 0.5 * el;
+                } else {
+                    // exact widening by integer operations
+                    unsigned long long* Fb = reinterpret_cast<unsigned long long*>(Fr);
+                    Fb[3 * (int64_t)i] = float_to_double_bits(__float_as_uint(fx));
+                    Fb[3 * (int64_t)i + 1] = float_to_double_bits(__float_as_uint(fy));
+                    Fb[3 * (int64_t)i + 2] = float_to_double_bits(__float_as_uint(fz));
+                    ff_add(wh, wl, 0.5f * w);
+                    ff_add(ech, ecl, 0.5f * ec);
+                    ff_add(elh, ell, 0.5f * el);
+                }
             }
         }
     }
+    if constexpr (kBuild) {
+        // the build's box; the list now stands until the next check says otherwise (a build
+        // without a cell list leaves the list pending)
+        if (cells_ok && blockIdx.x == 0 && threadIdx.x == 0) {
+            for (int t = 0; t < 3; ++t) la.nls->Lref[t] = cc->L[t];
+            la.nls->force = 0;
+        }
+        return;
+    }
     // fixed-order block sums
     if (lane == 0) {
+        if (!kF64) {
+            wsum = (double)wh + (double)wl;
+            ecsum = (double)ech + (double)ecl;
+            elsum = (double)elh + (double)ell;
+        }
         red[0][wib] = wsum;
         red[1][wib] = ecsum;
         red[2][wib] = elsum;
@@ -872,8 +1087,9 @@ static int pair_blocks(rbe_ctx ctx, int64_t N, bool fp64)
     return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->num_sms * per_sm));
 }
 
-// Grow the NPT scratch for N particles and a box whose edges may double.
-static rbe_status npt_ensure(rbe_ctx ctx, int64_t N, const double box[3], double rc)
+// Grow the NPT scratch for N particles and a box whose edges may double; with skin > 0 also
+// the neighbour list (twice the expected neighbours at the initial density, plus 64).
+static rbe_status npt_ensure(rbe_ctx ctx, int64_t N, const double box[3], double rc, double skin)
 {
     NptBuffers& b = ctx->npt;
     cudaError_t e;
@@ -926,6 +1142,27 @@ static rbe_status npt_ensure(rbe_ctx ctx, int64_t N, const double box[3], double
             return npt_fail(ctx, e, "cudaMalloc(cells)");
         b.cellcap = (int)cells;
     }
+    if (skin > 0.0) {
+        if (!b.nls && (e = ctx_alloc(ctx, reinterpret_cast<NListState**>(&b.nls), sizeof(NListState))) != cudaSuccess)
+            return npt_fail(ctx, e, "cudaMalloc(list state)");
+        const double rl = rc + skin, V = box[0] * box[1] * box[2];
+        const double expect = 4.0 / 3.0 * 3.14159265358979323846 * rl * rl * rl * (double)N / V;
+        const double capd = std::ceil((2.0 * expect + 64.0) / 32.0) * 32.0;
+        if (!(capd <= 65536.0)) return fail(ctx, RBE_EINVAL, "neighbour list too long: reduce rc + skin");
+        const int cap = (int)capd;
+        const int64_t entries = (int64_t)cap * N;
+        if (entries > b.nl_entries || N > b.ncap_list) {
+            ctx_free(ctx, b.nbr); ctx_free(ctx, b.nnb); ctx_free(ctx, b.sref);
+            b.nbr = nullptr; b.nnb = nullptr; b.sref = nullptr; b.nl_entries = 0; b.ncap_list = 0;
+            if ((e = ctx_alloc(ctx, &b.nbr, sizeof(int) * entries)) != cudaSuccess ||
+                (e = ctx_alloc(ctx, &b.nnb, sizeof(int) * N)) != cudaSuccess ||
+                (e = ctx_alloc(ctx, &b.sref, sizeof(float4) * N)) != cudaSuccess)
+                return npt_fail(ctx, e, "cudaMalloc(neighbour list)");
+            b.nl_entries = entries;
+            b.ncap_list = N;
+        }
+        b.nbr_cap = cap;
+    }
     const int need = pair_blocks(ctx, N, false) + (int)((N + kNptThreads - 1) / kNptThreads);
     if (need > b.partcap) {
         ctx_free(ctx, b.partials);
@@ -961,25 +1198,54 @@ static rbe_status npt_forces(rbe_ctx ctx, rbe_system* sys, uint64_t batch, int d
             return st;
     }
     if (prm.real && N > 0) {
-        cudaError_t e = cudaMemsetAsync(b.cnt, 0, sizeof(int) * b.cellcap, s);
-        if (e != cudaSuccess) return npt_fail(ctx, e, "cudaMemsetAsync(cells)");
-        const CellConsts* cc = static_cast<const CellConsts*>(b.cellc);
-        k_cl_count<<<nb, kNptThreads, 0, s>>>(N, sys->pos, cc, b.cid, b.cnt, ctx->d.status);
-        k_cl_scan<<<1, kScanThreads, 0, s>>>(cc, b.cnt, b.start, b.cursor);
-        k_cl_fill<<<nb, kNptThreads, 0, s>>>(N, b.cid, b.cursor, b.fill);
         const bool fp64 = ctx->precision == RBE_FP64;
         if (fp64 && b.n64 < N) return fail(ctx, RBE_ESTATE, "precision changed to FP64 after rbe_npt_init: call it again");
+        const bool list = prm.skin > 0.0;
+        if (list && (!b.nls || b.ncap_list < N)) return fail(ctx, RBE_ESTATE, "skin changed after rbe_npt_init: call it again");
+        NListState* nls = list ? static_cast<NListState*>(b.nls) : nullptr;
+        const CellConsts* cc = static_cast<const CellConsts*>(b.cellc);
+        if (list) {
+            const int grid = (int)std::min<int64_t>(nb, (int64_t)ctx->num_sms * 4);
+            if (fp64)
+                k_nl_check<true><<<grid, kNptThreads, 0, s>>>(N, sys->pos, sys->charge, b.sorted, b.spos32, b.spos64,
+                                                            b.sref, cc, nls);
+            else
+                k_nl_check<false><<<grid, kNptThreads, 0, s>>>(N, sys->pos, sys->charge, b.sorted, b.spos32, nullptr,
+                                                             b.sref, cc, nls);
+        }
+        cudaError_t e = cudaMemsetAsync(b.cnt, 0, sizeof(int) * b.cellcap, s);
+        if (e != cudaSuccess) return npt_fail(ctx, e, "cudaMemsetAsync(cells)");
+        k_cl_count<<<nb, kNptThreads, 0, s>>>(N, sys->pos, cc, b.cid, b.cnt, ctx->d.status, nls);
+        k_cl_scan<<<1, kScanThreads, 0, s>>>(cc, b.cnt, b.start, b.cursor, nls);
+        k_cl_fill<<<nb, kNptThreads, 0, s>>>(N, b.cid, b.cursor, b.fill, nls);
         const int64_t sort_blocks = ((int64_t)b.cellcap + kSortWarps - 1) / kSortWarps;
         k_cl_sort<<<(unsigned)sort_blocks, kSortWarps * 32, 0, s>>>(cc, b.cnt, b.start, b.fill,
                                                                   b.sorted, sys->pos, sys->charge, b.spos32,
-                                                                  fp64 ? b.spos64 : nullptr);
+                                                                  fp64 ? b.spos64 : nullptr, nls);
         const PairConst pc = make_pair_const(prm.rc, ctx->alpha, prm.qqr2e, prm.lj_sigma, prm.lj_eps);
-        if (fp64)
-            k_pair<true><<<nbp, kPairWarps * 32, 0, s>>>(N, cc, pc, b.cid, b.cnt, b.start, b.sorted,
-                                                         b.spos32, b.spos64, b.Fr, b.partials);
-        else
-            k_pair<false><<<nbp, kPairWarps * 32, 0, s>>>(N, cc, pc, b.cid, b.cnt, b.start, b.sorted,
-                                                          b.spos32, nullptr, b.Fr, b.partials);
+        const ListArgs la{nls, b.nbr, b.nnb, b.sref, ctx->d.status, b.nbr_cap};
+        const double4_32a* s64 = fp64 ? b.spos64 : nullptr;
+        auto pair = [&](auto f64_tag, auto mode_tag) {
+            constexpr bool F64 = decltype(f64_tag)::value;
+            constexpr int MODE = decltype(mode_tag)::value;
+            k_pair<F64, MODE><<<nbp, kPairWarps * 32, 0, s>>>(N, cc, pc, b.cid, b.cnt, b.start, b.sorted, b.spos32,
+                                                              s64, b.Fr, b.partials, la);
+        };
+        using T = std::true_type;
+        using F = std::false_type;
+        using Cells = std::integral_constant<int, kPairCells>;
+        using Build = std::integral_constant<int, kPairBuild>;
+        using List = std::integral_constant<int, kPairList>;
+        if (!list) {
+            if (fp64) pair(T{}, Cells{});
+            else pair(F{}, Cells{});
+        } else if (fp64) {
+            pair(T{}, Build{});
+            pair(T{}, List{});
+        } else {
+            pair(F{}, Build{});
+            pair(F{}, List{});
+        }
         if ((st = npt_check(ctx, "real-space kernels")) != RBE_OK) return st;
     }
     k_npt_finish<<<std::max(1, nb), kNptThreads, 0, s>>>(N, sys->mom, sys->force, b.mprop, b.Fk, b.Fr, b.WEk,
@@ -996,7 +1262,7 @@ static rbe_status npt_validate(rbe_ctx ctx, const rbe_system* sys)
     if (!sys->pos || !sys->mom || !sys->force || !sys->charge || !sys->mass || !sys->cell)
         return fail(ctx, RBE_EINVAL, "system buffers must not be NULL");
     if (!(p.dt > 0.0) || !(p.kT >= 0.0) || !(p.gamma >= 0.0) || !(p.gamma_V >= 0.0) || !(p.rc > 0.0) ||
-        !(p.max_disp >= 0.0) || (p.barostat && !(p.M_V > 0.0)))
+        !(p.max_disp >= 0.0) || (p.barostat && !(p.M_V > 0.0)) || !(p.skin >= 0.0) || !std::isfinite(p.skin))
         return fail(ctx, RBE_EINVAL, "invalid NPT parameters");
     if ((sys->step >> 56) != 0) return fail(ctx, RBE_EINVAL, "step must be < 2^56");
     return RBE_OK;
@@ -1023,7 +1289,7 @@ rbe_status npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch)
     if (st != RBE_OK) return st;
     double box[3];
     if ((st = npt_box_check(ctx, sys, box)) != RBE_OK) return st;
-    if ((st = npt_ensure(ctx, sys->N, box, sys->params.rc)) != RBE_OK) return st;
+    if ((st = npt_ensure(ctx, sys->N, box, sys->params.rc, sys->params.skin)) != RBE_OK) return st;
     // tables for boxes up to twice as long as the initial one
     int need = 0;
     for (int t = 0; t < 3; ++t) {
@@ -1037,7 +1303,12 @@ rbe_status npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch)
     NptBuffers& b = ctx->npt;
     k_mass_props<<<(unsigned)((sys->N + kNptThreads - 1) / kNptThreads), kNptThreads, 0, ctx->stream>>>(
         sys->N, sys->mass, b.mprop);
-    k_cell_consts<<<1, 32, 0, ctx->stream>>>(sys->cell, sys->params.rc, b.cellcap, static_cast<CellConsts*>(b.cellc));
+    const double skin = sys->params.skin > 0.0 ? sys->params.skin : 0.0;
+    k_cell_consts<<<1, 32, 0, ctx->stream>>>(sys->cell, sys->params.rc, sys->params.rc + skin, b.cellcap,
+                                             static_cast<CellConsts*>(b.cellc));
+    if (skin > 0.0)
+        k_nl_init<<<1, 32, 0, ctx->stream>>>(static_cast<NListState*>(b.nls), (float)(sys->params.rc + skin),
+                                             (float)sys->params.rc);
     k_npt_set_step<<<1, 32, 0, ctx->stream>>>(sys->cell, batch);
     if ((st = npt_check(ctx, "k_npt_set_step")) != RBE_OK) return st;
     st = npt_forces(ctx, sys, batch, 0);

@@ -85,7 +85,8 @@ static rbe_status sfail(rbe_server_s* s, rbe_status st, const std::string& msg)
 // Device bytes a replica of N particles holds while resident: its state (r, p, F: 72 B;
 // q, m: 16 B), the context's NPT scratch (k-space and real-space forces 48 B, cell list
 // 12 B, packed positions 16 B FP32 + 32 B FP64), the cell arrays (12 B per cell for edges up to twice the
-// initial box) and a fixed allowance for tables, frequency buffers and partial sums.
+// initial box), the neighbour list when the request uses one, and a fixed allowance for
+// tables, frequency buffers and partial sums.
 static int64_t replica_bytes(const rbe_request& r, int P)
 {
     int64_t cells = 1;
@@ -93,7 +94,14 @@ static int64_t replica_bytes(const rbe_request& r, int P)
         const double f = std::floor(2.0 * r.box[t] / r.params.rc);
         cells *= f >= 1.0 ? (f <= 4096.0 ? (int64_t)f : 4096) : 1;
     }
-    return r.N * (72 + 16 + 48 + 12 + 48) + 12 * cells + (int64_t)(P + 1) * 16 * 2048 + (4 << 20);
+    int64_t list = 0;  // neighbour list (skin > 0): entries per particle as rbe_npt_init sizes them
+    if (r.params.skin > 0.0) {
+        const double rl = r.params.rc + r.params.skin, V = r.box[0] * r.box[1] * r.box[2];
+        const double expect = 4.0 / 3.0 * 3.14159265358979323846 * rl * rl * rl * (double)r.N / V;
+        const int64_t cap = (int64_t)(std::ceil((2.0 * expect + 64.0) / 32.0) * 32.0);
+        list = r.N * (4 * cap + 4 + 16);
+    }
+    return r.N * (72 + 16 + 48 + 12 + 48) + 12 * cells + list + (int64_t)(P + 1) * 16 * 2048 + (4 << 20);
 }
 
 static void release_slot(rbe_server_s* s, Slot& sl)
