@@ -84,9 +84,9 @@ static rbe_status sfail(rbe_server_s* s, rbe_status st, const std::string& msg)
 
 // Device bytes a replica of N particles holds while resident: its state (r, p, F: 72 B;
 // q, m: 16 B), the context's NPT scratch (k-space and real-space forces 48 B, cell list
-// 12 B, packed positions 16 B FP32 + 32 B FP64), the cell arrays (12 B per cell for edges up to twice the
-// initial box), the neighbour list when the request uses one, and a fixed allowance for
-// tables, frequency buffers and partial sums.
+// 12 B, packed positions 16 B FP32 + 32 B FP64), the cell arrays (12 B per cell for edges
+// up to twice the initial box), the neighbour list when the request uses one, and a fixed
+// allowance for tables, frequency buffers and partial sums.
 static int64_t replica_bytes(const rbe_request& r, int P)
 {
     int64_t cells = 1;
