@@ -251,6 +251,7 @@ def run_ours(args, world, rank, local):
     serving = None if args.skip_serving else run_serving(args, world, rank)
     npt1 = None if args.skip_serving else run_npt_single(rbe, [1000, 10000, 100000], 20)
     batched = None if args.skip_serving else run_batched(rbe)
+    sweep = None if args.skip_sweep else run_sweep(rbe)
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
@@ -278,6 +279,8 @@ def run_ours(args, world, rank, local):
         line["serving"] = serving
     if batched:
         line["batched_kspace"] = batched
+    if sweep:
+        line["sweep"] = sweep
     if npt1:
         line["npt_one_replica"] = {"system": "jittered-lattice +-1 charges at 0.1/A^3, P=100, rc=7, Langevin NPT",
                                    "launch": "direct, one stream", "by_N": npt1}
@@ -423,6 +426,66 @@ def run_batched(rbe, n_items=64, P=100, iters=20):
     return out
 
 
+def run_sweep(rbe, steps=3):
+    """Large-N precision and roofline sweep: N in {1e5, 1e6, 4e6} uniform +-1 charges at 0.1 per
+    A^3, P in {100, 500, 2000}; the FP32-phase path with each rho accumulation (FP32 within a
+    tile, compensated FP32, FP64) and the FP64 path; pair evaluations/s (CUDA events, L2
+    flushed between steps), the MUFU fraction of the FP32-phase passes, and the errors of each
+    FP32-phase variant against the FP64 path on the same frequencies (forces: relative RMS;
+    virial: relative Frobenius; Pxx/Pyy/Pzz: largest relative error; E_k: relative)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    peak = rbe.rbe_measure_pipe(0, 4096)
+    out = []
+    for N in (100_000, 1_000_000, 4_000_000):
+        s = inputs.uniform_density(N)
+        pos = torch.as_tensor(s.pos).to(dev)
+        q = torch.as_tensor(s.q).to(dev)
+        F = torch.empty((N, 3), dtype=torch.float64, device=dev)
+        W = torch.empty(9, dtype=torch.float64, device=dev)
+        E = torch.empty(2, dtype=torch.float64, device=dev)
+        for P in (100, 500, 2000):
+            row = {"N": N, "P": P}
+            ref = None
+            variants = [("fp64", rbe.RBE_FP64, rbe.RBE_RHO_FP32), ("fp32_rho_fp32", rbe.RBE_FP32_PHASE, rbe.RBE_RHO_FP32),
+                        ("fp32_rho_comp32", rbe.RBE_FP32_PHASE, rbe.RBE_RHO_COMP32),
+                        ("fp32_rho_fp64", rbe.RBE_FP32_PHASE, rbe.RBE_RHO_FP64)]
+            for name, prec, acc in variants:
+                with rbe.Context(s.box, s.alpha, P, SEED, prec, acc, stream=stream.cuda_stream) as ctx:
+                    n = 1 if (prec == rbe.RBE_FP64 and N * P > 1e9) else steps
+                    ctx.forces_virial(pos, q, 7, F, W, E)  # warm-up
+                    ms = []
+                    for k in range(n):
+                        flush.fill_(float(k))
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        ctx.forces_virial(pos, q, 7, F, W, E)  # the same frequencies every time
+                        e1.record(stream)
+                        ms.append((e0, e1))
+                    torch.cuda.synchronize()
+                    ctx.sync()
+                    t = float(np.mean([a.elapsed_time(b) for a, b in ms])) * 1e-3
+                    r = {"pair_evals_per_s": N * P / t, "ms": t * 1e3}
+                    if prec != rbe.RBE_FP64:
+                        r["mufu_frac_of_measured"] = 4.0 * N * P / t / peak
+                    if ref is None:
+                        ref = (F.cpu().numpy(), W.cpu().numpy().reshape(3, 3), E.cpu().numpy())
+                    else:
+                        F1, W1, E1 = F.cpu().numpy(), W.cpu().numpy().reshape(3, 3), E.cpu().numpy()
+                        F0, W0, E0 = ref
+                        r["force_rel_rms"] = float(np.sqrt(np.mean((F1 - F0) ** 2) / np.mean(F0 ** 2)))
+                        r["virial_rel"] = float(np.linalg.norm(W1 - W0) / np.linalg.norm(W0))
+                        r["pressure_diag_rel_max"] = float(np.max(np.abs(np.diag(W1) - np.diag(W0)) / np.abs(np.diag(W0))))
+                        r["energy_rel"] = float(abs(E1[0] - E0[0]) / abs(E0[0]))
+                    row[name] = r
+            out.append(row)
+        del pos, q, F
+    return {"system": "uniform +-1 charges at 0.1 per A^3, alpha = 0.2", "steps": steps,
+            "mufu_peak_measured": peak, "points": out}
+
+
 def run_serving(args, world, rank):
     """Requests of Poisson arrivals at 20/s, N log-uniform in [1e3, 1e5] at 0.1 per A^3,
     P = 100, 100 NPT steps each, chunks of 10 steps: closed-loop capacity and open-loop
@@ -520,6 +583,8 @@ def main():
     ap.add_argument("--serve-fp64-sample", type=int, default=16)
     ap.add_argument("--profile-npt", type=int, default=0, help="time only NPT steps of one replica of this N")
     ap.add_argument("--profile-batched", action="store_true", help="time only the batched k-space evaluation")
+    ap.add_argument("--skip-sweep", action="store_true", help="leave out the large-N precision and roofline sweep")
+    ap.add_argument("--profile-sweep", action="store_true", help="run only the large-N sweep")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -533,6 +598,12 @@ def main():
         ms = npt_single(rbe, args.profile_npt, prec, args.steps, args.warmup)
         print(json.dumps({"metric": "NPT steps of one replica", "value": 1e3 / ms, "unit": "replica-steps/s",
                           "ms_per_step": ms, "N": args.profile_npt, "precision": args.precision}), flush=True)
+        return
+    if args.profile_sweep:
+        import torch
+        import paper_2110_14362_gb300 as rbe
+        torch.cuda.set_device(local)
+        print(json.dumps({"metric": "large-N sweep", "sweep": run_sweep(rbe, steps=args.steps)}), flush=True)
         return
     if args.profile_batched:
         # profiling aid: only the batched-versus-loop k-space measurement
