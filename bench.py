@@ -477,7 +477,9 @@ def run_sweep(rbe, steps=3):
                         F0, W0, E0 = ref
                         r["force_rel_rms"] = float(np.sqrt(np.mean((F1 - F0) ** 2) / np.mean(F0 ** 2)))
                         r["virial_rel"] = float(np.linalg.norm(W1 - W0) / np.linalg.norm(W0))
-                        r["pressure_diag_rel_max"] = float(np.max(np.abs(np.diag(W1) - np.diag(W0)) / np.abs(np.diag(W0))))
+                        dW = np.abs(np.diag(W1) - np.diag(W0))
+                        r["pressure_diag_rel_max"] = float(np.max(dW / np.abs(np.diag(W0))))
+                        r["pressure_diag_err_over_max_diag"] = float(np.max(dW) / np.max(np.abs(np.diag(W0))))
                         r["energy_rel"] = float(abs(E1[0] - E0[0]) / abs(E0[0]))
                     row[name] = r
             out.append(row)
