@@ -42,7 +42,7 @@ MUFU_OPS_PER_PAIR_PASS = 2.0
 # DRAM bytes per launch of the dominant kernel measured by ncu on this workload
 # (dram__bytes_read.sum + dram__bytes_write.sum), or None when not captured for the
 # current kernel version.  Source: profiles/ summaries.
-NCU_TRAFFIC = {("k_force", "slab"): 9648896, ("k_rho", "slab"): 9620480}
+NCU_TRAFFIC = {("k_force", "slab"): 9649664, ("k_rho", "slab"): 9626880}
 
 
 def workload(name: str):
