@@ -1,4 +1,5 @@
-// RBE k-space kernels for sm_103a and their launchers.
+// RBE k-space kernels for sm_103a and their launchers (the FP32-phase bodies live in
+// rbe_kspace_tiles.cuh, shared with the batched kernels of rbe_batch.cu).
 //
 // One evaluation (Sec. 4.2 of the paper) is up to five launches on the context's stream:
 //   k_tables   per-axis weights exp(-c m^2) as exact integers, their cumulative sums, H,
@@ -11,7 +12,8 @@
 //                                              Eq. (apppress); App. C Eq. (pressuretensorflexible)
 //   k_force_*  particle tiles x all frequencies: F_i                             Eq. (appforce)
 // No floating-point atomics: every sum runs in an order fixed by (N, K, plan), so
-// results are bitwise reproducible run to run.
+// results are bitwise reproducible run to run.  The host-buffer call can run the passes in
+// two particle groups with its copies pipelined (launch_evaluate_staged).
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -1,13 +1,18 @@
 // Isotropic Langevin NPT step on the device (Sec. 3.2-3.3 of the paper) with RBE k-space
-// forces (rbe_kspace.cu) and a nearest-image real space on a deterministic cell list.
+// forces (rbe_kspace.cu) and a nearest-image real space on a deterministic cell list, with or
+// without a neighbour list.
 //
 // One step is a fixed sequence of launches on the context's stream:
 //   k_npt_cell_a   one warp: V^p/2, the sub-step coefficients, V/2, O^p, V/2 (new box),
 //                  and the cell-list constants of the new box
 //   k_npt_drift    particles: R^p/2, R/2, O, R/2, wrap into the new box
 //   k-space        tables for the new box, sampler, rho, reduction, force pass
+//   k_nl_check     (neighbour list) packed positions in the list's order, largest
+//                  displacement since the build, rebuild decision on the device
 //   cell list      count, scan, fill, per-cell sort (deterministic order), packed positions
-//   k_pair         real-space forces, virial trace and energies (one warp per particle)
+//                  (with a list: only on rebuild steps; the launches exit at once otherwise)
+//   k_pair         real-space forces, virial trace and energies (one warp per particle):
+//                  from a cell search, or the list build (rebuild steps) and the list
 //   k_npt_finish   F = qqr2e F_k + F_r, R^p/2, kinetic sum; last block: P_ins and V^p/2
 // Nothing leaves the device between steps; the step index drives the RBE batch and noise.
 #include <cuda_runtime.h>
