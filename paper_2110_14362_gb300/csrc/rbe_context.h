@@ -159,6 +159,7 @@ rbe_status launch_tables(rbe_ctx ctx, const double* box_dev);
 rbe_status ensure_k_capacity(rbe_ctx ctx, int K);
 rbe_status launch_sample(rbe_ctx ctx, uint64_t step, int P);
 rbe_status launch_sample_device_box(rbe_ctx ctx, uint64_t step, int P, const unsigned long long* step_dev);
+rbe_status launch_tables_sample_device(rbe_ctx ctx, int P, const double* box_dev, const unsigned long long* step_dev);
 rbe_status npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch);
 rbe_status npt_run(rbe_ctx ctx, rbe_system* sys, int32_t nsteps);
 rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int K,

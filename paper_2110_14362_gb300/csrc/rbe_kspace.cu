@@ -37,6 +37,20 @@ k_tables(double bx, double by, double bz, const double* __restrict__ box_dev, do
     tables_body(bx, by, bz, box_dev, alpha, P, cum, cap, ks, status);
 }
 
+// Tables of the device box and the sampler in one block (the NPT step, where the box changes
+// every step): one launch instead of two, the tables read back from this block's own writes.
+__global__ void __launch_bounds__(kTableThreads)
+k_tables_sample(const double* __restrict__ box_dev, double alpha, int P, unsigned long long* __restrict__ cum,
+                int cap, int smem_cap, KState* __restrict__ ks, uint64_t seed,
+                const unsigned long long* __restrict__ step_dev, int4* __restrict__ m_out,
+                double* __restrict__ w_out, unsigned* __restrict__ status)
+{
+    tables_body(0.0, 0.0, 0.0, box_dev, alpha, P, cum, cap, ks, status);
+    __syncthreads();
+    for (int lb = 0; lb < P; lb += kTableThreads)
+        sample_body(lb, seed, 0, step_dev, P, cum, cap, smem_cap, ks, m_out, w_out, status);
+}
+
 // Frequency sampling, one thread per frequency (body in rbe_kspace_tiles.cuh).
 __global__ void k_sample(uint64_t seed, uint64_t step_arg, const unsigned long long* __restrict__ step_dev, int P,
                          const unsigned long long* __restrict__ cum, int cap, int smem_cap,
@@ -434,6 +448,22 @@ rbe_status launch_sample_device_box(rbe_ctx ctx, uint64_t step, int P, const uns
         ctx->d.status);
     record_event(ctx, 1);
     return check_launch(ctx, "k_sample");
+}
+
+// The NPT step's tables (from the device box) and sampler (at the device step index) in one
+// launch.
+rbe_status launch_tables_sample_device(rbe_ctx ctx, int P, const double* box_dev, const unsigned long long* step_dev)
+{
+    rbe_status st = ensure_k_capacity(ctx, P);
+    if (st != RBE_OK) return st;
+    record_event(ctx, 0);
+    const size_t smem = sizeof(unsigned long long) * 3 * (size_t)ctx->d.tab_cap;
+    const int smem_cap = smem <= (size_t)kSampleSmemMax ? ctx->d.tab_cap : 0;
+    k_tables_sample<<<1, kTableThreads, smem_cap ? smem : 0, ctx->stream>>>(
+        box_dev, ctx->alpha, P, ctx->d.cum, ctx->d.tab_cap, smem_cap, ctx->d.ks, ctx->seed, step_dev, ctx->d.m,
+        ctx->d.w, ctx->d.status);
+    record_event(ctx, 1);
+    return check_launch(ctx, "k_tables_sample");
 }
 
 rbe_status launch_weights_from_list(rbe_ctx ctx, int K, const int32_t* m, const double* w)

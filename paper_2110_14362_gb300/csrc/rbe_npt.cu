@@ -3,7 +3,7 @@
 // without a neighbour list.
 //
 // One step is a fixed sequence of launches on the context's stream:
-//   k_npt_cell_a   one warp: V^p/2, the sub-step coefficients, V/2, O^p, V/2 (new box),
+//   k_npt_cell_a   one block: V^p/2, the sub-step coefficients, V/2, O^p, V/2 (new box),
 //                  and the cell-list constants of the new box
 //   k_npt_drift    particles: R^p/2, R/2, O, R/2, wrap into the new box
 //   k-space        tables for the new box, sampler, rho, reduction, force pass
@@ -245,100 +245,108 @@ __global__ void k_npt_set_step(double* __restrict__ cell, uint64_t step)
     if (threadIdx.x == 0 && blockIdx.x == 0) cell[kCellStep] = __longlong_as_double((long long)step);
 }
 
-__global__ void __launch_bounds__(32)
+constexpr int kCellWarps = 4;  // k_npt_cell_a: warps
+
+__global__ void __launch_bounds__(kCellWarps * 32)
 k_npt_cell_a(double* __restrict__ cell, NptCoef* __restrict__ cf, rbe_npt_params prm, uint64_t seed, int cellcap,
              CellConsts* __restrict__ cc)
 {
-    // One warp.  The chain p_V -> box -> p_V -> box runs on lane 0; the exponentials of the
-    // sub-step coefficients and the cell noise, independent of one another, run on other
-    // lanes (single FP64 chains are slow on this GPU, parallel ones are not).
+    // The chain p_V -> box -> p_V -> box runs on warp 0; the exponentials of the sub-step
+    // coefficients and the cell noise, independent of one another, run on warps 1..3 (lane 0
+    // of each), i.e. on other SM sub-partitions: a single FP64 chain is slow on this GPU,
+    // parallel ones are not.  The arithmetic is the same as one thread doing it all.
     __shared__ double sh[24];
-    const int lane = threadIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t step = cell_step(cell);
     const double h = 0.5 * prm.dt;
     const double MV = prm.M_V;
     if (lane == 0) {
-        double L[3] = {cell[0], cell[1], cell[2]};
-        double V = L[0] * L[1] * L[2];
-        double pV = prm.barostat ? cell[3] : 0.0;
-        const double W = cell[4], K2 = cell[5];
-        if (prm.barostat) pV += h * ((K2 + W) / (3.0 * V) - prm.P_ext);
-        sh[0] = prm.barostat ? pV / (3.0 * MV * V) : 0.0;  // eps for the first R^p/2
-        if (prm.barostat) {
-            const double Vn = V + h * pV / MV;
-            const double f = cbrt(Vn / V);
-            for (int t = 0; t < 3; ++t) L[t] *= f;
-            V = L[0] * L[1] * L[2];
-        }
-        sh[1] = prm.barostat ? pV / (3.0 * MV * V) : 0.0;  // eps for the first R/2
-        sh[2] = pV;
-        sh[3] = L[0];
-        sh[4] = L[1];
-        sh[5] = L[2];
-        sh[6] = V;
-    } else if (lane == 1) {
-        // O^p: friction factor and the noise term of the cell
-        double gV = 1.0, nz = 0.0;
-        if (prm.barostat) {
-            gV = exp(-prm.gamma_V * prm.dt);
-            if (prm.noise) {
-                double z[4];
-                npt_normals(seed, 2u, step, 0u, z);
-                nz = sqrt(prm.kT * MV * (1.0 - gV * gV)) * z[0];
+        if (warp == 0) {
+            double L[3] = {cell[0], cell[1], cell[2]};
+            double V = L[0] * L[1] * L[2];
+            double pV = prm.barostat ? cell[3] : 0.0;
+            const double W = cell[4], K2 = cell[5];
+            if (prm.barostat) pV += h * ((K2 + W) / (3.0 * V) - prm.P_ext);
+            sh[0] = prm.barostat ? pV / (3.0 * MV * V) : 0.0;  // eps for the first R^p/2
+            if (prm.barostat) {
+                const double Vn = V + h * pV / MV;
+                const double f = cbrt(Vn / V);
+                for (int t = 0; t < 3; ++t) L[t] *= f;
+                V = L[0] * L[1] * L[2];
             }
+            sh[1] = prm.barostat ? pV / (3.0 * MV * V) : 0.0;  // eps for the first R/2
+            sh[2] = pV;
+            sh[3] = L[0];
+            sh[4] = L[1];
+            sh[5] = L[2];
+            sh[6] = V;
+        } else if (warp == 1) {
+            // O^p: friction factor and the noise term of the cell
+            double gV = 1.0, nz = 0.0;
+            if (prm.barostat) {
+                gV = exp(-prm.gamma_V * prm.dt);
+                if (prm.noise) {
+                    double z[4];
+                    npt_normals(seed, 2u, step, 0u, z);
+                    nz = sqrt(prm.kT * MV * (1.0 - gV * gV)) * z[0];
+                }
+            }
+            sh[7] = gV;
+            sh[8] = nz;
+        } else if (warp == 2) {
+            const double g = exp(-prm.gamma * prm.dt);
+            const double og = prm.kT * kFConv * (1.0 - g * g);
+            sh[9] = g;
+            sh[10] = og;
+            sh[11] = sqrt(og);
         }
-        sh[7] = gV;
-        sh[8] = nz;
-    } else if (lane == 2) {
-        const double g = exp(-prm.gamma * prm.dt);
-        const double og = prm.kT * kFConv * (1.0 - g * g);
-        sh[9] = g;
-        sh[10] = og;
-        sh[11] = sqrt(og);
     }
-    __syncwarp();
+    __syncthreads();
     if (lane == 0) {
-        double L[3] = {sh[3], sh[4], sh[5]};
-        double V = sh[6], pV = sh[2];
-        if (prm.barostat) {
-            pV *= sh[7];
-            if (prm.noise) pV += sh[8];
+        if (warp == 0) {
+            double L[3] = {sh[3], sh[4], sh[5]};
+            double V = sh[6], pV = sh[2];
+            if (prm.barostat) {
+                pV *= sh[7];
+                if (prm.noise) pV += sh[8];
+            }
+            sh[12] = prm.barostat ? pV / (3.0 * MV * V) : 0.0;  // eps for the second R/2
+            if (prm.barostat) {
+                const double Vn = V + h * pV / MV;
+                const double f = cbrt(Vn / V);
+                for (int t = 0; t < 3; ++t) L[t] *= f;
+                V = L[0] * L[1] * L[2];
+            }
+            sh[13] = prm.barostat ? pV / (3.0 * MV * V) : 0.0;  // eps for the second R^p/2
+            sh[2] = pV;
+            sh[3] = L[0];
+            sh[4] = L[1];
+            sh[5] = L[2];
+            sh[6] = V;
+        } else if (warp == 1) {
+            sh[14] = exp(-sh[0] * h);
+            sh[15] = expm1_over(-sh[0] * h, h);
+        } else if (warp == 2) {
+            sh[16] = exp(sh[1] * h) - 1.0;
+        } else {
+            sh[17] = expm1_over(sh[1] * h, h);
         }
-        sh[12] = prm.barostat ? pV / (3.0 * MV * V) : 0.0;  // eps for the second R/2
-        if (prm.barostat) {
-            const double Vn = V + h * pV / MV;
-            const double f = cbrt(Vn / V);
-            for (int t = 0; t < 3; ++t) L[t] *= f;
-            V = L[0] * L[1] * L[2];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        write_cell_consts(lane, sh + 3, prm.rc, prm.rc + (prm.skin > 0.0 ? prm.skin : 0.0), cellcap, cc);
+    } else if (lane == 0) {
+        if (warp == 1) {
+            sh[18] = exp(sh[12] * h) - 1.0;
+            sh[19] = expm1_over(sh[12] * h, h);
+        } else if (warp == 2) {
+            sh[20] = exp(-sh[13] * h);
+        } else {
+            sh[21] = expm1_over(-sh[13] * h, h);
         }
-        sh[13] = prm.barostat ? pV / (3.0 * MV * V) : 0.0;  // eps for the second R^p/2
-        sh[2] = pV;
-        sh[3] = L[0];
-        sh[4] = L[1];
-        sh[5] = L[2];
-        sh[6] = V;
-    } else if (lane == 1) {
-        sh[14] = exp(-sh[0] * h);
-    } else if (lane == 2) {
-        sh[15] = expm1_over(-sh[0] * h, h);
-    } else if (lane == 3) {
-        sh[16] = exp(sh[1] * h) - 1.0;
-    } else if (lane == 4) {
-        sh[17] = expm1_over(sh[1] * h, h);
     }
-    __syncwarp();
-    if (lane == 1) {
-        sh[18] = exp(sh[12] * h) - 1.0;
-    } else if (lane == 2) {
-        sh[19] = expm1_over(sh[12] * h, h);
-    } else if (lane == 3) {
-        sh[20] = exp(-sh[13] * h);
-    } else if (lane == 4) {
-        sh[21] = expm1_over(-sh[13] * h, h);
-    }
-    write_cell_consts(lane, sh + 3, prm.rc, prm.rc + (prm.skin > 0.0 ? prm.skin : 0.0), cellcap, cc);  // syncs
-    __syncwarp();
-    if (lane == 0) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
         NptCoef c;
         c.a1 = sh[14];
         c.b1 = sh[15];
@@ -1192,13 +1200,13 @@ static rbe_status npt_forces(rbe_ctx ctx, rbe_system* sys, uint64_t batch, int d
     const int nbp = pair_blocks(ctx, N, ctx->precision == RBE_FP64);
     rbe_status st;
     if (prm.kspace) {
-        // tables from the device box, then the evaluation
-        if ((st = launch_tables(ctx, sys->cell)) != RBE_OK) return st;
-        ctx->tables_dirty = true;  // the snapshot API must rebuild from its own box
-        if ((st = ensure_k_capacity(ctx, ctx->P)) != RBE_OK) return st;
-        if ((st = launch_sample_device_box(ctx, batch, ctx->P,
-                                           reinterpret_cast<const unsigned long long*>(sys->cell + kCellStep))) != RBE_OK)
+        // tables from the device box and the sampler (one launch), then the evaluation
+        (void)batch;  // the batch index is the device-resident step index (set by the caller)
+        if ((st = launch_tables_sample_device(ctx, ctx->P, sys->cell,
+                                              reinterpret_cast<const unsigned long long*>(sys->cell + kCellStep))) !=
+            RBE_OK)
             return st;
+        ctx->tables_dirty = true;  // the snapshot API must rebuild from its own box
         if ((st = launch_evaluate(ctx, N, sys->pos, sys->charge, ctx->P, true, b.Fk, b.WEk, b.WEk + 9)) != RBE_OK)
             return st;
     }
@@ -1335,7 +1343,7 @@ rbe_status npt_run(rbe_ctx ctx, rbe_system* sys, int32_t nsteps)
     const NptBuffers& b = ctx->npt;
     for (int32_t k = 0; k < nsteps; ++k) {
         const uint64_t step = sys->step;
-        k_npt_cell_a<<<1, 32, 0, s>>>(sys->cell, cf, sys->params, ctx->seed, b.cellcap,
+        k_npt_cell_a<<<1, kCellWarps * 32, 0, s>>>(sys->cell, cf, sys->params, ctx->seed, b.cellcap,
                                       static_cast<CellConsts*>(b.cellc));
         if (ctx->precision == RBE_FP64)
             k_npt_drift<false><<<nb, kNptThreads, 0, s>>>(N, sys->pos, sys->mom, sys->force, b.mprop, cf, ctx->seed,
