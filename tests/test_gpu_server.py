@@ -1,6 +1,7 @@
 """GPU tests of the serving loop (rbe_server_*): a replica's result does not depend on what
 else is resident, graph replay equals direct launches, admission respects the memory budget,
 and the served FP64 trajectory matches the oracle's NPT step (Sec. 3.2-3.3)."""
+import sys
 import time
 
 import numpy as np
@@ -31,11 +32,20 @@ def _system(n_side, seed, density=0.1):
     return pos, mom, q, m, np.array([L, L, L])
 
 
+SKIN = 0.0  # set per test: 0 = cell search every step, > 0 = neighbour list
+
+
 def _base(box, rc=6.0):
     V0 = float(np.prod(box))
     return dict(dt=0.001, kT=oracle.KB * 300.0, P_ext=1.0 * oracle.BAR, gamma=10.0, gamma_V=2.0,
                 M_V=oracle.piston_mass(0.5, 4.5e-5 / oracle.BAR, V0), rc=rc, qqr2e=oracle.QQR2E, lj_sigma=2.0,
                 lj_eps=0.5, max_disp=0.05, kspace=1, real=1, noise=1, barostat=1)
+
+
+def _dev_params(box):
+    prm = rbe.NptParams(**_base(box))
+    prm.skin = SKIN
+    return prm
 
 
 REQS = [  # (n_side, seed of the system, Philox seed, steps)
@@ -57,7 +67,7 @@ def _serve(reqs, precision, max_slots, chunk_steps=4, use_graphs=True, mem_budge
         for i in (order if order is not None else range(len(reqs))):
             n_side, sseed, pseed, nsteps = reqs[i]
             pos, mom, q, m, box = _system(n_side, sseed)
-            ids[i] = srv.submit(pos, mom, q, m, box, rbe.NptParams(**_base(box)), pseed, nsteps)
+            ids[i] = srv.submit(pos, mom, q, m, box, _dev_params(box), pseed, nsteps)
         t_end = time.monotonic() + DEADLINE_S
         peak = 0
         while True:
@@ -79,7 +89,7 @@ def _direct(req, precision):
     n_side, sseed, pseed, nsteps = req
     pos, mom, q, m, box = _system(n_side, sseed)
     with rbe.Context(box, ALPHA, P, pseed, precision) as ctx:
-        rep = rbe.NptReplica(pos, mom, q, m, box, rbe.NptParams(**_base(box)), cuda_device(), step=0)
+        rep = rbe.NptReplica(pos, mom, q, m, box, _dev_params(box), cuda_device(), step=0)
         rep.init(ctx, batch=0)
         rep.step(ctx, nsteps)
         ctx.sync()
@@ -144,3 +154,14 @@ def test_served_fp64_matches_oracle():
     d -= st.L * np.round(d / st.L)
     assert np.abs(d).max() < 1e-10 * st.L[0]
     assert np.abs(p - st.p).max() < 1e-10 * np.abs(st.p).max()
+
+
+@pytest.mark.parametrize("precision", [rbe.RBE_FP64, rbe.RBE_FP32_PHASE])
+def test_served_with_neighbour_lists(precision, monkeypatch):
+    """With neighbour lists (rebuilt on the device when needed): served == direct steps and a
+    request alone == the same request in a mix, bit for bit, as for the cell search."""
+    monkeypatch.setattr(sys.modules[__name__], "SKIN", 0.5)
+    mixed, _ = _serve(REQS, precision, max_slots=4, order=[3, 0, 1, 2])
+    alone = _serve([REQS[1]], precision, max_slots=1)[0][0]
+    _same(mixed[1], alone)
+    _same(mixed[0], _direct(REQS[0], precision))
