@@ -264,3 +264,20 @@ def test_nonfinite_input_is_reported():
         # the context stays usable and clean afterwards
         F, W, E = ctx.forces_virial_host(s.pos, s.q, 0)
         assert np.all(np.isfinite(F))
+
+
+def test_water_charges_parity():
+    """The 3000-molecule water charge set (9000 partial charges at 1 g/cm^3, alpha = 0.25,
+    P = 100): FP64 path at 1e-10 and FP32-phase path at 1e-5 against the oracle on the same
+    frequencies."""
+    s = inputs.water()
+    m, S = oracle.sample_k(s.box, s.alpha, s.P, SEED, 11)
+    F0, W0, Ek0, Es0, _ = oracle.rbe_kspace(s.pos, s.q, s.box, s.alpha, m, S / s.P)
+    F, W, E, _ = _run(s, s.P, 11, rbe.RBE_FP64)
+    assert rel_max_force(F, F0) <= 1e-10
+    assert rel_frob(W, W0) <= 1e-10
+    assert abs(E[0] - Ek0) <= 1e-10 * abs(Ek0) and abs(E[1] - Es0) <= 1e-12 * abs(Es0)
+    F, W, E, _ = _run(s, s.P, 11, rbe.RBE_FP32_PHASE)
+    assert rel_rms_force(F, F0) <= 1e-5
+    assert rel_frob(W, W0) <= 1e-5
+    assert abs(E[0] - Ek0) <= 1e-5 * abs(Ek0)
