@@ -99,7 +99,7 @@ class NptParams(ctypes.Structure):
                 ("lj_sigma", ctypes.c_double), ("lj_eps", ctypes.c_double), ("max_disp", ctypes.c_double),
                 ("P", ctypes.c_int32), ("kspace", ctypes.c_int32), ("real", ctypes.c_int32),
                 ("noise", ctypes.c_int32), ("barostat", ctypes.c_int32), ("pad", ctypes.c_int32),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("M_cell", ctypes.c_double * 3), ("gamma0", ctypes.c_double)]
 
 
 def _bind_npt(lib):
@@ -120,6 +120,17 @@ def _bind_npt(lib):
                                 _c_double_p, _c_double_p, _c_double_p, ctypes.c_uint64, ctypes.c_int32, P,
                                 _c_double_p, _c_double_p, _c_double_p]
     lib.orc_npt_run.restype = ctypes.c_int
+    lib.orc_npt_forces_diag.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p, ctypes.c_uint64, P,
+                                        _c_double_p, _c_double_p, _c_double_p]
+    lib.orc_npt_forces_diag.restype = ctypes.c_int
+    lib.orc_npt_step_rect.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p, _c_double_p,
+                                      _c_double_p, _c_double_p, _c_double_p, _c_double_p, ctypes.c_uint64, P,
+                                      _c_double_p]
+    lib.orc_npt_step_rect.restype = ctypes.c_int
+    lib.orc_npt_run_rect.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p, _c_double_p,
+                                     _c_double_p, _c_double_p, _c_double_p, _c_double_p, ctypes.c_uint64,
+                                     ctypes.c_int32, P, _c_double_p, _c_double_p, _c_double_p]
+    lib.orc_npt_run_rect.restype = ctypes.c_int
 
 
 def _dp(a):
@@ -279,14 +290,32 @@ def npt_params(**kw) -> NptParams:
     1 bar, dt = 1 fs, gamma = 10/ps, gamma_V = 2/ps, alpha = 0.2, rc = 7, LJ 2 A / 0.5 kJ/mol."""
     d = dict(dt=0.001, kT=KB * 300.0, P_ext=1.0 * BAR, gamma=10.0, gamma_V=2.0, M_V=1.0, alpha=0.2, rc=7.0,
              qqr2e=QQR2E, lj_sigma=2.0, lj_eps=0.5, max_disp=0.0, P=100, kspace=1, real=1, noise=1,
-             barostat=1, pad=0, seed=1)
+             barostat=1, pad=0, seed=1, M_cell=(1.0, 1.0, 1.0), gamma0=0.0)
     d.update(kw)
+    d["M_cell"] = (ctypes.c_double * 3)(*[float(x) for x in d["M_cell"]])
     return NptParams(**d)
 
 
 def piston_mass(tau_p: float, beta_T: float, V0: float) -> float:
     """M = tau_P^2 / (4 pi^2 beta_T V0): a harmonic volume oscillation of period tau_P (reading 13)."""
     return tau_p ** 2 / (4.0 * np.pi ** 2 * beta_T * V0)
+
+
+def piston_masses_rect(mode: int, tau_p: float, beta_T: float, box) -> tuple:
+    """Cell masses of the rectangular barostats for a harmonic oscillation of period tau_P of
+    each cell variable, taking a strain of one axis (or of the area) to change its pressure
+    by the relative volume change over beta_T: anisotropic (mode 2) M_j = V tau^2 /
+    (4 pi^2 beta_T l_j^2); semi-isotropic (mode 3) M_A = L tau^2 / (4 pi^2 beta_T A) in [0],
+    M_L = A tau^2 / (4 pi^2 beta_T L) in [2]."""
+    lx, ly, lz = (float(x) for x in box)
+    c = tau_p ** 2 / (4.0 * np.pi ** 2 * beta_T)
+    V = lx * ly * lz
+    if mode == 2:
+        return (c * V / lx ** 2, c * V / ly ** 2, c * V / lz ** 2)
+    if mode == 3:
+        A = lx * ly
+        return (c * lz / A, 0.0, c * A / lz)
+    raise ValueError("mode must be 2 (anisotropic) or 3 (semi-isotropic)")
 
 
 def npt_normals(seed: int, stream: int, step: int, index: int):
@@ -352,6 +381,50 @@ def npt_run(st: NptState, step0: int, nsteps: int, prm: NptParams):
                                ctypes.byref(st.pV), ctypes.byref(st.W), step0, nsteps, ctypes.byref(prm), _dp(V),
                                _dp(Pi), _dp(H)), "npt_run")
     return V, Pi, H
+
+
+class NptRectState:
+    """Oracle state of the rectangular-cell NPT step: positions, momenta, forces, box, cell
+    momenta pc[3] and the virial diagonal Wd[3] at the current positions."""
+
+    def __init__(self, r, p, q, m, L, pc=(0.0, 0.0, 0.0)):
+        self.r = _f64(r).copy()
+        self.p = _f64(p).copy()
+        self.q = _f64(q)
+        self.m = _f64(m)
+        self.L = _f64(L, (3,)).copy()
+        self.F = np.zeros_like(self.r)
+        self.pc = _f64(pc, (3,)).copy()
+        self.Wd = np.zeros(3)
+
+    @property
+    def N(self):
+        return self.q.shape[0]
+
+
+def npt_forces_rect(st: NptRectState, step: int, prm: NptParams):
+    E = np.zeros(3)
+    _check(_load().orc_npt_forces_diag(st.N, _dp(st.r), _dp(st.q), _dp(st.L), step, ctypes.byref(prm), _dp(st.F),
+                                       _dp(st.Wd), _dp(E)), "npt_forces_diag")
+    return E
+
+
+def npt_step_rect(st: NptRectState, step: int, prm: NptParams):
+    E = np.zeros(3)
+    _check(_load().orc_npt_step_rect(st.N, _dp(st.r), _dp(st.p), _dp(st.F), _dp(st.q), _dp(st.m), _dp(st.L),
+                                     _dp(st.pc), _dp(st.Wd), step, ctypes.byref(prm), _dp(E)), "npt_step_rect")
+    return E
+
+
+def npt_run_rect(st: NptRectState, step0: int, nsteps: int, prm: NptParams):
+    """nsteps steps; returns (box[n,3], diagonal pressure[n,3], extended energy[n])."""
+    L = np.zeros((nsteps, 3))
+    Pd = np.zeros((nsteps, 3))
+    H = np.zeros(nsteps)
+    _check(_load().orc_npt_run_rect(st.N, _dp(st.r), _dp(st.p), _dp(st.F), _dp(st.q), _dp(st.m), _dp(st.L),
+                                    _dp(st.pc), _dp(st.Wd), step0, nsteps, ctypes.byref(prm), _dp(L), _dp(Pd),
+                                    _dp(H)), "npt_run_rect")
+    return L, Pd, H
 
 
 def ewald_total(pos, q, box, alpha: float, rc: float, kmax: int):

@@ -60,9 +60,13 @@ typedef struct {
     int32_t kspace;   /* 1: RBE k-space forces and virial */
     int32_t real;     /* 1: erfc Coulomb + LJ real space */
     int32_t noise;    /* 1: Langevin noise in O and O^p */
-    int32_t barostat; /* 1: the cell moves (V^p, V, O^p); 0: V fixed, p_V = 0 */
+    int32_t barostat; /* 1: the cell moves (V^p, V, O^p); 0: V fixed, p_V = 0;
+                         2: rectangular cell, anisotropic; 3: semi-isotropic (orc_npt_step_rect) */
     int32_t pad;
     uint64_t seed;
+    double M_cell[3]; /* barostat 2: masses of l_x, l_y, l_z (kJ/mol ps^2/A^2);
+                         barostat 3: M_A (kJ/mol ps^2/A^4) in [0], M_L (kJ/mol ps^2/A^2) in [2] */
+    double gamma0;    /* barostat 3: surface tension times the number of surfaces, kJ/mol/A^2 */
 } orc_npt_params;
 
 /* ------------------------------------------------------------------------------ */
@@ -129,16 +133,18 @@ int orc_pair_real(int64_t N, const double* pos, const double* q, const double bo
     return NPT_OK;
 }
 
-/* Forces (kJ/mol/A) and the trace of the virial (kJ/mol) at the current state: RBE k-space
- * with the batch of `step` (Sec. 4.2 Eqs. (appforce), (apppress)) times qqr2e, plus the real
- * space.  Energies: E[0] k-space (incl. self), E[1] real Coulomb, E[2] Lennard-Jones. */
-int orc_npt_forces(int64_t N, const double* r, const double* q, const double L[3], uint64_t step,
-                   const orc_npt_params* prm, double* F, double* Wtr, double E[3])
+/* Forces (kJ/mol/A), the trace of the virial (kJ/mol) and, if Wd is given, its diagonal, at
+ * the current state: RBE k-space with the batch of `step` (Sec. 4.2 Eqs. (appforce),
+ * (apppress)) times qqr2e, plus the real space.  Energies: E[0] k-space (incl. self),
+ * E[1] real Coulomb, E[2] Lennard-Jones. */
+static int npt_forces_parts(int64_t N, const double* r, const double* q, const double L[3], uint64_t step,
+                            const orc_npt_params* prm, double* F, double* Wtr, double* Wd, double E[3])
 {
     double* Fk = (double*)calloc((size_t)(3 * N + 3), sizeof(double));
     if (!Fk) return NPT_ENOMEM;
     for (int64_t i = 0; i < 3 * N; ++i) F[i] = 0.0;
     double W = 0.0;
+    if (Wd) Wd[0] = Wd[1] = Wd[2] = 0.0;
     E[0] = E[1] = E[2] = 0.0;
     int st = NPT_OK;
     if (prm->kspace) {
@@ -157,6 +163,8 @@ int orc_npt_forces(int64_t N, const double* r, const double* q, const double L[3
         if (st == NPT_OK) {
             for (int64_t i = 0; i < 3 * N; ++i) F[i] += prm->qqr2e * Fk[i];
             W += prm->qqr2e * (Wk[0] + Wk[4] + Wk[8]);
+            if (Wd)
+                for (int t = 0; t < 3; ++t) Wd[t] = prm->qqr2e * Wk[4 * t];
             E[0] = prm->qqr2e * (Ek[0] + Ek[1]);
         }
         free(m);
@@ -168,6 +176,8 @@ int orc_npt_forces(int64_t N, const double* r, const double* q, const double L[3
         if (st == NPT_OK) {
             for (int64_t i = 0; i < 3 * N; ++i) F[i] += Fk[i];
             W += Wr[0] + Wr[4] + Wr[8];
+            if (Wd)
+                for (int t = 0; t < 3; ++t) Wd[t] += Wr[4 * t];
             E[1] = Er[0];
             E[2] = Er[1];
         }
@@ -175,6 +185,20 @@ int orc_npt_forces(int64_t N, const double* r, const double* q, const double L[3
     free(Fk);
     *Wtr = W;
     return st;
+}
+
+int orc_npt_forces(int64_t N, const double* r, const double* q, const double L[3], uint64_t step,
+                   const orc_npt_params* prm, double* F, double* Wtr, double E[3])
+{
+    return npt_forces_parts(N, r, q, L, step, prm, F, Wtr, NULL, E);
+}
+
+/* The same with the diagonal W_jj of the virial (k-space and real space) in Wd. */
+int orc_npt_forces_diag(int64_t N, const double* r, const double* q, const double L[3], uint64_t step,
+                        const orc_npt_params* prm, double* F, double Wd[3], double E[3])
+{
+    double Wtr;
+    return npt_forces_parts(N, r, q, L, step, prm, F, &Wtr, Wd, E);
 }
 
 /* ------------------------------------------------------------------------------ */
@@ -241,6 +265,7 @@ static void half_drift(int64_t N, double* r, const double* p, const double* m, d
 int orc_npt_step(int64_t N, double* r, double* p, double* F, const double* q, const double* m, double L[3],
                  double* pV, double* Wtr, uint64_t step, const orc_npt_params* prm, double E[3])
 {
+    if (prm->barostat < 0 || prm->barostat > 1) return NPT_EINVAL; /* rectangular cells: orc_npt_step_rect */
     const double h = 0.5 * prm->dt;
     double V = L[0] * L[1] * L[2];
     /* V^p/2 with the pressure of the current state */
@@ -319,6 +344,220 @@ int orc_npt_run(int64_t N, double* r, double* p, double* F, const double* q, con
         if (H_out)
             H_out[s] = 0.5 * K2 + E[0] + E[1] + E[2] + prm->P_ext * V +
                        (prm->barostat ? (*pV) * (*pV) / (2.0 * prm->M_V) : 0.0);
+    }
+    return NPT_OK;
+}
+
+/* ------------------------------------------------------------------------------ */
+/* Rectangular cell with per-axis fluctuation (appendix: the rectangular cell with
+ * anisotropic fluctuation, and the semi-isotropic constant surface-tension case).
+ *
+ * Anisotropic (barostat 2): h = diag(l_1, l_2, l_3), V = l_1 l_2 l_3,
+ *   dr_j/dt = p_j/m + eps_j r_j,   dp_j/dt = F_j - eps_j p_j - gamma p_j + noise,   eps_j = (dl_j/dt)/l_j,
+ *   dl_j/dt = pc_j / M_j,          dpc_j/dt = V ((P_ins)_jj - P) / l_j - gamma_V pc_j + sqrt(2 kT gamma_V M_j) xi_j,
+ * with (P_ins)_jj = (sum_i p_ij^2/m_i + W_jj) / V (the diagonal pressure of the rectangular
+ * cell).  Extended energy K + U + P V + sum_j pc_j^2 / (2 M_j).
+ *
+ * Semi-isotropic (barostat 3): h = diag(sqrt(A), sqrt(A), L) (a square cross-section, l_x = l_y),
+ *   eps_x = eps_y = (dA/dt)/(2A), eps_z = (dL/dt)/L,
+ *   dA/dt = p^A / M_A,   dp^A/dt = L (P_A - P) - gamma_V p^A + sqrt(2 kT gamma_V M_A) xi_A,
+ *   dL/dt = p^L / M_L,   dp^L/dt = A ((P_ins)_zz - P) - gamma_V p^L + sqrt(2 kT gamma_V M_L) xi_L,
+ * with P_A = ((P_ins)_xx + (P_ins)_yy)/2 + gamma0 / L.  Extended energy
+ * K + U + P A L - gamma0 A + (p^A)^2/(2 M_A) + (p^L)^2/(2 M_L).  One friction gamma_V serves
+ * both cell variables.
+ *
+ * Cell momenta pc[3]: anisotropic {pc_x, pc_y, pc_z}; semi-isotropic {p^A, 0, p^L}.  The
+ * splitting is the one of the isotropic step (Sec. 3.3) with the strain rate per axis:
+ *   V^p/2, R^p/2, V/2, R/2, O^p, O, R/2, V/2, [forces, W_jj], R^p/2, V^p/2,
+ * R and R^p solved exactly per axis with eps_j frozen; V/2 moves l_j (or A and L) linearly
+ * with pc frozen.  O^p draws the cell normals z[0..3] from the cell counter (stream 2) and
+ * gives slot j the normal z[j]. */
+static int rect_check(const double L[3], const orc_npt_params* prm)
+{
+    if (prm->barostat == 2) {
+        for (int j = 0; j < 3; ++j)
+            if (!(prm->M_cell[j] > 0.0)) return NPT_EINVAL;
+        return NPT_OK;
+    }
+    if (prm->barostat == 3) {
+        if (!(prm->M_cell[0] > 0.0) || !(prm->M_cell[2] > 0.0) || L[0] != L[1]) return NPT_EINVAL;
+        return NPT_OK;
+    }
+    return NPT_EINVAL;
+}
+
+/* eps_j = (dl_j/dt)/l_j for the current cell momenta and box */
+static void rect_eps(const double L[3], const double pc[3], const orc_npt_params* prm, double eps[3])
+{
+    if (prm->barostat == 2) {
+        for (int j = 0; j < 3; ++j) eps[j] = pc[j] / (prm->M_cell[j] * L[j]);
+    } else {
+        double A = L[0] * L[1];
+        eps[0] = eps[1] = pc[0] / (2.0 * prm->M_cell[0] * A);
+        eps[2] = pc[2] / (prm->M_cell[2] * L[2]);
+    }
+}
+
+static void kinetic2_axes(int64_t N, const double* p, const double* m, double K2[3])
+{
+    for (int j = 0; j < 3; ++j) {
+        double s = 0.0;
+        for (int64_t i = 0; i < N; ++i) s += p[3 * i + j] * p[3 * i + j] / m[i];
+        K2[j] = s / FCONV; /* sum_i p_ij^2 / m_i in kJ/mol */
+    }
+}
+
+/* V^p/2: the cell momenta take half a step of their force -dH/d(cell variable) */
+static void rect_kick_cell(double pc[3], const double L[3], const double K2[3], const double Wd[3],
+                           const orc_npt_params* prm)
+{
+    const double h = 0.5 * prm->dt;
+    if (prm->barostat == 2) {
+        double V = L[0] * L[1] * L[2];
+        for (int j = 0; j < 3; ++j) pc[j] += h * ((K2[j] + Wd[j] - prm->P_ext * V) / L[j]);
+    } else {
+        double A = L[0] * L[1];
+        /* L (P_A - P) = (2K_x + W_xx + 2K_y + W_yy) / (2A) - P L + gamma0 */
+        pc[0] += h * ((K2[0] + Wd[0] + K2[1] + Wd[1]) / (2.0 * A) - prm->P_ext * L[2] + prm->gamma0);
+        /* A ((P_ins)_zz - P) = (2K_z + W_zz) / L - P A */
+        pc[2] += h * ((K2[2] + Wd[2]) / L[2] - prm->P_ext * A);
+    }
+}
+
+/* V/2: the cell variables move with their momenta frozen */
+static void rect_move_cell(double L[3], const double pc[3], const orc_npt_params* prm)
+{
+    const double h = 0.5 * prm->dt;
+    if (prm->barostat == 2) {
+        for (int j = 0; j < 3; ++j) L[j] += h * pc[j] / prm->M_cell[j];
+    } else {
+        double A = L[0] * L[1] + h * pc[0] / prm->M_cell[0];
+        L[0] = L[1] = sqrt(A);
+        L[2] += h * pc[2] / prm->M_cell[2];
+    }
+}
+
+/* R^p/2 per axis: p_j <- p_j e^{-eps_j h} + 100 F_j (1 - e^{-eps_j h}) / eps_j */
+static void half_kick_particles_axes(int64_t N, double* p, const double* F, const double eps[3], double h)
+{
+    double a[3], b[3];
+    for (int j = 0; j < 3; ++j) {
+        a[j] = exp(-eps[j] * h);
+        b[j] = expm1_over(-eps[j] * h, h);
+    }
+    for (int64_t i = 0; i < N; ++i)
+        for (int j = 0; j < 3; ++j) p[3 * i + j] = p[3 * i + j] * a[j] + FCONV * F[3 * i + j] * b[j];
+}
+
+/* R/2 per axis: r_j <- r_j e^{eps_j h} + (p_j/m) (e^{eps_j h} - 1) / eps_j, with the cap */
+static void half_drift_axes(int64_t N, double* r, const double* p, const double* m, const double eps[3], double h,
+                            double cap)
+{
+    double a[3], b[3];
+    for (int j = 0; j < 3; ++j) {
+        a[j] = exp(eps[j] * h);
+        b[j] = expm1_over(eps[j] * h, h);
+    }
+    for (int64_t i = 0; i < N; ++i) {
+        double d[3];
+        for (int j = 0; j < 3; ++j) d[j] = r[3 * i + j] * (a[j] - 1.0) + (p[3 * i + j] / m[i]) * b[j];
+        if (cap > 0.0) {
+            double len = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            if (len > cap)
+                for (int j = 0; j < 3; ++j) d[j] *= cap / len;
+        }
+        for (int j = 0; j < 3; ++j) r[3 * i + j] += d[j];
+    }
+}
+
+/* One step of the rectangular cell.  State in/out: r, p, F (forces at r), L, pc, Wd (virial
+ * diagonal at r).  F and Wd must hold the values at the input state (orc_npt_forces_diag);
+ * on return they hold those of the new state, with the RBE batch of `step`. */
+int orc_npt_step_rect(int64_t N, double* r, double* p, double* F, const double* q, const double* m, double L[3],
+                      double pc[3], double Wd[3], uint64_t step, const orc_npt_params* prm, double E[3])
+{
+    int st = rect_check(L, prm);
+    if (st != NPT_OK) return st;
+    const double h = 0.5 * prm->dt;
+    double K2[3], eps[3];
+    /* V^p/2 with the pressure of the current state */
+    kinetic2_axes(N, p, m, K2);
+    rect_kick_cell(pc, L, K2, Wd, prm);
+    /* R^p/2 */
+    rect_eps(L, pc, prm, eps);
+    half_kick_particles_axes(N, p, F, eps, h);
+    /* V/2 */
+    rect_move_cell(L, pc, prm);
+    /* R/2 */
+    rect_eps(L, pc, prm, eps);
+    half_drift_axes(N, r, p, m, eps, h, 0.5 * prm->max_disp);
+    /* O^p */
+    {
+        double g = exp(-prm->gamma_V * prm->dt);
+        double z[4] = {0.0, 0.0, 0.0, 0.0};
+        if (prm->noise) orc_npt_normals(prm->seed, 2u, step, 0u, z);
+        for (int j = 0; j < 3; ++j) {
+            if (prm->barostat == 3 && j == 1) continue;
+            pc[j] *= g;
+            if (prm->noise) pc[j] += sqrt(prm->kT * prm->M_cell[j] * (1.0 - g * g)) * z[j];
+        }
+    }
+    /* O */
+    {
+        double g = exp(-prm->gamma * prm->dt);
+        for (int64_t i = 0; i < N; ++i) {
+            double z[4] = {0.0, 0.0, 0.0, 0.0};
+            if (prm->noise) orc_npt_normals(prm->seed, 1u, step, (uint32_t)i, z);
+            double s = sqrt(prm->kT * FCONV * m[i] * (1.0 - g * g));
+            for (int t = 0; t < 3; ++t) p[3 * i + t] = p[3 * i + t] * g + s * z[t];
+        }
+    }
+    /* R/2 */
+    rect_eps(L, pc, prm, eps);
+    half_drift_axes(N, r, p, m, eps, h, 0.5 * prm->max_disp);
+    /* V/2 */
+    rect_move_cell(L, pc, prm);
+    /* wrap into the new box */
+    for (int64_t i = 0; i < N; ++i)
+        for (int t = 0; t < 3; ++t) r[3 * i + t] -= L[t] * floor(r[3 * i + t] / L[t]);
+    /* forces and virial diagonal at the new state */
+    st = orc_npt_forces_diag(N, r, q, L, step, prm, F, Wd, E);
+    if (st != NPT_OK) return st;
+    /* R^p/2 */
+    rect_eps(L, pc, prm, eps);
+    half_kick_particles_axes(N, p, F, eps, h);
+    /* V^p/2 with the momenta after R^p/2 */
+    kinetic2_axes(N, p, m, K2);
+    rect_kick_cell(pc, L, K2, Wd, prm);
+    return NPT_OK;
+}
+
+/* n steps from step0; records per step the box (L_out, 3 per step), the diagonal pressure
+ * (P_out, 3 per step) and the extended energy (H_out), each optional. */
+int orc_npt_run_rect(int64_t N, double* r, double* p, double* F, const double* q, const double* m, double L[3],
+                     double pc[3], double Wd[3], uint64_t step0, int32_t nsteps, const orc_npt_params* prm,
+                     double* L_out, double* P_out, double* H_out)
+{
+    for (int32_t s = 0; s < nsteps; ++s) {
+        double E[3], K2[3];
+        int st = orc_npt_step_rect(N, r, p, F, q, m, L, pc, Wd, step0 + (uint64_t)s, prm, E);
+        if (st != NPT_OK) return st;
+        double V = L[0] * L[1] * L[2];
+        kinetic2_axes(N, p, m, K2);
+        for (int j = 0; j < 3; ++j) {
+            if (L_out) L_out[3 * s + j] = L[j];
+            if (P_out) P_out[3 * s + j] = (K2[j] + Wd[j]) / V;
+        }
+        if (H_out) {
+            double H = 0.5 * (K2[0] + K2[1] + K2[2]) + E[0] + E[1] + E[2] + prm->P_ext * V;
+            if (prm->barostat == 2) {
+                for (int j = 0; j < 3; ++j) H += pc[j] * pc[j] / (2.0 * prm->M_cell[j]);
+            } else {
+                H += -prm->gamma0 * L[0] * L[1] + pc[0] * pc[0] / (2.0 * prm->M_cell[0]) +
+                     pc[2] * pc[2] / (2.0 * prm->M_cell[2]);
+            }
+            H_out[s] = H;
+        }
     }
     return NPT_OK;
 }
