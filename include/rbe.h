@@ -184,26 +184,40 @@ rbe_status rbe_sample_k_noalloc(const double box[3], double alpha, int32_t P, ui
 rbe_status rbe_sync(rbe_ctx ctx);
 
 /* ---------------------------------------------------------------------------------
- * Isotropic Langevin NPT (Sec. 3.2 Eq. (24); Sec. 3.3 splitting
+ * Langevin NPT (Sec. 3.2 Eq. (24); Sec. 3.3 splitting
  *   V^p/2, R^p/2, V/2, R/2, O^p, O, R/2, V/2, [forces, P_ins], R^p/2, V^p/2
- * with the R and R^p flows solved exactly for frozen eps = p_V / (3 M V) and exact
+ * with the R and R^p flows solved exactly for frozen strain rates and exact
  * Ornstein--Uhlenbeck steps O, O^p).  Forces: the context's RBE k-space estimator (batch of
  * the step index, Sec. 4.2) times qqr2e, plus the nearest-image real space within rc:
  * qqr2e q_i q_j erfc(sqrt(alpha) r)/r + 4 eps ((sigma/r)^12 - (sigma/r)^6) (Sec. 4.1-4.2).
- * P_ins = (sum p^2/m + W_k + W_r) / (3V) (Sec. 4.1 Eq. (pressurecubic)).
  * Units: A, ps, g/mol, kJ/mol, e; momenta in g/mol A/ps (dp/dt = 100 F for F in kJ/mol/A);
- * pressure in kJ/mol/A^3; p_V in kJ/mol ps/A^3; M in kJ/mol ps^2/A^6.  The box scales
- * isotropically.  Noise: Philox-4x32-10 with the context's seed, counters
+ * pressure in kJ/mol/A^3.  Noise: Philox-4x32-10 with the context's seed, counters
  * (i, 0, step_lo, (1 << 24) | step_hi24) for particle i and (0, 0, step_lo, (2 << 24) |
  * step_hi24) for the cell, 32-bit uniforms (w + 1/2) 2^-32 and Box--Muller (the particle
- * normals in FP32 arithmetic on the FP32-phase path, FP64 otherwise). */
+ * normals in FP32 arithmetic on the FP32-phase path, FP64 otherwise).
+ *
+ * barostat 1, isotropic: the volume V with momentum p_V (kJ/mol ps/A^3) and mass M_V
+ *   (kJ/mol ps^2/A^6); eps = p_V / (3 M_V V) on every axis; P_ins = (sum p^2/m + W_k + W_r) / (3V)
+ *   (Sec. 4.1 Eq. (pressurecubic)); the box scales by (V'/V)^(1/3); the cell normal z[0].
+ * barostat 2, rectangular cell with anisotropic fluctuation (appendix): the edges l_j with
+ *   momenta pc_j (kJ/mol ps/A) and masses M_cell[j] (kJ/mol ps^2/A^2); eps_j = pc_j / (M_j l_j);
+ *   dpc_j/dt = V ((P_ins)_jj - P) / l_j - gamma_V pc_j + noise with (P_ins)_jj =
+ *   (sum_i p_ij^2/m_i + W_jj) / V, W_jj the diagonal of the k-space and real-space virials;
+ *   V/2 moves l_j by (dt/2) pc_j / M_j; slot j takes the cell normal z[j].
+ * barostat 3, semi-isotropic at constant surface tension (appendix): the area A = l_x l_y
+ *   (l_x = l_y required) with momentum pc_0 (kJ/mol ps/A^2) and mass M_cell[0]
+ *   (kJ/mol ps^2/A^4), the height L = l_z with momentum pc_2 and mass M_cell[2];
+ *   eps_x = eps_y = pc_0 / (2 M_A A), eps_z = pc_2 / (M_L L); dpc_0/dt = L (P_A - P) + noise,
+ *   P_A = ((P_ins)_xx + (P_ins)_yy)/2 + gamma0 / L; dpc_2/dt = A ((P_ins)_zz - P) + noise;
+ *   l_x = l_y = sqrt(A) after each move; the normals z[0] and z[2].
+ * gamma_V is the friction of every cell variable. */
 typedef struct {
     double dt;        /* time step, ps */
     double kT;        /* k_B T, kJ/mol */
     double P_ext;     /* external pressure, kJ/mol/A^3 */
     double gamma;     /* particle friction, 1/ps */
     double gamma_V;   /* cell friction, 1/ps */
-    double M_V;       /* piston mass, kJ/mol ps^2/A^6 (> 0 when barostat != 0) */
+    double M_V;       /* isotropic piston mass, kJ/mol ps^2/A^6 (> 0 when barostat == 1) */
     double rc;        /* real-space cutoff, A (rc <= box/2 on every axis) */
     double qqr2e;     /* Coulomb constant, kJ/mol A/e^2 */
     double lj_sigma;  /* A */
@@ -212,17 +226,28 @@ typedef struct {
     int32_t kspace;   /* 1: RBE k-space forces and virial */
     int32_t real;     /* 1: real-space forces and virial */
     int32_t noise;    /* 1: Langevin noise in O and O^p */
-    int32_t barostat; /* 1: the cell moves; 0: V fixed and p_V = 0 */
+    int32_t barostat; /* 0: the box is fixed; 1: isotropic; 2: anisotropic rectangular;
+                         3: semi-isotropic with surface tension */
     double skin;      /* A.  0: the real-space pairs come from a cell search every step.  > 0: from
                          a neighbour list of radius rc + skin, rebuilt on the device when the largest
                          displacement since the last build and the box change could have brought an
                          unlisted pair within rc (the same pairs either way) */
+    double M_cell[3]; /* barostat 2: masses of l_x, l_y, l_z (> 0); barostat 3: M_A in [0] and M_L
+                         in [2] (> 0), [1] unused */
+    double gamma0;    /* barostat 3: surface tension times the number of surfaces, kJ/mol/A^2 */
 } rbe_npt_params;
 
-/* Number of doubles of the device cell-state block: {l_x, l_y, l_z, p_V, W (virial trace at
- * the current positions), sum p^2/m /100 (= 2K), P_ins, E_k (k-space incl. self, x qqr2e),
- * E_coul (real space), E_lj, V, reserved...}. */
-#define RBE_CELL_DOUBLES 16
+/* Number of doubles of the device cell-state block:
+ *   [0..2]  l_x, l_y, l_z            [3]  p_V (barostat 1)
+ *   [4]     W, trace of the virial at the current positions (k-space x qqr2e + real space)
+ *   [5]     sum p^2/m / 100 (= 2K)   [6]  P_ins = (2K + W) / (3V)
+ *   [7]     E_k (k-space incl. self, x qqr2e)   [8] E_coul (real space)   [9] E_lj
+ *   [10]    V                        [11] step index (64-bit integer bits)
+ *   [12..14] cell momenta of barostats 2 and 3 (pc_x, pc_y, pc_z, or p^A, 0, p^L)
+ *   [16..18] W_xx, W_yy, W_zz        [19..21] sum_i p_ij^2/m_i / 100 per axis
+ *   [22..24] (P_ins)_xx, (P_ins)_yy, (P_ins)_zz   ([16..24] with barostat 2 and 3 only)
+ * the rest reserved. */
+#define RBE_CELL_DOUBLES 32
 
 /* One replica; every buffer is the caller's device memory.  `step` is the next step index
  * (the Philox counter of its RBE batch and noise); rbe_npt_step advances it. */
@@ -238,8 +263,9 @@ typedef struct {
     rbe_npt_params params;
 } rbe_system;
 
-/* Forces, virial trace and energies at the current state, with the RBE batch of index
- * `batch`; fills sys->force and cell[3..10] (p_V is kept).  Call once before the first step.
+/* Forces, virial and energies at the current state, with the RBE batch of index `batch`;
+ * fills sys->force, cell[4..10] and, with barostat 2 or 3, cell[16..24] (the cell momenta
+ * p_V and cell[12..14] are kept).  Call once before the first step.
  * Reads the initial box back (synchronises the context's stream) and sizes the per-axis
  * tables and the cell list for box edges up to twice the initial ones; a step whose box
  * leaves that range, or breaks rc <= l/2 with real space on, is flagged on the device and
@@ -346,6 +372,7 @@ typedef struct {
     int32_t nsteps;        /* steps to run, >= 1 */
     int32_t pad;
     rbe_npt_params params;
+    double pc[3];          /* initial cell momenta of barostats 2 and 3 (cell[12..14]) */
 } rbe_request;
 
 rbe_status rbe_server_create(const rbe_server_config* cfg, rbe_server* out);

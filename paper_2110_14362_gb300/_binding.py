@@ -35,7 +35,12 @@ class NptParams(ctypes.Structure):
                 ("rc", ctypes.c_double), ("qqr2e", ctypes.c_double), ("lj_sigma", ctypes.c_double),
                 ("lj_eps", ctypes.c_double), ("max_disp", ctypes.c_double), ("kspace", ctypes.c_int32),
                 ("real", ctypes.c_int32), ("noise", ctypes.c_int32), ("barostat", ctypes.c_int32),
-                ("skin", ctypes.c_double)]
+                ("skin", ctypes.c_double), ("M_cell", ctypes.c_double * 3), ("gamma0", ctypes.c_double)]
+
+    def __init__(self, **kw):
+        if "M_cell" in kw and not isinstance(kw["M_cell"], ctypes.Array):
+            kw["M_cell"] = (ctypes.c_double * 3)(*[float(x) for x in kw["M_cell"]])
+        super().__init__(**kw)
 
 
 class System(ctypes.Structure):
@@ -46,7 +51,10 @@ class System(ctypes.Structure):
                 ("cell", ctypes.c_void_p), ("step", ctypes.c_uint64), ("params", NptParams)]
 
 
-RBE_CELL_DOUBLES = 16
+RBE_CELL_DOUBLES = 32
+RBE_BAROSTAT_NONE, RBE_BAROSTAT_ISO, RBE_BAROSTAT_ANISO, RBE_BAROSTAT_SEMI = 0, 1, 2, 3
+# slots of the cell block (include/rbe.h)
+CELL_PC, CELL_WD, CELL_K2D, CELL_PD = 12, 16, 19, 22
 
 
 class BatchItem(ctypes.Structure):
@@ -65,7 +73,7 @@ class Request(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("pos", ctypes.c_void_p), ("mom", ctypes.c_void_p),
                 ("charge", ctypes.c_void_p), ("mass", ctypes.c_void_p), ("box", ctypes.c_double * 3),
                 ("pV", ctypes.c_double), ("seed", ctypes.c_uint64), ("nsteps", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("params", NptParams)]
+                ("pad", ctypes.c_int32), ("params", NptParams), ("pc", ctypes.c_double * 3)]
 
 # (name, restype, argtypes) of every exported symbol
 SIGNATURES = [
@@ -276,7 +284,8 @@ class NptReplica:
     """One device-resident NPT replica: torch CUDA tensors for r, p, F, q, m and the cell
     block, and the rbe_system that points at them."""
 
-    def __init__(self, pos, mom, charge, mass, box, params: NptParams, device, step: int = 0, pV: float = 0.0):
+    def __init__(self, pos, mom, charge, mass, box, params: NptParams, device, step: int = 0, pV: float = 0.0,
+                 pc=(0.0, 0.0, 0.0)):
         import torch
         f64 = torch.float64
         self.pos = torch.as_tensor(np.ascontiguousarray(pos), dtype=f64).to(device).contiguous()
@@ -287,6 +296,7 @@ class NptReplica:
         cell = np.zeros(RBE_CELL_DOUBLES)
         cell[:3] = np.asarray(box, dtype=np.float64).reshape(3)
         cell[3] = pV
+        cell[CELL_PC:CELL_PC + 3] = np.asarray(pc, dtype=np.float64).reshape(3)
         self.cell = torch.as_tensor(cell).to(device).contiguous()
         self.sys = System(N=int(self.charge.shape[0]), pos=self.pos.data_ptr(), mom=self.mom.data_ptr(),
                           force=self.force.data_ptr(), charge=self.charge.data_ptr(), mass=self.mass.data_ptr(),
@@ -386,6 +396,23 @@ def piston_mass(tau_P: float, beta_T: float, V0: float) -> float:
     return tau_P * tau_P / (4.0 * math.pi * math.pi * beta_T * V0)
 
 
+def piston_masses_rect(mode: int, tau_P: float, beta_T: float, box) -> tuple:
+    """Cell masses of the rectangular barostats (NptParams.M_cell) for a harmonic oscillation of
+    period tau_P (ps) of each cell variable, when a strain of one edge (or of the area) changes
+    the pressure on it by the relative volume change over beta_T (per kJ/mol/A^3).
+    Anisotropic (mode 2): M_j = V tau^2 / (4 pi^2 beta_T l_j^2).  Semi-isotropic (mode 3):
+    M_A = L tau^2 / (4 pi^2 beta_T A) in [0], M_L = A tau^2 / (4 pi^2 beta_T L) in [2]."""
+    lx, ly, lz = (float(x) for x in box)
+    c = tau_P * tau_P / (4.0 * math.pi * math.pi * beta_T)
+    if mode == RBE_BAROSTAT_ANISO:
+        V = lx * ly * lz
+        return (c * V / (lx * lx), c * V / (ly * ly), c * V / (lz * lz))
+    if mode == RBE_BAROSTAT_SEMI:
+        A = lx * ly
+        return (c * lz / A, 0.0, c * A / lz)
+    raise ValueError("mode must be RBE_BAROSTAT_ANISO or RBE_BAROSTAT_SEMI")
+
+
 class Server:
     """The C++ serving loop (rbe_server_*): submit requests, call progress() until all are
     done, read results and chunk-latency statistics."""
@@ -418,12 +445,14 @@ class Server:
         except Exception:
             pass
 
-    def submit(self, pos, mom, charge, mass, box, params: NptParams, seed: int, nsteps: int, pV: float = 0.0):
+    def submit(self, pos, mom, charge, mass, box, params: NptParams, seed: int, nsteps: int, pV: float = 0.0,
+               pc=(0.0, 0.0, 0.0)):
         arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (pos, mom, charge, mass)]
         req = Request(N=int(arrs[2].shape[0]), pos=arrs[0].ctypes.data, mom=arrs[1].ctypes.data,
                       charge=arrs[2].ctypes.data, mass=arrs[3].ctypes.data,
                       box=(ctypes.c_double * 3)(*[float(b) for b in box]), pV=float(pV), seed=int(seed),
-                      nsteps=int(nsteps), pad=0, params=params)
+                      nsteps=int(nsteps), pad=0, params=params,
+                      pc=(ctypes.c_double * 3)(*[float(x) for x in pc]))
         rid = ctypes.c_int64()
         self._check(load().rbe_server_submit(self.h, ctypes.byref(req), ctypes.byref(rid)))
         self._n[rid.value] = req.N

@@ -1,10 +1,12 @@
-// Isotropic Langevin NPT step on the device (Sec. 3.2-3.3 of the paper) with RBE k-space
+// Langevin NPT step on the device (Sec. 3.2-3.3 of the paper; the rectangular cell of the
+// appendix, anisotropic or semi-isotropic, by the same splitting per axis) with RBE k-space
 // forces (rbe_kspace.cu) and a nearest-image real space on a deterministic cell list, with or
 // without a neighbour list.
 //
 // One step is a fixed sequence of launches on the context's stream:
 //   k_npt_cell_a   one block: V^p/2, the sub-step coefficients, V/2, O^p, V/2 (new box),
-//                  and the cell-list constants of the new box
+//                  and the cell-list constants of the new box (k_npt_cell_rect for the
+//                  rectangular cell: the same per axis)
 //   k_npt_drift    particles: R^p/2, R/2, O, R/2, wrap into the new box
 //   k-space        tables for the new box, sampler, rho, reduction, force pass
 //   k_nl_check     (neighbour list) packed positions in the list's order, largest
@@ -37,17 +39,23 @@ constexpr int kPairBlocksPerSM = 4;  // k_pair (FP32): resident blocks per SM th
 constexpr int kPairBlocksPerSM64 = 2;  // k_pair (FP64): more registers per thread
 constexpr int kListBatch = 4;        // k_pair (list): list entries per lane loaded together
 constexpr int kHitCap = 32 * (kListBatch + 1);  // k_pair: buffered candidates per warp (< 32 + 32 kListBatch)
+// Per-block partial sums of the pair and finishing kernels: 8 doubles per block.  Isotropic:
+// finishing blocks {2K} at slot 0, pair blocks {W, E_coul, E_lj} at 1..3.  Rectangular cells:
+// finishing blocks {2K_x, 2K_y, 2K_z} at 0..2, pair blocks {W_xx, W_yy, W_zz, E_coul, E_lj} at 3..7.
+constexpr int kPartStride = 8;
 // rbe_npt_init sizes the per-axis tables and the cell list for box edges up to this many
 // times the initial ones; a box beyond it is flagged (RBE_ESTATE) by the step.
 constexpr double kBoxHeadroom = 2.0;
 
+// Sub-step coefficients of one step, per axis (the isotropic cell writes the same value on
+// every axis).
 struct NptCoef {
-    double a1, b1;      // R^p/2 before the forces: p <- a1 p + 100 F b1
-    double a2m1, b2;    // first R/2: r <- r + r (a2 - 1) + (p/m) b2
-    double g, og;       // O: p <- g p + sqrt(og m) z, og = 100 kT (1 - g^2)
-    double sog;         // sqrt(og): the O noise amplitude is sog sqrt(m)
-    double a3m1, b3;    // second R/2
-    double a4, b4;      // R^p/2 after the forces
+    double a1[3], b1[3];    // R^p/2 before the forces: p_j <- a1_j p_j + 100 F_j b1_j
+    double a2m1[3], b2[3];  // first R/2: r_j <- r_j + r_j (a2_j - 1) + (p_j/m) b2_j
+    double g, og;           // O: p <- g p + sqrt(og m) z, og = 100 kT (1 - g^2)
+    double sog;             // sqrt(og): the O noise amplitude is sog sqrt(m)
+    double a3m1[3], b3[3];  // second R/2
+    double a4[3], b4[3];    // R^p/2 after the forces
     double L[3];        // box after the second V/2
     double invL[3];     // 1 / L
     double half_cap;    // displacement cap per R/2
@@ -348,18 +356,18 @@ k_npt_cell_a(double* __restrict__ cell, NptCoef* __restrict__ cf, rbe_npt_params
     __syncthreads();
     if (threadIdx.x == 0) {
         NptCoef c;
-        c.a1 = sh[14];
-        c.b1 = sh[15];
-        c.a2m1 = sh[16];
-        c.b2 = sh[17];
         c.g = sh[9];
         c.og = sh[10];
         c.sog = sh[11];
-        c.a3m1 = sh[18];
-        c.b3 = sh[19];
-        c.a4 = sh[20];
-        c.b4 = sh[21];
         for (int t = 0; t < 3; ++t) {
+            c.a1[t] = sh[14];
+            c.b1[t] = sh[15];
+            c.a2m1[t] = sh[16];
+            c.b2[t] = sh[17];
+            c.a3m1[t] = sh[18];
+            c.b3[t] = sh[19];
+            c.a4[t] = sh[20];
+            c.b4[t] = sh[21];
             c.L[t] = sh[3 + t];
             c.invL[t] = cc->invL[t];
         }
@@ -373,6 +381,158 @@ k_npt_cell_a(double* __restrict__ cell, NptCoef* __restrict__ cf, rbe_npt_params
         cell[2] = sh[5];
         cell[3] = sh[2];
         cell[10] = sh[6];
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Cell-variable part of the step for the rectangular cell (appendix: barostat 2, the edges
+// l_j with momenta pc_j; barostat 3, the area A = l_x l_y and the height L), the splitting of
+// k_npt_cell_a with one strain rate per axis.  The chain of cell slot j (V^p/2, V/2, O^p,
+// V/2 with the strain rates between) runs on warp j (slots 0 and 2 when semi-isotropic); the
+// twelve exponentials of each stage (four per axis) run on warps 4..15, one each, since a
+// single FP64 chain is slow on this GPU and parallel ones are not.
+constexpr int kRectWarps = 16;
+constexpr int kCellPc = 12;   // cell momenta of the rectangular cell
+constexpr int kCellWd = 16;   // virial diagonal
+constexpr int kCellK2d = 19;  // sum p_j^2/m /100 per axis
+constexpr int kCellPd = 22;   // diagonal pressure
+
+// strain rate of slot j for cell momentum pc and edge l (semi-isotropic slot 0: A = l l)
+__device__ __forceinline__ double rect_eps(bool aniso, int j, double pc, double M, double l)
+{
+    return (aniso || j == 2) ? pc / (M * l) : pc / (2.0 * M * (l * l));
+}
+
+// V/2 of slot j: the edge (or the area, whose square root is the new edge) moves by h pc / M
+__device__ __forceinline__ double rect_move(bool aniso, int j, double pc, double M, double l, double h)
+{
+    return (aniso || j == 2) ? l + h * pc / M : sqrt(l * l + h * pc / M);
+}
+
+__global__ void __launch_bounds__(kRectWarps * 32)
+k_npt_cell_rect(double* __restrict__ cell, NptCoef* __restrict__ cf, rbe_npt_params prm, uint64_t seed, int cellcap,
+                CellConsts* __restrict__ cc)
+{
+    // shared: slot j at 8 j + {0 pc, 1 eps1, 2 eps2, 3 l', 4 eps3, 5 eps4, 6 l''}; 24..27 cell
+    // normals; 28 friction factor of O^p; 29..31 O coefficients; 32..55 the per-axis
+    // coefficients a1, b1, a2m1, b2, a3m1, b3, a4, b4 (3 each); 56..58 the new box
+    __shared__ double sh[64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t step = cell_step(cell);
+    const double h = 0.5 * prm.dt;
+    const bool aniso = prm.barostat == 2;
+    if (lane == 0) {
+        if (warp < 3) {
+            const int j = warp;
+            if (aniso || j != 1) {
+                // V^p/2 with the pressure of the current state, eps for R^p/2, V/2, eps for R/2
+                const double L0 = cell[0], L1 = cell[1], L2 = cell[2];
+                const double l = cell[j], M = prm.M_cell[j];
+                double pc = cell[kCellPc + j];
+                if (aniso) {
+                    const double V = L0 * L1 * L2;
+                    pc += h * ((cell[kCellK2d + j] + cell[kCellWd + j] - prm.P_ext * V) / l);
+                } else if (j == 0) {
+                    const double A = L0 * L1;
+                    pc += h * ((cell[kCellK2d] + cell[kCellWd] + cell[kCellK2d + 1] + cell[kCellWd + 1]) / (2.0 * A) -
+                               prm.P_ext * L2 + prm.gamma0);
+                } else {
+                    const double A = L0 * L1;
+                    pc += h * ((cell[kCellK2d + 2] + cell[kCellWd + 2]) / L2 - prm.P_ext * A);
+                }
+                const double ln = rect_move(aniso, j, pc, M, l, h);
+                sh[8 * j] = pc;
+                sh[8 * j + 1] = rect_eps(aniso, j, pc, M, l);
+                sh[8 * j + 2] = rect_eps(aniso, j, pc, M, ln);
+                sh[8 * j + 3] = ln;
+            }
+        } else if (warp == 3) {
+            const double g = exp(-prm.gamma * prm.dt);
+            const double og = prm.kT * kFConv * (1.0 - g * g);
+            sh[29] = g;
+            sh[30] = og;
+            sh[31] = sqrt(og);
+        } else if (warp == 4) {
+            double z[4] = {0.0, 0.0, 0.0, 0.0};
+            if (prm.noise) npt_normals(seed, 2u, step, 0u, z);
+            for (int t = 0; t < 4; ++t) sh[24 + t] = z[t];
+        } else if (warp == 5) {
+            sh[28] = exp(-prm.gamma_V * prm.dt);
+        }
+    }
+    __syncthreads();
+    if (lane == 0) {
+        if (warp < 3) {
+            const int j = warp;
+            if (aniso || j != 1) {
+                // O^p (slot j takes the cell normal z[j]), eps for R/2, V/2, eps for R^p/2
+                const double M = prm.M_cell[j], gV = sh[28];
+                double pc = sh[8 * j] * gV;
+                if (prm.noise) pc += sqrt(prm.kT * M * (1.0 - gV * gV)) * sh[24 + j];
+                const double l = sh[8 * j + 3];
+                const double ln = rect_move(aniso, j, pc, M, l, h);
+                sh[8 * j] = pc;
+                sh[8 * j + 4] = rect_eps(aniso, j, pc, M, l);
+                sh[8 * j + 5] = rect_eps(aniso, j, pc, M, ln);
+                sh[8 * j + 6] = ln;
+            }
+        } else if (warp >= 4) {
+            const int a = (warp - 4) >> 2, k = (warp - 4) & 3;
+            const int sl = (aniso || a != 1) ? a : 0;  // semi-isotropic: y moves with x
+            const double e1 = sh[8 * sl + 1], e2 = sh[8 * sl + 2];
+            if (k == 0) sh[32 + a] = exp(-e1 * h);
+            else if (k == 1) sh[35 + a] = expm1_over(-e1 * h, h);
+            else if (k == 2) sh[38 + a] = exp(e2 * h) - 1.0;
+            else sh[41 + a] = expm1_over(e2 * h, h);
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        if (lane == 0) {
+            sh[56] = sh[6];
+            sh[57] = aniso ? sh[14] : sh[6];
+            sh[58] = sh[22];
+        }
+        __syncwarp();
+        write_cell_consts(lane, sh + 56, prm.rc, prm.rc + (prm.skin > 0.0 ? prm.skin : 0.0), cellcap, cc);
+    } else if (lane == 0 && warp >= 4) {
+        const int a = (warp - 4) >> 2, k = (warp - 4) & 3;
+        const int sl = (aniso || a != 1) ? a : 0;
+        const double e3 = sh[8 * sl + 4], e4 = sh[8 * sl + 5];
+        if (k == 0) sh[44 + a] = exp(e3 * h) - 1.0;
+        else if (k == 1) sh[47 + a] = expm1_over(e3 * h, h);
+        else if (k == 2) sh[50 + a] = exp(-e4 * h);
+        else sh[53 + a] = expm1_over(-e4 * h, h);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        NptCoef c;
+        c.g = sh[29];
+        c.og = sh[30];
+        c.sog = sh[31];
+        for (int t = 0; t < 3; ++t) {
+            c.a1[t] = sh[32 + t];
+            c.b1[t] = sh[35 + t];
+            c.a2m1[t] = sh[38 + t];
+            c.b2[t] = sh[41 + t];
+            c.a3m1[t] = sh[44 + t];
+            c.b3[t] = sh[47 + t];
+            c.a4[t] = sh[50 + t];
+            c.b4[t] = sh[53 + t];
+            c.L[t] = sh[56 + t];
+            c.invL[t] = cc->invL[t];
+        }
+        c.half_cap = 0.5 * prm.max_disp;
+        c.V = sh[56] * sh[57] * sh[58];
+        c.noise = prm.noise;
+        c.pad = 0;
+        *cf = c;
+        for (int t = 0; t < 3; ++t) cell[t] = sh[56 + t];
+        cell[3] = 0.0;
+        cell[kCellPc] = sh[0];
+        cell[kCellPc + 1] = aniso ? sh[8] : 0.0;
+        cell[kCellPc + 2] = sh[16];
+        cell[10] = c.V;
     }
 }
 
@@ -413,8 +573,10 @@ __device__ __forceinline__ void npt_normals_f32(uint64_t seed, uint32_t stream, 
 }
 
 // Particle part before the forces: R^p/2, R/2, O, R/2, wrap into the new box.  kF32Noise:
-// the Langevin normals in FP32 (FP32-phase path); the state stays FP64 either way.
-template <bool kF32Noise>
+// the Langevin normals in FP32 (FP32-phase path); the state stays FP64 either way.  kRect:
+// per-axis coefficients (rectangular cell); otherwise those of axis 0 serve every axis, which
+// keeps the isotropic kernel's registers (and occupancy) as low as a scalar strain rate needs.
+template <bool kF32Noise, bool kRect>
 __global__ void __launch_bounds__(kNptThreads)
 k_npt_drift(int64_t N, double* __restrict__ pos, double* __restrict__ mom, const double* __restrict__ force,
             const double2* __restrict__ mprop, const NptCoef* __restrict__ cfp, uint64_t seed,
@@ -423,14 +585,20 @@ k_npt_drift(int64_t N, double* __restrict__ pos, double* __restrict__ mom, const
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const uint64_t step = cell_step(cell);
-    const NptCoef c = *cfp;
+    const NptCoef& c = *cfp;
     const double2 mp = mprop[i];  // (1/m, sqrt(m))
     const double inv_m = mp.x;
     double r[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
     double p[3] = {mom[3 * i], mom[3 * i + 1], mom[3 * i + 2]};
-    for (int t = 0; t < 3; ++t) p[t] = p[t] * c.a1 + kFConv * force[3 * i + t] * c.b1;
+    for (int t = 0; t < 3; ++t) {
+        const int x = kRect ? t : 0;
+        p[t] = p[t] * c.a1[x] + kFConv * force[3 * i + t] * c.b1[x];
+    }
     double d[3];
-    for (int t = 0; t < 3; ++t) d[t] = r[t] * c.a2m1 + (p[t] * inv_m) * c.b2;
+    for (int t = 0; t < 3; ++t) {
+        const int x = kRect ? t : 0;
+        d[t] = r[t] * c.a2m1[x] + (p[t] * inv_m) * c.b2[x];
+    }
     capped_add(r, d, c.half_cap);
     double z[4] = {0.0, 0.0, 0.0, 0.0};
     if (c.noise) {
@@ -439,7 +607,10 @@ k_npt_drift(int64_t N, double* __restrict__ pos, double* __restrict__ mom, const
     }
     const double s = c.sog * mp.y;
     for (int t = 0; t < 3; ++t) p[t] = p[t] * c.g + s * z[t];
-    for (int t = 0; t < 3; ++t) d[t] = r[t] * c.a3m1 + (p[t] * inv_m) * c.b3;
+    for (int t = 0; t < 3; ++t) {
+        const int x = kRect ? t : 0;
+        d[t] = r[t] * c.a3m1[x] + (p[t] * inv_m) * c.b3[x];
+    }
     capped_add(r, d, c.half_cap);
     for (int t = 0; t < 3; ++t) {
         r[t] -= c.L[t] * floor(r[t] * c.invL[t]);
@@ -593,8 +764,9 @@ k_cl_sort(const CellConsts* __restrict__ cc, const int* __restrict__ cnt, const 
 //   distance from the FP64 positions and applies the exact cutoff.
 //   f = -(dU/dr)/r for U = qqr2e q_i q_j erfc(sqrt(a) r)/r + 4 eps ((s/r)^12 - (s/r)^6); the
 //   lane sums go through a fixed shuffle tree, so the result does not depend on timing.
-// Each pair is visited from both ends: energies and the virial trace take half.  The warps
-// stride over the slots (grid-stride); per-block partials {W_r, E_coul, E_lj}.  A box that
+// Each pair is visited from both ends: energies and the virial take half.  The warps stride
+// over the slots (grid-stride); per-block partials {W_r, E_coul, E_lj} at slots 1..3, or with
+// kDiag (rectangular cells) {W_xx, W_yy, W_zz, E_coul, E_lj} at slots 3..7 (W_jj = sum f d_j^2).  A box that
 // outgrew the cell arrays (flagged by k_cl_count) leaves F_r = 0.
 // Pair constants, formed on the host in FP64 and rounded once: the kernel never derives
 // them itself (the FP32 kernel would otherwise recompute FP64 products in its loops).
@@ -643,7 +815,7 @@ struct ListArgs {
     int cap;
 };
 
-template <bool kF64, int kMode>
+template <bool kF64, int kMode, bool kDiag = false>
 __global__ void __launch_bounds__(kPairWarps * 32, kF64 ? kPairBlocksPerSM64 : kPairBlocksPerSM)
 k_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, const int* __restrict__ cid,
        const int* __restrict__ cnt,
@@ -656,7 +828,7 @@ k_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, const i
     constexpr bool kBuild = kMode == kPairBuild, kList = kMode == kPairList;
     if (kBuild && !la.nls->rebuild) return;  // the list stands (the same for every thread)
     __shared__ Hit hits[kPairWarps][kHitCap];
-    __shared__ double red[3][kPairWarps];
+    __shared__ double red[kDiag ? 5 : 3][kPairWarps];
     __shared__ double sL[3], sInvL[3];
     __shared__ float sLf[3], sInvLf[3], sPass;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -685,6 +857,9 @@ k_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, const i
     // GB300's narrow FP64 pipe)
     double wsum = 0.0, ecsum = 0.0, elsum = 0.0;
     float wh = 0.f, wl = 0.f, ech = 0.f, ecl = 0.f, elh = 0.f, ell = 0.f;
+    // kDiag: w, wsum, (wh, wl) hold the x part of the virial; y and z here
+    double wysum = 0.0, wzsum = 0.0;
+    float wyh = 0.f, wyl = 0.f, wzh = 0.f, wzl = 0.f;
     // no cell list this step (box beyond the cell arrays, flagged), or no list built yet
     const bool cells_ok = kList ? la.nls->force == 0 : cc->ncell >= 0;
     if (!cells_ok) {
@@ -770,6 +945,7 @@ k_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, const i
                 }
             }
             R fx = 0, fy = 0, fz = 0, w = 0, ec = 0, el = 0;
+            R wy = 0, wz = 0;
             int nh = 0;
             // one buffered candidate per lane (lanes >= count idle)
             auto evaluate = [&](int count, int base = 0) {
@@ -819,7 +995,13 @@ k_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, const i
                 fx -= f * dx;
                 fy -= f * dy;
                 fz -= f * dz;
-                w += f * r2;
+                if constexpr (kDiag) {
+                    w += f * dx * dx;
+                    wy += f * dy * dy;
+                    wz += f * dz * dz;
+                } else {
+                    w += f * r2;
+                }
             };
             // the search over one segment; MI: some axis has fewer than 3 cells (nearest image
             // per candidate there).  The loop body has no divergent branch: out-of-range lanes
@@ -933,6 +1115,10 @@ k_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, const i
                 fy += __shfl_xor_sync(0xffffffffu, fy, off);
                 fz += __shfl_xor_sync(0xffffffffu, fz, off);
                 w += __shfl_xor_sync(0xffffffffu, w, off);
+                if constexpr (kDiag) {
+                    wy += __shfl_xor_sync(0xffffffffu, wy, off);
+                    wz += __shfl_xor_sync(0xffffffffu, wz, off);
+                }
                 ec += __shfl_xor_sync(0xffffffffu, ec, off);
                 el += __shfl_xor_sync(0xffffffffu, el, off);
             }
@@ -942,6 +1128,10 @@ k_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, const i
                     Fr[3 * (int64_t)i + 1] = fy;
                     Fr[3 * (int64_t)i + 2] = fz;
                     wsum += 0.5 * w;
+                    if constexpr (kDiag) {
+                        wysum += 0.5 * wy;
+                        wzsum += 0.5 * wz;
+                    }
                     ecsum += 0.5 * ec;
                     elsum += 0.5 * el;
                 } else {
@@ -951,6 +1141,10 @@ k_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, const i
                     Fb[3 * (int64_t)i + 1] = float_to_double_bits(__float_as_uint(fy));
                     Fb[3 * (int64_t)i + 2] = float_to_double_bits(__float_as_uint(fz));
                     ff_add(wh, wl, 0.5f * w);
+                    if constexpr (kDiag) {
+                        ff_add(wyh, wyl, 0.5f * wy);
+                        ff_add(wzh, wzl, 0.5f * wz);
+                    }
                     ff_add(ech, ecl, 0.5f * ec);
                     ff_add(elh, ell, 0.5f * el);
                 }
@@ -972,23 +1166,36 @@ k_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, const i
             wsum = (double)wh + (double)wl;
             ecsum = (double)ech + (double)ecl;
             elsum = (double)elh + (double)ell;
+            if (kDiag) {
+                wysum = (double)wyh + (double)wyl;
+                wzsum = (double)wzh + (double)wzl;
+            }
         }
+        constexpr int o = kDiag ? 2 : 0;
         red[0][wib] = wsum;
-        red[1][wib] = ecsum;
-        red[2][wib] = elsum;
+        if (kDiag) {
+            red[1][wib] = wysum;
+            red[2][wib] = wzsum;
+        }
+        red[o + 1][wib] = ecsum;
+        red[o + 2][wib] = elsum;
     }
     __syncthreads();
-    if (threadIdx.x < 3) {
+    constexpr int nsum = kDiag ? 5 : 3;
+    if (threadIdx.x < nsum) {
         double t = 0.0;
         for (int wv = 0; wv < kPairWarps; ++wv) t += red[threadIdx.x][wv];
-        partials[4 * (size_t)blockIdx.x + 1 + threadIdx.x] = t;
+        partials[kPartStride * (size_t)blockIdx.x + (kDiag ? 3 : 1) + threadIdx.x] = t;
     }
 }
 
 // ---------------------------------------------------------------------------------
-// Forces F = qqr2e F_k + F_r; with do_kick, R^p/2 with (a4, b4); the kinetic sum 2K per
-// block; the last block sums the partials in a fixed order and finishes the pressure:
-// W = qqr2e tr(W_k) + W_r, P_ins = (2K + W)/(3V), and with do_kick V^p/2.
+// Forces F = qqr2e F_k + F_r; with do_kick, R^p/2 with (a4, b4); the kinetic sum per block
+// (2K, or per axis for the rectangular cell); the last block sums the partials in a fixed
+// order and finishes the pressure.  Isotropic: W = qqr2e tr(W_k) + W_r, P_ins = (2K + W)/(3V),
+// with do_kick V^p/2.  Rectangular cell: W_jj = qqr2e (W_k)_jj + (W_r)_jj, (P_ins)_jj =
+// (2K_j + W_jj)/V, with do_kick V^p/2 of the cell momenta (the forces of k_npt_cell_rect).
+template <bool kDiag>
 __global__ void __launch_bounds__(kNptThreads)
 k_npt_finish(int64_t N, double* __restrict__ mom, double* __restrict__ force, const double2* __restrict__ mprop,
              const double* __restrict__ Fk, const double* __restrict__ Fr, const double* __restrict__ WEk,
@@ -996,88 +1203,149 @@ k_npt_finish(int64_t N, double* __restrict__ mom, double* __restrict__ force, co
              unsigned* __restrict__ counter, double* __restrict__ cell, rbe_npt_params prm, int do_kick,
              unsigned* __restrict__ status)
 {
-    __shared__ double red[kNptThreads / 32];
+    __shared__ double red[3][kNptThreads / 32];
     __shared__ bool is_last;
+    constexpr bool diag = kDiag;  // rectangular cell
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double k2 = 0.0;
+    double k2 = 0.0, k2d[3] = {0.0, 0.0, 0.0};
     if (i < N) {
         const double inv_m = mprop[i].x;
-        double a = 1.0, b = 0.0;
-        if (do_kick) {
-            a = cfp->a4;
-            b = cfp->b4;
-        }
         for (int t = 0; t < 3; ++t) {
             const double F = (prm.kspace ? prm.qqr2e * Fk[3 * i + t] : 0.0) + (prm.real ? Fr[3 * i + t] : 0.0);
             force[3 * i + t] = F;
             double p = mom[3 * i + t];
             if (do_kick) {
-                p = p * a + kFConv * F * b;
+                p = p * cfp->a4[diag ? t : 0] + kFConv * F * cfp->b4[diag ? t : 0];
                 mom[3 * i + t] = p;
             }
-            k2 += p * p * inv_m;
+            if constexpr (diag) k2d[t] = p * p * inv_m * (1.0 / kFConv);
+            else k2 += p * p * inv_m;
         }
         k2 *= 1.0 / kFConv;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int nf = diag ? 3 : 1;  // kinetic partials per block
+    if constexpr (diag) {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) k2 += __shfl_xor_sync(0xffffffffu, k2, off);
-    if (lane == 0) red[warp] = k2;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int wv = 0; wv < kNptThreads / 32; ++wv) s += red[wv];
-        partials[4 * (size_t)(nblocks_pair + blockIdx.x)] = s;
-        __threadfence();
-        is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+        for (int off = 16; off > 0; off >>= 1)
+            for (int t = 0; t < 3; ++t) k2d[t] += __shfl_xor_sync(0xffffffffu, k2d[t], off);
+        if (lane == 0)
+            for (int t = 0; t < 3; ++t) red[t][warp] = k2d[t];
+    } else {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) k2 += __shfl_xor_sync(0xffffffffu, k2, off);
+        if (lane == 0) red[0][warp] = k2;
     }
+    __syncthreads();
+    if (threadIdx.x < nf) {
+        double sum = 0.0;
+        for (int wv = 0; wv < kNptThreads / 32; ++wv) sum += red[threadIdx.x][wv];
+        partials[kPartStride * (size_t)(nblocks_pair + blockIdx.x) + threadIdx.x] = sum;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
     __syncthreads();
     if (!is_last) return;
     __threadfence();
     // the last block: thread t sums the partials t, t + 256, ... and a fixed shared-memory
     // tree combines the threads, so the sums do not depend on which block came last
-    __shared__ double fin[4][kNptThreads];
+    __shared__ double fin[diag ? 8 : 4][kNptThreads];
+    constexpr int na = diag ? 8 : 4;  // slots [0, nf) kinetic, [nf, na) pair
     {
-        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        double v[na];
+#pragma unroll
+        for (int a = 0; a < na; ++a) v[a] = 0.0;
         for (int b = threadIdx.x; b < (int)gridDim.x; b += kNptThreads)
-            v[0] += __ldcg(partials + 4 * (size_t)(nblocks_pair + b));
+#pragma unroll
+            for (int a = 0; a < nf; ++a) v[a] += __ldcg(partials + kPartStride * (size_t)(nblocks_pair + b) + a);
         if (prm.real)
-            for (int b = threadIdx.x; b < nblocks_pair; b += kNptThreads) {
-                v[1] += __ldcg(partials + 4 * (size_t)b + 1);
-                v[2] += __ldcg(partials + 4 * (size_t)b + 2);
-                v[3] += __ldcg(partials + 4 * (size_t)b + 3);
-            }
-        for (int a = 0; a < 4; ++a) fin[a][threadIdx.x] = v[a];
+            for (int b = threadIdx.x; b < nblocks_pair; b += kNptThreads)
+#pragma unroll
+                for (int a = nf; a < na; ++a) v[a] += __ldcg(partials + kPartStride * (size_t)b + a);
+#pragma unroll
+        for (int a = 0; a < na; ++a) fin[a][threadIdx.x] = v[a];
     }
     __syncthreads();
     for (int half = kNptThreads / 2; half > 0; half >>= 1) {
         if (threadIdx.x < half)
-            for (int a = 0; a < 4; ++a) fin[a][threadIdx.x] += fin[a][threadIdx.x + half];
+#pragma unroll
+            for (int a = 0; a < na; ++a) fin[a][threadIdx.x] += fin[a][threadIdx.x + half];
         __syncthreads();
     }
-    if (threadIdx.x != 0) return;
-    const double K2 = fin[0][0], Wr = fin[1][0], Ec = fin[2][0], El = fin[3][0];
-    double Wk = 0.0, Ek = 0.0;
-    if (prm.kspace) {
-        Wk = prm.qqr2e * (__ldcg(WEk + 0) + __ldcg(WEk + 4) + __ldcg(WEk + 8));
-        Ek = prm.qqr2e * (__ldcg(WEk + 9) + __ldcg(WEk + 10));
+    if constexpr (!diag) {
+        if (threadIdx.x != 0) return;
+        const double K2 = fin[0][0], Wr = fin[1][0], Ec = fin[2][0], El = fin[3][0];
+        double Wk = 0.0, Ek = 0.0;
+        if (prm.kspace) {
+            Wk = prm.qqr2e * (__ldcg(WEk + 0) + __ldcg(WEk + 4) + __ldcg(WEk + 8));
+            Ek = prm.qqr2e * (__ldcg(WEk + 9) + __ldcg(WEk + 10));
+        }
+        const double W = Wk + Wr;
+        const double V = cell[0] * cell[1] * cell[2];
+        const double Pins = (K2 + W) / (3.0 * V);
+        double pV = prm.barostat ? cell[3] : 0.0;
+        if (do_kick && prm.barostat) pV += 0.5 * prm.dt * (Pins - prm.P_ext);
+        cell[3] = pV;
+        cell[4] = W;
+        cell[5] = K2;
+        cell[6] = Pins;
+        cell[7] = Ek;
+        cell[8] = Ec;
+        cell[9] = El;
+        cell[10] = V;
+        if (do_kick) cell[kCellStep] = __longlong_as_double((long long)(cell_step(cell) + 1));
+        if (!isfinite(Pins) || !isfinite(pV)) atomicOr(status, kStatusNonFinite);
+        *counter = 0u;
+        return;
     }
-    const double W = Wk + Wr;
-    const double V = cell[0] * cell[1] * cell[2];
-    const double Pins = (K2 + W) / (3.0 * V);
-    double pV = prm.barostat ? cell[3] : 0.0;
-    if (do_kick && prm.barostat) pV += 0.5 * prm.dt * (Pins - prm.P_ext);
-    cell[3] = pV;
-    cell[4] = W;
-    cell[5] = K2;
-    cell[6] = Pins;
-    cell[7] = Ek;
-    cell[8] = Ec;
-    cell[9] = El;
-    cell[10] = V;
-    if (do_kick) cell[kCellStep] = __longlong_as_double((long long)(cell_step(cell) + 1));
-    if (!isfinite(Pins) || !isfinite(pV)) atomicOr(status, kStatusNonFinite);
-    *counter = 0u;
+    // rectangular cell: lane j of warp 0 takes axis j
+    if (!diag || threadIdx.x >= 32) return;
+    __shared__ double sK[3], sW[3];
+    const int j = threadIdx.x;
+    if (j < 3) {
+        const double Wk = prm.kspace ? prm.qqr2e * __ldcg(WEk + 4 * j) : 0.0;
+        sK[j] = fin[j][0];
+        sW[j] = Wk + fin[3 + j][0];
+    }
+    __syncwarp();
+    const double L0 = cell[0], L1 = cell[1], L2 = cell[2];
+    const double V = L0 * L1 * L2;
+    if (j < 3) {
+        const double h = 0.5 * prm.dt;
+        double pc = cell[kCellPc + j];
+        if (do_kick) {
+            if (prm.barostat == 2) {
+                pc += h * ((sK[j] + sW[j] - prm.P_ext * V) / cell[j]);
+            } else if (j == 0) {
+                const double A = L0 * L1;
+                pc += h * ((sK[0] + sW[0] + sK[1] + sW[1]) / (2.0 * A) - prm.P_ext * L2 + prm.gamma0);
+            } else if (j == 2) {
+                const double A = L0 * L1;
+                pc += h * ((sK[2] + sW[2]) / L2 - prm.P_ext * A);
+            }
+        }
+        const double Pd = (sK[j] + sW[j]) / V;
+        cell[kCellPc + j] = pc;
+        cell[kCellWd + j] = sW[j];
+        cell[kCellK2d + j] = sK[j];
+        cell[kCellPd + j] = Pd;
+        if (!isfinite(pc) || !isfinite(Pd)) atomicOr(status, kStatusNonFinite);
+    }
+    if (j == 0) {
+        const double K2 = sK[0] + sK[1] + sK[2], W = sW[0] + sW[1] + sW[2];
+        const double Ek = prm.kspace ? prm.qqr2e * (__ldcg(WEk + 9) + __ldcg(WEk + 10)) : 0.0;
+        cell[3] = 0.0;
+        cell[4] = W;
+        cell[5] = K2;
+        cell[6] = (K2 + W) / (3.0 * V);
+        cell[7] = Ek;
+        cell[8] = fin[6][0];
+        cell[9] = fin[7][0];
+        cell[10] = V;
+        if (do_kick) cell[kCellStep] = __longlong_as_double((long long)(cell_step(cell) + 1));
+        *counter = 0u;
+    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -1181,7 +1449,7 @@ static rbe_status npt_ensure(rbe_ctx ctx, int64_t N, const double box[3], double
         ctx_free(ctx, b.partials);
         b.partials = nullptr;
         b.partcap = 0;
-        if ((e = ctx_alloc(ctx, &b.partials, sizeof(double) * 4 * (size_t)need)) != cudaSuccess)
+        if ((e = ctx_alloc(ctx, &b.partials, sizeof(double) * kPartStride * (size_t)need)) != cudaSuccess)
             return npt_fail(ctx, e, "cudaMalloc(npt partials)");
         b.partcap = need;
     }
@@ -1238,11 +1506,19 @@ static rbe_status npt_forces(rbe_ctx ctx, rbe_system* sys, uint64_t batch, int d
         const PairConst pc = make_pair_const(prm.rc, ctx->alpha, prm.qqr2e, prm.lj_sigma, prm.lj_eps);
         const ListArgs la{nls, b.nbr, b.nnb, b.sref, ctx->d.status, b.nbr_cap};
         const double4_32a* s64 = fp64 ? b.spos64 : nullptr;
+        const bool diag = prm.barostat >= 2;  // rectangular cell: the virial diagonal
         auto pair = [&](auto f64_tag, auto mode_tag) {
             constexpr bool F64 = decltype(f64_tag)::value;
             constexpr int MODE = decltype(mode_tag)::value;
-            k_pair<F64, MODE><<<nbp, kPairWarps * 32, 0, s>>>(N, cc, pc, b.cid, b.cnt, b.start, b.sorted, b.spos32,
-                                                              s64, b.Fr, b.partials, la);
+            if constexpr (MODE == kPairBuild)
+                k_pair<F64, MODE><<<nbp, kPairWarps * 32, 0, s>>>(N, cc, pc, b.cid, b.cnt, b.start, b.sorted,
+                                                                  b.spos32, s64, b.Fr, b.partials, la);
+            else if (diag)
+                k_pair<F64, MODE, true><<<nbp, kPairWarps * 32, 0, s>>>(N, cc, pc, b.cid, b.cnt, b.start, b.sorted,
+                                                                        b.spos32, s64, b.Fr, b.partials, la);
+            else
+                k_pair<F64, MODE><<<nbp, kPairWarps * 32, 0, s>>>(N, cc, pc, b.cid, b.cnt, b.start, b.sorted,
+                                                                  b.spos32, s64, b.Fr, b.partials, la);
         };
         using T = std::true_type;
         using F = std::false_type;
@@ -1261,9 +1537,14 @@ static rbe_status npt_forces(rbe_ctx ctx, rbe_system* sys, uint64_t batch, int d
         }
         if ((st = npt_check(ctx, "real-space kernels")) != RBE_OK) return st;
     }
-    k_npt_finish<<<std::max(1, nb), kNptThreads, 0, s>>>(N, sys->mom, sys->force, b.mprop, b.Fk, b.Fr, b.WEk,
-                                                         reinterpret_cast<const NptCoef*>(b.coef), b.partials, nbp,
-                                                         b.counter, sys->cell, prm, do_kick, ctx->d.status);
+    if (prm.barostat >= 2)
+        k_npt_finish<true><<<std::max(1, nb), kNptThreads, 0, s>>>(
+            N, sys->mom, sys->force, b.mprop, b.Fk, b.Fr, b.WEk, reinterpret_cast<const NptCoef*>(b.coef), b.partials,
+            nbp, b.counter, sys->cell, prm, do_kick, ctx->d.status);
+    else
+        k_npt_finish<false><<<std::max(1, nb), kNptThreads, 0, s>>>(
+            N, sys->mom, sys->force, b.mprop, b.Fk, b.Fr, b.WEk, reinterpret_cast<const NptCoef*>(b.coef), b.partials,
+            nbp, b.counter, sys->cell, prm, do_kick, ctx->d.status);
     return npt_check(ctx, "k_npt_finish");
 }
 
@@ -1275,8 +1556,15 @@ static rbe_status npt_validate(rbe_ctx ctx, const rbe_system* sys)
     if (!sys->pos || !sys->mom || !sys->force || !sys->charge || !sys->mass || !sys->cell)
         return fail(ctx, RBE_EINVAL, "system buffers must not be NULL");
     if (!(p.dt > 0.0) || !(p.kT >= 0.0) || !(p.gamma >= 0.0) || !(p.gamma_V >= 0.0) || !(p.rc > 0.0) ||
-        !(p.max_disp >= 0.0) || (p.barostat && !(p.M_V > 0.0)) || !(p.skin >= 0.0) || !std::isfinite(p.skin))
+        !(p.max_disp >= 0.0) || !(p.skin >= 0.0) || !std::isfinite(p.skin))
         return fail(ctx, RBE_EINVAL, "invalid NPT parameters");
+    if (p.barostat < 0 || p.barostat > 3) return fail(ctx, RBE_EINVAL, "barostat must be 0, 1, 2 or 3");
+    if (p.barostat == 1 && !(p.M_V > 0.0 && std::isfinite(p.M_V)))
+        return fail(ctx, RBE_EINVAL, "isotropic barostat needs M_V > 0");
+    for (int j = 0; j < 3; ++j)
+        if (((p.barostat == 2) || (p.barostat == 3 && j != 1)) && !(p.M_cell[j] > 0.0 && std::isfinite(p.M_cell[j])))
+            return fail(ctx, RBE_EINVAL, "rectangular barostat needs positive finite cell masses");
+    if (p.barostat == 3 && !std::isfinite(p.gamma0)) return fail(ctx, RBE_EINVAL, "gamma0 must be finite");
     if ((sys->step >> 56) != 0) return fail(ctx, RBE_EINVAL, "step must be < 2^56");
     return RBE_OK;
 }
@@ -1293,6 +1581,8 @@ static rbe_status npt_box_check(rbe_ctx ctx, const rbe_system* sys, double box[3
         if (sys->params.real && box[t] < 2.0 * sys->params.rc)
             return fail(ctx, RBE_EINVAL, "real space needs rc <= l/2 on every axis");
     }
+    if (sys->params.barostat == 3 && box[0] != box[1])
+        return fail(ctx, RBE_EINVAL, "the semi-isotropic cell needs l_x = l_y");
     return RBE_OK;
 }
 
@@ -1343,14 +1633,21 @@ rbe_status npt_run(rbe_ctx ctx, rbe_system* sys, int32_t nsteps)
     const NptBuffers& b = ctx->npt;
     for (int32_t k = 0; k < nsteps; ++k) {
         const uint64_t step = sys->step;
-        k_npt_cell_a<<<1, kCellWarps * 32, 0, s>>>(sys->cell, cf, sys->params, ctx->seed, b.cellcap,
-                                      static_cast<CellConsts*>(b.cellc));
-        if (ctx->precision == RBE_FP64)
-            k_npt_drift<false><<<nb, kNptThreads, 0, s>>>(N, sys->pos, sys->mom, sys->force, b.mprop, cf, ctx->seed,
-                                                          sys->cell);
+        if (sys->params.barostat >= 2)
+            k_npt_cell_rect<<<1, kRectWarps * 32, 0, s>>>(sys->cell, cf, sys->params, ctx->seed, b.cellcap,
+                                                          static_cast<CellConsts*>(b.cellc));
         else
-            k_npt_drift<true><<<nb, kNptThreads, 0, s>>>(N, sys->pos, sys->mom, sys->force, b.mprop, cf, ctx->seed,
-                                                         sys->cell);
+            k_npt_cell_a<<<1, kCellWarps * 32, 0, s>>>(sys->cell, cf, sys->params, ctx->seed, b.cellcap,
+                                                       static_cast<CellConsts*>(b.cellc));
+        const bool rect = sys->params.barostat >= 2;
+        auto drift = [&](auto f32_tag, auto rect_tag) {
+            k_npt_drift<decltype(f32_tag)::value, decltype(rect_tag)::value><<<nb, kNptThreads, 0, s>>>(
+                N, sys->pos, sys->mom, sys->force, b.mprop, cf, ctx->seed, sys->cell);
+        };
+        using T = std::true_type;
+        using F = std::false_type;
+        if (ctx->precision == RBE_FP64) rect ? drift(F{}, T{}) : drift(F{}, F{});
+        else rect ? drift(T{}, T{}) : drift(T{}, F{});
         if ((st = npt_check(ctx, "k_npt_cell_a/k_npt_drift")) != RBE_OK) return st;
         if ((st = npt_forces(ctx, sys, step, 1)) != RBE_OK) return st;
         sys->step = step + 1;

@@ -31,6 +31,7 @@ struct Request {
     std::vector<double> out_pos, out_mom, out_cell;
     int state = 0;  // 0 queued, 1 resident, 2 done, 3 failed
     rbe_status error = RBE_OK;
+    std::string error_msg;  // why the request failed
     double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
 };
 
@@ -165,6 +166,7 @@ static rbe_status admit(rbe_server_s* s, Slot& sl, int64_t id)
     double cell[RBE_CELL_DOUBLES] = {0};
     for (int t = 0; t < 3; ++t) cell[t] = rq.r.box[t];
     cell[3] = rq.r.pV;
+    for (int t = 0; t < 3; ++t) cell[12 + t] = rq.r.pc[t];
     cudaError_t e = cudaSuccess;
     if ((e = cudaMemcpyAsync(sl.pos, rq.pos.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice, sl.stream)) != cudaSuccess ||
         (e = cudaMemcpyAsync(sl.mom, rq.mom.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice, sl.stream)) != cudaSuccess ||
@@ -246,6 +248,7 @@ static rbe_status retire(rbe_server_s* s, Slot& sl)
     rbe_status st = e == cudaSuccess ? rbe_sync(sl.ctx) : RBE_ECUDA;
     rq.state = st == RBE_OK ? 2 : 3;
     rq.error = st;
+    if (st != RBE_OK) rq.error_msg = e == cudaSuccess ? rbe_last_error(sl.ctx) : cudaGetErrorString(e);
     rq.t_done = now_s(s);
     s->t_last_done = rq.t_done;
     ++s->n_done;
@@ -363,6 +366,7 @@ rbe_status rbe_server_progress(rbe_server s, int32_t wait, int32_t* n_queued, in
             if (st != RBE_OK) {
                 s->reqs[id]->state = 3;
                 s->reqs[id]->error = st;
+                s->reqs[id]->error_msg = s->last_error;
                 ++s->n_done;
                 return st;
             }
@@ -389,7 +393,7 @@ rbe_status rbe_server_result(rbe_server s, int64_t id, double* pos, double* mom,
 {
     if (!s || id < 0 || id >= (int64_t)s->reqs.size()) return RBE_EINVAL;
     const Request& rq = *s->reqs[id];
-    if (rq.state == 3) return sfail(s, rq.error, "request failed");
+    if (rq.state == 3) return sfail(s, rq.error, "request failed: " + rq.error_msg);
     if (rq.state != 2) return sfail(s, RBE_ESTATE, "request not finished");
     const int64_t N = rq.r.N;
     if (pos) std::memcpy(pos, rq.out_pos.data(), sizeof(double) * 3 * N);
