@@ -297,11 +297,17 @@ KB = 0.00831446261815324
 BAR = 6.02214076e-5
 
 
-def serve_params(rbe, box):
+def serve_params(rbe, box, barostat=1):
+    """NPT parameters of the serving system; barostat 2 / 3 are the anisotropic and
+    semi-isotropic rectangular cells with the same relaxation time and compressibility."""
     V0 = float(np.prod(box))
-    return rbe.NptParams(dt=0.001, kT=KB * 300.0, P_ext=1.0 * BAR, gamma=10.0, gamma_V=2.0,
-                         M_V=rbe.piston_mass(0.5, 4.5e-5 / BAR, V0), rc=SERVE_RC, qqr2e=1389.35457644382 / SERVE_EPS_R,
-                         lj_sigma=2.0, lj_eps=0.5, max_disp=0.05, kspace=1, real=1, noise=1, barostat=1, skin=SERVE_SKIN)
+    prm = rbe.NptParams(dt=0.001, kT=KB * 300.0, P_ext=1.0 * BAR, gamma=10.0, gamma_V=2.0,
+                        M_V=rbe.piston_mass(0.5, 4.5e-5 / BAR, V0), rc=SERVE_RC, qqr2e=1389.35457644382 / SERVE_EPS_R,
+                        lj_sigma=2.0, lj_eps=0.5, max_disp=0.05, kspace=1, real=1, noise=1, barostat=barostat,
+                        skin=SERVE_SKIN)
+    if barostat >= 2:
+        prm.M_cell = (type(prm.M_cell))(*rbe.piston_masses_rect(barostat, 0.5, 4.5e-5 / BAR, box))
+    return prm
 
 
 def serve(rbe, reqs, states, precision, max_slots, chunk, nsteps, use_graphs=True, open_loop=False,
@@ -338,12 +344,12 @@ def serve(rbe, reqs, states, precision, max_slots, chunk, nsteps, use_graphs=Tru
                                  "max": float(lat.max() * 1e3), "chunks": int(lat.size)}}
 
 
-def npt_single(rbe, N, precision, steps, warmup=3):
+def npt_single(rbe, N, precision, steps, warmup=3, barostat=1):
     """ms per NPT step of one replica of N particles (the serving system), launched directly
     on one stream, timed with CUDA events after `warmup` steps."""
     import torch
     pos, mom, q, m, box = inputs.npt_replica(N, 3)
-    prm = serve_params(rbe, box)
+    prm = serve_params(rbe, box, barostat)
     stream = torch.cuda.current_stream()
     with rbe.Context(box, SERVE_ALPHA, SERVE_P, 1003, precision, stream=stream.cuda_stream) as ctx:
         rep = rbe.NptReplica(pos, mom, q, m, box, prm, torch.device("cuda", torch.cuda.current_device()))
@@ -363,7 +369,10 @@ def run_npt_single(rbe, sizes, steps):
     for N in sizes:
         f32 = npt_single(rbe, N, rbe.RBE_FP32_PHASE, steps)
         f64 = npt_single(rbe, N, rbe.RBE_FP64, max(2, steps // 4))
-        out[str(N)] = {"fp32_ms_per_step": f32, "fp64_ms_per_step": f64, "fp32_over_fp64": f64 / f32}
+        out[str(N)] = {"fp32_ms_per_step": f32, "fp64_ms_per_step": f64, "fp32_over_fp64": f64 / f32,
+                       # the rectangular cells (per-axis virial and pistons), FP32-phase path
+                       "fp32_aniso_ms_per_step": npt_single(rbe, N, rbe.RBE_FP32_PHASE, steps, barostat=2),
+                       "fp32_semi_ms_per_step": npt_single(rbe, N, rbe.RBE_FP32_PHASE, steps, barostat=3)}
     return out
 
 
@@ -584,6 +593,8 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=64)
     ap.add_argument("--serve-fp64-sample", type=int, default=16)
     ap.add_argument("--profile-npt", type=int, default=0, help="time only NPT steps of one replica of this N")
+    ap.add_argument("--barostat", type=int, default=1, choices=(0, 1, 2, 3),
+                    help="with --profile-npt: 0 fixed box, 1 isotropic, 2 anisotropic, 3 semi-isotropic")
     ap.add_argument("--profile-batched", action="store_true", help="time only the batched k-space evaluation")
     ap.add_argument("--skip-sweep", action="store_true", help="leave out the large-N precision and roofline sweep")
     ap.add_argument("--profile-sweep", action="store_true", help="run only the large-N sweep")
@@ -597,9 +608,10 @@ def main():
         import paper_2110_14362_gb300 as rbe
         torch.cuda.set_device(local)
         prec = rbe.RBE_FP32_PHASE if args.precision == "fp32" else rbe.RBE_FP64
-        ms = npt_single(rbe, args.profile_npt, prec, args.steps, args.warmup)
+        ms = npt_single(rbe, args.profile_npt, prec, args.steps, args.warmup, barostat=args.barostat)
         print(json.dumps({"metric": "NPT steps of one replica", "value": 1e3 / ms, "unit": "replica-steps/s",
-                          "ms_per_step": ms, "N": args.profile_npt, "precision": args.precision}), flush=True)
+                          "ms_per_step": ms, "N": args.profile_npt, "precision": args.precision,
+                          "barostat": args.barostat}), flush=True)
         return
     if args.profile_sweep:
         import torch

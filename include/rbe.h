@@ -222,7 +222,8 @@ typedef struct {
     double qqr2e;     /* Coulomb constant, kJ/mol A/e^2 */
     double lj_sigma;  /* A */
     double lj_eps;    /* kJ/mol; 0 disables the Lennard-Jones term */
-    double max_disp;  /* cap on |dr| per step in A, split over the two R/2 sub-steps; 0 = none */
+    double max_disp;  /* cap on the peculiar displacement |(p/m) dt| per step in A, split over the two
+                         R/2 sub-steps; the dilation with the cell is not capped; 0 = none */
     int32_t kspace;   /* 1: RBE k-space forces and virial */
     int32_t real;     /* 1: real-space forces and virial */
     int32_t noise;    /* 1: Langevin noise in O and O^p */

@@ -55,7 +55,7 @@ typedef struct {
     double qqr2e;     /* Coulomb constant, kJ/mol A / e^2 */
     double lj_sigma;  /* A */
     double lj_eps;    /* kJ/mol (0: no Lennard-Jones) */
-    double max_disp;  /* cap on |dr| per R/2 sub-step, A (0: none) */
+    double max_disp;  /* cap on the peculiar |dr| per step, half per R/2 sub-step, A (0: none) */
     int32_t P;        /* RBE batch size */
     int32_t kspace;   /* 1: RBE k-space forces and virial */
     int32_t real;     /* 1: erfc Coulomb + LJ real space */
@@ -241,20 +241,29 @@ static void half_kick_particles(int64_t N, double* p, const double* F, double ep
     for (int64_t i = 0; i < 3 * N; ++i) p[i] = p[i] * a + FCONV * F[i] * b;
 }
 
-/* R/2: r <- r e^{eps h} + (p/m) (e^{eps h} - 1) / eps, with the optional displacement cap */
+/* The optional cap on the displacement of one R/2 sub-step applies to its peculiar part
+ * (p/m) (e^{eps h} - 1)/eps only: the affine part r (e^{eps h} - 1) is the cell's dilation,
+ * which every particle follows (capping it would hold back the particles far from the
+ * origin and distort the box). */
+static void cap_peculiar(double d[3], double cap)
+{
+    if (cap > 0.0) {
+        double len = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        if (len > cap)
+            for (int t = 0; t < 3; ++t) d[t] *= cap / len;
+    }
+}
+
+/* R/2: r <- r e^{eps h} + (p/m) (e^{eps h} - 1) / eps, with the optional cap */
 static void half_drift(int64_t N, double* r, const double* p, const double* m, double eps, double h, double cap)
 {
     double a = exp(eps * h);
     double b = expm1_over(eps * h, h);
     for (int64_t i = 0; i < N; ++i) {
         double d[3];
-        for (int t = 0; t < 3; ++t) d[t] = r[3 * i + t] * (a - 1.0) + (p[3 * i + t] / m[i]) * b;
-        if (cap > 0.0) {
-            double len = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-            if (len > cap)
-                for (int t = 0; t < 3; ++t) d[t] *= cap / len;
-        }
-        for (int t = 0; t < 3; ++t) r[3 * i + t] += d[t];
+        for (int t = 0; t < 3; ++t) d[t] = (p[3 * i + t] / m[i]) * b;
+        cap_peculiar(d, cap);
+        for (int t = 0; t < 3; ++t) r[3 * i + t] += r[3 * i + t] * (a - 1.0) + d[t];
     }
 }
 
@@ -449,7 +458,8 @@ static void half_kick_particles_axes(int64_t N, double* p, const double* F, cons
         for (int j = 0; j < 3; ++j) p[3 * i + j] = p[3 * i + j] * a[j] + FCONV * F[3 * i + j] * b[j];
 }
 
-/* R/2 per axis: r_j <- r_j e^{eps_j h} + (p_j/m) (e^{eps_j h} - 1) / eps_j, with the cap */
+/* R/2 per axis: r_j <- r_j e^{eps_j h} + (p_j/m) (e^{eps_j h} - 1) / eps_j, with the cap on
+ * the peculiar part */
 static void half_drift_axes(int64_t N, double* r, const double* p, const double* m, const double eps[3], double h,
                             double cap)
 {
@@ -460,13 +470,9 @@ static void half_drift_axes(int64_t N, double* r, const double* p, const double*
     }
     for (int64_t i = 0; i < N; ++i) {
         double d[3];
-        for (int j = 0; j < 3; ++j) d[j] = r[3 * i + j] * (a[j] - 1.0) + (p[3 * i + j] / m[i]) * b[j];
-        if (cap > 0.0) {
-            double len = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-            if (len > cap)
-                for (int j = 0; j < 3; ++j) d[j] *= cap / len;
-        }
-        for (int j = 0; j < 3; ++j) r[3 * i + j] += d[j];
+        for (int j = 0; j < 3; ++j) d[j] = (p[3 * i + j] / m[i]) * b[j];
+        cap_peculiar(d, cap);
+        for (int j = 0; j < 3; ++j) r[3 * i + j] += r[3 * i + j] * (a[j] - 1.0) + d[j];
     }
 }
 

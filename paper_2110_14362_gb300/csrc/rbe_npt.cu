@@ -536,8 +536,10 @@ k_npt_cell_rect(double* __restrict__ cell, NptCoef* __restrict__ cf, rbe_npt_par
     }
 }
 
-// r += d with |d| capped at cap (cap > 0); the square root only for a step that is capped.
-__device__ __forceinline__ void capped_add(double r[3], double d[3], double cap)
+// r += r (a - 1) + d with |d| capped at cap (cap > 0): the cap holds the peculiar part d =
+// (p/m) b of an R/2 sub-step, not the affine part r (a - 1), which is the cell's dilation
+// and scales with |r|.  The square root only for a step that is capped.
+__device__ __forceinline__ void drift_add(double r[3], const double am1[3], double d[3], double cap)
 {
     if (cap > 0.0) {
         const double l2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -546,7 +548,9 @@ __device__ __forceinline__ void capped_add(double r[3], double d[3], double cap)
             d[0] *= s; d[1] *= s; d[2] *= s;
         }
     }
-    r[0] += d[0]; r[1] += d[1]; r[2] += d[2];
+    r[0] += r[0] * am1[0] + d[0];
+    r[1] += r[1] * am1[1] + d[1];
+    r[2] += r[2] * am1[2] + d[2];
 }
 
 // The same four normals in FP32 (FP32-phase path): Box--Muller with the fast logarithm and
@@ -594,12 +598,13 @@ k_npt_drift(int64_t N, double* __restrict__ pos, double* __restrict__ mom, const
         const int x = kRect ? t : 0;
         p[t] = p[t] * c.a1[x] + kFConv * force[3 * i + t] * c.b1[x];
     }
-    double d[3];
+    double d[3], am1[3];
     for (int t = 0; t < 3; ++t) {
         const int x = kRect ? t : 0;
-        d[t] = r[t] * c.a2m1[x] + (p[t] * inv_m) * c.b2[x];
+        am1[t] = c.a2m1[x];
+        d[t] = (p[t] * inv_m) * c.b2[x];
     }
-    capped_add(r, d, c.half_cap);
+    drift_add(r, am1, d, c.half_cap);
     double z[4] = {0.0, 0.0, 0.0, 0.0};
     if (c.noise) {
         if (kF32Noise) npt_normals_f32(seed, 1u, step, (uint32_t)i, z);
@@ -609,9 +614,10 @@ k_npt_drift(int64_t N, double* __restrict__ pos, double* __restrict__ mom, const
     for (int t = 0; t < 3; ++t) p[t] = p[t] * c.g + s * z[t];
     for (int t = 0; t < 3; ++t) {
         const int x = kRect ? t : 0;
-        d[t] = r[t] * c.a3m1[x] + (p[t] * inv_m) * c.b3[x];
+        am1[t] = c.a3m1[x];
+        d[t] = (p[t] * inv_m) * c.b3[x];
     }
-    capped_add(r, d, c.half_cap);
+    drift_add(r, am1, d, c.half_cap);
     for (int t = 0; t < 3; ++t) {
         r[t] -= c.L[t] * floor(r[t] * c.invL[t]);
         pos[3 * i + t] = r[t];

@@ -208,3 +208,32 @@ def test_rect_rejects_bad_parameters():
     iso = oracle.NptState(np.zeros((2, 3)), np.zeros((2, 3)), np.zeros(2), np.ones(2), [10.0] * 3)
     with pytest.raises(RuntimeError):
         oracle.npt_step(iso, 0, oracle.npt_params(kspace=0, real=0, barostat=2))
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_cap_leaves_the_dilation_alone(mode):
+    """The displacement cap holds the peculiar motion (p/m) only: particles at rest in a fast
+    expanding cell follow its dilation whatever the cap, so a run with a tiny cap equals the run
+    without one, and the particles far from the origin keep their scaled coordinates."""
+    rng = np.random.default_rng(12)
+    N, L = 30, 60.0
+    r = rng.random((N, 3)) * L
+    out = []
+    for cap in (0.0, 1e-6):
+        kw = dict(kspace=0, real=0, noise=0, gamma=0.0, gamma_V=0.0, P_ext=0.0, dt=0.002, max_disp=cap,
+                  barostat=mode)
+        if mode == 1:
+            st = oracle.NptState(r, np.zeros((N, 3)), np.zeros(N), np.full(N, 20.0), [L] * 3, pV=270.0)
+            prm = oracle.npt_params(M_V=1e-3, **kw)
+            oracle.npt_forces(st, 0, prm)
+            oracle.npt_run(st, 0, 20, prm)
+        else:
+            st = oracle.NptRectState(r, np.zeros((N, 3)), np.zeros(N), np.full(N, 20.0), [L] * 3, pc=(50.0, 40.0, 60.0))
+            prm = oracle.npt_params(M_cell=(1.0, 1.0, 1.0), **kw)
+            oracle.npt_forces_rect(st, 0, prm)
+            oracle.npt_run_rect(st, 0, 20, prm)
+        out.append((st.r.copy(), st.L.copy()))
+    (r0, L0), (r1, L1) = out
+    assert np.all(L0 - L > 0.5)  # the cell grows fast: far particles move ~ 1 A per sub-step
+    assert np.array_equal(r0, r1) and np.array_equal(L0, L1)
+    assert np.abs(r0 / L0 - r / L).max() < 1e-3
