@@ -20,6 +20,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rbe_oracle.c")
 _SRC_NPT = os.path.join(_HERE, "npt_oracle.c")
+_SRC_SMP = os.path.join(_HERE, "sampler_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -33,7 +34,7 @@ _c_uint32_p = ctypes.POINTER(ctypes.c_uint32)
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc into ``oracle/_build/liboracle.so`` and return its path."""
     os.makedirs(_BUILD, exist_ok=True)
-    srcs = [s for s in (_SRC, _SRC_NPT) if os.path.exists(s)]
+    srcs = [s for s in (_SRC, _SRC_NPT, _SRC_SMP) if os.path.exists(s)]
     newest = max(os.path.getmtime(s) for s in srcs)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".{os.getpid()}.tmp"
@@ -87,6 +88,8 @@ def _load():
             lib.orc_direct_sum.restype = ctypes.c_double
             if hasattr(lib, "orc_npt_step"):
                 _bind_npt(lib)
+            if hasattr(lib, "orc_sample_k_mh"):
+                _bind_samplers(lib)
             _lib = lib
     return _lib
 
@@ -131,6 +134,22 @@ def _bind_npt(lib):
                                      _c_double_p, _c_double_p, _c_double_p, _c_double_p, ctypes.c_uint64,
                                      ctypes.c_int32, P, _c_double_p, _c_double_p, _c_double_p]
     lib.orc_npt_run_rect.restype = ctypes.c_int
+
+
+def _bind_samplers(lib):
+    lib.orc_own_log.argtypes = [ctypes.c_double]
+    lib.orc_own_log.restype = ctypes.c_double
+    lib.orc_own_erfc.argtypes = [ctypes.c_double]
+    lib.orc_own_erfc.restype = ctypes.c_double
+    lib.orc_rounded_gauss_mass.argtypes = [ctypes.c_int32, ctypes.c_double]
+    lib.orc_rounded_gauss_mass.restype = ctypes.c_double
+    lib.orc_polar_pair.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _c_double_p]
+    lib.orc_polar_pair.restype = ctypes.c_int
+    for name in ("orc_sample_k_offline", "orc_sample_k_mh"):
+        f = getattr(lib, name)
+        f.argtypes = [_c_double_p, ctypes.c_double, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, _c_int32_p,
+                      _c_double_p]
+        f.restype = ctypes.c_int
 
 
 def _dp(a):
@@ -197,6 +216,47 @@ def sample_k(box, alpha: float, P: int, seed: int, step: int):
     S = ctypes.c_double(0.0)
     _check(lib.orc_sample_k(_dp(b), alpha, P, seed, step, _ip(m), ctypes.byref(S)), "sample_k")
     return m, S.value
+
+
+def own_log(x: float) -> float:
+    return _load().orc_own_log(float(x))
+
+
+def own_erfc(x: float) -> float:
+    return _load().orc_own_erfc(float(x))
+
+
+def rounded_gauss_mass(m: int, g: float) -> float:
+    """Mass of [m - 1/2, m + 1/2) under N(0, sigma^2) with g = 1/(sigma sqrt 2)."""
+    return _load().orc_rounded_gauss_mass(int(m), float(g))
+
+
+def polar_pair(seed: int, step: int, l: int, d: int):
+    """One polar-method trial of the offline stream: (ok, z[2])."""
+    z = np.zeros(2)
+    ok = _load().orc_polar_pair(seed, step, l, d, _dp(z))
+    return bool(ok), z
+
+
+def sample_k_offline(box, alpha: float, P: int, seed: int, step: int):
+    """Offline approach of Sec. 4.3: m[P,3] (rounded scaled Gaussians) and S."""
+    lib = _load()
+    m = np.zeros((P, 3), dtype=np.int32)
+    S = ctypes.c_double(0.0)
+    _check(lib.orc_sample_k_offline(_dp(_f64(box, (3,))), alpha, P, seed, step, _ip(m), ctypes.byref(S)),
+           "sample_k_offline")
+    return m, S.value
+
+
+def sample_k_mh(box, alpha: float, P: int, seed: int, step: int, state):
+    """Online approach of Sec. 4.3: one MH step per slot from state[P,3] (int32, updated in
+    place; rows of zeros start from the exact draw).  Returns (state, S)."""
+    lib = _load()
+    assert state.dtype == np.int32 and state.shape == (P, 3) and state.flags.c_contiguous
+    S = ctypes.c_double(0.0)
+    _check(lib.orc_sample_k_mh(_dp(_f64(box, (3,))), alpha, P, seed, step, _ip(state), ctypes.byref(S)),
+           "sample_k_mh")
+    return state, S.value
 
 
 def ewald_kspace(pos, q, box, alpha: float, kmax: int):
