@@ -86,6 +86,25 @@ rbe_status rbe_set_seed(rbe_ctx ctx, uint64_t seed);
  * (rho_accum is ignored on the FP64 path). */
 rbe_status rbe_set_precision(rbe_ctx ctx, int32_t precision, int32_t rho_accum);
 
+/* Frequency samplers (Sec. 4.3).  EXACT (default): i.i.d. draws from the discrete Gaussian of
+ * Eq. (probexpression) by per-axis inverse CDF.  OFFLINE: the paper's offline approach, Gaussian
+ * z drawn independently of the box (Philox stream 3, Marsaglia's polar method), m_j =
+ * rint(z_j sqrt(alpha l_j^2 / (2 pi^2))), redrawn while m = 0; the weights stay S/P, so the
+ * rounding is a systematic bias (the paper notes it; the estimator is no longer unbiased).
+ * MH: the paper's online approach, one Metropolis--Hastings step per frequency slot and call,
+ * from the slot's previous m, with the offline draw as an independence proposal (its mass per
+ * integer the Gaussian mass of [m - 1/2, m + 1/2)) and the discrete Gaussian on Z^3 \ {0} as
+ * the target; acceptance uniform from Philox stream 4.  The chain state lives in the context
+ * (one slot per frequency, sized for the context's P); every rbe_set_sampler call resets it, and
+ * a reset slot starts from the EXACT draw of its next step.  Every floating-point step that
+ * decides an integer is a separately rounded IEEE operation written out in the library (own
+ * logarithm, erfc and exponential), so the draws match the oracle bit for bit.  Applies to
+ * rbe_sample_k, rbe_kspace_forces_virial(_host) and rbe_npt_step; the batched API and
+ * rbe_sample_k_noalloc always use EXACT.  A CUDA graph captured earlier keeps the sampler it
+ * was captured with.  RBE_EINVAL for an unknown sampler. */
+typedef enum { RBE_SAMPLER_EXACT = 0, RBE_SAMPLER_OFFLINE = 1, RBE_SAMPLER_MH = 2 } rbe_sampler;
+rbe_status rbe_set_sampler(rbe_ctx ctx, int32_t sampler);
+
 /* Replace the box lengths (same validity rule as rbe_create).  The per-axis sampling
  * tables are rebuilt on the device at the next evaluation. */
 rbe_status rbe_set_box(rbe_ctx ctx, const double box[3]);

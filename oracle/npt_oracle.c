@@ -39,6 +39,10 @@ enum { NPT_OK = 0, NPT_EINVAL = 1, NPT_ENOMEM = 2 };
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 int orc_sample_k(const double box[3], double alpha, int32_t P, uint64_t seed, uint64_t step,
                  int32_t* m_out, double* S_out);
+int orc_sample_k_offline(const double box[3], double alpha, int32_t P, uint64_t seed, uint64_t step,
+                         int32_t* m_out, double* S_out);
+int orc_sample_k_mh(const double box[3], double alpha, int32_t P, uint64_t seed, uint64_t step, int32_t* state,
+                    double* S_out);
 int orc_rbe_kspace(int64_t N, const double* pos, const double* q, const double box[3], double alpha,
                    int32_t P, const int32_t* m, const double* wl, double* F, double W[9], double E[2],
                    double* rho);
@@ -67,6 +71,9 @@ typedef struct {
     double M_cell[3]; /* barostat 2: masses of l_x, l_y, l_z (kJ/mol ps^2/A^2);
                          barostat 3: M_A (kJ/mol ps^2/A^4) in [0], M_L (kJ/mol ps^2/A^2) in [2] */
     double gamma0;    /* barostat 3: surface tension times the number of surfaces, kJ/mol/A^2 */
+    int32_t sampler;  /* frequencies: 0 exact, 1 offline, 2 Metropolis--Hastings (sampler_oracle.c) */
+    int32_t pad2;
+    int32_t* chain;   /* sampler 2: the chain state, P x 3 (in/out; rows of zeros start exact) */
 } orc_npt_params;
 
 /* ------------------------------------------------------------------------------ */
@@ -155,7 +162,18 @@ static int npt_forces_parts(int64_t N, const double* r, const double* q, const d
             return NPT_ENOMEM;
         }
         double S = 0.0, Wk[9], Ek[2];
-        st = orc_sample_k(L, prm->alpha, prm->P, prm->seed, step, m, &S);
+        if (prm->sampler == 1) {
+            st = orc_sample_k_offline(L, prm->alpha, prm->P, prm->seed, step, m, &S);
+        } else if (prm->sampler == 2) {
+            if (!prm->chain) {
+                st = NPT_EINVAL;
+            } else {
+                st = orc_sample_k_mh(L, prm->alpha, prm->P, prm->seed, step, prm->chain, &S);
+                for (int32_t j = 0; st == NPT_OK && j < 3 * prm->P; ++j) m[j] = prm->chain[j];
+            }
+        } else {
+            st = orc_sample_k(L, prm->alpha, prm->P, prm->seed, step, m, &S);
+        }
         if (st == NPT_OK) {
             for (int32_t l = 0; l < prm->P; ++l) wl[l] = S / (double)prm->P;
             st = orc_rbe_kspace(N, r, q, L, prm->alpha, prm->P, m, wl, Fk, Wk, Ek, NULL);

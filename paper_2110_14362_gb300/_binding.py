@@ -20,6 +20,7 @@ from . import _build
 RBE_OK, RBE_EINVAL, RBE_ENOMEM, RBE_ECUDA, RBE_ETIMEOUT, RBE_ENONFINITE, RBE_ESAMPLE, RBE_ESTATE = range(8)
 RBE_FP64, RBE_FP32_PHASE = 0, 1
 RBE_RHO_FP64, RBE_RHO_COMP32, RBE_RHO_FP32 = 0, 1, 2
+RBE_SAMPLER_EXACT, RBE_SAMPLER_OFFLINE, RBE_SAMPLER_MH = 0, 1, 2
 
 _lock = threading.Lock()
 _lib = None
@@ -81,6 +82,7 @@ SIGNATURES = [
     ("rbe_destroy", ctypes.c_int, [_vp]),
     ("rbe_set_stream", ctypes.c_int, [_vp, _vp]),
     ("rbe_set_precision", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
+    ("rbe_set_sampler", ctypes.c_int, [_vp, ctypes.c_int32]),
     ("rbe_set_seed", ctypes.c_int, [_vp, ctypes.c_uint64]),
     ("rbe_set_box", ctypes.c_int, [_vp, _dp]),
     ("rbe_sample_k", ctypes.c_int, [_vp, ctypes.c_uint64, _ip, _dp]),
@@ -195,6 +197,10 @@ def rbe_set_stream(h, stream_handle: int):
 
 def rbe_set_precision(h, precision: int, rho_accum: int = RBE_RHO_FP32):
     _check(load().rbe_set_precision(h, int(precision), int(rho_accum)), h)
+
+
+def rbe_set_sampler(h, sampler: int):
+    _check(load().rbe_set_sampler(h, int(sampler)), h)
 
 
 def rbe_set_seed(h, seed: int):
@@ -521,6 +527,10 @@ class Context:
 
     def set_precision(self, precision: int, rho_accum: int = RBE_RHO_FP32):
         rbe_set_precision(self.h, precision, rho_accum)
+
+    def set_sampler(self, sampler: int):
+        """RBE_SAMPLER_EXACT, _OFFLINE or _MH (Sec. 4.3); resets the MH chain."""
+        rbe_set_sampler(self.h, sampler)
 
     def set_box(self, box):
         rbe_set_box(self.h, box)

@@ -200,6 +200,7 @@ rbe_status rbe_destroy(rbe_ctx ctx)
     if (ctx->h_out) cudaFreeHost(ctx->h_out);
     free_npt(ctx->npt);
     free_buffers(ctx->d);
+    if (ctx->chain) cudaFree(ctx->chain);
     delete ctx;
     return RBE_OK;
 }
@@ -232,6 +233,31 @@ rbe_status rbe_set_precision(rbe_ctx ctx, int32_t precision, int32_t rho_accum)
         return fail(ctx, RBE_EINVAL, "unknown rho accumulation");
     ctx->precision = precision;
     ctx->rho_accum = rho_accum;
+    return RBE_OK;
+}
+
+rbe_status rbe_set_sampler(rbe_ctx ctx, int32_t sampler)
+{
+    if (!ctx) return RBE_EINVAL;
+    if (sampler != RBE_SAMPLER_EXACT && sampler != RBE_SAMPLER_OFFLINE && sampler != RBE_SAMPLER_MH)
+        return fail(ctx, RBE_EINVAL, "unknown sampler");
+    DeviceGuard g(ctx->device);
+    if (sampler == RBE_SAMPLER_MH) {
+        const int32_t need = ctx->P > 0 ? ctx->P : 1;
+        cudaError_t e = cudaSuccess;
+        if (ctx->chain_cap < need) {
+            ctx_free(ctx, ctx->chain);
+            ctx->chain = nullptr;
+            ctx->chain_cap = 0;
+            if ((e = ctx_alloc(ctx, &ctx->chain, sizeof(int4) * (size_t)need)) != cudaSuccess)
+                return cuda_fail(ctx, e, "cudaMallocAsync(MH chain)");
+            ctx->chain_cap = need;
+        }
+        // every slot starts again from the exact draw of its next sampling step
+        if ((e = cudaMemsetAsync(ctx->chain, 0, sizeof(int4) * (size_t)ctx->chain_cap, ctx->stream)) != cudaSuccess)
+            return cuda_fail(ctx, e, "cudaMemsetAsync(MH chain)");
+    }
+    ctx->sampler = sampler;
     return RBE_OK;
 }
 

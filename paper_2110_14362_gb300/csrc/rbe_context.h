@@ -115,6 +115,9 @@ struct rbe_ctx_s {
     uint64_t seed = 0;
     int32_t precision = RBE_FP64;
     int32_t rho_accum = RBE_RHO_FP32;
+    int32_t sampler = 0;             // rbe_sampler: exact, offline or Metropolis--Hastings (Sec. 4.3)
+    int4* chain = nullptr;           // MH state per frequency slot (m = 0: start from the exact draw)
+    int32_t chain_cap = 0;
     bool tables_dirty = true;
     int32_t last_K = 0;
     rbe::NptBuffers npt;

@@ -24,6 +24,7 @@
 #include "rbe_context.h"
 #include "rbe_device.cuh"
 #include "rbe_kspace_tiles.cuh"
+#include "rbe_sampler_variants.cuh"
 
 namespace rbe {
 
@@ -43,22 +44,29 @@ __global__ void __launch_bounds__(kTableThreads)
 k_tables_sample(const double* __restrict__ box_dev, double alpha, int P, unsigned long long* __restrict__ cum,
                 int cap, int smem_cap, KState* __restrict__ ks, uint64_t seed,
                 const unsigned long long* __restrict__ step_dev, int4* __restrict__ m_out,
-                double* __restrict__ w_out, unsigned* __restrict__ status)
+                double* __restrict__ w_out, unsigned* __restrict__ status, int mode, int4* __restrict__ chain)
 {
     tables_body(0.0, 0.0, 0.0, box_dev, alpha, P, cum, cap, ks, status);
     __syncthreads();
-    for (int lb = 0; lb < P; lb += kTableThreads)
-        sample_body(lb, seed, 0, step_dev, P, cum, cap, smem_cap, ks, m_out, w_out, status);
+    for (int lb = 0; lb < P; lb += kTableThreads) {
+        if (mode == kSamplerExact) sample_body(lb, seed, 0, step_dev, P, cum, cap, smem_cap, ks, m_out, w_out, status);
+        else sample_variant_body(lb, seed, 0, step_dev, P, cum, cap, ks, mode, chain, m_out, w_out, status);
+    }
 }
 
 // Frequency sampling, one thread per frequency (body in rbe_kspace_tiles.cuh).
 __global__ void k_sample(uint64_t seed, uint64_t step_arg, const unsigned long long* __restrict__ step_dev, int P,
                          const unsigned long long* __restrict__ cum, int cap, int smem_cap,
                          const KState* __restrict__ ks, int4* __restrict__ m_out, double* __restrict__ w_out,
-                         unsigned* __restrict__ status)
+                         unsigned* __restrict__ status, int mode, int4* __restrict__ chain)
 {
-    sample_body((int)(blockIdx.x * blockDim.x), seed, step_arg, step_dev, P, cum, cap, smem_cap, ks, m_out, w_out,
-                status);
+    // the mode is the same for every thread: the exact sampler's code path is unchanged
+    if (mode == kSamplerExact)
+        sample_body((int)(blockIdx.x * blockDim.x), seed, step_arg, step_dev, P, cum, cap, smem_cap, ks, m_out, w_out,
+                    status);
+    else
+        sample_variant_body((int)(blockIdx.x * blockDim.x), seed, step_arg, step_dev, P, cum, cap, ks, mode, chain,
+                            m_out, w_out, status);
 }
 
 // Caller-given frequencies and weights (weighted mode).
@@ -435,17 +443,27 @@ rbe_status launch_sample(rbe_ctx ctx, uint64_t step, int P)
 
 // The sampler on the tables already on the device (built by launch_tables from any box);
 // step_dev, when not NULL, points at a device-resident step index used instead of step.
+// The MH chain holds one state per frequency slot; a sampling call for more slots than it holds
+// is refused (rbe_set_sampler sizes it for the context's P).
+static rbe_status check_chain(rbe_ctx ctx, int P)
+{
+    if (ctx->sampler == kSamplerMH && (!ctx->chain || ctx->chain_cap < P))
+        return fail(ctx, RBE_ESTATE, "the Metropolis-Hastings chain holds fewer slots than this call samples");
+    return RBE_OK;
+}
+
 rbe_status launch_sample_device_box(rbe_ctx ctx, uint64_t step, int P, const unsigned long long* step_dev)
 {
     rbe_status st = ensure_k_capacity(ctx, P);
     if (st != RBE_OK) return st;
+    if ((st = check_chain(ctx, P)) != RBE_OK) return st;
     record_event(ctx, 0);
     const int threads = 128;
     const size_t smem = sizeof(unsigned long long) * 3 * (size_t)ctx->d.tab_cap;
     const int smem_cap = smem <= (size_t)kSampleSmemMax ? ctx->d.tab_cap : 0;
     k_sample<<<(P + threads - 1) / threads, threads, smem_cap ? smem : 0, ctx->stream>>>(
         ctx->seed, step, step_dev, P, ctx->d.cum, ctx->d.tab_cap, smem_cap, ctx->d.ks, ctx->d.m, ctx->d.w,
-        ctx->d.status);
+        ctx->d.status, ctx->sampler, ctx->chain);
     record_event(ctx, 1);
     return check_launch(ctx, "k_sample");
 }
@@ -456,12 +474,13 @@ rbe_status launch_tables_sample_device(rbe_ctx ctx, int P, const double* box_dev
 {
     rbe_status st = ensure_k_capacity(ctx, P);
     if (st != RBE_OK) return st;
+    if ((st = check_chain(ctx, P)) != RBE_OK) return st;
     record_event(ctx, 0);
     const size_t smem = sizeof(unsigned long long) * 3 * (size_t)ctx->d.tab_cap;
     const int smem_cap = smem <= (size_t)kSampleSmemMax ? ctx->d.tab_cap : 0;
     k_tables_sample<<<1, kTableThreads, smem_cap ? smem : 0, ctx->stream>>>(
         box_dev, ctx->alpha, P, ctx->d.cum, ctx->d.tab_cap, smem_cap, ctx->d.ks, ctx->seed, step_dev, ctx->d.m,
-        ctx->d.w, ctx->d.status);
+        ctx->d.w, ctx->d.status, ctx->sampler, ctx->chain);
     record_event(ctx, 1);
     return check_launch(ctx, "k_tables_sample");
 }
