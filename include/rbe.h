@@ -105,6 +105,19 @@ rbe_status rbe_set_precision(rbe_ctx ctx, int32_t precision, int32_t rho_accum);
 typedef enum { RBE_SAMPLER_EXACT = 0, RBE_SAMPLER_OFFLINE = 1, RBE_SAMPLER_MH = 2 } rbe_sampler;
 rbe_status rbe_set_sampler(rbe_ctx ctx, int32_t sampler);
 
+/* A separate batch of Ptilde frequencies for the pressure (Eq. (apppress) with its own p~; the
+ * paper notes that the force and pressure samples may differ).  0 (default): energy and virial
+ * come from the force batch.  Ptilde > 0: every sampling step draws P + Ptilde frequencies (the
+ * force batch in slots [0, P), the same draws as without a pressure batch; the pressure batch in
+ * slots [P, P + Ptilde), Philox slot counters continuing past P); forces use the force batch with
+ * weights S/P, the virial and the energy (E_k, E_self) the pressure batch with weights S/Ptilde.
+ * Applies to rbe_kspace_forces_virial(_host) and rbe_npt_step (its pressure and energies); with
+ * RBE_SAMPLER_MH the chain grows to P + Ptilde slots and restarts from the exact draw.  The host-
+ * buffer call then copies in, evaluates and copies out without pipelining.  rbe_sample_k still
+ * returns the force batch; rbe_get_rho returns the pressure batch's rho.  RBE_EINVAL unless
+ * 0 <= Ptilde <= 2^20. */
+rbe_status rbe_set_pressure_batch(rbe_ctx ctx, int32_t Ptilde);
+
 /* Replace the box lengths (same validity rule as rbe_create).  The per-axis sampling
  * tables are rebuilt on the device at the next evaluation. */
 rbe_status rbe_set_box(rbe_ctx ctx, const double box[3]);

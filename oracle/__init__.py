@@ -103,7 +103,8 @@ class NptParams(ctypes.Structure):
                 ("P", ctypes.c_int32), ("kspace", ctypes.c_int32), ("real", ctypes.c_int32),
                 ("noise", ctypes.c_int32), ("barostat", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("M_cell", ctypes.c_double * 3), ("gamma0", ctypes.c_double),
-                ("sampler", ctypes.c_int32), ("pad2", ctypes.c_int32), ("chain", ctypes.c_void_p)]
+                ("sampler", ctypes.c_int32), ("pad2", ctypes.c_int32), ("chain", ctypes.c_void_p),
+                ("Ptilde", ctypes.c_int32), ("pad3", ctypes.c_int32)]
 
 
 def _bind_npt(lib):
@@ -351,7 +352,8 @@ def npt_params(**kw) -> NptParams:
     1 bar, dt = 1 fs, gamma = 10/ps, gamma_V = 2/ps, alpha = 0.2, rc = 7, LJ 2 A / 0.5 kJ/mol."""
     d = dict(dt=0.001, kT=KB * 300.0, P_ext=1.0 * BAR, gamma=10.0, gamma_V=2.0, M_V=1.0, alpha=0.2, rc=7.0,
              qqr2e=QQR2E, lj_sigma=2.0, lj_eps=0.5, max_disp=0.0, P=100, kspace=1, real=1, noise=1,
-             barostat=1, pad=0, seed=1, M_cell=(1.0, 1.0, 1.0), gamma0=0.0, sampler=0, pad2=0, chain=None)
+             barostat=1, pad=0, seed=1, M_cell=(1.0, 1.0, 1.0), gamma0=0.0, sampler=0, pad2=0, chain=None,
+             Ptilde=0, pad3=0)
     d.update(kw)
     d["M_cell"] = (ctypes.c_double * 3)(*[float(x) for x in d["M_cell"]])
     return NptParams(**d)

@@ -73,7 +73,10 @@ typedef struct {
     double gamma0;    /* barostat 3: surface tension times the number of surfaces, kJ/mol/A^2 */
     int32_t sampler;  /* frequencies: 0 exact, 1 offline, 2 Metropolis--Hastings (sampler_oracle.c) */
     int32_t pad2;
-    int32_t* chain;   /* sampler 2: the chain state, P x 3 (in/out; rows of zeros start exact) */
+    int32_t* chain;   /* sampler 2: the chain state, (P + Ptilde) x 3 (in/out; rows of zeros start exact) */
+    int32_t Ptilde;   /* > 0: a separate pressure batch (Eq. (apppress)) of Ptilde frequencies for the
+                         virial and the k-space energy, slots [P, P + Ptilde) of the same draw */
+    int32_t pad3;
 } orc_npt_params;
 
 /* ------------------------------------------------------------------------------ */
@@ -155,29 +158,37 @@ static int npt_forces_parts(int64_t N, const double* r, const double* q, const d
     E[0] = E[1] = E[2] = 0.0;
     int st = NPT_OK;
     if (prm->kspace) {
-        int32_t* m = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)prm->P);
-        double* wl = (double*)malloc(sizeof(double) * (size_t)prm->P);
-        if (!m || !wl) {
-            free(m); free(wl); free(Fk);
+        /* force batch: slots [0, P), weights S/P (Eq. (appforce)); pressure batch: slots
+         * [P, P + Ptilde), weights S/Ptilde (Eq. (apppress)), or the force batch when Ptilde = 0 */
+        const int32_t Pt = prm->Ptilde > 0 ? prm->Ptilde : 0;
+        const int32_t Ptot = prm->P + Pt;
+        int32_t* m = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)(Ptot > 0 ? Ptot : 1));
+        double* wl = (double*)malloc(sizeof(double) * (size_t)(Ptot > 0 ? Ptot : 1));
+        double* Fp = Pt > 0 ? (double*)calloc((size_t)(3 * N + 3), sizeof(double)) : NULL;
+        if (!m || !wl || (Pt > 0 && !Fp)) {
+            free(m); free(wl); free(Fp); free(Fk);
             return NPT_ENOMEM;
         }
         double S = 0.0, Wk[9], Ek[2];
         if (prm->sampler == 1) {
-            st = orc_sample_k_offline(L, prm->alpha, prm->P, prm->seed, step, m, &S);
+            st = orc_sample_k_offline(L, prm->alpha, Ptot, prm->seed, step, m, &S);
         } else if (prm->sampler == 2) {
             if (!prm->chain) {
                 st = NPT_EINVAL;
             } else {
-                st = orc_sample_k_mh(L, prm->alpha, prm->P, prm->seed, step, prm->chain, &S);
-                for (int32_t j = 0; st == NPT_OK && j < 3 * prm->P; ++j) m[j] = prm->chain[j];
+                st = orc_sample_k_mh(L, prm->alpha, Ptot, prm->seed, step, prm->chain, &S);
+                for (int32_t j = 0; st == NPT_OK && j < 3 * Ptot; ++j) m[j] = prm->chain[j];
             }
         } else {
-            st = orc_sample_k(L, prm->alpha, prm->P, prm->seed, step, m, &S);
+            st = orc_sample_k(L, prm->alpha, Ptot, prm->seed, step, m, &S);
         }
         if (st == NPT_OK) {
             for (int32_t l = 0; l < prm->P; ++l) wl[l] = S / (double)prm->P;
+            for (int32_t l = prm->P; l < Ptot; ++l) wl[l] = S / (double)Pt;
             st = orc_rbe_kspace(N, r, q, L, prm->alpha, prm->P, m, wl, Fk, Wk, Ek, NULL);
         }
+        if (st == NPT_OK && Pt > 0)
+            st = orc_rbe_kspace(N, r, q, L, prm->alpha, Pt, m + 3 * prm->P, wl + prm->P, Fp, Wk, Ek, NULL);
         if (st == NPT_OK) {
             for (int64_t i = 0; i < 3 * N; ++i) F[i] += prm->qqr2e * Fk[i];
             W += prm->qqr2e * (Wk[0] + Wk[4] + Wk[8]);
@@ -187,6 +198,7 @@ static int npt_forces_parts(int64_t N, const double* r, const double* q, const d
         }
         free(m);
         free(wl);
+        free(Fp);
     }
     if (st == NPT_OK && prm->real) {
         double Wr[9], Er[2];

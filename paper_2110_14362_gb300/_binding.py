@@ -83,6 +83,7 @@ SIGNATURES = [
     ("rbe_set_stream", ctypes.c_int, [_vp, _vp]),
     ("rbe_set_precision", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
     ("rbe_set_sampler", ctypes.c_int, [_vp, ctypes.c_int32]),
+    ("rbe_set_pressure_batch", ctypes.c_int, [_vp, ctypes.c_int32]),
     ("rbe_set_seed", ctypes.c_int, [_vp, ctypes.c_uint64]),
     ("rbe_set_box", ctypes.c_int, [_vp, _dp]),
     ("rbe_sample_k", ctypes.c_int, [_vp, ctypes.c_uint64, _ip, _dp]),
@@ -201,6 +202,10 @@ def rbe_set_precision(h, precision: int, rho_accum: int = RBE_RHO_FP32):
 
 def rbe_set_sampler(h, sampler: int):
     _check(load().rbe_set_sampler(h, int(sampler)), h)
+
+
+def rbe_set_pressure_batch(h, Ptilde: int):
+    _check(load().rbe_set_pressure_batch(h, int(Ptilde)), h)
 
 
 def rbe_set_seed(h, seed: int):
@@ -531,6 +536,10 @@ class Context:
     def set_sampler(self, sampler: int):
         """RBE_SAMPLER_EXACT, _OFFLINE or _MH (Sec. 4.3); resets the MH chain."""
         rbe_set_sampler(self.h, sampler)
+
+    def set_pressure_batch(self, Ptilde: int):
+        """A separate batch of Ptilde frequencies for the virial and energy (0: the force batch)."""
+        rbe_set_pressure_batch(self.h, Ptilde)
 
     def set_box(self, box):
         rbe_set_box(self.h, box)

@@ -243,7 +243,7 @@ rbe_status rbe_set_sampler(rbe_ctx ctx, int32_t sampler)
         return fail(ctx, RBE_EINVAL, "unknown sampler");
     DeviceGuard g(ctx->device);
     if (sampler == RBE_SAMPLER_MH) {
-        const int32_t need = ctx->P > 0 ? ctx->P : 1;
+        const int32_t need = ctx->P + ctx->Ptilde > 0 ? ctx->P + ctx->Ptilde : 1;
         cudaError_t e = cudaSuccess;
         if (ctx->chain_cap < need) {
             ctx_free(ctx, ctx->chain);
@@ -259,6 +259,15 @@ rbe_status rbe_set_sampler(rbe_ctx ctx, int32_t sampler)
     }
     ctx->sampler = sampler;
     return RBE_OK;
+}
+
+rbe_status rbe_set_pressure_batch(rbe_ctx ctx, int32_t Ptilde)
+{
+    if (!ctx) return RBE_EINVAL;
+    if (Ptilde < 0 || Ptilde > (1 << 20)) return fail(ctx, RBE_EINVAL, "Ptilde must be in [0, 2^20]");
+    ctx->Ptilde = Ptilde;
+    // an MH chain grows with the slots (and every slot restarts from the exact draw)
+    return ctx->sampler == RBE_SAMPLER_MH ? rbe_set_sampler(ctx, RBE_SAMPLER_MH) : RBE_OK;
 }
 
 rbe_status rbe_set_box(rbe_ctx ctx, const double box[3])
@@ -313,7 +322,7 @@ rbe_status rbe_kspace_forces_virial(rbe_ctx ctx, int64_t N, const double* positi
     if ((st = check_dev(ctx, energy_out, "energy_out", false)) != RBE_OK) return st;
     st = launch_sample(ctx, step, ctx->P);
     if (st != RBE_OK) return st;
-    return launch_evaluate(ctx, N, positions, charges, ctx->P, true, forces_out, virial_out, energy_out);
+    return launch_rbe(ctx, N, positions, charges, ctx->P, forces_out, virial_out, energy_out);
 }
 
 // The copy stream and events of the pipelined host-buffer call (created on first use).
@@ -362,7 +371,7 @@ rbe_status rbe_kspace_forces_virial_host(rbe_ctx ctx, int64_t N, const double* p
     cudaStream_t s = ctx->stream;
     // pipelined on the FP32-phase path for systems large enough to split; plain copies else
     const int pieces = N >= (1 << 17) ? 2 : 1;
-    const bool piped = ctx->precision == RBE_FP32_PHASE && pieces > 1;
+    const bool piped = ctx->precision == RBE_FP32_PHASE && pieces > 1 && ctx->Ptilde == 0;
     rbe_status st;
     if (piped) {
         // the copy stream starts after the main stream's earlier work (the staging buffers
@@ -384,7 +393,7 @@ rbe_status rbe_kspace_forces_virial_host(rbe_ctx ctx, int64_t N, const double* p
                 (err = cudaMemcpyAsync(d.q, charges, sizeof(double) * N, cudaMemcpyHostToDevice, s)) != cudaSuccess)
                 return cuda_fail(ctx, err, "cudaMemcpyAsync(H2D)");
         }
-        st = launch_evaluate(ctx, N, d.pos, d.q, ctx->P, true, d.F, d.WE, d.WE + 9);
+        st = launch_rbe(ctx, N, d.pos, d.q, ctx->P, d.F, d.WE, d.WE + 9);
         if (st != RBE_OK) return st;
         if (forces_out && N > 0 &&
             (err = cudaMemcpyAsync(forces_out, d.F, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, s)) != cudaSuccess)

@@ -62,7 +62,7 @@ __global__ void k_bsample(const BItem* __restrict__ items, int P, int blocks_per
     const int r = blockIdx.x / blocks_per_item;
     const int lb = (blockIdx.x % blocks_per_item) * kSampleBlock;
     const BItem it = items[r];
-    sample_body(lb, it.seed, it.step, nullptr, P, cum + (size_t)r * 3 * cap, cap, smem_cap, ks + r,
+    sample_body(lb, it.seed, it.step, nullptr, P, P, cum + (size_t)r * 3 * cap, cap, smem_cap, ks + r,
                 m + (size_t)r * P, w + (size_t)r * P, status);
 }
 

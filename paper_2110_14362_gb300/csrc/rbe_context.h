@@ -118,6 +118,7 @@ struct rbe_ctx_s {
     int32_t sampler = 0;             // rbe_sampler: exact, offline or Metropolis--Hastings (Sec. 4.3)
     int4* chain = nullptr;           // MH state per frequency slot (m = 0: start from the exact draw)
     int32_t chain_cap = 0;
+    int32_t Ptilde = 0;              // frequencies of a separate pressure batch (0: the force batch)
     bool tables_dirty = true;
     int32_t last_K = 0;
     rbe::NptBuffers npt;
@@ -167,6 +168,8 @@ rbe_status npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch);
 rbe_status npt_run(rbe_ctx ctx, rbe_system* sys, int32_t nsteps);
 rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int K,
                            bool uniform_weight, double* F, double* W, double* E);
+rbe_status launch_rbe(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int P, double* F, double* W,
+                      double* E);
 // Pieces of the pipelined host-buffer evaluation (copy stream events: 1 + 2 kMaxPieces).
 constexpr int kMaxPieces = 8;
 rbe_status launch_evaluate_staged(rbe_ctx ctx, int64_t N, const double* h_pos, const double* h_q, double* h_F,

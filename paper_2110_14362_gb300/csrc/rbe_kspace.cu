@@ -41,32 +41,34 @@ k_tables(double bx, double by, double bz, const double* __restrict__ box_dev, do
 // Tables of the device box and the sampler in one block (the NPT step, where the box changes
 // every step): one launch instead of two, the tables read back from this block's own writes.
 __global__ void __launch_bounds__(kTableThreads)
-k_tables_sample(const double* __restrict__ box_dev, double alpha, int P, unsigned long long* __restrict__ cum,
+k_tables_sample(const double* __restrict__ box_dev, double alpha, int Pf, int P, unsigned long long* __restrict__ cum,
                 int cap, int smem_cap, KState* __restrict__ ks, uint64_t seed,
                 const unsigned long long* __restrict__ step_dev, int4* __restrict__ m_out,
                 double* __restrict__ w_out, unsigned* __restrict__ status, int mode, int4* __restrict__ chain)
 {
-    tables_body(0.0, 0.0, 0.0, box_dev, alpha, P, cum, cap, ks, status);
+    tables_body(0.0, 0.0, 0.0, box_dev, alpha, Pf, cum, cap, ks, status);
     __syncthreads();
     for (int lb = 0; lb < P; lb += kTableThreads) {
-        if (mode == kSamplerExact) sample_body(lb, seed, 0, step_dev, P, cum, cap, smem_cap, ks, m_out, w_out, status);
-        else sample_variant_body(lb, seed, 0, step_dev, P, cum, cap, ks, mode, chain, m_out, w_out, status);
+        if (mode == kSamplerExact)
+            sample_body(lb, seed, 0, step_dev, P, Pf, cum, cap, smem_cap, ks, m_out, w_out, status);
+        else
+            sample_variant_body(lb, seed, 0, step_dev, P, Pf, cum, cap, ks, mode, chain, m_out, w_out, status);
     }
 }
 
 // Frequency sampling, one thread per frequency (body in rbe_kspace_tiles.cuh).
-__global__ void k_sample(uint64_t seed, uint64_t step_arg, const unsigned long long* __restrict__ step_dev, int P,
+__global__ void k_sample(uint64_t seed, uint64_t step_arg, const unsigned long long* __restrict__ step_dev, int P, int Pf,
                          const unsigned long long* __restrict__ cum, int cap, int smem_cap,
                          const KState* __restrict__ ks, int4* __restrict__ m_out, double* __restrict__ w_out,
                          unsigned* __restrict__ status, int mode, int4* __restrict__ chain)
 {
     // the mode is the same for every thread: the exact sampler's code path is unchanged
     if (mode == kSamplerExact)
-        sample_body((int)(blockIdx.x * blockDim.x), seed, step_arg, step_dev, P, cum, cap, smem_cap, ks, m_out, w_out,
-                    status);
+        sample_body((int)(blockIdx.x * blockDim.x), seed, step_arg, step_dev, P, Pf, cum, cap, smem_cap, ks, m_out,
+                    w_out, status);
     else
-        sample_variant_body((int)(blockIdx.x * blockDim.x), seed, step_arg, step_dev, P, cum, cap, ks, mode, chain,
-                            m_out, w_out, status);
+        sample_variant_body((int)(blockIdx.x * blockDim.x), seed, step_arg, step_dev, P, Pf, cum, cap, ks, mode,
+                            chain, m_out, w_out, status);
 }
 
 // Caller-given frequencies and weights (weighted mode).
@@ -452,17 +454,20 @@ static rbe_status check_chain(rbe_ctx ctx, int P)
     return RBE_OK;
 }
 
+// P is the force batch; with a pressure batch (ctx->Ptilde > 0) the sampler draws P + Ptilde
+// slots, the pressure batch in slots [P, P + Ptilde) (Philox slot counters continue past P).
 rbe_status launch_sample_device_box(rbe_ctx ctx, uint64_t step, int P, const unsigned long long* step_dev)
 {
-    rbe_status st = ensure_k_capacity(ctx, P);
+    const int Ptot = P + ctx->Ptilde;
+    rbe_status st = ensure_k_capacity(ctx, Ptot);
     if (st != RBE_OK) return st;
-    if ((st = check_chain(ctx, P)) != RBE_OK) return st;
+    if ((st = check_chain(ctx, Ptot)) != RBE_OK) return st;
     record_event(ctx, 0);
     const int threads = 128;
     const size_t smem = sizeof(unsigned long long) * 3 * (size_t)ctx->d.tab_cap;
     const int smem_cap = smem <= (size_t)kSampleSmemMax ? ctx->d.tab_cap : 0;
-    k_sample<<<(P + threads - 1) / threads, threads, smem_cap ? smem : 0, ctx->stream>>>(
-        ctx->seed, step, step_dev, P, ctx->d.cum, ctx->d.tab_cap, smem_cap, ctx->d.ks, ctx->d.m, ctx->d.w,
+    k_sample<<<(Ptot + threads - 1) / threads, threads, smem_cap ? smem : 0, ctx->stream>>>(
+        ctx->seed, step, step_dev, Ptot, P, ctx->d.cum, ctx->d.tab_cap, smem_cap, ctx->d.ks, ctx->d.m, ctx->d.w,
         ctx->d.status, ctx->sampler, ctx->chain);
     record_event(ctx, 1);
     return check_launch(ctx, "k_sample");
@@ -472,14 +477,15 @@ rbe_status launch_sample_device_box(rbe_ctx ctx, uint64_t step, int P, const uns
 // launch.
 rbe_status launch_tables_sample_device(rbe_ctx ctx, int P, const double* box_dev, const unsigned long long* step_dev)
 {
-    rbe_status st = ensure_k_capacity(ctx, P);
+    const int Ptot = P + ctx->Ptilde;
+    rbe_status st = ensure_k_capacity(ctx, Ptot);
     if (st != RBE_OK) return st;
-    if ((st = check_chain(ctx, P)) != RBE_OK) return st;
+    if ((st = check_chain(ctx, Ptot)) != RBE_OK) return st;
     record_event(ctx, 0);
     const size_t smem = sizeof(unsigned long long) * 3 * (size_t)ctx->d.tab_cap;
     const int smem_cap = smem <= (size_t)kSampleSmemMax ? ctx->d.tab_cap : 0;
     k_tables_sample<<<1, kTableThreads, smem_cap ? smem : 0, ctx->stream>>>(
-        box_dev, ctx->alpha, P, ctx->d.cum, ctx->d.tab_cap, smem_cap, ctx->d.ks, ctx->seed, step_dev, ctx->d.m,
+        box_dev, ctx->alpha, P, Ptot, ctx->d.cum, ctx->d.tab_cap, smem_cap, ctx->d.ks, ctx->seed, step_dev, ctx->d.m,
         ctx->d.w, ctx->d.status, ctx->sampler, ctx->chain);
     record_event(ctx, 1);
     return check_launch(ctx, "k_tables_sample");
@@ -613,10 +619,15 @@ static rbe_status evaluate_shape(rbe_ctx ctx, int64_t N, int K, EvalShape* out)
     return RBE_OK;
 }
 
-rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int K,
-                           bool /*uniform_weight*/, double* F, double* W, double* E)
+// One evaluation over the frequencies [koff, koff + K) of the sampled batch: rho, reduction and,
+// with forces, the force pass; W and E (either may be NULL) from the same frequencies.  Without
+// forces only the energy and virial are formed (the pressure batch of Eq. (apppress)).
+static rbe_status launch_evaluate_range(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int koff, int K,
+                                        bool forces, double* F, double* W, double* E)
 {
     DeviceBuffers& d = ctx->d;
+    const int4* m_in = d.m + koff;
+    const double* w_in = d.w + koff;
     EvalShape sh;
     rbe_status st0 = evaluate_shape(ctx, N, K, &sh);
     if (st0 != RBE_OK) return st0;
@@ -629,12 +640,12 @@ rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const doub
     float4* part32 = static_cast<float4*>(d.partials);
     const KState* ks = d.ks;
     if (fp64) {
-        k_rho_f64<<<grid, p.kthreads, 0, s>>>(pos, q, N, ks, d.m, K, p.chunk_len, p.nchunks, part64, d.status);
+        k_rho_f64<<<grid, p.kthreads, 0, s>>>(pos, q, N, ks, m_in, K, p.chunk_len, p.nchunks, part64, d.status);
     } else {
         auto kern = ctx->rho_accum == RBE_RHO_FP64     ? k_rho_f32<RBE_RHO_FP64>
                     : ctx->rho_accum == RBE_RHO_COMP32 ? k_rho_f32<RBE_RHO_COMP32>
                                                        : k_rho_f32<RBE_RHO_FP32>;
-        cudaError_t err = launch_pdl(kern, grid, dim3(p.kthreads), 0, s, pos, q, N, ks, (const int4*)d.m, K,
+        cudaError_t err = launch_pdl(kern, grid, dim3(p.kthreads), 0, s, pos, q, N, ks, m_in, K,
                                      p.chunk_len, p.nchunks, part32, d.status, 0);
         if (err != cudaSuccess) return cuda_fail(ctx, err, "launch k_rho_f32");
     }
@@ -642,11 +653,11 @@ rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const doub
     if (st != RBE_OK) return st;
     record_event(ctx, 2);
     if (fp64) {
-        k_reduce<<<K + 1, kReduceThreads, 0, s>>>(part64, p.nchunks, K, d.m, d.w, ks, d.rho, d.terms, d.coef_d,
+        k_reduce<<<K + 1, kReduceThreads, 0, s>>>(part64, p.nchunks, K, m_in, w_in, ks, d.rho, d.terms, d.coef_d,
                                                    d.counter, d.status, W, E);
     } else {
         cudaError_t err = launch_pdl(k_reduce_f32, dim3(K + 1), dim3(kReduceThreads), 0, s, (const float4*)part32,
-                                     p.nchunks, K, (const int4*)d.m, (const double*)d.w, ks, d.rho,
+                                     p.nchunks, K, m_in, w_in, ks, d.rho,
                                      reinterpret_cast<float*>(d.terms), d.coef_m, d.coef_f, d.status);
         if (err != cudaSuccess) return cuda_fail(ctx, err, "launch k_reduce_f32");
     }
@@ -654,13 +665,13 @@ rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const doub
     if (st != RBE_OK) return st;
     record_event(ctx, 3);
     if (fp64) {
-        if (p.fblocks > 0) {
+        if (forces && p.fblocks > 0) {
             k_force_f64<2><<<p.fblocks, kT, 0, s>>>(pos, q, N, p.per_block, ks, d.m, d.coef_d, K, F);
             st = check_launch(ctx, "k_force");
         }
     } else {
         // one extra block computes the energy and virial sums
-        cudaError_t err = launch_pdl(k_force_f32, dim3(p.fblocks + 1), dim3(kForceThreads), force_smem, s, pos, q,
+        cudaError_t err = launch_pdl(k_force_f32, dim3((forces ? p.fblocks : 0) + 1), dim3(kForceThreads), force_smem, s, pos, q,
                                      N, p.per_block, ks, (const int4*)d.coef_m, (const float4*)d.coef_f, K, F,
                                      d.status, reinterpret_cast<const float*>(d.terms), W, E, (int64_t)0, 1);
         st = err == cudaSuccess ? RBE_OK : cuda_fail(ctx, err, "launch k_force_f32");
@@ -669,6 +680,24 @@ rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const doub
     record_event(ctx, 4);
     ctx->last_K = K;
     return RBE_OK;
+}
+
+rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int K,
+                           bool /*uniform_weight*/, double* F, double* W, double* E)
+{
+    return launch_evaluate_range(ctx, N, pos, q, 0, K, true, F, W, E);
+}
+
+// The RBE evaluation of a sampled step: forces from the force batch (slots [0, P)) and, with a
+// pressure batch (ctx->Ptilde > 0), energy and virial from slots [P, P + Ptilde) with weights
+// S/Ptilde (Eqs. (appforce), (apppress) with p and p~); otherwise all from the one batch.
+rbe_status launch_rbe(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int P, double* F, double* W,
+                      double* E)
+{
+    if (ctx->Ptilde <= 0) return launch_evaluate_range(ctx, N, pos, q, 0, P, true, F, W, E);
+    rbe_status st = launch_evaluate_range(ctx, N, pos, q, 0, P, true, F, nullptr, nullptr);
+    if (st != RBE_OK) return st;
+    return launch_evaluate_range(ctx, N, pos, q, P, ctx->Ptilde, false, nullptr, W, E);
 }
 
 // The host-buffer evaluation on the FP32-phase path, pipelined in quarters: the particles

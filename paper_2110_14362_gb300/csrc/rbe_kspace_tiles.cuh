@@ -168,8 +168,10 @@ __device__ __forceinline__ unsigned long long scaled_target(unsigned long long U
 // operations only: U from 53 bits of Philox output, T = floor(U C_2M / 2^53), and the
 // search over the integer cumulative weights.  The block copies the three rows to shared
 // memory when they fit (smem_cap > 0).
+// Slots [0, Pf) are the force batch (weight S/P_f, the tables' wP); slots [Pf, P), when P > Pf,
+// a separate pressure batch (weight S/(P - Pf), Eq. (apppress) with its own p~).
 __device__ __forceinline__ void sample_body(int lbase, uint64_t seed, uint64_t step_arg,
-                                            const unsigned long long* __restrict__ step_dev, int P,
+                                            const unsigned long long* __restrict__ step_dev, int P, int Pf,
                          const unsigned long long* __restrict__ cum, int cap, int smem_cap,
                          const KState* __restrict__ ks, int4* __restrict__ m_out, double* __restrict__ w_out,
                          unsigned* __restrict__ status)
@@ -213,7 +215,7 @@ __device__ __forceinline__ void sample_body(int lbase, uint64_t seed, uint64_t s
         m = make_int4(1, 0, 0, 0);  // keeps the evaluation finite; the call reports RBE_ESAMPLE
     }
     m_out[l] = m;
-    w_out[l] = wP;
+    w_out[l] = l < Pf ? wP : ks->S / (double)(P - Pf);
 }
 
 // Fixed-order block sum of a float-float value per thread; valid in thread 0.

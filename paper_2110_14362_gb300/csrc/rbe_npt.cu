@@ -1481,7 +1481,7 @@ static rbe_status npt_forces(rbe_ctx ctx, rbe_system* sys, uint64_t batch, int d
             RBE_OK)
             return st;
         ctx->tables_dirty = true;  // the snapshot API must rebuild from its own box
-        if ((st = launch_evaluate(ctx, N, sys->pos, sys->charge, ctx->P, true, b.Fk, b.WEk, b.WEk + 9)) != RBE_OK)
+        if ((st = launch_rbe(ctx, N, sys->pos, sys->charge, ctx->P, b.Fk, b.WEk, b.WEk + 9)) != RBE_OK)
             return st;
     }
     if (prm.real && N > 0) {

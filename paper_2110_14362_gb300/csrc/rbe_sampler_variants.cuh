@@ -161,9 +161,10 @@ __device__ __forceinline__ bool smp_exact(const unsigned long long* __restrict__
 }
 
 // Slots lbase + threadIdx.x of the offline or MH sampler; chain[P] holds the MH state (m = 0:
-// start from the exact draw).  Weights S/P, like the exact sampler.
+// start from the exact draw).  Weights as the exact sampler's (force slots [0, Pf), pressure
+// slots [Pf, P)).
 __device__ __forceinline__ void sample_variant_body(int lbase, uint64_t seed, uint64_t step_arg,
-                                                    const unsigned long long* __restrict__ step_dev, int P,
+                                                    const unsigned long long* __restrict__ step_dev, int P, int Pf,
                                                     const unsigned long long* __restrict__ cum, int cap,
                                                     const KState* __restrict__ ks, int mode, int4* __restrict__ chain,
                                                     int4* __restrict__ m_out, double* __restrict__ w_out,
@@ -214,7 +215,7 @@ __device__ __forceinline__ void sample_variant_body(int lbase, uint64_t seed, ui
         m = make_int4(1, 0, 0, 0);  // keeps the evaluation finite; the call reports RBE_ESAMPLE
     }
     m_out[l] = m;
-    w_out[l] = ks->wP;
+    w_out[l] = l < Pf ? ks->wP : ks->S / (double)(P - Pf);
 }
 
 }  // namespace rbe
