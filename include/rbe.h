@@ -118,6 +118,16 @@ rbe_status rbe_set_sampler(rbe_ctx ctx, int32_t sampler);
  * 0 <= Ptilde <= 2^20. */
 rbe_status rbe_set_pressure_batch(rbe_ctx ctx, int32_t Ptilde);
 
+/* Sample reuse for the NPT step (Sec. 4.3, the strategy that updates the samples every M
+ * steps).  M = 1 (default): every step draws its own frequencies.  M > 1: at a step s with
+ * s mod M = 0 the sampler draws M batches at once from that step's box (counter step s, batch i
+ * in slots [i (P + Ptilde), (i + 1) (P + Ptilde))), kept on the device; step s + i evaluates
+ * batch i with the wave vectors k = 2 pi m / l and the weights S/P (S/Ptilde) of its own box.
+ * Batch 0 is the ordinary draw of step s; the later batches carry the stale-box error the paper
+ * describes.  Applies to rbe_npt_step only.  RBE_EINVAL unless 1 <= M <= 1024, or with the
+ * Metropolis--Hastings sampler (the two exclude each other). */
+rbe_status rbe_set_sample_reuse(rbe_ctx ctx, int32_t M);
+
 /* Replace the box lengths (same validity rule as rbe_create).  The per-axis sampling
  * tables are rebuilt on the device at the next evaluation. */
 rbe_status rbe_set_box(rbe_ctx ctx, const double box[3]);

@@ -104,7 +104,7 @@ class NptParams(ctypes.Structure):
                 ("noise", ctypes.c_int32), ("barostat", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("M_cell", ctypes.c_double * 3), ("gamma0", ctypes.c_double),
                 ("sampler", ctypes.c_int32), ("pad2", ctypes.c_int32), ("chain", ctypes.c_void_p),
-                ("Ptilde", ctypes.c_int32), ("pad3", ctypes.c_int32)]
+                ("Ptilde", ctypes.c_int32), ("reuse", ctypes.c_int32), ("reuse_m", ctypes.c_void_p)]
 
 
 def _bind_npt(lib):
@@ -353,7 +353,7 @@ def npt_params(**kw) -> NptParams:
     d = dict(dt=0.001, kT=KB * 300.0, P_ext=1.0 * BAR, gamma=10.0, gamma_V=2.0, M_V=1.0, alpha=0.2, rc=7.0,
              qqr2e=QQR2E, lj_sigma=2.0, lj_eps=0.5, max_disp=0.0, P=100, kspace=1, real=1, noise=1,
              barostat=1, pad=0, seed=1, M_cell=(1.0, 1.0, 1.0), gamma0=0.0, sampler=0, pad2=0, chain=None,
-             Ptilde=0, pad3=0)
+             Ptilde=0, reuse=1, reuse_m=None)
     d.update(kw)
     d["M_cell"] = (ctypes.c_double * 3)(*[float(x) for x in d["M_cell"]])
     return NptParams(**d)

@@ -76,7 +76,10 @@ typedef struct {
     int32_t* chain;   /* sampler 2: the chain state, (P + Ptilde) x 3 (in/out; rows of zeros start exact) */
     int32_t Ptilde;   /* > 0: a separate pressure batch (Eq. (apppress)) of Ptilde frequencies for the
                          virial and the k-space energy, slots [P, P + Ptilde) of the same draw */
-    int32_t pad3;
+    int32_t reuse;    /* > 1: samples drawn every `reuse` steps (Sec. 4.3): at a step s with
+                         s mod reuse = 0, reuse batches of P + Ptilde slots from the box of step s
+                         into reuse_m; step s + i evaluates batch i with its own box's k and S */
+    int32_t* reuse_m; /* reuse x (P + Ptilde) x 3 (kept between steps) */
 } orc_npt_params;
 
 /* ------------------------------------------------------------------------------ */
@@ -170,7 +173,22 @@ static int npt_forces_parts(int64_t N, const double* r, const double* q, const d
             return NPT_ENOMEM;
         }
         double S = 0.0, Wk[9], Ek[2];
-        if (prm->sampler == 1) {
+        if (prm->reuse > 1 && prm->sampler != 2) {
+            const int32_t i = (int32_t)(step % (uint64_t)prm->reuse);
+            if (!prm->reuse_m) {
+                st = NPT_EINVAL;
+            } else if (i == 0) {
+                /* draw every batch from this step's box (batch 0 is the ordinary draw) */
+                int32_t Pall = prm->reuse * Ptot;
+                st = prm->sampler == 1 ? orc_sample_k_offline(L, prm->alpha, Pall, prm->seed, step, prm->reuse_m, &S)
+                                       : orc_sample_k(L, prm->alpha, Pall, prm->seed, step, prm->reuse_m, &S);
+            }
+            /* S of the current box (the weights), batch i of the kept draws */
+            if (st == NPT_OK) st = orc_sample_k(L, prm->alpha, 0, prm->seed, step, NULL, &S);
+            for (int32_t j = 0; st == NPT_OK && j < 3 * Ptot; ++j) m[j] = prm->reuse_m[3 * (size_t)i * Ptot + j];
+        } else if (prm->reuse > 1) {
+            st = NPT_EINVAL; /* reuse and the Metropolis--Hastings chain exclude each other */
+        } else if (prm->sampler == 1) {
             st = orc_sample_k_offline(L, prm->alpha, Ptot, prm->seed, step, m, &S);
         } else if (prm->sampler == 2) {
             if (!prm->chain) {

@@ -15,5 +15,5 @@ from ._binding import (  # noqa: F401
     NptParams, System, NptReplica, rbe_npt_init, rbe_npt_step, RBE_CELL_DOUBLES, Server, ServerConfig, Request, piston_mass,
     piston_masses_rect, RBE_BAROSTAT_NONE, RBE_BAROSTAT_ISO, RBE_BAROSTAT_ANISO, RBE_BAROSTAT_SEMI, CELL_PC,
     CELL_WD, CELL_K2D, CELL_PD, Batch, BatchItem,
-    rbe_set_seed, rbe_set_sampler, rbe_set_pressure_batch, RBE_SAMPLER_EXACT, RBE_SAMPLER_OFFLINE, RBE_SAMPLER_MH,
+    rbe_set_seed, rbe_set_sampler, rbe_set_pressure_batch, rbe_set_sample_reuse, RBE_SAMPLER_EXACT, RBE_SAMPLER_OFFLINE, RBE_SAMPLER_MH,
 )

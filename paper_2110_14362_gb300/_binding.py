@@ -84,6 +84,7 @@ SIGNATURES = [
     ("rbe_set_precision", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
     ("rbe_set_sampler", ctypes.c_int, [_vp, ctypes.c_int32]),
     ("rbe_set_pressure_batch", ctypes.c_int, [_vp, ctypes.c_int32]),
+    ("rbe_set_sample_reuse", ctypes.c_int, [_vp, ctypes.c_int32]),
     ("rbe_set_seed", ctypes.c_int, [_vp, ctypes.c_uint64]),
     ("rbe_set_box", ctypes.c_int, [_vp, _dp]),
     ("rbe_sample_k", ctypes.c_int, [_vp, ctypes.c_uint64, _ip, _dp]),
@@ -206,6 +207,10 @@ def rbe_set_sampler(h, sampler: int):
 
 def rbe_set_pressure_batch(h, Ptilde: int):
     _check(load().rbe_set_pressure_batch(h, int(Ptilde)), h)
+
+
+def rbe_set_sample_reuse(h, M: int):
+    _check(load().rbe_set_sample_reuse(h, int(M)), h)
 
 
 def rbe_set_seed(h, seed: int):
@@ -540,6 +545,10 @@ class Context:
     def set_pressure_batch(self, Ptilde: int):
         """A separate batch of Ptilde frequencies for the virial and energy (0: the force batch)."""
         rbe_set_pressure_batch(self.h, Ptilde)
+
+    def set_sample_reuse(self, M: int):
+        """NPT: draw the frequencies of M steps at once, every M steps (1: every step)."""
+        rbe_set_sample_reuse(self.h, M)
 
     def set_box(self, box):
         rbe_set_box(self.h, box)

@@ -201,6 +201,7 @@ rbe_status rbe_destroy(rbe_ctx ctx)
     free_npt(ctx->npt);
     free_buffers(ctx->d);
     if (ctx->chain) cudaFree(ctx->chain);
+    if (ctx->m_all) cudaFree(ctx->m_all);
     delete ctx;
     return RBE_OK;
 }
@@ -242,6 +243,8 @@ rbe_status rbe_set_sampler(rbe_ctx ctx, int32_t sampler)
     if (sampler != RBE_SAMPLER_EXACT && sampler != RBE_SAMPLER_OFFLINE && sampler != RBE_SAMPLER_MH)
         return fail(ctx, RBE_EINVAL, "unknown sampler");
     DeviceGuard g(ctx->device);
+    if (sampler == RBE_SAMPLER_MH && ctx->reuse > 1)
+        return fail(ctx, RBE_EINVAL, "sample reuse and the Metropolis-Hastings chain exclude each other");
     if (sampler == RBE_SAMPLER_MH) {
         const int32_t need = ctx->P + ctx->Ptilde > 0 ? ctx->P + ctx->Ptilde : 1;
         cudaError_t e = cudaSuccess;
@@ -268,6 +271,16 @@ rbe_status rbe_set_pressure_batch(rbe_ctx ctx, int32_t Ptilde)
     ctx->Ptilde = Ptilde;
     // an MH chain grows with the slots (and every slot restarts from the exact draw)
     return ctx->sampler == RBE_SAMPLER_MH ? rbe_set_sampler(ctx, RBE_SAMPLER_MH) : RBE_OK;
+}
+
+rbe_status rbe_set_sample_reuse(rbe_ctx ctx, int32_t M)
+{
+    if (!ctx) return RBE_EINVAL;
+    if (M < 1 || M > 1024) return fail(ctx, RBE_EINVAL, "M must be in [1, 1024]");
+    if (M > 1 && ctx->sampler == RBE_SAMPLER_MH)
+        return fail(ctx, RBE_EINVAL, "sample reuse and the Metropolis-Hastings chain exclude each other");
+    ctx->reuse = M;
+    return RBE_OK;
 }
 
 rbe_status rbe_set_box(rbe_ctx ctx, const double box[3])

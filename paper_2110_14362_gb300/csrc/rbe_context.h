@@ -119,6 +119,9 @@ struct rbe_ctx_s {
     int4* chain = nullptr;           // MH state per frequency slot (m = 0: start from the exact draw)
     int32_t chain_cap = 0;
     int32_t Ptilde = 0;              // frequencies of a separate pressure batch (0: the force batch)
+    int32_t reuse = 1;               // NPT: samples drawn every `reuse` steps, kept on the device
+    int4* m_all = nullptr;           // reuse > 1: the kept batches, reuse x (P + Ptilde)
+    int64_t m_all_cap = 0;
     bool tables_dirty = true;
     int32_t last_K = 0;
     rbe::NptBuffers npt;

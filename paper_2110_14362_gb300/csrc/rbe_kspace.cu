@@ -40,19 +40,45 @@ k_tables(double bx, double by, double bz, const double* __restrict__ box_dev, do
 
 // Tables of the device box and the sampler in one block (the NPT step, where the box changes
 // every step): one launch instead of two, the tables read back from this block's own writes.
+// reuse > 1 (samples kept for `reuse` steps, Sec. 4.3): at a step s with s mod reuse = 0 the
+// block draws reuse * P slots (counter step s, slot i P + l for batch i) from this step's tables
+// into m_all; step s + i takes batch i, with the weights of its own (current) tables.
 __global__ void __launch_bounds__(kTableThreads)
 k_tables_sample(const double* __restrict__ box_dev, double alpha, int Pf, int P, unsigned long long* __restrict__ cum,
                 int cap, int smem_cap, KState* __restrict__ ks, uint64_t seed,
                 const unsigned long long* __restrict__ step_dev, int4* __restrict__ m_out,
-                double* __restrict__ w_out, unsigned* __restrict__ status, int mode, int4* __restrict__ chain)
+                double* __restrict__ w_out, unsigned* __restrict__ status, int mode, int4* __restrict__ chain,
+                int reuse, int4* __restrict__ m_all)
 {
     tables_body(0.0, 0.0, 0.0, box_dev, alpha, Pf, cum, cap, ks, status);
     __syncthreads();
-    for (int lb = 0; lb < P; lb += kTableThreads) {
-        if (mode == kSamplerExact)
-            sample_body(lb, seed, 0, step_dev, P, Pf, cum, cap, smem_cap, ks, m_out, w_out, status);
-        else
-            sample_variant_body(lb, seed, 0, step_dev, P, Pf, cum, cap, ks, mode, chain, m_out, w_out, status);
+    if (reuse <= 1) {
+        for (int lb = 0; lb < P; lb += kTableThreads) {
+            if (mode == kSamplerExact)
+                sample_body(lb, seed, 0, step_dev, P, Pf, cum, cap, smem_cap, ks, m_out, w_out, status);
+            else
+                sample_variant_body(lb, seed, 0, step_dev, P, Pf, cum, cap, ks, mode, chain, m_out, w_out, status);
+        }
+        return;
+    }
+    const uint64_t step = *step_dev;
+    const int i = (int)(step % (uint64_t)reuse);  // the same for every thread
+    if (i == 0) {
+        const int Pall = reuse * P;
+        for (int lb = 0; lb < Pall; lb += kTableThreads) {
+            if (mode == kSamplerExact)
+                sample_body(lb, seed, 0, step_dev, Pall, Pall, cum, cap, smem_cap, ks, m_all, nullptr, status);
+            else
+                sample_variant_body(lb, seed, 0, step_dev, Pall, Pall, cum, cap, ks, mode, chain, m_all, nullptr,
+                                    status);
+        }
+        __syncthreads();
+    }
+    pdl_trigger();
+    const double wP = ks->wP, wT = P > Pf ? ks->S / (double)(P - Pf) : 0.0;
+    for (int l = threadIdx.x; l < P; l += kTableThreads) {
+        m_out[l] = m_all[(size_t)i * P + l];
+        w_out[l] = l < Pf ? wP : wT;
     }
 }
 
@@ -481,12 +507,26 @@ rbe_status launch_tables_sample_device(rbe_ctx ctx, int P, const double* box_dev
     rbe_status st = ensure_k_capacity(ctx, Ptot);
     if (st != RBE_OK) return st;
     if ((st = check_chain(ctx, Ptot)) != RBE_OK) return st;
+    const int reuse = ctx->reuse > 1 ? ctx->reuse : 1;
+    if (reuse > 1) {
+        if (ctx->sampler == kSamplerMH)
+            return fail(ctx, RBE_ESTATE, "sample reuse and the Metropolis-Hastings chain exclude each other");
+        const int64_t need = (int64_t)reuse * Ptot;
+        if (need > ctx->m_all_cap) {
+            ctx_free(ctx, ctx->m_all);
+            ctx->m_all = nullptr;
+            ctx->m_all_cap = 0;
+            cudaError_t e = ctx_alloc(ctx, &ctx->m_all, sizeof(int4) * (size_t)need);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMallocAsync(reused samples)");
+            ctx->m_all_cap = need;
+        }
+    }
     record_event(ctx, 0);
     const size_t smem = sizeof(unsigned long long) * 3 * (size_t)ctx->d.tab_cap;
     const int smem_cap = smem <= (size_t)kSampleSmemMax ? ctx->d.tab_cap : 0;
     k_tables_sample<<<1, kTableThreads, smem_cap ? smem : 0, ctx->stream>>>(
         box_dev, ctx->alpha, P, Ptot, ctx->d.cum, ctx->d.tab_cap, smem_cap, ctx->d.ks, ctx->seed, step_dev, ctx->d.m,
-        ctx->d.w, ctx->d.status, ctx->sampler, ctx->chain);
+        ctx->d.w, ctx->d.status, ctx->sampler, ctx->chain, reuse, ctx->m_all);
     record_event(ctx, 1);
     return check_launch(ctx, "k_tables_sample");
 }

@@ -215,7 +215,7 @@ __device__ __forceinline__ void sample_variant_body(int lbase, uint64_t seed, ui
         m = make_int4(1, 0, 0, 0);  // keeps the evaluation finite; the call reports RBE_ESAMPLE
     }
     m_out[l] = m;
-    w_out[l] = l < Pf ? ks->wP : ks->S / (double)(P - Pf);
+    if (w_out) w_out[l] = l < Pf ? ks->wP : ks->S / (double)(P - Pf);
 }
 
 }  // namespace rbe

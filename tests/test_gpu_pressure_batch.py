@@ -107,3 +107,68 @@ def test_pressure_batch_rejects_bad_sizes():
             with pytest.raises(rbe.RBEError) as e:
                 ctx.set_pressure_batch(bad)
             assert e.value.status == rbe.RBE_EINVAL
+
+
+def _npt_lattice(n_side=8, seed=2):
+    N = n_side ** 3
+    L = (N / 0.1) ** (1 / 3)
+    rng = np.random.default_rng(seed)
+    g = (np.arange(n_side) + 0.5) * (L / n_side)
+    pos = np.mod(np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+                 + rng.uniform(-0.3, 0.3, (N, 3)), L)
+    q = np.where(np.arange(N) % 2 == 0, 1.0, -1.0)
+    m = np.full(N, 20.0)
+    mom = rng.normal(size=(N, 3)) * np.sqrt(oracle.KB * 300 * 100 * m)[:, None]
+    base = dict(dt=0.001, kT=oracle.KB * 300.0, P_ext=oracle.BAR, gamma=10.0, gamma_V=2.0,
+                M_V=oracle.piston_mass(0.5, 4.5e-5 / oracle.BAR, L ** 3), rc=6.5, qqr2e=oracle.QQR2E / 78.5,
+                lj_sigma=2.0, lj_eps=0.5, max_disp=0.05, kspace=1, real=1, noise=1, barostat=1)
+    return pos, mom, q, m, np.array([L, L, L]), base
+
+
+@pytest.mark.parametrize("sampler,Pt", [(rbe.RBE_SAMPLER_EXACT, 0), (rbe.RBE_SAMPLER_OFFLINE, 40)])
+def test_npt_sample_reuse(sampler, Pt):
+    """Samples drawn every M = 4 steps from the box of the drawing step (Sec. 4.3): nine NPT steps
+    (three refreshes) against the oracle's NPT step with the same reuse, at 1e-10; the run differs
+    from the one without reuse (the kept batches are really used)."""
+    P, seed, M, n = 100, 99, 4, 9
+    pos, mom, q, m, box, base = _npt_lattice()
+    dev = cuda_device()
+    res = {}
+    for reuse in (1, M):
+        with rbe.Context(box, ALPHA, P, seed, rbe.RBE_FP64) as ctx:
+            ctx.set_sampler(sampler)
+            ctx.set_pressure_batch(Pt)
+            ctx.set_sample_reuse(reuse)
+            rep = rbe.NptReplica(pos, mom, q, m, box, rbe.NptParams(**base), dev, step=0)
+            rep.init(ctx, batch=0)
+            rep.step(ctx, n)
+            ctx.sync()
+            res[reuse] = rep.state()
+    r_d, p_d, F_d, L_d, cell = res[M]
+    buf = np.zeros((M * (P + Pt), 3), dtype=np.int32)
+    prm = oracle.npt_params(alpha=ALPHA, P=P, seed=seed, sampler=sampler, Ptilde=Pt, reuse=M,
+                            reuse_m=buf.ctypes.data, **base)
+    st = oracle.NptState(pos, mom, q, m, box)
+    oracle.npt_forces(st, 0, prm)
+    for s in range(n):
+        oracle.npt_step(st, s, prm)
+    assert np.allclose(L_d, st.L, rtol=1e-12, atol=0)
+    assert np.abs(p_d - st.p).max() < 1e-10 * np.abs(st.p).max()
+    assert np.abs(F_d - st.F).max() < 1e-10 * np.abs(st.F).max()
+    assert abs(cell[4] - st.W.value) < 1e-10 * abs(st.W.value)
+    assert np.abs(res[1][2] - F_d).max() > 1e-6 * np.abs(F_d).max()
+
+
+def test_sample_reuse_and_mh_exclude_each_other():
+    cuda_device()
+    with rbe.Context((20.0, 20.0, 20.0), ALPHA, 16, 1, rbe.RBE_FP64) as ctx:
+        ctx.set_sampler(rbe.RBE_SAMPLER_MH)
+        with pytest.raises(rbe.RBEError):
+            ctx.set_sample_reuse(4)
+        ctx.set_sampler(rbe.RBE_SAMPLER_EXACT)
+        ctx.set_sample_reuse(4)
+        with pytest.raises(rbe.RBEError):
+            ctx.set_sampler(rbe.RBE_SAMPLER_MH)
+        for bad in (0, 1025):
+            with pytest.raises(rbe.RBEError):
+                ctx.set_sample_reuse(bad)
