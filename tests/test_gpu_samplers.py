@@ -125,3 +125,32 @@ def test_npt_with_variant_samplers(sampler):
     assert np.abs(d).max() < 1e-10 * L
     assert np.abs(p_d - st.p).max() < 1e-10 * np.abs(st.p).max()
     assert np.abs(F_d - st.F).max() < 1e-10 * np.abs(st.F).max()
+
+
+@pytest.mark.parametrize("sampler", [rbe.RBE_SAMPLER_EXACT, rbe.RBE_SAMPLER_OFFLINE, rbe.RBE_SAMPLER_MH])
+def test_sampler_bias_on_the_device(sampler):
+    """The mean device force over 400 steps (P = 500, sigma = 0.5 per axis) converges to the exact
+    expectation of its sampler: the Ewald force for the exact and MH samplers, the offline
+    expectation (21 % of the force RMS away from it) for the offline one.  Standard errors from 20
+    batch means of 20 steps (the MH chain correlates consecutive steps)."""
+    import torch
+    from test_oracle_samplers import offline_bias_case
+    pos, q, box, alpha, F_off, F_ew, _, _ = offline_bias_case()
+    dev = cuda_device()
+    N, P, n = q.shape[0], 500, 400
+    tp, tq = torch.as_tensor(pos).to(dev), torch.as_tensor(q).to(dev)
+    Fs = np.zeros((n, N, 3))
+    with rbe.Context(box, alpha, P, 5, rbe.RBE_FP64) as ctx:
+        ctx.set_stream(torch.cuda.current_stream().cuda_stream)
+        ctx.set_sampler(sampler)
+        F = torch.empty((N, 3), dtype=torch.float64, device=dev)
+        for s in range(n):
+            ctx.forces_virial(tp, tq, s, F)
+            Fs[s] = F.cpu().numpy()
+    bm = Fs.reshape(20, 20, N, 3).mean(1)
+    mean, se = bm.mean(0), bm.std(0, ddof=1) / np.sqrt(20)
+    target, other = (F_off, F_ew) if sampler == rbe.RBE_SAMPLER_OFFLINE else (F_ew, F_off)
+    chi_t = np.mean(((mean - target) / se) ** 2)
+    chi_o = np.mean(((mean - other) / se) ** 2)
+    assert chi_t < 2.0, chi_t  # about 1.1-1.3 for the right expectation (t with 19 dof, correlated components)
+    assert chi_o > 10 * chi_t, (chi_t, chi_o)

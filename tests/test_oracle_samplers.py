@@ -171,3 +171,63 @@ def test_mh_slot_starts_from_the_exact_draw():
     assert np.array_equal(st, m)
     _, S2 = oracle.sample_k_offline(box, ALPHA, 1, 8, 3)
     assert S2 == S
+
+
+def _offline_expectation_weights(box, alpha, kmax):
+    """m over the cube |m_j| <= kmax without 0 and the weights S P_off(m) that make the weighted
+    RBE sum the expectation of the offline estimator (S = sum of exp(-k^2/4 alpha) over m != 0)."""
+    sig = _sigmas(box, alpha)
+    r = np.arange(-kmax, kmax + 1)
+    q = [stats.norm.sf((np.abs(r) - 0.5) / s) - stats.norm.sf((np.abs(r) + 0.5) / s) for s in sig]
+    for j, s in enumerate(sig):
+        q[j][r == 0] = special.erf(0.5 / (s * math.sqrt(2.0)))
+    mm = np.stack(np.meshgrid(r, r, r, indexing="ij"), -1).reshape(-1, 3)
+    mm = mm[np.any(mm != 0, axis=1)]
+    p = q[0][mm[:, 0] + kmax] * q[1][mm[:, 1] + kmax] * q[2][mm[:, 2] + kmax]
+    p0 = q[0][kmax] * q[1][kmax] * q[2][kmax]
+    w = [np.exp(-(math.pi ** 2) * r.astype(float) ** 2 / (alpha * l * l)) for l in box]
+    S = w[0].sum() * w[1].sum() * w[2].sum() - 1.0
+    return mm.astype(np.int32), S * p / (1.0 - p0)
+
+
+def offline_bias_case(alpha=0.05):
+    """200 +-1 charges in a box of 10 (alpha = 0.05: sigma = 0.50 per axis; alpha = 1: sigma = 2.25):
+    returns positions, charges, box, alpha and the exact expectations of the offline and the exact
+    (Ewald) force and virial."""
+    rng = np.random.default_rng(12)
+    box, N = (10.0, 10.0, 10.0), 200
+    pos = rng.random((N, 3)) * 10.0
+    q = np.where(np.arange(N) % 2 == 0, 1.0, -1.0)
+    kmax = 8 if alpha < 0.5 else 16
+    m, w = _offline_expectation_weights(box, alpha, kmax)
+    F_off, W_off, *_ = oracle.rbe_kspace(pos, q, box, alpha, m, w)
+    F_ew, W_ew, *_ = oracle.ewald_kspace(pos, q, box, alpha, kmax)
+    return pos, q, box, alpha, F_off, F_ew, W_off, W_ew
+
+
+def test_offline_bias_is_exactly_computable_and_real():
+    """The expectation of the offline estimator (weights S P_off(m) over the full cube) differs from
+    the Ewald force by 21 % of its RMS at sigma = 0.5 and still by 1.8 % at sigma = 2.25: rounding a
+    continuous Gaussian adds 1/12 to its variance, so the masses of the two laws differ at relative
+    order 1/(24 sigma^2), not exponentially; the exact sampler's expectation (weights S P(m) =
+    exp(-k^2/4 alpha)) is the Ewald force itself."""
+    pos, q, box, alpha, F_off, F_ew, W_off, W_ew = offline_bias_case()
+    rel = np.sqrt(np.mean((F_off - F_ew) ** 2) / np.mean(F_ew ** 2))
+    assert rel > 0.1, rel
+    *_, F_off2, F_ew2, _, _ = offline_bias_case(alpha=1.0)
+    rel2 = np.sqrt(np.mean((F_off2 - F_ew2) ** 2) / np.mean(F_ew2 ** 2))
+    assert 5e-3 < rel2 < rel / 4, (rel, rel2)
+    r = np.arange(-8, 9)
+    mm = np.stack(np.meshgrid(r, r, r, indexing="ij"), -1).reshape(-1, 3)
+    mm = mm[np.any(mm != 0, axis=1)].astype(np.int32)
+    k2 = ((2 * math.pi * mm / np.array(box)) ** 2).sum(1)
+    F_ex, *_ = oracle.rbe_kspace(pos, q, box, alpha, mm, np.exp(-k2 / (4 * alpha)))
+    assert np.abs(F_ex - F_ew).max() < 1e-12 * np.abs(F_ew).max()
+    # the Monte-Carlo mean of the oracle's own offline draws heads for F_off, not F_ew
+    acc = np.zeros_like(F_off)
+    n = 60
+    for s in range(n):
+        m, S = oracle.sample_k_offline(box, alpha, 500, 3, s)
+        acc += oracle.rbe_kspace(pos, q, box, alpha, m, S / 500)[0]
+    mean = acc / n
+    assert np.sqrt(np.mean((mean - F_off) ** 2)) < 0.5 * np.sqrt(np.mean((mean - F_ew) ** 2))
