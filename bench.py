@@ -344,7 +344,7 @@ def serve(rbe, reqs, states, precision, max_slots, chunk, nsteps, use_graphs=Tru
                                  "max": float(lat.max() * 1e3), "chunks": int(lat.size)}}
 
 
-def npt_single(rbe, N, precision, steps, warmup=3, barostat=1):
+def npt_single(rbe, N, precision, steps, warmup=3, barostat=1, sampler=0, ptilde=0, reuse=1):
     """ms per NPT step of one replica of N particles (the serving system), launched directly
     on one stream, timed with CUDA events after `warmup` steps."""
     import torch
@@ -352,6 +352,9 @@ def npt_single(rbe, N, precision, steps, warmup=3, barostat=1):
     prm = serve_params(rbe, box, barostat)
     stream = torch.cuda.current_stream()
     with rbe.Context(box, SERVE_ALPHA, SERVE_P, 1003, precision, stream=stream.cuda_stream) as ctx:
+        ctx.set_sampler(sampler)
+        ctx.set_pressure_batch(ptilde)
+        ctx.set_sample_reuse(reuse)
         rep = rbe.NptReplica(pos, mom, q, m, box, prm, torch.device("cuda", torch.cuda.current_device()))
         rep.init(ctx, batch=0)
         rep.step(ctx, warmup)
@@ -595,6 +598,10 @@ def main():
     ap.add_argument("--profile-npt", type=int, default=0, help="time only NPT steps of one replica of this N")
     ap.add_argument("--barostat", type=int, default=1, choices=(0, 1, 2, 3),
                     help="with --profile-npt: 0 fixed box, 1 isotropic, 2 anisotropic, 3 semi-isotropic")
+    ap.add_argument("--sampler", choices=["exact", "offline", "mh"], default="exact",
+                    help="with --profile-npt: the frequency sampler (Sec. 4.3 variants)")
+    ap.add_argument("--ptilde", type=int, default=0, help="with --profile-npt: a separate pressure batch")
+    ap.add_argument("--reuse", type=int, default=1, help="with --profile-npt: samples drawn every M steps")
     ap.add_argument("--profile-batched", action="store_true", help="time only the batched k-space evaluation")
     ap.add_argument("--skip-sweep", action="store_true", help="leave out the large-N precision and roofline sweep")
     ap.add_argument("--profile-sweep", action="store_true", help="run only the large-N sweep")
@@ -608,10 +615,13 @@ def main():
         import paper_2110_14362_gb300 as rbe
         torch.cuda.set_device(local)
         prec = rbe.RBE_FP32_PHASE if args.precision == "fp32" else rbe.RBE_FP64
-        ms = npt_single(rbe, args.profile_npt, prec, args.steps, args.warmup, barostat=args.barostat)
+        smp = {"exact": rbe.RBE_SAMPLER_EXACT, "offline": rbe.RBE_SAMPLER_OFFLINE, "mh": rbe.RBE_SAMPLER_MH}
+        ms = npt_single(rbe, args.profile_npt, prec, args.steps, args.warmup, barostat=args.barostat,
+                        sampler=smp[args.sampler], ptilde=args.ptilde, reuse=args.reuse)
         print(json.dumps({"metric": "NPT steps of one replica", "value": 1e3 / ms, "unit": "replica-steps/s",
                           "ms_per_step": ms, "N": args.profile_npt, "precision": args.precision,
-                          "barostat": args.barostat}), flush=True)
+                          "barostat": args.barostat, "sampler": args.sampler, "ptilde": args.ptilde,
+                          "reuse": args.reuse}), flush=True)
         return
     if args.profile_sweep:
         import torch
