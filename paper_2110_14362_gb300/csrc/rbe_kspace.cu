@@ -489,6 +489,13 @@ rbe_status launch_sample_device_box(rbe_ctx ctx, uint64_t step, int P, const uns
     if (st != RBE_OK) return st;
     if ((st = check_chain(ctx, Ptot)) != RBE_OK) return st;
     record_event(ctx, 0);
+    if (ctx->sampler == kSamplerMH) {
+        k_sample_mh<<<(Ptot + kMhSlots - 1) / kMhSlots, kMhWarps * 32, 0, ctx->stream>>>(
+            ctx->seed, step, step_dev, Ptot, P, ctx->d.cum, ctx->d.tab_cap, ctx->d.ks, ctx->chain, ctx->d.m,
+            ctx->d.w, ctx->d.status);
+        record_event(ctx, 1);
+        return check_launch(ctx, "k_sample_mh");
+    }
     const int threads = 128;
     const size_t smem = sizeof(unsigned long long) * 3 * (size_t)ctx->d.tab_cap;
     const int smem_cap = smem <= (size_t)kSampleSmemMax ? ctx->d.tab_cap : 0;
@@ -524,11 +531,19 @@ rbe_status launch_tables_sample_device(rbe_ctx ctx, int P, const double* box_dev
     record_event(ctx, 0);
     const size_t smem = sizeof(unsigned long long) * 3 * (size_t)ctx->d.tab_cap;
     const int smem_cap = smem <= (size_t)kSampleSmemMax ? ctx->d.tab_cap : 0;
+    // the MH chain runs in its own multi-warp launch after the tables (k_sample_mh)
+    const bool mh = ctx->sampler == kSamplerMH;
     k_tables_sample<<<1, kTableThreads, smem_cap ? smem : 0, ctx->stream>>>(
-        box_dev, ctx->alpha, P, Ptot, ctx->d.cum, ctx->d.tab_cap, smem_cap, ctx->d.ks, ctx->seed, step_dev, ctx->d.m,
-        ctx->d.w, ctx->d.status, ctx->sampler, ctx->chain, reuse, ctx->m_all);
+        box_dev, ctx->alpha, P, mh ? 0 : Ptot, ctx->d.cum, ctx->d.tab_cap, smem_cap, ctx->d.ks, ctx->seed, step_dev,
+        ctx->d.m, ctx->d.w, ctx->d.status, ctx->sampler, ctx->chain, reuse, ctx->m_all);
+    if (mh) {
+        if ((st = check_launch(ctx, "k_tables_sample")) != RBE_OK) return st;
+        k_sample_mh<<<(Ptot + kMhSlots - 1) / kMhSlots, kMhWarps * 32, 0, ctx->stream>>>(
+            ctx->seed, 0, step_dev, Ptot, P, ctx->d.cum, ctx->d.tab_cap, ctx->d.ks, ctx->chain, ctx->d.m, ctx->d.w,
+            ctx->d.status);
+    }
     record_event(ctx, 1);
-    return check_launch(ctx, "k_tables_sample");
+    return check_launch(ctx, mh ? "k_sample_mh" : "k_tables_sample");
 }
 
 rbe_status launch_weights_from_list(rbe_ctx ctx, int K, const int32_t* m, const double* w)

@@ -50,26 +50,36 @@ __device__ __forceinline__ double smp_exp0(double x)
     return x < -700.0 ? 0.0 : table_exp(x);
 }
 
-// erf on [0, 2]: sum_n (-1)^n x^(2n+1) / (n! (2n+1)) times 2/sqrt(pi), 60 terms.
+// 1/n and 1/(2n + 1), n = 0..60, each the correctly rounded quotient (constant-folded IEEE
+// division), so that multiplying by them gives the same bits as a host that divides 1.0 by n.
+__constant__ double kSmpInvN[61] = {0.0, 1.0 / 1.0, 1.0 / 2.0, 1.0 / 3.0, 1.0 / 4.0, 1.0 / 5.0, 1.0 / 6.0, 1.0 / 7.0, 1.0 / 8.0, 1.0 / 9.0, 1.0 / 10.0, 1.0 / 11.0, 1.0 / 12.0, 1.0 / 13.0, 1.0 / 14.0, 1.0 / 15.0, 1.0 / 16.0, 1.0 / 17.0, 1.0 / 18.0, 1.0 / 19.0, 1.0 / 20.0, 1.0 / 21.0, 1.0 / 22.0, 1.0 / 23.0, 1.0 / 24.0, 1.0 / 25.0, 1.0 / 26.0, 1.0 / 27.0, 1.0 / 28.0, 1.0 / 29.0, 1.0 / 30.0, 1.0 / 31.0, 1.0 / 32.0, 1.0 / 33.0, 1.0 / 34.0, 1.0 / 35.0, 1.0 / 36.0, 1.0 / 37.0, 1.0 / 38.0, 1.0 / 39.0, 1.0 / 40.0, 1.0 / 41.0, 1.0 / 42.0, 1.0 / 43.0, 1.0 / 44.0, 1.0 / 45.0, 1.0 / 46.0, 1.0 / 47.0, 1.0 / 48.0, 1.0 / 49.0, 1.0 / 50.0, 1.0 / 51.0, 1.0 / 52.0, 1.0 / 53.0, 1.0 / 54.0, 1.0 / 55.0, 1.0 / 56.0, 1.0 / 57.0, 1.0 / 58.0, 1.0 / 59.0, 1.0 / 60.0};
+__constant__ double kSmpInvOdd[61] = {1.0 / 1.0, 1.0 / 3.0, 1.0 / 5.0, 1.0 / 7.0, 1.0 / 9.0, 1.0 / 11.0, 1.0 / 13.0, 1.0 / 15.0, 1.0 / 17.0, 1.0 / 19.0, 1.0 / 21.0, 1.0 / 23.0, 1.0 / 25.0, 1.0 / 27.0, 1.0 / 29.0, 1.0 / 31.0, 1.0 / 33.0, 1.0 / 35.0, 1.0 / 37.0, 1.0 / 39.0, 1.0 / 41.0, 1.0 / 43.0, 1.0 / 45.0, 1.0 / 47.0, 1.0 / 49.0, 1.0 / 51.0, 1.0 / 53.0, 1.0 / 55.0, 1.0 / 57.0, 1.0 / 59.0, 1.0 / 61.0, 1.0 / 63.0, 1.0 / 65.0, 1.0 / 67.0, 1.0 / 69.0, 1.0 / 71.0, 1.0 / 73.0, 1.0 / 75.0, 1.0 / 77.0, 1.0 / 79.0, 1.0 / 81.0, 1.0 / 83.0, 1.0 / 85.0, 1.0 / 87.0, 1.0 / 89.0, 1.0 / 91.0, 1.0 / 93.0, 1.0 / 95.0, 1.0 / 97.0, 1.0 / 99.0, 1.0 / 101.0, 1.0 / 103.0, 1.0 / 105.0, 1.0 / 107.0, 1.0 / 109.0, 1.0 / 111.0, 1.0 / 113.0, 1.0 / 115.0, 1.0 / 117.0, 1.0 / 119.0, 1.0 / 121.0};
+
+// erf on [0, 2]: sum_n (-1)^n x^(2n+1) / (n! (2n+1)) times 2/sqrt(pi); term n is
+// t_n = t_(n-1) (-x^2) (1/n), added as t_n (1/(2n+1)); the sum stops after the first term below
+// 2^-60 of the running sum (at most 60 terms).
 __device__ __forceinline__ double smp_erf_series(double x)
 {
     const double x2 = __dmul_rn(x, x);
     double t = x, sum = x;
     for (int n = 1; n <= 60; ++n) {
-        t = __ddiv_rn(__dmul_rn(t, -x2), (double)n);
-        sum = __dadd_rn(sum, __ddiv_rn(t, (double)(2 * n + 1)));
+        t = __dmul_rn(__dmul_rn(t, -x2), kSmpInvN[n]);
+        const double term = __dmul_rn(t, kSmpInvOdd[n]);
+        sum = __dadd_rn(sum, term);
+        if (fabs(term) < __dmul_rn(0x1.0p-60, fabs(sum))) break;
     }
     return __dmul_rn(sum, 0x1.20dd750429b6dp+0);
 }
 
 // erfc for x >= 0: 1 - erf on [0, 2], exp(-x^2)/(sqrt(pi) K) beyond with the continued
-// fraction K = x + (1/2)/(x + 1/(x + (3/2)/(x + ...))) from depth 80, 0 from 26 on.
+// fraction K = x + (1/2)/(x + 1/(x + (3/2)/(x + ...))) from depth ceil(10 + 200/x^2), 0 from 26 on.
 __device__ __forceinline__ double smp_erfc(double x)
 {
     if (x <= 2.0) return __dsub_rn(1.0, smp_erf_series(x));
     if (x >= 26.0) return 0.0;
     double f = x;
-    for (int n = 80; n >= 1; --n) f = __dadd_rn(x, __ddiv_rn(__dmul_rn(0.5, (double)n), f));
+    const int depth = (int)ceil(__dadd_rn(10.0, __ddiv_rn(200.0, __dmul_rn(x, x))));
+    for (int n = depth; n >= 1; --n) f = __dadd_rn(x, __ddiv_rn(__dmul_rn(0.5, (double)n), f));
     return __ddiv_rn(smp_exp0(-__dmul_rn(x, x)), __dmul_rn(0x1.c5bf891b4ef6bp+0, f));
 }
 
@@ -213,6 +223,88 @@ __device__ __forceinline__ void sample_variant_body(int lbase, uint64_t seed, ui
     if (!ok) {
         atomicOr(status, kStatusSample);
         m = make_int4(1, 0, 0, 0);  // keeps the evaluation finite; the call reports RBE_ESAMPLE
+    }
+    m_out[l] = m;
+    if (w_out) w_out[l] = l < Pf ? ks->wP : ks->S / (double)(P - Pf);
+}
+
+}  // namespace rbe
+
+namespace rbe {
+
+// The MH step of 32 slots per block (6 warps): warp 0 forms the proposals (and the exact draw of
+// a slot whose chain is at m = 0); warps 0..5 each form one factor of the acceptance for all 32
+// slots, F = exp(-c_a m'_a^2) mass(m_a) (warps 0..2, axis a, numerator) or exp(-c_a m_a^2)
+// mass(m'_a) (warps 3..5, denominator), so that no warp runs more than one mass's FP64 chain
+// (each FP64 warp instruction occupies GB300's narrow pipe for the whole warp, however few lanes
+// are active: the six chains must sit on different warps); warp 0 multiplies the factors in
+// axis order, exactly as one thread would, and accepts.  Same draws as sample_variant_body.
+constexpr int kMhSlots = 32, kMhWarps = 6;
+
+__global__ void __launch_bounds__(kMhWarps * 32)
+k_sample_mh(uint64_t seed, uint64_t step_arg, const unsigned long long* __restrict__ step_dev, int P, int Pf,
+            const unsigned long long* __restrict__ cum, int cap, const KState* __restrict__ ks,
+            int4* __restrict__ chain, int4* __restrict__ m_out, double* __restrict__ w_out,
+            unsigned* __restrict__ status)
+{
+    __shared__ int4 s_cur[kMhSlots], s_mp[kMhSlots];
+    __shared__ int s_state[kMhSlots];  // 0 propose, 1 exact start, 2 failed
+    __shared__ double s_f[kMhWarps][kMhSlots];
+    pdl_wait();
+    pdl_trigger();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int l = blockIdx.x * kMhSlots + lane;
+    const bool live = l < P;
+    const uint64_t step = step_dev ? *step_dev : step_arg;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const uint32_t c2 = (uint32_t)step, c3 = (uint32_t)((step >> 32) & 0xFFFFFFu);
+    const double alpha = ks->alpha;
+    if (warp == 0 && live) {
+        double sig[3];
+        const double ra2 = __dsqrt_rn(__dmul_rn(alpha, 0.5));
+        for (int t = 0; t < 3; ++t) sig[t] = __ddiv_rn(__dmul_rn(ra2, ks->L[t]), kPi);
+        int4 cur = chain[l], mp = make_int4(0, 0, 0, 0);
+        int state = 0;
+        if (cur.x == 0 && cur.y == 0 && cur.z == 0) {
+            state = smp_exact(cum, cap, ks, k0, k1, c2, c3, l, cur) ? 1 : 2;
+        } else if (!smp_offline(sig, k0, k1, c2, c3, l, mp)) {
+            state = 2;
+        }
+        s_cur[lane] = cur;
+        s_mp[lane] = mp;
+        s_state[lane] = state;
+    }
+    __syncthreads();
+    if (live && s_state[lane] == 0) {
+        const int a = warp % 3;
+        const bool numerator = warp < 3;
+        const int4 cur = s_cur[lane], mp = s_mp[lane];
+        const int ca[3] = {cur.x, cur.y, cur.z}, pa[3] = {mp.x, mp.y, mp.z};
+        const double c = axis_c(alpha, ks->L[a]);
+        const double g = __ddiv_rn(kPi, __dmul_rn(__dsqrt_rn(alpha), ks->L[a]));
+        const double e = (double)(numerator ? pa[a] : ca[a]);
+        s_f[warp][lane] = __dmul_rn(smp_exp0(-__dmul_rn(c, __dmul_rn(e, e))), smp_mass(numerator ? ca[a] : pa[a], g));
+    }
+    __syncthreads();
+    if (warp != 0 || !live) return;
+    int4 cur = s_cur[lane];
+    const int state = s_state[lane];
+    if (state == 0) {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)l, 0u, c2, (4u << 24) | c3), k0, k1);
+        const double u = smp_u53(w.x, w.y);
+        double num = 1.0, den = 1.0;
+        for (int t = 0; t < 3; ++t) {
+            num = __dmul_rn(num, s_f[t][lane]);
+            den = __dmul_rn(den, s_f[3 + t][lane]);
+        }
+        if (__dmul_rn(u, den) < num) cur = s_mp[lane];
+    }
+    int4 m = cur;
+    if (state == 2) {
+        atomicOr(status, kStatusSample);
+        m = make_int4(1, 0, 0, 0);  // keeps the evaluation finite; the call reports RBE_ESAMPLE
+    } else {
+        chain[l] = cur;
     }
     m_out[l] = m;
     if (w_out) w_out[l] = l < Pf ? ks->wP : ks->S / (double)(P - Pf);
