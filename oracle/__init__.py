@@ -21,6 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rbe_oracle.c")
 _SRC_NPT = os.path.join(_HERE, "npt_oracle.c")
 _SRC_SMP = os.path.join(_HERE, "sampler_oracle.c")
+_SRC_GEN = os.path.join(_HERE, "general_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -34,7 +35,7 @@ _c_uint32_p = ctypes.POINTER(ctypes.c_uint32)
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc into ``oracle/_build/liboracle.so`` and return its path."""
     os.makedirs(_BUILD, exist_ok=True)
-    srcs = [s for s in (_SRC, _SRC_NPT, _SRC_SMP) if os.path.exists(s)]
+    srcs = [s for s in (_SRC, _SRC_NPT, _SRC_SMP, _SRC_GEN) if os.path.exists(s)]
     newest = max(os.path.getmtime(s) for s in srcs)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".{os.getpid()}.tmp"
@@ -90,6 +91,8 @@ def _load():
                 _bind_npt(lib)
             if hasattr(lib, "orc_sample_k_mh"):
                 _bind_samplers(lib)
+            if hasattr(lib, "orc_gen_kspace"):
+                _bind_general(lib)
             _lib = lib
     return _lib
 
@@ -152,6 +155,28 @@ def _bind_samplers(lib):
         f.argtypes = [_c_double_p, ctypes.c_double, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, _c_int32_p,
                       _c_double_p]
         f.restype = ctypes.c_int
+
+
+def _bind_general(lib):
+    lib.orc_gen_inverse.argtypes = [_c_double_p, _c_double_p]
+    lib.orc_gen_inverse.restype = ctypes.c_double
+    lib.orc_gen_metric.argtypes = [_c_double_p, _c_double_p]
+    lib.orc_gen_metric.restype = None
+    lib.orc_gen_kspace.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p, ctypes.c_double,
+                                   ctypes.c_int32, _c_int32_p, _c_double_p, _c_double_p, _c_double_p, _c_double_p]
+    lib.orc_gen_kspace.restype = ctypes.c_int
+    lib.orc_gen_ewald_kspace.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p, ctypes.c_double,
+                                         ctypes.c_int32, _c_double_p, _c_double_p, _c_double_p]
+    lib.orc_gen_ewald_kspace.restype = ctypes.c_int
+    lib.orc_gen_ewald_real.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p, ctypes.c_double,
+                                       ctypes.c_double, _c_double_p, _c_double_p, _c_double_p]
+    lib.orc_gen_ewald_real.restype = ctypes.c_int
+    for name in ("orc_gen_S", "orc_gen_S_direct"):
+        getattr(lib, name).argtypes = [_c_double_p, ctypes.c_double]
+        getattr(lib, name).restype = ctypes.c_double
+    lib.orc_gen_sample_k_mh.argtypes = [_c_double_p, ctypes.c_double, ctypes.c_int32, ctypes.c_uint64,
+                                        ctypes.c_uint64, _c_int32_p, _c_double_p]
+    lib.orc_gen_sample_k_mh.restype = ctypes.c_int
 
 
 def _dp(a):
@@ -495,3 +520,61 @@ def ewald_total(pos, q, box, alpha: float, rc: float, kmax: int):
     Fk, Wk, Ek, Es = ewald_kspace(pos, q, box, alpha, kmax)
     Fr, Wr, Er = ewald_real(pos, q, box, alpha, rc)
     return Fk + Fr, Wk + Wr, Ek + Es + Er
+
+
+# ---------------------------------------------------------------------------------
+# General (triclinic) cell (general_oracle.c): h is 3x3 with the cell vectors as columns.
+def gen_kspace(pos, q, h, alpha: float, m, weights):
+    """k-space sums over the listed m with the given weights: (F[N,3], W[3,3], E_k, E_self)."""
+    lib = _load()
+    pos, q = _f64(pos), _f64(q)
+    N = q.shape[0]
+    m = np.ascontiguousarray(m, dtype=np.int32).reshape(-1, 3)
+    K = m.shape[0]
+    w = np.asarray(weights, dtype=np.float64)
+    w = np.full(K, float(w)) if w.ndim == 0 else np.ascontiguousarray(w)
+    F, W, E = np.zeros((N, 3)), np.zeros((3, 3)), np.zeros(2)
+    _check(lib.orc_gen_kspace(N, _dp(pos), _dp(q), _dp(_f64(h, (3, 3))), alpha, K, _ip(m), _dp(w), _dp(F), _dp(W),
+                              _dp(E)), "gen_kspace")
+    return F, W, E[0], E[1]
+
+
+def gen_ewald_kspace(pos, q, h, alpha: float, kmax: int):
+    lib = _load()
+    pos, q = _f64(pos), _f64(q)
+    N = q.shape[0]
+    F, W, E = np.zeros((N, 3)), np.zeros((3, 3)), np.zeros(2)
+    _check(lib.orc_gen_ewald_kspace(N, _dp(pos), _dp(q), _dp(_f64(h, (3, 3))), alpha, kmax, _dp(F), _dp(W), _dp(E)),
+           "gen_ewald_kspace")
+    return F, W, E[0], E[1]
+
+
+def gen_ewald_real(pos, q, h, alpha: float, rc: float):
+    lib = _load()
+    pos, q = _f64(pos), _f64(q)
+    N = q.shape[0]
+    F, W, E = np.zeros((N, 3)), np.zeros((3, 3)), ctypes.c_double(0.0)
+    _check(lib.orc_gen_ewald_real(N, _dp(pos), _dp(q), _dp(_f64(h, (3, 3))), alpha, rc, _dp(F), _dp(W),
+                                  ctypes.byref(E)), "gen_ewald_real")
+    return F, W, E.value
+
+
+def gen_S(h, alpha: float, direct: bool = False) -> float:
+    lib = _load()
+    f = lib.orc_gen_S_direct if direct else lib.orc_gen_S
+    return f(_dp(_f64(h, (3, 3))), alpha)
+
+
+def gen_metric(h):
+    G = np.zeros((3, 3))
+    _load().orc_gen_metric(_dp(_f64(h, (3, 3))), _dp(G))
+    return G
+
+
+def gen_sample_k_mh(h, alpha: float, P: int, seed: int, step: int, state):
+    """General-cell MH sampler: state[P,3] int32 updated in place; returns (state, S)."""
+    assert state.dtype == np.int32 and state.shape == (P, 3) and state.flags.c_contiguous
+    S = ctypes.c_double(0.0)
+    _check(_load().orc_gen_sample_k_mh(_dp(_f64(h, (3, 3))), alpha, P, seed, step, _ip(state), ctypes.byref(S)),
+           "gen_sample_k_mh")
+    return state, S.value
