@@ -128,6 +128,29 @@ rbe_status rbe_set_pressure_batch(rbe_ctx ctx, int32_t Ptilde);
  * Metropolis--Hastings sampler (the two exclude each other). */
 rbe_status rbe_set_sample_reuse(rbe_ctx ctx, int32_t M);
 
+/* RBE k-space forces, virial and energy in a general (triclinic) cell (App. C, the fully
+ * flexible cell).  h: host 3x3, row-major, the cell vectors as COLUMNS (h[3 i + j] = component i
+ * of vector j), det h > 0; positions any real (r = h s, s scaled coordinates); wave vectors
+ * k = 2 pi h^{-T} m, the phase k.r = 2 pi m.s.  Frequencies: the law exp(-pi^2 m^T G m / alpha)
+ * (G = h^{-1} h^{-T}) does not factorise, so each slot runs a Metropolis--Hastings chain (the
+ * paper's suggestion): an independence proposal from the exact product of per-axis discrete
+ * Gaussians with lengths l_j = sqrt(lambda) |a_j| (|a_j| the cell vector lengths, lambda =
+ * max_j (1 + sum_{k != j} |cos theta_jk|), so the ratio of target to proposal is bounded and a
+ * rectangular cell proposes the target itself), Philox stream 0 as the exact sampler with these
+ * lengths; acceptance with O(m) = (pi^2/alpha) m^T G m - sum_j (pi^2/(alpha l_j^2)) m_j^2: m'
+ * when O(m') <= O(m), else when u < exp(O(m) - O(m')), u from stream 5 (l, 0, step_lo,
+ * (5 << 24) | step_hi24).  The chain state is the context's (P slots); a slot at m = 0 (first
+ * call, or after rbe_set_sampler) starts from the proposal; m matches the oracle bit for bit.
+ * Weights S/P with S = sum_{m != 0} exp(-pi^2 m^T G m / alpha) from the Poisson dual sum
+ * (alpha/pi)^{3/2} V sum_n exp(-alpha |h n|^2) - 1.  Outputs as rbe_kspace_forces_virial: forces
+ * (device N*3, overwritten), virial (device 9, the full tensor of App. C Eq.
+ * (pressuretensorflexible), or NULL), energy (device 2: E_k, E_self, or NULL).  Runs the context's
+ * precision (the FP32-phase passes on the scaled coordinates).  Asynchronous; RBE_EINVAL for a
+ * singular, non-finite or oversized cell or bad arguments; device errors via rbe_sync. */
+rbe_status rbe_kspace_forces_virial_general(rbe_ctx ctx, int64_t N, const double* positions, const double* charges,
+                                            const double h[9], uint64_t step, double* forces_out,
+                                            double* virial_out, double* energy_out);
+
 /* Replace the box lengths (same validity rule as rbe_create).  The per-axis sampling
  * tables are rebuilt on the device at the next evaluation. */
 rbe_status rbe_set_box(rbe_ctx ctx, const double box[3]);

@@ -85,6 +85,8 @@ SIGNATURES = [
     ("rbe_set_sampler", ctypes.c_int, [_vp, ctypes.c_int32]),
     ("rbe_set_pressure_batch", ctypes.c_int, [_vp, ctypes.c_int32]),
     ("rbe_set_sample_reuse", ctypes.c_int, [_vp, ctypes.c_int32]),
+    ("rbe_kspace_forces_virial_general", ctypes.c_int, [_vp, ctypes.c_int64, _vp, _vp, _dp, ctypes.c_uint64, _vp, _vp,
+                                                        _vp]),
     ("rbe_set_seed", ctypes.c_int, [_vp, ctypes.c_uint64]),
     ("rbe_set_box", ctypes.c_int, [_vp, _dp]),
     ("rbe_sample_k", ctypes.c_int, [_vp, ctypes.c_uint64, _ip, _dp]),
@@ -545,6 +547,17 @@ class Context:
     def set_pressure_batch(self, Ptilde: int):
         """A separate batch of Ptilde frequencies for the virial and energy (0: the force batch)."""
         rbe_set_pressure_batch(self.h, Ptilde)
+
+    def forces_virial_general(self, positions, charges, h, step: int, forces_out, virial_out=None, energy_out=None):
+        """k-space forces/virial/energy in the general cell h (3x3, cell vectors as columns); torch
+        CUDA float64 tensors for positions (N, 3), charges (N,), forces_out (N, 3), virial_out (9,),
+        energy_out (2,)."""
+        hh = np.ascontiguousarray(np.asarray(h, dtype=np.float64).reshape(3, 3))
+        N = int(charges.shape[0])
+        ptr = lambda t: None if t is None else t.data_ptr()
+        _check(load().rbe_kspace_forces_virial_general(self.h, N, ptr(positions), ptr(charges),
+                                                       hh.ctypes.data_as(_dp), int(step), ptr(forces_out),
+                                                       ptr(virial_out), ptr(energy_out)), self.h)
 
     def set_sample_reuse(self, M: int):
         """NPT: draw the frequencies of M steps at once, every M steps (1: every step)."""

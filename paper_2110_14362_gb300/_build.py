@@ -20,8 +20,10 @@ OUT_DIR = os.path.join(PKG, "_lib")
 OBJ_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "librbe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# host code: no fused multiply-add contraction (-ffp-contract=off), so that the host-side cell
+# quantities that decide sampled integers round the same on x86 and Arm hosts
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-              "-I" + os.path.join(ROOT, "include")]
+              "-Xcompiler", "-ffp-contract=off", "-I" + os.path.join(ROOT, "include")]
 
 
 def nvcc() -> str:

@@ -202,6 +202,8 @@ rbe_status rbe_destroy(rbe_ctx ctx)
     free_buffers(ctx->d);
     if (ctx->chain) cudaFree(ctx->chain);
     if (ctx->m_all) cudaFree(ctx->m_all);
+    if (ctx->gchain) cudaFree(ctx->gchain);
+    if (ctx->gpos) cudaFree(ctx->gpos);
     delete ctx;
     return RBE_OK;
 }
@@ -259,6 +261,10 @@ rbe_status rbe_set_sampler(rbe_ctx ctx, int32_t sampler)
         // every slot starts again from the exact draw of its next sampling step
         if ((e = cudaMemsetAsync(ctx->chain, 0, sizeof(int4) * (size_t)ctx->chain_cap, ctx->stream)) != cudaSuccess)
             return cuda_fail(ctx, e, "cudaMemsetAsync(MH chain)");
+    }
+    if (ctx->gchain) {  // the general cell's chains restart too
+        cudaError_t e = cudaMemsetAsync(ctx->gchain, 0, sizeof(int4) * (size_t)ctx->gchain_cap, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync(general chain)");
     }
     ctx->sampler = sampler;
     return RBE_OK;

@@ -122,6 +122,10 @@ struct rbe_ctx_s {
     int32_t reuse = 1;               // NPT: samples drawn every `reuse` steps, kept on the device
     int4* m_all = nullptr;           // reuse > 1: the kept batches, reuse x (P + Ptilde)
     int64_t m_all_cap = 0;
+    int4* gchain = nullptr;          // general cell: the MH state per slot (m = 0: start from the proposal)
+    int32_t gchain_cap = 0;
+    double* gpos = nullptr;          // general cell: scaled coordinates s = h^{-1} r, N x 3
+    int64_t gpos_cap = 0;
     bool tables_dirty = true;
     int32_t last_K = 0;
     rbe::NptBuffers npt;
@@ -173,6 +177,7 @@ rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const doub
                            bool uniform_weight, double* F, double* W, double* E);
 rbe_status launch_rbe(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int P, double* F, double* W,
                       double* E);
+rbe_status launch_tables_box(rbe_ctx ctx, const double box[3]);
 // Pieces of the pipelined host-buffer evaluation (copy stream events: 1 + 2 kMaxPieces).
 constexpr int kMaxPieces = 8;
 rbe_status launch_evaluate_staged(rbe_ctx ctx, int64_t N, const double* h_pos, const double* h_q, double* h_F,

@@ -426,6 +426,16 @@ rbe_status launch_tables(rbe_ctx ctx, const double* box_dev)
     return check_launch(ctx, "k_tables");
 }
 
+// Tables and box state of an explicit box (the general cell's proposal lengths and its unit cube);
+// the context's own box tables are rebuilt at the next rectangular evaluation.
+rbe_status launch_tables_box(rbe_ctx ctx, const double box[3])
+{
+    k_tables<<<1, kTableThreads, 0, ctx->stream>>>(box[0], box[1], box[2], nullptr, ctx->alpha, ctx->P, ctx->d.cum,
+                                                   ctx->d.tab_cap, ctx->d.ks, ctx->d.status);
+    ctx->tables_dirty = true;
+    return check_launch(ctx, "k_tables");
+}
+
 rbe_status ensure_tables(rbe_ctx ctx)
 {
     if (!ctx->tables_dirty) return RBE_OK;

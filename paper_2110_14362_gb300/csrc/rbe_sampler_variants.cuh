@@ -52,8 +52,8 @@ __device__ __forceinline__ double smp_exp0(double x)
 
 // 1/n and 1/(2n + 1), n = 0..60, each the correctly rounded quotient (constant-folded IEEE
 // division), so that multiplying by them gives the same bits as a host that divides 1.0 by n.
-__constant__ double kSmpInvN[61] = {0.0, 1.0 / 1.0, 1.0 / 2.0, 1.0 / 3.0, 1.0 / 4.0, 1.0 / 5.0, 1.0 / 6.0, 1.0 / 7.0, 1.0 / 8.0, 1.0 / 9.0, 1.0 / 10.0, 1.0 / 11.0, 1.0 / 12.0, 1.0 / 13.0, 1.0 / 14.0, 1.0 / 15.0, 1.0 / 16.0, 1.0 / 17.0, 1.0 / 18.0, 1.0 / 19.0, 1.0 / 20.0, 1.0 / 21.0, 1.0 / 22.0, 1.0 / 23.0, 1.0 / 24.0, 1.0 / 25.0, 1.0 / 26.0, 1.0 / 27.0, 1.0 / 28.0, 1.0 / 29.0, 1.0 / 30.0, 1.0 / 31.0, 1.0 / 32.0, 1.0 / 33.0, 1.0 / 34.0, 1.0 / 35.0, 1.0 / 36.0, 1.0 / 37.0, 1.0 / 38.0, 1.0 / 39.0, 1.0 / 40.0, 1.0 / 41.0, 1.0 / 42.0, 1.0 / 43.0, 1.0 / 44.0, 1.0 / 45.0, 1.0 / 46.0, 1.0 / 47.0, 1.0 / 48.0, 1.0 / 49.0, 1.0 / 50.0, 1.0 / 51.0, 1.0 / 52.0, 1.0 / 53.0, 1.0 / 54.0, 1.0 / 55.0, 1.0 / 56.0, 1.0 / 57.0, 1.0 / 58.0, 1.0 / 59.0, 1.0 / 60.0};
-__constant__ double kSmpInvOdd[61] = {1.0 / 1.0, 1.0 / 3.0, 1.0 / 5.0, 1.0 / 7.0, 1.0 / 9.0, 1.0 / 11.0, 1.0 / 13.0, 1.0 / 15.0, 1.0 / 17.0, 1.0 / 19.0, 1.0 / 21.0, 1.0 / 23.0, 1.0 / 25.0, 1.0 / 27.0, 1.0 / 29.0, 1.0 / 31.0, 1.0 / 33.0, 1.0 / 35.0, 1.0 / 37.0, 1.0 / 39.0, 1.0 / 41.0, 1.0 / 43.0, 1.0 / 45.0, 1.0 / 47.0, 1.0 / 49.0, 1.0 / 51.0, 1.0 / 53.0, 1.0 / 55.0, 1.0 / 57.0, 1.0 / 59.0, 1.0 / 61.0, 1.0 / 63.0, 1.0 / 65.0, 1.0 / 67.0, 1.0 / 69.0, 1.0 / 71.0, 1.0 / 73.0, 1.0 / 75.0, 1.0 / 77.0, 1.0 / 79.0, 1.0 / 81.0, 1.0 / 83.0, 1.0 / 85.0, 1.0 / 87.0, 1.0 / 89.0, 1.0 / 91.0, 1.0 / 93.0, 1.0 / 95.0, 1.0 / 97.0, 1.0 / 99.0, 1.0 / 101.0, 1.0 / 103.0, 1.0 / 105.0, 1.0 / 107.0, 1.0 / 109.0, 1.0 / 111.0, 1.0 / 113.0, 1.0 / 115.0, 1.0 / 117.0, 1.0 / 119.0, 1.0 / 121.0};
+static __constant__ double kSmpInvN[61] = {0.0, 1.0 / 1.0, 1.0 / 2.0, 1.0 / 3.0, 1.0 / 4.0, 1.0 / 5.0, 1.0 / 6.0, 1.0 / 7.0, 1.0 / 8.0, 1.0 / 9.0, 1.0 / 10.0, 1.0 / 11.0, 1.0 / 12.0, 1.0 / 13.0, 1.0 / 14.0, 1.0 / 15.0, 1.0 / 16.0, 1.0 / 17.0, 1.0 / 18.0, 1.0 / 19.0, 1.0 / 20.0, 1.0 / 21.0, 1.0 / 22.0, 1.0 / 23.0, 1.0 / 24.0, 1.0 / 25.0, 1.0 / 26.0, 1.0 / 27.0, 1.0 / 28.0, 1.0 / 29.0, 1.0 / 30.0, 1.0 / 31.0, 1.0 / 32.0, 1.0 / 33.0, 1.0 / 34.0, 1.0 / 35.0, 1.0 / 36.0, 1.0 / 37.0, 1.0 / 38.0, 1.0 / 39.0, 1.0 / 40.0, 1.0 / 41.0, 1.0 / 42.0, 1.0 / 43.0, 1.0 / 44.0, 1.0 / 45.0, 1.0 / 46.0, 1.0 / 47.0, 1.0 / 48.0, 1.0 / 49.0, 1.0 / 50.0, 1.0 / 51.0, 1.0 / 52.0, 1.0 / 53.0, 1.0 / 54.0, 1.0 / 55.0, 1.0 / 56.0, 1.0 / 57.0, 1.0 / 58.0, 1.0 / 59.0, 1.0 / 60.0};
+static __constant__ double kSmpInvOdd[61] = {1.0 / 1.0, 1.0 / 3.0, 1.0 / 5.0, 1.0 / 7.0, 1.0 / 9.0, 1.0 / 11.0, 1.0 / 13.0, 1.0 / 15.0, 1.0 / 17.0, 1.0 / 19.0, 1.0 / 21.0, 1.0 / 23.0, 1.0 / 25.0, 1.0 / 27.0, 1.0 / 29.0, 1.0 / 31.0, 1.0 / 33.0, 1.0 / 35.0, 1.0 / 37.0, 1.0 / 39.0, 1.0 / 41.0, 1.0 / 43.0, 1.0 / 45.0, 1.0 / 47.0, 1.0 / 49.0, 1.0 / 51.0, 1.0 / 53.0, 1.0 / 55.0, 1.0 / 57.0, 1.0 / 59.0, 1.0 / 61.0, 1.0 / 63.0, 1.0 / 65.0, 1.0 / 67.0, 1.0 / 69.0, 1.0 / 71.0, 1.0 / 73.0, 1.0 / 75.0, 1.0 / 77.0, 1.0 / 79.0, 1.0 / 81.0, 1.0 / 83.0, 1.0 / 85.0, 1.0 / 87.0, 1.0 / 89.0, 1.0 / 91.0, 1.0 / 93.0, 1.0 / 95.0, 1.0 / 97.0, 1.0 / 99.0, 1.0 / 101.0, 1.0 / 103.0, 1.0 / 105.0, 1.0 / 107.0, 1.0 / 109.0, 1.0 / 111.0, 1.0 / 113.0, 1.0 / 115.0, 1.0 / 117.0, 1.0 / 119.0, 1.0 / 121.0};
 
 // erf on [0, 2]: sum_n (-1)^n x^(2n+1) / (n! (2n+1)) times 2/sqrt(pi); term n is
 // t_n = t_(n-1) (-x^2) (1/n), added as t_n (1/(2n+1)); the sum stops after the first term below
@@ -241,7 +241,7 @@ namespace rbe {
 // axis order, exactly as one thread would, and accepts.  Same draws as sample_variant_body.
 constexpr int kMhSlots = 32, kMhWarps = 6;
 
-__global__ void __launch_bounds__(kMhWarps * 32)
+static __global__ void __launch_bounds__(kMhWarps * 32)
 k_sample_mh(uint64_t seed, uint64_t step_arg, const unsigned long long* __restrict__ step_dev, int P, int Pf,
             const unsigned long long* __restrict__ cum, int cap, const KState* __restrict__ ks,
             int4* __restrict__ chain, int4* __restrict__ m_out, double* __restrict__ w_out,
