@@ -379,6 +379,48 @@ def run_npt_single(rbe, sizes, steps):
     return out
 
 
+def run_general(rbe, steps=20, warmup=3):
+    """The general-cell (triclinic) k-space path on the slab workload with the box sheared
+    (tilts 10, -8 and 12 A), FP32-phase and FP64, against the rectangular path on the unsheared
+    slab: N P pair evaluations per second, CUDA events per evaluation, L2 flushed between them."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    s = inputs.slab()
+    box = np.asarray(s.box, dtype=np.float64)
+    h = np.array([[box[0], 10.0, -8.0], [0.0, box[1], 12.0], [0.0, 0.0, box[2]]])
+    frac = np.asarray(s.pos) / box  # the slab's scaled coordinates, placed in the sheared cell
+    pos_g = torch.as_tensor(frac @ h.T).to(dev)
+    pos_r = torch.as_tensor(np.asarray(s.pos)).to(dev)
+    q = torch.as_tensor(np.asarray(s.q)).to(dev)
+    N = q.shape[0]
+    F = torch.empty((N, 3), dtype=torch.float64, device=dev)
+    W = torch.empty(9, dtype=torch.float64, device=dev)
+    E = torch.empty(2, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {"N": int(N), "P": int(s.P), "tilts_A": [10.0, -8.0, 12.0]}
+    for name, prec in (("fp32_phase", rbe.RBE_FP32_PHASE), ("fp64", rbe.RBE_FP64)):
+        n = steps if prec == rbe.RBE_FP32_PHASE else max(2, steps // 4)
+        with rbe.Context(box, s.alpha, s.P, 12345, prec, stream=stream.cuda_stream) as ctx:
+            for label, fn in (("general", lambda k: ctx.forces_virial_general(pos_g, q, h, k, F, W, E)),
+                              ("rectangular", lambda k: ctx.forces_virial(pos_r, q, k, F, W, E))):
+                for k in range(warmup):
+                    fn(k)
+                ms = []
+                for k in range(n):
+                    flush.fill_(float(k))
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    fn(warmup + k)
+                    e1.record(stream)
+                    ctx.sync()
+                    ms.append(e0.elapsed_time(e1))
+                t = float(np.median(ms))
+                out[f"{name}_{label}_ms"] = t
+                out[f"{name}_{label}_pair_evals_per_s"] = N * s.P / (t * 1e-3)
+    return out
+
+
 def run_batched(rbe, n_items=64, P=100, iters=20):
     """Batched k-space (one evaluation of n_items uneven systems in five launches, autotuned
     tiles) against a loop of single-system evaluations of the same systems on one stream:
@@ -603,6 +645,8 @@ def main():
     ap.add_argument("--ptilde", type=int, default=0, help="with --profile-npt: a separate pressure batch")
     ap.add_argument("--reuse", type=int, default=1, help="with --profile-npt: samples drawn every M steps")
     ap.add_argument("--profile-batched", action="store_true", help="time only the batched k-space evaluation")
+    ap.add_argument("--profile-general", action="store_true",
+                    help="time only the general-cell (triclinic) k-space path on the sheared slab")
     ap.add_argument("--skip-sweep", action="store_true", help="leave out the large-N precision and roofline sweep")
     ap.add_argument("--profile-sweep", action="store_true", help="run only the large-N sweep")
     args = ap.parse_args()
@@ -628,6 +672,13 @@ def main():
         import paper_2110_14362_gb300 as rbe
         torch.cuda.set_device(local)
         print(json.dumps({"metric": "large-N sweep", "sweep": run_sweep(rbe, steps=args.steps)}), flush=True)
+        return
+    if args.profile_general:
+        import torch
+        import paper_2110_14362_gb300 as rbe
+        torch.cuda.set_device(local)
+        print(json.dumps({"metric": "general-cell k-space", "general": run_general(rbe, steps=args.steps)}),
+              flush=True)
         return
     if args.profile_batched:
         # profiling aid: only the batched-versus-loop k-space measurement
