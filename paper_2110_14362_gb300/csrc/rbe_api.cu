@@ -78,7 +78,7 @@ static bool is_device_ptr(const void* p)
     return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
 }
 
-static rbe_status check_dev(rbe_ctx ctx, const void* p, const char* name, bool required)
+rbe_status check_dev(rbe_ctx ctx, const void* p, const char* name, bool required)
 {
     if (!p) return required ? fail(ctx, RBE_EINVAL, std::string(name) + " is NULL") : RBE_OK;
     if (reinterpret_cast<uintptr_t>(p) % 8 != 0) return fail(ctx, RBE_EINVAL, std::string(name) + " is not 8-byte aligned");

@@ -159,6 +159,8 @@ inline void ctx_free(rbe_ctx ctx, void* p)
 // Device validation helpers (rbe_api.cu).
 rbe_status fail(rbe_ctx ctx, rbe_status st, const std::string& msg);
 rbe_status cuda_fail(rbe_ctx ctx, cudaError_t err, const char* what);
+// A device pointer argument: NULL allowed unless required, 8-byte aligned, device memory (rbe_api.cu).
+rbe_status check_dev(rbe_ctx ctx, const void* p, const char* name, bool required);
 
 // Host-side rule shared by create/set_box: the per-axis table size for (alpha, l).
 int host_axis_M(double alpha, double ell);

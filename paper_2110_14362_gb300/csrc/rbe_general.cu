@@ -240,7 +240,13 @@ rbe_status rbe_kspace_forces_virial_general(rbe_ctx ctx, int64_t N, const double
     if (!h) return fail(ctx, RBE_EINVAL, "h is NULL");
     if (N < 0 || N > ((int64_t)1 << 31) - 256) return fail(ctx, RBE_EINVAL, "N out of range [0, 2^31 - 256]");
     if ((step >> 56) != 0) return fail(ctx, RBE_EINVAL, "step must be < 2^56");
-    if (N > 0 && (!positions || !charges || !forces_out)) return fail(ctx, RBE_EINVAL, "NULL device buffer");
+    rbe_status st;
+    if ((st = check_dev(ctx, positions, "positions", N > 0)) != RBE_OK ||
+        (st = check_dev(ctx, charges, "charges", N > 0)) != RBE_OK ||
+        (st = check_dev(ctx, forces_out, "forces_out", N > 0)) != RBE_OK ||
+        (st = check_dev(ctx, virial_out, "virial_out", false)) != RBE_OK ||
+        (st = check_dev(ctx, energy_out, "energy_out", false)) != RBE_OK)
+        return st;
     for (int t = 0; t < 9; ++t)
         if (!std::isfinite(h[t])) return fail(ctx, RBE_EINVAL, "h must be finite");
     const int P = ctx->P;
@@ -258,7 +264,6 @@ rbe_status rbe_kspace_forces_virial_general(rbe_ctx ctx, int64_t N, const double
         if (M > (1 << 20)) return fail(ctx, RBE_EINVAL, "alpha |a_j|^2 too large for the per-axis tables");
         need = std::max(need, 2 * M + 1);
     }
-    rbe_status st;
     if ((st = ensure_table_capacity(ctx, need)) != RBE_OK) return st;
     if ((st = ensure_k_capacity(ctx, P)) != RBE_OK) return st;
     if (ctx->gchain_cap < P) {

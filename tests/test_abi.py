@@ -51,6 +51,12 @@ def test_argument_validation_without_gpu():
     assert lib.rbe_measure_pipe(7, 10, None) == rbe.RBE_EINVAL
     for st in range(8):
         assert lib.rbe_status_string(st).startswith(b"RBE_")
+    # the sampler, pressure-batch, reuse and general-cell entries refuse a NULL context
+    assert lib.rbe_set_sampler(None, rbe.RBE_SAMPLER_MH) == rbe.RBE_EINVAL
+    assert lib.rbe_set_pressure_batch(None, 10) == rbe.RBE_EINVAL
+    assert lib.rbe_set_sample_reuse(None, 4) == rbe.RBE_EINVAL
+    cell = (ctypes.c_double * 9)(10.0, 0, 0, 0, 10.0, 0, 0, 0, 10.0)
+    assert lib.rbe_kspace_forces_virial_general(None, 0, None, None, cell, 0, None, None, None) == rbe.RBE_EINVAL
 
 
 def test_python_binding_raises_without_fallback():
