@@ -22,6 +22,7 @@ _SRC = os.path.join(_HERE, "rbe_oracle.c")
 _SRC_NPT = os.path.join(_HERE, "npt_oracle.c")
 _SRC_SMP = os.path.join(_HERE, "sampler_oracle.c")
 _SRC_GEN = os.path.join(_HERE, "general_oracle.c")
+_SRC_FLX = os.path.join(_HERE, "flexible_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -35,7 +36,7 @@ _c_uint32_p = ctypes.POINTER(ctypes.c_uint32)
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc into ``oracle/_build/liboracle.so`` and return its path."""
     os.makedirs(_BUILD, exist_ok=True)
-    srcs = [s for s in (_SRC, _SRC_NPT, _SRC_SMP, _SRC_GEN) if os.path.exists(s)]
+    srcs = [s for s in (_SRC, _SRC_NPT, _SRC_SMP, _SRC_GEN, _SRC_FLX) if os.path.exists(s)]
     newest = max(os.path.getmtime(s) for s in srcs)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".{os.getpid()}.tmp"
@@ -93,6 +94,8 @@ def _load():
                 _bind_samplers(lib)
             if hasattr(lib, "orc_gen_kspace"):
                 _bind_general(lib)
+            if hasattr(lib, "orc_flex_step"):
+                _bind_flexible(lib)
             _lib = lib
     return _lib
 
@@ -177,6 +180,34 @@ def _bind_general(lib):
     lib.orc_gen_sample_k_mh.argtypes = [_c_double_p, ctypes.c_double, ctypes.c_int32, ctypes.c_uint64,
                                         ctypes.c_uint64, _c_int32_p, _c_double_p]
     lib.orc_gen_sample_k_mh.restype = ctypes.c_int
+
+
+class FlexParams(ctypes.Structure):
+    """Parameters of the flexible-cell NPT step (mirrors orc_flex_params in flexible_oracle.c)."""
+    _fields_ = [("dt", ctypes.c_double), ("kT", ctypes.c_double), ("P_ext", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("gamma_h", ctypes.c_double), ("M", ctypes.c_double * 9),
+                ("alpha", ctypes.c_double), ("rc", ctypes.c_double), ("qqr2e", ctypes.c_double),
+                ("lj_sigma", ctypes.c_double), ("lj_eps", ctypes.c_double), ("max_disp", ctypes.c_double),
+                ("chi", ctypes.c_double), ("P", ctypes.c_int32), ("kspace", ctypes.c_int32), ("real", ctypes.c_int32),
+                ("noise", ctypes.c_int32), ("seed", ctypes.c_uint64), ("chain", ctypes.c_void_p)]
+
+
+def _bind_flexible(lib):
+    F = ctypes.POINTER(FlexParams)
+    lib.orc_flex_pair_real.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       _c_double_p, _c_double_p, _c_double_p]
+    lib.orc_flex_pair_real.restype = ctypes.c_int
+    lib.orc_flex_forces.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p, ctypes.c_uint64, F,
+                                    _c_double_p, _c_double_p, _c_double_p]
+    lib.orc_flex_forces.restype = ctypes.c_int
+    lib.orc_flex_step.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p, _c_double_p, _c_double_p,
+                                  _c_double_p, _c_double_p, _c_double_p, ctypes.c_uint64, F, _c_double_p]
+    lib.orc_flex_step.restype = ctypes.c_int
+    lib.orc_flex_run.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p, _c_double_p, _c_double_p,
+                                 _c_double_p, _c_double_p, _c_double_p, ctypes.c_uint64, ctypes.c_int32, F,
+                                 _c_double_p, _c_double_p, _c_double_p]
+    lib.orc_flex_run.restype = ctypes.c_int
 
 
 def _dp(a):
@@ -578,3 +609,59 @@ def gen_sample_k_mh(h, alpha: float, P: int, seed: int, step: int, state):
     _check(_load().orc_gen_sample_k_mh(_dp(_f64(h, (3, 3))), alpha, P, seed, step, _ip(state), ctypes.byref(S)),
            "gen_sample_k_mh")
     return state, S.value
+
+
+# ---------------------------------------------------------------------------------
+# Flexible-cell Langevin NPT (flexible_oracle.c)
+def flex_params(**kw) -> FlexParams:
+    d = dict(dt=0.001, kT=KB * 300.0, P_ext=1.0 * BAR, gamma=10.0, gamma_h=2.0, M=(1.0,) * 9, alpha=0.2, rc=7.0,
+             qqr2e=QQR2E, lj_sigma=2.0, lj_eps=0.5, max_disp=0.0, chi=2.0, P=100, kspace=1, real=1, noise=1, seed=1,
+             chain=None)
+    d.update(kw)
+    d["M"] = (ctypes.c_double * 9)(*[float(x) for x in np.asarray(d["M"], dtype=float).reshape(9)])
+    return FlexParams(**d)
+
+
+class FlexState:
+    """Oracle state of the flexible-cell step: r, p, F, h (3x3), p^h (3x3), W (3x3), and the MH chain."""
+
+    def __init__(self, r, p, q, m, h, ph=None, P=100):
+        self.r = _f64(r).copy()
+        self.p = _f64(p).copy()
+        self.q = _f64(q)
+        self.m = _f64(m)
+        self.h = _f64(h, (3, 3)).copy()
+        self.ph = np.zeros((3, 3)) if ph is None else _f64(ph, (3, 3)).copy()
+        self.F = np.zeros_like(self.r)
+        self.W = np.zeros((3, 3))
+        self.chain = np.zeros((max(P, 1), 3), dtype=np.int32)
+
+    @property
+    def N(self):
+        return self.q.shape[0]
+
+    def bind(self, prm: FlexParams):
+        prm.chain = self.chain.ctypes.data
+        return prm
+
+
+def flex_forces(st: FlexState, step: int, prm: FlexParams):
+    E = np.zeros(3)
+    _check(_load().orc_flex_forces(st.N, _dp(st.r), _dp(st.q), _dp(st.h), step, ctypes.byref(st.bind(prm)),
+                                   _dp(st.F), _dp(st.W), _dp(E)), "flex_forces")
+    return E
+
+
+def flex_step(st: FlexState, step: int, prm: FlexParams):
+    E = np.zeros(3)
+    _check(_load().orc_flex_step(st.N, _dp(st.r), _dp(st.p), _dp(st.F), _dp(st.q), _dp(st.m), _dp(st.h), _dp(st.ph),
+                                 _dp(st.W), step, ctypes.byref(st.bind(prm)), _dp(E)), "flex_step")
+    return E
+
+
+def flex_run(st: FlexState, step0: int, n: int, prm: FlexParams):
+    """n steps; returns (h[n,3,3], P_ins[n,3,3], extended energy[n])."""
+    hs, Ps, H = np.zeros((n, 3, 3)), np.zeros((n, 3, 3)), np.zeros(n)
+    _check(_load().orc_flex_run(st.N, _dp(st.r), _dp(st.p), _dp(st.F), _dp(st.q), _dp(st.m), _dp(st.h), _dp(st.ph),
+                                _dp(st.W), step0, n, ctypes.byref(st.bind(prm)), _dp(hs), _dp(Ps), _dp(H)), "flex_run")
+    return hs, Ps, H
