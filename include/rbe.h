@@ -347,6 +347,83 @@ rbe_status rbe_npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch);
 rbe_status rbe_npt_step(rbe_ctx ctx, rbe_system* sys, int32_t nsteps);
 
 /* ---------------------------------------------------------------------------------
+ * Langevin NPT with a fully flexible cell (App. A, the fully flexible cells; the k-space of
+ * App. C in a general cell).  The cell h is 3x3, row-major, with the cell vectors a, b, c as its
+ * columns (r = h s for scaled coordinates s) and det h > 0; its momenta p^h (kJ/mol ps/A) and
+ * masses M (kJ/mol ps^2/A^2) have one entry per entry of h.  With A = (dh/dt) h^{-1}:
+ *   dr/dt = p/m + A r,   dp/dt = 100 F - A^T p - gamma p + sqrt(2 gamma 100 kT m) xi,
+ *   dh/dt = p^h / M (entrywise),
+ *   dp^h/dt = (Kt + W - (P V + chi kT) I) h^{-T} - gamma_h p^h + sqrt(2 gamma_h kT M) xi,
+ * Kt = sum_i p_i p_i^T / (100 m_i), W the full virial tensor (k-space x qqr2e plus real space),
+ * V = det h.  chi = 2 (d - 1) weights the cells by det(h)^{1-d}, the isobaric ensemble of a
+ * flexible cell; without friction and noise the step conserves, to O(dt^2),
+ *   H = K + U + P V + chi kT ln V + sum (p^h)^2 / (2 M).
+ * Splitting of rbe_npt_step with matrices: R^p/2 (p <- e^{-A^T t} p + t phi(-A^T t) 100 F),
+ * R/2 (r <- e^{A t} r + t phi(A t) p/m, the peculiar part capped), V/2 (h += t p^h/M), O^p, O,
+ * V^p/2 (p^h += t (Kt + W - (P V + chi kT) I) h^{-T}), with t = dt/2, A frozen over each
+ * sub-step and phi(X) = sum_k X^k / (k+1)!.  Cell noise: Philox stream 2 (rbe_npt_step's cell
+ * counter) at indices 0 (the diagonal: z[0], z[1], z[2]), 1 and 2 (the off-diagonal entries in
+ * row-major order: z1[0..3], z2[0..1]).  Positions are wrapped to s in [0, 1) after every step.
+ * k-space: the RBE estimator of rbe_kspace_forces_virial_general (the context's general-cell MH
+ * chain, P frequencies, batch = the step index) times qqr2e; the context's sampler, pressure
+ * batch and sample reuse settings do not apply.  Real space: the pair terms of rbe_npt_step by
+ * the minimum image in scaled coordinates, on a cell list in s; needs rc <= w_j / 2 for the
+ * three widths w_j = V / |a_k x a_l| of the cell. */
+typedef struct {
+    double dt;        /* ps */
+    double kT;        /* kJ/mol */
+    double P_ext;     /* kJ/mol/A^3 */
+    double gamma;     /* particle friction, 1/ps */
+    double gamma_h;   /* cell friction, 1/ps */
+    double M[9];      /* cell masses, row-major like h, each > 0 */
+    double rc;        /* real-space cutoff, A */
+    double qqr2e;     /* Coulomb constant, kJ/mol A/e^2 */
+    double lj_sigma;  /* A */
+    double lj_eps;    /* kJ/mol; 0 disables the Lennard-Jones term */
+    double max_disp;  /* cap on the peculiar displacement per step (split over the two R/2), A; 0 = none */
+    double chi;       /* 2 for the flexible-cell ensemble; 0 drops the ln V term */
+    int32_t kspace;   /* 1: RBE k-space forces and virial */
+    int32_t real;     /* 1: real-space forces and virial */
+    int32_t noise;    /* 1: Langevin noise in O and O^p */
+    int32_t pad;
+} rbe_flex_params;
+
+/* Doubles of the device cell block of the flexible cell:
+ *   [0..8]   h (row-major)         [9..17]  p^h            [18..26] W (full virial tensor)
+ *   [27..35] Kt = sum p p^T/(100 m)  [36..44] pressure tensor (Kt + W) / V
+ *   [45] E_k (k-space incl. self, x qqr2e)  [46] E_coul (real space)  [47] E_lj  [48] V
+ *   [49] H, the extended energy     [50] step index (64-bit integer bits)
+ * the rest reserved. */
+#define RBE_FLEX_CELL_DOUBLES 64
+
+/* One flexible-cell replica; every buffer is the caller's device memory (8-byte aligned). */
+typedef struct {
+    int64_t N;
+    double* pos;          /* device N*3, wrapped to scaled coordinates in [0, 1) after every step */
+    double* mom;          /* device N*3 */
+    double* force;        /* device N*3 (kept between steps) */
+    const double* charge; /* device N */
+    const double* mass;   /* device N */
+    double* cell;         /* device RBE_FLEX_CELL_DOUBLES: h and p^h set by the caller */
+    uint64_t step;        /* host: the next step index */
+    rbe_flex_params params;
+} rbe_flex_system;
+
+/* Forces, virial tensor, energies and H at the current state with the RBE batch `batch`;
+ * fills sys->force and cell[18..49] (h and p^h are kept).  Call once before the first step.
+ * Reads h back (synchronises the context's stream) and sizes the tables and the cell list for
+ * cell vectors up to twice as long, and widths up to twice as wide, as the initial ones; a
+ * step whose cell leaves that range, or breaks rc <= w_j/2 with real space on, is flagged on
+ * the device and reported as RBE_ESTATE by the next rbe_sync.  RBE_EINVAL for bad pointers,
+ * parameters or cells. */
+rbe_status rbe_flex_init(rbe_ctx ctx, rbe_flex_system* sys, uint64_t batch);
+
+/* Advance nsteps >= 1 steps; asynchronous on the context's stream; sys->step advances by
+ * nsteps.  The step index also lives on the device (cell[50]), so the launches of one call may
+ * be captured in a CUDA graph and replayed. */
+rbe_status rbe_flex_step(rbe_ctx ctx, rbe_flex_system* sys, int32_t nsteps);
+
+/* ---------------------------------------------------------------------------------
  * Batched k-space evaluation: many systems of uneven N (the RBE force, energy and virial of
  * Sec. 4.2 for each) in five launches per evaluation, FP32-phase path with plain FP32
  * accumulation inside a staged tile.  The batch fixes alpha and P; every item brings its own

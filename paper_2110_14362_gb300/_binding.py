@@ -52,6 +52,33 @@ class System(ctypes.Structure):
                 ("cell", ctypes.c_void_p), ("step", ctypes.c_uint64), ("params", NptParams)]
 
 
+class FlexParams(ctypes.Structure):
+    """rbe_flex_params (include/rbe.h): the fully flexible cell."""
+    _fields_ = [("dt", ctypes.c_double), ("kT", ctypes.c_double), ("P_ext", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("gamma_h", ctypes.c_double), ("M", ctypes.c_double * 9),
+                ("rc", ctypes.c_double), ("qqr2e", ctypes.c_double), ("lj_sigma", ctypes.c_double),
+                ("lj_eps", ctypes.c_double), ("max_disp", ctypes.c_double), ("chi", ctypes.c_double),
+                ("kspace", ctypes.c_int32), ("real", ctypes.c_int32), ("noise", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+    def __init__(self, **kw):
+        if "M" in kw and not isinstance(kw["M"], ctypes.Array):
+            kw["M"] = (ctypes.c_double * 9)(*[float(x) for x in np.asarray(kw["M"], dtype=np.float64).reshape(9)])
+        super().__init__(**kw)
+
+
+class FlexSystem(ctypes.Structure):
+    """rbe_flex_system (include/rbe.h)."""
+    _fields_ = [("N", ctypes.c_int64), ("pos", ctypes.c_void_p), ("mom", ctypes.c_void_p),
+                ("force", ctypes.c_void_p), ("charge", ctypes.c_void_p), ("mass", ctypes.c_void_p),
+                ("cell", ctypes.c_void_p), ("step", ctypes.c_uint64), ("params", FlexParams)]
+
+
+RBE_FLEX_CELL_DOUBLES = 64
+# slots of the flexible cell block (include/rbe.h)
+FLEX_H, FLEX_PH, FLEX_W, FLEX_KT, FLEX_PT = 0, 9, 18, 27, 36
+FLEX_EK, FLEX_EC, FLEX_EL, FLEX_V, FLEX_HAM, FLEX_STEP = 45, 46, 47, 48, 49, 50
+
 RBE_CELL_DOUBLES = 32
 RBE_BAROSTAT_NONE, RBE_BAROSTAT_ISO, RBE_BAROSTAT_ANISO, RBE_BAROSTAT_SEMI = 0, 1, 2, 3
 # slots of the cell block (include/rbe.h)
@@ -104,6 +131,8 @@ SIGNATURES = [
      [_dp, ctypes.c_double, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, _vp, _vp, _vp]),
     ("rbe_npt_init", ctypes.c_int, [_vp, ctypes.POINTER(System), ctypes.c_uint64]),
     ("rbe_npt_step", ctypes.c_int, [_vp, ctypes.POINTER(System), ctypes.c_int32]),
+    ("rbe_flex_init", ctypes.c_int, [_vp, ctypes.POINTER(FlexSystem), ctypes.c_uint64]),
+    ("rbe_flex_step", ctypes.c_int, [_vp, ctypes.POINTER(FlexSystem), ctypes.c_int32]),
     ("rbe_batch_create", ctypes.c_int, [ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                         ctypes.POINTER(_vp)]),
     ("rbe_batch_destroy", ctypes.c_int, [_vp]),
@@ -330,6 +359,52 @@ class NptReplica:
         """(pos, mom, force, box, cell block) as NumPy arrays (synchronises)."""
         c = self.cell.cpu().numpy()
         return (self.pos.cpu().numpy(), self.mom.cpu().numpy(), self.force.cpu().numpy(), c[:3].copy(), c)
+
+
+def rbe_flex_init(h, sys_: "FlexSystem", batch: int):
+    _check(load().rbe_flex_init(h, ctypes.byref(sys_), int(batch)), h)
+
+
+def rbe_flex_step(h, sys_: "FlexSystem", nsteps: int):
+    _check(load().rbe_flex_step(h, ctypes.byref(sys_), int(nsteps)), h)
+
+
+class FlexReplica:
+    """One device-resident replica with a fully flexible cell: torch CUDA tensors for r, p, F, q,
+    m and the cell block (h and p^h row-major, the cell vectors as the columns of h), and the
+    rbe_flex_system that points at them."""
+
+    def __init__(self, pos, mom, charge, mass, h, params: FlexParams, device, step: int = 0, ph=None):
+        import torch
+        f64 = torch.float64
+        self.pos = torch.as_tensor(np.ascontiguousarray(pos), dtype=f64).to(device).contiguous()
+        self.mom = torch.as_tensor(np.ascontiguousarray(mom), dtype=f64).to(device).contiguous()
+        self.force = torch.zeros_like(self.pos)
+        self.charge = torch.as_tensor(np.ascontiguousarray(charge), dtype=f64).to(device).contiguous()
+        self.mass = torch.as_tensor(np.ascontiguousarray(mass), dtype=f64).to(device).contiguous()
+        cell = np.zeros(RBE_FLEX_CELL_DOUBLES)
+        cell[FLEX_H:FLEX_H + 9] = np.asarray(h, dtype=np.float64).reshape(9)
+        if ph is not None:
+            cell[FLEX_PH:FLEX_PH + 9] = np.asarray(ph, dtype=np.float64).reshape(9)
+        self.cell = torch.as_tensor(cell).to(device).contiguous()
+        self.sys = FlexSystem(N=int(self.charge.shape[0]), pos=self.pos.data_ptr(), mom=self.mom.data_ptr(),
+                              force=self.force.data_ptr(), charge=self.charge.data_ptr(), mass=self.mass.data_ptr(),
+                              cell=self.cell.data_ptr(), step=int(step), params=params)
+
+    def init(self, ctx: "Context", batch: int | None = None):
+        rbe_flex_init(ctx.h, self.sys, self.sys.step if batch is None else batch)
+
+    def step(self, ctx: "Context", nsteps: int = 1):
+        rbe_flex_step(ctx.h, self.sys, nsteps)
+
+    def state(self):
+        """dict of NumPy arrays: r, p, F, h, ph, W, Kt, Pt (3x3), Ek, Ec, El, V, H (synchronises)."""
+        c = self.cell.cpu().numpy()
+        m = lambda o: c[o:o + 9].reshape(3, 3).copy()  # noqa: E731
+        return {"r": self.pos.cpu().numpy(), "p": self.mom.cpu().numpy(), "F": self.force.cpu().numpy(),
+                "h": m(FLEX_H), "ph": m(FLEX_PH), "W": m(FLEX_W), "Kt": m(FLEX_KT), "Pt": m(FLEX_PT),
+                "Ek": c[FLEX_EK], "Ec": c[FLEX_EC], "El": c[FLEX_EL], "V": c[FLEX_V], "H": c[FLEX_HAM],
+                "step": int(c[FLEX_STEP:FLEX_STEP + 1].view(np.int64)[0])}
 
 
 class Batch:

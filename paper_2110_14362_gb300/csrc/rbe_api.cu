@@ -204,6 +204,8 @@ rbe_status rbe_destroy(rbe_ctx ctx)
     if (ctx->m_all) cudaFree(ctx->m_all);
     if (ctx->gchain) cudaFree(ctx->gchain);
     if (ctx->gpos) cudaFree(ctx->gpos);
+    if (ctx->flex_coef) cudaFree(ctx->flex_coef);
+    if (ctx->gcell_dev) cudaFree(ctx->gcell_dev);
     delete ctx;
     return RBE_OK;
 }
@@ -500,6 +502,32 @@ rbe_status rbe_npt_step(rbe_ctx ctx, rbe_system* sys, int32_t nsteps)
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(ctx, RBE_ECUDA, "cannot select the context's device");
     return npt_run(ctx, sys, nsteps);
+}
+
+rbe_status rbe_flex_init(rbe_ctx ctx, rbe_flex_system* sys, uint64_t batch)
+{
+    if (!ctx) return RBE_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(ctx, RBE_ECUDA, "cannot select the context's device");
+    if (sys) {
+        rbe_status st;
+        const int64_t N = sys->N;
+        if ((st = check_dev(ctx, sys->pos, "pos", N > 0)) != RBE_OK) return st;
+        if ((st = check_dev(ctx, sys->mom, "mom", N > 0)) != RBE_OK) return st;
+        if ((st = check_dev(ctx, sys->force, "force", N > 0)) != RBE_OK) return st;
+        if ((st = check_dev(ctx, sys->charge, "charge", N > 0)) != RBE_OK) return st;
+        if ((st = check_dev(ctx, sys->mass, "mass", N > 0)) != RBE_OK) return st;
+        if ((st = check_dev(ctx, sys->cell, "cell", true)) != RBE_OK) return st;
+    }
+    return flex_init(ctx, sys, batch);
+}
+
+rbe_status rbe_flex_step(rbe_ctx ctx, rbe_flex_system* sys, int32_t nsteps)
+{
+    if (!ctx) return RBE_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(ctx, RBE_ECUDA, "cannot select the context's device");
+    return flex_run(ctx, sys, nsteps);
 }
 
 rbe_status rbe_set_kernel_timing(rbe_ctx ctx, int32_t enable)

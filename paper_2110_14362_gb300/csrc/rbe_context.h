@@ -130,6 +130,9 @@ struct rbe_ctx_s {
     int32_t last_K = 0;
     rbe::NptBuffers npt;
     int64_t npt_ready_N = -1;        // N of the system rbe_npt_init prepared the scratch for
+    int64_t flex_ready_N = -1;       // N of the system rbe_flex_init prepared the scratch for
+    void* flex_coef = nullptr;       // per-step coefficients of the flexible-cell step (rbe_flex.cu)
+    void* gcell_dev = nullptr;       // general-cell quantities of the current cell (rbe_flex.cu)
     bool timing = false;             // record CUDA events around each evaluation kernel
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     // pipelined host-buffer calls: a copy stream, its events, pinned outputs (virial, energy,
@@ -175,6 +178,15 @@ rbe_status launch_sample_device_box(rbe_ctx ctx, uint64_t step, int P, const uns
 rbe_status launch_tables_sample_device(rbe_ctx ctx, int P, const double* box_dev, const unsigned long long* step_dev);
 rbe_status npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch);
 rbe_status npt_run(rbe_ctx ctx, rbe_system* sys, int32_t nsteps);
+// Shared with the flexible-cell step (rbe_npt.cu): scratch for N particles and cells of edges up
+// to twice `box` (plus a list with skin > 0), the pair kernel's grid, the cell list of the
+// constants in npt.cellc (nls: the neighbour-list state or NULL).
+rbe_status npt_ensure(rbe_ctx ctx, int64_t N, const double box[3], double rc, double skin);
+int pair_blocks(rbe_ctx ctx, int64_t N, bool fp64);
+rbe_status launch_cell_list(rbe_ctx ctx, int64_t N, const double* pos, const double* q, void* nls, bool fp64);
+// The flexible-cell step (rbe_flex.cu).
+rbe_status flex_init(rbe_ctx ctx, rbe_flex_system* sys, uint64_t batch);
+rbe_status flex_run(rbe_ctx ctx, rbe_flex_system* sys, int32_t nsteps);
 rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int K,
                            bool uniform_weight, double* F, double* W, double* E);
 rbe_status launch_rbe(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int P, double* F, double* W,

@@ -27,22 +27,10 @@
 
 #include "rbe_context.h"
 #include "rbe_device.cuh"
+#include "rbe_npt_common.cuh"
 
 namespace rbe {
 
-constexpr double kFConv = 100.0;  // kJ/mol/A per g/mol -> A/ps^2
-constexpr int kNptThreads = 256;
-constexpr int kScanThreads = 1024;
-constexpr int kSortWarps = 8;        // k_cl_sort: warps (cells) per block
-constexpr int kPairWarps = 8;        // k_pair: warps (particles in flight) per block
-constexpr int kPairBlocksPerSM = 4;  // k_pair (FP32): resident blocks per SM the grid is sized for
-constexpr int kPairBlocksPerSM64 = 2;  // k_pair (FP64): more registers per thread
-constexpr int kListBatch = 4;        // k_pair (list): list entries per lane loaded together
-constexpr int kHitCap = 32 * (kListBatch + 1);  // k_pair: buffered candidates per warp (< 32 + 32 kListBatch)
-// Per-block partial sums of the pair and finishing kernels: 8 doubles per block.  Isotropic:
-// finishing blocks {2K} at slot 0, pair blocks {W, E_coul, E_lj} at 1..3.  Rectangular cells:
-// finishing blocks {2K_x, 2K_y, 2K_z} at 0..2, pair blocks {W_xx, W_yy, W_zz, E_coul, E_lj} at 3..7.
-constexpr int kPartStride = 8;
 // rbe_npt_init sizes the per-axis tables and the cell list for box edges up to this many
 // times the initial ones; a box beyond it is flagged (RBE_ESTATE) by the step.
 constexpr double kBoxHeadroom = 2.0;
@@ -71,25 +59,6 @@ __device__ __forceinline__ double expm1_over(double x, double t)
     return t * expm1(x) / x;
 }
 
-// Four standard normals from one Philox call: u = (w + 1/2) 2^-32, Box--Muller.
-__device__ __forceinline__ void npt_normals(uint64_t seed, uint32_t stream, uint64_t step, uint32_t index,
-                                            double z[4])
-{
-    const uint4 w = philox4x32_10(make_uint4(index, 0u, (uint32_t)step,
-                                             (stream << 24) | (uint32_t)((step >> 32) & 0xFFFFFFu)),
-                                  (uint32_t)seed, (uint32_t)(seed >> 32));
-    const double u0 = ((double)w.x + 0.5) * 0x1.0p-32, u1 = ((double)w.y + 0.5) * 0x1.0p-32;
-    const double u2 = ((double)w.z + 0.5) * 0x1.0p-32, u3 = ((double)w.w + 0.5) * 0x1.0p-32;
-    double s, c;
-    const double r0 = sqrt(-2.0 * log(u0));
-    sincospi(2.0 * u1, &s, &c);
-    z[0] = r0 * c;
-    z[1] = r0 * s;
-    const double r1 = sqrt(-2.0 * log(u2));
-    sincospi(2.0 * u3, &s, &c);
-    z[2] = r1 * c;
-    z[3] = r1 * s;
-}
 
 // ---------------------------------------------------------------------------------
 // Cell-variable part of the step (Sec. 3.3): V^p/2, R^p/2 coefficient, V/2, R/2
@@ -103,25 +72,6 @@ __device__ __forceinline__ uint64_t cell_step(const double* cell)
     return (uint64_t)__double_as_longlong(cell[kCellStep]);
 }
 
-// Constants of the cell list for the current box, written once per step (by the cell
-// update, or k_cell_consts before the first forces), so that no kernel of the step divides
-// by the box or by rc itself (FP64 divisions are slow on this GPU).
-struct CellConsts {
-    double L[3], invL[3];
-    float Lf[3], invLf[3];
-    float pass64;  // FP64 path: squared FP32 search radius (rc plus 2^-16 l_max)
-    int nc[3];     // cells per axis, floor(l / rc) clamped to 1..2^20
-    int ncell;     // nc0 nc1 nc2, or -1 when that exceeds the cell arrays
-    int ok;        // ncell >= 0 and rc <= l/2 on every axis
-};
-
-__device__ __forceinline__ int cell_dim(double l, double rc)
-{
-    // clamped in FP64 before the conversion: any box (huge, infinite, NaN) gives 1..2^20
-    // cells per axis, whose product cannot overflow and is checked against the capacity
-    const double f = floor(l / rc);
-    return f >= 1.0 ? (f <= 1048576.0 ? (int)f : 1048576) : 1;
-}
 
 // Lanes 0..2 of one warp: axis `lane` of the box L; then lane 0 the totals.  Cells of at
 // least rcell (rc, or rc + skin when a neighbour list is built from them).
@@ -553,28 +503,6 @@ __device__ __forceinline__ void drift_add(double r[3], const double am1[3], doub
     r[2] += r[2] * am1[2] + d[2];
 }
 
-// The same four normals in FP32 (FP32-phase path): Box--Muller with the fast logarithm and
-// sine/cosine; the angle 2 pi u is taken as 2 pi (u - 1/2) + pi, so that the argument of the
-// fast sine/cosine stays in [-pi, pi).
-__device__ __forceinline__ void npt_normals_f32(uint64_t seed, uint32_t stream, uint64_t step, uint32_t index,
-                                                double z[4])
-{
-    const uint4 w = philox4x32_10(make_uint4(index, 0u, (uint32_t)step,
-                                             (stream << 24) | (uint32_t)((step >> 32) & 0xFFFFFFu)),
-                                  (uint32_t)seed, (uint32_t)(seed >> 32));
-    const float k = 0x1.0p-32f, two_pi = 6.28318530717958647692f;
-    const float u0 = ((float)w.x + 0.5f) * k, u1 = ((float)w.y + 0.5f) * k;
-    const float u2 = ((float)w.z + 0.5f) * k, u3 = ((float)w.w + 0.5f) * k;
-    float s, c;
-    const float r0 = sqrtf(-2.0f * __logf(u0));
-    __sincosf(two_pi * (u1 - 0.5f), &s, &c);
-    z[0] = -(double)(r0 * c);
-    z[1] = -(double)(r0 * s);
-    const float r1 = sqrtf(-2.0f * __logf(u2));
-    __sincosf(two_pi * (u3 - 0.5f), &s, &c);
-    z[2] = -(double)(r1 * c);
-    z[3] = -(double)(r1 * s);
-}
 
 // Particle part before the forces: R^p/2, R/2, O, R/2, wrap into the new box.  kF32Noise:
 // the Langevin normals in FP32 (FP32-phase path); the state stays FP64 either way.  kRect:
@@ -774,38 +702,6 @@ k_cl_sort(const CellConsts* __restrict__ cc, const int* __restrict__ cnt, const 
 // over the slots (grid-stride); per-block partials {W_r, E_coul, E_lj} at slots 1..3, or with
 // kDiag (rectangular cells) {W_xx, W_yy, W_zz, E_coul, E_lj} at slots 3..7 (W_jj = sum f d_j^2).  A box that
 // outgrew the cell arrays (flagged by k_cl_count) leaves F_r = 0.
-// Pair constants, formed on the host in FP64 and rounded once: the kernel never derives
-// them itself (the FP32 kernel would otherwise recompute FP64 products in its loops).
-struct PairConst {
-    double rc, rc2, sa, a, two_sa_pi, qk, s2, e4, e24;
-    float rcf, rc2f, saf, af, two_sa_pif, qkf, s2f, e4f, e24f;
-    int lj;
-};
-
-static PairConst make_pair_const(double rc, double alpha, double qqr2e, double lj_sigma, double lj_eps)
-{
-    PairConst c;
-    c.rc = rc;
-    c.rc2 = rc * rc;
-    c.sa = std::sqrt(alpha);
-    c.a = alpha;
-    c.two_sa_pi = 2.0 * std::sqrt(alpha / 3.14159265358979323846);
-    c.qk = qqr2e;
-    c.s2 = lj_sigma * lj_sigma;
-    c.e4 = 4.0 * lj_eps;
-    c.e24 = 24.0 * lj_eps;
-    c.rcf = (float)c.rc;
-    c.rc2f = (float)c.rc2;
-    c.saf = (float)c.sa;
-    c.af = (float)c.a;
-    c.two_sa_pif = (float)c.two_sa_pi;
-    c.qkf = (float)c.qk;
-    c.s2f = (float)c.s2;
-    c.e4f = (float)c.e4;
-    c.e24f = (float)c.e24;
-    c.lj = lj_eps != 0.0;
-    return c;
-}
 
 // Modes of the pair kernel: search the cells and evaluate (no list), search the cells within
 // the list radius and write the list (only on a rebuild step), evaluate the listed pairs.
@@ -1367,7 +1263,7 @@ static rbe_status npt_check(rbe_ctx ctx, const char* what)
 
 // Blocks of the pair kernel: one warp per particle, at most one resident wave (the warps
 // stride over the rest).  The FP32 count is the larger one and sizes the partials.
-static int pair_blocks(rbe_ctx ctx, int64_t N, bool fp64)
+int pair_blocks(rbe_ctx ctx, int64_t N, bool fp64)
 {
     const int64_t want = (N + kPairWarps - 1) / kPairWarps;
     const int per_sm = fp64 ? kPairBlocksPerSM64 : kPairBlocksPerSM;
@@ -1376,7 +1272,7 @@ static int pair_blocks(rbe_ctx ctx, int64_t N, bool fp64)
 
 // Grow the NPT scratch for N particles and a box whose edges may double; with skin > 0 also
 // the neighbour list (twice the expected neighbours at the initial density, plus 64).
-static rbe_status npt_ensure(rbe_ctx ctx, int64_t N, const double box[3], double rc, double skin)
+rbe_status npt_ensure(rbe_ctx ctx, int64_t N, const double box[3], double rc, double skin)
 {
     NptBuffers& b = ctx->npt;
     cudaError_t e;
@@ -1462,6 +1358,27 @@ static rbe_status npt_ensure(rbe_ctx ctx, int64_t N, const double box[3], double
     return RBE_OK;
 }
 
+// The cell list of the constants in ctx->npt.cellc: count, scan, fill, per-cell sort and the
+// packed positions (FP64 as well with fp64).  With a neighbour list (nls) the launches exit at
+// once on steps that do not rebuild it.
+rbe_status launch_cell_list(rbe_ctx ctx, int64_t N, const double* pos, const double* q, void* nls_v, bool fp64)
+{
+    NptBuffers& b = ctx->npt;
+    cudaStream_t s = ctx->stream;
+    NListState* nls = static_cast<NListState*>(nls_v);
+    const CellConsts* cc = static_cast<const CellConsts*>(b.cellc);
+    const int nb = (int)((N + kNptThreads - 1) / kNptThreads);
+    cudaError_t e = cudaMemsetAsync(b.cnt, 0, sizeof(int) * b.cellcap, s);
+    if (e != cudaSuccess) return npt_fail(ctx, e, "cudaMemsetAsync(cells)");
+    k_cl_count<<<nb, kNptThreads, 0, s>>>(N, pos, cc, b.cid, b.cnt, ctx->d.status, nls);
+    k_cl_scan<<<1, kScanThreads, 0, s>>>(cc, b.cnt, b.start, b.cursor, nls);
+    k_cl_fill<<<nb, kNptThreads, 0, s>>>(N, b.cid, b.cursor, b.fill, nls);
+    const int64_t sort_blocks = ((int64_t)b.cellcap + kSortWarps - 1) / kSortWarps;
+    k_cl_sort<<<(unsigned)sort_blocks, kSortWarps * 32, 0, s>>>(cc, b.cnt, b.start, b.fill, b.sorted, pos, q, b.spos32,
+                                                              fp64 ? b.spos64 : nullptr, nls);
+    return npt_check(ctx, "cell list");
+}
+
 // Forces, virial and energies at the current state (k-space batch `batch`), then the
 // finishing kernel (with or without the R^p/2 and V^p/2 of the step's end).
 static rbe_status npt_forces(rbe_ctx ctx, rbe_system* sys, uint64_t batch, int do_kick)
@@ -1500,15 +1417,7 @@ static rbe_status npt_forces(rbe_ctx ctx, rbe_system* sys, uint64_t batch, int d
                 k_nl_check<false><<<grid, kNptThreads, 0, s>>>(N, sys->pos, sys->charge, b.sorted, b.spos32, nullptr,
                                                              b.sref, cc, nls);
         }
-        cudaError_t e = cudaMemsetAsync(b.cnt, 0, sizeof(int) * b.cellcap, s);
-        if (e != cudaSuccess) return npt_fail(ctx, e, "cudaMemsetAsync(cells)");
-        k_cl_count<<<nb, kNptThreads, 0, s>>>(N, sys->pos, cc, b.cid, b.cnt, ctx->d.status, nls);
-        k_cl_scan<<<1, kScanThreads, 0, s>>>(cc, b.cnt, b.start, b.cursor, nls);
-        k_cl_fill<<<nb, kNptThreads, 0, s>>>(N, b.cid, b.cursor, b.fill, nls);
-        const int64_t sort_blocks = ((int64_t)b.cellcap + kSortWarps - 1) / kSortWarps;
-        k_cl_sort<<<(unsigned)sort_blocks, kSortWarps * 32, 0, s>>>(cc, b.cnt, b.start, b.fill,
-                                                                  b.sorted, sys->pos, sys->charge, b.spos32,
-                                                                  fp64 ? b.spos64 : nullptr, nls);
+        if ((st = launch_cell_list(ctx, N, sys->pos, sys->charge, nls, fp64)) != RBE_OK) return st;
         const PairConst pc = make_pair_const(prm.rc, ctx->alpha, prm.qqr2e, prm.lj_sigma, prm.lj_eps);
         const ListArgs la{nls, b.nbr, b.nnb, b.sref, ctx->d.status, b.nbr_cap};
         const double4_32a* s64 = fp64 ? b.spos64 : nullptr;
@@ -1608,6 +1517,7 @@ rbe_status npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch)
     }
     if ((st = ensure_table_capacity(ctx, need)) != RBE_OK) return st;
     ctx->npt_ready_N = sys->N;
+    ctx->flex_ready_N = -1;  // the shared scratch now holds this system's masses and cell list
     // per-particle 1/m and sqrt(m), and the cell-list constants of the initial box
     NptBuffers& b = ctx->npt;
     k_mass_props<<<(unsigned)((sys->N + kNptThreads - 1) / kNptThreads), kNptThreads, 0, ctx->stream>>>(

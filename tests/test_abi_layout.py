@@ -17,6 +17,8 @@ STRUCTS = {
     "rbe_batch_item": B.BatchItem,
     "rbe_server_config": B.ServerConfig,
     "rbe_request": B.Request,
+    "rbe_flex_params": B.FlexParams,
+    "rbe_flex_system": B.FlexSystem,
 }
 
 
@@ -27,6 +29,7 @@ def _c_layout(tmp_path):
         for f in py._fields_:
             lines.append(f'printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
     lines.append('printf("RBE_CELL_DOUBLES %d\\n", RBE_CELL_DOUBLES);')
+    lines.append('printf("RBE_FLEX_CELL_DOUBLES %d\\n", RBE_FLEX_CELL_DOUBLES);')
     lines += ["return 0;", "}"]
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines))
@@ -44,3 +47,4 @@ def test_ctypes_structs_match_header(tmp_path):
         for f in py._fields_:
             assert c[f"{cname} {f[0]}"] == getattr(py, f[0]).offset, (cname, f[0])
     assert c["RBE_CELL_DOUBLES"] == B.RBE_CELL_DOUBLES
+    assert c["RBE_FLEX_CELL_DOUBLES"] == B.RBE_FLEX_CELL_DOUBLES
