@@ -344,18 +344,38 @@ def serve(rbe, reqs, states, precision, max_slots, chunk, nsteps, use_graphs=Tru
                                  "max": float(lat.max() * 1e3), "chunks": int(lat.size)}}
 
 
+FLEX_TILT = (0.10, -0.08, 0.12)  # xy, xz, yz tilts of the flexible-cell workload, in units of the edge
+
+
+def flex_replica(rbe, N, device):
+    """The serving system in a sheared cell h = L (I + T) (tilts FLEX_TILT), the fully flexible
+    cell with the rectangular barostat's masses on the diagonal and their geometric means off it,
+    the serving system's neighbour-list skin; the cell starts at rest.  Returns the FlexReplica."""
+    pos, mom, q, m, box = inputs.npt_replica(N, 3)
+    L = float(box[0])
+    h = np.diag(box).astype(np.float64)
+    h[0, 1], h[0, 2], h[1, 2] = FLEX_TILT[0] * L, FLEX_TILT[1] * L, FLEX_TILT[2] * L
+    Md = np.asarray(rbe.piston_masses_rect(2, 0.5, 4.5e-5 / BAR, box))
+    prm = rbe.FlexParams(dt=0.001, kT=KB * 300.0, P_ext=1.0 * BAR, gamma=10.0, gamma_h=2.0, M=np.sqrt(np.outer(Md, Md)),
+                         rc=SERVE_RC, qqr2e=1389.35457644382 / SERVE_EPS_R, lj_sigma=2.0, lj_eps=0.5, max_disp=0.05,
+                         chi=2.0, kspace=1, real=1, noise=1, skin=SERVE_SKIN)
+    return rbe.FlexReplica((pos / L) @ h.T, mom, q, m, h, prm, device)
+
+
 def npt_single(rbe, N, precision, steps, warmup=3, barostat=1, sampler=0, ptilde=0, reuse=1):
     """ms per NPT step of one replica of N particles (the serving system), launched directly
-    on one stream, timed with CUDA events after `warmup` steps."""
+    on one stream, timed with CUDA events after `warmup` steps.  barostat 4: the fully flexible
+    cell (flex_replica)."""
     import torch
     pos, mom, q, m, box = inputs.npt_replica(N, 3)
-    prm = serve_params(rbe, box, barostat)
     stream = torch.cuda.current_stream()
     with rbe.Context(box, SERVE_ALPHA, SERVE_P, 1003, precision, stream=stream.cuda_stream) as ctx:
         ctx.set_sampler(sampler)
         ctx.set_pressure_batch(ptilde)
         ctx.set_sample_reuse(reuse)
-        rep = rbe.NptReplica(pos, mom, q, m, box, prm, torch.device("cuda", torch.cuda.current_device()))
+        dev = torch.device("cuda", torch.cuda.current_device())
+        rep = flex_replica(rbe, N, dev) if barostat == 4 else rbe.NptReplica(pos, mom, q, m, box,
+                                                                          serve_params(rbe, box, barostat), dev)
         rep.init(ctx, batch=0)
         rep.step(ctx, warmup)
         ctx.sync()
@@ -375,7 +395,9 @@ def run_npt_single(rbe, sizes, steps):
         out[str(N)] = {"fp32_ms_per_step": f32, "fp64_ms_per_step": f64, "fp32_over_fp64": f64 / f32,
                        # the rectangular cells (per-axis virial and pistons), FP32-phase path
                        "fp32_aniso_ms_per_step": npt_single(rbe, N, rbe.RBE_FP32_PHASE, steps, barostat=2),
-                       "fp32_semi_ms_per_step": npt_single(rbe, N, rbe.RBE_FP32_PHASE, steps, barostat=3)}
+                       "fp32_semi_ms_per_step": npt_single(rbe, N, rbe.RBE_FP32_PHASE, steps, barostat=3),
+                       # the fully flexible (sheared) cell: general-cell k-space and triclinic real space
+                       "fp32_flex_ms_per_step": npt_single(rbe, N, rbe.RBE_FP32_PHASE, steps, barostat=4)}
     return out
 
 
@@ -638,8 +660,9 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=64)
     ap.add_argument("--serve-fp64-sample", type=int, default=16)
     ap.add_argument("--profile-npt", type=int, default=0, help="time only NPT steps of one replica of this N")
-    ap.add_argument("--barostat", type=int, default=1, choices=(0, 1, 2, 3),
-                    help="with --profile-npt: 0 fixed box, 1 isotropic, 2 anisotropic, 3 semi-isotropic")
+    ap.add_argument("--barostat", type=int, default=1, choices=(0, 1, 2, 3, 4),
+                    help="with --profile-npt: 0 fixed box, 1 isotropic, 2 anisotropic, 3 semi-isotropic, "
+                         "4 fully flexible (sheared) cell")
     ap.add_argument("--sampler", choices=["exact", "offline", "mh"], default="exact",
                     help="with --profile-npt: the frequency sampler (Sec. 4.3 variants)")
     ap.add_argument("--ptilde", type=int, default=0, help="with --profile-npt: a separate pressure batch")

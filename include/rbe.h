@@ -367,8 +367,8 @@ rbe_status rbe_npt_step(rbe_ctx ctx, rbe_system* sys, int32_t nsteps);
  * k-space: the RBE estimator of rbe_kspace_forces_virial_general (the context's general-cell MH
  * chain, P frequencies, batch = the step index) times qqr2e; the context's sampler, pressure
  * batch and sample reuse settings do not apply.  Real space: the pair terms of rbe_npt_step by
- * the minimum image in scaled coordinates, on a cell list in s; needs rc <= w_j / 2 for the
- * three widths w_j = V / |a_k x a_l| of the cell. */
+ * the minimum image in scaled coordinates, on a cell list in s or a neighbour list built from
+ * it; needs rc (+ skin) <= w_j / 2 for the three widths w_j = V / |a_k x a_l| of the cell. */
 typedef struct {
     double dt;        /* ps */
     double kT;        /* kJ/mol */
@@ -386,6 +386,10 @@ typedef struct {
     int32_t real;     /* 1: real-space forces and virial */
     int32_t noise;    /* 1: Langevin noise in O and O^p */
     int32_t pad;
+    double skin;      /* A.  0: the real-space pairs come from a cell search every step.  > 0: from a
+                         neighbour list of radius rc + skin (needs rc + skin <= w_j / 2), rebuilt on
+                         the device when the largest displacement since the build and the cell's
+                         deformation h h_ref^{-1} could have brought an unlisted pair within rc */
 } rbe_flex_params;
 
 /* Doubles of the device cell block of the flexible cell:
@@ -393,6 +397,7 @@ typedef struct {
  *   [27..35] Kt = sum p p^T/(100 m)  [36..44] pressure tensor (Kt + W) / V
  *   [45] E_k (k-space incl. self, x qqr2e)  [46] E_coul (real space)  [47] E_lj  [48] V
  *   [49] H, the extended energy     [50] step index (64-bit integer bits)
+ *   [51] neighbour-list builds so far (skin > 0)
  * the rest reserved. */
 #define RBE_FLEX_CELL_DOUBLES 64
 

@@ -14,7 +14,7 @@ from ._binding import (  # noqa: F401
     rbe_version, rbe_set_kernel_timing, rbe_get_kernel_times, rbe_measure_pipe, rbe_sample_k_noalloc,
     NptParams, System, NptReplica, rbe_npt_init, rbe_npt_step, RBE_CELL_DOUBLES,
     FlexParams, FlexSystem, FlexReplica, rbe_flex_init, rbe_flex_step, RBE_FLEX_CELL_DOUBLES,
-    FLEX_H, FLEX_PH, FLEX_W, FLEX_KT, FLEX_PT, FLEX_EK, FLEX_EC, FLEX_EL, FLEX_V, FLEX_HAM, FLEX_STEP, Server, ServerConfig, Request, piston_mass,
+    FLEX_H, FLEX_PH, FLEX_W, FLEX_KT, FLEX_PT, FLEX_EK, FLEX_EC, FLEX_EL, FLEX_V, FLEX_HAM, FLEX_STEP, FLEX_BUILDS, Server, ServerConfig, Request, piston_mass,
     piston_masses_rect, RBE_BAROSTAT_NONE, RBE_BAROSTAT_ISO, RBE_BAROSTAT_ANISO, RBE_BAROSTAT_SEMI, CELL_PC,
     CELL_WD, CELL_K2D, CELL_PD, Batch, BatchItem,
     rbe_set_seed, rbe_set_sampler, rbe_set_pressure_batch, rbe_set_sample_reuse, RBE_SAMPLER_EXACT, RBE_SAMPLER_OFFLINE, RBE_SAMPLER_MH,

@@ -59,7 +59,7 @@ class FlexParams(ctypes.Structure):
                 ("rc", ctypes.c_double), ("qqr2e", ctypes.c_double), ("lj_sigma", ctypes.c_double),
                 ("lj_eps", ctypes.c_double), ("max_disp", ctypes.c_double), ("chi", ctypes.c_double),
                 ("kspace", ctypes.c_int32), ("real", ctypes.c_int32), ("noise", ctypes.c_int32),
-                ("pad", ctypes.c_int32)]
+                ("pad", ctypes.c_int32), ("skin", ctypes.c_double)]
 
     def __init__(self, **kw):
         if "M" in kw and not isinstance(kw["M"], ctypes.Array):
@@ -77,7 +77,7 @@ class FlexSystem(ctypes.Structure):
 RBE_FLEX_CELL_DOUBLES = 64
 # slots of the flexible cell block (include/rbe.h)
 FLEX_H, FLEX_PH, FLEX_W, FLEX_KT, FLEX_PT = 0, 9, 18, 27, 36
-FLEX_EK, FLEX_EC, FLEX_EL, FLEX_V, FLEX_HAM, FLEX_STEP = 45, 46, 47, 48, 49, 50
+FLEX_EK, FLEX_EC, FLEX_EL, FLEX_V, FLEX_HAM, FLEX_STEP, FLEX_BUILDS = 45, 46, 47, 48, 49, 50, 51
 
 RBE_CELL_DOUBLES = 32
 RBE_BAROSTAT_NONE, RBE_BAROSTAT_ISO, RBE_BAROSTAT_ANISO, RBE_BAROSTAT_SEMI = 0, 1, 2, 3
@@ -398,13 +398,14 @@ class FlexReplica:
         rbe_flex_step(ctx.h, self.sys, nsteps)
 
     def state(self):
-        """dict of NumPy arrays: r, p, F, h, ph, W, Kt, Pt (3x3), Ek, Ec, El, V, H (synchronises)."""
+        """dict of NumPy arrays: r, p, F, h, ph, W, Kt, Pt (3x3), Ek, Ec, El, V, H, the step index and the
+        neighbour-list builds so far (synchronises)."""
         c = self.cell.cpu().numpy()
         m = lambda o: c[o:o + 9].reshape(3, 3).copy()  # noqa: E731
         return {"r": self.pos.cpu().numpy(), "p": self.mom.cpu().numpy(), "F": self.force.cpu().numpy(),
                 "h": m(FLEX_H), "ph": m(FLEX_PH), "W": m(FLEX_W), "Kt": m(FLEX_KT), "Pt": m(FLEX_PT),
                 "Ek": c[FLEX_EK], "Ec": c[FLEX_EC], "El": c[FLEX_EL], "V": c[FLEX_V], "H": c[FLEX_HAM],
-                "step": int(c[FLEX_STEP:FLEX_STEP + 1].view(np.int64)[0])}
+                "step": int(c[FLEX_STEP:FLEX_STEP + 1].view(np.int64)[0]), "builds": int(c[FLEX_BUILDS])}
 
 
 class Batch:

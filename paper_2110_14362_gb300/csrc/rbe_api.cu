@@ -206,6 +206,7 @@ rbe_status rbe_destroy(rbe_ctx ctx)
     if (ctx->gpos) cudaFree(ctx->gpos);
     if (ctx->flex_coef) cudaFree(ctx->flex_coef);
     if (ctx->gcell_dev) cudaFree(ctx->gcell_dev);
+    if (ctx->flex_nls) cudaFree(ctx->flex_nls);
     delete ctx;
     return RBE_OK;
 }

@@ -133,6 +133,7 @@ struct rbe_ctx_s {
     int64_t flex_ready_N = -1;       // N of the system rbe_flex_init prepared the scratch for
     void* flex_coef = nullptr;       // per-step coefficients of the flexible-cell step (rbe_flex.cu)
     void* gcell_dev = nullptr;       // general-cell quantities of the current cell (rbe_flex.cu)
+    void* flex_nls = nullptr;        // neighbour-list state of the flexible-cell step (rbe_flex.cu)
     bool timing = false;             // record CUDA events around each evaluation kernel
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     // pipelined host-buffer calls: a copy stream, its events, pinned outputs (virial, energy,

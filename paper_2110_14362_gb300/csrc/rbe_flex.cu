@@ -50,6 +50,30 @@ struct FlexCoef {
     int noise, pad;
 };
 
+constexpr int kFxBuilds = 51;  // neighbour-list builds so far (cell block)
+
+// Neighbour-list state of the flexible cell.  The list holds, for every slot of the cell order of
+// its build, the slots within rl = rc + skin by the minimum image at the build (rl <= w_j / 2, so
+// every other image of a pair is at least rl away too).  Since then the cell has deformed by
+// F = h h_ref^{-1} and every particle has moved by at most D (measured with the current h): an
+// unlisted pair is now at least sigma_min(F) rl - 2 D >= (1 - |F - I|_F) rl - 2 D apart, and the
+// list stands while that is at least rc.
+struct FlexNList {
+    NListState base;             // rl, rc, the displacement maximum and the rebuild flags (the
+                                 // cell-list kernels read base.rebuild)
+    double href[9], hrefinv[9];  // the cell at the last build and its inverse
+};
+
+struct FlexListArgs {
+    FlexNList* nl;
+    int* nbr;          // [slot * cap + k]
+    int* nnb;          // per slot
+    float4* sref;      // per slot: s at the build
+    unsigned* status;  // kStatusList on overflow
+    double* cell;      // the build count
+    int cap;
+};
+
 __device__ __forceinline__ uint64_t flex_step(const double* cell)
 {
     return (uint64_t)__double_as_longlong(cell[kFxStep]);
@@ -78,17 +102,22 @@ __device__ __forceinline__ double m_inv(double h, int a, int b, double& det)
     return num / det;
 }
 
-// max over lanes 0..8 of |v| (lanes 9..31 mirror lane 8)
-__device__ __forceinline__ double m_maxabs(double v)
-{
-    double m = fabs(v);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
-    return m;
-}
+// 1/k for k = 0..41 (entry 0 unused), rounded once by the compiler: the series below multiply by
+// them instead of dividing (an FP64 division is a long instruction sequence on this GPU).
+__constant__ double kInvK[42] = {
+    0.0,        1.0,        1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,  1.0 / 7,  1.0 / 8,  1.0 / 9,
+    1.0 / 10, 1.0 / 11, 1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15, 1.0 / 16, 1.0 / 17, 1.0 / 18, 1.0 / 19,
+    1.0 / 20, 1.0 / 21, 1.0 / 22, 1.0 / 23, 1.0 / 24, 1.0 / 25, 1.0 / 26, 1.0 / 27, 1.0 / 28, 1.0 / 29,
+    1.0 / 30, 1.0 / 31, 1.0 / 32, 1.0 / 33, 1.0 / 34, 1.0 / 35, 1.0 / 36, 1.0 / 37, 1.0 / 38, 1.0 / 39,
+    1.0 / 40, 1.0 / 41};
+
+// The biased exponent and leading mantissa bits of |v| (the high word without its sign): ordered
+// like |v| to within a factor of 2^(2^-20).
+__device__ __forceinline__ int m_mag(double v) { return __double2hiint(v) & 0x7fffffff; }
 
 // e^X and phi(X) = sum_k X^k / (k+1)! by their Taylor series, summed until the largest entry of
-// the term is below 1e-20 of the largest entry of the sum (at most 40 terms).
+// the term is 2^-67 (7e-21) or less of the largest entry of the sum (at most 40 terms).  The
+// comparison runs on the exponent bits (integer instructions).
 __device__ __forceinline__ void m_exp_phi(double x, int e, int a, int b, double& E, double& Phi)
 {
     double term = (e == 0 || e == 4 || e == 8) ? 1.0 : 0.0;
@@ -97,10 +126,11 @@ __device__ __forceinline__ void m_exp_phi(double x, int e, int a, int b, double&
     const double x0 = m_get(x, b), x1 = m_get(x, 3 + b), x2 = m_get(x, 6 + b);
     for (int k = 1; k <= 40; ++k) {
         const double t0 = m_get(term, 3 * a), t1 = m_get(term, 3 * a + 1), t2 = m_get(term, 3 * a + 2);
-        term = (t0 * x0 + t1 * x1 + t2 * x2) / (double)k;
+        term = (t0 * x0 + t1 * x1 + t2 * x2) * kInvK[k];
         E += term;
-        Phi += term / (double)(k + 1);
-        if (m_maxabs(term) < 1e-20 * m_maxabs(E)) break;  // the same on every lane
+        Phi += term * kInvK[k + 1];
+        const int mt = __reduce_max_sync(0xffffffffu, m_mag(term)), me = __reduce_max_sync(0xffffffffu, m_mag(E));
+        if (mt < me - (67 << 20)) break;  // the same on every lane
     }
 }
 
@@ -160,15 +190,15 @@ __device__ __forceinline__ double gen_cell_lanes(const double* h, double alpha, 
 // the dual lattice sum of S (warps 5..7).  Stage 3: the coefficients, the general cell, the
 // cell-list constants in the unit cube of s (n_j = floor(w_j / rc) cells along s_j, w_j =
 // 1/|row j of h^{-1}| the distance between the lattice planes, so that a pair within rc lies in
-// neighbouring cells).  With advance = 0 only the quantities of the current cell (the first
-// forces).  A cell that is not invertible, or whose dual sum would leave the prepared range, is
+// neighbouring cells; rcell = rc + skin with a neighbour list, whose build searches the cells
+// within rc + skin).  With advance = 0 only the quantities of the current cell (the first forces).  A cell that is not invertible, or whose dual sum would leave the prepared range, is
 // flagged (kStatusBox) and its step's results are not to be used.
 constexpr int kFlexCellWarps = 8;
 constexpr int kDualThreads = 3 * 32;  // warps 5..7
 
 __global__ void __launch_bounds__(kFlexCellWarps * 32)
 k_flex_cell(double* __restrict__ cell, FlexCoef* __restrict__ cf, GenCell* __restrict__ gc, CellConsts* __restrict__ cc,
-            const rbe_flex_params prm, double alpha, int P, uint64_t seed, int cellcap, int advance,
+            const rbe_flex_params prm, double alpha, int P, uint64_t seed, int cellcap, double rcell, int advance,
             unsigned* __restrict__ status)
 {
     __shared__ double sX[4][9], sE[4][9], sP[4][9];
@@ -181,24 +211,25 @@ k_flex_cell(double* __restrict__ cell, FlexCoef* __restrict__ cf, GenCell* __res
     const int e = lane < 9 ? lane : 8, ea = e / 3, eb = e % 3;
     const uint64_t step = flex_step(cell);
     const double t = 0.5 * prm.dt;
-    if (lane == 0) {
-        if (warp == 1) {
-            double z0[4] = {0.0, 0.0, 0.0, 0.0}, z1[4] = {0.0, 0.0, 0.0, 0.0}, z2[4] = {0.0, 0.0, 0.0, 0.0};
-            if (advance && prm.noise) {
-                npt_normals(seed, 2u, step, 0u, z0);
-                npt_normals(seed, 2u, step, 1u, z1);
-                npt_normals(seed, 2u, step, 2u, z2);
-            }
-            // diagonal entries 0, 4, 8 take z0[0..2] (the rectangular cell's slots); the
-            // off-diagonal entries 1, 2, 3, 5, 6, 7 take z1[0..3], z2[0..1]
-            sz[0] = z0[0]; sz[1] = z1[0]; sz[2] = z1[1]; sz[3] = z1[2]; sz[4] = z0[1];
-            sz[5] = z1[3]; sz[6] = z2[0]; sz[7] = z2[1]; sz[8] = z0[2];
-            sg[0] = exp(-prm.gamma_h * prm.dt);
-        } else if (warp == 2) {
-            const double g = exp(-prm.gamma * prm.dt);
-            sg[1] = g;
-            sg[2] = sqrt(prm.kT * kFConv * (1.0 - g * g));
+    if (warp == 1 && lane < 3) {
+        // the cell normals of counter indices 0, 1, 2 on three lanes: the diagonal entries 0, 4, 8
+        // take index 0's z[0..2] (the rectangular cell's slots); the off-diagonal entries
+        // 1, 2, 3, 5, 6, 7 take index 1's z[0..3] and index 2's z[0..1]
+        double z[4] = {0.0, 0.0, 0.0, 0.0};
+        if (advance && prm.noise) npt_normals(seed, 2u, step, (uint32_t)lane, z);
+        if (lane == 0) {
+            sz[0] = z[0]; sz[4] = z[1]; sz[8] = z[2];
+        } else if (lane == 1) {
+            sz[1] = z[0]; sz[2] = z[1]; sz[3] = z[2]; sz[5] = z[3];
+        } else {
+            sz[6] = z[0]; sz[7] = z[1];
         }
+    } else if (warp == 2 && lane == 0) {
+        sg[0] = exp(-prm.gamma_h * prm.dt);
+    } else if (warp == 3 && lane == 0) {
+        const double g = exp(-prm.gamma * prm.dt);
+        sg[1] = g;
+        sg[2] = sqrt(prm.kT * kFConv * (1.0 - g * g));
     }
     __syncthreads();
     if (warp == 0) {
@@ -292,7 +323,8 @@ k_flex_cell(double* __restrict__ cell, FlexCoef* __restrict__ cf, GenCell* __res
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
         if (lane == 0) {
-            const double S = pow(alpha / kPi, 1.5) * sgc.V * v - 1.0;
+            const double ap = alpha / kPi;
+            const double S = ap * sqrt(ap) * sgc.V * v - 1.0;
             sgc.S = S;
             sgc.wP = S / (double)(P > 0 ? P : 1);
             if (!(S > 0.0) || !isfinite(S)) atomicOr(status, kStatusBox);
@@ -305,9 +337,9 @@ k_flex_cell(double* __restrict__ cell, FlexCoef* __restrict__ cf, GenCell* __res
         cc->invL[lane] = 1.0;
         cc->Lf[lane] = 1.0f;
         cc->invLf[lane] = 1.0f;
-        const int n = cell_dim(w, prm.rc);
+        const int n = cell_dim(w, rcell);
         cc->nc[lane] = n;
-        const bool okw = 2.0 * prm.rc <= w;
+        const bool okw = 2.0 * rcell <= w;
         const unsigned m = __ballot_sync(0x7u, okw);
         const int n0 = __shfl_sync(0x7u, n, 0), n1 = __shfl_sync(0x7u, n, 1), n2 = __shfl_sync(0x7u, n, 2);
         if (lane == 0) {
@@ -456,6 +488,97 @@ k_flex_kvirial(int P, const int4* __restrict__ m, const double2* __restrict__ rh
     gen_virial_block(P, m, rho, g, alpha, W_out, status);
 }
 
+// Per step with a neighbour list, before the cell list: the scaled positions and charges packed
+// in the list's slot order, the largest displacement since the build (minimum image in s, length
+// with the current h, FP32), and on the last block the rebuild decision.  Until the first build
+// there is no slot order: the kernel then only asks for a build.
+template <bool kF64>
+__global__ void __launch_bounds__(kNptThreads)
+k_flex_nl_check(int64_t N, const double* __restrict__ sbuf, const double* __restrict__ q,
+                const int* __restrict__ sorted, float4* __restrict__ spos32, double4_32a* __restrict__ spos64,
+                const float4* __restrict__ sref, const FlexCoef* __restrict__ cf, FlexNList* __restrict__ nl)
+{
+    __shared__ float smax[kNptThreads / 32];
+    __shared__ bool last;
+    const bool force = nl->base.force != 0;
+    float d2max = 0.f;
+    if (!force) {
+        float h[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) h[a] = (float)cf->h[a];
+        for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < N; u += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t i = sorted[u];
+            const double x = sbuf[3 * i], y = sbuf[3 * i + 1], z = sbuf[3 * i + 2], qq = q[i];
+            spos32[u] = make_float4((float)x, (float)y, (float)z, (float)qq);
+            if (kF64) {
+                double4_32a v;
+                v.x = x;
+                v.y = y;
+                v.z = z;
+                v.w = qq;
+                spos64[u] = v;
+            }
+            const float4 r0 = sref[u];
+            float a = (float)x - r0.x, b = (float)y - r0.y, c = (float)z - r0.z;
+            a -= rintf(a);
+            b -= rintf(b);
+            c -= rintf(c);
+            const float dx = h[0] * a + h[1] * b + h[2] * c, dy = h[3] * a + h[4] * b + h[5] * c,
+                        dz = h[6] * a + h[7] * b + h[8] * c;
+            const float d2 = dx * dx + dy * dy + dz * dz;
+            d2max = d2 > d2max ? d2 : d2max;  // NaN compares false: caught by the cell checks
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) d2max = fmaxf(d2max, __shfl_xor_sync(0xffffffffu, d2max, off));
+    if (lane == 0) smax[warp] = d2max;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < kNptThreads / 32; ++w) m = fmaxf(m, smax[w]);
+        atomicMax(&nl->base.maxd2, __float_as_uint(m));
+        __threadfence();
+        last = atomicAdd(&nl->base.counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || warp != 0) return;
+    __threadfence();
+    // warp 0 of the last block: F = h h_ref^{-1} one entry per lane, |F - I|_F by a shuffle sum
+    const int e = lane < 9 ? lane : 8, ea = e / 3, eb = e % 3;
+    const double F = m_mul(cf->h[e], nl->hrefinv[e], ea, eb);
+    double d = lane < 9 ? F - (ea == eb ? 1.0 : 0.0) : 0.0;
+    d *= d;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+    if (lane == 0) {
+        const double D = sqrt((double)__uint_as_float(atomicAdd(&nl->base.maxd2, 0u)));
+        const double f = 1.0 - sqrt(d);
+        // a margin of 1e-3 A covers the FP32 rounding of the displacements
+        const bool stands = !force && f * ((double)nl->base.rl) - 2.0 * D - 1e-3 >= (double)nl->base.rc;
+        nl->base.rebuild = stands ? 0 : 1;
+        nl->base.maxd2 = 0u;
+        nl->base.counter = 0u;
+    }
+}
+
+__global__ void k_flex_nl_init(FlexNList* __restrict__ nl, float rl, float rc, double* __restrict__ cell)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int a = 0; a < 3; ++a) nl->base.Lref[a] = 1.0;
+    nl->base.rl = rl;
+    nl->base.rc = rc;
+    nl->base.maxd2 = 0u;
+    nl->base.counter = 0u;
+    nl->base.rebuild = 1;
+    nl->base.force = 1;
+    for (int a = 0; a < 9; ++a) {
+        nl->href[a] = (a % 4 == 0) ? 1.0 : 0.0;
+        nl->hrefinv[a] = (a % 4 == 0) ? 1.0 : 0.0;
+    }
+    cell[kFxBuilds] = 0.0;
+}
+
 // ---------------------------------------------------------------------------------
 // Real space in the general cell (Sec. 4.1 Eqs. (U2), (force)): one warp per particle in cell
 // order, the 3 x 3 rows of neighbouring cells of the cell list in s (the cells cx-1..cx+1 of a
@@ -470,13 +593,17 @@ k_flex_kvirial(int P, const int4* __restrict__ m, const double2* __restrict__ rh
 // at slots 0..7.  A cell beyond the cell arrays (flagged by k_cl_count) leaves F_r = 0.
 constexpr int kFlexHitCap = 64;  // < 32 buffered + 32 new
 
-template <bool kF64>
+// Modes as the rectangular kernel's: search the cells and evaluate, search the cells within
+// rc + skin and write the list (rebuild steps only), evaluate the listed pairs.
+template <bool kF64, int kMode>
 __global__ void __launch_bounds__(kPairWarps * 32, kF64 ? kPairBlocksPerSM64 : 3)
 k_flex_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, const FlexCoef* __restrict__ cf,
             const int* __restrict__ cid, const int* __restrict__ cnt, const int* __restrict__ start,
             const int* __restrict__ sorted, const float4* __restrict__ spos32, const double4_32a* __restrict__ spos64,
-            double* __restrict__ Fr, double* __restrict__ partials)
+            double* __restrict__ Fr, double* __restrict__ partials, const FlexListArgs la)
 {
+    constexpr bool kBuild = kMode == 1, kList = kMode == 2;
+    if (kBuild && !la.nl->base.rebuild) return;  // the list stands (the same for every thread)
     using R = typename std::conditional<kF64, double, float>::type;
     struct Hit {
         R x, y, z, q;
@@ -491,9 +618,13 @@ k_flex_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, co
     double ws[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, ecsum = 0.0, elsum = 0.0;  // FP64 path
     float wh[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, wl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // FP32 path
     float ech = 0.f, ecl = 0.f, elh = 0.f, ell = 0.f;
-    if (cc->ncell < 0) {
-        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < 3 * N; j += (int64_t)gridDim.x * blockDim.x)
-            Fr[j] = 0.0;
+    // no cell list this step (a cell beyond the cell arrays, flagged), or no list built yet
+    const bool cells_ok = kList ? la.nl->base.force == 0 : cc->ncell >= 0;
+    if (!cells_ok) {
+        if (!kBuild)
+            for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < 3 * N;
+                 j += (int64_t)gridDim.x * blockDim.x)
+                Fr[j] = 0.0;
     } else {
         R h[9];
 #pragma unroll
@@ -507,6 +638,9 @@ k_flex_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, co
             qk = pc.qkf, s2 = pc.s2f, e4 = pc.e4f, e24 = pc.e24f;
         }
         const bool lj = pc.lj != 0;
+        // the build keeps every candidate within rl plus a margin above the rounding of a
+        // distance (a superset is harmless)
+        const R search2 = kBuild ? (R)((double)la.nl->base.rl * (double)la.nl->base.rl * (1.0 + 1e-5)) : rc2;
         const int nwarps = gridDim.x * kPairWarps;
         for (int u = blockIdx.x * kPairWarps + wib; u < (int)N; u += nwarps) {
             const int i = sorted[u];
@@ -520,7 +654,7 @@ k_flex_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, co
             }
             // segment of this lane: row r = lane / 2 of the 3 x 3 rows, part lane % 2
             int lo = 0, hi = 0;
-            {
+            if (!kList) {
                 const int c = cid[i];
                 const int cxy = nc[0] * nc[1];
                 const int cz = c / cxy, cy = (c - cz * cxy) / nc[0], cx = c - cz * cxy - cy * nc[0];
@@ -590,41 +724,69 @@ k_flex_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, co
                 w[4] += f * dx * dz;
                 w[5] += f * dy * dz;
             };
-            for (int g = 0; g < 18; ++g) {
-                const int glo = __shfl_sync(0xffffffffu, lo, g), ghi = __shfl_sync(0xffffffffu, hi, g);
-                for (int s0 = glo; s0 < ghi; s0 += 32) {  // the same trip count on every lane
-                    const int sl = s0 + lane;
-                    const bool valid = sl < ghi && sl != u;
-                    const int sj = sl < ghi ? sl : glo;
-                    R ds[3], qj;
-                    if constexpr (kF64) {
-                        const double4_32a o = spos64[sj];
-                        ds[0] = o.x - si[0], ds[1] = o.y - si[1], ds[2] = o.z - si[2], qj = o.w;
-                    } else {
-                        const float4 o = spos32[sj];
-                        ds[0] = o.x - si[0], ds[1] = o.y - si[1], ds[2] = o.z - si[2], qj = o.w;
-                    }
+            // one candidate slot sj per lane (valid: a candidate at all): its separation by the
+            // minimum image in s; hits go to the buffer (build: to the list)
+            auto consider = [&](bool valid, int sj) {
+                R ds[3], qj;
+                if constexpr (kF64) {
+                    const double4_32a o = spos64[sj];
+                    ds[0] = o.x - si[0], ds[1] = o.y - si[1], ds[2] = o.z - si[2], qj = o.w;
+                } else {
+                    const float4 o = spos32[sj];
+                    ds[0] = o.x - si[0], ds[1] = o.y - si[1], ds[2] = o.z - si[2], qj = o.w;
+                }
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) ds[a] -= rint(ds[a]);
-                    const R dx = h[0] * ds[0] + h[1] * ds[1] + h[2] * ds[2];
-                    const R dy = h[3] * ds[0] + h[4] * ds[1] + h[5] * ds[2];
-                    const R dz = h[6] * ds[0] + h[7] * ds[1] + h[8] * ds[2];
-                    const bool hit = valid && dx * dx + dy * dy + dz * dz < rc2;
-                    const unsigned m = __ballot_sync(0xffffffffu, hit);
+                for (int a = 0; a < 3; ++a) ds[a] -= rint(ds[a]);
+                const R dx = h[0] * ds[0] + h[1] * ds[1] + h[2] * ds[2];
+                const R dy = h[3] * ds[0] + h[4] * ds[1] + h[5] * ds[2];
+                const R dz = h[6] * ds[0] + h[7] * ds[1] + h[8] * ds[2];
+                const bool hit = valid && dx * dx + dy * dy + dz * dz < search2;
+                const unsigned m = __ballot_sync(0xffffffffu, hit);
+                if constexpr (kBuild) {
                     if (hit) {
-                        const int slot = nh + __popc(m & ((1u << lane) - 1u));
-                        hits[wib][slot] = Hit{dx, dy, dz, qj};
+                        const int p = nh + __popc(m & ((1u << lane) - 1u));
+                        if (p < la.cap) la.nbr[(int64_t)u * la.cap + p] = sj;
                     }
                     nh += __popc(m);
-                    if (nh >= 32) {
-                        __syncwarp();
-                        evaluate(32);
-                        __syncwarp();
-                        if (lane < nh - 32) hits[wib][lane] = hits[wib][32 + lane];
-                        __syncwarp();
-                        nh -= 32;
+                    return;
+                }
+                if (hit) {
+                    const int slot = nh + __popc(m & ((1u << lane) - 1u));
+                    hits[wib][slot] = Hit{dx, dy, dz, qj};
+                }
+                nh += __popc(m);
+                if (nh >= 32) {
+                    __syncwarp();
+                    evaluate(32);
+                    __syncwarp();
+                    if (lane < nh - 32) hits[wib][lane] = hits[wib][32 + lane];
+                    __syncwarp();
+                    nh -= 32;
+                }
+            };
+            if constexpr (kList) {
+                const int nn = la.nnb[u];
+                const int* row = la.nbr + (int64_t)u * la.cap;
+                for (int k0 = 0; k0 < nn; k0 += 32) {  // the same trip count on every lane
+                    const int k = k0 + lane;
+                    consider(k < nn, row[k < nn ? k : nn - 1]);
+                }
+            } else {
+                for (int g = 0; g < 18; ++g) {
+                    const int glo = __shfl_sync(0xffffffffu, lo, g), ghi = __shfl_sync(0xffffffffu, hi, g);
+                    for (int s0 = glo; s0 < ghi; s0 += 32) {  // the same trip count on every lane
+                        const int sl = s0 + lane;
+                        consider(sl < ghi && sl != u, sl < ghi ? sl : glo);
                     }
                 }
+            }
+            if constexpr (kBuild) {
+                if (lane == 0) {
+                    la.nnb[u] = nh < la.cap ? nh : la.cap;
+                    la.sref[u] = make_float4((float)si[0], (float)si[1], (float)si[2], 0.f);
+                    if (nh > la.cap) atomicOr(la.status, kStatusList);
+                }
+                continue;
             }
             __syncwarp();
             evaluate(nh);
@@ -660,6 +822,20 @@ k_flex_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, co
                 }
             }
         }
+    }
+    if constexpr (kBuild) {
+        // the build's cell; the list now stands until a check says otherwise (a build without a
+        // cell list leaves the list pending)
+        if (cells_ok && blockIdx.x == 0) {
+            if (threadIdx.x < 9) {
+                la.nl->href[threadIdx.x] = cf->h[threadIdx.x];
+                la.nl->hrefinv[threadIdx.x] = cf->hinv[threadIdx.x];
+            } else if (threadIdx.x == 32) {
+                la.nl->base.force = 0;
+                la.cell[kFxBuilds] += 1.0;
+            }
+        }
+        return;
     }
     if (lane == 0) {
         if (!kF64) {
@@ -829,7 +1005,8 @@ static rbe_status flex_validate(rbe_ctx ctx, const rbe_flex_system* sys)
     if (!(p.dt > 0.0) || !std::isfinite(p.dt) || !(p.kT >= 0.0) || !std::isfinite(p.kT) || !(p.gamma >= 0.0) ||
         !std::isfinite(p.gamma) || !(p.gamma_h >= 0.0) || !std::isfinite(p.gamma_h) || !std::isfinite(p.P_ext) ||
         !(p.rc > 0.0) || !std::isfinite(p.rc) || !(p.max_disp >= 0.0) || !std::isfinite(p.chi) ||
-        !std::isfinite(p.qqr2e) || !std::isfinite(p.lj_sigma) || !std::isfinite(p.lj_eps))
+        !std::isfinite(p.qqr2e) || !std::isfinite(p.lj_sigma) || !std::isfinite(p.lj_eps) || !(p.skin >= 0.0) ||
+        !std::isfinite(p.skin))
         return fail(ctx, RBE_EINVAL, "invalid flexible-cell parameters");
     for (int a = 0; a < 9; ++a)
         if (!(p.M[a] > 0.0) || !std::isfinite(p.M[a])) return fail(ctx, RBE_EINVAL, "cell masses must be positive and finite");
@@ -891,15 +1068,45 @@ static rbe_status flex_forces(rbe_ctx ctx, rbe_flex_system* sys, int do_kick)
     }
     if (prm.real) {
         if (fp64 && b.n64 < N) return fail(ctx, RBE_ESTATE, "precision changed to FP64 after rbe_flex_init: call it again");
-        if ((st = launch_cell_list(ctx, N, ctx->gpos, sys->charge, nullptr, fp64)) != RBE_OK) return st;
+        const bool list = prm.skin > 0.0;
+        FlexNList* nl = static_cast<FlexNList*>(ctx->flex_nls);
+        if (list && (!nl || b.ncap_list < N)) return fail(ctx, RBE_ESTATE, "skin changed after rbe_flex_init: call it again");
+        double4_32a* s64 = fp64 ? b.spos64 : nullptr;
+        if (list) {
+            const int grid = (int)std::min<int64_t>(nb, (int64_t)ctx->num_sms * 4);
+            if (fp64)
+                k_flex_nl_check<true><<<grid, kNptThreads, 0, s>>>(N, ctx->gpos, sys->charge, b.sorted, b.spos32, s64,
+                                                                 b.sref, cf, nl);
+            else
+                k_flex_nl_check<false><<<grid, kNptThreads, 0, s>>>(N, ctx->gpos, sys->charge, b.sorted, b.spos32,
+                                                                  nullptr, b.sref, cf, nl);
+        }
+        if ((st = launch_cell_list(ctx, N, ctx->gpos, sys->charge, list ? &nl->base : nullptr, fp64)) != RBE_OK)
+            return st;
         const PairConst pc = make_pair_const(prm.rc, ctx->alpha, prm.qqr2e, prm.lj_sigma, prm.lj_eps);
         const CellConsts* cc = static_cast<const CellConsts*>(b.cellc);
-        if (fp64)
-            k_flex_pair<true><<<nbp, kPairWarps * 32, 0, s>>>(N, cc, pc, cf, b.cid, b.cnt, b.start, b.sorted, b.spos32,
-                                                            b.spos64, b.Fr, b.partials);
-        else
-            k_flex_pair<false><<<nbp, kPairWarps * 32, 0, s>>>(N, cc, pc, cf, b.cid, b.cnt, b.start, b.sorted, b.spos32,
-                                                             nullptr, b.Fr, b.partials);
+        const FlexListArgs la{nl, b.nbr, b.nnb, b.sref, ctx->d.status, sys->cell, b.nbr_cap};
+        auto pair = [&](auto f64_tag, auto mode_tag) {
+            constexpr bool F64 = decltype(f64_tag)::value;
+            constexpr int MODE = decltype(mode_tag)::value;
+            k_flex_pair<F64, MODE><<<nbp, kPairWarps * 32, 0, s>>>(N, cc, pc, cf, b.cid, b.cnt, b.start, b.sorted,
+                                                                   b.spos32, s64, b.Fr, b.partials, la);
+        };
+        using T = std::true_type;
+        using F = std::false_type;
+        using Cells = std::integral_constant<int, 0>;
+        using Build = std::integral_constant<int, 1>;
+        using List = std::integral_constant<int, 2>;
+        if (!list) {
+            if (fp64) pair(T{}, Cells{});
+            else pair(F{}, Cells{});
+        } else if (fp64) {
+            pair(T{}, Build{});
+            pair(T{}, List{});
+        } else {
+            pair(F{}, Build{});
+            pair(F{}, List{});
+        }
         if ((st = flex_check(ctx, "k_flex_pair")) != RBE_OK) return st;
     }
     k_flex_finish<<<std::max(1, nb), kNptThreads, 0, s>>>(N, sys->mom, sys->force, b.mprop, b.Fk, b.Fr, b.WEk, cf,
@@ -912,8 +1119,8 @@ static rbe_status flex_cell_launch(rbe_ctx ctx, rbe_flex_system* sys, int advanc
 {
     k_flex_cell<<<1, kFlexCellWarps * 32, 0, ctx->stream>>>(
         sys->cell, static_cast<FlexCoef*>(ctx->flex_coef), static_cast<GenCell*>(ctx->gcell_dev),
-        static_cast<CellConsts*>(ctx->npt.cellc), sys->params, ctx->alpha, ctx->P, ctx->seed, ctx->npt.cellcap, advance,
-        ctx->d.status);
+        static_cast<CellConsts*>(ctx->npt.cellc), sys->params, ctx->alpha, ctx->P, ctx->seed, ctx->npt.cellcap,
+        sys->params.rc + sys->params.skin, advance, ctx->d.status);
     return flex_check(ctx, "k_flex_cell");
 }
 
@@ -930,10 +1137,16 @@ rbe_status flex_init(rbe_ctx ctx, rbe_flex_system* sys, uint64_t batch)
     if (!flex_cell_geometry(h, len, width)) return fail(ctx, RBE_EINVAL, "the cell must be finite with det h > 0");
     if (prm.real)
         for (int j = 0; j < 3; ++j)
-            if (width[j] < 2.0 * prm.rc)
-                return fail(ctx, RBE_EINVAL, "real space needs rc <= w/2 for every width of the cell");
-    // scratch of the rectangular step, its cell list sized for widths up to twice the initial
-    if ((st = npt_ensure(ctx, sys->N, width, prm.rc, 0.0)) != RBE_OK) return st;
+            if (width[j] < 2.0 * (prm.rc + prm.skin))
+                return fail(ctx, RBE_EINVAL, "real space needs rc + skin <= w/2 for every width of the cell");
+    // scratch of the rectangular step, its cell list sized for widths up to twice the initial (and
+    // with skin > 0 the neighbour list, sized by the density N / (w_0 w_1 w_2) >= N / V)
+    if ((st = npt_ensure(ctx, sys->N, width, prm.rc, prm.skin)) != RBE_OK) return st;
+    if (prm.skin > 0.0 && !ctx->flex_nls) {
+        FlexNList* nl = nullptr;
+        if ((e = ctx_alloc(ctx, &nl, sizeof(FlexNList))) != cudaSuccess) return cuda_fail(ctx, e, "flexible-cell list state");
+        ctx->flex_nls = nl;
+    }
     // proposal tables for lengths up to sqrt(3) x twice the initial cell vectors, and the unit cube
     int need = 2 * host_axis_M(ctx->alpha, 1.0) + 1;
     for (int j = 0; j < 3; ++j) {
@@ -977,6 +1190,9 @@ rbe_status flex_init(rbe_ctx ctx, rbe_flex_system* sys, uint64_t batch)
     const int nb = (int)((sys->N + kNptThreads - 1) / kNptThreads);
     k_flex_mass<<<nb, kNptThreads, 0, ctx->stream>>>(sys->N, sys->mass, b.mprop);
     k_flex_set_step<<<1, 32, 0, ctx->stream>>>(sys->cell, batch);
+    if (prm.skin > 0.0)
+        k_flex_nl_init<<<1, 32, 0, ctx->stream>>>(static_cast<FlexNList*>(ctx->flex_nls), (float)(prm.rc + prm.skin),
+                                                  (float)prm.rc, sys->cell);
     if ((st = flex_check(ctx, "k_flex_set_step")) != RBE_OK) return st;
     if ((st = flex_cell_launch(ctx, sys, 0)) != RBE_OK) return st;
     k_flex_scale<<<nb, kNptThreads, 0, ctx->stream>>>(sys->N, sys->pos, static_cast<const FlexCoef*>(ctx->flex_coef),

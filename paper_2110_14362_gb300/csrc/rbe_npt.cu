@@ -103,19 +103,6 @@ __global__ void k_cell_consts(const double* __restrict__ cell, double rc, double
     write_cell_consts(threadIdx.x, cell, rc, rcell, cellcap, cc);
 }
 
-// Neighbour-list state of a replica.  The list holds, for every slot of the cell order of its
-// build, the slots within rl = rc + skin (by the nearest image) at the build.  With D the
-// largest displacement since then (in units of the build's box) and f the smallest ratio of
-// the box edges to the build's, every unlisted pair is now at least f (rl - 2 D) apart: the
-// list stands while that is at least rc.
-struct NListState {
-    double Lref[3];    // box at the last build
-    float rl, rc;
-    unsigned maxd2;    // bits of the largest squared displacement of this step (non-negative float)
-    unsigned counter;  // last-block counter of the check
-    int rebuild;       // 1: this step rebuilds the list
-    int force;         // 1: build at the next step (set by rbe_npt_init)
-};
 
 // Per step, before the cell list: refresh the packed positions in the list's slot order and
 // decide whether the list must be rebuilt.  Until the first build there is no slot order:

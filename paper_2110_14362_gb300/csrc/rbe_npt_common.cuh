@@ -124,4 +124,18 @@ static inline PairConst make_pair_const(double rc, double alpha, double qqr2e, d
     return c;
 }
 
+// Neighbour-list state of a replica.  The list holds, for every slot of the cell order of its
+// build, the slots within rl = rc + skin (by the nearest image) at the build.  With D the
+// largest displacement since then (in units of the build's box) and f the smallest ratio of
+// the box edges to the build's, every unlisted pair is now at least f (rl - 2 D) apart: the
+// list stands while that is at least rc.
+struct NListState {
+    double Lref[3];    // box at the last build
+    float rl, rc;
+    unsigned maxd2;    // bits of the largest squared displacement of this step (non-negative float)
+    unsigned counter;  // last-block counter of the check
+    int rebuild;       // 1: this step rebuilds the list
+    int force;         // 1: build at the next step (set by rbe_npt_init)
+};
+
 }  // namespace rbe

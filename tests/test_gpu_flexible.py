@@ -50,7 +50,8 @@ def _params(h, rc, **kw):
     base = dict(dt=0.001, kT=KT, P_ext=oracle.BAR, gamma=10.0, gamma_h=2.0, M=M, rc=rc, qqr2e=QQ, lj_sigma=2.0,
                 lj_eps=0.5, max_disp=0.05, chi=2.0, kspace=1, real=1, noise=1)
     base.update(kw)
-    dev = rbe.FlexParams(**base)
+    skin = base.pop("skin", 0.0)
+    dev = rbe.FlexParams(skin=skin, **base)
     orc = oracle.flex_params(alpha=ALPHA, P=P, seed=SEED, **base)
     rates = np.array([[0.4, 0.3, -0.2], [-0.25, -0.3, 0.2], [0.15, -0.1, 0.2]])  # dh/dt, A/ps
     return dev, orc, np.asarray(M) * rates
@@ -92,8 +93,10 @@ CASES = [  # (lattice counts, tilts xy, xz, yz, rc): 2 to 4 cells per axis of th
 
 
 @pytest.mark.parametrize("counts,tilt,rc", CASES)
-def test_flex_fp64_parity(counts, tilt, rc):
-    got, st, E = _run_both(counts, tilt, rc, 4, rbe.RBE_FP64)
+@pytest.mark.parametrize("skin", [0.0, 1.0])
+def test_flex_fp64_parity(counts, tilt, rc, skin):
+    got, st, E = _run_both(counts, tilt, rc, 4, rbe.RBE_FP64, skin=skin)
+    assert got["builds"] == (1 if skin > 0 else 0)
     assert np.abs(got["h"] - st.h).max() < 1e-12 * np.abs(st.h).max(), (got["h"], st.h)
     assert np.abs(np.tril(got["h"], -1) - np.tril(st.h, -1)).max() < 1e-12 * np.abs(st.h).max()
     assert _mi_dist(got["r"], st.r, st.h) < 1e-10 * np.abs(st.h).max()
@@ -126,12 +129,13 @@ def test_flex_fp64_components(kw):
     assert np.abs(got["W"] - st.W).max() < 1e-10 * np.abs(st.W).max()
 
 
-def test_flex_fp32_phase_parity():
+@pytest.mark.parametrize("skin", [0.0, 1.0])
+def test_flex_fp32_phase_parity(skin):
     """FP32 real space and FP32-phase k-space: forces and momenta to 1e-5 relative RMS, the virial
     to 1e-5 of its largest entry, the cell momenta to 1e-5 of the scale of their kicks (the force
     on p^h is a small difference of Kt + W and P V) and the cell to what that moves it."""
     nsteps, dt = 4, 0.001
-    got, st, E = _run_both((10, 9, 11), (0.2, -0.1, 0.15), 6.0, nsteps, rbe.RBE_FP32_PHASE)
+    got, st, E = _run_both((10, 9, 11), (0.2, -0.1, 0.15), 6.0, nsteps, rbe.RBE_FP32_PHASE, skin=skin)
     assert _rel(got["F"], st.F) < 1e-5
     assert _rel(got["p"], st.p) < 1e-5
     assert np.abs(got["W"] - st.W).max() < 1e-5 * np.abs(st.W).max()
@@ -142,6 +146,32 @@ def test_flex_fp32_phase_parity():
     assert np.abs(got["ph"] - st.ph).max() < 1e-5 * kick
     M = _masses(_system((10, 9, 11), (0.2, -0.1, 0.15))[4])
     assert np.abs(got["h"] - st.h).max() < 1e-5 * kick * nsteps * dt / M.min() + 1e-12 * np.abs(st.h).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_neighbour_list_rebuilds_and_matches_the_cell_search(precision):
+    """200 steps of a cell deforming at several A/ps with a thin skin: the list is rebuilt many
+    times (displacements and the deformation h h_ref^{-1} both count), and the trajectory is the
+    cell search's to rounding."""
+    prec = rbe.RBE_FP64 if precision == "fp64" else rbe.RBE_FP32_PHASE
+    pos, mom, q, m, h = _system((8, 8, 9), (0.2, -0.15, 0.1))
+    dev = cuda_device()
+    out = []
+    for skin in (0.0, 0.4):
+        prm, _, ph = _params(h, 6.0, skin=skin)
+        with rbe.Context(np.diag(h), ALPHA, P, SEED, prec) as ctx:
+            rep = rbe.FlexReplica(pos, mom, q, m, h, prm, dev, step=0, ph=ph * 4.0)
+            rep.init(ctx, batch=0)
+            rep.step(ctx, 200)
+            ctx.sync()
+            out.append(rep.state())
+    a, b = out
+    assert a["builds"] == 0 and b["builds"] >= 5, b["builds"]
+    assert np.abs(b["h"] - h).max() > 0.2  # the cell moved by more than the skin
+    tol = 1e-8 if precision == "fp64" else 2e-3
+    assert np.abs(a["h"] - b["h"]).max() < tol * np.abs(a["h"]).max()
+    assert _rel(b["p"], a["p"]) < tol
+    assert _rel(b["F"], a["F"]) < tol * 10
 
 
 def test_frozen_shear_without_chi_is_the_rectangular_device_step():
@@ -195,6 +225,7 @@ def test_flex_energy_conservation_on_device():
     ph = np.array([[2.0, 1.0, -1.5], [1.2, -2.0, 1.0], [-1.0, 1.5, 1.8]])
     kw = dict(dt=0.001, kT=KT, P_ext=oracle.BAR, gamma=0.0, gamma_h=0.0, M=np.full((3, 3), 5.0), rc=6.2,
               qqr2e=oracle.QQR2E, lj_sigma=2.0, lj_eps=0.5, max_disp=0.0, chi=2.0, kspace=0, real=1, noise=0)
+    # (the widths of this 16 A cell leave no room for a skin: rc already fills half of them)
     dev = cuda_device()
     Hd = []
     with rbe.Context(np.diag(h), ALPHA, P, SEED, rbe.RBE_FP64) as ctx:
