@@ -207,6 +207,9 @@ rbe_status rbe_destroy(rbe_ctx ctx)
     if (ctx->flex_coef) cudaFree(ctx->flex_coef);
     if (ctx->gcell_dev) cudaFree(ctx->gcell_dev);
     if (ctx->flex_nls) cudaFree(ctx->flex_nls);
+    if (ctx->flex_cpos32) cudaFree(ctx->flex_cpos32);
+    if (ctx->flex_cpos64) cudaFree(ctx->flex_cpos64);
+    if (ctx->flex_code) cudaFree(ctx->flex_code);
     delete ctx;
     return RBE_OK;
 }

@@ -134,6 +134,10 @@ struct rbe_ctx_s {
     void* flex_coef = nullptr;       // per-step coefficients of the flexible-cell step (rbe_flex.cu)
     void* gcell_dev = nullptr;       // general-cell quantities of the current cell (rbe_flex.cu)
     void* flex_nls = nullptr;        // neighbour-list state of the flexible-cell step (rbe_flex.cu)
+    float4* flex_cpos32 = nullptr;   // flexible cell with a list: unwrapped Cartesian positions per slot
+    double4_32a* flex_cpos64 = nullptr;  // the same in FP64 (FP64 path)
+    unsigned char* flex_code = nullptr;  // image of each list entry at the build
+    int64_t flex_cpos_cap = 0, flex_cpos64_cap = 0, flex_code_cap = 0;
     bool timing = false;             // record CUDA events around each evaluation kernel
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     // pipelined host-buffer calls: a copy stream, its events, pinned outputs (virial, energy,

@@ -64,15 +64,26 @@ struct FlexNList {
     double href[9], hrefinv[9];  // the cell at the last build and its inverse
 };
 
+// The listed pairs are evaluated in Cartesian coordinates: each particle's unwrapped position
+// r_u = h (s + n_wrap) (n_wrap: the lattice vector its s has wrapped by since the build) and, per
+// list entry, the image n of the pair at the build (a byte, (n_x + 1) + 3 (n_y + 1) + 9 (n_z + 1)),
+// so that the separation is r_u,j - r_u,i + h n with the current h.  Every other image of a listed
+// pair was at least rl away at the build, so the bound above keeps it beyond rc as well.
 struct FlexListArgs {
     FlexNList* nl;
-    int* nbr;          // [slot * cap + k]
-    int* nnb;          // per slot
-    float4* sref;      // per slot: s at the build
-    unsigned* status;  // kStatusList on overflow
-    double* cell;      // the build count
+    int* nbr;              // [slot * cap + k]
+    unsigned char* code;   // [slot * cap + k]: image of the entry at the build
+    int* nnb;              // per slot
+    float4* sref;          // per slot: s at the build
+    float4* cpos32;        // per slot: unwrapped Cartesian position and charge (FP32)
+    double4_32a* cpos64;   // per slot: the same in FP64 (FP64 path)
+    const double* sbuf;    // per particle: s in [0, 1)
+    unsigned* status;      // kStatusList on overflow
+    double* cell;          // the build count
     int cap;
 };
+
+__device__ __forceinline__ int image_code(int nx, int ny, int nz) { return (nx + 1) + 3 * (ny + 1) + 9 * (nz + 1); }
 
 __device__ __forceinline__ uint64_t flex_step(const double* cell)
 {
@@ -488,14 +499,14 @@ k_flex_kvirial(int P, const int4* __restrict__ m, const double2* __restrict__ rh
     gen_virial_block(P, m, rho, g, alpha, W_out, status);
 }
 
-// Per step with a neighbour list, before the cell list: the scaled positions and charges packed
-// in the list's slot order, the largest displacement since the build (minimum image in s, length
-// with the current h, FP32), and on the last block the rebuild decision.  Until the first build
+// Per step with a neighbour list, before the cell list: the unwrapped Cartesian positions and
+// charges packed in the list's slot order, the largest displacement since the build (length with
+// the current h, FP32), and on the last block the rebuild decision.  Until the first build
 // there is no slot order: the kernel then only asks for a build.
 template <bool kF64>
 __global__ void __launch_bounds__(kNptThreads)
 k_flex_nl_check(int64_t N, const double* __restrict__ sbuf, const double* __restrict__ q,
-                const int* __restrict__ sorted, float4* __restrict__ spos32, double4_32a* __restrict__ spos64,
+                const int* __restrict__ sorted, float4* __restrict__ cpos32, double4_32a* __restrict__ cpos64,
                 const float4* __restrict__ sref, const FlexCoef* __restrict__ cf, FlexNList* __restrict__ nl)
 {
     __shared__ float smax[kNptThreads / 32];
@@ -503,28 +514,36 @@ k_flex_nl_check(int64_t N, const double* __restrict__ sbuf, const double* __rest
     const bool force = nl->base.force != 0;
     float d2max = 0.f;
     if (!force) {
-        float h[9];
+        double h[9];
+        float hf[9];
 #pragma unroll
-        for (int a = 0; a < 9; ++a) h[a] = (float)cf->h[a];
+        for (int a = 0; a < 9; ++a) {
+            h[a] = cf->h[a];
+            hf[a] = (float)h[a];
+        }
         for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < N; u += (int64_t)gridDim.x * blockDim.x) {
             const int64_t i = sorted[u];
-            const double x = sbuf[3 * i], y = sbuf[3 * i + 1], z = sbuf[3 * i + 2], qq = q[i];
-            spos32[u] = make_float4((float)x, (float)y, (float)z, (float)qq);
+            const float4 r0 = sref[u];
+            // s unwrapped since the build: s + n_wrap, n_wrap = -rint(s - s_ref)
+            double su[3] = {sbuf[3 * i], sbuf[3 * i + 1], sbuf[3 * i + 2]};
+            su[0] -= rint(su[0] - (double)r0.x);
+            su[1] -= rint(su[1] - (double)r0.y);
+            su[2] -= rint(su[2] - (double)r0.z);
+            const double qq = q[i];
+            double r[3];
+            for (int a = 0; a < 3; ++a) r[a] = h[3 * a] * su[0] + h[3 * a + 1] * su[1] + h[3 * a + 2] * su[2];
+            cpos32[u] = make_float4((float)r[0], (float)r[1], (float)r[2], (float)qq);
             if (kF64) {
                 double4_32a v;
-                v.x = x;
-                v.y = y;
-                v.z = z;
+                v.x = r[0];
+                v.y = r[1];
+                v.z = r[2];
                 v.w = qq;
-                spos64[u] = v;
+                cpos64[u] = v;
             }
-            const float4 r0 = sref[u];
-            float a = (float)x - r0.x, b = (float)y - r0.y, c = (float)z - r0.z;
-            a -= rintf(a);
-            b -= rintf(b);
-            c -= rintf(c);
-            const float dx = h[0] * a + h[1] * b + h[2] * c, dy = h[3] * a + h[4] * b + h[5] * c,
-                        dz = h[6] * a + h[7] * b + h[8] * c;
+            const float a = (float)su[0] - r0.x, b = (float)su[1] - r0.y, c = (float)su[2] - r0.z;
+            const float dx = hf[0] * a + hf[1] * b + hf[2] * c, dy = hf[3] * a + hf[4] * b + hf[5] * c,
+                        dz = hf[6] * a + hf[7] * b + hf[8] * c;
             const float d2 = dx * dx + dy * dy + dz * dz;
             d2max = d2 > d2max ? d2 : d2max;  // NaN compares false: caught by the cell checks
         }
@@ -591,7 +610,7 @@ __global__ void k_flex_nl_init(FlexNList* __restrict__ nl, float rl, float rc, d
 // evaluation, float-float sums per warp.  Each pair is visited from both ends: energies and
 // the virial take half.  Per-block partials {W_xx, W_yy, W_zz, W_xy, W_xz, W_yz, E_coul, E_lj}
 // at slots 0..7.  A cell beyond the cell arrays (flagged by k_cl_count) leaves F_r = 0.
-constexpr int kFlexHitCap = 64;  // < 32 buffered + 32 new
+constexpr int kFlexHitCap = 32 * (kListBatch + 1);  // < 32 buffered + 32 kListBatch new (the list pass)
 
 // Modes as the rectangular kernel's: search the cells and evaluate, search the cells within
 // rc + skin and write the list (rebuild steps only), evaluate the listed pairs.
@@ -611,8 +630,14 @@ k_flex_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, co
     __shared__ Hit hits[kPairWarps][kFlexHitCap];
     __shared__ double red[8][kPairWarps];
     __shared__ R shm[9];
+    __shared__ R sshift[27][3];  // list: the images h n, n in {-1, 0, 1}^3, by code
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     if (threadIdx.x < 9) shm[threadIdx.x] = (R)cf->h[threadIdx.x];
+    if (kList && threadIdx.x >= 32 && threadIdx.x < 32 + 27) {
+        const int c = threadIdx.x - 32;
+        const double n[3] = {(double)(c % 3 - 1), (double)((c / 3) % 3 - 1), (double)(c / 9 - 1)};
+        for (int a = 0; a < 3; ++a) sshift[c][a] = (R)(cf->h[3 * a] * n[0] + cf->h[3 * a + 1] * n[1] + cf->h[3 * a + 2] * n[2]);
+    }
     __syncthreads();
     const int nc[3] = {cc->nc[0], cc->nc[1], cc->nc[2]};
     double ws[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, ecsum = 0.0, elsum = 0.0;  // FP64 path
@@ -644,12 +669,12 @@ k_flex_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, co
         const int nwarps = gridDim.x * kPairWarps;
         for (int u = blockIdx.x * kPairWarps + wib; u < (int)N; u += nwarps) {
             const int i = sorted[u];
-            R si[3], qi;
+            R si[3], qi;  // cells and build: s; list: the unwrapped Cartesian position
             if constexpr (kF64) {
-                const double4_32a m64 = spos64[u];
+                const double4_32a m64 = kList ? la.cpos64[u] : spos64[u];
                 si[0] = m64.x, si[1] = m64.y, si[2] = m64.z, qi = m64.w;
             } else {
-                const float4 m32 = spos32[u];
+                const float4 m32 = kList ? la.cpos32[u] : spos32[u];
                 si[0] = m32.x, si[1] = m32.y, si[2] = m32.z, qi = m32.w;
             }
             // segment of this lane: row r = lane / 2 of the 3 x 3 rows, part lane % 2
@@ -688,9 +713,9 @@ k_flex_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, co
             R fx = 0, fy = 0, fz = 0, ec = 0, el = 0;
             R w[6] = {0, 0, 0, 0, 0, 0};  // xx, yy, zz, xy, xz, yz
             int nh = 0;
-            auto evaluate = [&](int count) {
+            auto evaluate = [&](int count, int base) {
                 if (lane >= count) return;
-                const Hit ht = hits[wib][lane];
+                const Hit ht = hits[wib][base + lane];
                 const R dx = ht.x, dy = ht.y, dz = ht.z, qj = ht.q;
                 const R r2 = dx * dx + dy * dy + dz * dz;
                 R inv_r, r, ex;
@@ -735,8 +760,12 @@ k_flex_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, co
                     const float4 o = spos32[sj];
                     ds[0] = o.x - si[0], ds[1] = o.y - si[1], ds[2] = o.z - si[2], qj = o.w;
                 }
+                R n[3];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) ds[a] -= rint(ds[a]);
+                for (int a = 0; a < 3; ++a) {
+                    n[a] = rint(ds[a]);
+                    ds[a] -= n[a];
+                }
                 const R dx = h[0] * ds[0] + h[1] * ds[1] + h[2] * ds[2];
                 const R dy = h[3] * ds[0] + h[4] * ds[1] + h[5] * ds[2];
                 const R dz = h[6] * ds[0] + h[7] * ds[1] + h[8] * ds[2];
@@ -745,7 +774,11 @@ k_flex_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, co
                 if constexpr (kBuild) {
                     if (hit) {
                         const int p = nh + __popc(m & ((1u << lane) - 1u));
-                        if (p < la.cap) la.nbr[(int64_t)u * la.cap + p] = sj;
+                        if (p < la.cap) {
+                            la.nbr[(int64_t)u * la.cap + p] = sj;
+                            // the image added to s_j - s_i is -n
+                            la.code[(int64_t)u * la.cap + p] = (unsigned char)image_code(-(int)n[0], -(int)n[1], -(int)n[2]);
+                        }
                     }
                     nh += __popc(m);
                     return;
@@ -757,7 +790,7 @@ k_flex_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, co
                 nh += __popc(m);
                 if (nh >= 32) {
                     __syncwarp();
-                    evaluate(32);
+                    evaluate(32, 0);
                     __syncwarp();
                     if (lane < nh - 32) hits[wib][lane] = hits[wib][32 + lane];
                     __syncwarp();
@@ -765,11 +798,53 @@ k_flex_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, co
                 }
             };
             if constexpr (kList) {
+                // the listed entries: r_u,j - r_u,i + h n (the build's image)
                 const int nn = la.nnb[u];
                 const int* row = la.nbr + (int64_t)u * la.cap;
-                for (int k0 = 0; k0 < nn; k0 += 32) {  // the same trip count on every lane
-                    const int k = k0 + lane;
-                    consider(k < nn, row[k < nn ? k : nn - 1]);
+                const unsigned char* crow = la.code + (int64_t)u * la.cap;
+                // kListBatch x 32 entries at a time: all their list entries and images are loaded,
+                // then all their positions, so that the loads overlap; then the compaction
+                for (int k0 = 0; k0 < nn; k0 += 32 * kListBatch) {  // the same trip count on every lane
+                    int sj[kListBatch], cd[kListBatch];
+#pragma unroll
+                    for (int a = 0; a < kListBatch; ++a) {
+                        const int k = k0 + 32 * a + lane;
+                        const int kk = k < nn ? k : nn - 1;
+                        sj[a] = row[kk];
+                        cd[a] = crow[kk];
+                    }
+                    R ox[kListBatch], oy[kListBatch], oz[kListBatch], oq[kListBatch];
+#pragma unroll
+                    for (int a = 0; a < kListBatch; ++a) {
+                        if constexpr (kF64) {
+                            const double4_32a o = la.cpos64[sj[a]];
+                            ox[a] = o.x, oy[a] = o.y, oz[a] = o.z, oq[a] = o.w;
+                        } else {
+                            const float4 o = la.cpos32[sj[a]];
+                            ox[a] = o.x, oy[a] = o.y, oz[a] = o.z, oq[a] = o.w;
+                        }
+                    }
+#pragma unroll
+                    for (int a = 0; a < kListBatch; ++a) {
+                        const int k = k0 + 32 * a + lane;
+                        const R dx = (ox[a] - si[0]) + sshift[cd[a]][0], dy = (oy[a] - si[1]) + sshift[cd[a]][1],
+                                dz = (oz[a] - si[2]) + sshift[cd[a]][2];
+                        const bool hit = k < nn && dx * dx + dy * dy + dz * dz < rc2;
+                        const unsigned m = __ballot_sync(0xffffffffu, hit);
+                        if (hit) {
+                            const int slot = nh + __popc(m & ((1u << lane) - 1u));
+                            hits[wib][slot] = Hit{dx, dy, dz, oq[a]};
+                        }
+                        nh += __popc(m);
+                    }
+                    // evaluate whole groups of 32 and keep the rest at the front
+                    __syncwarp();
+                    int b0 = 0;
+                    for (; b0 + 32 <= nh; b0 += 32) evaluate(32, b0);
+                    __syncwarp();
+                    if (b0 > 0 && lane < nh - b0) hits[wib][lane] = hits[wib][b0 + lane];
+                    __syncwarp();
+                    nh -= b0;
                 }
             } else {
                 for (int g = 0; g < 18; ++g) {
@@ -785,11 +860,25 @@ k_flex_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, co
                     la.nnb[u] = nh < la.cap ? nh : la.cap;
                     la.sref[u] = make_float4((float)si[0], (float)si[1], (float)si[2], 0.f);
                     if (nh > la.cap) atomicOr(la.status, kStatusList);
+                } else if (lane == 1) {
+                    // the slot's Cartesian position at the build (no wraps yet) for the list pass
+                    const double s0 = la.sbuf[3 * (int64_t)i], s1 = la.sbuf[3 * (int64_t)i + 1], s2 = la.sbuf[3 * (int64_t)i + 2];
+                    double r[3];
+                    for (int a = 0; a < 3; ++a) r[a] = cf->h[3 * a] * s0 + cf->h[3 * a + 1] * s1 + cf->h[3 * a + 2] * s2;
+                    la.cpos32[u] = make_float4((float)r[0], (float)r[1], (float)r[2], (float)qi);
+                    if (kF64) {
+                        double4_32a v;
+                        v.x = r[0];
+                        v.y = r[1];
+                        v.z = r[2];
+                        v.w = qi;
+                        la.cpos64[u] = v;
+                    }
                 }
                 continue;
             }
             __syncwarp();
-            evaluate(nh);
+            evaluate(nh, 0);
             __syncwarp();
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
@@ -1070,22 +1159,26 @@ static rbe_status flex_forces(rbe_ctx ctx, rbe_flex_system* sys, int do_kick)
         if (fp64 && b.n64 < N) return fail(ctx, RBE_ESTATE, "precision changed to FP64 after rbe_flex_init: call it again");
         const bool list = prm.skin > 0.0;
         FlexNList* nl = static_cast<FlexNList*>(ctx->flex_nls);
-        if (list && (!nl || b.ncap_list < N)) return fail(ctx, RBE_ESTATE, "skin changed after rbe_flex_init: call it again");
+        if (list && (!nl || b.ncap_list < N || ctx->flex_cpos_cap < N || ctx->flex_code_cap < b.nl_entries ||
+                     (fp64 && ctx->flex_cpos64_cap < N)))
+            return fail(ctx, RBE_ESTATE, "skin or precision changed after rbe_flex_init: call it again");
         double4_32a* s64 = fp64 ? b.spos64 : nullptr;
+        double4_32a* c64 = fp64 ? ctx->flex_cpos64 : nullptr;
         if (list) {
             const int grid = (int)std::min<int64_t>(nb, (int64_t)ctx->num_sms * 4);
             if (fp64)
-                k_flex_nl_check<true><<<grid, kNptThreads, 0, s>>>(N, ctx->gpos, sys->charge, b.sorted, b.spos32, s64,
-                                                                 b.sref, cf, nl);
+                k_flex_nl_check<true><<<grid, kNptThreads, 0, s>>>(N, ctx->gpos, sys->charge, b.sorted,
+                                                                 ctx->flex_cpos32, c64, b.sref, cf, nl);
             else
-                k_flex_nl_check<false><<<grid, kNptThreads, 0, s>>>(N, ctx->gpos, sys->charge, b.sorted, b.spos32,
-                                                                  nullptr, b.sref, cf, nl);
+                k_flex_nl_check<false><<<grid, kNptThreads, 0, s>>>(N, ctx->gpos, sys->charge, b.sorted,
+                                                                  ctx->flex_cpos32, nullptr, b.sref, cf, nl);
         }
         if ((st = launch_cell_list(ctx, N, ctx->gpos, sys->charge, list ? &nl->base : nullptr, fp64)) != RBE_OK)
             return st;
         const PairConst pc = make_pair_const(prm.rc, ctx->alpha, prm.qqr2e, prm.lj_sigma, prm.lj_eps);
         const CellConsts* cc = static_cast<const CellConsts*>(b.cellc);
-        const FlexListArgs la{nl, b.nbr, b.nnb, b.sref, ctx->d.status, sys->cell, b.nbr_cap};
+        const FlexListArgs la{nl,       b.nbr,     ctx->flex_code, b.nnb,     b.sref, ctx->flex_cpos32,
+                              c64,      ctx->gpos, ctx->d.status,  sys->cell, b.nbr_cap};
         auto pair = [&](auto f64_tag, auto mode_tag) {
             constexpr bool F64 = decltype(f64_tag)::value;
             constexpr int MODE = decltype(mode_tag)::value;
@@ -1142,10 +1235,38 @@ rbe_status flex_init(rbe_ctx ctx, rbe_flex_system* sys, uint64_t batch)
     // scratch of the rectangular step, its cell list sized for widths up to twice the initial (and
     // with skin > 0 the neighbour list, sized by the density N / (w_0 w_1 w_2) >= N / V)
     if ((st = npt_ensure(ctx, sys->N, width, prm.rc, prm.skin)) != RBE_OK) return st;
-    if (prm.skin > 0.0 && !ctx->flex_nls) {
-        FlexNList* nl = nullptr;
-        if ((e = ctx_alloc(ctx, &nl, sizeof(FlexNList))) != cudaSuccess) return cuda_fail(ctx, e, "flexible-cell list state");
-        ctx->flex_nls = nl;
+    if (prm.skin > 0.0) {
+        if (!ctx->flex_nls) {
+            FlexNList* nl = nullptr;
+            if ((e = ctx_alloc(ctx, &nl, sizeof(FlexNList))) != cudaSuccess)
+                return cuda_fail(ctx, e, "flexible-cell list state");
+            ctx->flex_nls = nl;
+        }
+        NptBuffers& nb_ = ctx->npt;
+        if (ctx->flex_code_cap < nb_.nl_entries) {
+            ctx_free(ctx, ctx->flex_code);
+            ctx->flex_code = nullptr;
+            ctx->flex_code_cap = 0;
+            if ((e = ctx_alloc(ctx, &ctx->flex_code, (size_t)nb_.nl_entries)) != cudaSuccess)
+                return cuda_fail(ctx, e, "flexible-cell list images");
+            ctx->flex_code_cap = nb_.nl_entries;
+        }
+        if (ctx->flex_cpos_cap < sys->N) {
+            ctx_free(ctx, ctx->flex_cpos32);
+            ctx->flex_cpos32 = nullptr;
+            ctx->flex_cpos_cap = 0;
+            if ((e = ctx_alloc(ctx, &ctx->flex_cpos32, sizeof(float4) * (size_t)sys->N)) != cudaSuccess)
+                return cuda_fail(ctx, e, "flexible-cell list positions");
+            ctx->flex_cpos_cap = sys->N;
+        }
+        if (ctx->precision == RBE_FP64 && ctx->flex_cpos64_cap < sys->N) {
+            ctx_free(ctx, ctx->flex_cpos64);
+            ctx->flex_cpos64 = nullptr;
+            ctx->flex_cpos64_cap = 0;
+            if ((e = ctx_alloc(ctx, &ctx->flex_cpos64, sizeof(double4_32a) * (size_t)sys->N)) != cudaSuccess)
+                return cuda_fail(ctx, e, "flexible-cell list positions (FP64)");
+            ctx->flex_cpos64_cap = sys->N;
+        }
     }
     // proposal tables for lengths up to sqrt(3) x twice the initial cell vectors, and the unit cube
     int need = 2 * host_axis_M(ctx->alpha, 1.0) + 1;
