@@ -11,6 +11,7 @@ pressure tensor); each C function states the equation it restates.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -23,6 +24,7 @@ _SRC_NPT = os.path.join(_HERE, "npt_oracle.c")
 _SRC_SMP = os.path.join(_HERE, "sampler_oracle.c")
 _SRC_GEN = os.path.join(_HERE, "general_oracle.c")
 _SRC_FLX = os.path.join(_HERE, "flexible_oracle.c")
+_SRC_WAT = os.path.join(_HERE, "water_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -36,7 +38,7 @@ _c_uint32_p = ctypes.POINTER(ctypes.c_uint32)
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc into ``oracle/_build/liboracle.so`` and return its path."""
     os.makedirs(_BUILD, exist_ok=True)
-    srcs = [s for s in (_SRC, _SRC_NPT, _SRC_SMP, _SRC_GEN, _SRC_FLX) if os.path.exists(s)]
+    srcs = [s for s in (_SRC, _SRC_NPT, _SRC_SMP, _SRC_GEN, _SRC_FLX, _SRC_WAT) if os.path.exists(s)]
     newest = max(os.path.getmtime(s) for s in srcs)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".{os.getpid()}.tmp"
@@ -96,6 +98,8 @@ def _load():
                 _bind_general(lib)
             if hasattr(lib, "orc_flex_step"):
                 _bind_flexible(lib)
+            if hasattr(lib, "orc_water_step"):
+                _bind_water(lib)
             _lib = lib
     return _lib
 
@@ -665,3 +669,110 @@ def flex_run(st: FlexState, step0: int, n: int, prm: FlexParams):
     _check(_load().orc_flex_run(st.N, _dp(st.r), _dp(st.p), _dp(st.F), _dp(st.q), _dp(st.m), _dp(st.h), _dp(st.ph),
                                 _dp(st.W), step0, n, ctypes.byref(st.bind(prm)), _dp(hs), _dp(Ps), _dp(H)), "flex_run")
     return hs, Ps, H
+
+
+# ---------------------------------------------------------------------------------
+# Rigid 3-site water (water_oracle.c)
+class WaterParams(ctypes.Structure):
+    """Constraint settings of the rigid-water step (mirrors orc_water_params)."""
+    _fields_ = [("d_OH", ctypes.c_double), ("d_HH", ctypes.c_double), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+def water_params(d_OH=1.0, angle_deg=109.47, tol=1e-14, max_iter=500) -> WaterParams:
+    """O-H length, H-O-H angle (the H-H length follows), SHAKE tolerance and sweep limit."""
+    d_HH = 2.0 * d_OH * math.sin(math.radians(angle_deg) / 2.0)
+    return WaterParams(d_OH=d_OH, d_HH=d_HH, tol=tol, max_iter=max_iter, pad=0)
+
+
+def _bind_water(lib):
+    P = ctypes.POINTER(NptParams)
+    Wp = ctypes.POINTER(WaterParams)
+    lib.orc_water_real.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _c_double_p,
+                                   _c_double_p, _c_double_p]
+    lib.orc_water_real.restype = ctypes.c_int
+    lib.orc_water_virial_corr.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p, _c_double_p]
+    lib.orc_water_virial_corr.restype = ctypes.c_double
+    lib.orc_water_forces.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p, _c_double_p,
+                                     ctypes.c_uint64, P, _c_double_p, _c_double_p, _c_double_p]
+    lib.orc_water_forces.restype = ctypes.c_int
+    lib.orc_water_step.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p, _c_double_p, _c_double_p,
+                                   _c_double_p, _c_double_p, _c_double_p, ctypes.c_uint64, P, Wp, _c_double_p]
+    lib.orc_water_step.restype = ctypes.c_int
+    lib.orc_water_run.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p, _c_double_p, _c_double_p,
+                                  _c_double_p, _c_double_p, _c_double_p, ctypes.c_uint64, ctypes.c_int32, P, Wp,
+                                  _c_double_p, _c_double_p, _c_double_p]
+    lib.orc_water_run.restype = ctypes.c_int
+    lib.orc_water_violation.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p, _c_double_p, Wp,
+                                        _c_double_p]
+    lib.orc_water_violation.restype = None
+
+
+def water_real(pos, q, box, alpha, rc, qqr2e, lj_sigma, lj_eps):
+    """Real space between molecules plus the exclusions: (F[3n,3], W trace, E_coul, E_lj, E_excl)."""
+    pos = _f64(pos)
+    q = _f64(q)
+    F = np.zeros_like(pos)
+    W = ctypes.c_double(0.0)
+    E = np.zeros(3)
+    _check(_load().orc_water_real(q.shape[0] // 3, _dp(pos), _dp(q), _dp(_f64(box, (3,))), alpha, rc, qqr2e,
+                                  lj_sigma, lj_eps, _dp(F), ctypes.byref(W), _dp(E)), "water_real")
+    return F, W.value, E[0], E[1], E[2]
+
+
+def water_virial_corr(pos, m, box, F):
+    """-sum_i F_i . d_i (d_i the site's offset from its molecule's centre)."""
+    pos = _f64(pos)
+    return _load().orc_water_virial_corr(pos.shape[0] // 3, _dp(pos), _dp(_f64(m)), _dp(_f64(box, (3,))),
+                                         _dp(_f64(F)))
+
+
+class WaterState:
+    """Oracle state of the rigid-water step: sites (O, H, H per molecule), momenta, forces, box,
+    piston momentum and molecular virial."""
+
+    def __init__(self, r, p, q, m, L, pV=0.0):
+        self.r = _f64(r).copy()
+        self.p = _f64(p).copy()
+        self.q = _f64(q)
+        self.m = _f64(m)
+        self.L = _f64(L, (3,)).copy()
+        self.F = np.zeros_like(self.r)
+        self.pV = ctypes.c_double(pV)
+        self.W = ctypes.c_double(0.0)
+
+    @property
+    def Nmol(self):
+        return self.q.shape[0] // 3
+
+
+def water_forces(st: WaterState, step: int, prm: NptParams):
+    E = np.zeros(4)
+    _check(_load().orc_water_forces(st.Nmol, _dp(st.r), _dp(st.q), _dp(st.m), _dp(st.L), step, ctypes.byref(prm),
+                                    _dp(st.F), ctypes.byref(st.W), _dp(E)), "water_forces")
+    return E
+
+
+def water_step(st: WaterState, step: int, prm: NptParams, wp: WaterParams):
+    E = np.zeros(4)
+    _check(_load().orc_water_step(st.Nmol, _dp(st.r), _dp(st.p), _dp(st.F), _dp(st.q), _dp(st.m), _dp(st.L),
+                                  ctypes.byref(st.pV), ctypes.byref(st.W), step, ctypes.byref(prm), ctypes.byref(wp),
+                                  _dp(E)), "water_step")
+    return E
+
+
+def water_run(st: WaterState, step0: int, n: int, prm: NptParams, wp: WaterParams):
+    """n steps; returns (V, molecular P_ins, extended energy) per step."""
+    V, Pi, H = np.zeros(n), np.zeros(n), np.zeros(n)
+    _check(_load().orc_water_run(st.Nmol, _dp(st.r), _dp(st.p), _dp(st.F), _dp(st.q), _dp(st.m), _dp(st.L),
+                                 ctypes.byref(st.pV), ctypes.byref(st.W), step0, n, ctypes.byref(prm),
+                                 ctypes.byref(wp), _dp(V), _dp(Pi), _dp(H)), "water_run")
+    return V, Pi, H
+
+
+def water_violation(st: WaterState, wp: WaterParams):
+    """(largest relative distance violation, largest relative velocity-constraint violation)."""
+    out = np.zeros(2)
+    _load().orc_water_violation(st.Nmol, _dp(st.r), _dp(st.p), _dp(st.m), _dp(st.L), ctypes.byref(wp), _dp(out))
+    return out
