@@ -24,9 +24,12 @@
  * qqr2e, minus the intramolecular part of the Ewald sum, -qqr2e q_i q_j erf(sqrt(a) r)/r for the
  * three site pairs of each molecule, plus the real space between sites of different molecules
  * (qqr2e q_i q_j erfc(sqrt(a) r)/r within rc, nearest image) and LJ 12-6 between oxygens.
- * Sites are ordered O, H, H per molecule.  Positions are wrapped into the box per site after each
- * step; a molecule is made whole by the nearest image of each H from its O, and its centre is
- * taken from that whole molecule.
+ * Sites are ordered O, H, H per molecule.  After each step every molecule is moved by the lattice
+ * vector that brings its oxygen into [0, L), so molecules stay whole in storage (sites may sit up
+ * to a bond length outside the box): wrapping the sites one by one would let a box change between
+ * the wrap and the next use of the nearest image distort a molecule that straddles the boundary
+ * by the change of L.  A molecule is rebuilt whole from its oxygen by the nearest image (a no-op
+ * on stored molecules), and its centre is taken from that whole molecule.
  * Extended energy (orc_water_run): sum p^2/(2 m)/100 + U + P V + p_V^2/(2 M_V).
  */
 #include <math.h>
@@ -447,8 +450,12 @@ int orc_water_step(int64_t Nmol, double* r, double* p, double* F, const double* 
         scale_box_w(L, V + h * (*pV) / prm->M_V);
         V = L[0] * L[1] * L[2];
     }
-    for (int64_t i = 0; i < 3 * Nmol; ++i)
-        for (int t = 0; t < 3; ++t) r[3 * i + t] -= L[t] * floor(r[3 * i + t] / L[t]);
+    /* wrap by molecule: the lattice vector that brings the oxygen into [0, L) moves all its sites */
+    for (int64_t I = 0; I < Nmol; ++I)
+        for (int t = 0; t < 3; ++t) {
+            const double sh = L[t] * floor(r[9 * I + t] / L[t]);
+            for (int k = 0; k < 3; ++k) r[9 * I + 3 * k + t] -= sh;
+        }
     st = orc_water_forces(Nmol, r, q, m, L, step, prm, F, Wmol, E);
     if (st != WAT_OK) return st;
     eps = prm->barostat ? *pV / (3.0 * prm->M_V * V) : 0.0;
