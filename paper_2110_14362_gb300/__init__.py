@@ -13,6 +13,7 @@ from ._binding import (  # noqa: F401
     rbe_kspace_forces_virial, rbe_kspace_forces_virial_host, rbe_kspace_weighted, rbe_get_rho, rbe_sync,
     rbe_version, rbe_set_kernel_timing, rbe_get_kernel_times, rbe_measure_pipe, rbe_sample_k_noalloc,
     NptParams, System, NptReplica, rbe_npt_init, rbe_npt_step, RBE_CELL_DOUBLES,
+    WaterParams, water_params, WaterReplica, rbe_water_init, rbe_water_step, CELL_EXCL,
     FlexParams, FlexSystem, FlexReplica, rbe_flex_init, rbe_flex_step, RBE_FLEX_CELL_DOUBLES,
     FLEX_H, FLEX_PH, FLEX_W, FLEX_KT, FLEX_PT, FLEX_EK, FLEX_EC, FLEX_EL, FLEX_V, FLEX_HAM, FLEX_STEP, FLEX_BUILDS, Server, ServerConfig, Request, piston_mass,
     piston_masses_rect, RBE_BAROSTAT_NONE, RBE_BAROSTAT_ISO, RBE_BAROSTAT_ANISO, RBE_BAROSTAT_SEMI, CELL_PC,

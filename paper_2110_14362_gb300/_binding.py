@@ -74,6 +74,21 @@ class FlexSystem(ctypes.Structure):
                 ("cell", ctypes.c_void_p), ("step", ctypes.c_uint64), ("params", FlexParams)]
 
 
+class WaterParams(ctypes.Structure):
+    """rbe_water_params (include/rbe.h): the rigid 3-site water constraints."""
+    _fields_ = [("d_OH", ctypes.c_double), ("d_HH", ctypes.c_double), ("shake_tol", ctypes.c_double),
+                ("shake_max_iter", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+def water_params(d_OH: float = 1.0, angle_deg: float = 109.47, shake_tol: float = 1e-14,
+                 shake_max_iter: int = 500) -> WaterParams:
+    """O-H length and H-O-H angle (the H-H length follows), SHAKE tolerance and sweep limit."""
+    return WaterParams(d_OH=d_OH, d_HH=2.0 * d_OH * math.sin(math.radians(angle_deg) / 2.0), shake_tol=shake_tol,
+                       shake_max_iter=shake_max_iter, pad=0)
+
+
+CELL_EXCL = 25  # rigid water: the exclusion energy in the cell block
+
 RBE_FLEX_CELL_DOUBLES = 64
 # slots of the flexible cell block (include/rbe.h)
 FLEX_H, FLEX_PH, FLEX_W, FLEX_KT, FLEX_PT = 0, 9, 18, 27, 36
@@ -131,6 +146,8 @@ SIGNATURES = [
      [_dp, ctypes.c_double, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, _vp, _vp, _vp]),
     ("rbe_npt_init", ctypes.c_int, [_vp, ctypes.POINTER(System), ctypes.c_uint64]),
     ("rbe_npt_step", ctypes.c_int, [_vp, ctypes.POINTER(System), ctypes.c_int32]),
+    ("rbe_water_init", ctypes.c_int, [_vp, ctypes.POINTER(System), ctypes.POINTER(WaterParams), ctypes.c_uint64]),
+    ("rbe_water_step", ctypes.c_int, [_vp, ctypes.POINTER(System), ctypes.POINTER(WaterParams), ctypes.c_int32]),
     ("rbe_flex_init", ctypes.c_int, [_vp, ctypes.POINTER(FlexSystem), ctypes.c_uint64]),
     ("rbe_flex_step", ctypes.c_int, [_vp, ctypes.POINTER(FlexSystem), ctypes.c_int32]),
     ("rbe_batch_create", ctypes.c_int, [ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
@@ -359,6 +376,30 @@ class NptReplica:
         """(pos, mom, force, box, cell block) as NumPy arrays (synchronises)."""
         c = self.cell.cpu().numpy()
         return (self.pos.cpu().numpy(), self.mom.cpu().numpy(), self.force.cpu().numpy(), c[:3].copy(), c)
+
+
+def rbe_water_init(h, sys_: "System", wp: WaterParams, batch: int):
+    _check(load().rbe_water_init(h, ctypes.byref(sys_), ctypes.byref(wp), int(batch)), h)
+
+
+def rbe_water_step(h, sys_: "System", wp: WaterParams, nsteps: int):
+    _check(load().rbe_water_step(h, ctypes.byref(sys_), ctypes.byref(wp), int(nsteps)), h)
+
+
+class WaterReplica(NptReplica):
+    """A device-resident rigid-water system (sites O, H, H per molecule) on the NPT replica's
+    buffers, stepped by rbe_water_init / rbe_water_step."""
+
+    def __init__(self, pos, mom, charge, mass, box, params: NptParams, device, wp: WaterParams | None = None,
+                 step: int = 0, pV: float = 0.0):
+        super().__init__(pos, mom, charge, mass, box, params, device, step=step, pV=pV)
+        self.wp = wp if wp is not None else water_params()
+
+    def init(self, ctx: "Context", batch: int | None = None):
+        rbe_water_init(ctx.h, self.sys, self.wp, self.sys.step if batch is None else batch)
+
+    def step(self, ctx: "Context", nsteps: int = 1):
+        rbe_water_step(ctx.h, self.sys, self.wp, nsteps)
 
 
 def rbe_flex_init(h, sys_: "FlexSystem", batch: int):

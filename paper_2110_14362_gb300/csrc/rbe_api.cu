@@ -97,6 +97,8 @@ static rbe_status status_from_bits(rbe_ctx ctx, unsigned bits)
     if (bits & kStatusBox)
         return fail(ctx, RBE_ESTATE,
                     "the box left the range rbe_npt_init prepared (cell list capacity, or rc > l/2 on some axis)");
+    if (bits & kStatusShake)
+        return fail(ctx, RBE_ESTATE, "SHAKE did not converge within its sweep limit (a molecule was torn apart)");
     if (bits & kStatusTimeout) return fail(ctx, RBE_ETIMEOUT, "a bounded device wait gave up");
     if (bits & kStatusNonFinite) return fail(ctx, RBE_ENONFINITE, "rho(k) or an output is not finite");
     return RBE_OK;
@@ -532,6 +534,32 @@ rbe_status rbe_flex_step(rbe_ctx ctx, rbe_flex_system* sys, int32_t nsteps)
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(ctx, RBE_ECUDA, "cannot select the context's device");
     return flex_run(ctx, sys, nsteps);
+}
+
+rbe_status rbe_water_init(rbe_ctx ctx, rbe_system* sys, const rbe_water_params* wp, uint64_t batch)
+{
+    if (!ctx) return RBE_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(ctx, RBE_ECUDA, "cannot select the context's device");
+    if (sys) {
+        rbe_status st;
+        const int64_t N = sys->N;
+        if ((st = check_dev(ctx, sys->pos, "pos", N > 0)) != RBE_OK) return st;
+        if ((st = check_dev(ctx, sys->mom, "mom", N > 0)) != RBE_OK) return st;
+        if ((st = check_dev(ctx, sys->force, "force", N > 0)) != RBE_OK) return st;
+        if ((st = check_dev(ctx, sys->charge, "charge", N > 0)) != RBE_OK) return st;
+        if ((st = check_dev(ctx, sys->mass, "mass", N > 0)) != RBE_OK) return st;
+        if ((st = check_dev(ctx, sys->cell, "cell", true)) != RBE_OK) return st;
+    }
+    return water_init(ctx, sys, wp, batch);
+}
+
+rbe_status rbe_water_step(rbe_ctx ctx, rbe_system* sys, const rbe_water_params* wp, int32_t nsteps)
+{
+    if (!ctx) return RBE_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(ctx, RBE_ECUDA, "cannot select the context's device");
+    return water_run(ctx, sys, wp, nsteps);
 }
 
 rbe_status rbe_set_kernel_timing(rbe_ctx ctx, int32_t enable)

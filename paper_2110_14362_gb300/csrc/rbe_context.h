@@ -131,6 +131,7 @@ struct rbe_ctx_s {
     rbe::NptBuffers npt;
     int64_t npt_ready_N = -1;        // N of the system rbe_npt_init prepared the scratch for
     int64_t flex_ready_N = -1;       // N of the system rbe_flex_init prepared the scratch for
+    int64_t water_ready_N = -1;      // N of the system rbe_water_init prepared the scratch for
     void* flex_coef = nullptr;       // per-step coefficients of the flexible-cell step (rbe_flex.cu)
     void* gcell_dev = nullptr;       // general-cell quantities of the current cell (rbe_flex.cu)
     void* flex_nls = nullptr;        // neighbour-list state of the flexible-cell step (rbe_flex.cu)
@@ -189,6 +190,15 @@ rbe_status npt_run(rbe_ctx ctx, rbe_system* sys, int32_t nsteps);
 rbe_status npt_ensure(rbe_ctx ctx, int64_t N, const double box[3], double rc, double skin);
 int pair_blocks(rbe_ctx ctx, int64_t N, bool fp64);
 rbe_status launch_cell_list(rbe_ctx ctx, int64_t N, const double* pos, const double* q, void* nls, bool fp64);
+// Shared with the rigid-water step (rbe_npt.cu): parameter checks, the setup of rbe_npt_init
+// before its first forces, the device step index, the isotropic cell part of a step.
+rbe_status npt_validate(rbe_ctx ctx, const rbe_system* sys);
+rbe_status npt_prepare(rbe_ctx ctx, rbe_system* sys, uint64_t batch);
+rbe_status launch_npt_set_step(rbe_ctx ctx, double* cell, uint64_t step);
+rbe_status launch_npt_cell_iso(rbe_ctx ctx, rbe_system* sys);
+// The rigid-water step (rbe_water.cu).
+rbe_status water_init(rbe_ctx ctx, rbe_system* sys, const rbe_water_params* wp, uint64_t batch);
+rbe_status water_run(rbe_ctx ctx, rbe_system* sys, const rbe_water_params* wp, int32_t nsteps);
 // The flexible-cell step (rbe_flex.cu).
 rbe_status flex_init(rbe_ctx ctx, rbe_flex_system* sys, uint64_t batch);
 rbe_status flex_run(rbe_ctx ctx, rbe_flex_system* sys, int32_t nsteps);

@@ -23,6 +23,7 @@ constexpr unsigned kStatusTable = 4u;      // the sampling table did not fit its
 constexpr unsigned kStatusTimeout = 8u;    // a bounded wait gave up
 constexpr unsigned kStatusBox = 16u;       // NPT: the box outgrew the cell list or broke rc <= l/2
 constexpr unsigned kStatusList = 32u;      // NPT: a particle had more neighbours than the list holds
+constexpr unsigned kStatusShake = 64u;     // rigid water: SHAKE did not converge within its sweep limit
 
 // ---------------------------------------------------------------------------------
 // Programmatic dependent launch: a kernel launched with programmatic stream

@@ -1307,6 +1307,7 @@ rbe_status flex_init(rbe_ctx ctx, rbe_flex_system* sys, uint64_t batch)
     }
     ctx->flex_ready_N = sys->N;
     ctx->npt_ready_N = -1;  // the shared scratch now holds this system's masses and cell list
+    ctx->water_ready_N = -1;
     NptBuffers& b = ctx->npt;
     const int nb = (int)((sys->N + kNptThreads - 1) / kNptThreads);
     k_flex_mass<<<nb, kNptThreads, 0, ctx->stream>>>(sys->N, sys->mass, b.mprop);

@@ -35,22 +35,6 @@ namespace rbe {
 // times the initial ones; a box beyond it is flagged (RBE_ESTATE) by the step.
 constexpr double kBoxHeadroom = 2.0;
 
-// Sub-step coefficients of one step, per axis (the isotropic cell writes the same value on
-// every axis).
-struct NptCoef {
-    double a1[3], b1[3];    // R^p/2 before the forces: p_j <- a1_j p_j + 100 F_j b1_j
-    double a2m1[3], b2[3];  // first R/2: r_j <- r_j + r_j (a2_j - 1) + (p_j/m) b2_j
-    double g, og;           // O: p <- g p + sqrt(og m) z, og = 100 kT (1 - g^2)
-    double sog;             // sqrt(og): the O noise amplitude is sog sqrt(m)
-    double a3m1[3], b3[3];  // second R/2
-    double a4[3], b4[3];    // R^p/2 after the forces
-    double L[3];        // box after the second V/2
-    double invL[3];     // 1 / L
-    double half_cap;    // displacement cap per R/2
-    double V;
-    int noise;
-    int pad;
-};
 
 // (e^x - 1)/x * t with x = eps t; the series for tiny x.
 __device__ __forceinline__ double expm1_over(double x, double t)
@@ -65,12 +49,6 @@ __device__ __forceinline__ double expm1_over(double x, double t)
 // coefficient, O^p, R/2 coefficient, V/2, R^p/2 coefficient.  cell = {l, p_V, W, 2K, ...}.
 // The step index lives on the device (cell[kCellStep] as 64-bit integer bits), so that a
 // captured sequence of steps can be replayed: every kernel reads it, k_npt_finish advances it.
-constexpr int kCellStep = 11;
-
-__device__ __forceinline__ uint64_t cell_step(const double* cell)
-{
-    return (uint64_t)__double_as_longlong(cell[kCellStep]);
-}
 
 
 // Lanes 0..2 of one warp: axis `lane` of the box L; then lane 0 the totals.  Cells of at
@@ -1450,7 +1428,7 @@ static rbe_status npt_forces(rbe_ctx ctx, rbe_system* sys, uint64_t batch, int d
     return npt_check(ctx, "k_npt_finish");
 }
 
-static rbe_status npt_validate(rbe_ctx ctx, const rbe_system* sys)
+rbe_status npt_validate(rbe_ctx ctx, const rbe_system* sys)
 {
     if (!sys) return fail(ctx, RBE_EINVAL, "system is NULL");
     const rbe_npt_params& p = sys->params;
@@ -1488,10 +1466,12 @@ static rbe_status npt_box_check(rbe_ctx ctx, const rbe_system* sys, double box[3
     return RBE_OK;
 }
 
-rbe_status npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch)
+// Everything of rbe_npt_init before the first forces: the box check, scratch, tables, 1/m and
+// sqrt(m), the cell-list constants of the initial box, the list state, the step index set to
+// `batch` (shared with the rigid-water step).
+rbe_status npt_prepare(rbe_ctx ctx, rbe_system* sys, uint64_t batch)
 {
-    rbe_status st = npt_validate(ctx, sys);
-    if (st != RBE_OK) return st;
+    rbe_status st;
     double box[3];
     if ((st = npt_box_check(ctx, sys, box)) != RBE_OK) return st;
     if ((st = npt_ensure(ctx, sys->N, box, sys->params.rc, sys->params.skin)) != RBE_OK) return st;
@@ -1505,6 +1485,7 @@ rbe_status npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch)
     if ((st = ensure_table_capacity(ctx, need)) != RBE_OK) return st;
     ctx->npt_ready_N = sys->N;
     ctx->flex_ready_N = -1;  // the shared scratch now holds this system's masses and cell list
+    ctx->water_ready_N = -1;
     // per-particle 1/m and sqrt(m), and the cell-list constants of the initial box
     NptBuffers& b = ctx->npt;
     k_mass_props<<<(unsigned)((sys->N + kNptThreads - 1) / kNptThreads), kNptThreads, 0, ctx->stream>>>(
@@ -1516,7 +1497,29 @@ rbe_status npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch)
         k_nl_init<<<1, 32, 0, ctx->stream>>>(static_cast<NListState*>(b.nls), (float)(sys->params.rc + skin),
                                              (float)sys->params.rc);
     k_npt_set_step<<<1, 32, 0, ctx->stream>>>(sys->cell, batch);
-    if ((st = npt_check(ctx, "k_npt_set_step")) != RBE_OK) return st;
+    return npt_check(ctx, "k_npt_set_step");
+}
+
+rbe_status launch_npt_set_step(rbe_ctx ctx, double* cell, uint64_t step)
+{
+    k_npt_set_step<<<1, 32, 0, ctx->stream>>>(cell, step);
+    return npt_check(ctx, "k_npt_set_step");
+}
+
+// The isotropic cell part of a step (k_npt_cell_a) into ctx->npt.coef and the cell constants.
+rbe_status launch_npt_cell_iso(rbe_ctx ctx, rbe_system* sys)
+{
+    k_npt_cell_a<<<1, kCellWarps * 32, 0, ctx->stream>>>(sys->cell, reinterpret_cast<NptCoef*>(ctx->npt.coef),
+                                                       sys->params, ctx->seed, ctx->npt.cellcap,
+                                                       static_cast<CellConsts*>(ctx->npt.cellc));
+    return npt_check(ctx, "k_npt_cell_a");
+}
+
+rbe_status npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch)
+{
+    rbe_status st = npt_validate(ctx, sys);
+    if (st != RBE_OK) return st;
+    if ((st = npt_prepare(ctx, sys, batch)) != RBE_OK) return st;
     st = npt_forces(ctx, sys, batch, 0);
     if (st != RBE_OK) return st;
     k_npt_set_step<<<1, 32, 0, ctx->stream>>>(sys->cell, sys->step);

@@ -138,4 +138,29 @@ struct NListState {
     int force;         // 1: build at the next step (set by rbe_npt_init)
 };
 
+// Sub-step coefficients of one step, per axis (the isotropic cell writes the same value on
+// every axis).
+struct NptCoef {
+    double a1[3], b1[3];    // R^p/2 before the forces: p_j <- a1_j p_j + 100 F_j b1_j
+    double a2m1[3], b2[3];  // first R/2: r_j <- r_j + r_j (a2_j - 1) + (p_j/m) b2_j
+    double g, og;           // O: p <- g p + sqrt(og m) z, og = 100 kT (1 - g^2)
+    double sog;             // sqrt(og): the O noise amplitude is sog sqrt(m)
+    double a3m1[3], b3[3];  // second R/2
+    double a4[3], b4[3];    // R^p/2 after the forces
+    double L[3];        // box after the second V/2
+    double invL[3];     // 1 / L
+    double half_cap;    // displacement cap per R/2
+    double V;
+    int noise;
+    int pad;
+};
+
+// The step index lives in the cell block (cell[kCellStep], 64-bit integer bits).
+constexpr int kCellStep = 11;
+
+__device__ __forceinline__ uint64_t cell_step(const double* cell)
+{
+    return (uint64_t)__double_as_longlong(cell[kCellStep]);
+}
+
 }  // namespace rbe

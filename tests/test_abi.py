@@ -58,6 +58,8 @@ def test_argument_validation_without_gpu():
     cell = (ctypes.c_double * 9)(10.0, 0, 0, 0, 10.0, 0, 0, 0, 10.0)
     assert lib.rbe_kspace_forces_virial_general(None, 0, None, None, cell, 0, None, None, None) == rbe.RBE_EINVAL
     assert lib.rbe_flex_init(None, None, 0) == rbe.RBE_EINVAL
+    assert lib.rbe_water_init(None, None, None, 0) == rbe.RBE_EINVAL
+    assert lib.rbe_water_step(None, None, None, 1) == rbe.RBE_EINVAL
     assert lib.rbe_flex_step(None, None, 1) == rbe.RBE_EINVAL
 
 

@@ -18,6 +18,7 @@ STRUCTS = {
     "rbe_server_config": B.ServerConfig,
     "rbe_request": B.Request,
     "rbe_flex_params": B.FlexParams,
+    "rbe_water_params": B.WaterParams,
     "rbe_flex_system": B.FlexSystem,
 }
 
