@@ -251,6 +251,7 @@ def run_ours(args, world, rank, local):
     serving = None if args.skip_serving else run_serving(args, world, rank)
     npt1 = None if args.skip_serving else run_npt_single(rbe, [1000, 10000, 100000], 20)
     batched = None if args.skip_serving else run_batched(rbe)
+    water = None if args.skip_serving else run_water(rbe, steps=1000, warmup=20)
     sweep = None if args.skip_sweep else run_sweep(rbe)
 
     cpu = None
@@ -279,6 +280,8 @@ def run_ours(args, world, rank, local):
         line["serving"] = serving
     if batched:
         line["batched_kspace"] = batched
+    if water:
+        line["water_npt"] = water
     if sweep:
         line["sweep"] = sweep
     if npt1:
@@ -399,6 +402,51 @@ def run_npt_single(rbe, sizes, steps):
                        # the fully flexible (sheared) cell: general-cell k-space and triclinic real space
                        "fp32_flex_ms_per_step": npt_single(rbe, N, rbe.RBE_FP32_PHASE, steps, barostat=4)}
     return out
+
+
+WATER_MASS = (15.9994, 1.008, 1.008)
+
+
+def run_water(rbe, steps=1000, warmup=20):
+    """The plain-method rigid-water NPT run: 3000 molecules (O -0.8476, H +0.4238, O-H 1 A,
+    H-O-H 109.47 deg, LJ O-O 3.166 A / 0.650 kJ/mol) at random orientations on a jittered lattice
+    at 1 g/cm^3 (`inputs.water`), alpha = 0.25, rc = 10 A, P = 100, FP64, Langevin isotropic NPT at
+    300 K and 1 bar, dt = 1 fs, a 0.05 A cap on the centres' peculiar displacement per step (the
+    random orientations overlap at the start).  ms per step by CUDA events over `steps` steps after
+    `warmup`; density, molecular pressure and the largest bond error at the end."""
+    import torch
+    s = inputs.water(3000)
+    box = np.asarray(s.box, dtype=np.float64)
+    n = len(s.q) // 3
+    m = np.tile(WATER_MASS, n)
+    rng = np.random.default_rng(7)
+    mom = rng.standard_normal((3 * n, 3)) * np.sqrt(KB * 300.0 * 100.0 * m)[:, None]
+    V0 = float(np.prod(box))
+    prm = rbe.NptParams(dt=0.001, kT=KB * 300.0, P_ext=1.0 * BAR, gamma=10.0, gamma_V=2.0,
+                        M_V=rbe.piston_mass(0.5, 4.5e-5 / BAR, V0), rc=10.0, qqr2e=1389.35457644382,
+                        lj_sigma=3.166, lj_eps=0.650, max_disp=0.05, kspace=1, real=1, noise=1, barostat=1)
+    stream = torch.cuda.current_stream()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    with rbe.Context(box, s.alpha, s.P, 2024, rbe.RBE_FP64, stream=stream.cuda_stream) as ctx:
+        rep = rbe.WaterReplica(np.asarray(s.pos), mom, np.asarray(s.q), m, box, prm, dev)
+        rep.init(ctx, batch=0)
+        rep.step(ctx, warmup)
+        ctx.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep.step(ctx, steps)
+        e1.record(stream)
+        ctx.sync()
+        ms = e0.elapsed_time(e1) / steps
+        r, p, F, L, cell = rep.state()
+    mol = r.reshape(-1, 3, 3)
+    bond = float(np.abs(np.linalg.norm(mol[:, 1:] - mol[:, :1], axis=2) - 1.0).max())
+    V = float(np.prod(L))
+    return {"molecules": n, "sites": 3 * n, "alpha": s.alpha, "P": s.P, "rc": 10.0, "precision": "fp64",
+            "steps": steps, "warmup": warmup, "ms_per_step": ms, "steps_per_s": 1e3 / ms,
+            "site_pair_evals_per_s": 3 * n * s.P / (ms * 1e-3),
+            "density_g_cm3": n * 18.01528 / (0.602214076 * V), "P_ins_bar": float(cell[6]) / BAR,
+            "max_bond_error_A": bond}
 
 
 def run_general(rbe, steps=20, warmup=3):
@@ -668,6 +716,8 @@ def main():
     ap.add_argument("--ptilde", type=int, default=0, help="with --profile-npt: a separate pressure batch")
     ap.add_argument("--reuse", type=int, default=1, help="with --profile-npt: samples drawn every M steps")
     ap.add_argument("--profile-batched", action="store_true", help="time only the batched k-space evaluation")
+    ap.add_argument("--profile-water", action="store_true",
+                    help="run only the rigid-water NPT run (3000 molecules, FP64, --steps steps)")
     ap.add_argument("--profile-general", action="store_true",
                     help="time only the general-cell (triclinic) k-space path on the sheared slab")
     ap.add_argument("--skip-sweep", action="store_true", help="leave out the large-N precision and roofline sweep")
@@ -695,6 +745,13 @@ def main():
         import paper_2110_14362_gb300 as rbe
         torch.cuda.set_device(local)
         print(json.dumps({"metric": "large-N sweep", "sweep": run_sweep(rbe, steps=args.steps)}), flush=True)
+        return
+    if args.profile_water:
+        import torch
+        import paper_2110_14362_gb300 as rbe
+        torch.cuda.set_device(local)
+        print(json.dumps({"metric": "rigid-water NPT run", "water_npt": run_water(rbe, steps=args.steps,
+                                                                                  warmup=args.warmup)}), flush=True)
         return
     if args.profile_general:
         import torch
