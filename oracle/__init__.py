@@ -39,7 +39,7 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc into ``oracle/_build/liboracle.so`` and return its path."""
     os.makedirs(_BUILD, exist_ok=True)
     srcs = [s for s in (_SRC, _SRC_NPT, _SRC_SMP, _SRC_GEN, _SRC_FLX, _SRC_WAT) if os.path.exists(s)]
-    newest = max(os.path.getmtime(s) for s in srcs)
+    newest = max(os.path.getmtime(s) for s in srcs + [os.path.join(_HERE, "npt_params.h")])
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",

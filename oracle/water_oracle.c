@@ -44,18 +44,7 @@
 enum { WAT_OK = 0, WAT_EINVAL = 1, WAT_ENOMEM = 2, WAT_ESHAKE = 3 };
 #define FCONV 100.0
 
-/* the NPT oracle's parameters (npt_oracle.c); the water step uses the isotropic fields */
-typedef struct {
-    double dt, kT, P_ext, gamma, gamma_V, M_V, alpha, rc, qqr2e, lj_sigma, lj_eps, max_disp;
-    int32_t P, kspace, real, noise, barostat, pad;
-    uint64_t seed;
-    double M_cell[3];
-    double gamma0;
-    int32_t sampler, pad2;
-    int32_t* chain;
-    int32_t Ptilde, reuse;
-    int32_t* reuse_m;
-} orc_npt_params;
+#include "npt_params.h"
 
 typedef struct {
     double d_OH, d_HH; /* constraint lengths, A */
