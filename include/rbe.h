@@ -353,9 +353,10 @@ rbe_status rbe_npt_step(rbe_ctx ctx, rbe_system* sys, int32_t nsteps);
  * parameters acting between oxygens only.  Each molecule's centre of mass follows the isotropic
  * Langevin NPT equations (Sec. 3.2, splitting of Sec. 3.3) with the molecule's mass and total
  * force, the cell scaling the centres only; the internal motion is constrained: R^p/2 kicks the
- * internal momenta by (dt/2) 100 (F_i - m_i F/M), R/2 moves the offsets freely and SHAKE restores
- * the O-H, O-H and H-H distances (sweeps in that order until every |r^2 - d^2| <= tol d^2, its
- * displacement entering the momenta), O acts on every site (Philox stream 1 at the site index),
+ * internal momenta by (dt/2) 100 (F_i - m_i F/M), R/2 moves the offsets freely and the SHAKE
+ * equations restore the O-H, O-H and H-H distances (corrections along the old separations, solved by
+ * Newton's method on the three multipliers until every |r^2 - d^2| <= tol d^2; the displacement
+ * enters the momenta), O acts on every site (Philox stream 1 at the site index),
  * and after R^p/2, R/2 and O the momenta are projected onto the velocity constraints (RATTLE).
  * The barostat sees (sum_I |P_I|^2 / M_I / 100 + W_mol) / (3V), W_mol = W - sum_i F_i . d_i (d_i
  * the site's offset from its molecule's centre).  Forces: the context's RBE k-space over all sites
@@ -364,13 +365,14 @@ rbe_status rbe_npt_step(rbe_ctx ctx, rbe_system* sys, int32_t nsteps);
  * oxygens (FP64, whatever the context's precision; the k-space follows it).  Cell block as
  * rbe_npt_step's isotropic one (cell[4] = W_mol, cell[5] = the centres' 2K, cell[6] the molecular
  * P_ins), plus cell[25] = the exclusion energy.  Molecules are made whole from their oxygen by
- * the nearest image; sites are wrapped into the box after every step.  A molecule whose SHAKE
- * does not converge within shake_max_iter sweeps is flagged (RBE_ESTATE at the next rbe_sync). */
+ * the nearest image; after every step a molecule moves by the lattice vector that brings its
+ * oxygen into the box.  A molecule whose constraint solve does not converge within
+ * shake_max_iter iterations is flagged (RBE_ESTATE at the next rbe_sync). */
 typedef struct {
     double d_OH;          /* O-H distance, A */
     double d_HH;          /* H-H distance, A */
     double shake_tol;     /* relative tolerance of |r^2 - d^2| / d^2, > 0 */
-    int32_t shake_max_iter; /* sweeps per molecule and R/2 at most, >= 1 */
+    int32_t shake_max_iter; /* constraint-solve iterations per molecule and R/2 at most, >= 1 */
     int32_t pad;
 } rbe_water_params;
 

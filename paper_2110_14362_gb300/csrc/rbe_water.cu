@@ -30,48 +30,22 @@ constexpr int kWaterThreads = 128;  // molecules per block of the per-molecule k
 constexpr int kCellExcl = 25;       // cell block: the exclusion energy
 constexpr int kWaterHitCap = 64;    // buffered candidates per warp (< 32 buffered + 32 new)
 
-__device__ __constant__ int kWPa[3] = {0, 0, 1};
-__device__ __constant__ int kWPb[3] = {1, 2, 2};
+// the sites of constraint c: (0,1), (0,2), (1,2)
+__host__ __device__ constexpr int wpa(int c) { return c == 2 ? 1 : 0; }
+__host__ __device__ constexpr int wpb(int c) { return c == 0 ? 1 : 2; }
 
 // The molecule starting at site 3I made whole from its oxygen by the nearest image.
 __device__ __forceinline__ void w_whole(const double* __restrict__ pos, int64_t I, const double L[3],
                                         const double inv[3], double x[3][3])
 {
+    #pragma unroll
     for (int t = 0; t < 3; ++t) x[0][t] = pos[9 * I + t];
     for (int s = 1; s < 3; ++s)
+        #pragma unroll
         for (int t = 0; t < 3; ++t) {
             const double d = pos[9 * I + 3 * s + t] - x[0][t];
             x[s][t] = x[0][t] + (d - L[t] * rint(d * inv[t]));
         }
-}
-
-// SHAKE for one molecule: sweeps over (0,1), (0,2), (1,2), each moving its sites along their old
-// separation, g = (d^2 - |s|^2) / (2 (1/m_a + 1/m_b) s . s_old); stops after a sweep in which every
-// constraint was within tol d^2 before its correction.  Returns false when max_iter sweeps did
-// not get there.
-__device__ bool w_shake(double x[3][3], const double xo[3][3], const double m3[3], const rbe_water_params& wp)
-{
-    const double dd[3] = {wp.d_OH * wp.d_OH, wp.d_OH * wp.d_OH, wp.d_HH * wp.d_HH};
-    for (int it = 0; it < wp.shake_max_iter; ++it) {
-        bool done = true;
-        for (int c = 0; c < 3; ++c) {
-            const int a = kWPa[c], b = kWPb[c];
-            double s[3], so[3];
-            for (int t = 0; t < 3; ++t) {
-                s[t] = x[a][t] - x[b][t];
-                so[t] = xo[a][t] - xo[b][t];
-            }
-            const double diff = dd[c] - (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
-            if (fabs(diff) > wp.shake_tol * dd[c]) done = false;
-            const double g = diff / (2.0 * (1.0 / m3[a] + 1.0 / m3[b]) * (s[0] * so[0] + s[1] * so[1] + s[2] * so[2]));
-            for (int t = 0; t < 3; ++t) {
-                x[a][t] += g * so[t] / m3[a];
-                x[b][t] -= g * so[t] / m3[b];
-            }
-        }
-        if (done) return true;
-    }
-    return false;
 }
 
 __device__ __forceinline__ double det3(const double A[3][3])
@@ -80,93 +54,175 @@ __device__ __forceinline__ double det3(const double A[3][3])
            A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
 }
 
-// RATTLE's velocity stage: p_i += sum_c mu_c s_c (e_{i,a_c} - e_{i,b_c}), s_c = x_{a_c} - x_{b_c},
-// mu solving the 3x3 system that makes every (v_a - v_b) . s_c vanish (Cramer's rule).
-__device__ void w_project(double p[3][3], const double x[3][3], const double m3[3])
+// x = A^{-1} b by Cramer's rule with one reciprocal of det A.
+__device__ __forceinline__ void solve3(const double A[3][3], const double b[3], double x[3])
 {
-    double s[3][3];
-    for (int c = 0; c < 3; ++c)
-        for (int t = 0; t < 3; ++t) s[c][t] = x[kWPa[c]][t] - x[kWPb[c]][t];
-    double A[3][3], b[3];
-    for (int c = 0; c < 3; ++c) {
-        const int a = kWPa[c], bb = kWPb[c];
-        double dv = 0.0;
-        for (int t = 0; t < 3; ++t) dv += (p[a][t] / m3[a] - p[bb][t] / m3[bb]) * s[c][t];
-        b[c] = -dv;
-        for (int d = 0; d < 3; ++d) {
-            const double k = ((a == kWPa[d]) - (a == kWPb[d])) / m3[a] - ((bb == kWPa[d]) - (bb == kWPb[d])) / m3[bb];
-            A[c][d] = k * (s[c][0] * s[d][0] + s[c][1] * s[d][1] + s[c][2] * s[d][2]);
-        }
-    }
-    const double det = det3(A);
-    double mu[3];
+    const double id = 1.0 / det3(A);
+    #pragma unroll
     for (int k = 0; k < 3; ++k) {
         double B[3][3];
+        #pragma unroll
         for (int c = 0; c < 3; ++c)
+            #pragma unroll
             for (int d = 0; d < 3; ++d) B[c][d] = d == k ? b[c] : A[c][d];
-        mu[k] = det3(B) / det;
+        x[k] = det3(B) * id;
     }
+}
+
+// The change of (x_a - x_b) of constraint c per unit multiplier of constraint d, in units of
+// s_d: ((a_c == a_d) - (a_c == b_d))/m_{a_c} - ((b_c == a_d) - (b_c == b_d))/m_{b_c}.
+__device__ __forceinline__ double coupling(int c, int d, const double im[3])
+{
+    const int a = wpa(c), b = wpb(c);
+    return ((a == wpa(d)) - (a == wpb(d))) * im[a] - ((b == wpa(d)) - (b == wpb(d))) * im[b];
+}
+
+// The position constraints of one molecule after an unconstrained move from the constrained xo:
+// x_i <- x_i + sum_d lambda_d s_old,d (e_{i,a_d} - e_{i,b_d}) / m_i with lambda making every
+// |x_a - x_b|^2 = d^2, the equations SHAKE solves (corrections along the old separations).  Here by
+// Newton's method on lambda (each step an exact 3x3 solve, quadratic convergence from lambda = 0):
+// it stops once every |r^2 - d^2| <= tol d^2, at the root SHAKE's sweeps converge to.  Returns
+// false when max_iter iterations did not get there.
+__device__ bool w_shake(double x[3][3], const double xo[3][3], const double im[3], const rbe_water_params& wp)
+{
+    const double dd[3] = {wp.d_OH * wp.d_OH, wp.d_OH * wp.d_OH, wp.d_HH * wp.d_HH};
+    double so[3][3], K[3][3];
+    #pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        #pragma unroll
+        for (int t = 0; t < 3; ++t) so[c][t] = xo[wpa(c)][t] - xo[wpb(c)][t];
+        #pragma unroll
+        for (int d = 0; d < 3; ++d) K[c][d] = coupling(c, d, im);
+    }
+    for (int it = 0; it < wp.shake_max_iter; ++it) {
+        double s[3][3], g[3];
+        bool done = true;
+        #pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            #pragma unroll
+            for (int t = 0; t < 3; ++t) s[c][t] = x[wpa(c)][t] - x[wpb(c)][t];
+            g[c] = s[c][0] * s[c][0] + s[c][1] * s[c][1] + s[c][2] * s[c][2] - dd[c];
+            if (fabs(g[c]) > wp.shake_tol * dd[c]) done = false;
+        }
+        if (done) return true;
+        double J[3][3], dl[3], rhs[3] = {-g[0], -g[1], -g[2]};
+        #pragma unroll
+        for (int c = 0; c < 3; ++c)
+            #pragma unroll
+            for (int d = 0; d < 3; ++d)
+                J[c][d] = 2.0 * K[c][d] * (s[c][0] * so[d][0] + s[c][1] * so[d][1] + s[c][2] * so[d][2]);
+        solve3(J, rhs, dl);
+        #pragma unroll
+        for (int d = 0; d < 3; ++d)
+            #pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                x[wpa(d)][t] += dl[d] * so[d][t] * im[wpa(d)];
+                x[wpb(d)][t] -= dl[d] * so[d][t] * im[wpb(d)];
+            }
+    }
+    return false;
+}
+
+// RATTLE's velocity stage: p_i += sum_c mu_c s_c (e_{i,a_c} - e_{i,b_c}), s_c = x_{a_c} - x_{b_c},
+// mu solving the 3x3 system that makes every (v_a - v_b) . s_c vanish (Cramer's rule).
+__device__ void w_project(double p[3][3], const double x[3][3], const double im[3])
+{
+    double s[3][3];
+    #pragma unroll
     for (int c = 0; c < 3; ++c)
+        #pragma unroll
+        for (int t = 0; t < 3; ++t) s[c][t] = x[wpa(c)][t] - x[wpb(c)][t];
+    double A[3][3], b[3], mu[3];
+    #pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int a = wpa(c), bb = wpb(c);
+        double dv = 0.0;
+        #pragma unroll
+        for (int t = 0; t < 3; ++t) dv += (p[a][t] * im[a] - p[bb][t] * im[bb]) * s[c][t];
+        b[c] = -dv;
+        #pragma unroll
+        for (int d = 0; d < 3; ++d)
+            A[c][d] = coupling(c, d, im) * (s[c][0] * s[d][0] + s[c][1] * s[d][1] + s[c][2] * s[d][2]);
+    }
+    solve3(A, b, mu);
+    #pragma unroll
+    for (int c = 0; c < 3; ++c)
+        #pragma unroll
         for (int t = 0; t < 3; ++t) {
-            p[kWPa[c]][t] += mu[c] * s[c][t];
-            p[kWPb[c]][t] -= mu[c] * s[c][t];
+            p[wpa(c)][t] += mu[c] * s[c][t];
+            p[wpb(c)][t] -= mu[c] * s[c][t];
         }
 }
 
 // R^p/2 of one molecule: the centre's exact flow P <- P a + 100 F b, the internal momenta kicked by
 // 100 h (F_i - m_i F / M), then the projection.
-__device__ void w_kick(double p[3][3], const double F[3][3], const double x[3][3], const double m3[3], double a,
-                       double b, double h)
+__device__ void w_kick(double p[3][3], const double F[3][3], const double x[3][3], const double m3[3],
+                       const double im[3], double a, double b, double h)
 {
     const double M = m3[0] + m3[1] + m3[2];
     double P[3] = {0.0, 0.0, 0.0}, Ft[3] = {0.0, 0.0, 0.0};
+    #pragma unroll
     for (int k = 0; k < 3; ++k)
+        #pragma unroll
         for (int t = 0; t < 3; ++t) {
             P[t] += p[k][t];
             Ft[t] += F[k][t];
         }
     double dP[3];
+    #pragma unroll
     for (int t = 0; t < 3; ++t) dP[t] = P[t] * a + kFConv * Ft[t] * b - P[t];
+    #pragma unroll
     for (int k = 0; k < 3; ++k)
+        #pragma unroll
         for (int t = 0; t < 3; ++t) p[k][t] += kFConv * h * (F[k][t] - m3[k] * Ft[t] / M) + (m3[k] / M) * dP[t];
-    w_project(p, x, m3);
+    w_project(p, x, im);
 }
 
 // R/2 of one molecule: the centre R <- R + R (a - 1) + cap((P/M) b), the offsets moved by h (p/m
 // - P/M) and SHAKEn, the SHAKE displacement added to the momenta as m dd / h, then the projection
 // at the new positions.  Returns false when SHAKE did not converge.
-__device__ bool w_drift(double x[3][3], double p[3][3], const double m3[3], double am1, double b, double h, double cap,
-                        const rbe_water_params& wp)
+__device__ bool w_drift(double x[3][3], double p[3][3], const double m3[3], const double im[3], double am1, double b,
+                        double h, double cap, const rbe_water_params& wp)
 {
     const double M = m3[0] + m3[1] + m3[2];
     double R[3], P[3] = {0.0, 0.0, 0.0}, d[3][3], dn[3][3], ds[3][3];
+    #pragma unroll
     for (int t = 0; t < 3; ++t) R[t] = (m3[0] * x[0][t] + m3[1] * x[1][t] + m3[2] * x[2][t]) / M;
+    #pragma unroll
     for (int k = 0; k < 3; ++k)
+        #pragma unroll
         for (int t = 0; t < 3; ++t) {
             P[t] += p[k][t];
             d[k][t] = x[k][t] - R[t];
         }
     double D[3];
+    #pragma unroll
     for (int t = 0; t < 3; ++t) D[t] = (P[t] / M) * b;
     if (cap > 0.0) {
         const double len = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
         if (len > cap)
+            #pragma unroll
             for (int t = 0; t < 3; ++t) D[t] *= cap / len;
     }
     double Rn[3];
+    #pragma unroll
     for (int t = 0; t < 3; ++t) Rn[t] = R[t] + R[t] * am1 + D[t];
+    #pragma unroll
     for (int k = 0; k < 3; ++k)
+        #pragma unroll
         for (int t = 0; t < 3; ++t) {
-            dn[k][t] = d[k][t] + h * (p[k][t] / m3[k] - P[t] / M);
+            dn[k][t] = d[k][t] + h * (p[k][t] * im[k] - P[t] / M);
             ds[k][t] = dn[k][t];
         }
-    const bool ok = w_shake(ds, d, m3, wp);
+    const bool ok = w_shake(ds, d, im, wp);
+    #pragma unroll
     for (int k = 0; k < 3; ++k)
+        #pragma unroll
         for (int t = 0; t < 3; ++t) {
             p[k][t] += m3[k] * (ds[k][t] - dn[k][t]) / h;
             x[k][t] = Rn[t] + ds[k][t];
         }
-    w_project(p, x, m3);
+    w_project(p, x, im);
     return ok;
 }
 
@@ -181,8 +237,10 @@ k_water_whole(int64_t Nmol, double* __restrict__ pos, const double* __restrict__
     const double inv[3] = {1.0 / L[0], 1.0 / L[1], 1.0 / L[2]};
     double x[3][3];
     w_whole(pos, I, L, inv, x);
+    #pragma unroll
     for (int t = 0; t < 3; ++t) {
         const double sh = L[t] * floor(x[0][t] * inv[t]);
+        #pragma unroll
         for (int k = 0; k < 3; ++k) pos[9 * I + 3 * k + t] = x[k][t] - sh;
     }
 }
@@ -201,24 +259,31 @@ k_water_drift(int64_t Nmol, double* __restrict__ pos, double* __restrict__ mom, 
     const double m3[3] = {mass[3 * I], mass[3 * I + 1], mass[3 * I + 2]};
     double x[3][3], p[3][3], F[3][3];
     w_whole(pos, I, c.L, c.invL, x);
+    #pragma unroll
     for (int k = 0; k < 3; ++k)
+        #pragma unroll
         for (int t = 0; t < 3; ++t) {
             p[k][t] = mom[9 * I + 3 * k + t];
             F[k][t] = force[9 * I + 3 * k + t];
         }
-    w_kick(p, F, x, m3, c.a1[0], c.b1[0], h);
-    bool ok = w_drift(x, p, m3, c.a2m1[0], c.b2[0], h, c.half_cap, wp);
+    const double im[3] = {1.0 / m3[0], 1.0 / m3[1], 1.0 / m3[2]};
+    w_kick(p, F, x, m3, im, c.a1[0], c.b1[0], h);
+    bool ok = w_drift(x, p, m3, im, c.a2m1[0], c.b2[0], h, c.half_cap, wp);
+    #pragma unroll
     for (int k = 0; k < 3; ++k) {
         double z[4] = {0.0, 0.0, 0.0, 0.0};
         if (c.noise) npt_normals(seed, 1u, step, (uint32_t)(3 * I + k), z);
         const double s = c.sog * sqrt(m3[k]);
+        #pragma unroll
         for (int t = 0; t < 3; ++t) p[k][t] = p[k][t] * c.g + s * z[t];
     }
-    w_project(p, x, m3);
-    ok = w_drift(x, p, m3, c.a3m1[0], c.b3[0], h, c.half_cap, wp) && ok;
+    w_project(p, x, im);
+    ok = w_drift(x, p, m3, im, c.a3m1[0], c.b3[0], h, c.half_cap, wp) && ok;
     if (!ok) atomicOr(status, kStatusShake);
+    #pragma unroll
     for (int t = 0; t < 3; ++t) {
         const double sh = c.L[t] * floor(x[0][t] * c.invL[t]);
+        #pragma unroll
         for (int k = 0; k < 3; ++k) {
             pos[9 * I + 3 * k + t] = x[k][t] - sh;
             mom[9 * I + 3 * k + t] = p[k][t];
@@ -231,25 +296,28 @@ k_water_drift(int64_t Nmol, double* __restrict__ pos, double* __restrict__ mom, 
 // of the current box: one warp per site in cell order; the lanes set up the 18 row segments of
 // the neighbouring cells (an axis with fewer than 3 cells visits each of its cells once) and
 // stride over their slots; the separation is the nearest image per pair (sites may sit up to a
-// bond outside the box).  A candidate of the same molecule (site index / 3) is skipped; LJ acts
-// between oxygens (site index divisible by 3).  Hits go to a per-warp buffer in ballot order and
-// are evaluated 32 at a time, one per lane; lane sums through a fixed shuffle tree.  Each pair is
+// bond outside the box).  The search runs on the FP32 packed positions with rc plus a margin above
+// their rounding; the hits (slots) go to a per-warp buffer in ballot order and are evaluated 32 at a
+// time, one per lane, in FP64 from the FP64 packed positions with the exact cutoff.  A hit of the
+// same molecule (site index / 3) is skipped; LJ acts between oxygens (site index divisible by 3).
+// Lane sums through a fixed shuffle tree.  Each pair is
 // visited from both ends: energies and the virial take half.  Per-block partials {W_r, E_coul,
 // E_lj} at slots 1..3 (the isotropic layout).  A box beyond the cell arrays leaves F_r = 0.
 __global__ void __launch_bounds__(kPairWarps * 32, kPairBlocksPerSM64)
 k_water_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, const int* __restrict__ cid,
              const int* __restrict__ cnt, const int* __restrict__ start, const int* __restrict__ sorted,
-             const double4_32a* __restrict__ spos64, double* __restrict__ Fr, double* __restrict__ partials)
+             const float4* __restrict__ spos32, const double4_32a* __restrict__ spos64, double* __restrict__ Fr,
+             double* __restrict__ partials)
 {
-    struct Hit {
-        double x, y, z, q;
-        int lj;
-    };
-    __shared__ Hit hits[kPairWarps][kWaterHitCap];
+    __shared__ int hits[kPairWarps][kWaterHitCap];  // slots of candidates within the FP32 search radius
     __shared__ double red[3][kPairWarps];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nc[3] = {cc->nc[0], cc->nc[1], cc->nc[2]};
     const double L[3] = {cc->L[0], cc->L[1], cc->L[2]}, inv[3] = {cc->invL[0], cc->invL[1], cc->invL[2]};
+    const float Lf[3] = {cc->Lf[0], cc->Lf[1], cc->Lf[2]}, invf[3] = {cc->invLf[0], cc->invLf[1], cc->invLf[2]};
+    // FP32 search radius: rc plus 2^-16 l_max, far above the FP32 rounding of a separation; the
+    // exact cutoff is applied in FP64
+    const float pass = cc->pass64;
     double wsum = 0.0, ecsum = 0.0, elsum = 0.0;
     if (cc->ncell < 0) {
         for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < 3 * N; j += (int64_t)gridDim.x * blockDim.x)
@@ -259,6 +327,7 @@ k_water_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, c
         for (int u = blockIdx.x * kPairWarps + wib; u < (int)N; u += nwarps) {
             const int i = sorted[u];
             const double4_32a me = spos64[u];
+            const float4 me32 = spos32[u];
             const int mol_i = i / 3;
             const bool oxy_i = i % 3 == 0;
             int lo = 0, hi = 0;
@@ -297,38 +366,42 @@ k_water_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, c
             int nh = 0;
             auto evaluate = [&](int count) {
                 if (lane >= count) return;
-                const Hit ht = hits[wib][lane];
-                const double r2 = ht.x * ht.x + ht.y * ht.y + ht.z * ht.z;
+                const int sj = hits[wib][lane];
+                const int j = sorted[sj];
+                if (j / 3 == mol_i) return;  // the same molecule (the site itself included)
+                const double4_32a o = spos64[sj];
+                double d[3] = {o.x - me.x, o.y - me.y, o.z - me.z};
+                #pragma unroll
+                for (int t = 0; t < 3; ++t) d[t] -= L[t] * rint(d[t] * inv[t]);
+                const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (!(r2 < pc.rc2)) return;
                 const double r = sqrt(r2), inv_r = 1.0 / r, inv_r2 = inv_r * inv_r;
-                const double coul = pc.qk * me.w * ht.q * inv_r;
+                const double coul = pc.qk * me.w * o.w * inv_r;
                 const double er = erfc(pc.sa * r);
                 ec += coul * er;
                 double f = coul * (er + pc.two_sa_pi * r * exp(-pc.a * r2)) * inv_r2;
-                if (ht.lj && pc.lj) {
+                if (oxy_i && j % 3 == 0 && pc.lj) {
                     const double sr2 = pc.s2 * inv_r2, sr6 = sr2 * sr2 * sr2;
                     el += pc.e4 * (sr6 * sr6 - sr6);
                     f += pc.e24 * (2.0 * sr6 * sr6 - sr6) * inv_r2;
                 }
-                fx -= f * ht.x;
-                fy -= f * ht.y;
-                fz -= f * ht.z;
+                fx -= f * d[0];
+                fy -= f * d[1];
+                fz -= f * d[2];
                 w += f * r2;
             };
             for (int g = 0; g < 18; ++g) {
                 const int glo = __shfl_sync(0xffffffffu, lo, g), ghi = __shfl_sync(0xffffffffu, hi, g);
                 for (int s0 = glo; s0 < ghi; s0 += 32) {  // the same trip count on every lane
                     const int sl = s0 + lane;
-                    const int sj = sl < ghi ? sl : glo;
-                    const int j = sorted[sj];
-                    const double4_32a o = spos64[sj];
-                    double d[3] = {o.x - me.x, o.y - me.y, o.z - me.z};
-                    for (int t = 0; t < 3; ++t) d[t] -= L[t] * rint(d[t] * inv[t]);
-                    const bool hit = sl < ghi && j / 3 != mol_i && d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < pc.rc2;
+                    const float4 o = spos32[sl < ghi ? sl : glo];
+                    float dx = o.x - me32.x, dy = o.y - me32.y, dz = o.z - me32.z;
+                    dx -= Lf[0] * rintf(dx * invf[0]);
+                    dy -= Lf[1] * rintf(dy * invf[1]);
+                    dz -= Lf[2] * rintf(dz * invf[2]);
+                    const bool hit = sl < ghi && sl != u && dx * dx + dy * dy + dz * dz < pass;
                     const unsigned m = __ballot_sync(0xffffffffu, hit);
-                    if (hit) {
-                        const int slot = nh + __popc(m & ((1u << lane) - 1u));
-                        hits[wib][slot] = Hit{d[0], d[1], d[2], o.w, (oxy_i && j % 3 == 0) ? 1 : 0};
-                    }
+                    if (hit) hits[wib][nh + __popc(m & ((1u << lane) - 1u))] = sl;
                     nh += __popc(m);
                     if (nh >= 32) {
                         __syncwarp();
@@ -400,7 +473,9 @@ k_water_finish(int64_t Nmol, double* __restrict__ mom, double* __restrict__ forc
         const double m3[3] = {mass[3 * I], mass[3 * I + 1], mass[3 * I + 2]};
         double x[3][3], F[3][3], p[3][3];
         w_whole(pos, I, L, inv, x);
+        #pragma unroll
         for (int k = 0; k < 3; ++k)
+            #pragma unroll
             for (int t = 0; t < 3; ++t) {
                 const int64_t j = 9 * I + 3 * k + t;
                 F[k][t] = (prm.kspace ? prm.qqr2e * Fk[j] : 0.0) + (prm.real ? Fr[j] : 0.0);
@@ -408,14 +483,17 @@ k_water_finish(int64_t Nmol, double* __restrict__ mom, double* __restrict__ forc
             }
         if (prm.real) {
             const double sa = sqrt(alpha), tsp = 2.0 * sqrt(alpha / kPi);
+            #pragma unroll
             for (int cp = 0; cp < 3; ++cp) {
-                const int a = kWPa[cp], b = kWPb[cp];
+                const int a = wpa(cp), b = wpb(cp);
                 double d[3];
+                #pragma unroll
                 for (int t = 0; t < 3; ++t) d[t] = x[b][t] - x[a][t];
                 const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2], r = sqrt(r2);
                 const double qq = prm.qqr2e * q[3 * I + a] * q[3 * I + b], ef = erf(sa * r);
                 const double f = qq * (tsp * exp(-alpha * r2) / r - ef / r2) / r;
                 ex -= qq * ef / r;
+                #pragma unroll
                 for (int t = 0; t < 3; ++t) {
                     F[b][t] += f * d[t];
                     F[a][t] -= f * d[t];
@@ -425,19 +503,27 @@ k_water_finish(int64_t Nmol, double* __restrict__ mom, double* __restrict__ forc
         }
         const double M = m3[0] + m3[1] + m3[2];
         double R[3];
+        #pragma unroll
         for (int t = 0; t < 3; ++t) R[t] = (m3[0] * x[0][t] + m3[1] * x[1][t] + m3[2] * x[2][t]) / M;
+        #pragma unroll
         for (int k = 0; k < 3; ++k)
+            #pragma unroll
             for (int t = 0; t < 3; ++t) {
                 wc -= F[k][t] * (x[k][t] - R[t]);
                 force[9 * I + 3 * k + t] = F[k][t];
             }
         if (do_kick) {
-            w_kick(p, F, x, m3, c.a4[0], c.b4[0], 0.5 * prm.dt);
+            const double im[3] = {1.0 / m3[0], 1.0 / m3[1], 1.0 / m3[2]};
+            w_kick(p, F, x, m3, im, c.a4[0], c.b4[0], 0.5 * prm.dt);
+            #pragma unroll
             for (int k = 0; k < 3; ++k)
+                #pragma unroll
                 for (int t = 0; t < 3; ++t) mom[9 * I + 3 * k + t] = p[k][t];
         }
         double P[3] = {0.0, 0.0, 0.0};
+        #pragma unroll
         for (int k = 0; k < 3; ++k)
+            #pragma unroll
             for (int t = 0; t < 3; ++t) P[t] += p[k][t];
         k2 = (P[0] * P[0] + P[1] * P[1] + P[2] * P[2]) / M * (1.0 / kFConv);
     }
@@ -558,7 +644,7 @@ static rbe_status water_forces(rbe_ctx ctx, rbe_system* sys, int do_kick)
         if ((st = launch_cell_list(ctx, N, sys->pos, sys->charge, nullptr, true)) != RBE_OK) return st;
         const PairConst pc = make_pair_const(prm.rc, ctx->alpha, prm.qqr2e, prm.lj_sigma, prm.lj_eps);
         k_water_pair<<<nbp, kPairWarps * 32, 0, s>>>(N, static_cast<const CellConsts*>(b.cellc), pc, b.cid, b.cnt,
-                                                     b.start, b.sorted, b.spos64, b.Fr, b.partials);
+                                                     b.start, b.sorted, b.spos32, b.spos64, b.Fr, b.partials);
         if ((st = water_check(ctx, "k_water_pair")) != RBE_OK) return st;
     }
     const int nbm = (int)std::max<int64_t>(1, (Nmol + kWaterThreads - 1) / kWaterThreads);
