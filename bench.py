@@ -407,13 +407,15 @@ def run_npt_single(rbe, sizes, steps):
 WATER_MASS = (15.9994, 1.008, 1.008)
 
 
-def run_water(rbe, steps=1000, warmup=20):
+def run_water(rbe, steps=1000, warmup=20, alpha=None, barostat=1):
     """The plain-method rigid-water NPT run: 3000 molecules (O -0.8476, H +0.4238, O-H 1 A,
     H-O-H 109.47 deg, LJ O-O 3.166 A / 0.650 kJ/mol) at random orientations on a jittered lattice
     at 1 g/cm^3 (`inputs.water`), alpha = 0.25, rc = 10 A, P = 100, FP64, Langevin isotropic NPT at
     300 K and 1 bar, dt = 1 fs, a 0.05 A cap on the centres' peculiar displacement per step (the
     random orientations overlap at the start).  ms per step by CUDA events over `steps` steps after
-    `warmup`; density, molecular pressure and the largest bond error at the end."""
+    `warmup`; density, molecular pressure, temperature (6 degrees of freedom per molecule) and the
+    largest bond error at the end.  alpha (default: the configuration's 0.25) and barostat (0: fixed
+    box) can be changed to study the run."""
     import torch
     s = inputs.water(3000)
     box = np.asarray(s.box, dtype=np.float64)
@@ -424,10 +426,11 @@ def run_water(rbe, steps=1000, warmup=20):
     V0 = float(np.prod(box))
     prm = rbe.NptParams(dt=0.001, kT=KB * 300.0, P_ext=1.0 * BAR, gamma=10.0, gamma_V=2.0,
                         M_V=rbe.piston_mass(0.5, 4.5e-5 / BAR, V0), rc=10.0, qqr2e=1389.35457644382,
-                        lj_sigma=3.166, lj_eps=0.650, max_disp=0.05, kspace=1, real=1, noise=1, barostat=1)
+                        lj_sigma=3.166, lj_eps=0.650, max_disp=0.05, kspace=1, real=1, noise=1, barostat=barostat)
     stream = torch.cuda.current_stream()
     dev = torch.device("cuda", torch.cuda.current_device())
-    with rbe.Context(box, s.alpha, s.P, 2024, rbe.RBE_FP64, stream=stream.cuda_stream) as ctx:
+    a = s.alpha if alpha is None else alpha
+    with rbe.Context(box, a, s.P, 2024, rbe.RBE_FP64, stream=stream.cuda_stream) as ctx:
         rep = rbe.WaterReplica(np.asarray(s.pos), mom, np.asarray(s.q), m, box, prm, dev)
         rep.init(ctx, batch=0)
         rep.step(ctx, warmup)
@@ -442,8 +445,10 @@ def run_water(rbe, steps=1000, warmup=20):
     mol = r.reshape(-1, 3, 3)
     bond = float(np.abs(np.linalg.norm(mol[:, 1:] - mol[:, :1], axis=2) - 1.0).max())
     V = float(np.prod(L))
-    return {"molecules": n, "sites": 3 * n, "alpha": s.alpha, "P": s.P, "rc": 10.0, "precision": "fp64",
-            "steps": steps, "warmup": warmup, "ms_per_step": ms, "steps_per_s": 1e3 / ms,
+    T = float(np.sum(p ** 2 / m[:, None]) / 100.0 / (6 * n * KB))
+    return {"molecules": n, "sites": 3 * n, "alpha": a, "P": s.P, "rc": 10.0, "precision": "fp64",
+            "barostat": barostat, "steps": steps, "warmup": warmup, "ms_per_step": ms, "steps_per_s": 1e3 / ms,
+            "T_K": T,
             "site_pair_evals_per_s": 3 * n * s.P / (ms * 1e-3),
             "density_g_cm3": n * 18.01528 / (0.602214076 * V), "P_ins_bar": float(cell[6]) / BAR,
             "max_bond_error_A": bond}
@@ -718,6 +723,9 @@ def main():
     ap.add_argument("--profile-batched", action="store_true", help="time only the batched k-space evaluation")
     ap.add_argument("--profile-water", action="store_true",
                     help="run only the rigid-water NPT run (3000 molecules, FP64, --steps steps)")
+    ap.add_argument("--water-alpha", type=float, default=None, help="with --profile-water: another alpha")
+    ap.add_argument("--water-barostat", type=int, default=1, choices=(0, 1),
+                    help="with --profile-water: 0 keeps the box fixed")
     ap.add_argument("--profile-general", action="store_true",
                     help="time only the general-cell (triclinic) k-space path on the sheared slab")
     ap.add_argument("--skip-sweep", action="store_true", help="leave out the large-N precision and roofline sweep")
@@ -750,8 +758,9 @@ def main():
         import torch
         import paper_2110_14362_gb300 as rbe
         torch.cuda.set_device(local)
-        print(json.dumps({"metric": "rigid-water NPT run", "water_npt": run_water(rbe, steps=args.steps,
-                                                                                  warmup=args.warmup)}), flush=True)
+        print(json.dumps({"metric": "rigid-water NPT run",
+                          "water_npt": run_water(rbe, steps=args.steps, warmup=args.warmup, alpha=args.water_alpha,
+                                                 barostat=args.water_barostat)}), flush=True)
         return
     if args.profile_general:
         import torch
