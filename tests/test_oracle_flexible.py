@@ -133,3 +133,34 @@ def test_free_particles_keep_the_canonical_momentum():
         assert np.abs(st.h - h).max() > 0.1
         out.append(np.abs(st.p @ st.h - pi0).max() / np.abs(pi0).max())
     assert out[0] < 1e-5 and out[1] < out[0] / 3.5, out
+
+
+@pytest.mark.slow
+def test_cell_momenta_equipartition():
+    """Ideal gas (no forces) with friction and noise on every cell entry: at stationarity each of the
+    nine cell momenta is Gaussian with <(p^h_te)^2> = kT M_te (the extended energy is separable in
+    p^h), whatever the cell does; masses 10x apart pin the amplitude and the mass of every entry's
+    noise, the off-diagonal ones included."""
+    rng = np.random.default_rng(12)
+    n = 8
+    L = 20.0
+    h = np.diag([L, L, L])
+    M = np.array([[1.0, 2.0, 4.0], [6.0, 10.0, 1.5], [3.0, 0.8, 5.0]])
+    pos = rng.random((n, 3)) * L
+    p = rng.normal(size=(n, 3)) * np.sqrt(KT * 100 * 20.0)
+    prm = oracle.flex_params(dt=0.002, gamma=5.0, gamma_h=20.0, noise=1, kspace=0, real=0, M=M, chi=2.0,
+                             P_ext=(n + 1) * KT / L ** 3, seed=31)
+    st = oracle.FlexState(pos, p, np.zeros(n), np.full(n, 20.0), h)
+    oracle.flex_forces(st, 0, prm)
+    oracle.flex_run(st, 0, 2000, prm)
+    acc = np.zeros((3, 3))
+    nblk, per = 40, 1000
+    blocks = np.zeros((nblk, 3, 3))
+    for b in range(nblk):
+        for k in range(per):
+            oracle.flex_step(st, 2000 + b * per + k, prm)
+            blocks[b] += st.ph ** 2
+        blocks[b] /= per * KT * M
+    mean = blocks.mean(0)
+    se = blocks.std(0, ddof=1) / np.sqrt(nblk)
+    assert np.all(np.abs(mean - 1.0) < 4 * se + 0.03), (mean, se)
