@@ -275,3 +275,34 @@ def test_flex_rejects_bad_input():
         rep.step(ctx, 2)
         ctx.sync()
         assert torch.isfinite(rep.pos).all()
+
+
+def test_flex_graph_replay_equals_direct_steps():
+    """One step captured in a CUDA graph and replayed three times ends bit for bit where three
+    direct steps end (the step index lives on the device; every sum runs in a fixed order)."""
+    import torch
+    pos, mom, q, m, h = _system((8, 8, 9), (0.2, -0.15, 0.1))
+    prm, _, ph = _params(h, 6.0, skin=1.0)
+    dev = cuda_device()
+    out = []
+    for use_graph in (False, True):
+        s = torch.cuda.Stream()
+        with rbe.Context(np.diag(h), ALPHA, P, SEED, rbe.RBE_FP32_PHASE, stream=s.cuda_stream) as ctx:
+            rep = rbe.FlexReplica(pos, mom, q, m, h, prm, dev, step=0, ph=ph)
+            rep.init(ctx, batch=0)
+            ctx.sync()
+            if use_graph:
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+                    rep.step(ctx, 1)
+                for _ in range(3):
+                    g.replay()
+                torch.cuda.synchronize()
+            else:
+                rep.step(ctx, 3)
+            ctx.sync()
+            out.append(rep.state())
+    a, b = out
+    assert b["step"] == 3
+    for k in ("r", "p", "F", "h", "ph", "W"):
+        assert np.array_equal(a[k], b[k]), k

@@ -175,3 +175,34 @@ def test_water_rejects_bad_input():
         rep.step(ctx, 2)
         ctx.sync()
         assert torch.isfinite(rep.pos).all()
+
+
+def test_water_graph_replay_equals_direct_steps():
+    """One water step captured in a CUDA graph and replayed three times ends bit for bit where three
+    direct steps end."""
+    import torch
+    L = _box_1gcc(64)
+    pos, mom, q, m, box = _waters(4, L, 3)
+    prm, _ = _params(L, 6.0)
+    dev = cuda_device()
+    out = []
+    for use_graph in (False, True):
+        s = torch.cuda.Stream()
+        with rbe.Context(box, ALPHA, P, SEED, rbe.RBE_FP64, stream=s.cuda_stream) as ctx:
+            rep = rbe.WaterReplica(pos, mom, q, m, box, prm, dev)
+            rep.init(ctx, batch=0)
+            ctx.sync()
+            if use_graph:
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+                    rep.step(ctx, 1)
+                for _ in range(3):
+                    g.replay()
+                torch.cuda.synchronize()
+            else:
+                rep.step(ctx, 3)
+            ctx.sync()
+            out.append(rep.state())
+    (r1, p1, F1, L1, c1), (r2, p2, F2, L2, c2) = out
+    assert np.array_equal(r1, r2) and np.array_equal(p1, p2) and np.array_equal(F1, F2)
+    assert np.array_equal(c1, c2)
