@@ -306,3 +306,26 @@ def test_flex_graph_replay_equals_direct_steps():
     assert b["step"] == 3
     for k in ("r", "p", "F", "h", "ph", "W"):
         assert np.array_equal(a[k], b[k]), k
+
+
+def test_flex_cell_leaving_the_prepared_range_is_reported():
+    """A cell edge driven down at 1000 A/ps (a light mass on h_xx; no interactions, so nothing
+    pushes back, but the real-space cell list still runs) falls below 2 rc within a few steps: the
+    step flags it and the next sync reports RBE_ESTATE (no fault: the cell list keeps at least one
+    cell per axis and every index in range)."""
+    pos, mom, q, m, h = _system((6, 6, 7), (0.15, -0.1, 0.12))
+    M = _masses(h)
+    M[0, 0] = 0.01
+    prm, _, _ = _params(h, 5.0, M=M, noise=0, lj_eps=0.0, qqr2e=0.0, kspace=0)
+    ph = np.zeros((3, 3))
+    ph[0, 0] = -1000.0 * M[0, 0]
+    dev = cuda_device()
+    with rbe.Context(np.diag(h), ALPHA, P, SEED, rbe.RBE_FP64) as ctx:
+        rep = rbe.FlexReplica(pos, mom, q, m, h, prm, dev, ph=ph)
+        rep.init(ctx)
+        rep.step(ctx, 4)
+        with pytest.raises(rbe.RBEError) as e:
+            ctx.sync()
+        assert e.value.status == rbe.RBE_ESTATE
+        st = rep.state()
+        assert st["h"][0, 0] < 12.0 and np.isfinite(st["r"]).all()

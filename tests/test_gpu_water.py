@@ -206,3 +206,23 @@ def test_water_graph_replay_equals_direct_steps():
     (r1, p1, F1, L1, c1), (r2, p2, F2, L2, c2) = out
     assert np.array_equal(r1, r2) and np.array_equal(p1, p2) and np.array_equal(F1, F2)
     assert np.array_equal(c1, c2)
+
+
+def test_water_unconverged_constraints_are_reported():
+    """A constraint solve limited to one iteration cannot converge: the step flags it, the next
+    sync reports RBE_ESTATE, and the context runs a good system afterwards."""
+    L = _box_1gcc(64)
+    pos, mom, q, m, box = _waters(4, L, 2)
+    prm, _ = _params(L, 6.0)
+    dev = cuda_device()
+    with rbe.Context(box, ALPHA, P, SEED, rbe.RBE_FP64) as ctx:
+        rep = rbe.WaterReplica(pos, mom, q, m, box, prm, dev, wp=rbe.water_params(shake_max_iter=1))
+        rep.init(ctx)
+        rep.step(ctx, 1)
+        with pytest.raises(rbe.RBEError) as e:
+            ctx.sync()
+        assert e.value.status == rbe.RBE_ESTATE and "SHAKE" in str(e.value)
+        rep = rbe.WaterReplica(pos, mom, q, m, box, prm, dev)
+        rep.init(ctx)
+        rep.step(ctx, 2)
+        ctx.sync()
