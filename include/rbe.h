@@ -538,7 +538,8 @@ typedef struct {
                             counts N*196 + 12*C + (P+1)*32768 + 4 MiB bytes (state, NPT scratch,
                             C = prod_t floor(2 l_t / rc) cells, tables), plus N*(4*cap + 20) with a
                             neighbour list (cap = 2 x the expected neighbours within rc + skin, + 64,
-                            rounded up to 32) */
+                            rounded up to 32), plus 128 (P + ptilde) + 16 reuse (P + ptilde) for the
+                            frequency buffers (the reuse term when reuse > 1) */
     int32_t use_graphs;  /* 1: replay a captured graph per chunk; 0: launch the steps directly */
     int32_t pad;
 } rbe_server_config;
@@ -556,6 +557,11 @@ typedef struct {
     int32_t pad;
     rbe_npt_params params;
     double pc[3];          /* initial cell momenta of barostats 2 and 3 (cell[12..14]) */
+    int32_t sampler;       /* rbe_sampler of this replica's frequencies (rbe_set_sampler) */
+    int32_t ptilde;        /* >= 0: a separate pressure batch (rbe_set_pressure_batch) */
+    int32_t reuse;         /* samples drawn every `reuse` steps (rbe_set_sample_reuse, <= 1024); 0 or 1:
+                              every step; excluded with the Metropolis--Hastings sampler */
+    int32_t pad2;
 } rbe_request;
 
 rbe_status rbe_server_create(const rbe_server_config* cfg, rbe_server* out);

@@ -116,7 +116,9 @@ class Request(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("pos", ctypes.c_void_p), ("mom", ctypes.c_void_p),
                 ("charge", ctypes.c_void_p), ("mass", ctypes.c_void_p), ("box", ctypes.c_double * 3),
                 ("pV", ctypes.c_double), ("seed", ctypes.c_uint64), ("nsteps", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("params", NptParams), ("pc", ctypes.c_double * 3)]
+                ("pad", ctypes.c_int32), ("params", NptParams), ("pc", ctypes.c_double * 3),
+                ("sampler", ctypes.c_int32), ("ptilde", ctypes.c_int32), ("reuse", ctypes.c_int32),
+                ("pad2", ctypes.c_int32)]
 
 # (name, restype, argtypes) of every exported symbol
 SIGNATURES = [
@@ -581,13 +583,14 @@ class Server:
             pass
 
     def submit(self, pos, mom, charge, mass, box, params: NptParams, seed: int, nsteps: int, pV: float = 0.0,
-               pc=(0.0, 0.0, 0.0)):
+               pc=(0.0, 0.0, 0.0), sampler: int = 0, ptilde: int = 0, reuse: int = 1):
         arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (pos, mom, charge, mass)]
         req = Request(N=int(arrs[2].shape[0]), pos=arrs[0].ctypes.data, mom=arrs[1].ctypes.data,
                       charge=arrs[2].ctypes.data, mass=arrs[3].ctypes.data,
                       box=(ctypes.c_double * 3)(*[float(b) for b in box]), pV=float(pV), seed=int(seed),
                       nsteps=int(nsteps), pad=0, params=params,
-                      pc=(ctypes.c_double * 3)(*[float(x) for x in pc]))
+                      pc=(ctypes.c_double * 3)(*[float(x) for x in pc]), sampler=int(sampler), ptilde=int(ptilde),
+                      reuse=int(reuse), pad2=0)
         rid = ctypes.c_int64()
         self._check(load().rbe_server_submit(self.h, ctypes.byref(req), ctypes.byref(rid)))
         self._n[rid.value] = req.N

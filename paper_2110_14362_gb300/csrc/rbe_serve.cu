@@ -102,7 +102,10 @@ static int64_t replica_bytes(const rbe_request& r, int P)
         const int64_t cap = (int64_t)(std::ceil((2.0 * expect + 64.0) / 32.0) * 32.0);
         list = r.N * (4 * cap + 4 + 16);
     }
-    return r.N * (72 + 16 + 48 + 12 + 48) + 12 * cells + list + (int64_t)(P + 1) * 16 * 2048 + (4 << 20);
+    // frequency buffers of the force and pressure batches (each slot ~100 B) and the reused draws
+    const int64_t Ptot = (int64_t)P + std::max(0, r.ptilde);
+    const int64_t freq = Ptot * 112 + (r.reuse > 1 ? (int64_t)r.reuse * Ptot * 16 : 0) + Ptot * 16;
+    return r.N * (72 + 16 + 48 + 12 + 48) + 12 * cells + list + (int64_t)(P + 1) * 16 * 2048 + freq + (4 << 20);
 }
 
 static void release_slot(rbe_server_s* s, Slot& sl)
@@ -163,6 +166,14 @@ static rbe_status admit(rbe_server_s* s, Slot& sl, int64_t id)
     }
     rbe_set_seed(sl.ctx, rq.r.seed);
     if ((st = rbe_set_box(sl.ctx, rq.r.box)) != RBE_OK) return sfail(s, st, rbe_last_error(sl.ctx));
+    // the request's sampling (a slot's context is reused: every admission sets all three, the
+    // exact sampler first so that neither a previous MH chain nor a previous reuse excludes the
+    // request's combination; an MH chain starts afresh)
+    if ((st = rbe_set_sampler(sl.ctx, RBE_SAMPLER_EXACT)) != RBE_OK ||
+        (st = rbe_set_sample_reuse(sl.ctx, rq.r.reuse > 1 ? rq.r.reuse : 1)) != RBE_OK ||
+        (st = rbe_set_sampler(sl.ctx, rq.r.sampler)) != RBE_OK ||
+        (st = rbe_set_pressure_batch(sl.ctx, rq.r.ptilde)) != RBE_OK)
+        return sfail(s, st, rbe_last_error(sl.ctx));
     double cell[RBE_CELL_DOUBLES] = {0};
     for (int t = 0; t < 3; ++t) cell[t] = rq.r.box[t];
     cell[3] = rq.r.pV;
@@ -309,6 +320,11 @@ rbe_status rbe_server_submit(rbe_server s, const rbe_request* req, int64_t* id)
         return sfail(s, RBE_EINVAL, "invalid request");
     for (int t = 0; t < 3; ++t)
         if (!(req->box[t] > 0.0)) return sfail(s, RBE_EINVAL, "box lengths must be > 0");
+    if (req->sampler < 0 || req->sampler > 2 || req->ptilde < 0 || req->ptilde > 65536 || req->reuse < 0 ||
+        req->reuse > 1024)
+        return sfail(s, RBE_EINVAL, "invalid sampler, pressure batch or reuse");
+    if (req->sampler == 2 && req->reuse > 1)
+        return sfail(s, RBE_EINVAL, "sample reuse and the Metropolis-Hastings chain exclude each other");
     if (replica_bytes(*req, s->cfg.P) > s->cfg.mem_budget)
         return sfail(s, RBE_ENOMEM, "request larger than the whole memory budget");
     auto rq = std::make_unique<Request>();

@@ -165,3 +165,51 @@ def test_served_with_neighbour_lists(precision, monkeypatch):
     alone = _serve([REQS[1]], precision, max_slots=1)[0][0]
     _same(mixed[1], alone)
     _same(mixed[0], _direct(REQS[0], precision))
+
+
+@pytest.mark.parametrize("kw", [dict(sampler=rbe.RBE_SAMPLER_MH, ptilde=40), dict(sampler=rbe.RBE_SAMPLER_OFFLINE),
+                                dict(reuse=4, ptilde=20)])
+def test_served_sampler_variants_equal_direct(kw):
+    """A request carrying the paper's sampler variants (Sec. 4.3), a pressure batch or sample reuse
+    is served bit for bit as the same settings stepped directly; a slot reused by requests with
+    different settings (an MH chain after reuse and back) applies each request's own."""
+    precision = rbe.RBE_FP32_PHASE
+    cuda_device()
+    srv = rbe.Server(ALPHA, P, precision, max_slots=1, chunk_steps=4, mem_budget=8 << 30, use_graphs=True)
+    try:
+        n_side, sseed, pseed, nsteps = REQS[0]
+        pos, mom, q, m, box = _system(n_side, sseed)
+        rid_plain = srv.submit(pos, mom, q, m, box, _dev_params(box), pseed, nsteps)
+        rid = srv.submit(pos, mom, q, m, box, _dev_params(box), pseed, nsteps, **kw)
+        rid_back = srv.submit(pos, mom, q, m, box, _dev_params(box), pseed, nsteps)
+        while srv.progress(wait=True)[2] < 3:
+            pass
+        served = srv.result(rid)
+        plain, back = srv.result(rid_plain), srv.result(rid_back)
+    finally:
+        srv.close()
+    with rbe.Context(box, ALPHA, P, pseed, precision) as ctx:
+        ctx.set_sampler(kw.get("sampler", rbe.RBE_SAMPLER_EXACT))
+        ctx.set_pressure_batch(kw.get("ptilde", 0))
+        ctx.set_sample_reuse(kw.get("reuse", 1))
+        rep = rbe.NptReplica(pos, mom, q, m, box, _dev_params(box), cuda_device(), step=0)
+        rep.init(ctx, batch=0)
+        rep.step(ctx, nsteps)
+        ctx.sync()
+        r, p, F, L, cell = rep.state()
+    _same(served, (r, p, cell))
+    _same(plain, back)  # the settings did not leak into the next request
+    assert not np.array_equal(served[1], plain[1])
+
+
+def test_server_rejects_bad_sampling_settings():
+    cuda_device()
+    srv = rbe.Server(ALPHA, P, rbe.RBE_FP32_PHASE, max_slots=1, chunk_steps=4, mem_budget=8 << 30)
+    try:
+        pos, mom, q, m, box = _system(*REQS[0][:2])
+        for kw in (dict(sampler=3), dict(ptilde=-1), dict(reuse=2000), dict(sampler=rbe.RBE_SAMPLER_MH, reuse=4)):
+            with pytest.raises(rbe.RBEError) as e:
+                srv.submit(pos, mom, q, m, box, _dev_params(box), 1, 4, **kw)
+            assert e.value.status == rbe.RBE_EINVAL
+    finally:
+        srv.close()
