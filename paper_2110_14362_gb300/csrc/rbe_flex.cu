@@ -615,7 +615,7 @@ constexpr int kFlexHitCap = 32 * (kListBatch + 1);  // < 32 buffered + 32 kListB
 // Modes as the rectangular kernel's: search the cells and evaluate, search the cells within
 // rc + skin and write the list (rebuild steps only), evaluate the listed pairs.
 template <bool kF64, int kMode>
-__global__ void __launch_bounds__(kPairWarps * 32, kF64 ? kPairBlocksPerSM64 : 3)
+__global__ void __launch_bounds__(kPairWarps * 32, kF64 ? kPairBlocksPerSM64 : (kMode == 2 ? kPairBlocksPerSM : 3))
 k_flex_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, const FlexCoef* __restrict__ cf,
             const int* __restrict__ cid, const int* __restrict__ cnt, const int* __restrict__ start,
             const int* __restrict__ sorted, const float4* __restrict__ spos32, const double4_32a* __restrict__ spos64,
@@ -1137,6 +1137,7 @@ static rbe_status flex_forces(rbe_ctx ctx, rbe_flex_system* sys, int do_kick)
     const int nbp = pair_blocks(ctx, N, fp64);
     const FlexCoef* cf = static_cast<const FlexCoef*>(ctx->flex_coef);
     const GenCell* gc = static_cast<const GenCell*>(ctx->gcell_dev);
+    int nbp_eval = nbp;  // blocks of the evaluating pair launch (their partials)
     rbe_status st;
     if (prm.kspace) {
         const int P = ctx->P;
@@ -1179,11 +1180,23 @@ static rbe_status flex_forces(rbe_ctx ctx, rbe_flex_system* sys, int do_kick)
         const CellConsts* cc = static_cast<const CellConsts*>(b.cellc);
         const FlexListArgs la{nl,       b.nbr,     ctx->flex_code, b.nnb,     b.sref, ctx->flex_cpos32,
                               c64,      ctx->gpos, ctx->d.status,  sys->cell, b.nbr_cap};
+        // one resident wave of the variant launched: the warps stride over the slots, and a second
+        // partial wave would run at a fraction of the occupancy
         auto pair = [&](auto f64_tag, auto mode_tag) {
             constexpr bool F64 = decltype(f64_tag)::value;
             constexpr int MODE = decltype(mode_tag)::value;
-            k_flex_pair<F64, MODE><<<nbp, kPairWarps * 32, 0, s>>>(N, cc, pc, cf, b.cid, b.cnt, b.start, b.sorted,
-                                                                   b.spos32, s64, b.Fr, b.partials, la);
+            static int bps = 0;
+            if (!bps) {
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_flex_pair<F64, MODE>, kPairWarps * 32, 0) !=
+                        cudaSuccess ||
+                    bps < 1)
+                    bps = 1;
+                cudaGetLastError();
+            }
+            const int grid = std::max(1, std::min(nbp, ctx->num_sms * bps));
+            if (MODE != 1) nbp_eval = grid;
+            k_flex_pair<F64, MODE><<<grid, kPairWarps * 32, 0, s>>>(N, cc, pc, cf, b.cid, b.cnt, b.start, b.sorted,
+                                                                    b.spos32, s64, b.Fr, b.partials, la);
         };
         using T = std::true_type;
         using F = std::false_type;
@@ -1203,7 +1216,7 @@ static rbe_status flex_forces(rbe_ctx ctx, rbe_flex_system* sys, int do_kick)
         if ((st = flex_check(ctx, "k_flex_pair")) != RBE_OK) return st;
     }
     k_flex_finish<<<std::max(1, nb), kNptThreads, 0, s>>>(N, sys->mom, sys->force, b.mprop, b.Fk, b.Fr, b.WEk, cf,
-                                                          b.partials, nbp, b.counter, sys->cell, prm, do_kick,
+                                                          b.partials, nbp_eval, b.counter, sys->cell, prm, do_kick,
                                                           ctx->d.status);
     return flex_check(ctx, "k_flex_finish");
 }
