@@ -329,3 +329,30 @@ def test_flex_cell_leaving_the_prepared_range_is_reported():
         assert e.value.status == rbe.RBE_ESTATE
         st = rep.state()
         assert st["h"][0, 0] < 12.0 and np.isfinite(st["r"]).all()
+
+
+def test_flex_single_particle_matches_oracle():
+    """One charge in a sheared cell: no pairs, a k-space force of zero up to rounding (the batch's
+    Im(e^{-ik.r} rho) cancels) but a k-space virial and energy; the cell and the particle follow the
+    oracle."""
+    h = np.array([[12.0, 2.0, -1.0], [0.0, 13.0, 1.5], [0.0, 0.0, 14.0]])
+    pos, mom = np.array([[3.0, 4.0, 5.0]]), np.array([[10.0, -5.0, 3.0]])
+    q, m = np.array([1.0]), np.array([20.0])
+    prm_d, prm_o, ph = _params(h, 5.0)
+    dev = cuda_device()
+    with rbe.Context(np.diag(h), ALPHA, P, SEED, rbe.RBE_FP64) as ctx:
+        rep = rbe.FlexReplica(pos, mom, q, m, h, prm_d, dev, step=0, ph=ph)
+        rep.init(ctx, batch=0)
+        rep.step(ctx, 3)
+        ctx.sync()
+        got = rep.state()
+    st = oracle.FlexState(pos, mom, q, m, h, ph=ph, P=P)
+    oracle.flex_forces(st, 0, prm_o)
+    for s in range(3):
+        E = oracle.flex_step(st, s, prm_o)
+    assert np.abs(got["h"] - st.h).max() < 1e-12 * np.abs(st.h).max()
+    assert _mi_dist(got["r"], st.r, st.h) < 1e-10 * np.abs(st.h).max()
+    assert np.abs(got["p"] - st.p).max() < 1e-10 * np.abs(st.p).max()
+    assert np.abs(got["F"]).max() < 1e-9 and np.abs(st.F).max() < 1e-9
+    assert np.abs(got["W"] - st.W).max() < 1e-10 * np.abs(st.W).max()
+    assert abs(got["Ek"] - E[0]) < 1e-10 * abs(E[0])

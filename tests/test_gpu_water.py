@@ -226,3 +226,31 @@ def test_water_unconverged_constraints_are_reported():
         rep.init(ctx)
         rep.step(ctx, 2)
         ctx.sync()
+
+
+def test_water_single_molecule_matches_oracle():
+    """One molecule: no pairs between molecules, the exclusion and the k-space of its own three
+    sites only; the device follows the oracle."""
+    L = 12.0
+    rng = np.random.default_rng(9)
+    pos = np.array([[5.0, 6.0, 7.0]]) + LOCAL
+    m = MASS.copy()
+    mom = rng.normal(size=(3, 3)) * np.sqrt(KT * 100 * m)[:, None]
+    box = np.array([L, L, L])
+    prm_d, prm_o = _params(L, 5.0, M_V=oracle.piston_mass(0.5, 4.5e-5 / oracle.BAR, L ** 3))
+    dev = cuda_device()
+    with rbe.Context(box, ALPHA, P, SEED, rbe.RBE_FP64) as ctx:
+        rep = rbe.WaterReplica(pos, mom, Q, m, box, prm_d, dev)
+        rep.init(ctx, batch=0)
+        rep.step(ctx, 3)
+        ctx.sync()
+        r, p, F, Lb, cell = rep.state()
+    st = oracle.WaterState(pos, mom, Q, m, box)
+    oracle.water_forces(st, 0, prm_o)
+    for s in range(3):
+        E = oracle.water_step(st, s, prm_o, oracle.water_params())
+    assert np.abs(Lb - st.L).max() < 1e-12 * L
+    assert _mi(r, st.r, st.L) < 1e-10 * L
+    assert np.abs(p - st.p).max() < 1e-10 * np.abs(st.p).max()
+    assert np.abs(F - st.F).max() < 1e-10 * np.abs(st.F).max()
+    assert abs(cell[rbe.CELL_EXCL] - E[3]) < 1e-10 * abs(E[3])
