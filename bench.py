@@ -254,9 +254,10 @@ def run_ours(args, world, rank, local):
     water = None if args.skip_serving else run_water(rbe, steps=1000, warmup=20)
     sweep = None if args.skip_sweep else run_sweep(rbe)
 
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         cpu = cpu_baseline(s, budget_s=args.cpu_seconds)
+        cpu_all = cpu_baseline_all_cores(s, budget_s=args.cpu_seconds / 3)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -272,6 +273,7 @@ def run_ours(args, world, rank, local):
         "e2e": e2e,
         "roofline": roof,
         "cpu_baseline": cpu,
+        "cpu_baseline_all_cores": cpu_all,
         "clocks": clocks,
     }
     if other:
@@ -662,6 +664,31 @@ def cpu_baseline(s, budget_s: float = 15.0):
     return {"value": n2 * s.P / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {n2} of {s.N} particles x all P={s.P} frequencies (rho pass + force pass, FP64, "
                       f"single thread), {dt:.1f} s"}
+
+
+def cpu_baseline_all_cores(s, budget_s: float = 5.0):
+    """The same oracle loops built with OpenMP (frequencies of the rho pass and particles of
+    the force pass shared among every host core, the results the same bits), on a bounded
+    sample sized like cpu_baseline's; None where gcc has no OpenMP runtime."""
+    import subprocess
+    import oracle
+    try:
+        oracle.build_omp()
+    except (subprocess.CalledProcessError, OSError):
+        return None
+    cores = int(os.environ.get("OMP_NUM_THREADS", 0)) or len(os.sched_getaffinity(0))
+    m, S = oracle.sample_k(s.box, s.alpha, s.P, SEED, 0)
+    n = min(s.N, 1024)
+    t0 = time.perf_counter()
+    oracle.rbe_kspace(s.pos[:n], s.q[:n], s.box, s.alpha, m, S / s.P, all_cores=True)
+    dt = time.perf_counter() - t0
+    n2 = int(min(s.N, max(n, n * budget_s / max(dt, 1e-6) * 0.8)))
+    t0 = time.perf_counter()
+    oracle.rbe_kspace(s.pos[:n2], s.q[:n2], s.box, s.alpha, m, S / s.P, all_cores=True)
+    dt = time.perf_counter() - t0
+    return {"value": n2 * s.P / dt, "unit": UNIT, "cores": cores, "kind": "oracle (OpenMP build)",
+            "sample": f"first {n2} of {s.N} particles x all P={s.P} frequencies (rho pass + force pass, FP64, "
+                      f"{cores} threads), {dt:.1f} s"}
 
 
 def run_reference(args, world, rank):

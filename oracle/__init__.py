@@ -27,6 +27,7 @@ _SRC_FLX = os.path.join(_HERE, "flexible_oracle.c")
 _SRC_WAT = os.path.join(_HERE, "water_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
+_LIB_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -47,6 +48,37 @@ def build(force: bool = False) -> str:
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+_lib_omp = None
+
+
+def build_omp(force: bool = False) -> str:
+    """Compile ``rbe_oracle.c`` alone with ``-fopenmp`` into ``oracle/_build/liboracle_omp.so``
+    (the all-cores timing build of the k-space oracle; the same loops and results as the
+    single-thread build, its outer loops shared among the threads).  Raises
+    ``subprocess.CalledProcessError`` where the compiler has no OpenMP runtime."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < os.path.getmtime(_SRC):
+        tmp = _LIB_OMP + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+               "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True, capture_output=True)
+        os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
+
+
+def _load_omp():
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            lib = ctypes.CDLL(build_omp())
+            lib.orc_rbe_kspace.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p,
+                                           ctypes.c_double, ctypes.c_int32, _c_int32_p, _c_double_p,
+                                           _c_double_p, _c_double_p, _c_double_p, _c_double_p]
+            lib.orc_rbe_kspace.restype = ctypes.c_int
+            _lib_omp = lib
+    return _lib_omp
 
 
 def _load():
@@ -336,9 +368,11 @@ def ewald_kspace(pos, q, box, alpha: float, kmax: int):
     return F, W, E[0], E[1]
 
 
-def rbe_kspace(pos, q, box, alpha: float, m, weights):
-    """RBE estimators on a given batch: (F[N,3], W[3,3], E_k, E_self, rho[P] complex)."""
-    lib = _load()
+def rbe_kspace(pos, q, box, alpha: float, m, weights, all_cores: bool = False):
+    """RBE estimators on a given batch: (F[N,3], W[3,3], E_k, E_self, rho[P] complex).
+    ``all_cores`` runs the OpenMP build (``OMP_NUM_THREADS`` threads, else every core); the
+    results are the same bits."""
+    lib = _load_omp() if all_cores else _load()
     pos = _f64(pos)
     q = _f64(q)
     N = q.shape[0]

@@ -288,7 +288,10 @@ int orc_ewald_kspace(int64_t N, const double* pos, const double* q, const double
  *   F_i   = -sum_l w_l (4 pi q_i k_l / (V |k_l|^2)) Im(e^{-i k_l.r_i} rho_l)
  *   W     = (2 pi / V) sum_l w_l |rho_l|^2/|k_l|^2 [I - 2(1/|k_l|^2 + 1/4a) k_l k_l]
  *   E_k   = (2 pi / V) sum_l w_l |rho_l|^2/|k_l|^2 ;  E_self as above.
- * rho (2P doubles, interleaved re/im) may be NULL. */
+ * rho (2P doubles, interleaved re/im) may be NULL.
+ * Built with -fopenmp (the all-cores timing build), the rho loop runs its frequencies and
+ * the force loop its particles on several threads; each iteration's sums keep the index
+ * order above, so both builds return the same bits. */
 int orc_rbe_kspace(int64_t N, const double* pos, const double* q, const double box[3],
                    double alpha, int32_t P, const int32_t* m, const double* wl,
                    double* F, double W[9], double E[2], double* rho)
@@ -298,8 +301,10 @@ int orc_rbe_kspace(int64_t N, const double* pos, const double* q, const double b
     double V = box[0] * box[1] * box[2];
     double* rr = (double*)malloc(sizeof(double) * (size_t)(2 * P + 2));
     if (!rr) return ORC_ENOMEM;
-    for (int32_t l = 0; l < P; ++l) {
+    for (int32_t l = 0; l < P; ++l)
         if (m[3 * l] == 0 && m[3 * l + 1] == 0 && m[3 * l + 2] == 0) { free(rr); return ORC_EINVAL; }
+#pragma omp parallel for schedule(static)
+    for (int32_t l = 0; l < P; ++l) {
         double k[3] = {2.0 * M_PI * m[3 * l] / box[0], 2.0 * M_PI * m[3 * l + 1] / box[1],
                        2.0 * M_PI * m[3 * l + 2] / box[2]};
         double re = 0.0, im = 0.0;
@@ -311,6 +316,7 @@ int orc_rbe_kspace(int64_t N, const double* pos, const double* q, const double b
         rr[2 * l] = re;
         rr[2 * l + 1] = im;
     }
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < N; ++i) {
         double f[3] = {0.0, 0.0, 0.0};
         for (int32_t l = 0; l < P; ++l) {

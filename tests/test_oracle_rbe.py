@@ -109,3 +109,19 @@ def test_unbiased_with_proposition_1_variance():
     assert z.max() < 5.0, z.max()
     zP = abs(accP / B - P2) / math.sqrt(varP / (P * B))
     assert zP < 5.0, zP
+
+
+def test_all_cores_build_returns_the_same_bits():
+    """The OpenMP timing build shares the frequencies (rho) and the particles (forces) among
+    threads without changing any sum's order: every output equals the single-thread build's."""
+    import subprocess
+    try:
+        oracle.build_omp()
+    except (subprocess.CalledProcessError, OSError) as e:
+        pytest.skip(f"no OpenMP runtime for gcc here: {e}")
+    s = inputs.small_snapshot()
+    m, S = oracle.sample_k(s.box, s.alpha, 37, 12345, 2)
+    a = oracle.rbe_kspace(s.pos, s.q, s.box, s.alpha, m, S / 37)
+    b = oracle.rbe_kspace(s.pos, s.q, s.box, s.alpha, m, S / 37, all_cores=True)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
