@@ -213,6 +213,21 @@ def run_ours(args, world, rank, local):
         ms64, _ = timed_loop(ctx64, max(2, min(args.steps, 5)), 2, 50_000)
         other = {"precision": "fp64", "value": pairs / (sum(ms64) / len(ms64) / 1e3), "unit": UNIT,
                  "ms_per_step": sum(ms64) / len(ms64)}
+        # accuracy of the timed FP32-phase path against the FP64 path on the same frequencies
+        # (the same seed and step draw the same batch in both contexts)
+        ctx64.forces_virial(pos, q, 60_000, F, W, E)
+        ctx64.sync()
+        F0, W0, E0 = F.cpu().numpy(), W.cpu().numpy().reshape(3, 3), E.cpu().numpy()
+        ctx.forces_virial(pos, q, 60_000, F, W, E)
+        ctx.sync()
+        F1, W1, E1 = F.cpu().numpy(), W.cpu().numpy().reshape(3, 3), E.cpu().numpy()
+        dW = np.abs(np.diag(W1) - np.diag(W0))
+        other["fp32_phase_vs_fp64"] = {
+            "force_rel_rms": float(np.sqrt(np.mean((F1 - F0) ** 2) / np.mean(F0 ** 2))),
+            "virial_rel": float(np.linalg.norm(W1 - W0) / np.linalg.norm(W0)),
+            "pressure_diag_rel": [float(x) for x in dW / np.abs(np.diag(W0))],
+            "energy_rel": float(abs(E1[0] - E0[0]) / abs(E0[0])),
+            "bar": "force relative RMS <= 1e-5"}
         ctx64.close()
 
     # end to end through the public host-buffer call: pinned host inputs in, forces out
