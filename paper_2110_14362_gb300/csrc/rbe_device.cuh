@@ -122,6 +122,18 @@ __device__ __forceinline__ float fixed_phase(int mx, int my, int mz, uint32_t sx
     return fmaf(__uint_as_float((t >> 9) | 0x3f800000u), 6.28318530717958647692f, -9.42477796076937971538f);
 }
 
+// The same mapping of m.s - phi, for a phase offset given in the same fixed point: off =
+// 2^31 + 2^8 - phi (mod 2^32), phi in revolutions x 2^32.  The force pass uses it to take
+// one sine per pair (sin(theta - arg rho) instead of the pair sin theta, cos theta).
+__device__ __forceinline__ float fixed_phase_off(int mx, int my, int mz, uint32_t sx, uint32_t sy, uint32_t sz,
+                                                 uint32_t off)
+{
+    uint32_t t = (uint32_t)mx * sx + off;
+    t += (uint32_t)my * sy;
+    t += (uint32_t)mz * sz;
+    return fmaf(__uint_as_float((t >> 9) | 0x3f800000u), 6.28318530717958647692f, -9.42477796076937971538f);
+}
+
 // ---------------------------------------------------------------------------------
 // Integer-only conversions.  GB300 executes FP64 instructions on a narrow pipe (about
 // 1.7 FP64 FMA per clock per SM), so the FP32-phase path converts its FP64 inputs with

@@ -425,11 +425,16 @@ __device__ __forceinline__ void reduce_f32_row(int l, const float4* __restrict__
     t[5] = -e * b * kx * kz;
     t[6] = -e * b * ky * kz;
     t[7] = 0.f;
+    // Im(e^{-ik.r} rho) = |rho| sin(arg rho - theta): the force pass takes one sine per pair of
+    // the phase shifted by arg rho (harmonic addition), its amplitude R = beta |rho| folded
+    // into the coefficients, and arg rho as a 32-bit fixed-point offset of the phase.
     const float beta = cb * wl * ikk;
-    const float A = beta * im, B = beta * re;
+    const float R = beta * sqrtf(rho2);
+    const double phi = (double)atan2f(im, re) * 683565275.57643158978;  // revolutions x 2^32
+    const uint32_t off = 0x80000100u - (uint32_t)(unsigned long long)__double2ll_rn(phi);
     rho[l] = make_double2(ff_to_double(rh, rl), ff_to_double(ih, il));
-    coef_m[l] = make_int4(mi.x, mi.y, mi.z, __float_as_int(A));
-    coef_f[l] = make_float4(B, (float)mi.x, (float)mi.y, (float)mi.z);
+    coef_m[l] = make_int4(mi.x, mi.y, mi.z, (int)off);
+    coef_f[l] = make_float4(R, R * (float)mi.x, R * (float)mi.y, R * (float)mi.z);
     if (!isfinite(re) || !isfinite(im)) atomicOr(status, kStatusNonFinite);
 }
 
@@ -490,13 +495,14 @@ __device__ __forceinline__ void final_sums_f32(const float* __restrict__ terms, 
 // =================================================================================
 // Force pass, FP32-phase path.  Blocks of kForceWarps warps; block b owns particles
 // [b * per_block, (b+1) * per_block).  The frequencies are staged in shared memory (as
-// (mx, my, mz, A) and (B, mx, my, mz)) and split into kForceWarps contiguous slices, one
+// (mx, my, mz, off_l) and (R_l, R_l mx, R_l my, R_l mz), R_l = beta_l |rho_l| and off_l the
+// fixed-point phase offset of arg rho_l) and split into kForceWarps contiguous slices, one
 // per warp.  Particles are converted once per block into shared memory, kForceThreads at
 // a time; each round of kForceRound particles is processed by every warp against its
 // slice (kForcePPT particles per lane), and the warps' partial forces are summed in
 // shared memory in a fixed order.  No FP64 instruction runs:
-//   F_i,theta = q_i (2 pi / l_theta) sum_l m_l,theta (sin B_l - cos A_l)
-// is formed in FP32 and widened to double exactly.  The launch carries one extra block
+//   F_i,theta = q_i (2 pi / l_theta) sum_l R_l m_l,theta sin(theta_il - arg rho_l)
+// (one sine per pair) is formed in FP32 and widened to double exactly.  The launch carries one extra block
 // that computes the energy and virial sums (final_sums_f32) meanwhile.
 __device__ __forceinline__ void force_f32_block(int64_t blk, const double* __restrict__ pos,
                                                 const double* __restrict__ q, int64_t N, int64_t per_block,
@@ -555,12 +561,11 @@ __device__ __forceinline__ void force_f32_block(int64_t blk, const double* __res
                 for (int l = l0; l < l1; ++l) {
                     const int4 a = sm[l];
                     const float4 b = sf[l];
-                    const float A = __int_as_float(a.w);
 #pragma unroll
                     for (int p = 0; p < kForcePPT; ++p) {
-                        float sn, cs;
-                        __sincosf(fixed_phase(a.x, a.y, a.z, pr[p].x, pr[p].y, pr[p].z), &sn, &cs);
-                        const float g = fmaf(sn, b.x, -cs * A);
+                        // g = R sin(theta - arg rho) = beta (Re rho sin theta - Im rho cos theta)
+                        const float g = __sinf(fixed_phase_off(a.x, a.y, a.z, pr[p].x, pr[p].y, pr[p].z,
+                                                               (uint32_t)a.w));
                         gx[p] = fmaf(g, b.y, gx[p]);
                         gy[p] = fmaf(g, b.z, gy[p]);
                         gz[p] = fmaf(g, b.w, gz[p]);
