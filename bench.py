@@ -282,6 +282,8 @@ def run_ours(args, world, rank, local):
         "config": {"workload": s.name, "N": s.N, "P": s.P, "alpha": s.alpha, "box": [float(b) for b in s.box],
                    "precision": args.precision, "rho_accum": "fp32-tile/fp64", "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world} (independent systems, no collective)"},
+        # phases evaluated per second: one per pair in each of the two passes (2 N P per evaluation)
+        "phases_per_s": 2.0 * value,
         "kernel_ms": {n: float(v) for n, v in zip(names, kmean)},
         "wall_s_timed_region": wall,
         "gpu_launches": 4 * args.steps,
