@@ -97,6 +97,30 @@ def test_empty_system(precision):
     assert torch.all(W == 0) and torch.all(E == 0)
 
 
+@pytest.mark.parametrize("precision", [rbe.RBE_FP64, rbe.RBE_FP32_PHASE])
+def test_vanishing_structure_factor(precision):
+    """A neutral pair at one point has rho(k) = 0 for every k: forces, k-space energy and
+    virial are exactly zero (the FP32-phase force pass then shifts its phase by arg 0 with a
+    zero amplitude), and the self energy is -sqrt(alpha/pi) sum q^2."""
+    import torch
+    dev = cuda_device()
+    alpha = 0.7
+    pos = torch.tensor([[1.3, 2.7, 4.1], [1.3, 2.7, 4.1]], dtype=torch.float64, device=dev)
+    q = torch.tensor([1.0, -1.0], dtype=torch.float64, device=dev)
+    F = torch.full((2, 3), float("nan"), dtype=torch.float64, device=dev)
+    W = torch.full((9,), float("nan"), dtype=torch.float64, device=dev)
+    E = torch.full((2,), float("nan"), dtype=torch.float64, device=dev)
+    with rbe.Context([9.0, 10.0, 11.0], alpha, 300, 5, precision) as ctx:
+        ctx.forces_virial(pos, q, 3, F, W, E)
+        ctx.sync()
+        rho = ctx.rho()
+    assert np.all(np.asarray(rho) == 0)
+    assert torch.all(F == 0) and torch.all(W == 0) and E[0].item() == 0.0
+    _, _, _, Es, _ = oracle.rbe_kspace(pos.cpu().numpy(), q.cpu().numpy(), [9.0, 10.0, 11.0], alpha,
+                                       np.array([[1, 0, 0]], dtype=np.int32), 1.0)
+    assert abs(E[1].item() - Es) <= 1e-6 * abs(Es)
+
+
 def test_weighted_full_k_equals_ewald():
     import torch
     s = inputs.small_snapshot()
