@@ -54,7 +54,9 @@ typedef enum {
 
 typedef enum {
     RBE_FP64 = 0,        /* phases, sincos and accumulation in FP64 */
-    RBE_FP32_PHASE = 1   /* exact 32-bit fixed-point phase m.s mod 1, FP32 sincos, FP64 across tiles */
+    RBE_FP32_PHASE = 1   /* exact 32-bit fixed-point phase m.s mod 1, FP32 sine and cosine (rho pass)
+                            and one FP32 sine of the phase shifted by arg rho (force pass),
+                            float-float sums across tiles */
 } rbe_precision;
 
 typedef enum {
