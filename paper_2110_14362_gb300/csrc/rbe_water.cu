@@ -26,7 +26,11 @@
 
 namespace rbe {
 
-constexpr int kWaterThreads = 128;  // molecules per block of the per-molecule kernels
+// Molecules per block of the per-molecule kernels (k_water_whole, k_water_drift, k_water_finish):
+// one warp, so that their FP64 constraint and virial arithmetic spreads over as many SMs'
+// FP64 pipes as there are warps of molecules (3000 molecules: 94 SMs, against 24 with blocks of
+// 128, where the drift took 97 us bound by the FP64 pipe of those 24 SMs).
+constexpr int kWaterThreads = 32;
 constexpr int kCellExcl = 25;       // cell block: the exclusion energy
 constexpr int kWaterHitCap = 64;    // buffered candidates per warp (< 32 buffered + 32 new)
 
@@ -667,6 +671,17 @@ rbe_status water_init(rbe_ctx ctx, rbe_system* sys, const rbe_water_params* wp, 
     ctx->npt_ready_N = -1;  // the shared scratch now holds a water system
     ctx->flex_ready_N = -1;
     const int64_t Nmol = sys->N / 3;
+    // block partials: the pair pass's blocks, then one slot row per finishing block
+    NptBuffers& b = ctx->npt;
+    const int need = pair_blocks(ctx, sys->N, true) + (int)std::max<int64_t>(1, (Nmol + kWaterThreads - 1) / kWaterThreads);
+    if (need > b.partcap) {
+        ctx_free(ctx, b.partials);
+        b.partials = nullptr;
+        b.partcap = 0;
+        cudaError_t e = ctx_alloc(ctx, &b.partials, sizeof(double) * kPartStride * (size_t)need);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(water partials)");
+        b.partcap = need;
+    }
     k_water_whole<<<(unsigned)((Nmol + kWaterThreads - 1) / kWaterThreads), kWaterThreads, 0, ctx->stream>>>(
         Nmol, sys->pos, sys->cell);
     if ((st = water_check(ctx, "k_water_whole")) != RBE_OK) return st;
