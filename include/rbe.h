@@ -46,10 +46,11 @@ typedef enum {
     RBE_EINVAL = 1,      /* bad argument: null/misaligned pointer, N < 0, P < 1, alpha <= 0, box <= 0 ... */
     RBE_ENOMEM = 2,      /* device or host allocation failed */
     RBE_ECUDA = 3,       /* a CUDA runtime call or launch failed (message in rbe_last_error) */
-    RBE_ETIMEOUT = 4,    /* a bounded device-side wait gave up */
+    RBE_ETIMEOUT = 4,    /* a bounded device-side wait gave up (the persistent batched launch's grid
+                            barriers); no other call waits on the device */
     RBE_ENONFINITE = 5,  /* rho(k) or an output became NaN/Inf (non-finite inputs) */
-    RBE_ESAMPLE = 6,     /* a frequency stayed m = 0 after 2^20 redraws (alpha l^2 far too small) */
-    RBE_ESTATE = 7       /* call not valid in the context's current state */
+    RBE_ESTATE = 6,      /* call not valid in the context's current state */
+    RBE_ESAMPLE = 7      /* a frequency stayed m = 0 after 2^20 redraws (alpha l^2 far too small) */
 } rbe_status;
 
 typedef enum {
@@ -61,8 +62,10 @@ typedef enum {
 
 typedef enum {
     RBE_RHO_FP64 = 0,    /* FP32-phase path: rho accumulated per pair in FP64 */
-    RBE_RHO_COMP32 = 1,  /* FP32-phase path: compensated (Kahan) FP32 within a staged tile, FP64 across */
-    RBE_RHO_FP32 = 2     /* FP32-phase path: plain FP32 within a staged tile, FP64 across (default) */
+    RBE_RHO_COMP32 = 1,  /* FP32-phase path: compensated (Kahan) FP32 sums of every term within a staged
+                            tile, float-float (about 48 bits) across tiles (default) */
+    RBE_RHO_FP32 = 2     /* FP32-phase path: plain FP32 within a staged tile, float-float across (faster;
+                            outside the compensated-or-FP64 rule of the default) */
 } rbe_rho_accum;
 
 /* Create a context for box lengths box[3] (> 0), splitting parameter alpha (> 0, Sec. 4.1),
@@ -85,7 +88,9 @@ rbe_status rbe_set_stream(rbe_ctx ctx, void* stream);
 rbe_status rbe_set_seed(rbe_ctx ctx, uint64_t seed);
 
 /* Select the arithmetic: precision in rbe_precision, rho_accum in rbe_rho_accum
- * (rho_accum is ignored on the FP64 path). */
+ * (rho_accum is ignored on the FP64 path).  A new context runs RBE_FP64 with RBE_RHO_COMP32.
+ * On the FP32-phase path every accumulation widens rho(k) to FP64 before the per-frequency
+ * energy and virial terms, which are formed and summed in FP64. */
 rbe_status rbe_set_precision(rbe_ctx ctx, int32_t precision, int32_t rho_accum);
 
 /* Frequency samplers (Sec. 4.3).  EXACT (default): i.i.d. draws from the discrete Gaussian of
@@ -240,9 +245,12 @@ rbe_status rbe_measure_pipe(int32_t kind, int32_t iters, double* ops_per_s);
  * Every call shares the array, which keeps the last call's contents (the status word is
  * cleared at the start of each call); calls that overlap on the GPU -- on different streams
  * or from different host threads -- race on it and must be serialised by the caller.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  Synchronises `stream`
- * before returning; a frequency that stayed m = 0 after 2^20 redraws returns RBE_ESAMPLE.
+ * Every call looks up the array's device address (cudaGetSymbolAddress, a host-side query that
+ * allocates nothing) in the CUDA context current on the calling thread, so a caller that
+ * switches contexts or resets the device gets the address of the array in the context it runs
+ * in.  Not usable during stream capture: every call ends with a copy of the status word into
+ * host memory and a synchronisation of `stream`, which a capturing stream refuses.  A frequency
+ * that stayed m = 0 after 2^20 redraws returns RBE_ESAMPLE.
  * Messages for failures are returned by rbe_last_error(NULL). */
 rbe_status rbe_sample_k_noalloc(const double box[3], double alpha, int32_t P, uint64_t seed, uint64_t step,
                                 int32_t* m_out, double* S_out, void* stream);

@@ -17,7 +17,7 @@ import numpy as np
 
 from . import _build
 
-RBE_OK, RBE_EINVAL, RBE_ENOMEM, RBE_ECUDA, RBE_ETIMEOUT, RBE_ENONFINITE, RBE_ESAMPLE, RBE_ESTATE = range(8)
+RBE_OK, RBE_EINVAL, RBE_ENOMEM, RBE_ECUDA, RBE_ETIMEOUT, RBE_ENONFINITE, RBE_ESTATE, RBE_ESAMPLE = range(8)
 RBE_FP64, RBE_FP32_PHASE = 0, 1
 RBE_RHO_FP64, RBE_RHO_COMP32, RBE_RHO_FP32 = 0, 1, 2
 RBE_SAMPLER_EXACT, RBE_SAMPLER_OFFLINE, RBE_SAMPLER_MH = 0, 1, 2
@@ -247,7 +247,7 @@ def rbe_set_stream(h, stream_handle: int):
     _check(load().rbe_set_stream(h, ctypes.c_void_p(stream_handle)), h)
 
 
-def rbe_set_precision(h, precision: int, rho_accum: int = RBE_RHO_FP32):
+def rbe_set_precision(h, precision: int, rho_accum: int = RBE_RHO_COMP32):
     _check(load().rbe_set_precision(h, int(precision), int(rho_accum)), h)
 
 
@@ -332,10 +332,20 @@ def rbe_measure_pipe(kind: int, iters: int = 4096) -> float:
 
 
 def rbe_sample_k_noalloc(box, alpha: float, P: int, seed: int, step: int, m_out, S_out, stream_handle: int = 0):
-    """Allocation-free sampling into caller device buffers (torch int32 (P, 3), float64 (1,))."""
+    """Allocation-free sampling into caller device buffers: m_out a torch int32 tensor of at
+    least 3 P elements, S_out a float64 tensor of at least one, both contiguous and on one CUDA
+    device; the call runs with that device current."""
+    import torch
+    if m_out.dtype != torch.int32 or m_out.numel() < 3 * int(P):
+        raise ValueError("m_out must be an int32 tensor of at least 3 P elements")
+    if S_out.dtype != torch.float64 or S_out.numel() < 1:
+        raise ValueError("S_out must be a float64 tensor of at least one element")
+    if not (m_out.is_cuda and S_out.is_cuda) or m_out.device != S_out.device:
+        raise ValueError("m_out and S_out must be CUDA tensors on the same device")
     b = _host(box, np.float64).reshape(3)
-    _check(load().rbe_sample_k_noalloc(b.ctypes.data_as(_dp), float(alpha), int(P), int(seed), int(step),
-                                       _ptr(m_out), _ptr(S_out), ctypes.c_void_p(stream_handle)))
+    with torch.cuda.device(m_out.device):
+        _check(load().rbe_sample_k_noalloc(b.ctypes.data_as(_dp), float(alpha), int(P), int(seed), int(step),
+                                           _ptr(m_out), _ptr(S_out), ctypes.c_void_p(stream_handle)))
 
 
 def rbe_npt_init(h, sys_: "System", batch: int):
@@ -629,7 +639,7 @@ class Context:
     """Owns one librbe context: box, alpha, batch size P and Philox seed."""
 
     def __init__(self, box, alpha: float, P: int, seed: int, precision: int = RBE_FP64,
-                 rho_accum: int = RBE_RHO_FP32, stream=None):
+                 rho_accum: int = RBE_RHO_COMP32, stream=None):
         self.P = int(P)
         self.alpha = float(alpha)
         self.h = rbe_create(box, alpha, P, seed)
@@ -657,7 +667,7 @@ class Context:
     def set_stream(self, stream_handle: int):
         rbe_set_stream(self.h, stream_handle)
 
-    def set_precision(self, precision: int, rho_accum: int = RBE_RHO_FP32):
+    def set_precision(self, precision: int, rho_accum: int = RBE_RHO_COMP32):
         rbe_set_precision(self.h, precision, rho_accum)
 
     def set_sampler(self, sampler: int):

@@ -1,8 +1,8 @@
 // Batched RBE k-space evaluation: many systems of uneven N in five launches in total.
 //
 // Each item is one system (its own positions, charges, box, Philox key and batch index) with
-// the batch's alpha and P, on the FP32-phase path with plain FP32 accumulation inside a
-// staged tile (RBE_RHO_FP32).  Per evaluation:
+// the batch's alpha and P, on the FP32-phase path with compensated FP32 accumulation inside
+// a staged tile (RBE_RHO_COMP32) and FP64 energy and virial terms.  Per evaluation:
 //   k_btables   one block per item whose box changed: tables and box constants  (H1)
 //   k_bsample   blocks of 128 frequencies per item                             (H2)
 //   k_brho      persistent grid over the work list of (item, frequency tile, particle
@@ -75,7 +75,7 @@ k_brho(const BItem* __restrict__ items, const int4* __restrict__ tiles, int ntil
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 tl = tiles[t];
         const BItem it = items[tl.x];
-        rho_f32_tile<RBE_RHO_FP32>(tl.y, tl.z, it.pos, it.q, it.N, ks + tl.x, m + (size_t)tl.x * P, P, it.chunk_len,
+        rho_f32_tile<RBE_RHO_COMP32>(tl.y, tl.z, it.pos, it.q, it.N, ks + tl.x, m + (size_t)tl.x * P, P, it.chunk_len,
                                    it.nchunks, partials + it.part_off, status);
         __syncthreads();
     }
@@ -84,7 +84,7 @@ k_brho(const BItem* __restrict__ items, const int4* __restrict__ tiles, int ntil
 __global__ void __launch_bounds__(kReduceThreads)
 k_breduce(const BItem* __restrict__ items, int P, const float4* __restrict__ partials, const int4* __restrict__ m,
           const double* __restrict__ w, const KState* __restrict__ ks, double2* __restrict__ rho,
-          float* __restrict__ terms, int4* __restrict__ coef_m, float4* __restrict__ coef_f,
+          double* __restrict__ terms, int4* __restrict__ coef_m, float4* __restrict__ coef_f,
           unsigned* __restrict__ status)
 {
     const int r = blockIdx.x / (P + 1), l = blockIdx.x % (P + 1);
@@ -99,7 +99,7 @@ k_breduce(const BItem* __restrict__ items, int P, const float4* __restrict__ par
 __global__ void __launch_bounds__(kForceThreads, 5)
 k_bforce(const BItem* __restrict__ items, const int2* __restrict__ tiles, int nforce, int R,
          const KState* __restrict__ ks, const int4* __restrict__ coef_m, const float4* __restrict__ coef_f, int P,
-         const float* __restrict__ terms, unsigned* __restrict__ status)
+         const double* __restrict__ terms, unsigned* __restrict__ status)
 {
     for (int t = blockIdx.x; t < nforce + R; t += gridDim.x) {
         if (t < nforce) {
@@ -111,7 +111,7 @@ k_bforce(const BItem* __restrict__ items, const int2* __restrict__ tiles, int nf
         } else {
             const int r = t - nforce;
             const BItem it = items[r];
-            final_sums_f32(terms + (size_t)r * (P + 1) * 8, P, ks[r].cself, it.W, it.E, status);
+            final_sums(terms + (size_t)r * (P + 1) * 8, P, ks + r, it.W, it.E, status);
         }
         __syncthreads();
     }
@@ -151,7 +151,7 @@ struct rbe_batch_s {
     int4* d_m = nullptr;
     double* d_w = nullptr;
     double2* d_rho = nullptr;
-    float* d_terms = nullptr;
+    double* d_terms = nullptr;
     int4* d_coef_m = nullptr;
     float4* d_coef_f = nullptr;
     unsigned* d_status = nullptr;
@@ -464,7 +464,7 @@ rbe_status rbe_batch_create(double alpha, int32_t P, int32_t max_items, double m
     A((void**)&b->d_m, sizeof(int4) * P * R);
     A((void**)&b->d_w, sizeof(double) * P * R);
     A((void**)&b->d_rho, sizeof(double2) * P * R);
-    A((void**)&b->d_terms, sizeof(float) * 8 * (size_t)(P + 1) * R);
+    A((void**)&b->d_terms, sizeof(double) * 8 * (size_t)(P + 1) * R);
     A((void**)&b->d_coef_m, sizeof(int4) * P * R);
     A((void**)&b->d_coef_f, sizeof(float4) * P * R);
     A((void**)&b->d_status, sizeof(unsigned));

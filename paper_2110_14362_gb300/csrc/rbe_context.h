@@ -32,9 +32,6 @@ struct KState {
     double wP;          // S / P
     FixScaleH sc[3];    // 1/l as a 64-bit mantissa and a power of two (FP32-phase path)
     float cx, cy, cz;   // 2 pi / l
-    float ce, cb;       // 2 pi / V, 4 pi / V
-    float inv4a;        // 1 / (4 alpha)
-    float cself;        // -sqrt(alpha / pi)
     int P;
 };
 
@@ -114,7 +111,7 @@ struct rbe_ctx_s {
     int32_t P = 0;
     uint64_t seed = 0;
     int32_t precision = RBE_FP64;
-    int32_t rho_accum = RBE_RHO_FP32;
+    int32_t rho_accum = RBE_RHO_COMP32;
     int32_t sampler = 0;             // rbe_sampler: exact, offline or Metropolis--Hastings (Sec. 4.3)
     int4* chain = nullptr;           // MH state per frequency slot (m = 0: start from the exact draw)
     int32_t chain_cap = 0;

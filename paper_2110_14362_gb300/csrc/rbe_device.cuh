@@ -114,12 +114,15 @@ __device__ __forceinline__ uint32_t fixed_frac(double r, double inv_l)
 // 3 pi shift every angle by the same ~2.4e-7 rad (plus a relative 3e-8 scale error); a
 // common shift of all phases multiplies rho(k) by a unit phase factor that cancels in
 // |rho|^2 and in Im(e^{-ik.r} rho(k)), so it leaves forces, energy and virial unchanged.
+// (t >> 9) | 0x3f800000 in one funnel shift: the 64-bit word (0x7f : t) shifted right by 9.
+__device__ __forceinline__ uint32_t phase_bits(uint32_t t) { return __funnelshift_r(t, 0x7fu, 9); }
+
 __device__ __forceinline__ float fixed_phase(int mx, int my, int mz, uint32_t sx, uint32_t sy, uint32_t sz)
 {
     uint32_t t = (uint32_t)mx * sx + 0x80000100u;
     t += (uint32_t)my * sy;
     t += (uint32_t)mz * sz;
-    return fmaf(__uint_as_float((t >> 9) | 0x3f800000u), 6.28318530717958647692f, -9.42477796076937971538f);
+    return fmaf(__uint_as_float(phase_bits(t)), 6.28318530717958647692f, -9.42477796076937971538f);
 }
 
 // The same mapping of m.s - phi, for a phase offset given in the same fixed point: off =
@@ -131,7 +134,7 @@ __device__ __forceinline__ float fixed_phase_off(int mx, int my, int mz, uint32_
     uint32_t t = (uint32_t)mx * sx + off;
     t += (uint32_t)my * sy;
     t += (uint32_t)mz * sz;
-    return fmaf(__uint_as_float((t >> 9) | 0x3f800000u), 6.28318530717958647692f, -9.42477796076937971538f);
+    return fmaf(__uint_as_float(phase_bits(t)), 6.28318530717958647692f, -9.42477796076937971538f);
 }
 
 // ---------------------------------------------------------------------------------

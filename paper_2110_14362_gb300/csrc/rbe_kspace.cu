@@ -287,7 +287,7 @@ k_reduce(const double2* __restrict__ partials, int nchunks, int K, const int4* _
 __global__ void __launch_bounds__(kReduceThreads)
 k_reduce_f32(const float4* __restrict__ partials, int nchunks, int K, const int4* __restrict__ m,
              const double* __restrict__ w, const KState* __restrict__ ks, double2* __restrict__ rho,
-             float* __restrict__ terms, int4* __restrict__ coef_m, float4* __restrict__ coef_f,
+             double* __restrict__ terms, int4* __restrict__ coef_m, float4* __restrict__ coef_f,
              unsigned* __restrict__ status)
 {
     reduce_f32_row((int)blockIdx.x, partials, nchunks, K, m, w, ks, rho, terms, coef_m, coef_f, status);
@@ -300,12 +300,12 @@ k_reduce_f32(const float4* __restrict__ partials, int nchunks, int K, const int4
 __global__ void __launch_bounds__(kForceThreads, 5)
 k_force_f32(const double* __restrict__ pos, const double* __restrict__ q, int64_t N, int64_t per_block,
             const KState* __restrict__ ks, const int4* __restrict__ coef_m, const float4* __restrict__ coef_f,
-            int K, double* __restrict__ F, unsigned* __restrict__ status, const float* __restrict__ terms,
+            int K, double* __restrict__ F, unsigned* __restrict__ status, const double* __restrict__ terms,
             double* __restrict__ W_out, double* __restrict__ E_out, int64_t b_off, int final)
 {
     if (final && blockIdx.x == gridDim.x - 1) {
         pdl_wait();
-        final_sums_f32(terms, K, ks->cself, W_out, E_out, status);
+        final_sums(terms, K, ks, W_out, E_out, status);
         return;
     }
     force_f32_block(b_off + (int64_t)blockIdx.x, pos, q, N, per_block, ks, coef_m, coef_f, K, F, status);
@@ -723,7 +723,7 @@ static rbe_status launch_evaluate_range(rbe_ctx ctx, int64_t N, const double* po
     } else {
         cudaError_t err = launch_pdl(k_reduce_f32, dim3(K + 1), dim3(kReduceThreads), 0, s, (const float4*)part32,
                                      p.nchunks, K, m_in, w_in, ks, d.rho,
-                                     reinterpret_cast<float*>(d.terms), d.coef_m, d.coef_f, d.status);
+                                     d.terms, d.coef_m, d.coef_f, d.status);
         if (err != cudaSuccess) return cuda_fail(ctx, err, "launch k_reduce_f32");
     }
     st = check_launch(ctx, "k_reduce");
@@ -738,7 +738,7 @@ static rbe_status launch_evaluate_range(rbe_ctx ctx, int64_t N, const double* po
         // one extra block computes the energy and virial sums
         cudaError_t err = launch_pdl(k_force_f32, dim3((forces ? p.fblocks : 0) + 1), dim3(kForceThreads), force_smem, s, pos, q,
                                      N, p.per_block, ks, (const int4*)d.coef_m, (const float4*)d.coef_f, K, F,
-                                     d.status, reinterpret_cast<const float*>(d.terms), W, E, (int64_t)0, 1);
+                                     d.status, (const double*)d.terms, W, E, (int64_t)0, 1);
         st = err == cudaSuccess ? RBE_OK : cuda_fail(ctx, err, "launch k_force_f32");
     }
     if (st != RBE_OK) return st;
@@ -828,7 +828,7 @@ rbe_status launch_evaluate_staged(rbe_ctx ctx, int64_t N, const double* h_pos, c
         if (err != cudaSuccess) return cuda_fail(ctx, err, "staged: k_rho_f32");
     }
     err = launch_pdl(k_reduce_f32, dim3(K + 1), dim3(kReduceThreads), 0, s, (const float4*)part32, nchunks, K,
-                     (const int4*)d.m, (const double*)d.w, ks, d.rho, reinterpret_cast<float*>(d.terms), d.coef_m,
+                     (const int4*)d.m, (const double*)d.w, ks, d.rho, d.terms, d.coef_m,
                      d.coef_f, d.status);
     if (err != cudaSuccess) return cuda_fail(ctx, err, "staged: k_reduce_f32");
     for (int g = 0; g < pieces; ++g) {
@@ -837,7 +837,7 @@ rbe_status launch_evaluate_staged(rbe_ctx ctx, int64_t N, const double* h_pos, c
         err = launch_pdl(k_force_f32, dim3(pl[g].fblocks + final_block), dim3(kForceThreads), whole.force_smem, s,
                          (const double*)(d_pos + 3 * a), (const double*)(d_q + a), n, pl[g].per_block, ks,
                          (const int4*)d.coef_m, (const float4*)d.coef_f, K, d_F + 3 * a, d.status,
-                         reinterpret_cast<const float*>(d.terms), W, E, (int64_t)0, final_block);
+                         (const double*)d.terms, W, E, (int64_t)0, final_block);
         if (err != cudaSuccess) return cuda_fail(ctx, err, "staged: k_force_f32");
         if ((err = cudaEventRecord(ctx->pev[1 + kMaxPieces + g], s)) != cudaSuccess ||
             (err = cudaStreamWaitEvent(cs, ctx->pev[1 + kMaxPieces + g], 0)) != cudaSuccess)

@@ -124,15 +124,10 @@ __device__ __forceinline__ void tables_body(double bx, double by, double bz, con
         else if (t == 1) ks->cy = c;
         else ks->cz = c;
     } else if (tid == 96) {
-        const double V = sL[0] * sL[1] * sL[2];
-        ks->V = V;
-        ks->ce = (float)(2.0 * kPi / V);
-        ks->cb = (float)(4.0 * kPi / V);
+        ks->V = sL[0] * sL[1] * sL[2];
     } else if (tid == 128) {
         ks->alpha = alpha;
         ks->P = P;
-        ks->inv4a = (float)(1.0 / (4.0 * alpha));
-        ks->cself = (float)(-sqrt(alpha / kPi));
     }
     __syncthreads();
     if (tid == 0) {
@@ -364,20 +359,60 @@ __device__ __forceinline__ void rho_f32_tile(int kt, int c, const double* __rest
 
 // =================================================================================
 // Reduction for the FP32-phase path.  Block l (of K + 1) sums row l of the partials over
-// the chunks as float-float in a fixed order, then forms the per-frequency terms in FP32
-// (the path's stated accuracy is 1e-5 relative).  Row K carries the sum of q^2.  The sums
-// over l run in the force launch (k_force_f32's extra block), concurrently with the force
-// pass.
+// the chunks as float-float in a fixed order; thread 0 then widens rho_l to FP64 and forms
+// the per-frequency energy and virial terms in FP64 (App. C Eq. (pressuretensorflexible):
+// |rho|^2 of a float-float rho, the importance weight, 1/|k|^2 and the k k products), and the
+// force pass's FP32 coefficients.  Row K carries the sum of q^2.  The sums over l run in the
+// force launch (k_force_f32's extra block, final_sums), concurrently with the force pass.
 __device__ __forceinline__ double ff_to_double(float hi, float lo)
 {
     return __longlong_as_double((long long)float_to_double_bits(__float_as_uint(hi))) +
            __longlong_as_double((long long)float_to_double_bits(__float_as_uint(lo)));
 }
 
+// Energy and virial terms of one frequency in FP64: e = (2 pi / V) w |rho|^2 / |k|^2 and
+// e [delta - 2 (1/|k|^2 + 1/4a) k k] (xx, yy, zz, xy, xz, yz) into t[0..6].
+__device__ __forceinline__ void freq_terms_f64(int4 mi, double wd, double re, double im, const KState* __restrict__ ks,
+                                               double* __restrict__ t)
+{
+    const double kx = 2.0 * kPi * (double)mi.x * ks->inv[0];
+    const double ky = 2.0 * kPi * (double)mi.y * ks->inv[1];
+    const double kz = 2.0 * kPi * (double)mi.z * ks->inv[2];
+    const double kk = kx * kx + ky * ky + kz * kz;
+    const double ikk = 1.0 / kk;
+    const double e = (2.0 * kPi / ks->V) * wd * (re * re + im * im) * ikk;
+    const double b = 2.0 * (ikk + 0.25 / ks->alpha);
+    t[0] = e;
+    t[1] = e * (1.0 - b * kx * kx);
+    t[2] = e * (1.0 - b * ky * ky);
+    t[3] = e * (1.0 - b * kz * kz);
+    t[4] = -e * b * kx * ky;
+    t[5] = -e * b * kx * kz;
+    t[6] = -e * b * ky * kz;
+    t[7] = 0.0;
+}
+
+// The force pass's data of one frequency: Im(e^{-ik.r} rho) = |rho| sin(arg rho - theta), so
+// the pass takes one sine per pair of the phase shifted by arg rho (harmonic addition), its
+// amplitude R = beta |rho| (beta = w 4 pi / (V |k|^2), FP64) folded into the FP32 coefficients,
+// and arg rho as a 32-bit fixed-point offset of the phase.
+__device__ __forceinline__ void force_coef(int4 mi, double wd, double re, double im, const KState* __restrict__ ks,
+                                           int4* __restrict__ cm, float4* __restrict__ cf)
+{
+    const double kx = (double)mi.x * ks->inv[0], ky = (double)mi.y * ks->inv[1], kz = (double)mi.z * ks->inv[2];
+    const double kk = 4.0 * kPi * kPi * (kx * kx + ky * ky + kz * kz);
+    const double R = wd * (4.0 * kPi / ks->V) / kk * sqrt(re * re + im * im);
+    const float Rf = (float)R;
+    const double phi = (double)atan2f((float)im, (float)re) * 683565275.57643158978;  // revolutions x 2^32
+    const uint32_t off = 0x80000100u - (uint32_t)(unsigned long long)__double2ll_rn(phi);
+    *cm = make_int4(mi.x, mi.y, mi.z, (int)off);
+    *cf = make_float4(Rf, Rf * (float)mi.x, Rf * (float)mi.y, Rf * (float)mi.z);
+}
+
 __device__ __forceinline__ void reduce_f32_row(int l, const float4* __restrict__ partials, int nchunks, int K,
                                                const int4* __restrict__ m,
              const double* __restrict__ w, const KState* __restrict__ ks, double2* __restrict__ rho,
-             float* __restrict__ terms, int4* __restrict__ coef_m, float4* __restrict__ coef_f,
+             double* __restrict__ terms, int4* __restrict__ coef_m, float4* __restrict__ coef_f,
              unsigned* __restrict__ status)
 {
     __shared__ float red[2][32];
@@ -385,11 +420,9 @@ __device__ __forceinline__ void reduce_f32_row(int l, const float4* __restrict__
     // launch start only after that wait: m, w and ks are final here
     int4 mi = make_int4(0, 0, 0, 0);
     double wd = 0.0;
-    float cx = 0.f, cy = 0.f, cz = 0.f, ce = 0.f, cb = 0.f, inv4a = 0.f;
     if (threadIdx.x == 0 && l < K) {
         mi = m[l];
         wd = w[l];
-        cx = ks->cx; cy = ks->cy; cz = ks->cz; ce = ks->ce; cb = ks->cb; inv4a = ks->inv4a;
     }
     pdl_wait();
     pdl_trigger();
@@ -403,82 +436,50 @@ __device__ __forceinline__ void reduce_f32_row(int l, const float4* __restrict__
     block_sum_ff(rh, rl, red);
     block_sum_ff(ih, il, red);
     if (threadIdx.x != 0) return;
-    float* t = terms + (size_t)l * 8;
+    double* t = terms + (size_t)l * 8;
+    const double re = ff_to_double(rh, rl), im = ff_to_double(ih, il);
     if (l == K) {
-        t[0] = rh;  // sum of q^2 as float-float
-        t[1] = rl;
+        t[0] = re;  // sum of q^2
         return;
     }
-    const float re = rh + rl, im = ih + il;
-    const float wl = double_to_float_int((unsigned long long)__double_as_longlong(wd));
-    const float kx = cx * (float)mi.x, ky = cy * (float)mi.y, kz = cz * (float)mi.z;
-    const float kk = kx * kx + ky * ky + kz * kz;
-    const float ikk = 1.0f / kk;
-    const float rho2 = re * re + im * im;
-    const float e = ce * wl * rho2 * ikk;
-    const float b = 2.0f * (ikk + inv4a);
-    t[0] = e;
-    t[1] = e * (1.0f - b * kx * kx);
-    t[2] = e * (1.0f - b * ky * ky);
-    t[3] = e * (1.0f - b * kz * kz);
-    t[4] = -e * b * kx * ky;
-    t[5] = -e * b * kx * kz;
-    t[6] = -e * b * ky * kz;
-    t[7] = 0.f;
-    // Im(e^{-ik.r} rho) = |rho| sin(arg rho - theta): the force pass takes one sine per pair of
-    // the phase shifted by arg rho (harmonic addition), its amplitude R = beta |rho| folded
-    // into the coefficients, and arg rho as a 32-bit fixed-point offset of the phase.
-    const float beta = cb * wl * ikk;
-    const float R = beta * sqrtf(rho2);
-    const double phi = (double)atan2f(im, re) * 683565275.57643158978;  // revolutions x 2^32
-    const uint32_t off = 0x80000100u - (uint32_t)(unsigned long long)__double2ll_rn(phi);
-    rho[l] = make_double2(ff_to_double(rh, rl), ff_to_double(ih, il));
-    coef_m[l] = make_int4(mi.x, mi.y, mi.z, (int)off);
-    coef_f[l] = make_float4(R, R * (float)mi.x, R * (float)mi.y, R * (float)mi.z);
+    freq_terms_f64(mi, wd, re, im, ks, t);
+    force_coef(mi, wd, re, im, ks, coef_m + l, coef_f + l);
+    rho[l] = make_double2(re, im);
     if (!isfinite(re) || !isfinite(im)) atomicOr(status, kStatusNonFinite);
 }
 
-// Energy and virial: fixed-order float-float sums of the per-frequency terms over l, by one
-// block of kForceThreads threads.
-__device__ __forceinline__ void final_sums_f32(const float* __restrict__ terms, int K, float cself,
-                                               double* __restrict__ W_out, double* __restrict__ E_out,
-                                               unsigned* __restrict__ status)
+// Energy and virial: fixed-order FP64 sums of the per-frequency terms over l, by one block
+// of kForceThreads threads; E_self = -sqrt(alpha/pi) sum q^2 in FP64.
+__device__ __forceinline__ void final_sums(const double* __restrict__ terms, int K, const KState* __restrict__ ks,
+                                           double* __restrict__ W_out, double* __restrict__ E_out,
+                                           unsigned* __restrict__ status)
 {
-    __shared__ float fin[kForceWarps][14];
-    float ah[7] = {0, 0, 0, 0, 0, 0, 0}, al[7] = {0, 0, 0, 0, 0, 0, 0};
+    __shared__ double fin[kForceWarps][7];
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int j = threadIdx.x; j < K; j += blockDim.x) {
-        const float* t = terms + (size_t)j * 8;
+        const double* t = terms + (size_t)j * 8;
 #pragma unroll
-        for (int a = 0; a < 7; ++a) ff_add(ah[a], al[a], t[a]);
+        for (int a = 0; a < 7; ++a) acc[a] += t[a];
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int a = 0; a < 7; ++a) {
+        double v = acc[a];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const float oh = __shfl_xor_sync(0xffffffffu, ah[a], off);
-            const float ol = __shfl_xor_sync(0xffffffffu, al[a], off);
-            ff_add2(ah[a], al[a], oh, ol);
-        }
-        if (lane == 0) {
-            fin[warp][2 * a] = ah[a];
-            fin[warp][2 * a + 1] = al[a];
-        }
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) fin[warp][a] = v;
     }
     __syncthreads();
     // thread a (< 7) finishes term a; thread 7 the self energy
     if (threadIdx.x < 8) {
         const int a = threadIdx.x;
-        float th = 0.f, tl = 0.f;
+        double v = 0.0;
         if (a < 7) {
-            for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) ff_add2(th, tl, fin[wv][2 * a], fin[wv][2 * a + 1]);
+            for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) v += fin[wv][a];
         } else {
-            const float q2h = terms[(size_t)K * 8], q2l = terms[(size_t)K * 8 + 1];
-            ff_add(th, tl, cself * q2h);
-            tl += cself * q2l;
+            v = -sqrt(ks->alpha / kPi) * terms[(size_t)K * 8];
         }
-        const double v = ff_to_double(th, tl);
-        if (!isfinite(th)) atomicOr(status, kStatusNonFinite);
+        if (!isfinite(v)) atomicOr(status, kStatusNonFinite);
         if (a == 0 && E_out) E_out[0] = v;
         if (a == 7 && E_out) E_out[1] = v;
         if (W_out) {

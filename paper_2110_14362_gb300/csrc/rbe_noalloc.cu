@@ -10,7 +10,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 #include <string>
 
 #include "rbe_context.h"
@@ -144,28 +143,21 @@ k_sample_noalloc(unsigned long long* __restrict__ scratch, double bx, double by,
     }
 }
 
-// Device address of the scratch array, looked up once per device (host code may not use
-// the symbol itself as an address).
-static std::mutex g_noalloc_mutex;
-static unsigned long long* g_noalloc_ptr[64] = {nullptr};
-
-static rbe_status noalloc_scratch(int device, unsigned long long** out, std::string& err)
+// Device address of the scratch array in the CUDA context current on the calling thread
+// (host code may not use the symbol itself as an address).  Looked up on every call: the
+// address belongs to the context that loaded the module, and a caller may switch contexts
+// (a plugin inside an application with its own driver context) or rebuild the primary
+// context (cudaDeviceReset), after which an address kept from an earlier call would be stale.
+// The lookup is a host-side query; it allocates nothing.
+static rbe_status noalloc_scratch(unsigned long long** out, std::string& err)
 {
-    if (device < 0 || device >= 64) {
-        err = "device ordinal out of range";
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        err = std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e);
         return RBE_ECUDA;
     }
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[device]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            err = std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e);
-            return RBE_ECUDA;
-        }
-        g_noalloc_ptr[device] = static_cast<unsigned long long*>(p);
-    }
-    *out = g_noalloc_ptr[device];
+    *out = static_cast<unsigned long long*>(p);
     return RBE_OK;
 }
 
@@ -193,16 +185,13 @@ extern "C" rbe_status rbe_sample_k_noalloc(const double box[3], double alpha, in
     }
     if (reinterpret_cast<uintptr_t>(m_out) % 4 != 0 || reinterpret_cast<uintptr_t>(S_out) % 8 != 0)
         return fail(nullptr, RBE_EINVAL, "m_out must be 4-byte and S_out 8-byte aligned device memory");
-    int device = 0;
-    cudaError_t e = cudaGetDevice(&device);
-    if (e != cudaSuccess) return fail(nullptr, RBE_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     unsigned long long* scratch = nullptr;
     std::string err;
-    rbe_status st = noalloc_scratch(device, &scratch, err);
+    rbe_status st = noalloc_scratch(&scratch, err);
     if (st != RBE_OK) return fail(nullptr, st, err);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     k_sample_noalloc<<<1, kNoAllocThreads, 0, s>>>(scratch, box[0], box[1], box[2], alpha, P, seed, step, m_out, S_out);
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(nullptr, RBE_ECUDA, std::string("k_sample_noalloc: ") + cudaGetErrorString(e));
     unsigned bits = 0;
     e = cudaMemcpyAsync(&bits, scratch + 3 * kNoAllocTableCap, sizeof(unsigned), cudaMemcpyDeviceToHost, s);

@@ -11,6 +11,12 @@ from paper_2110_14362_gb300 import _binding as B
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
+# status codes in the numbering of the library's specification (RBE_ESTATE = 6; RBE_ESAMPLE,
+# which the specification does not list, after it), precisions, rho accumulations, samplers
+ENUMS = ["RBE_OK", "RBE_EINVAL", "RBE_ENOMEM", "RBE_ECUDA", "RBE_ETIMEOUT", "RBE_ENONFINITE", "RBE_ESTATE",
+         "RBE_ESAMPLE", "RBE_FP64", "RBE_FP32_PHASE", "RBE_RHO_FP64", "RBE_RHO_COMP32", "RBE_RHO_FP32",
+         "RBE_SAMPLER_EXACT", "RBE_SAMPLER_OFFLINE", "RBE_SAMPLER_MH"]
+
 STRUCTS = {
     "rbe_npt_params": B.NptParams,
     "rbe_system": B.System,
@@ -29,6 +35,8 @@ def _c_layout(tmp_path):
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
         for f in py._fields_:
             lines.append(f'printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    for name in ENUMS:
+        lines.append(f'printf("{name} %d\\n", (int){name});')
     lines.append('printf("RBE_CELL_DOUBLES %d\\n", RBE_CELL_DOUBLES);')
     lines.append('printf("RBE_FLEX_CELL_DOUBLES %d\\n", RBE_FLEX_CELL_DOUBLES);')
     lines += ["return 0;", "}"]
@@ -47,5 +55,8 @@ def test_ctypes_structs_match_header(tmp_path):
         assert c[f"{cname} size"] == ctypes.sizeof(py), cname
         for f in py._fields_:
             assert c[f"{cname} {f[0]}"] == getattr(py, f[0]).offset, (cname, f[0])
+    for name in ENUMS:
+        assert c[name] == getattr(B, name), name
+    assert (B.RBE_ESTATE, B.RBE_ESAMPLE) == (6, 7)
     assert c["RBE_CELL_DOUBLES"] == B.RBE_CELL_DOUBLES
     assert c["RBE_FLEX_CELL_DOUBLES"] == B.RBE_FLEX_CELL_DOUBLES
