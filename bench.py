@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 
 from paper_2110_14362_gb300 import inputs  # noqa: E402
 
-METRIC = "RBE k-space N*P pair evaluations/s (FP32-phase; FP64 alongside)"
+METRIC = "RBE k-space N*P pair evaluations/s (FP32-phase at 1e-5; FP64 alongside)"
 UNIT = "pair-evals/s"
 SEED = 12345
 
@@ -42,7 +42,11 @@ MUFU_OPS_PER_PAIR = {"k_rho": 2.0, "k_force": 1.0}
 # DRAM bytes per launch of the dominant kernel measured by ncu on this workload
 # (dram__bytes_read.sum + dram__bytes_write.sum), or None when not captured for the
 # current kernel version.  Source: profiles/ summaries.
-NCU_TRAFFIC = {("k_force", "slab"): 9652395, ("k_rho", "slab"): 9626880}
+NCU_TRAFFIC = {}
+
+# launches of the library's own kernels per evaluation at a fixed box: the sampler, the rho
+# pass, the rho reduction and the force pass
+GPU_LAUNCHES_PER_STEP = 4
 
 
 def workload(name: str):
@@ -146,14 +150,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def run_ours(args, world, rank, local):
-    import torch
-    import paper_2110_14362_gb300 as rbe
+ACCUM_NAMES = {0: "fp64 per pair", 1: "compensated fp32 (Kahan) per tile, float-float across tiles",
+               2: "plain fp32 per tile, float-float across tiles"}
 
+
+def measure_kspace(rbe, s, args, world, rank, local, precision, accum, with_fp64=True, with_e2e=True):
+    """One k-space workload through rbe_kspace_forces_virial: device-timed pair evaluations/s
+    (CUDA events per step on the launching stream, L2 flushed between steps outside the events),
+    per-kernel times, the roofline of the dominant kernel, the end-to-end rate through the
+    host-buffer call, the FP64 path on the same workload and the errors of the FP32-phase path
+    against it on one shared batch."""
+    import torch
     dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    s = workload(args.workload)
-    precision = rbe.RBE_FP32_PHASE if args.precision == "fp32" else rbe.RBE_FP64
     pos = torch.as_tensor(s.pos).to(dev).contiguous()
     q = torch.as_tensor(s.q).to(dev).contiguous()
     F = torch.empty((s.N, 3), dtype=torch.float64, device=dev)
@@ -162,6 +170,7 @@ def run_ours(args, world, rank, local):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     seed = SEED + rank
+    pairs = float(s.N) * s.P
 
     def timed_loop(ctx, steps, warmup, first_step):
         ctx.set_stream(stream.cuda_stream)
@@ -182,37 +191,51 @@ def run_ours(args, world, rank, local):
         barrier(world)
         wall = time.perf_counter() - t0
         ctx.sync()
-        ms = [a.elapsed_time(b) for a, b in evs]
-        return ms, wall
+        return [a.elapsed_time(b) for a, b in evs], wall
 
-    ctx = rbe.Context(s.box, s.alpha, s.P, seed, precision)
+    ctx = rbe.Context(s.box, s.alpha, s.P, seed, precision, accum)
     with ClockSampler(local) as clk:
         ms, wall = timed_loop(ctx, args.steps, args.warmup, 0)
     clocks = clk.summary()
-    dev_s = sum(ms) / 1e3
-    dev_s_max = max_over_ranks(world, dev_s)
-    pairs = float(s.N) * s.P
+    dev_s_max = max_over_ranks(world, sum(ms) / 1e3)
     value = world * args.steps * pairs / dev_s_max
 
     # per-kernel durations (live, CUDA events recorded by the library on its stream)
     ctx.set_kernel_timing(True)
     kt = []
-    for k in range(max(3, min(args.steps, 20))):
+    for k in range(max(3, min(args.steps, 10))):
         flush.fill_(float(k))
         ctx.forces_virial(pos, q, 10_000 + k, F, W, E)
         kt.append(ctx.kernel_times())
     ctx.set_kernel_timing(False)
-    kmean = np.mean(np.array(kt), axis=0)  # sample, rho, reduce, force
+    kmean = np.mean(np.array(kt), axis=0)
     names = ["k_sample", "k_rho", "k_reduce", "k_force"]
     dom = int(np.argmax(kmean))
+    out = {"value": value, "unit": UNIT, "ms_per_step": dev_s_max * 1e3 / args.steps, "wall_s_timed_region": wall,
+           "clocks": clocks, "phases_per_s": 2.0 * value,
+           "kernel_ms": {n: float(v) for n, v in zip(names, kmean)}}
 
-    # FP64 on the same workload, a few steps (the plain single-system FP64 path)
-    other = None
-    if args.precision == "fp32" and not args.skip_fp64:
+    if precision == rbe.RBE_FP32_PHASE:
+        peak = rbe.rbe_measure_pipe(0, 4096)
+        dom_ms = float(kmean[dom])
+        achieved = MUFU_OPS_PER_PAIR[names[dom]] * pairs / (dom_ms * 1e-3)
+        out["roofline"] = {
+            "bound": "alu", "pipe": "MUFU (sin/cos)", "kernel": names[dom], "achieved": achieved / 1e9,
+            "peak": peak / 1e9, "unit": "Gop/s", "frac": achieved / peak,
+            "peak_source": "of measured: MUFU sin.approx rate on this GPU (rbe_measure_pipe; 16/clk/SM x 152 SMs "
+                           "x 2.07 GHz nominal)",
+            "traffic": NCU_TRAFFIC.get((names[dom], s.name))}
+        # the whole evaluation against the same peak, at the schedule's 3 MUFU operations per pair
+        out["evaluation_mufu_frac"] = 3.0 * value / world / peak
+        # and against the algorithmic minimum of one sine and one cosine per pair
+        out["evaluation_mufu_frac_algorithmic_min"] = 2.0 * value / world / peak
+
+    if with_fp64 and precision == rbe.RBE_FP32_PHASE:
         ctx64 = rbe.Context(s.box, s.alpha, s.P, seed, rbe.RBE_FP64)
-        ms64, _ = timed_loop(ctx64, max(2, min(args.steps, 5)), 2, 50_000)
+        n64 = 2 if pairs > 1e9 else max(2, min(args.steps, 5))
+        ms64, _ = timed_loop(ctx64, n64, 1 if pairs > 1e9 else 2, 50_000)
         other = {"precision": "fp64", "value": pairs / (sum(ms64) / len(ms64) / 1e3), "unit": UNIT,
-                 "ms_per_step": sum(ms64) / len(ms64)}
+                 "ms_per_step": sum(ms64) / len(ms64), "steps": n64}
         # accuracy of the timed FP32-phase path against the FP64 path on the same frequencies
         # (the same seed and step draw the same batch in both contexts)
         ctx64.forces_virial(pos, q, 60_000, F, W, E)
@@ -226,47 +249,56 @@ def run_ours(args, world, rank, local):
             "force_rel_rms": float(np.sqrt(np.mean((F1 - F0) ** 2) / np.mean(F0 ** 2))),
             "virial_rel": float(np.linalg.norm(W1 - W0) / np.linalg.norm(W0)),
             "pressure_diag_rel": [float(x) for x in dW / np.abs(np.diag(W0))],
+            "pressure_diag_err_over_max_diag": float(np.max(dW) / np.max(np.abs(np.diag(W0)))),
             "energy_rel": float(abs(E1[0] - E0[0]) / abs(E0[0])),
             "bar": "force relative RMS <= 1e-5"}
+        out["fp32_phase_over_fp64"] = value / world / other["value"]
+        out["fp64_same_workload"] = other
         ctx64.close()
 
-    # end to end through the public host-buffer call: pinned host inputs in, forces out
-    pos_h = torch.empty((s.N, 3), dtype=torch.float64, pin_memory=True)
-    q_h = torch.empty((s.N,), dtype=torch.float64, pin_memory=True)
-    F_h = torch.empty((s.N, 3), dtype=torch.float64, pin_memory=True)
-    pos_h.copy_(torch.as_tensor(s.pos))
-    q_h.copy_(torch.as_tensor(s.q))
-    pn, qn, Fn = pos_h.numpy(), q_h.numpy(), F_h.numpy()
-    for w in range(2):
-        rbe.rbe_kspace_forces_virial_host(ctx.h, pn, qn, 20_000 + w, Fn)
-    barrier(world)
-    t0 = time.perf_counter()
-    for k in range(args.steps):
-        rbe.rbe_kspace_forces_virial_host(ctx.h, pn, qn, 30_000 + k, Fn)
-    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
-    e2e = {"value": world * args.steps * pairs / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(pn.nbytes + qn.nbytes),
-           "d2h_bytes_per_step": int(Fn.nbytes + 11 * 8)}
-
-    # roofline of the dominant kernel against the measured MUFU throughput
-    peak_mufu = rbe.rbe_measure_pipe(0, 4096)
-    dom_ms = float(kmean[dom])
-    if args.precision == "fp32" and names[dom] in ("k_rho", "k_force"):
-        achieved = MUFU_OPS_PER_PAIR[names[dom]] * pairs / (dom_ms * 1e-3)
-        roof = {"bound": "alu", "pipe": "MUFU (sin/cos)", "kernel": names[dom], "achieved": achieved / 1e9,
-                "peak": peak_mufu / 1e9, "unit": "Gop/s", "frac": achieved / peak_mufu,
-                "peak_source": "measured on this GPU by rbe_measure_pipe(MUFU sin.approx)",
-                "traffic": NCU_TRAFFIC.get((names[dom], args.workload))}
-    else:
-        peak_dfma = rbe.rbe_measure_pipe(2, 1024)
-        roof = {"bound": "alu", "pipe": "FP64 FMA", "kernel": names[dom], "achieved": None,
-                "peak": peak_dfma / 1e9, "unit": "GDFMA/s", "frac": None, "traffic": None}
+    if with_e2e:
+        # end to end through the public host-buffer call: pinned host inputs in, forces out
+        pos_h = torch.empty((s.N, 3), dtype=torch.float64, pin_memory=True)
+        q_h = torch.empty((s.N,), dtype=torch.float64, pin_memory=True)
+        F_h = torch.empty((s.N, 3), dtype=torch.float64, pin_memory=True)
+        pos_h.copy_(torch.as_tensor(s.pos))
+        q_h.copy_(torch.as_tensor(s.q))
+        pn, qn, Fn = pos_h.numpy(), q_h.numpy(), F_h.numpy()
+        for w in range(2):
+            rbe.rbe_kspace_forces_virial_host(ctx.h, pn, qn, 20_000 + w, Fn)
+        barrier(world)
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            rbe.rbe_kspace_forces_virial_host(ctx.h, pn, qn, 30_000 + k, Fn)
+        e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+        out["e2e"] = {"value": world * args.steps * pairs / e2e_s, "unit": UNIT,
+                      "h2d_bytes_per_step": int(pn.nbytes + qn.nbytes),
+                      "d2h_bytes_per_step": int(Fn.nbytes + 11 * 8)}
     ctx.close()
+    del pos, q, F, flush
+    return out
 
+
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_2110_14362_gb300 as rbe
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    s = workload(args.workload)
+    precision = rbe.RBE_FP32_PHASE if args.precision == "fp32" else rbe.RBE_FP64
+    accum = {"comp32": rbe.RBE_RHO_COMP32, "fp32": rbe.RBE_RHO_FP32, "fp64": rbe.RBE_RHO_FP64}[args.rho_accum]
+    head = measure_kspace(rbe, s, args, world, rank, local, precision, accum, with_fp64=not args.skip_fp64)
+
+    extra = {}
+    if not args.skip_slab and args.workload != "slab":
+        # the semi-isotropic slab (300k charges, P = 200): Pxx, Pyy, Pzz of both paths
+        extra["slab"] = dict(workload="slab-N300000-P200", rho_accum=ACCUM_NAMES[accum],
+                             **measure_kspace(rbe, workload("slab"), args, world, rank, local, precision, accum))
     serving = None if args.skip_serving else run_serving(args, world, rank)
     npt1 = None if args.skip_serving else run_npt_single(rbe, [1000, 10000, 100000], 20)
     batched = None if args.skip_serving else run_batched(rbe)
-    water = None if args.skip_serving else run_water(rbe, steps=1000, warmup=20)
+    water = None if args.skip_serving else run_water_both(rbe)
     sweep = None if args.skip_sweep else run_sweep(rbe)
 
     cpu = cpu_all = None
@@ -275,26 +307,33 @@ def run_ours(args, world, rank, local):
         cpu_all = cpu_baseline_all_cores(s, budget_s=args.cpu_seconds / 3)
 
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": dev_s_max * 1e3 / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32-phase/f64-accum" if args.precision == "fp32" else "f64",
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32-phase (int32 fixed-point phase, fp32 sincos) / f64 sums" if precision == rbe.RBE_FP32_PHASE
+                 else "f64",
         "data": "synthetic (seeded NumPy; shapes of the paper's workloads)",
         "config": {"workload": s.name, "N": s.N, "P": s.P, "alpha": s.alpha, "box": [float(b) for b in s.box],
-                   "precision": args.precision, "rho_accum": "fp32-tile/fp64", "l2": "flushed between steps (256 MB write)",
+                   "precision": args.precision,
+                   "rho_accum": ACCUM_NAMES[accum] if precision == rbe.RBE_FP32_PHASE else "fp64",
+                   "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world} (independent systems, no collective)"},
-        # phases evaluated per second: one per pair in each of the two passes (2 N P per evaluation)
-        "phases_per_s": 2.0 * value,
-        "kernel_ms": {n: float(v) for n, v in zip(names, kmean)},
-        "wall_s_timed_region": wall,
-        "gpu_launches": 4 * args.steps,
-        "e2e": e2e,
-        "roofline": roof,
+        "phases_per_s": head["phases_per_s"],
+        "kernel_ms": head["kernel_ms"],
+        "wall_s_timed_region": head["wall_s_timed_region"],
+        "gpu_launches": GPU_LAUNCHES_PER_STEP * args.steps,
+        "e2e": head["e2e"],
+        "roofline": head.get("roofline"),
+        "evaluation_mufu_frac": head.get("evaluation_mufu_frac"),
+        "evaluation_mufu_frac_algorithmic_min": head.get("evaluation_mufu_frac_algorithmic_min"),
         "cpu_baseline": cpu,
         "cpu_baseline_all_cores": cpu_all,
-        "clocks": clocks,
+        "clocks": head["clocks"],
     }
-    if other:
-        line["fp64_same_workload"] = other
+    if "fp64_same_workload" in head:
+        line["fp64_same_workload"] = head["fp64_same_workload"]
+        line["fp32_phase_over_fp64"] = head["fp32_phase_over_fp64"]
+    line.update(extra)
     if serving:
         line["serving"] = serving
     if batched:
@@ -426,14 +465,15 @@ def run_npt_single(rbe, sizes, steps):
 WATER_MASS = (15.9994, 1.008, 1.008)
 
 
-def run_water(rbe, steps=1000, warmup=20, alpha=None, barostat=1):
+def run_water(rbe, steps=1000, warmup=20, alpha=None, barostat=1, dense_steps=10):
     """The plain-method rigid-water NPT run: 3000 molecules (O -0.8476, H +0.4238, O-H 1 A,
     H-O-H 109.47 deg, LJ O-O 3.166 A / 0.650 kJ/mol) at random orientations on a jittered lattice
     at 1 g/cm^3 (`inputs.water`), alpha = 0.25, rc = 10 A, P = 100, FP64, Langevin isotropic NPT at
     300 K and 1 bar, dt = 1 fs, a 0.05 A cap on the centres' peculiar displacement per step (the
     random orientations overlap at the start).  ms per step by CUDA events over `steps` steps after
     `warmup`; density, molecular pressure, temperature (6 degrees of freedom per molecule) and the
-    largest bond error at the end.  alpha (default: the configuration's 0.25) and barostat (0: fixed
+    largest bond error at the end; `dense_steps` steps after the first three timed on their own
+    (the system still at 1 g/cm^3), with the density and temperature after them.  alpha (default: the configuration's 0.25) and barostat (0: fixed
     box) can be changed to study the run."""
     import torch
     s = inputs.water(3000)
@@ -449,28 +489,50 @@ def run_water(rbe, steps=1000, warmup=20, alpha=None, barostat=1):
     stream = torch.cuda.current_stream()
     dev = torch.device("cuda", torch.cuda.current_device())
     a = s.alpha if alpha is None else alpha
+    def density(L):
+        return n * 18.01528 / (0.602214076 * float(np.prod(L)))
+
+    def temperature(p):
+        return float(np.sum(p ** 2 / m[:, None]) / 100.0 / (6 * n * KB))
+
+    def timed(rep, ctx, k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep.step(ctx, k)
+        e1.record(stream)
+        ctx.sync()
+        return e0.elapsed_time(e1) / k
+
     with rbe.Context(box, a, s.P, 2024, rbe.RBE_FP64, stream=stream.cuda_stream) as ctx:
         rep = rbe.WaterReplica(np.asarray(s.pos), mom, np.asarray(s.q), m, box, prm, dev)
         rep.init(ctx, batch=0)
-        rep.step(ctx, warmup)
+        rep.step(ctx, 3)
         ctx.sync()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        rep.step(ctx, steps)
-        e1.record(stream)
+        # the first steps, still at the starting density of 1 g/cm^3
+        ms_dense = timed(rep, ctx, dense_steps)
+        _, p_d, _, L_d, _ = rep.state()
+        rep.step(ctx, max(0, warmup - 3 - dense_steps))
         ctx.sync()
-        ms = e0.elapsed_time(e1) / steps
+        ms = timed(rep, ctx, steps)
         r, p, F, L, cell = rep.state()
     mol = r.reshape(-1, 3, 3)
     bond = float(np.abs(np.linalg.norm(mol[:, 1:] - mol[:, :1], axis=2) - 1.0).max())
-    V = float(np.prod(L))
-    T = float(np.sum(p ** 2 / m[:, None]) / 100.0 / (6 * n * KB))
     return {"molecules": n, "sites": 3 * n, "alpha": a, "P": s.P, "rc": 10.0, "precision": "fp64",
             "barostat": barostat, "steps": steps, "warmup": warmup, "ms_per_step": ms, "steps_per_s": 1e3 / ms,
-            "T_K": T,
+            "T_K": temperature(p), "density_g_cm3": density(L), "P_ins_bar": float(cell[6]) / BAR,
             "site_pair_evals_per_s": 3 * n * s.P / (ms * 1e-3),
-            "density_g_cm3": n * 18.01528 / (0.602214076 * V), "P_ins_bar": float(cell[6]) / BAR,
+            "first_steps": {"steps": dense_steps, "ms_per_step": ms_dense, "density_g_cm3_after": density(L_d),
+                            "T_K_after": temperature(p_d)},
             "max_bond_error_A": bond}
+
+
+def run_water_both(rbe, steps=1000, warmup=20):
+    """The water configuration's run at its alpha = 0.25 (the RBE force noise of P = 100 heats
+    it and the cell expands: final T and density are reported beside the ms per step, and the
+    first steps at 1 g/cm^3 are timed on their own) and the same run at alpha = 0.08, which
+    holds ~300 K and ~1 g/cm^3 over the run."""
+    return {"configuration_alpha_0.25": run_water(rbe, steps=steps, warmup=warmup),
+            "alpha_0.08": run_water(rbe, steps=steps, warmup=warmup, alpha=0.08)}
 
 
 def run_general(rbe, steps=20, warmup=3):
@@ -630,6 +692,43 @@ def run_sweep(rbe, steps=3):
                         r["pressure_diag_err_over_max_diag"] = float(np.max(dW) / np.max(np.abs(np.diag(W0))))
                         r["energy_rel"] = float(abs(E1[0] - E0[0]) / abs(E0[0]))
                     row[name] = r
+            # float32 (x, y, z, q) input, compensated accumulation: the error of the input's rounding
+            # (the FP64 path on the rounded positions against the FP64 path on the FP64 ones) apart
+            # from the error of the evaluation (against the FP64 path on the rounded positions)
+            xyzq = torch.cat([pos, q[:, None]], dim=1).to(torch.float32).contiguous()
+            pos_r = xyzq[:, :3].to(torch.float64).contiguous()
+            q_r = xyzq[:, 3].to(torch.float64).contiguous()
+            with rbe.Context(s.box, s.alpha, P, SEED, rbe.RBE_FP64, stream=stream.cuda_stream) as ctx:
+                ctx.forces_virial(pos_r, q_r, 7, F, W, E)
+                ctx.sync()
+                Fr, Wr, Er = F.cpu().numpy(), W.cpu().numpy().reshape(3, 3), E.cpu().numpy()
+            with rbe.Context(s.box, s.alpha, P, SEED, rbe.RBE_FP32_PHASE, rbe.RBE_RHO_COMP32,
+                             stream=stream.cuda_stream) as ctx:
+                ctx.forces_virial_xyzq(xyzq, 7, F, W, E)
+                ms = []
+                for k in range(steps):
+                    flush.fill_(float(k))
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ctx.forces_virial_xyzq(xyzq, 7, F, W, E)
+                    e1.record(stream)
+                    ms.append((e0, e1))
+                torch.cuda.synchronize()
+                ctx.sync()
+                t = float(np.mean([a.elapsed_time(b) for a, b in ms])) * 1e-3
+                F1, W1, E1 = F.cpu().numpy(), W.cpu().numpy().reshape(3, 3), E.cpu().numpy()
+            F0, W0, E0 = ref
+
+            def errs(Fa, Wa, Ea, Fb, Wb, Eb):
+                return {"force_rel_rms": float(np.sqrt(np.mean((Fa - Fb) ** 2) / np.mean(Fb ** 2))),
+                        "virial_rel": float(np.linalg.norm(Wa - Wb) / np.linalg.norm(Wb)),
+                        "pressure_diag_rel_max": float(np.max(np.abs(np.diag(Wa) - np.diag(Wb)) / np.abs(np.diag(Wb)))),
+                        "energy_rel": float(abs(Ea[0] - Eb[0]) / abs(Eb[0]))}
+            row["fp32_xyzq_comp32"] = {"pair_evals_per_s": N * P / t, "ms": t * 1e3,
+                                       "mufu_frac_of_measured": 3.0 * N * P / t / peak,
+                                       "input_rounding_error": errs(Fr, Wr, Er, F0, W0, E0),
+                                       "compute_error": errs(F1, W1, E1, Fr, Wr, Er)}
+            del xyzq, pos_r, q_r
             out.append(row)
         del pos, q, F
     return {"system": "uniform +-1 charges at 0.1 per A^3, alpha = 0.2", "steps": steps,
@@ -745,7 +844,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="slab")
+    ap.add_argument("--workload", default="uniform4e6-P2000")
+    ap.add_argument("--rho-accum", choices=["comp32", "fp32", "fp64"], default="comp32",
+                    help="rho accumulation of the FP32-phase path (default: compensated FP32)")
+    ap.add_argument("--skip-slab", action="store_true", help="leave out the slab workload's line")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")

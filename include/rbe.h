@@ -184,6 +184,16 @@ rbe_status rbe_kspace_forces_virial(rbe_ctx ctx, int64_t N, const double* positi
                                     const double* charges, uint64_t step, double* forces_out,
                                     double* virial_out, double* energy_out);
 
+/* The same evaluation with float32 positions and charges: xyzq is device memory holding one
+ * float4 (x, y, z, q) per particle, N*4 floats, 16-byte aligned.  Each coordinate is widened to
+ * the double it equals (exactly) and enters the same exact fixed-point phase as the FP64 input,
+ * so the result is the evaluation of the float-rounded positions and charges: the error of the
+ * input's rounding is separate from the path's own.  Needs the RBE_FP32_PHASE precision
+ * (RBE_EINVAL otherwise); the context's rho accumulation applies.  Other arguments as
+ * rbe_kspace_forces_virial.  Asynchronous. */
+rbe_status rbe_kspace_forces_virial_xyzq(rbe_ctx ctx, int64_t N, const float* xyzq, uint64_t step,
+                                         double* forces_out, double* virial_out, double* energy_out);
+
 /* The same evaluation on HOST buffers: copies positions and charges to context-owned
  * device buffers, evaluates, copies forces, virial and energy back, synchronises the
  * stream and returns any latched device error.  forces_out may be NULL.  On the FP32-phase

@@ -34,6 +34,7 @@ _lib = None
 _c_double_p = ctypes.POINTER(ctypes.c_double)
 _c_int32_p = ctypes.POINTER(ctypes.c_int32)
 _c_uint32_p = ctypes.POINTER(ctypes.c_uint32)
+_c_int64_p = ctypes.POINTER(ctypes.c_int64)
 
 
 def build(force: bool = False) -> str:
@@ -77,6 +78,11 @@ def _load_omp():
                                            ctypes.c_double, ctypes.c_int32, _c_int32_p, _c_double_p,
                                            _c_double_p, _c_double_p, _c_double_p, _c_double_p]
             lib.orc_rbe_kspace.restype = ctypes.c_int
+            lib.orc_rbe_kspace_subset.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p,
+                                                  ctypes.c_double, ctypes.c_int32, _c_int32_p, _c_double_p,
+                                                  ctypes.c_int64, _c_int64_p, _c_double_p, _c_double_p,
+                                                  _c_double_p, _c_double_p]
+            lib.orc_rbe_kspace_subset.restype = ctypes.c_int
             _lib_omp = lib
     return _lib_omp
 
@@ -110,6 +116,11 @@ def _load():
                                            ctypes.c_double, ctypes.c_int32, _c_int32_p, _c_double_p,
                                            _c_double_p, _c_double_p, _c_double_p, _c_double_p]
             lib.orc_rbe_kspace.restype = ctypes.c_int
+            lib.orc_rbe_kspace_subset.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p,
+                                                  ctypes.c_double, ctypes.c_int32, _c_int32_p, _c_double_p,
+                                                  ctypes.c_int64, _c_int64_p, _c_double_p, _c_double_p,
+                                                  _c_double_p, _c_double_p]
+            lib.orc_rbe_kspace_subset.restype = ctypes.c_int
             lib.orc_rbe_snapshot.argtypes = [ctypes.c_int64, _c_double_p, _c_double_p, _c_double_p,
                                              ctypes.c_double, ctypes.c_int32, ctypes.c_uint64,
                                              ctypes.c_uint64, _c_double_p, _c_double_p, _c_double_p,
@@ -389,6 +400,32 @@ def rbe_kspace(pos, q, box, alpha: float, m, weights, all_cores: bool = False):
     rho = np.zeros(2 * P)
     _check(lib.orc_rbe_kspace(N, _dp(pos), _dp(q), _dp(b), alpha, P, _ip(m), _dp(wl), _dp(F), _dp(W),
                               _dp(E), _dp(rho)), "rbe_kspace")
+    return F, W, E[0], E[1], rho[0::2] + 1j * rho[1::2]
+
+
+def rbe_kspace_subset(pos, q, box, alpha: float, m, weights, idx, all_cores: bool = False):
+    """The RBE estimators with the forces of the particles ``idx`` only: (F[len(idx),3],
+    W[3,3], E_k, E_self, rho[P] complex); rho, W and E over all particles.  Each force row is
+    the bits ``rbe_kspace`` gives for that particle."""
+    lib = _load_omp() if all_cores else _load()
+    pos = _f64(pos)
+    q = _f64(q)
+    N = q.shape[0]
+    m = np.ascontiguousarray(m, dtype=np.int32).reshape(-1, 3)
+    P = m.shape[0]
+    wl = np.asarray(weights, dtype=np.float64)
+    wl = np.full(P, float(wl)) if wl.ndim == 0 else np.ascontiguousarray(wl)
+    if wl.shape != (P,):
+        raise ValueError("weights must be a scalar or have one entry per frequency")
+    ix = np.ascontiguousarray(idx, dtype=np.int64).reshape(-1)
+    b = _f64(box, (3,))
+    F = np.zeros((ix.shape[0], 3))
+    W = np.zeros((3, 3))
+    E = np.zeros(2)
+    rho = np.zeros(2 * P)
+    _check(lib.orc_rbe_kspace_subset(N, _dp(pos), _dp(q), _dp(b), alpha, P, _ip(m), _dp(wl), ix.shape[0],
+                                     ix.ctypes.data_as(_c_int64_p), _dp(F), _dp(W), _dp(E), _dp(rho)),
+           "rbe_kspace_subset")
     return F, W, E[0], E[1], rho[0::2] + 1j * rho[1::2]
 
 

@@ -292,17 +292,19 @@ int orc_ewald_kspace(int64_t N, const double* pos, const double* q, const double
  * Built with -fopenmp (the all-cores timing build), the rho loop runs its frequencies and
  * the force loop its particles on several threads; each iteration's sums keep the index
  * order above, so both builds return the same bits. */
-int orc_rbe_kspace(int64_t N, const double* pos, const double* q, const double box[3],
-                   double alpha, int32_t P, const int32_t* m, const double* wl,
-                   double* F, double W[9], double E[2], double* rho)
+static int rbe_check(int64_t N, const double box[3], double alpha, int32_t P, const int32_t* m)
 {
     if (N < 0 || P < 0 || !(alpha > 0.0)) return ORC_EINVAL;
     for (int t = 0; t < 3; ++t) if (!(box[t] > 0.0)) return ORC_EINVAL;
-    double V = box[0] * box[1] * box[2];
-    double* rr = (double*)malloc(sizeof(double) * (size_t)(2 * P + 2));
-    if (!rr) return ORC_ENOMEM;
     for (int32_t l = 0; l < P; ++l)
-        if (m[3 * l] == 0 && m[3 * l + 1] == 0 && m[3 * l + 2] == 0) { free(rr); return ORC_EINVAL; }
+        if (m[3 * l] == 0 && m[3 * l + 1] == 0 && m[3 * l + 2] == 0) return ORC_EINVAL;
+    return ORC_OK;
+}
+
+/* rho_l = sum_i q_i e^{i k_l.r_i}, rr[2l] = Re, rr[2l+1] = Im (Sec. 4.1). */
+static void rbe_rho(int64_t N, const double* pos, const double* q, const double box[3], int32_t P,
+                    const int32_t* m, double* rr)
+{
 #pragma omp parallel for schedule(static)
     for (int32_t l = 0; l < P; ++l) {
         double k[3] = {2.0 * M_PI * m[3 * l] / box[0], 2.0 * M_PI * m[3 * l + 1] / box[1],
@@ -316,24 +318,32 @@ int orc_rbe_kspace(int64_t N, const double* pos, const double* q, const double b
         rr[2 * l] = re;
         rr[2 * l + 1] = im;
     }
-#pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < N; ++i) {
-        double f[3] = {0.0, 0.0, 0.0};
-        for (int32_t l = 0; l < P; ++l) {
-            double k[3] = {2.0 * M_PI * m[3 * l] / box[0], 2.0 * M_PI * m[3 * l + 1] / box[1],
-                           2.0 * M_PI * m[3 * l + 2] / box[2]};
-            double kk = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
-            double th = k[0] * pos[3 * i] + k[1] * pos[3 * i + 1] + k[2] * pos[3 * i + 2];
-            double imt = cos(th) * rr[2 * l + 1] - sin(th) * rr[2 * l];
-            double s = -wl[l] * (4.0 * M_PI * q[i] / (V * kk)) * imt;
-            f[0] += s * k[0];
-            f[1] += s * k[1];
-            f[2] += s * k[2];
-        }
-        F[3 * i] = f[0];
-        F[3 * i + 1] = f[1];
-        F[3 * i + 2] = f[2];
+}
+
+/* F_i = -sum_l w_l (4 pi q_i k_l / (V |k_l|^2)) Im(e^{-i k_l.r_i} rho_l) for one particle
+ * (Eq. (appforce)). */
+static void rbe_force_one(const double* r, double qi, const double box[3], double V, int32_t P,
+                          const int32_t* m, const double* wl, const double* rr, double f[3])
+{
+    f[0] = f[1] = f[2] = 0.0;
+    for (int32_t l = 0; l < P; ++l) {
+        double k[3] = {2.0 * M_PI * m[3 * l] / box[0], 2.0 * M_PI * m[3 * l + 1] / box[1],
+                       2.0 * M_PI * m[3 * l + 2] / box[2]};
+        double kk = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        double th = k[0] * r[0] + k[1] * r[1] + k[2] * r[2];
+        double imt = cos(th) * rr[2 * l + 1] - sin(th) * rr[2 * l];
+        double s = -wl[l] * (4.0 * M_PI * qi / (V * kk)) * imt;
+        f[0] += s * k[0];
+        f[1] += s * k[1];
+        f[2] += s * k[2];
     }
+}
+
+/* W (App. C) and E_k, E_self from rho (Eqs. (apppress), (U1fourier)). */
+static void rbe_virial_energy(int64_t N, const double* q, const double box[3], double alpha, int32_t P,
+                              const int32_t* m, const double* wl, const double* rr, double W[9], double E[2])
+{
+    double V = box[0] * box[1] * box[2];
     for (int j = 0; j < 9; ++j) W[j] = 0.0;
     double Ek = 0.0;
     for (int32_t l = 0; l < P; ++l) {
@@ -352,6 +362,47 @@ int orc_rbe_kspace(int64_t N, const double* pos, const double* q, const double b
     for (int64_t i = 0; i < N; ++i) q2 += q[i] * q[i];
     E[0] = Ek;
     E[1] = -sqrt(alpha / M_PI) * q2;
+}
+
+int orc_rbe_kspace(int64_t N, const double* pos, const double* q, const double box[3],
+                   double alpha, int32_t P, const int32_t* m, const double* wl,
+                   double* F, double W[9], double E[2], double* rho)
+{
+    int st = rbe_check(N, box, alpha, P, m);
+    if (st != ORC_OK) return st;
+    double V = box[0] * box[1] * box[2];
+    double* rr = (double*)malloc(sizeof(double) * (size_t)(2 * P + 2));
+    if (!rr) return ORC_ENOMEM;
+    rbe_rho(N, pos, q, box, P, m, rr);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) rbe_force_one(pos + 3 * i, q[i], box, V, P, m, wl, rr, F + 3 * i);
+    rbe_virial_energy(N, q, box, alpha, P, m, wl, rr, W, E);
+    if (rho) for (int32_t l = 0; l < 2 * P; ++l) rho[l] = rr[l];
+    free(rr);
+    return ORC_OK;
+}
+
+/* The same estimators with the forces of listed particles only: rho over all N particles,
+ * F_sub[j] = F_{idx[j]} (each row the bits orc_rbe_kspace gives for that particle), W and E
+ * as above.  For the largest workloads, where the forces of every particle would double a
+ * long oracle run, the forces are compared on a seeded subset. */
+int orc_rbe_kspace_subset(int64_t N, const double* pos, const double* q, const double box[3],
+                          double alpha, int32_t P, const int32_t* m, const double* wl,
+                          int64_t n_sub, const int64_t* idx, double* F_sub, double W[9], double E[2],
+                          double* rho)
+{
+    int st = rbe_check(N, box, alpha, P, m);
+    if (st != ORC_OK) return st;
+    if (n_sub < 0) return ORC_EINVAL;
+    for (int64_t j = 0; j < n_sub; ++j) if (idx[j] < 0 || idx[j] >= N) return ORC_EINVAL;
+    double V = box[0] * box[1] * box[2];
+    double* rr = (double*)malloc(sizeof(double) * (size_t)(2 * P + 2));
+    if (!rr) return ORC_ENOMEM;
+    rbe_rho(N, pos, q, box, P, m, rr);
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < n_sub; ++j)
+        rbe_force_one(pos + 3 * idx[j], q[idx[j]], box, V, P, m, wl, rr, F_sub + 3 * j);
+    rbe_virial_energy(N, q, box, alpha, P, m, wl, rr, W, E);
     if (rho) for (int32_t l = 0; l < 2 * P; ++l) rho[l] = rr[l];
     free(rr);
     return ORC_OK;

@@ -10,7 +10,7 @@ from ._binding import (  # noqa: F401
     RBE_FP64, RBE_FP32_PHASE, RBE_RHO_FP64, RBE_RHO_COMP32, RBE_RHO_FP32,
     RBEError, Context, load, library_path,
     rbe_create, rbe_destroy, rbe_set_stream, rbe_set_precision, rbe_set_box, rbe_sample_k,
-    rbe_kspace_forces_virial, rbe_kspace_forces_virial_host, rbe_kspace_weighted, rbe_get_rho, rbe_sync,
+    rbe_kspace_forces_virial, rbe_kspace_forces_virial_host, rbe_kspace_forces_virial_xyzq, rbe_kspace_weighted, rbe_get_rho, rbe_sync,
     rbe_version, rbe_set_kernel_timing, rbe_get_kernel_times, rbe_measure_pipe, rbe_sample_k_noalloc,
     NptParams, System, NptReplica, rbe_npt_init, rbe_npt_step, RBE_CELL_DOUBLES,
     WaterParams, water_params, WaterReplica, rbe_water_init, rbe_water_step, CELL_EXCL,

@@ -135,6 +135,7 @@ SIGNATURES = [
     ("rbe_set_box", ctypes.c_int, [_vp, _dp]),
     ("rbe_sample_k", ctypes.c_int, [_vp, ctypes.c_uint64, _ip, _dp]),
     ("rbe_kspace_forces_virial", ctypes.c_int, [_vp, ctypes.c_int64, _vp, _vp, ctypes.c_uint64, _vp, _vp, _vp]),
+    ("rbe_kspace_forces_virial_xyzq", ctypes.c_int, [_vp, ctypes.c_int64, _vp, ctypes.c_uint64, _vp, _vp, _vp]),
     ("rbe_kspace_forces_virial_host", ctypes.c_int,
      [_vp, ctypes.c_int64, _dp, _dp, ctypes.c_uint64, _dp, _dp, _dp]),
     ("rbe_kspace_weighted", ctypes.c_int,
@@ -283,6 +284,16 @@ def rbe_kspace_forces_virial(h, positions, charges, step: int, forces_out, viria
     N = int(charges.shape[0])
     _check(load().rbe_kspace_forces_virial(h, N, _ptr(positions), _ptr(charges), int(step), _ptr(forces_out),
                                            _ptr(virial_out), _ptr(energy_out)), h)
+
+
+def rbe_kspace_forces_virial_xyzq(h, xyzq, step: int, forces_out, virial_out=None, energy_out=None):
+    """Evaluation on float32 positions and charges: xyzq a torch float32 CUDA tensor (N, 4)."""
+    import torch
+    if xyzq.dtype != torch.float32 or xyzq.dim() != 2 or xyzq.shape[1] != 4:
+        raise ValueError("xyzq must be a float32 tensor of shape (N, 4)")
+    N = int(xyzq.shape[0])
+    _check(load().rbe_kspace_forces_virial_xyzq(h, N, _ptr(xyzq), int(step), _ptr(forces_out), _ptr(virial_out),
+                                                _ptr(energy_out)), h)
 
 
 def rbe_kspace_forces_virial_host(h, positions, charges, step: int, forces_out=None):
@@ -701,6 +712,9 @@ class Context:
 
     def forces_virial(self, positions, charges, step: int, forces_out, virial_out=None, energy_out=None):
         rbe_kspace_forces_virial(self.h, positions, charges, step, forces_out, virial_out, energy_out)
+
+    def forces_virial_xyzq(self, xyzq, step: int, forces_out, virial_out=None, energy_out=None):
+        rbe_kspace_forces_virial_xyzq(self.h, xyzq, step, forces_out, virial_out, energy_out)
 
     def forces_virial_host(self, positions, charges, step: int):
         return rbe_kspace_forces_virial_host(self.h, positions, charges, step)

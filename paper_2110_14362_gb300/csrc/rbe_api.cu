@@ -352,6 +352,28 @@ rbe_status rbe_kspace_forces_virial(rbe_ctx ctx, int64_t N, const double* positi
     return launch_rbe(ctx, N, positions, charges, ctx->P, forces_out, virial_out, energy_out);
 }
 
+rbe_status rbe_kspace_forces_virial_xyzq(rbe_ctx ctx, int64_t N, const float* xyzq, uint64_t step,
+                                         double* forces_out, double* virial_out, double* energy_out)
+{
+    if (!ctx) return RBE_EINVAL;
+    if (N < 0 || N > kMaxN) return fail(ctx, RBE_EINVAL, "N out of range [0, 2^31 - 256]");
+    if ((step >> 56) != 0) return fail(ctx, RBE_EINVAL, "step must be < 2^56");
+    if (ctx->precision != RBE_FP32_PHASE)
+        return fail(ctx, RBE_EINVAL, "float4 xyzq positions need the RBE_FP32_PHASE precision");
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(ctx, RBE_ECUDA, "cannot select the context's device");
+    rbe_status st;
+    if ((st = check_dev(ctx, xyzq, "xyzq", N > 0)) != RBE_OK) return st;
+    if (N > 0 && reinterpret_cast<uintptr_t>(xyzq) % 16 != 0)
+        return fail(ctx, RBE_EINVAL, "xyzq must be 16-byte aligned (one float4 per particle)");
+    if ((st = check_dev(ctx, forces_out, "forces_out", N > 0)) != RBE_OK) return st;
+    if ((st = check_dev(ctx, virial_out, "virial_out", false)) != RBE_OK) return st;
+    if ((st = check_dev(ctx, energy_out, "energy_out", false)) != RBE_OK) return st;
+    st = launch_sample(ctx, step, ctx->P);
+    if (st != RBE_OK) return st;
+    return launch_rbe(ctx, N, xyzq, nullptr, ctx->P, forces_out, virial_out, energy_out, true);
+}
+
 // The copy stream and events of the pipelined host-buffer call (created on first use).
 static rbe_status ensure_copy_stream(rbe_ctx ctx)
 {

@@ -75,7 +75,7 @@ k_brho(const BItem* __restrict__ items, const int4* __restrict__ tiles, int ntil
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 tl = tiles[t];
         const BItem it = items[tl.x];
-        rho_f32_tile<RBE_RHO_COMP32>(tl.y, tl.z, it.pos, it.q, it.N, ks + tl.x, m + (size_t)tl.x * P, P, it.chunk_len,
+        rho_f32_tile<RBE_RHO_COMP32, 1>(tl.y, tl.z, it.pos, it.q, it.N, ks + tl.x, m + (size_t)tl.x * P, P, it.chunk_len,
                                    it.nchunks, partials + it.part_off, status);
         __syncthreads();
     }
@@ -106,7 +106,7 @@ k_bforce(const BItem* __restrict__ items, const int2* __restrict__ tiles, int nf
             const int2 tl = tiles[t];
             const BItem it = items[tl.x];
             const size_t o = (size_t)tl.x * P;
-            force_f32_block((int64_t)tl.y, it.pos, it.q, it.N, it.per_block, ks + tl.x, coef_m + o, coef_f + o, P,
+            force_f32_block<false>((int64_t)tl.y, it.pos, it.q, it.N, it.per_block, ks + tl.x, coef_m + o, coef_f + o, P,
                             it.F, status);
         } else {
             const int r = t - nforce;

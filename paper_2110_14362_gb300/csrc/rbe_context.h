@@ -35,9 +35,17 @@ struct KState {
     int P;
 };
 
-// Launch plan of the N x K pair kernels (chosen by plan_* in rbe_kspace.cu).
+// Frequency tiling of the rho pass (rho_shape in rbe_kspace.cu).
+struct RhoShape {
+    int kf;             // frequencies per thread (1, 2 or 4)
+    int ktiles;         // frequency tiles
+    int kthreads;       // threads per block: whole warps
+};
+
+// Launch plan of the N x K pair kernels (chosen by make_plan in rbe_kspace.cu).
 struct Plan {
-    int ktiles;         // frequency tiles in the rho pass (one thread per frequency)
+    int kf;             // frequencies per thread in the rho pass
+    int ktiles;         // frequency tiles in the rho pass (kthreads x kf frequencies each)
     int kthreads;       // threads per rho block: whole warps, <= 256
     int nchunks;        // particle chunks in the rho pass
     int64_t chunk_len;  // particles per chunk
@@ -201,8 +209,10 @@ rbe_status flex_init(rbe_ctx ctx, rbe_flex_system* sys, uint64_t batch);
 rbe_status flex_run(rbe_ctx ctx, rbe_flex_system* sys, int32_t nsteps);
 rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int K,
                            bool uniform_weight, double* F, double* W, double* E);
-rbe_status launch_rbe(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int P, double* F, double* W,
-                      double* E);
+// pos: N x 3 double with charges q, or with xyzq one float4 (x, y, z, q) per particle (q unused,
+// FP32-phase path only).
+rbe_status launch_rbe(rbe_ctx ctx, int64_t N, const void* pos, const double* q, int P, double* F, double* W,
+                      double* E, bool xyzq = false);
 rbe_status launch_tables_box(rbe_ctx ctx, const double box[3]);
 // Pieces of the pipelined host-buffer evaluation (copy stream events: 1 + 2 kMaxPieces).
 constexpr int kMaxPieces = 8;

@@ -127,14 +127,39 @@ __device__ __forceinline__ double block_sum(double v, double* scratch32)
 
 // Block (kt, c) handles frequency tile kt and particle chunk c_off + c (c_off: the first chunk
 // of a piece when the staged host call feeds the pass piece by piece).
-template <int ACC>
-__global__ void __launch_bounds__(kMaxRhoThreads, 8)
-k_rho_f32(const double* __restrict__ pos, const double* __restrict__ q, int64_t N, const KState* __restrict__ ks,
+// F frequencies per thread: blocks of at most kMaxRhoThreads threads for F = 1, kRhoThreadsF
+// threads for F = 2 and 4.
+// XYZQ: positions and charges as one float4 (x, y, z, q) per particle in pos (q unused).
+template <int ACC, int F, bool XYZQ>
+__global__ void __launch_bounds__(F == 1 ? kMaxRhoThreads : kRhoThreadsF, F == 1 ? 6 : 8)
+k_rho_f32(const void* __restrict__ pos, const double* __restrict__ q, int64_t N, const KState* __restrict__ ks,
           const int4* __restrict__ m, int K, int64_t chunk_len, int nchunks, float4* __restrict__ partials,
           unsigned* __restrict__ status, int c_off)
 {
-    rho_f32_tile<ACC>((int)blockIdx.x, c_off + (int)blockIdx.y, pos, q, N, ks, m, K, chunk_len, nchunks, partials,
-                      status);
+    rho_f32_tile<ACC, F, XYZQ>((int)blockIdx.x, c_off + (int)blockIdx.y, pos, q, N, ks, m, K, chunk_len, nchunks,
+                               partials, status);
+}
+
+using RhoKernel = void (*)(const void*, const double*, int64_t, const KState*, const int4*, int, int64_t, int,
+                           float4*, unsigned*, int);
+
+template <int ACC, bool XYZQ>
+static RhoKernel rho_kernel_f(int F)
+{
+    return F == 4 ? k_rho_f32<ACC, 4, XYZQ> : (F == 2 ? k_rho_f32<ACC, 2, XYZQ> : k_rho_f32<ACC, 1, XYZQ>);
+}
+
+template <bool XYZQ>
+static RhoKernel rho_kernel_x(int accum, int F)
+{
+    return accum == RBE_RHO_FP64     ? rho_kernel_f<RBE_RHO_FP64, XYZQ>(F)
+           : accum == RBE_RHO_COMP32 ? rho_kernel_f<RBE_RHO_COMP32, XYZQ>(F)
+                                     : rho_kernel_f<RBE_RHO_FP32, XYZQ>(F);
+}
+
+static RhoKernel rho_kernel(int accum, int F, bool xyzq = false)
+{
+    return xyzq ? rho_kernel_x<true>(accum, F) : rho_kernel_x<false>(accum, F);
 }
 
 // rho pass, FP64 path: s = r / l wrapped to [0, 1); t = m.s - rint(m.s); sincospi(2t).
@@ -297,8 +322,9 @@ k_reduce_f32(const float4* __restrict__ partials, int nchunks, int K, const int4
 // block that computes the energy and virial sums (final_sums_f32) meanwhile.
 // Blocks [0, gridDim.x - final) take particle blocks b_off + blockIdx.x; with final = 1 the
 // last block computes the energy and virial sums.
+template <bool XYZQ>
 __global__ void __launch_bounds__(kForceThreads, 5)
-k_force_f32(const double* __restrict__ pos, const double* __restrict__ q, int64_t N, int64_t per_block,
+k_force_f32(const void* __restrict__ pos, const double* __restrict__ q, int64_t N, int64_t per_block,
             const KState* __restrict__ ks, const int4* __restrict__ coef_m, const float4* __restrict__ coef_f,
             int K, double* __restrict__ F, unsigned* __restrict__ status, const double* __restrict__ terms,
             double* __restrict__ W_out, double* __restrict__ E_out, int64_t b_off, int final)
@@ -308,7 +334,7 @@ k_force_f32(const double* __restrict__ pos, const double* __restrict__ q, int64_
         final_sums(terms, K, ks, W_out, E_out, status);
         return;
     }
-    force_f32_block(b_off + (int64_t)blockIdx.x, pos, q, N, per_block, ks, coef_m, coef_f, K, F, status);
+    force_f32_block<XYZQ>(b_off + (int64_t)blockIdx.x, pos, q, N, per_block, ks, coef_m, coef_f, K, F, status);
 }
 
 // Force pass, FP64 path: particle tiles of kT * PPT, frequencies staged kForceKT at a time.
@@ -598,16 +624,16 @@ static int blocks_per_sm(Kern kern, int threads, size_t dyn_smem = 0)
     return std::max(1, n);
 }
 
-// Launch plan.  rho pass: frequency tiles of at most 256 threads, sized in whole warps
-// so that few lanes idle; particle chunks so that the grid is one full wave of resident
-// blocks with equal particle counts.  Force pass: whole rounds of force_unit particles
-// per block, at most one resident wave.
-static Plan make_plan(rbe_ctx ctx, int64_t N, int K, int rho_bps, int force_bps, int force_unit)
+// Launch plan.  rho pass: frequency tiles of kthreads x kf frequencies (kf frequencies per
+// thread), particle chunks so that the grid is one full wave of resident blocks with equal
+// particle counts.  Force pass: whole rounds of force_unit particles per block, at most one
+// resident wave.
+static Plan make_plan(rbe_ctx ctx, int64_t N, int K, const RhoShape& rs, int rho_bps, int force_bps, int force_unit)
 {
     Plan p{};
-    p.ktiles = (K + kMaxRhoThreads - 1) / kMaxRhoThreads;
-    const int per_tile = (K + p.ktiles - 1) / p.ktiles;
-    p.kthreads = std::min(kMaxRhoThreads, 32 * ((per_tile + 31) / 32));
+    p.kf = rs.kf;
+    p.ktiles = rs.ktiles;
+    p.kthreads = rs.kthreads;
     const int64_t want = std::max<int64_t>(1, (int64_t)ctx->num_sms * rho_bps / p.ktiles);
     const int64_t max_chunks = std::max<int64_t>(1, (N + 63) / 64);  // at least 64 particles per chunk
     p.nchunks = (int)std::min<int64_t>(want, max_chunks);
@@ -647,30 +673,70 @@ struct EvalShape {
     bool fp64;
 };
 
+// Frequency tiling of the FP32-phase rho pass: kf frequencies per thread (1, 2 or 4) and
+// kthreads threads per block (whole warps).  The choice minimises a per-pair instruction
+// estimate: the pair's own work (base), one broadcast load per kf pairs, the particle
+// conversion spread over the tile's frequencies, divided by the fraction of lanes that hold a
+// frequency.
+static RhoShape rho_shape(int K, int accum)
+{
+    const double base = accum == RBE_RHO_COMP32 ? 16.0 : (accum == RBE_RHO_FP64 ? 14.0 : 10.0);
+    RhoShape best{1, 1, 32};
+    double best_cost = 1e30;
+    for (int F : {4, 2, 1}) {
+        const int tmax = F == 1 ? kMaxRhoThreads : kRhoThreadsF;
+        const int ktiles = (K + tmax * F - 1) / (tmax * F);
+        const int per = (K + ktiles - 1) / ktiles;             // frequencies per tile
+        const int T = std::min(tmax, 32 * ((per + F * 32 - 1) / (F * 32)));
+        const double eff = (double)K / ((double)ktiles * T * F);
+        const double cost = (base + 1.0 / F + 55.0 / (T * F)) / eff;
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best = RhoShape{F, ktiles, T};
+        }
+    }
+    return best;
+}
+
 static rbe_status evaluate_shape(rbe_ctx ctx, int64_t N, int K, EvalShape* out)
 {
     DeviceBuffers& d = ctx->d;
     const bool fp64 = ctx->precision == RBE_FP64;
-    static int rho32_threads = 0, rho64_threads = 0, bps_f64 = 0;
-    if (!rho32_threads) {
-        rho32_threads = blocks_per_sm(k_rho_f32<RBE_RHO_FP32>, kMaxRhoThreads) * kMaxRhoThreads;
+    static int rho64_threads = 0, bps_f64 = 0;
+    static int rho32_bps[3][3] = {{0}};  // [accum][F index] resident blocks per SM at the F's block size
+    if (!rho64_threads) {
         rho64_threads = blocks_per_sm(k_rho_f64, kMaxRhoThreads) * kMaxRhoThreads;
         bps_f64 = blocks_per_sm(k_force_f64<2>, kT);
-        cudaFuncSetAttribute(k_force_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(32 * kForceStageK));
+        cudaFuncSetAttribute(k_force_f32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(32 * kForceStageK));
+        cudaFuncSetAttribute(k_force_f32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(32 * kForceStageK));
     }
     const int kstage = std::min(K, kForceStageK);
     const size_t force_smem = fp64 ? 0 : (size_t)32 * kstage;
     static int cached_kstage = -1, cached_bps_force = 1;
     if (!fp64 && kstage != cached_kstage) {
-        cached_bps_force = blocks_per_sm(k_force_f32, kForceThreads, force_smem);
+        cached_bps_force = blocks_per_sm(k_force_f32<false>, kForceThreads, force_smem);
         cached_kstage = kstage;
     }
     const int bps_force = fp64 ? bps_f64 : cached_bps_force;
-    // resident rho blocks per SM at the tile's block size (threads per SM / block size)
-    const int ktiles = (K + kMaxRhoThreads - 1) / kMaxRhoThreads;
-    const int kthreads = std::min(kMaxRhoThreads, 32 * (((K + ktiles - 1) / ktiles + 31) / 32));
-    const int rho_bps = std::max(1, std::min(32, (fp64 ? rho64_threads : rho32_threads) / kthreads));
-    const Plan p = make_plan(ctx, N, K, rho_bps, bps_force, fp64 ? kT * 2 : kForceRound);
+    RhoShape rs;
+    int rho_bps;
+    if (fp64) {
+        rs.kf = 1;
+        rs.ktiles = (K + kMaxRhoThreads - 1) / kMaxRhoThreads;
+        rs.kthreads = std::min(kMaxRhoThreads, 32 * (((K + rs.ktiles - 1) / rs.ktiles + 31) / 32));
+        rho_bps = std::max(1, std::min(32, rho64_threads / rs.kthreads));
+    } else {
+        rs = rho_shape(K, ctx->rho_accum);
+        const int a = ctx->rho_accum < 0 || ctx->rho_accum > 2 ? 1 : ctx->rho_accum;
+        const int fi = rs.kf == 4 ? 2 : (rs.kf == 2 ? 1 : 0);
+        int& bps = rho32_bps[a][fi];
+        if (!bps) {
+            const int tmax = rs.kf == 1 ? kMaxRhoThreads : kRhoThreadsF;
+            bps = std::max(1, blocks_per_sm(rho_kernel(a, rs.kf), tmax) * tmax);  // resident threads per SM
+        }
+        rho_bps = std::max(1, std::min(32, bps / rs.kthreads));
+    }
+    const Plan p = make_plan(ctx, N, K, rs, rho_bps, bps_force, fp64 ? kT * 2 : kForceRound);
     const size_t need = (size_t)(K + 1) * p.nchunks;
     if (need > d.part_cap) {
         ctx_free(ctx, d.partials);
@@ -687,8 +753,8 @@ static rbe_status evaluate_shape(rbe_ctx ctx, int64_t N, int K, EvalShape* out)
 // One evaluation over the frequencies [koff, koff + K) of the sampled batch: rho, reduction and,
 // with forces, the force pass; W and E (either may be NULL) from the same frequencies.  Without
 // forces only the energy and virial are formed (the pressure batch of Eq. (apppress)).
-static rbe_status launch_evaluate_range(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int koff, int K,
-                                        bool forces, double* F, double* W, double* E)
+static rbe_status launch_evaluate_range(rbe_ctx ctx, int64_t N, const void* pos, const double* q, int koff, int K,
+                                        bool forces, double* F, double* W, double* E, bool xyzq)
 {
     DeviceBuffers& d = ctx->d;
     const int4* m_in = d.m + koff;
@@ -705,11 +771,10 @@ static rbe_status launch_evaluate_range(rbe_ctx ctx, int64_t N, const double* po
     float4* part32 = static_cast<float4*>(d.partials);
     const KState* ks = d.ks;
     if (fp64) {
-        k_rho_f64<<<grid, p.kthreads, 0, s>>>(pos, q, N, ks, m_in, K, p.chunk_len, p.nchunks, part64, d.status);
+        k_rho_f64<<<grid, p.kthreads, 0, s>>>(static_cast<const double*>(pos), q, N, ks, m_in, K, p.chunk_len,
+                                              p.nchunks, part64, d.status);
     } else {
-        auto kern = ctx->rho_accum == RBE_RHO_FP64     ? k_rho_f32<RBE_RHO_FP64>
-                    : ctx->rho_accum == RBE_RHO_COMP32 ? k_rho_f32<RBE_RHO_COMP32>
-                                                       : k_rho_f32<RBE_RHO_FP32>;
+        const RhoKernel kern = rho_kernel(ctx->rho_accum, p.kf, xyzq);
         cudaError_t err = launch_pdl(kern, grid, dim3(p.kthreads), 0, s, pos, q, N, ks, m_in, K,
                                      p.chunk_len, p.nchunks, part32, d.status, 0);
         if (err != cudaSuccess) return cuda_fail(ctx, err, "launch k_rho_f32");
@@ -731,12 +796,14 @@ static rbe_status launch_evaluate_range(rbe_ctx ctx, int64_t N, const double* po
     record_event(ctx, 3);
     if (fp64) {
         if (forces && p.fblocks > 0) {
-            k_force_f64<2><<<p.fblocks, kT, 0, s>>>(pos, q, N, p.per_block, ks, d.m, d.coef_d, K, F);
+            k_force_f64<2><<<p.fblocks, kT, 0, s>>>(static_cast<const double*>(pos), q, N, p.per_block, ks, d.m,
+                                                    d.coef_d, K, F);
             st = check_launch(ctx, "k_force");
         }
     } else {
         // one extra block computes the energy and virial sums
-        cudaError_t err = launch_pdl(k_force_f32, dim3((forces ? p.fblocks : 0) + 1), dim3(kForceThreads), force_smem, s, pos, q,
+        cudaError_t err = launch_pdl(xyzq ? k_force_f32<true> : k_force_f32<false>, dim3((forces ? p.fblocks : 0) + 1),
+                                     dim3(kForceThreads), force_smem, s, pos, q,
                                      N, p.per_block, ks, (const int4*)d.coef_m, (const float4*)d.coef_f, K, F,
                                      d.status, (const double*)d.terms, W, E, (int64_t)0, 1);
         st = err == cudaSuccess ? RBE_OK : cuda_fail(ctx, err, "launch k_force_f32");
@@ -750,19 +817,19 @@ static rbe_status launch_evaluate_range(rbe_ctx ctx, int64_t N, const double* po
 rbe_status launch_evaluate(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int K,
                            bool /*uniform_weight*/, double* F, double* W, double* E)
 {
-    return launch_evaluate_range(ctx, N, pos, q, 0, K, true, F, W, E);
+    return launch_evaluate_range(ctx, N, pos, q, 0, K, true, F, W, E, false);
 }
 
 // The RBE evaluation of a sampled step: forces from the force batch (slots [0, P)) and, with a
 // pressure batch (ctx->Ptilde > 0), energy and virial from slots [P, P + Ptilde) with weights
 // S/Ptilde (Eqs. (appforce), (apppress) with p and p~); otherwise all from the one batch.
-rbe_status launch_rbe(rbe_ctx ctx, int64_t N, const double* pos, const double* q, int P, double* F, double* W,
-                      double* E)
+rbe_status launch_rbe(rbe_ctx ctx, int64_t N, const void* pos, const double* q, int P, double* F, double* W,
+                      double* E, bool xyzq)
 {
-    if (ctx->Ptilde <= 0) return launch_evaluate_range(ctx, N, pos, q, 0, P, true, F, W, E);
-    rbe_status st = launch_evaluate_range(ctx, N, pos, q, 0, P, true, F, nullptr, nullptr);
+    if (ctx->Ptilde <= 0) return launch_evaluate_range(ctx, N, pos, q, 0, P, true, F, W, E, xyzq);
+    rbe_status st = launch_evaluate_range(ctx, N, pos, q, 0, P, true, F, nullptr, nullptr, xyzq);
     if (st != RBE_OK) return st;
-    return launch_evaluate_range(ctx, N, pos, q, P, ctx->Ptilde, false, nullptr, W, E);
+    return launch_evaluate_range(ctx, N, pos, q, P, ctx->Ptilde, false, nullptr, W, E, xyzq);
 }
 
 // The host-buffer evaluation on the FP32-phase path, pipelined in quarters: the particles
@@ -807,9 +874,6 @@ rbe_status launch_evaluate_staged(rbe_ctx ctx, int64_t N, const double* h_pos, c
     cudaStream_t s = ctx->stream, cs = ctx->copy_stream;
     const KState* ks = d.ks;
     float4* part32 = static_cast<float4*>(d.partials);
-    auto kern = ctx->rho_accum == RBE_RHO_FP64     ? k_rho_f32<RBE_RHO_FP64>
-                : ctx->rho_accum == RBE_RHO_COMP32 ? k_rho_f32<RBE_RHO_COMP32>
-                                                   : k_rho_f32<RBE_RHO_FP32>;
     cudaError_t err;
     // (the caller has ordered the copy stream after the main stream's earlier work)
     for (int g = 0; g < pieces; ++g) {
@@ -822,7 +886,8 @@ rbe_status launch_evaluate_staged(rbe_ctx ctx, int64_t N, const double* h_pos, c
             (err = cudaStreamWaitEvent(s, ctx->pev[1 + g], 0)) != cudaSuccess)
             return cuda_fail(ctx, err, "staged: input event");
         // group g: rows of stride nchunks, its columns from coff[g]
-        err = launch_pdl(kern, dim3(pl[g].ktiles, pl[g].nchunks), dim3(pl[g].kthreads), 0, s,
+        err = launch_pdl(rho_kernel(ctx->rho_accum, pl[g].kf), dim3(pl[g].ktiles, pl[g].nchunks),
+                         dim3(pl[g].kthreads), 0, s,
                          (const double*)(d_pos + 3 * a), (const double*)(d_q + a), n, ks, (const int4*)d.m, K,
                          pl[g].chunk_len, nchunks, part32 + coff[g], d.status, 0);
         if (err != cudaSuccess) return cuda_fail(ctx, err, "staged: k_rho_f32");
@@ -834,7 +899,7 @@ rbe_status launch_evaluate_staged(rbe_ctx ctx, int64_t N, const double* h_pos, c
     for (int g = 0; g < pieces; ++g) {
         const int64_t a = i0[g], n = i0[g + 1] - i0[g];
         const int final_block = g == pieces - 1 ? 1 : 0;
-        err = launch_pdl(k_force_f32, dim3(pl[g].fblocks + final_block), dim3(kForceThreads), whole.force_smem, s,
+        err = launch_pdl(k_force_f32<false>, dim3(pl[g].fblocks + final_block), dim3(kForceThreads), whole.force_smem, s,
                          (const double*)(d_pos + 3 * a), (const double*)(d_q + a), n, pl[g].per_block, ks,
                          (const int4*)d.coef_m, (const float4*)d.coef_f, K, d_F + 3 * a, d.status,
                          (const double*)d.terms, W, E, (int64_t)0, final_block);

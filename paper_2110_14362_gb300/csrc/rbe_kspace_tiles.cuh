@@ -12,7 +12,8 @@
 namespace rbe {
 
 constexpr int kTableThreads = 1024;   // k_tables block
-constexpr int kMaxRhoThreads = 256;
+constexpr int kMaxRhoThreads = 256;   // threads of a rho block with one frequency per thread
+constexpr int kRhoThreadsF = 128;     // threads of a rho block with 2 or 4 frequencies per thread
 constexpr int kReduceThreads = 256;
 constexpr int kForceWarps = 8;
 constexpr int kForceThreads = 32 * kForceWarps;
@@ -258,99 +259,158 @@ __device__ __forceinline__ uint4 load_fixed(const double* __restrict__ pos, cons
                       __float_as_uint(double_to_float_int(bq)));
 }
 
+// The same record from a float4 (x, y, z, q) input: each coordinate is widened to the double
+// it equals (exact) and converted as above, so a float position gives the fixed point of that
+// double; q is taken as it is.
+__device__ __forceinline__ uint4 load_fixed_f4(const float4* __restrict__ xyzq, int64_t i, FixScale scx,
+                                               FixScale scy, FixScale scz, unsigned* __restrict__ status)
+{
+    const float4 v = xyzq[i];
+    const uint32_t bx = __float_as_uint(v.x), by = __float_as_uint(v.y), bz = __float_as_uint(v.z);
+    const uint32_t bq = __float_as_uint(v.w);
+    if (((bx >> 23) & 0xffu) == 0xffu || ((by >> 23) & 0xffu) == 0xffu || ((bz >> 23) & 0xffu) == 0xffu ||
+        ((bq >> 23) & 0xffu) == 0xffu)
+        atomicOr(status, kStatusNonFinite);  // infinity or NaN
+    return make_uint4(fixed_frac_int(float_to_double_bits(bx), scx), fixed_frac_int(float_to_double_bits(by), scy),
+                      fixed_frac_int(float_to_double_bits(bz), scz), bq);
+}
+
+// A particle's record from either input form: XYZQ selects the float4 (x, y, z, q) array in
+// pos (q unused), else pos is N x 3 double and q N double.
+template <bool XYZQ>
+__device__ __forceinline__ uint4 load_record(const void* __restrict__ pos, const double* __restrict__ q, int64_t i,
+                                             FixScale scx, FixScale scy, FixScale scz, unsigned* __restrict__ status)
+{
+    if (XYZQ) return load_fixed_f4(static_cast<const float4*>(pos), i, scx, scy, scz, status);
+    return load_fixed(static_cast<const double*>(pos), q, i, scx, scy, scz, status);
+}
+
 // =================================================================================
-// rho pass, FP32-phase path.  Block (kt, c) has blockDim.x (a multiple of 32, <= 256)
-// threads; thread j owns frequency kt * blockDim.x + j and runs over the particles
-// [c * chunk_len, (c + 1) * chunk_len), staged in shared memory blockDim.x at a time as
-// 32-bit fixed-point (s_x, s_y, s_z) plus q as float and read as broadcasts.  No FP64
-// instruction runs per particle or per pair: sums across staged tiles are float-float.
-// ACC: RBE_RHO_FP32 (plain FP32 within a staged tile), RBE_RHO_COMP32 (Kahan-compensated
-//      FP32 within a tile), RBE_RHO_FP64 (FP64 per pair; slow on GB300, for reference).
+// rho pass, FP32-phase path.  Block (kt, c) has blockDim.x threads (whole warps) and covers
+// the frequency tile of blockDim.x * F frequencies: thread j owns frequencies
+// kt * blockDim.x * F + f * blockDim.x + j (f < F), and runs over the particles
+// [c * chunk_len, (c + 1) * chunk_len), staged in shared memory kRhoStage at a time as 32-bit
+// fixed-point (s_x, s_y, s_z) plus q as float and read as broadcasts: one shared-memory load
+// feeds F pairs.  No FP64 instruction runs per particle or per pair: sums across staged tiles
+// are float-float.
+// ACC: RBE_RHO_COMP32 (Kahan-compensated FP32 sum of every term within a staged tile),
+//      RBE_RHO_FP32 (plain FP32 within a tile), RBE_RHO_FP64 (FP64 per pair; slow on GB300).
 // Partials: float4 (Re hi, Re lo, Im hi, Im lo) at [l * nchunks + c]; row K holds the
 // chunk's sum of q^2 (hi, lo).  The box constants are read from ks before pdl_wait: the
 // kernel that wrote them (k_tables) runs before the sampler, which is this launch's
 // predecessor, and the sampler starts only after k_tables has completed.
-template <int ACC>
-__device__ __forceinline__ void rho_f32_tile(int kt, int c, const double* __restrict__ pos,
+constexpr int kRhoStage = 256;  // particles staged per tile
+
+template <int ACC, int F, bool XYZQ = false>
+__device__ __forceinline__ void rho_f32_tile(int kt, int c, const void* __restrict__ pos,
                                              const double* __restrict__ q, int64_t N, const KState* __restrict__ ks,
           const int4* __restrict__ m, int K, int64_t chunk_len, int nchunks, float4* __restrict__ partials,
           unsigned* __restrict__ status)
 {
-    __shared__ uint4 sp[kMaxRhoThreads];
+    __shared__ uint4 sp[kRhoStage];
     __shared__ float red[2][32];
     __shared__ unsigned bad;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int l = kt * nt + tid;
+    const int lbase = kt * nt * F + tid;
     const FixScale scx = fs(ks->sc[0]), scy = fs(ks->sc[1]), scz = fs(ks->sc[2]);
-    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f, q2h = 0.f, q2l = 0.f;
-    double are = 0.0, aim = 0.0;
+    float rh[F], rl[F], ih[F], il[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) rh[f] = rl[f] = ih[f] = il[f] = 0.f;
+    float q2h = 0.f, q2l = 0.f;
     const int64_t start = (int64_t)c * chunk_len;
     const int64_t end = min(N, start + chunk_len);
     if (tid == 0) bad = 0u;
     __syncthreads();
     // the first tile is staged before waiting for the sampler (inputs only)
-    uint4 rec0 = make_uint4(0u, 0u, 0u, 0u);
-    if (start + tid < end) {
-        rec0 = load_fixed(pos, q, start + tid, scx, scy, scz, &bad);
-        const float qf = __uint_as_float(rec0.w);
-        ff_add(q2h, q2l, qf * qf);
+    for (int j = tid; j < kRhoStage; j += nt) {
+        const int64_t i = start + j;
+        uint4 rec = make_uint4(0u, 0u, 0u, 0u);
+        if (i < end) {
+            rec = load_record<XYZQ>(pos, q, i, scx, scy, scz, &bad);
+            const float qf = __uint_as_float(rec.w);
+            ff_add(q2h, q2l, qf * qf);
+        }
+        sp[j] = rec;
     }
     pdl_wait();
     pdl_trigger();
-    const int4 mv = l < K ? m[l] : make_int4(0, 0, 0, 0);
-    for (int64_t base = start; base < end; base += nt) {
-        const int64_t i = base + tid;
-        uint4 rec = rec0;
+    int4 mv[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        const int l = lbase + f * nt;
+        mv[f] = l < K ? m[l] : make_int4(0, 0, 0, 0);
+    }
+    for (int64_t base = start; base < end; base += kRhoStage) {
         if (base != start) {
-            rec = make_uint4(0u, 0u, 0u, 0u);
-            if (i < end) {
-                rec = load_fixed(pos, q, i, scx, scy, scz, status);
-                const float qf = __uint_as_float(rec.w);
-                ff_add(q2h, q2l, qf * qf);
+            __syncthreads();  // every thread is done with the previous tile
+            for (int j = tid; j < kRhoStage; j += nt) {
+                const int64_t i = base + j;
+                uint4 rec = make_uint4(0u, 0u, 0u, 0u);
+                if (i < end) {
+                    rec = load_record<XYZQ>(pos, q, i, scx, scy, scz, status);
+                    const float qf = __uint_as_float(rec.w);
+                    ff_add(q2h, q2l, qf * qf);
+                }
+                sp[j] = rec;
             }
         }
-        sp[tid] = rec;
         __syncthreads();
-        const int n_here = (int)min((int64_t)nt, end - base);
-        float re = 0.f, im = 0.f, cre = 0.f, cim = 0.f;
-#pragma unroll 4
+        const int n_here = (int)min((int64_t)kRhoStage, end - base);
+        float re[F], im[F], cre[F], cim[F];
+        double are[F], aim[F];
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            re[f] = im[f] = cre[f] = cim[f] = 0.f;
+            are[f] = aim[f] = 0.0;
+        }
+#pragma unroll 2
         for (int p = 0; p < n_here; ++p) {
             const uint4 r = sp[p];
             const float qp = __uint_as_float(r.w);
-            const float th = fixed_phase(mv.x, mv.y, mv.z, r.x, r.y, r.z);
-            float sn, cs;
-            __sincosf(th, &sn, &cs);
-            if (ACC == RBE_RHO_FP32) {
-                re = fmaf(qp, cs, re);
-                im = fmaf(qp, sn, im);
-            } else if (ACC == RBE_RHO_COMP32) {
-                const float yr = qp * cs - cre;
-                const float tr = re + yr;
-                cre = (tr - re) - yr;
-                re = tr;
-                const float yi = qp * sn - cim;
-                const float ti = im + yi;
-                cim = (ti - im) - yi;
-                im = ti;
-            } else {
-                are = fma((double)qp, (double)cs, are);
-                aim = fma((double)qp, (double)sn, aim);
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                const float th = fixed_phase(mv[f].x, mv[f].y, mv[f].z, r.x, r.y, r.z);
+                float sn, cs;
+                __sincosf(th, &sn, &cs);
+                if (ACC == RBE_RHO_FP32) {
+                    re[f] = fmaf(qp, cs, re[f]);
+                    im[f] = fmaf(qp, sn, im[f]);
+                } else if (ACC == RBE_RHO_COMP32) {
+                    // Kahan: the rounding error of each addition is carried into the next term
+                    const float yr = fmaf(qp, cs, -cre[f]);
+                    const float tr = re[f] + yr;
+                    cre[f] = (tr - re[f]) - yr;
+                    re[f] = tr;
+                    const float yi = fmaf(qp, sn, -cim[f]);
+                    const float ti = im[f] + yi;
+                    cim[f] = (ti - im[f]) - yi;
+                    im[f] = ti;
+                } else {
+                    are[f] = fma((double)qp, (double)cs, are[f]);
+                    aim[f] = fma((double)qp, (double)sn, aim[f]);
+                }
             }
         }
-        if (ACC != RBE_RHO_FP64) {
-            ff_add(rh, rl, re);
-            rl -= cre;
-            ff_add(ih, il, im);
-            il -= cim;
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            if (ACC == RBE_RHO_FP64) {
+                const float ah = (float)are[f], bh = (float)aim[f];
+                ff_add2(rh[f], rl[f], ah, (float)(are[f] - (double)ah));
+                ff_add2(ih[f], il[f], bh, (float)(aim[f] - (double)bh));
+            } else {
+                ff_add(rh[f], rl[f], re[f]);
+                rl[f] -= cre[f];
+                ff_add(ih[f], il[f], im[f]);
+                il[f] -= cim[f];
+            }
         }
-        __syncthreads();
-    }
-    if (ACC == RBE_RHO_FP64) {
-        rh = (float)are; rl = (float)(are - (double)rh);
-        ih = (float)aim; il = (float)(aim - (double)ih);
     }
     if (tid == 0 && bad) atomicOr(status, kStatusNonFinite);  // flagged while staging the first tile
-    if (l < K) partials[(size_t)l * nchunks + c] = make_float4(rh, rl, ih, il);
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        const int l = lbase + f * nt;
+        if (l < K) partials[(size_t)l * nchunks + c] = make_float4(rh[f], rl[f], ih[f], il[f]);
+    }
     if (kt == 0) {
         block_sum_ff(q2h, q2l, red);  // sum of q^2 over the chunk, for E_self
         if (tid == 0) partials[(size_t)K * nchunks + c] = make_float4(q2h, q2l, 0.f, 0.f);
@@ -505,7 +565,8 @@ __device__ __forceinline__ void final_sums(const double* __restrict__ terms, int
 //   F_i,theta = q_i (2 pi / l_theta) sum_l R_l m_l,theta sin(theta_il - arg rho_l)
 // (one sine per pair) is formed in FP32 and widened to double exactly.  The launch carries one extra block
 // that computes the energy and virial sums (final_sums_f32) meanwhile.
-__device__ __forceinline__ void force_f32_block(int64_t blk, const double* __restrict__ pos,
+template <bool XYZQ = false>
+__device__ __forceinline__ void force_f32_block(int64_t blk, const void* __restrict__ pos,
                                                 const double* __restrict__ q, int64_t N, int64_t per_block,
                                                 const KState* __restrict__ ks, const int4* __restrict__ coef_m,
                                                 const float4* __restrict__ coef_f, int K, double* __restrict__ F,
@@ -529,14 +590,16 @@ __device__ __forceinline__ void force_f32_block(int64_t blk, const double* __res
     // the first particle tile is converted before waiting for the reduction (inputs only)
     if (tid == 0) bad = 0u;
     __syncthreads();
-    const uint4 first = b0 + tid < b1 ? load_fixed(pos, q, b0 + tid, scx, scy, scz, &bad) : make_uint4(0u, 0u, 0u, 0u);
+    const uint4 first =
+        b0 + tid < b1 ? load_record<XYZQ>(pos, q, b0 + tid, scx, scy, scz, &bad) : make_uint4(0u, 0u, 0u, 0u);
     pdl_wait();
     for (int64_t sbase = b0; sbase < b1; sbase += kForceThreads) {
         // convert up to kForceThreads particles into shared memory
         const int64_t i = sbase + tid;
         __syncthreads();
         sp[tid] = sbase == b0 ? first
-                              : (i < b1 ? load_fixed(pos, q, i, scx, scy, scz, status) : make_uint4(0u, 0u, 0u, 0u));
+                              : (i < b1 ? load_record<XYZQ>(pos, q, i, scx, scy, scz, status)
+                                        : make_uint4(0u, 0u, 0u, 0u));
         if (sbase == b0 && tid == 0 && bad) atomicOr(status, kStatusNonFinite);
         const int nstaged = (int)min((int64_t)kForceThreads, b1 - sbase);
         for (int r0 = 0; r0 < nstaged; r0 += kForceRound) {

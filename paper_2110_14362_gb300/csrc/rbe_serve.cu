@@ -161,7 +161,7 @@ static rbe_status admit(rbe_server_s* s, Slot& sl, int64_t id)
     if (!sl.ctx) {
         st = rbe_create(rq.r.box, s->cfg.alpha, s->cfg.P, rq.r.seed, &sl.ctx);
         if (st != RBE_OK) return sfail(s, st, std::string("slot context: ") + rbe_last_error(nullptr));
-        rbe_set_precision(sl.ctx, s->cfg.precision, RBE_RHO_FP32);
+        rbe_set_precision(sl.ctx, s->cfg.precision, RBE_RHO_COMP32);
         if ((st = rbe_set_stream(sl.ctx, sl.stream)) != RBE_OK) return st;
     }
     rbe_set_seed(sl.ctx, rq.r.seed);

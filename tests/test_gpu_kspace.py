@@ -3,6 +3,8 @@
 Tolerances: sampled m and S bit-exact; FP64 path max|dF|/RMS(F), |dW|_F/|W|_F and
 |dE|/|E| <= 1e-10; FP32-phase path RMS(dF)/RMS(F) <= 1e-5 with the same bound on the
 virial and the energy."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -17,7 +19,7 @@ pytestmark = pytest.mark.gpu
 SEED = 12345
 
 
-def _run(sys_, P, step, precision, accum=rbe.RBE_RHO_FP32, seed=SEED, box=None):
+def _run(sys_, P, step, precision, accum=rbe.RBE_RHO_COMP32, seed=SEED, box=None):
     import torch
     box = sys_.box if box is None else box
     dev = cuda_device()
@@ -164,16 +166,29 @@ def test_fp32_phase_parity_mid(N, P):
     assert abs(E[0] - Ek0) <= 1e-5 * abs(Ek0)
 
 
-def test_full_size_slab_both_paths():
-    """The slab workload at full size (300k charges, P = 200) in the launch configuration the
-    benchmark times: every output against the oracle."""
+@functools.lru_cache(maxsize=1)
+def _slab_oracle():
     s = inputs.slab()
-    F0, W0, Ek0, Es0, m0, S0 = oracle.rbe_snapshot(s.pos, s.q, s.box, s.alpha, s.P, SEED, 0)
+    return s, oracle.rbe_snapshot(s.pos, s.q, s.box, s.alpha, s.P, SEED, 0)
+
+
+def test_full_size_slab_fp64():
+    """The slab workload at full size (300k charges, P = 200): every output of the FP64 path
+    against the oracle."""
+    s, (F0, W0, Ek0, Es0, m0, S0) = _slab_oracle()
     F, W, E, _ = _run(s, s.P, 0, rbe.RBE_FP64)
     assert rel_max_force(F, F0) <= 1e-10
     assert rel_frob(W, W0) <= 1e-10
     assert abs(E[0] - Ek0) <= 1e-10 * abs(Ek0)
-    F, W, E, _ = _run(s, s.P, 0, rbe.RBE_FP32_PHASE)
+
+
+@pytest.mark.parametrize("accum", [rbe.RBE_RHO_COMP32, rbe.RBE_RHO_FP32, rbe.RBE_RHO_FP64])
+def test_full_size_slab_fp32_phase(accum):
+    """The slab workload at full size on the FP32-phase path with each rho accumulation, in
+    the launch configuration the benchmark times: forces, Pxx, Pyy, Pzz and E_k against the
+    oracle."""
+    s, (F0, W0, Ek0, Es0, m0, S0) = _slab_oracle()
+    F, W, E, _ = _run(s, s.P, 0, rbe.RBE_FP32_PHASE, accum)
     assert rel_rms_force(F, F0) <= 1e-5
     for a in range(3):  # Pxx, Pyy, Pzz separately
         assert abs(W[a, a] - W0[a, a]) <= 1e-5 * np.abs(np.diag(W0)).max()
@@ -305,3 +320,60 @@ def test_water_charges_parity():
     assert rel_rms_force(F, F0) <= 1e-5
     assert rel_frob(W, W0) <= 1e-5
     assert abs(E[0] - Ek0) <= 1e-5 * abs(Ek0)
+
+
+def _xyzq(pos, q):
+    import torch
+    return to_dev(np.concatenate([pos, q[:, None]], axis=1).astype(np.float32))
+
+
+@pytest.mark.parametrize("N,P", [(20000, 200), (5003, 517), (1, 64)])
+def test_xyzq_input(N, P):
+    """float4 (x, y, z, q) input: bit for bit the evaluation of the float-rounded positions given
+    as doubles, and within 1e-5 of the oracle fed the same float-rounded positions (the compute
+    error); the rounding of the input itself is a separate, larger error."""
+    import torch
+    s = inputs.uniform_density(N, P=P)
+    pos32, q32 = s.pos.astype(np.float32), s.q.astype(np.float32)
+    pos_r, q_r = pos32.astype(np.float64), q32.astype(np.float64)
+    dev = cuda_device()
+    F = torch.full((N, 3), float("nan"), dtype=torch.float64, device=dev)
+    W = torch.full((9,), float("nan"), dtype=torch.float64, device=dev)
+    E = torch.full((2,), float("nan"), dtype=torch.float64, device=dev)
+    with rbe.Context(s.box, s.alpha, P, SEED, rbe.RBE_FP32_PHASE) as ctx:
+        ctx.set_stream(torch.cuda.current_stream().cuda_stream)
+        ctx.forces_virial_xyzq(_xyzq(s.pos, s.q), 4, F, W, E)
+        ctx.sync()
+    Fx, Wx, Ex = F.cpu().numpy(), W.cpu().numpy().reshape(3, 3), E.cpu().numpy()
+    sr = inputs.System(pos_r, q_r, s.box, s.alpha, P, s.rc, "rounded")
+    Fd, Wd, Ed, _ = _run(sr, P, 4, rbe.RBE_FP32_PHASE)
+    assert np.array_equal(Fx, Fd) and np.array_equal(Wx, Wd) and np.array_equal(Ex, Ed)
+    if N > 1:
+        m, S = oracle.sample_k(s.box, s.alpha, P, SEED, 4)
+        F0, W0, Ek0, _, _ = oracle.rbe_kspace(pos_r, q_r, s.box, s.alpha, m, S / P)
+        assert rel_rms_force(Fx, F0) <= 1e-5
+        assert rel_frob(Wx, W0) <= 1e-5
+        assert abs(Ex[0] - Ek0) <= 1e-5 * abs(Ek0)
+
+
+def test_xyzq_rejections():
+    import torch
+    dev = cuda_device()
+    s = inputs.small_snapshot()
+    F = torch.empty((s.N, 3), dtype=torch.float64, device=dev)
+    buf = torch.zeros(4 * s.N + 4, dtype=torch.float32, device=dev)
+    lib = rbe._binding.load()
+    with rbe.Context(s.box, s.alpha, s.P, 1, rbe.RBE_FP64) as ctx:
+        with pytest.raises(rbe.RBEError) as e:  # the FP64 path takes no float input
+            ctx.forces_virial_xyzq(_xyzq(s.pos, s.q), 0, F)
+        assert e.value.status == rbe.RBE_EINVAL
+        ctx.set_precision(rbe.RBE_FP32_PHASE)
+        st = lib.rbe_kspace_forces_virial_xyzq(ctx.h, s.N, rbe._binding.ctypes.c_void_p(buf.data_ptr() + 8), 0,
+                                               rbe._binding._ptr(F), None, None)
+        assert st == rbe.RBE_EINVAL  # 8 but not 16-byte aligned
+        bad = np.concatenate([s.pos, s.q[:, None]], axis=1).astype(np.float32)
+        bad[5, 2] = np.inf
+        with pytest.raises(rbe.RBEError) as e:
+            ctx.forces_virial_xyzq(to_dev(bad), 0, F)
+            ctx.sync()
+        assert e.value.status == rbe.RBE_ENONFINITE

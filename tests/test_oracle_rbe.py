@@ -125,3 +125,26 @@ def test_all_cores_build_returns_the_same_bits():
     b = oracle.rbe_kspace(s.pos, s.q, s.box, s.alpha, m, S / 37, all_cores=True)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("all_cores", [False, True])
+def test_subset_forces_are_the_full_estimators_rows(all_cores):
+    """The subset variant (rho over all particles, forces of listed particles only; the check of
+    the largest workloads) returns, for any list of indices (repeats and any order allowed),
+    the very rows of the full estimator, and the same rho, virial and energies bit for bit."""
+    import subprocess
+    if all_cores:
+        try:
+            oracle.build_omp()
+        except (subprocess.CalledProcessError, OSError) as e:
+            pytest.skip(f"no OpenMP runtime for gcc here: {e}")
+    s = inputs.uniform_density(3000, P=64)
+    m, S = oracle.sample_k(s.box, s.alpha, 64, 12345, 9)
+    F, W, Ek, Es, rho = oracle.rbe_kspace(s.pos, s.q, s.box, s.alpha, m, S / 64)
+    idx = np.random.default_rng(4).integers(0, 3000, 257)
+    idx[:3] = [2999, 0, 2999]
+    Fs, Ws, Eks, Ess, rhos = oracle.rbe_kspace_subset(s.pos, s.q, s.box, s.alpha, m, S / 64, idx, all_cores)
+    assert np.array_equal(Fs, F[idx])
+    assert np.array_equal(Ws, W) and Eks == Ek and Ess == Es and np.array_equal(rhos, rho)
+    with pytest.raises(RuntimeError):
+        oracle.rbe_kspace_subset(s.pos, s.q, s.box, s.alpha, m, S / 64, [3000])
