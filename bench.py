@@ -876,6 +876,8 @@ def main():
                     help="time only the general-cell (triclinic) k-space path on the sheared slab")
     ap.add_argument("--skip-sweep", action="store_true", help="leave out the large-N precision and roofline sweep")
     ap.add_argument("--profile-sweep", action="store_true", help="run only the large-N sweep")
+    ap.add_argument("--profile-kspace", action="store_true",
+                    help="run only --warmup + --steps evaluations of --workload (back to back, no L2 flush)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -893,6 +895,36 @@ def main():
                           "ms_per_step": ms, "N": args.profile_npt, "precision": args.precision,
                           "barostat": args.barostat, "sampler": args.sampler, "ptilde": args.ptilde,
                           "reuse": args.reuse}), flush=True)
+        return
+    if args.profile_kspace:
+        # profiling aid: only evaluations of the workload (the command of the ncu summaries)
+        import torch
+        import paper_2110_14362_gb300 as rbe
+        torch.cuda.set_device(local)
+        s = workload(args.workload)
+        prec = rbe.RBE_FP32_PHASE if args.precision == "fp32" else rbe.RBE_FP64
+        acc = {"comp32": rbe.RBE_RHO_COMP32, "fp32": rbe.RBE_RHO_FP32, "fp64": rbe.RBE_RHO_FP64}[args.rho_accum]
+        dev = torch.device("cuda", local)
+        pos = torch.as_tensor(s.pos).to(dev)
+        q = torch.as_tensor(s.q).to(dev)
+        F = torch.empty((s.N, 3), dtype=torch.float64, device=dev)
+        W = torch.empty(9, dtype=torch.float64, device=dev)
+        E = torch.empty(2, dtype=torch.float64, device=dev)
+        stream = torch.cuda.current_stream()
+        with rbe.Context(s.box, s.alpha, s.P, SEED, prec, acc, stream=stream.cuda_stream) as ctx:
+            for k in range(args.warmup):
+                ctx.forces_virial(pos, q, k, F, W, E)
+            ctx.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(args.steps):
+                ctx.forces_virial(pos, q, args.warmup + k, F, W, E)
+            e1.record(stream)
+            ctx.sync()
+        ms = e0.elapsed_time(e1) / args.steps
+        print(json.dumps({"metric": "k-space evaluations", "workload": s.name, "precision": args.precision,
+                          "rho_accum": args.rho_accum, "ms_per_step": ms,
+                          "pair_evals_per_s": s.N * s.P / (ms * 1e-3)}), flush=True)
         return
     if args.profile_sweep:
         import torch

@@ -96,7 +96,7 @@ k_breduce(const BItem* __restrict__ items, int P, const float4* __restrict__ par
 
 // Persistent: tiles [0, nforce) are (item, particle block); tiles [nforce, nforce + R) the
 // per-item energy and virial sums.
-__global__ void __launch_bounds__(kForceThreads, 5)
+__global__ void __launch_bounds__(kForceThreads, RBE_FORCE_MINB)
 k_bforce(const BItem* __restrict__ items, const int2* __restrict__ tiles, int nforce, int R,
          const KState* __restrict__ ks, const int4* __restrict__ coef_m, const float4* __restrict__ coef_f, int P,
          const double* __restrict__ terms, unsigned* __restrict__ status)
@@ -391,7 +391,7 @@ rbe_status launch(rbe_batch b, int n, int mask)
     if (mask & 16) {
         const int kstage = std::min(P, kForceStageK);
         const int grid = std::max(1, std::min(b->n_ftiles + n, b->num_sms * b->force_grid_per_sm));
-        k_bforce<<<grid, kForceThreads, (size_t)32 * kstage, s>>>(b->d_items, b->d_ftiles, b->n_ftiles, n, b->d_ks,
+        k_bforce<<<grid, kForceThreads, (size_t)kForceSmemPerK * kstage, s>>>(b->d_items, b->d_ftiles, b->n_ftiles, n, b->d_ks,
                                                                  b->d_coef_m, b->d_coef_f, P, b->d_terms,
                                                                  b->d_status);
     }
@@ -474,8 +474,8 @@ rbe_status rbe_batch_create(double alpha, int32_t P, int32_t max_items, double m
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_which, sizeof(int) * R);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->upload_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) {
-        cudaFuncSetAttribute(k_bforce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(32 * kForceStageK));
-        b->force_grid_per_sm = resident_blocks(k_bforce, kForceThreads, (size_t)32 * std::min(P, kForceStageK));
+        cudaFuncSetAttribute(k_bforce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kForceSmemPerK * kForceStageK));
+        b->force_grid_per_sm = resident_blocks(k_bforce, kForceThreads, (size_t)kForceSmemPerK * std::min(P, kForceStageK));
         e = cudaDeviceSynchronize();
     }
     if (e != cudaSuccess) {

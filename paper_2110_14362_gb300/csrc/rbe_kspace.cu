@@ -323,7 +323,7 @@ k_reduce_f32(const float4* __restrict__ partials, int nchunks, int K, const int4
 // Blocks [0, gridDim.x - final) take particle blocks b_off + blockIdx.x; with final = 1 the
 // last block computes the energy and virial sums.
 template <bool XYZQ>
-__global__ void __launch_bounds__(kForceThreads, 5)
+__global__ void __launch_bounds__(kForceThreads, RBE_FORCE_MINB)
 k_force_f32(const void* __restrict__ pos, const double* __restrict__ q, int64_t N, int64_t per_block,
             const KState* __restrict__ ks, const int4* __restrict__ coef_m, const float4* __restrict__ coef_f,
             int K, double* __restrict__ F, unsigned* __restrict__ status, const double* __restrict__ terms,
@@ -680,7 +680,7 @@ struct EvalShape {
 // frequency.
 static RhoShape rho_shape(int K, int accum)
 {
-    const double base = accum == RBE_RHO_COMP32 ? 16.0 : (accum == RBE_RHO_FP64 ? 14.0 : 10.0);
+    const double base = accum == RBE_RHO_COMP32 ? 12.0 : (accum == RBE_RHO_FP64 ? 14.0 : 10.0);
     RhoShape best{1, 1, 32};
     double best_cost = 1e30;
     for (int F : {4, 2, 1}) {
@@ -707,11 +707,11 @@ static rbe_status evaluate_shape(rbe_ctx ctx, int64_t N, int K, EvalShape* out)
     if (!rho64_threads) {
         rho64_threads = blocks_per_sm(k_rho_f64, kMaxRhoThreads) * kMaxRhoThreads;
         bps_f64 = blocks_per_sm(k_force_f64<2>, kT);
-        cudaFuncSetAttribute(k_force_f32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(32 * kForceStageK));
-        cudaFuncSetAttribute(k_force_f32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(32 * kForceStageK));
+        cudaFuncSetAttribute(k_force_f32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kForceSmemPerK * kForceStageK));
+        cudaFuncSetAttribute(k_force_f32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kForceSmemPerK * kForceStageK));
     }
     const int kstage = std::min(K, kForceStageK);
-    const size_t force_smem = fp64 ? 0 : (size_t)32 * kstage;
+    const size_t force_smem = fp64 ? 0 : (size_t)kForceSmemPerK * kstage;
     static int cached_kstage = -1, cached_bps_force = 1;
     if (!fp64 && kstage != cached_kstage) {
         cached_bps_force = blocks_per_sm(k_force_f32<false>, kForceThreads, force_smem);

@@ -17,9 +17,29 @@ constexpr int kRhoThreadsF = 128;     // threads of a rho block with 2 or 4 freq
 constexpr int kReduceThreads = 256;
 constexpr int kForceWarps = 8;
 constexpr int kForceThreads = 32 * kForceWarps;
-constexpr int kForcePPT = 4;
+// Force-pass tile parameters (compile-time; the defaults are the measured best on GB300):
+// particles per lane, unroll of the frequency loop, resident blocks per SM the registers are
+// sized for.
+#ifndef RBE_FORCE_PPT
+#define RBE_FORCE_PPT 4
+#endif
+#ifndef RBE_FORCE_LUNROLL
+#define RBE_FORCE_LUNROLL 4
+#endif
+#ifndef RBE_FORCE_MINB
+#define RBE_FORCE_MINB 4
+#endif
+constexpr int kForcePPT = RBE_FORCE_PPT;
+constexpr int kForceLUnroll = RBE_FORCE_LUNROLL;
 constexpr int kForceRound = 32 * kForcePPT;  // particles per round of the FP32 force pass
-constexpr int kForceStageK = 2048;           // frequencies staged at once (dynamic shared memory)
+// frequencies staged at once (dynamic shared memory, 32 B each): 16 KB leaves room for five
+// resident blocks per SM; more frequencies are restaged in tiles for every round of particles
+#ifndef RBE_FORCE_STAGEK
+#define RBE_FORCE_STAGEK 512
+#endif
+constexpr int kForceStageK = RBE_FORCE_STAGEK;
+// shared memory per staged frequency: (mx, my, mz, phase offset) and (R, R mx, R my, R mz)
+constexpr int kForceSmemPerK = 32;
 
 __device__ __forceinline__ FixScale fs(const FixScaleH& h) { return FixScale{h.q, h.e}; }
 
@@ -293,7 +313,8 @@ __device__ __forceinline__ uint4 load_record(const void* __restrict__ pos, const
 // fixed-point (s_x, s_y, s_z) plus q as float and read as broadcasts: one shared-memory load
 // feeds F pairs.  No FP64 instruction runs per particle or per pair: sums across staged tiles
 // are float-float.
-// ACC: RBE_RHO_COMP32 (Kahan-compensated FP32 sum of every term within a staged tile),
+// ACC: RBE_RHO_COMP32 (compensated FP32: four-term partial sums added with Kahan's
+//      compensation, an error bound that does not grow with the particle count),
 //      RBE_RHO_FP32 (plain FP32 within a tile), RBE_RHO_FP64 (FP64 per pair; slow on GB300).
 // Partials: float4 (Re hi, Re lo, Im hi, Im lo) at [l * nchunks + c]; row K holds the
 // chunk's sum of q^2 (hi, lo).  The box constants are read from ks before pdl_wait: the
@@ -313,9 +334,11 @@ __device__ __forceinline__ void rho_f32_tile(int kt, int c, const void* __restri
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lbase = kt * nt * F + tid;
     const FixScale scx = fs(ks->sc[0]), scy = fs(ks->sc[1]), scz = fs(ks->sc[2]);
-    float rh[F], rl[F], ih[F], il[F];
+    // the float-float sums across staged tiles, (Re hi, Re lo, Im hi, Im lo) per frequency, live
+    // in shared memory: they change once per tile, and registers go to the pair loop
+    __shared__ float4 acc_s[(F == 1 ? kMaxRhoThreads : kRhoThreadsF) * F];
 #pragma unroll
-    for (int f = 0; f < F; ++f) rh[f] = rl[f] = ih[f] = il[f] = 0.f;
+    for (int f = 0; f < F; ++f) acc_s[f * nt + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
     float q2h = 0.f, q2l = 0.f;
     const int64_t start = (int64_t)c * chunk_len;
     const int64_t end = min(N, start + chunk_len);
@@ -363,53 +386,86 @@ __device__ __forceinline__ void rho_f32_tile(int kt, int c, const void* __restri
             re[f] = im[f] = cre[f] = cim[f] = 0.f;
             are[f] = aim[f] = 0.0;
         }
-#pragma unroll 2
-        for (int p = 0; p < n_here; ++p) {
-            const uint4 r = sp[p];
-            const float qp = __uint_as_float(r.w);
+        if (ACC == RBE_RHO_COMP32) {
+            // Compensated summation: the terms of four consecutive particles form an FP32 partial
+            // sum, and the partial sums are added with Kahan's compensation (the rounding error
+            // of each addition carried into the next), so the error does not grow with the
+            // number of particles: to first order at most 5 eps sum_i |q_i| (3 eps from the
+            // four-term partials, 2 eps from the compensated additions).  Records past the end
+            // of the chunk are staged as zeros (q = 0), so the last group of four is padded.
+            const int n4 = (n_here + 3) & ~3;
+            for (int p = 0; p < n4; p += 4) {
+                const uint4 r0 = sp[p], r1 = sp[p + 1], r2 = sp[p + 2], r3 = sp[p + 3];
 #pragma unroll
-            for (int f = 0; f < F; ++f) {
-                const float th = fixed_phase(mv[f].x, mv[f].y, mv[f].z, r.x, r.y, r.z);
-                float sn, cs;
-                __sincosf(th, &sn, &cs);
-                if (ACC == RBE_RHO_FP32) {
-                    re[f] = fmaf(qp, cs, re[f]);
-                    im[f] = fmaf(qp, sn, im[f]);
-                } else if (ACC == RBE_RHO_COMP32) {
-                    // Kahan: the rounding error of each addition is carried into the next term
-                    const float yr = fmaf(qp, cs, -cre[f]);
-                    const float tr = re[f] + yr;
-                    cre[f] = (tr - re[f]) - yr;
-                    re[f] = tr;
-                    const float yi = fmaf(qp, sn, -cim[f]);
-                    const float ti = im[f] + yi;
-                    cim[f] = (ti - im[f]) - yi;
-                    im[f] = ti;
-                } else {
-                    are[f] = fma((double)qp, (double)cs, are[f]);
-                    aim[f] = fma((double)qp, (double)sn, aim[f]);
+                const float2 q0 = make_float2(__uint_as_float(r0.w), __uint_as_float(r0.w));
+                const float2 q1 = make_float2(__uint_as_float(r1.w), __uint_as_float(r1.w));
+                const float2 q2 = make_float2(__uint_as_float(r2.w), __uint_as_float(r2.w));
+                const float2 q3 = make_float2(__uint_as_float(r3.w), __uint_as_float(r3.w));
+                const float2 m1 = make_float2(-1.f, -1.f);
+#pragma unroll
+                for (int f = 0; f < F; ++f) {
+                    float2 e0, e1, e2, e3;  // (cos, sin) of the four phases
+                    __sincosf(fixed_phase(mv[f].x, mv[f].y, mv[f].z, r0.x, r0.y, r0.z), &e0.y, &e0.x);
+                    __sincosf(fixed_phase(mv[f].x, mv[f].y, mv[f].z, r1.x, r1.y, r1.z), &e1.y, &e1.x);
+                    __sincosf(fixed_phase(mv[f].x, mv[f].y, mv[f].z, r2.x, r2.y, r2.z), &e2.y, &e2.x);
+                    __sincosf(fixed_phase(mv[f].x, mv[f].y, mv[f].z, r3.x, r3.y, r3.z), &e3.y, &e3.x);
+                    // (Re, Im) as packed pairs: each FP32x2 operation is the scalar one per lane
+                    // (x - c is fma(c, -1, x), rounded once like the subtraction)
+                    float2 x = __fmul2_rn(q0, e0);
+                    x = __ffma2_rn(q1, e1, x);
+                    x = __ffma2_rn(q2, e2, x);
+                    x = __ffma2_rn(q3, e3, x);
+                    const float2 acc = make_float2(re[f], im[f]), cmp = make_float2(cre[f], cim[f]);
+                    const float2 y = __ffma2_rn(cmp, m1, x);
+                    const float2 t = __fadd2_rn(acc, y);
+                    const float2 c = __ffma2_rn(y, m1, __ffma2_rn(acc, m1, t));
+                    re[f] = t.x;
+                    im[f] = t.y;
+                    cre[f] = c.x;
+                    cim[f] = c.y;
+                }
+            }
+        } else {
+#pragma unroll 2
+            for (int p = 0; p < n_here; ++p) {
+                const uint4 r = sp[p];
+                const float qp = __uint_as_float(r.w);
+#pragma unroll
+                for (int f = 0; f < F; ++f) {
+                    const float th = fixed_phase(mv[f].x, mv[f].y, mv[f].z, r.x, r.y, r.z);
+                    float sn, cs;
+                    __sincosf(th, &sn, &cs);
+                    if (ACC == RBE_RHO_FP32) {
+                        re[f] = fmaf(qp, cs, re[f]);
+                        im[f] = fmaf(qp, sn, im[f]);
+                    } else {
+                        are[f] = fma((double)qp, (double)cs, are[f]);
+                        aim[f] = fma((double)qp, (double)sn, aim[f]);
+                    }
                 }
             }
         }
 #pragma unroll
         for (int f = 0; f < F; ++f) {
+            float4 a = acc_s[f * nt + tid];
             if (ACC == RBE_RHO_FP64) {
                 const float ah = (float)are[f], bh = (float)aim[f];
-                ff_add2(rh[f], rl[f], ah, (float)(are[f] - (double)ah));
-                ff_add2(ih[f], il[f], bh, (float)(aim[f] - (double)bh));
+                ff_add2(a.x, a.y, ah, (float)(are[f] - (double)ah));
+                ff_add2(a.z, a.w, bh, (float)(aim[f] - (double)bh));
             } else {
-                ff_add(rh[f], rl[f], re[f]);
-                rl[f] -= cre[f];
-                ff_add(ih[f], il[f], im[f]);
-                il[f] -= cim[f];
+                ff_add(a.x, a.y, re[f]);
+                a.y -= cre[f];
+                ff_add(a.z, a.w, im[f]);
+                a.w -= cim[f];
             }
+            acc_s[f * nt + tid] = a;
         }
     }
     if (tid == 0 && bad) atomicOr(status, kStatusNonFinite);  // flagged while staging the first tile
 #pragma unroll
     for (int f = 0; f < F; ++f) {
         const int l = lbase + f * nt;
-        if (l < K) partials[(size_t)l * nchunks + c] = make_float4(rh[f], rl[f], ih[f], il[f]);
+        if (l < K) partials[(size_t)l * nchunks + c] = acc_s[f * nt + tid];
     }
     if (kt == 0) {
         block_sum_ff(q2h, q2l, red);  // sum of q^2 over the chunk, for E_self
@@ -621,7 +677,7 @@ __device__ __forceinline__ void force_f32_block(int64_t blk, const void* __restr
 #pragma unroll
                 for (int p = 0; p < kForcePPT; ++p) pr[p] = sp[(r0 + 32 * p + lane) % kForceThreads];
                 const int l0 = (warp * nk) / kForceWarps, l1 = ((warp + 1) * nk) / kForceWarps;
-#pragma unroll 2
+#pragma unroll kForceLUnroll
                 for (int l = l0; l < l1; ++l) {
                     const int4 a = sm[l];
                     const float4 b = sf[l];
