@@ -598,8 +598,25 @@ rbe_status rbe_server_submit(rbe_server s, const rbe_request* req, int64_t* id);
  * finished (or nothing is left).  Outputs (may be NULL): queued, resident, finished counts. */
 rbe_status rbe_server_progress(rbe_server s, int32_t wait, int32_t* n_queued, int32_t* n_active, int64_t* n_done);
 
+/* Cancel a request: a queued one leaves the queue at once; a resident one leaves its slot at
+ * the end of its chunk in flight (observed by a later rbe_server_progress), and its slot serves
+ * the next request.  A cancelled request counts as done; its result is RBE_ESTATE ("request
+ * cancelled").  RBE_ESTATE for a request that has already finished, RBE_EINVAL for an unknown
+ * id.  The other requests are unaffected. */
+rbe_status rbe_server_cancel(rbe_server s, int64_t id);
+
+/* Where a request stands: *state 0 queued, 1 resident, 2 finished, 3 failed, 4 cancelled; *error
+ * the failure's status (RBE_OK unless 3 or 4).  Either pointer may be NULL.  A resident
+ * replica whose device status word latched an error (non-finite values, a box outside the
+ * range rbe_npt_init prepared, a full neighbour list, ...) is evicted at the end of the chunk
+ * that raised it: the server reads every replica's status word after each chunk, and that
+ * replica fails with the error while the others run on. */
+rbe_status rbe_server_request_state(rbe_server s, int64_t id, int32_t* state, rbe_status* error);
+
 /* Final state of a finished request into host memory (any pointer may be NULL): pos, mom
- * N*3 and the cell block (RBE_CELL_DOUBLES).  RBE_ESTATE while it runs. */
+ * N*3 and the cell block (RBE_CELL_DOUBLES).  RBE_ESTATE while it runs or after it was
+ * cancelled; the failure's status (with its message in rbe_server_last_error) for a request
+ * that failed. */
 rbe_status rbe_server_result(rbe_server s, int64_t id, double* pos, double* mom, double* cell);
 
 /* Per-chunk latencies in seconds (launch to observed completion), up to `capacity` of them;

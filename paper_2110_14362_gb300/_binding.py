@@ -170,6 +170,9 @@ SIGNATURES = [
     ("rbe_server_progress", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]),
     ("rbe_server_result", ctypes.c_int, [_vp, ctypes.c_int64, _dp, _dp, _dp]),
+    ("rbe_server_cancel", ctypes.c_int, [_vp, ctypes.c_int64]),
+    ("rbe_server_request_state", ctypes.c_int, [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
+                                                ctypes.POINTER(ctypes.c_int)]),
     ("rbe_server_stats", ctypes.c_int, [_vp, _dp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_int64), _dp]),
     ("rbe_server_last_error", ctypes.c_char_p, [_vp]),
@@ -631,6 +634,15 @@ class Server:
         self._check(load().rbe_server_result(self.h, rid, pos.ctypes.data_as(_dp), mom.ctypes.data_as(_dp),
                                              cell.ctypes.data_as(_dp)))
         return pos, mom, cell
+
+    def cancel(self, rid: int):
+        self._check(load().rbe_server_cancel(self.h, int(rid)))
+
+    def state(self, rid: int):
+        """(state, error): state 0 queued, 1 resident, 2 finished, 3 failed, 4 cancelled."""
+        st, err = ctypes.c_int32(), ctypes.c_int()
+        self._check(load().rbe_server_request_state(self.h, int(rid), ctypes.byref(st), ctypes.byref(err)))
+        return st.value, err.value
 
     def stats(self):
         n, steps, span = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()

@@ -88,9 +88,12 @@ rbe_status check_dev(rbe_ctx ctx, const void* p, const char* name, bool required
 
 constexpr int64_t kMaxN = (int64_t(1) << 31) - 256;
 
-static rbe_status status_from_bits(rbe_ctx ctx, unsigned bits)
+// Non-finite values are reported first: they are the cause when a NaN or infinity has also
+// carried the box out of its prepared range.
+rbe_status status_from_bits(rbe_ctx ctx, unsigned bits)
 {
     if (bits & kStatusSample) return fail(ctx, RBE_ESAMPLE, "a frequency stayed m = 0 after 2^20 redraws");
+    if (bits & kStatusNonFinite) return fail(ctx, RBE_ENONFINITE, "rho(k) or an output is not finite");
     if (bits & kStatusTable) return fail(ctx, RBE_ESTATE, "sampling table capacity exceeded on the device");
     if (bits & kStatusList)
         return fail(ctx, RBE_ESTATE, "neighbour list capacity exceeded (the density rose far above its initial value)");
@@ -100,7 +103,6 @@ static rbe_status status_from_bits(rbe_ctx ctx, unsigned bits)
     if (bits & kStatusShake)
         return fail(ctx, RBE_ESTATE, "SHAKE did not converge within its sweep limit (a molecule was torn apart)");
     if (bits & kStatusTimeout) return fail(ctx, RBE_ETIMEOUT, "a bounded device wait gave up");
-    if (bits & kStatusNonFinite) return fail(ctx, RBE_ENONFINITE, "rho(k) or an output is not finite");
     return RBE_OK;
 }
 

@@ -176,6 +176,9 @@ rbe_status cuda_fail(rbe_ctx ctx, cudaError_t err, const char* what);
 // A device pointer argument: NULL allowed unless required, 8-byte aligned, device memory (rbe_api.cu).
 rbe_status check_dev(rbe_ctx ctx, const void* p, const char* name, bool required);
 
+// The status of latched device bits (the message set on ctx), RBE_OK for none (rbe_api.cu).
+rbe_status status_from_bits(rbe_ctx ctx, unsigned bits);
+
 // Host-side rule shared by create/set_box: the per-axis table size for (alpha, l).
 int host_axis_M(double alpha, double ell);
 

@@ -8,6 +8,13 @@
 // is device-resident, so one graph serves every chunk).  Chunks of different replicas run
 // concurrently on the GPU and new requests are admitted while others run.  Latency of a
 // chunk = host time from its launch to the observation of its completion event.
+//
+// Failures stay with their request: after every chunk the slot's device status word is copied
+// into pinned host memory on the slot's stream, before the completion event, so a replica that
+// latched an error (non-finite values, a box outside its prepared range, a full neighbour
+// list) is evicted at the end of that chunk with the error as its result, and its slot serves
+// the next request; the other replicas run on untouched.  A request can also be cancelled,
+// queued or resident (a resident one leaves at the end of its chunk in flight).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,7 +36,7 @@ struct Request {
     rbe_request r;
     std::vector<double> pos, mom, q, m;  // copies of the caller's host inputs
     std::vector<double> out_pos, out_mom, out_cell;
-    int state = 0;  // 0 queued, 1 resident, 2 done, 3 failed
+    int state = 0;  // 0 queued, 1 resident, 2 done, 3 failed, 4 cancelled
     rbe_status error = RBE_OK;
     std::string error_msg;  // why the request failed
     double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
@@ -51,6 +58,8 @@ struct Slot {
     cudaGraphExec_t graph = nullptr;
     int32_t graph_steps = 0;
     int64_t bytes = 0;
+    unsigned* h_status = nullptr;  // pinned: the context's device status word after the last chunk
+    bool cancel = false;           // leave at the end of the chunk in flight
 };
 
 }  // namespace
@@ -120,6 +129,7 @@ static void release_slot(rbe_server_s* s, Slot& sl)
     sl.busy = false;
     sl.req = -1;
     sl.in_flight = false;
+    sl.cancel = false;
 }
 
 static rbe_status ensure_slot_buffers(rbe_server_s* s, Slot& sl, int64_t N)
@@ -127,7 +137,9 @@ static rbe_status ensure_slot_buffers(rbe_server_s* s, Slot& sl, int64_t N)
     if (!sl.stream) {
         cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&sl.h_status), sizeof(unsigned));
         if (e != cudaSuccess) return sfail(s, RBE_ECUDA, std::string("slot stream: ") + cudaGetErrorString(e));
+        *sl.h_status = 0u;
     }
     if (N > sl.ncap) {
         for (double** p : {&sl.pos, &sl.mom, &sl.force, &sl.charge, &sl.mass}) {
@@ -234,8 +246,11 @@ static rbe_status launch_chunk(rbe_server_s* s, Slot& sl)
         st = rbe_npt_step(sl.ctx, &sl.sys, n);
         if (st != RBE_OK) return sfail(s, st, rbe_last_error(sl.ctx));
     }
-    cudaError_t e = cudaEventRecord(sl.done, sl.stream);
-    if (e != cudaSuccess) return sfail(s, RBE_ECUDA, std::string("cudaEventRecord: ") + cudaGetErrorString(e));
+    // the replica's latched device errors, read by progress() once the chunk is complete
+    cudaError_t e = cudaMemcpyAsync(sl.h_status, sl.ctx->d.status, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                    sl.stream);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
+    if (e != cudaSuccess) return sfail(s, RBE_ECUDA, std::string("chunk status: ") + cudaGetErrorString(e));
     sl.in_flight = true;
     sl.chunk_in_flight = n;
     sl.t_launch = now_s(s);
@@ -265,6 +280,23 @@ static rbe_status retire(rbe_server_s* s, Slot& sl)
     ++s->n_done;
     release_slot(s, sl);
     return RBE_OK;  // a failed request is reported through rbe_server_result, not here
+}
+
+// End a resident request before its last step: `state` 3 (failed with `st`, message from the
+// slot's context) or 4 (cancelled).  Its chunk in flight has completed (or none was launched);
+// the latched status word is cleared on the slot's stream for the slot's next request.
+static void evict(rbe_server_s* s, Slot& sl, int state, rbe_status st, const std::string& msg)
+{
+    Request& rq = *s->reqs[sl.req];
+    rq.state = state;
+    rq.error = st;
+    rq.error_msg = msg;
+    rq.t_done = now_s(s);
+    s->t_last_done = rq.t_done;
+    ++s->n_done;
+    if (sl.ctx) cudaMemsetAsync(sl.ctx->d.status, 0, sizeof(unsigned), sl.stream);
+    *sl.h_status = 0u;
+    release_slot(s, sl);
 }
 
 }  // namespace rbe
@@ -305,6 +337,7 @@ rbe_status rbe_server_destroy(rbe_server s)
         if (sl.stream) cudaStreamSynchronize(sl.stream);
         if (sl.done) cudaEventDestroy(sl.done);
         if (sl.stream) cudaStreamDestroy(sl.stream);
+        if (sl.h_status) cudaFreeHost(sl.h_status);
     }
     if (cur >= 0 && cur != s->device) cudaSetDevice(cur);
     delete s;
@@ -363,7 +396,16 @@ rbe_status rbe_server_progress(rbe_server s, int32_t wait, int32_t* n_queued, in
             sl.steps_left -= sl.chunk_in_flight;
             s->steps_done += sl.chunk_in_flight;
             any_done = true;
-            if (sl.steps_left <= 0) retire(s, sl);
+            const unsigned bits = *sl.h_status;
+            if (bits) {
+                const rbe_status st = status_from_bits(sl.ctx, bits);
+                evict(s, sl, 3, st, std::string("evicted after step ") + std::to_string(sl.sys.step) + ": " +
+                                        rbe_last_error(sl.ctx));
+            } else if (sl.cancel) {
+                evict(s, sl, 4, RBE_ESTATE, "request cancelled");
+            } else if (sl.steps_left <= 0) {
+                retire(s, sl);
+            }
         }
         // 2. admit while a slot is free and the budget allows (first come, first served)
         while (!s->queue.empty()) {
@@ -405,10 +447,53 @@ rbe_status rbe_server_progress(rbe_server s, int32_t wait, int32_t* n_queued, in
     return RBE_OK;
 }
 
+rbe_status rbe_server_cancel(rbe_server s, int64_t id)
+{
+    if (!s || id < 0 || id >= (int64_t)s->reqs.size()) return RBE_EINVAL;
+    Request& rq = *s->reqs[id];
+    if (rq.state == 0) {
+        for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
+            if (*it == id) {
+                s->queue.erase(it);
+                break;
+            }
+        rq.state = 4;
+        rq.error = RBE_ESTATE;
+        rq.error_msg = "request cancelled";
+        ++s->n_done;
+        return RBE_OK;
+    }
+    if (rq.state != 1) return sfail(s, RBE_ESTATE, "request already finished");
+    for (Slot& sl : s->slots)
+        if (sl.busy && sl.req == id) {
+            if (sl.in_flight) {
+                sl.cancel = true;  // progress() ends it when its chunk completes
+            } else {
+                int cur = -1;
+                cudaGetDevice(&cur);
+                if (cur != s->device) cudaSetDevice(s->device);
+                evict(s, sl, 4, RBE_ESTATE, "request cancelled");
+                if (cur >= 0 && cur != s->device) cudaSetDevice(cur);
+            }
+            return RBE_OK;
+        }
+    return sfail(s, RBE_ESTATE, "request not resident");
+}
+
+rbe_status rbe_server_request_state(rbe_server s, int64_t id, int32_t* state, rbe_status* error)
+{
+    if (!s || id < 0 || id >= (int64_t)s->reqs.size()) return RBE_EINVAL;
+    const Request& rq = *s->reqs[id];
+    if (state) *state = rq.state;
+    if (error) *error = rq.state >= 3 ? rq.error : RBE_OK;
+    return RBE_OK;
+}
+
 rbe_status rbe_server_result(rbe_server s, int64_t id, double* pos, double* mom, double* cell)
 {
     if (!s || id < 0 || id >= (int64_t)s->reqs.size()) return RBE_EINVAL;
     const Request& rq = *s->reqs[id];
+    if (rq.state == 4) return sfail(s, RBE_ESTATE, "request cancelled");
     if (rq.state == 3) return sfail(s, rq.error, "request failed: " + rq.error_msg);
     if (rq.state != 2) return sfail(s, RBE_ESTATE, "request not finished");
     const int64_t N = rq.r.N;

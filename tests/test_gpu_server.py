@@ -213,3 +213,78 @@ def test_server_rejects_bad_sampling_settings():
             assert e.value.status == rbe.RBE_EINVAL
     finally:
         srv.close()
+
+
+def _run_until_done(srv, n, t_end):
+    while True:
+        nq, na, nd = srv.progress(wait=True)
+        if nd == n:
+            return
+        assert time.monotonic() < t_end, "serving loop did not finish"
+
+
+@pytest.mark.parametrize("precision", [rbe.RBE_FP64, rbe.RBE_FP32_PHASE])
+def test_nonfinite_request_is_evicted_and_the_others_run_on(precision):
+    """A request whose host positions hold a NaN latches RBE_ENONFINITE on its replica's device
+    status word; the server reads it after the first chunk, evicts that replica with the error
+    as its result, and the three good requests resident beside it end bit for bit as when each
+    runs alone (its direct steps)."""
+    cuda_device()
+    srv = rbe.Server(ALPHA, P, precision, max_slots=4, chunk_steps=4, mem_budget=8 << 30)
+    try:
+        ids = {}
+        for i, (n_side, sseed, pseed, nsteps) in enumerate(REQS):
+            pos, mom, q, m, box = _system(n_side, sseed)
+            if i == 2:
+                pos = pos.copy()
+                pos[5, 1] = np.nan
+            ids[i] = srv.submit(pos, mom, q, m, box, _dev_params(box), pseed, nsteps)
+        _run_until_done(srv, len(ids), time.monotonic() + DEADLINE_S)
+        assert srv.state(ids[2]) == (3, rbe.RBE_ENONFINITE)
+        with pytest.raises(rbe.RBEError) as e:
+            srv.result(ids[2])
+        assert e.value.status == rbe.RBE_ENONFINITE
+        lat, steps, _ = srv.stats()
+        good = [0, 1, 3]
+        # the bad replica ran one chunk and left
+        assert len(lat) == sum(-(-REQS[i][3] // 4) for i in good) + 1
+        for i in good:
+            assert srv.state(ids[i]) == (2, rbe.RBE_OK)
+            _same(srv.result(ids[i]), _direct(REQS[i], precision))
+    finally:
+        srv.close()
+
+
+def test_cancel_queued_and_resident_requests():
+    """rbe_server_cancel takes a queued request out of the queue at once and a resident one out
+    of its slot at the end of its chunk in flight; cancelled requests report RBE_ESTATE, the
+    freed slot serves a later request, and the requests that ran are bit for bit their direct
+    steps."""
+    cuda_device()
+    precision = rbe.RBE_FP32_PHASE
+    srv = rbe.Server(ALPHA, P, precision, max_slots=2, chunk_steps=4, mem_budget=8 << 30)
+    try:
+        def submit(i):
+            n_side, sseed, pseed, nsteps = REQS[i]
+            pos, mom, q, m, box = _system(n_side, sseed)
+            return srv.submit(pos, mom, q, m, box, _dev_params(box), pseed, nsteps)
+        a, b, c = submit(0), submit(1), submit(3)
+        srv.progress(wait=False)  # a and b resident with a chunk in flight, c queued
+        assert srv.state(a)[0] == 1 and srv.state(b)[0] == 1 and srv.state(c)[0] == 0
+        srv.cancel(c)
+        srv.cancel(b)
+        assert srv.state(c) == (4, rbe.RBE_ESTATE)
+        d = submit(2)  # takes b's slot once b has left
+        _run_until_done(srv, 4, time.monotonic() + DEADLINE_S)
+        for rid in (b, c):
+            assert srv.state(rid) == (4, rbe.RBE_ESTATE)
+            with pytest.raises(rbe.RBEError) as e:
+                srv.result(rid)
+            assert e.value.status == rbe.RBE_ESTATE
+        with pytest.raises(rbe.RBEError) as e:
+            srv.cancel(a)  # finished
+        assert e.value.status == rbe.RBE_ESTATE
+        _same(srv.result(a), _direct(REQS[0], precision))
+        _same(srv.result(d), _direct(REQS[2], precision))
+    finally:
+        srv.close()

@@ -81,3 +81,31 @@ def test_null_arguments():
     assert lib.rbe_server_progress(None, 0, None, None, None) == rbe.RBE_EINVAL
     assert lib.rbe_server_destroy(None) == rbe.RBE_OK
     assert lib.rbe_server_last_error(None) == b""
+
+
+def test_cancel_queued_request_on_the_host():
+    """Cancelling a queued request is host logic: it leaves the queue, counts as done, reports
+    state 4 with RBE_ESTATE, its result is RBE_ESTATE, and a second cancel is refused; the other
+    queued request is untouched."""
+    lib = b.load()
+    st, h = _create(_cfg())
+    assert st == rbe.RBE_OK
+    try:
+        rid = ctypes.c_int64(-1)
+        req, keep = _request()
+        assert lib.rbe_server_submit(h, ctypes.byref(req), ctypes.byref(rid)) == rbe.RBE_OK
+        assert lib.rbe_server_submit(h, ctypes.byref(req), ctypes.byref(rid)) == rbe.RBE_OK
+        state, err = ctypes.c_int32(-1), ctypes.c_int(-1)
+        assert lib.rbe_server_request_state(h, 0, ctypes.byref(state), ctypes.byref(err)) == rbe.RBE_OK
+        assert (state.value, err.value) == (0, rbe.RBE_OK)
+        assert lib.rbe_server_cancel(h, 0) == rbe.RBE_OK
+        assert lib.rbe_server_request_state(h, 0, ctypes.byref(state), ctypes.byref(err)) == rbe.RBE_OK
+        assert (state.value, err.value) == (4, rbe.RBE_ESTATE)
+        assert lib.rbe_server_result(h, 0, None, None, None) == rbe.RBE_ESTATE
+        assert b"cancelled" in lib.rbe_server_last_error(h)
+        assert lib.rbe_server_cancel(h, 0) == rbe.RBE_ESTATE
+        assert lib.rbe_server_request_state(h, 1, ctypes.byref(state), None) == rbe.RBE_OK and state.value == 0
+        assert lib.rbe_server_cancel(h, 9) == rbe.RBE_EINVAL
+        assert lib.rbe_server_request_state(h, 9, None, None) == rbe.RBE_EINVAL
+    finally:
+        lib.rbe_server_destroy(h)
