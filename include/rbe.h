@@ -62,8 +62,10 @@ typedef enum {
 
 typedef enum {
     RBE_RHO_FP64 = 0,    /* FP32-phase path: rho accumulated per pair in FP64 */
-    RBE_RHO_COMP32 = 1,  /* FP32-phase path: compensated (Kahan) FP32 sums of every term within a staged
-                            tile, float-float (about 48 bits) across tiles (default) */
+    RBE_RHO_COMP32 = 1,  /* FP32-phase path: compensated FP32 summation within a staged tile (FP32
+                            partial sums of four consecutive particles added with Kahan's
+                            compensation: a rounding error that does not grow with the particle
+                            count), float-float (about 48 bits) across tiles (default) */
     RBE_RHO_FP32 = 2     /* FP32-phase path: plain FP32 within a staged tile, float-float across (faster;
                             outside the compensated-or-FP64 rule of the default) */
 } rbe_rho_accum;
@@ -485,13 +487,19 @@ rbe_status rbe_flex_step(rbe_ctx ctx, rbe_flex_system* sys, int32_t nsteps);
 
 /* ---------------------------------------------------------------------------------
  * Batched k-space evaluation: many systems of uneven N (the RBE force, energy and virial of
- * Sec. 4.2 for each) in five launches per evaluation, FP32-phase path with plain FP32
- * accumulation inside a staged tile.  The batch fixes alpha and P; every item brings its own
- * positions, charges, box, Philox key and batch index, and gets the same frequencies m as
- * rbe_sample_k with that key and index.  Work runs as persistent grids over a work list of
- * (item, tile) pairs; the tile shapes are the batch's (rbe_batch_set_tiles, or chosen by
- * rbe_batch_autotune).  An item's outputs depend only on its own inputs and the tile shapes,
- * not on the other items.  No counterpart in the paper (its runs are single systems). */
+ * Sec. 4.2 for each) in ONE persistent launch per evaluation: a cooperative grid of resident
+ * blocks that runs the five passes (tables, sampling, rho, rho reduction, forces with energy and
+ * virial) with a grid barrier between them, each pass a loop over a work list of (item, tile)
+ * units.  The barriers wait a bounded time (about a quarter of a second); a barrier that gives up
+ * latches RBE_ETIMEOUT, reported by rbe_batch_sync.  FP32-phase path with compensated FP32
+ * accumulation (RBE_RHO_COMP32) and FP64 energy and virial terms.  The batch fixes alpha and P;
+ * every item brings its own positions, charges, box, Philox key and batch index, and gets the
+ * same frequencies m as rbe_sample_k with that key and index; an item's box and index may also
+ * live in device memory (box_dev, step_dev: an NPT replica's cell block), read at run time, so a
+ * captured graph of the evaluation follows them.  Tile shapes are the batch's
+ * (rbe_batch_set_tiles, or chosen by rbe_batch_autotune).  An item's outputs depend only on its
+ * own inputs and the tile shapes, not on the other items.  No counterpart in the paper (its runs
+ * are single systems). */
 typedef struct rbe_batch_s* rbe_batch;
 
 typedef struct {
@@ -504,6 +512,11 @@ typedef struct {
     double box[3];         /* rectangular box of this item */
     uint64_t seed;         /* Philox key of this item */
     uint64_t step;         /* batch index (< 2^56) */
+    const double* box_dev;     /* NULL, or the item's box in device memory (3 doubles, 8-byte aligned):
+                                  read by every evaluation (its tables rebuilt each time) instead of
+                                  box[], which then only bounds the table size check */
+    const uint64_t* step_dev;  /* NULL, or the item's batch index in device memory (read by every
+                                  evaluation instead of step) */
 } rbe_batch_item;
 
 /* A batch for up to max_items items with boxes no longer than max_box on any axis (sizes the
@@ -512,9 +525,10 @@ rbe_status rbe_batch_create(double alpha, int32_t P, int32_t max_items, double m
 rbe_status rbe_batch_destroy(rbe_batch b);
 /* Stream of later evaluations (a cudaStream_t; NULL = legacy default); synchronises the old one. */
 rbe_status rbe_batch_set_stream(rbe_batch b, void* stream);
-/* Tile shapes: rho_k frequencies per rho tile (a multiple of 32 in [32, 256]), rho_chunk
- * particles per rho chunk (>= 32), force_block particles per force tile (a positive multiple of
- * 128).  All three 0 restores the defaults. */
+/* Tile shapes: rho_k frequencies per rho tile (32, 64, 128 or 256; a block of 256 threads runs
+ * 256 / rho_k particle sub-streams of the tile), rho_chunk particles per rho chunk (>= 32),
+ * force_block particles per force tile (a positive multiple of 128).  All three 0 restores the
+ * defaults. */
 rbe_status rbe_batch_set_tiles(rbe_batch b, int32_t rho_k, int32_t rho_chunk, int32_t force_block);
 rbe_status rbe_batch_get_tiles(rbe_batch b, int32_t* rho_k, int32_t* rho_chunk, int32_t* force_block);
 
@@ -532,6 +546,18 @@ rbe_status rbe_kspace_forces_virial_batched(rbe_batch b, const rbe_batch_item* i
  * items' outputs are overwritten.  *best_ms (may be NULL): mean time of one evaluation with
  * the chosen shapes.  Synchronous. */
 rbe_status rbe_batch_autotune(rbe_batch b, const rbe_batch_item* items, int32_t n, int32_t reps, double* best_ms);
+
+/* 1 (default): one persistent cooperative launch per evaluation; 0: one launch per pass (the same
+ * tile bodies and results, bit for bit).  RBE_EINVAL for other values. */
+rbe_status rbe_batch_set_persistent(rbe_batch b, int32_t enable);
+
+/* Test of the failure path of the persistent launch (no counterpart in the paper): with
+ * enable = 1 the grid barriers of later persistent evaluations wait for one block more than the
+ * grid has, so every wait runs out after its one-second limit, the blocks leave the kernel, and
+ * rbe_batch_sync reports RBE_ETIMEOUT (the outputs of that evaluation are incomplete); 0
+ * restores normal operation, and the next evaluation is complete again.  RBE_EINVAL for other
+ * values. */
+rbe_status rbe_batch_test_barrier_timeout(rbe_batch b, int32_t enable);
 
 /* Waits for the batch's stream and reports device-side errors of earlier evaluations. */
 rbe_status rbe_batch_sync(rbe_batch b);

@@ -103,7 +103,8 @@ CELL_PC, CELL_WD, CELL_K2D, CELL_PD = 12, 16, 19, 22
 class BatchItem(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("pos", ctypes.c_void_p), ("charge", ctypes.c_void_p),
                 ("forces", ctypes.c_void_p), ("virial", ctypes.c_void_p), ("energy", ctypes.c_void_p),
-                ("box", ctypes.c_double * 3), ("seed", ctypes.c_uint64), ("step", ctypes.c_uint64)]
+                ("box", ctypes.c_double * 3), ("seed", ctypes.c_uint64), ("step", ctypes.c_uint64),
+                ("box_dev", ctypes.c_void_p), ("step_dev", ctypes.c_void_p)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -158,6 +159,8 @@ SIGNATURES = [
     ("rbe_batch_destroy", ctypes.c_int, [_vp]),
     ("rbe_batch_set_stream", ctypes.c_int, [_vp, _vp]),
     ("rbe_batch_set_tiles", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    ("rbe_batch_set_persistent", ctypes.c_int, [_vp, ctypes.c_int32]),
+    ("rbe_batch_test_barrier_timeout", ctypes.c_int, [_vp, ctypes.c_int32]),
     ("rbe_batch_get_tiles", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                            ctypes.POINTER(ctypes.c_int32)]),
     ("rbe_kspace_forces_virial_batched", ctypes.c_int, [_vp, ctypes.POINTER(BatchItem), ctypes.c_int32]),
@@ -518,11 +521,13 @@ class Batch:
         arr = (BatchItem * len(systems))()
         for k, sy in enumerate(systems):
             E = sy.get("E")
+            bd, sd = sy.get("box_dev"), sy.get("step_dev")
             arr[k] = BatchItem(N=int(sy["q"].shape[0]), pos=sy["pos"].data_ptr(), charge=sy["q"].data_ptr(),
                                forces=sy["F"].data_ptr(), virial=sy["W"].data_ptr(),
                                energy=E.data_ptr() if E is not None else None,
                                box=(ctypes.c_double * 3)(*[float(b) for b in sy["box"]]), seed=int(sy["seed"]),
-                               step=int(sy["step"]))
+                               step=int(sy["step"]), box_dev=bd.data_ptr() if bd is not None else None,
+                               step_dev=sd.data_ptr() if sd is not None else None)
         return arr
 
     def evaluate(self, items):
@@ -534,6 +539,12 @@ class Batch:
         ms = ctypes.c_double()
         self._check(load().rbe_batch_autotune(self.h, arr, len(arr), int(reps), ctypes.byref(ms)))
         return ms.value
+
+    def test_barrier_timeout(self, enable: bool):
+        self._check(load().rbe_batch_test_barrier_timeout(self.h, int(bool(enable))))
+
+    def set_persistent(self, enable: bool):
+        self._check(load().rbe_batch_set_persistent(self.h, int(bool(enable))))
 
     def set_tiles(self, rho_k: int, rho_chunk: int, force_block: int):
         self._check(load().rbe_batch_set_tiles(self.h, int(rho_k), int(rho_chunk), int(force_block)))

@@ -1,20 +1,23 @@
-// Batched RBE k-space evaluation: many systems of uneven N in five launches in total.
+// Batched RBE k-space evaluation: many systems of uneven N in one persistent launch.
 //
 // Each item is one system (its own positions, charges, box, Philox key and batch index) with
 // the batch's alpha and P, on the FP32-phase path with compensated FP32 accumulation inside
-// a staged tile (RBE_RHO_COMP32) and FP64 energy and virial terms.  Per evaluation:
-//   k_btables   one block per item whose box changed: tables and box constants  (H1)
-//   k_bsample   blocks of 128 frequencies per item                             (H2)
-//   k_brho      persistent grid over the work list of (item, frequency tile, particle
-//               chunk) tiles: partial rho(k) per chunk                         (H4)
-//   k_breduce   one block per (item, frequency): rho(k), terms, force coefficients (H3, H6)
-//   k_bforce    persistent grid over (item, particle block) tiles, then one final-sum tile
-//               per item: forces, virial, energies                             (H5, H6)
+// a staged tile (RBE_RHO_COMP32) and FP64 energy and virial terms.  One evaluation is one
+// cooperative launch of k_batch whose blocks stay resident and run five passes, with a grid
+// barrier (bounded wait) between consecutive passes:
+//   tables   one unit per item whose box changed (or lives on the device): tables and box
+//            constants                                                           (H1)
+//   sample   units of 256 frequencies per item                                   (H2)
+//   rho      the work list of (item, frequency tile, particle chunk) tiles: partial rho(k)
+//            per chunk                                                           (H4)
+//   reduce   one unit per (item, frequency): rho(k), terms, force coefficients   (H3, H6)
+//   force    the work list of (item, particle block) tiles, then one final-sum unit per item:
+//            forces, virial, energies                                            (H5, H6)
 // The tiles run the single-system kernels' bodies (rbe_kspace_tiles.cuh).  Tile shapes
 // (frequencies per rho tile, particles per rho chunk, particles per force block) are the
 // batch's, set by hand or by rbe_batch_autotune, which times the candidate shapes on the
-// caller's items.  An item's result depends only on its own inputs and the tile shapes, never
-// on the other items (fixed-order sums inside the item's tiles).
+// caller's items pass by pass.  An item's result depends only on its own inputs and the tile
+// shapes, never on the other items (fixed-order sums inside the item's tiles).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,6 +39,8 @@ struct BItem {
     double* F;
     double* W;
     double* E;
+    const double* box_dev;                // the item's box in device memory (read every evaluation), or NULL
+    const unsigned long long* step_dev;   // the item's batch index in device memory, or NULL: `step`
     int64_t N;
     uint64_t seed, step;
     int64_t chunk_len, per_block;
@@ -43,77 +48,201 @@ struct BItem {
     int nchunks, fblocks;
 };
 
-constexpr int kSampleBlock = 128;
+// Every batched kernel runs blocks of kBThreads threads; a sampling unit covers kSampleBlock
+// frequencies of one item.
+constexpr int kBThreads = kForceThreads;
+constexpr int kSampleBlock = kBThreads;
+// Bounded wait of the grid barrier: one second by the GPU's global timer (and at most
+// kBarrierSpins polls), then the block gives up and the evaluation reports RBE_ETIMEOUT.
+constexpr unsigned long long kBarrierNs = 1000000000ull;
+constexpr int kBarrierSpins = 1 << 24;
+// unroll of the force pass's frequency loop in the batched kernel, whose registers are shared by
+// all five passes
+#ifndef RBE_BATCH_FORCE_LUNROLL
+#define RBE_BATCH_FORCE_LUNROLL 2
+#endif
+constexpr int kBatchForceUnroll = RBE_BATCH_FORCE_LUNROLL;
 
-__global__ void __launch_bounds__(kTableThreads)
-k_btables(const double* __restrict__ boxes, const int* __restrict__ which, double alpha, int P,
-          unsigned long long* __restrict__ cum, int cap, KState* __restrict__ ks, unsigned* __restrict__ status)
+struct GridBar {
+    unsigned count;     // blocks arrived at the current barrier
+    unsigned pad[31];   // (the count and the generation on lines of their own)
+    unsigned gen;       // barriers completed
+};
+
+// Everything the five passes of one batched evaluation read and write.
+struct BArgs {
+    const BItem* items;
+    int n, P;
+    const double* boxes;        // host-given boxes (3 per item)
+    const int* which;           // items whose tables are rebuilt
+    int nw;
+    double alpha;
+    unsigned long long* cum;    // per item: 3 x cap cumulative weights
+    int cap, smem_cap;
+    KState* ks;
+    int bpi;                    // sampling units per item
+    int4* m;
+    double* w;
+    const int4* rtiles;         // (item, frequency tile, chunk)
+    int nrt, S;                 // rho tiles; particle sub-streams of a rho block (kBThreads / rho_k)
+    float4* part;
+    double2* rho;
+    double* terms;
+    int4* coef_m;
+    float4* coef_f;
+    const int2* ftiles;         // (item, particle block)
+    int nft;
+    unsigned* status;
+    GridBar* bar;
+    int bar_extra;              // test hook: arrivals the barriers wait for beyond the grid (0)
+};
+
+// Grid-wide barrier of a cooperative launch with a bounded wait.  Thread 0 of each block reads
+// the generation, then arrives with an acquire-release add on the count (its block's writes,
+// ordered before it by the block barrier and a fence, are visible to whoever observes the
+// arrival); the last block to arrive resets the count and advances the generation with an
+// acquire-release add; the others poll the generation with acquire loads and a short back-off.
+// Returns false, after latching kStatusTimeout, when the other blocks did not all arrive within
+// kBarrierSpins polls: the caller then leaves the kernel, and the other blocks' later barriers
+// time out in turn.  The words are zeroed before every launch.
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
 {
-    const int r = which[blockIdx.x];
-    const double* b = boxes + 3 * (size_t)r;
-    tables_body(b[0], b[1], b[2], nullptr, alpha, P, cum + (size_t)r * 3 * cap, cap, ks + r, status);
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
-__global__ void k_bsample(const BItem* __restrict__ items, int P, int blocks_per_item,
-                          const unsigned long long* __restrict__ cum, int cap, int smem_cap,
-                          const KState* __restrict__ ks, int4* __restrict__ m, double* __restrict__ w,
-                          unsigned* __restrict__ status)
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v)
 {
-    const int r = blockIdx.x / blocks_per_item;
-    const int lb = (blockIdx.x % blocks_per_item) * kSampleBlock;
-    const BItem it = items[r];
-    sample_body(lb, it.seed, it.step, nullptr, P, P, cum + (size_t)r * 3 * cap, cap, smem_cap, ks + r,
-                m + (size_t)r * P, w + (size_t)r * P, status);
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
 }
 
-// Persistent: block b takes tiles b, b + gridDim.x, ...; tile = (item, frequency tile,
-// particle chunk).  blockDim.x = frequencies per tile.
-__global__ void __launch_bounds__(kMaxRhoThreads, 8)
-k_brho(const BItem* __restrict__ items, const int4* __restrict__ tiles, int ntiles, const KState* __restrict__ ks,
-       const int4* __restrict__ m, int P, float4* __restrict__ partials, unsigned* __restrict__ status)
+__device__ __forceinline__ unsigned long long global_ns()
 {
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int4 tl = tiles[t];
-        const BItem it = items[tl.x];
-        rho_f32_tile<RBE_RHO_COMP32, 1>(tl.y, tl.z, it.pos, it.q, it.N, ks + tl.x, m + (size_t)tl.x * P, P, it.chunk_len,
-                                   it.nchunks, partials + it.part_off, status);
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ bool grid_sync(GridBar* bar, unsigned nblocks, unsigned* status)
+{
+    __shared__ unsigned ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned good = 1u;
+        __threadfence();
+        const unsigned g = ld_acquire(&bar->gen);
+        if (atom_add_acq_rel(&bar->count, 1u) + 1u == nblocks) {
+            bar->count = 0u;  // ordered before the release below
+            atom_add_acq_rel(&bar->gen, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            for (int it = 0; ld_acquire(&bar->gen) == g; ++it) {
+                if (it >= kBarrierSpins || global_ns() - t0 > kBarrierNs) {
+                    good = 0u;
+                    atomicOr(status, kStatusTimeout);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0u;
+}
+
+// The passes (Sec. 4.2 for each item), each a loop of units over the blocks of the grid.
+__device__ __forceinline__ void pass_tables(const BArgs& a)
+{
+    for (int w = blockIdx.x; w < a.nw; w += gridDim.x) {
+        const int r = a.which[w];
+        const double* b = a.boxes + 3 * (size_t)r;
+        tables_body(b[0], b[1], b[2], a.items[r].box_dev, a.alpha, a.P, a.cum + (size_t)r * 3 * a.cap, a.cap, a.ks + r,
+                    a.status);
         __syncthreads();
     }
 }
 
-__global__ void __launch_bounds__(kReduceThreads)
-k_breduce(const BItem* __restrict__ items, int P, const float4* __restrict__ partials, const int4* __restrict__ m,
-          const double* __restrict__ w, const KState* __restrict__ ks, double2* __restrict__ rho,
-          double* __restrict__ terms, int4* __restrict__ coef_m, float4* __restrict__ coef_f,
-          unsigned* __restrict__ status)
+__device__ __forceinline__ void pass_sample(const BArgs& a)
 {
-    const int r = blockIdx.x / (P + 1), l = blockIdx.x % (P + 1);
-    const BItem it = items[r];
-    const size_t o = (size_t)r * P;
-    reduce_f32_row(l, partials + it.part_off, it.nchunks, P, m + o, w + o, ks + r, rho + o,
-                   terms + (size_t)r * (P + 1) * 8, coef_m + o, coef_f + o, status);
+    for (int u = blockIdx.x; u < a.n * a.bpi; u += gridDim.x) {
+        const int r = u / a.bpi, lb = (u % a.bpi) * kSampleBlock;
+        const BItem& it = a.items[r];
+        sample_body(lb, it.seed, it.step, it.step_dev, a.P, a.P, a.cum + (size_t)r * 3 * a.cap, a.cap, a.smem_cap,
+                    a.ks + r, a.m + (size_t)r * a.P, a.w + (size_t)r * a.P, a.status);
+        __syncthreads();
+    }
 }
 
-// Persistent: tiles [0, nforce) are (item, particle block); tiles [nforce, nforce + R) the
-// per-item energy and virial sums.
-__global__ void __launch_bounds__(kForceThreads, RBE_FORCE_MINB)
-k_bforce(const BItem* __restrict__ items, const int2* __restrict__ tiles, int nforce, int R,
-         const KState* __restrict__ ks, const int4* __restrict__ coef_m, const float4* __restrict__ coef_f, int P,
-         const double* __restrict__ terms, unsigned* __restrict__ status)
+__device__ __forceinline__ void pass_rho(const BArgs& a)
 {
-    for (int t = blockIdx.x; t < nforce + R; t += gridDim.x) {
-        if (t < nforce) {
-            const int2 tl = tiles[t];
-            const BItem it = items[tl.x];
-            const size_t o = (size_t)tl.x * P;
-            force_f32_block<false>((int64_t)tl.y, it.pos, it.q, it.N, it.per_block, ks + tl.x, coef_m + o, coef_f + o, P,
-                            it.F, status);
+    for (int t = blockIdx.x; t < a.nrt; t += gridDim.x) {
+        const int4 tl = a.rtiles[t];
+        const BItem& it = a.items[tl.x];
+        rho_f32_tile<RBE_RHO_COMP32, 1>(tl.y, tl.z, it.pos, it.q, it.N, a.ks + tl.x, a.m + (size_t)tl.x * a.P, a.P,
+                                        it.chunk_len, it.nchunks, a.part + it.part_off, a.status, a.S);
+        __syncthreads();
+    }
+}
+
+// one (item, frequency) row per warp
+__device__ __forceinline__ void pass_reduce(const BArgs& a)
+{
+    const int wpb = kBThreads / 32, warp = threadIdx.x >> 5;
+    for (int u = blockIdx.x * wpb + warp; u < a.n * (a.P + 1); u += gridDim.x * wpb) {
+        const int r = u / (a.P + 1), l = u % (a.P + 1);
+        const BItem& it = a.items[r];
+        const size_t o = (size_t)r * a.P;
+        reduce_f32_row_warp(l, a.part + it.part_off, it.nchunks, a.P, a.m + o, a.w + o, a.ks + r, a.rho + o,
+                            a.terms + (size_t)r * (a.P + 1) * 8, a.coef_m + o, a.coef_f + o, a.status);
+    }
+}
+
+// tiles [0, nft) are (item, particle block); tiles [nft, nft + n) the per-item energy and
+// virial sums
+__device__ __forceinline__ void pass_force(const BArgs& a)
+{
+    for (int t = blockIdx.x; t < a.nft + a.n; t += gridDim.x) {
+        if (t < a.nft) {
+            const int2 tl = a.ftiles[t];
+            const BItem& it = a.items[tl.x];
+            const size_t o = (size_t)tl.x * a.P;
+            force_f32_block<false, kBatchForceUnroll>((int64_t)tl.y, it.pos, it.q, it.N, it.per_block, a.ks + tl.x, a.coef_m + o,
+                                   a.coef_f + o, a.P, it.F, a.status);
         } else {
-            const int r = t - nforce;
-            const BItem it = items[r];
-            final_sums(terms + (size_t)r * (P + 1) * 8, P, ks + r, it.W, it.E, status);
+            const int r = t - a.nft;
+            const BItem& it = a.items[r];
+            final_sums(a.terms + (size_t)r * (a.P + 1) * 8, a.P, a.ks + r, it.W, it.E, a.status);
         }
         __syncthreads();
+    }
+}
+
+// The batched evaluation: the passes in `mask` (1 tables, 2 sample, 4 rho, 8 reduce, 16
+// force).  All five in one launch is the persistent form: a cooperative launch whose blocks
+// all stay resident, with a grid barrier between consecutive passes; a single pass runs as an
+// ordinary launch (the tuner times passes one by one).
+#ifndef RBE_BATCH_MINB
+#define RBE_BATCH_MINB 2
+#endif
+__global__ void __launch_bounds__(kBThreads, RBE_BATCH_MINB) k_batch(BArgs a, int mask)
+{
+    bool first = true;
+    const int passes[5] = {1, 2, 4, 8, 16};
+    for (int k = 0; k < 5; ++k) {
+        if (!(mask & passes[k])) continue;
+        if (!first && !grid_sync(a.bar, gridDim.x + (unsigned)a.bar_extra, a.status)) return;
+        first = false;
+        switch (k) {
+        case 0: pass_tables(a); break;
+        case 1: pass_sample(a); break;
+        case 2: pass_rho(a); break;
+        case 3: pass_reduce(a); break;
+        default: pass_force(a); break;
+        }
     }
 }
 
@@ -171,8 +300,10 @@ struct rbe_batch_s {
     int n_rtiles = 0, n_ftiles = 0;
     std::vector<int4> h_rtiles;
     std::vector<int2> h_ftiles;
-    int rho_grid_per_sm[kMaxRhoThreads / 32 + 1] = {0};
-    int force_grid_per_sm = 1;
+    int grid_per_sm = 1;      // resident blocks of k_batch per SM (the persistent grid)
+    GridBar* d_bar = nullptr;  // the grid barrier of the persistent launch
+    bool persistent = true;    // one cooperative launch per evaluation (else one launch per pass)
+    int bar_extra = 0;         // test hook of the barriers' timeout (rbe_batch_test_barrier_timeout)
     cudaEvent_t upload_ev = nullptr;  // after the last upload of the pinned descriptors
     bool upload_pending = false;
     std::string last_error;
@@ -231,17 +362,22 @@ bool capturing(cudaStream_t s)
 
 bool valid_tiles(int P, int rho_k, int rho_chunk, int force_block)
 {
-    return rho_k >= 32 && rho_k <= kMaxRhoThreads && rho_k % 32 == 0 && rho_chunk >= 32 && rho_chunk <= (1 << 24) &&
-           force_block >= kForceRound && force_block % kForceRound == 0 && force_block <= (1 << 24) && P >= 1;
+    // a rho tile of rho_k frequencies fills a block of kBThreads threads with kBThreads / rho_k
+    // particle sub-streams
+    return (rho_k == 32 || rho_k == 64 || rho_k == 128 || rho_k == 256) && rho_chunk >= 32 &&
+           rho_chunk <= (1 << 24) && force_block >= kForceRound && force_block % kForceRound == 0 &&
+           force_block <= (1 << 24) && P >= 1;
 }
 
-// The tile shapes the planner uses when none were set: the single-system planner's
-// frequency tiles (whole warps, at most 256 frequencies) and chunks of 256 particles.
+// The tile shapes the planner uses when none were set: frequency tiles of the smallest power
+// of two (32 to 256) that covers P in the fewest tiles, chunks of 256 particles.
 void default_tiles(rbe_batch b)
 {
-    const int ktiles = (b->P + kMaxRhoThreads - 1) / kMaxRhoThreads;
+    const int ktiles = (b->P + kBThreads - 1) / kBThreads;
     const int per = (b->P + ktiles - 1) / ktiles;
-    b->rho_k = std::min(kMaxRhoThreads, 32 * ((per + 31) / 32));
+    int k = 32;
+    while (k < per) k *= 2;
+    b->rho_k = k;
     b->rho_chunk = 256;
     b->force_block = 2 * kForceRound;
 }
@@ -268,6 +404,8 @@ rbe_status validate_items(rbe_batch b, const rbe_batch_item* items, int n)
             if (2 * host_axis_M(b->alpha, l) + 1 > b->cap)
                 return bfail(b, RBE_EINVAL, "item box beyond the batch's table capacity (rbe_batch_create max_box)");
         }
+        if ((reinterpret_cast<uintptr_t>(it.box_dev) | reinterpret_cast<uintptr_t>(it.step_dev)) % 8)
+            return bfail(b, RBE_EINVAL, "item box_dev and step_dev must be 8-byte aligned");
     }
     return RBE_OK;
 }
@@ -332,12 +470,15 @@ rbe_status plan(rbe_batch b, const rbe_batch_item* items, int n)
         it.N = items[r].N;
         it.seed = items[r].seed;
         it.step = items[r].step;
+        it.box_dev = items[r].box_dev;
+        it.step_dev = reinterpret_cast<const unsigned long long*>(items[r].step_dev);
     }
     return RBE_OK;
 }
 
-// The launches of one evaluation; which of the five passes run is given by the mask
-// (1 tables, 2 sample, 4 rho, 8 reduce, 16 force) so that the tuner can time one pass.
+// One evaluation: the passes in `mask` (1 tables, 2 sample, 4 rho, 8 reduce, 16 force; the
+// tuner times one pass at a time).  All five: one persistent cooperative launch of k_batch
+// (grid barriers between the passes), or, with persistence off, one launch per pass.
 rbe_status launch(rbe_batch b, int n, int mask)
 {
     cudaStream_t s = b->stream;
@@ -346,56 +487,83 @@ rbe_status launch(rbe_batch b, int n, int mask)
         return bcuda(b, e, "upload items");
     const bool cap = capturing(s);
     const int P = b->P;
+    int nw = 0;
     if (mask & 1) {
-        // tables of the items whose box changed since the last evaluation
-        int nw = 0;
+        // tables of the items whose host box changed since the last evaluation, and of every item
+        // whose box lives on the device
         for (int r = 0; r < n; ++r) {
             const double* bx = b->h_boxes + 3 * (size_t)r;
             const bool changed = b->last_boxes.size() < 3 * (size_t)(r + 1) || b->last_boxes[3 * r] != bx[0] ||
                                  b->last_boxes[3 * r + 1] != bx[1] || b->last_boxes[3 * r + 2] != bx[2];
-            if (changed) b->h_which[nw++] = r;
+            if (changed || b->h_items[r].box_dev) b->h_which[nw++] = r;
         }
-        if (nw > 0) {
-            if ((e = cudaMemcpyAsync(b->d_boxes, b->h_boxes, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s)) !=
-                    cudaSuccess ||
-                (e = cudaMemcpyAsync(b->d_which, b->h_which, sizeof(int) * nw, cudaMemcpyHostToDevice, s)) !=
-                    cudaSuccess)
-                return bcuda(b, e, "upload boxes");
-            k_btables<<<nw, kTableThreads, 0, s>>>(b->d_boxes, b->d_which, b->alpha, P, b->d_cum, b->cap, b->d_ks,
-                                                   b->d_status);
-            b->last_boxes.assign(b->h_boxes, b->h_boxes + 3 * (size_t)n);
-        }
+        if (nw > 0 &&
+            ((e = cudaMemcpyAsync(b->d_boxes, b->h_boxes, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s)) !=
+                 cudaSuccess ||
+             (e = cudaMemcpyAsync(b->d_which, b->h_which, sizeof(int) * nw, cudaMemcpyHostToDevice, s)) != cudaSuccess))
+            return bcuda(b, e, "upload boxes");
+        b->last_boxes.assign(b->h_boxes, b->h_boxes + 3 * (size_t)n);
     }
     // the pinned descriptors (and boxes) may be overwritten once these copies have run
     if (!cap) {
         if ((e = cudaEventRecord(b->upload_ev, s)) != cudaSuccess) return bcuda(b, e, "cudaEventRecord");
         b->upload_pending = true;
     }
-    if (mask & 2) {
-        const int bpi = (P + kSampleBlock - 1) / kSampleBlock;
-        const size_t smem = sizeof(unsigned long long) * 3 * (size_t)b->cap;
-        const int smem_cap = smem <= 48 * 1024 ? b->cap : 0;
-        k_bsample<<<n * bpi, kSampleBlock, smem_cap ? smem : 0, s>>>(b->d_items, P, bpi, b->d_cum, b->cap, smem_cap,
-                                                                    b->d_ks, b->d_m, b->d_w, b->d_status);
+    BArgs a;
+    a.items = b->d_items;
+    a.n = n;
+    a.P = P;
+    a.boxes = b->d_boxes;
+    a.which = b->d_which;
+    a.nw = nw;
+    a.alpha = b->alpha;
+    a.cum = b->d_cum;
+    a.cap = b->cap;
+    const size_t table_smem = sizeof(unsigned long long) * 3 * (size_t)b->cap;
+    a.smem_cap = table_smem <= 48 * 1024 ? b->cap : 0;
+    a.ks = b->d_ks;
+    a.bpi = (P + kSampleBlock - 1) / kSampleBlock;
+    a.m = b->d_m;
+    a.w = b->d_w;
+    a.rtiles = b->d_rtiles;
+    a.nrt = b->n_rtiles;
+    a.S = kBThreads / b->rho_k;
+    a.part = b->d_part;
+    a.rho = b->d_rho;
+    a.terms = b->d_terms;
+    a.coef_m = b->d_coef_m;
+    a.coef_f = b->d_coef_f;
+    a.ftiles = b->d_ftiles;
+    a.nft = b->n_ftiles;
+    a.status = b->d_status;
+    a.bar = b->d_bar;
+    a.bar_extra = b->bar_extra;
+    const size_t smem = std::max(a.smem_cap ? table_smem : 0, (size_t)kForceSmemPerK * std::min(P, kForceStageK));
+    const int resident = std::max(1, b->num_sms * b->grid_per_sm);
+    auto run = [&](int m, int units, bool coop) -> cudaError_t {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(coop ? resident : std::max(1, std::min(units, resident)));
+        cfg.blockDim = dim3(kBThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = coop ? 1 : 0;
+        return cudaLaunchKernelEx(&cfg, k_batch, a, m);
+    };
+    if (mask == 31 && b->persistent) {
+        // the barrier words start at zero for every launch (a launch that timed out leaves them set)
+        if ((e = cudaMemsetAsync(b->d_bar, 0, sizeof(GridBar), s)) != cudaSuccess) return bcuda(b, e, "barrier reset");
+        if ((e = run(31, 0, true)) != cudaSuccess) return bcuda(b, e, "persistent batched k-space launch");
+        return RBE_OK;
     }
-    if (mask & 4) {
-        int& per_sm = b->rho_grid_per_sm[b->rho_k / 32];
-        if (per_sm == 0) per_sm = resident_blocks(k_brho, b->rho_k, 0);
-        const int grid = std::max(1, std::min(b->n_rtiles, b->num_sms * per_sm));
-        k_brho<<<grid, b->rho_k, 0, s>>>(b->d_items, b->d_rtiles, b->n_rtiles, b->d_ks, b->d_m, P, b->d_part,
-                                         b->d_status);
+    const int units[5] = {nw, n * a.bpi, a.nrt, (n * (P + 1) + kBThreads / 32 - 1) / (kBThreads / 32), a.nft + n};
+    for (int k = 0; k < 5; ++k) {
+        if (!(mask & (1 << k)) || units[k] == 0) continue;
+        if ((e = run(1 << k, units[k], false)) != cudaSuccess) return bcuda(b, e, "batched k-space pass");
     }
-    if (mask & 8)
-        k_breduce<<<n * (P + 1), kReduceThreads, 0, s>>>(b->d_items, P, b->d_part, b->d_m, b->d_w, b->d_ks, b->d_rho,
-                                                         b->d_terms, b->d_coef_m, b->d_coef_f, b->d_status);
-    if (mask & 16) {
-        const int kstage = std::min(P, kForceStageK);
-        const int grid = std::max(1, std::min(b->n_ftiles + n, b->num_sms * b->force_grid_per_sm));
-        k_bforce<<<grid, kForceThreads, (size_t)kForceSmemPerK * kstage, s>>>(b->d_items, b->d_ftiles, b->n_ftiles, n, b->d_ks,
-                                                                 b->d_coef_m, b->d_coef_f, P, b->d_terms,
-                                                                 b->d_status);
-    }
-    if ((e = cudaGetLastError()) != cudaSuccess) return bcuda(b, e, "batched k-space launch");
     return RBE_OK;
 }
 
@@ -421,7 +589,7 @@ void free_batch(rbe_batch b)
     for (void* p : {(void*)b->d_items, (void*)b->d_boxes, (void*)b->d_which, (void*)b->d_ks, (void*)b->d_cum,
                     (void*)b->d_m, (void*)b->d_w, (void*)b->d_rho, (void*)b->d_terms, (void*)b->d_coef_m,
                     (void*)b->d_coef_f, (void*)b->d_status, (void*)b->d_part, (void*)b->d_rtiles,
-                    (void*)b->d_ftiles})
+                    (void*)b->d_ftiles, (void*)b->d_bar})
         if (p) cudaFree(p);
     if (b->h_items) cudaFreeHost(b->h_items);
     if (b->h_boxes) cudaFreeHost(b->h_boxes);
@@ -468,14 +636,20 @@ rbe_status rbe_batch_create(double alpha, int32_t P, int32_t max_items, double m
     A((void**)&b->d_coef_m, sizeof(int4) * P * R);
     A((void**)&b->d_coef_f, sizeof(float4) * P * R);
     A((void**)&b->d_status, sizeof(unsigned));
+    A((void**)&b->d_bar, sizeof(GridBar));
     if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(b->d_bar, 0, sizeof(GridBar));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_items, sizeof(BItem) * R);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_boxes, sizeof(double) * 3 * R);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_which, sizeof(int) * R);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->upload_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) {
-        cudaFuncSetAttribute(k_bforce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kForceSmemPerK * kForceStageK));
-        b->force_grid_per_sm = resident_blocks(k_bforce, kForceThreads, (size_t)kForceSmemPerK * std::min(P, kForceStageK));
+        // dynamic shared memory: the sampler's tables (when they fit 48 KB) or the force pass's
+        // staged frequencies; the persistent grid is every block that fits at once
+        const size_t tsm = sizeof(unsigned long long) * 3 * (size_t)b->cap;
+        const size_t smem = std::max(tsm <= 48 * 1024 ? tsm : 0, (size_t)kForceSmemPerK * std::min(P, kForceStageK));
+        cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        b->grid_per_sm = resident_blocks(k_batch, kBThreads, smem);
         e = cudaDeviceSynchronize();
     }
     if (e != cudaSuccess) {
@@ -523,6 +697,22 @@ rbe_status rbe_batch_set_tiles(rbe_batch b, int32_t rho_k, int32_t rho_chunk, in
     return RBE_OK;
 }
 
+rbe_status rbe_batch_set_persistent(rbe_batch b, int32_t enable)
+{
+    if (!b) return RBE_EINVAL;
+    if (enable != 0 && enable != 1) return bfail(b, RBE_EINVAL, "enable must be 0 or 1");
+    b->persistent = enable == 1;
+    return RBE_OK;
+}
+
+rbe_status rbe_batch_test_barrier_timeout(rbe_batch b, int32_t enable)
+{
+    if (!b) return RBE_EINVAL;
+    if (enable != 0 && enable != 1) return bfail(b, RBE_EINVAL, "enable must be 0 or 1");
+    b->bar_extra = enable;
+    return RBE_OK;
+}
+
 rbe_status rbe_batch_get_tiles(rbe_batch b, int32_t* rho_k, int32_t* rho_chunk, int32_t* force_block)
 {
     if (!b) return RBE_EINVAL;
@@ -564,7 +754,7 @@ rbe_status rbe_batch_autotune(rbe_batch b, const rbe_batch_item* items, int32_t 
         *ms /= (float)reps;
         return RBE_OK;
     };
-    const int rho_ks[] = {32, 64, 96, 128, 192, 256};
+    const int rho_ks[] = {32, 64, 128, 256};
     const int chunks[] = {64, 128, 256, 512, 1024, 2048};
     const int fblocks[] = {128, 256, 512, 1024, 2048};
     rbe_status st = RBE_OK;
@@ -577,7 +767,7 @@ rbe_status rbe_batch_autotune(rbe_batch b, const rbe_batch_item* items, int32_t 
     for (int k : rho_ks) {
         if (st != RBE_OK) break;
         const int ktiles = (b->P + k - 1) / k;
-        if (k - ((b->P + ktiles - 1) / ktiles) >= 32) continue;  // a whole idle warp per tile
+        if (ktiles > 1 && k < 32 * ((((b->P + ktiles - 1) / ktiles) + 31) / 32)) continue;
         for (int c : chunks) {
             b->rho_k = k;
             b->rho_chunk = c;
@@ -626,6 +816,8 @@ rbe_status rbe_batch_sync(rbe_batch b)
     if (bits) {
         cudaMemset(b->d_status, 0, sizeof(unsigned));
         if (bits & kStatusSample) return bfail(b, RBE_ESAMPLE, "a frequency stayed m = 0 after 2^20 redraws");
+        if (bits & kStatusTimeout)
+            return bfail(b, RBE_ETIMEOUT, "a grid barrier of the persistent launch gave up waiting (one second)");
         if (bits & kStatusTable) return bfail(b, RBE_ESTATE, "sampling table capacity exceeded");
         return bfail(b, RBE_ENONFINITE, "rho(k) or an output is not finite");
     }

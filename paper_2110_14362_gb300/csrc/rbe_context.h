@@ -39,7 +39,8 @@ struct KState {
 struct RhoShape {
     int kf;             // frequencies per thread (1, 2 or 4)
     int ktiles;         // frequency tiles
-    int kthreads;       // threads per block: whole warps
+    int kthreads;       // threads per block: whole warps (ksub sub-streams of kthreads / ksub lanes)
+    int ksub;           // particle sub-streams per block
 };
 
 // Launch plan of the N x K pair kernels (chosen by make_plan in rbe_kspace.cu).
@@ -47,6 +48,7 @@ struct Plan {
     int kf;             // frequencies per thread in the rho pass
     int ktiles;         // frequency tiles in the rho pass (kthreads x kf frequencies each)
     int kthreads;       // threads per rho block: whole warps, <= 256
+    int ksub;           // particle sub-streams per rho block
     int nchunks;        // particle chunks in the rho pass
     int64_t chunk_len;  // particles per chunk
     int ppt;            // particles per thread in the force pass

@@ -28,6 +28,17 @@
 
 namespace rbe {
 
+// Rho-pass planning constants (compile-time): particle sub-streams per block at most, and the
+// fewest particles per chunk.
+#ifndef RBE_RHO_MAXSUB
+#define RBE_RHO_MAXSUB 4
+#endif
+#ifndef RBE_RHO_MINCHUNK
+#define RBE_RHO_MINCHUNK 64
+#endif
+constexpr int kRhoMaxSub = RBE_RHO_MAXSUB;
+constexpr int kRhoMinChunk = RBE_RHO_MINCHUNK;
+
 constexpr int kT = 128;               // threads per block of the FP64 force pass
 constexpr int kForceKT = 256;         // frequencies staged per tile in the FP64 force pass
 
@@ -134,14 +145,14 @@ template <int ACC, int F, bool XYZQ>
 __global__ void __launch_bounds__(F == 1 ? kMaxRhoThreads : kRhoThreadsF, F == 1 ? 6 : 8)
 k_rho_f32(const void* __restrict__ pos, const double* __restrict__ q, int64_t N, const KState* __restrict__ ks,
           const int4* __restrict__ m, int K, int64_t chunk_len, int nchunks, float4* __restrict__ partials,
-          unsigned* __restrict__ status, int c_off)
+          unsigned* __restrict__ status, int c_off, int S)
 {
     rho_f32_tile<ACC, F, XYZQ>((int)blockIdx.x, c_off + (int)blockIdx.y, pos, q, N, ks, m, K, chunk_len, nchunks,
-                               partials, status);
+                               partials, status, S);
 }
 
 using RhoKernel = void (*)(const void*, const double*, int64_t, const KState*, const int4*, int, int64_t, int,
-                           float4*, unsigned*, int);
+                           float4*, unsigned*, int, int);
 
 template <int ACC, bool XYZQ>
 static RhoKernel rho_kernel_f(int F)
@@ -634,8 +645,10 @@ static Plan make_plan(rbe_ctx ctx, int64_t N, int K, const RhoShape& rs, int rho
     p.kf = rs.kf;
     p.ktiles = rs.ktiles;
     p.kthreads = rs.kthreads;
+    p.ksub = rs.ksub;
     const int64_t want = std::max<int64_t>(1, (int64_t)ctx->num_sms * rho_bps / p.ktiles);
-    const int64_t max_chunks = std::max<int64_t>(1, (N + 63) / 64);  // at least 64 particles per chunk
+    // at least one staged tile of particles per chunk (fewer leave the block's fixed costs unpaid)
+    const int64_t max_chunks = std::max<int64_t>(1, (N + kRhoMinChunk - 1) / kRhoMinChunk);
     p.nchunks = (int)std::min<int64_t>(want, max_chunks);
     p.chunk_len = std::max<int64_t>(1, (N + p.nchunks - 1) / p.nchunks);
     p.nchunks = (int)std::max<int64_t>(1, (N + p.chunk_len - 1) / p.chunk_len);
@@ -678,10 +691,12 @@ struct EvalShape {
 // estimate: the pair's own work (base), one broadcast load per kf pairs, the particle
 // conversion spread over the tile's frequencies, divided by the fraction of lanes that hold a
 // frequency.
+// A tile narrower than the block's warps is given particle sub-streams (S = block threads / T,
+// a power of two), so that every block runs kRhoThreadsF threads or more.
 static RhoShape rho_shape(int K, int accum)
 {
     const double base = accum == RBE_RHO_COMP32 ? 12.0 : (accum == RBE_RHO_FP64 ? 14.0 : 10.0);
-    RhoShape best{1, 1, 32};
+    RhoShape best{1, 1, 32, 1};
     double best_cost = 1e30;
     for (int F : {4, 2, 1}) {
         const int tmax = F == 1 ? kMaxRhoThreads : kRhoThreadsF;
@@ -692,7 +707,9 @@ static RhoShape rho_shape(int K, int accum)
         const double cost = (base + 1.0 / F + 55.0 / (T * F)) / eff;
         if (cost < best_cost - 1e-9) {
             best_cost = cost;
-            best = RhoShape{F, ktiles, T};
+            int S = 1;
+            while (T * S * 2 <= kRhoThreadsF && S * 2 <= kRhoMaxSub) S *= 2;
+            best = RhoShape{F, ktiles, T * S, S};
         }
     }
     return best;
@@ -724,6 +741,7 @@ static rbe_status evaluate_shape(rbe_ctx ctx, int64_t N, int K, EvalShape* out)
         rs.kf = 1;
         rs.ktiles = (K + kMaxRhoThreads - 1) / kMaxRhoThreads;
         rs.kthreads = std::min(kMaxRhoThreads, 32 * (((K + rs.ktiles - 1) / rs.ktiles + 31) / 32));
+        rs.ksub = 1;
         rho_bps = std::max(1, std::min(32, rho64_threads / rs.kthreads));
     } else {
         rs = rho_shape(K, ctx->rho_accum);
@@ -776,7 +794,7 @@ static rbe_status launch_evaluate_range(rbe_ctx ctx, int64_t N, const void* pos,
     } else {
         const RhoKernel kern = rho_kernel(ctx->rho_accum, p.kf, xyzq);
         cudaError_t err = launch_pdl(kern, grid, dim3(p.kthreads), 0, s, pos, q, N, ks, m_in, K,
-                                     p.chunk_len, p.nchunks, part32, d.status, 0);
+                                     p.chunk_len, p.nchunks, part32, d.status, 0, p.ksub);
         if (err != cudaSuccess) return cuda_fail(ctx, err, "launch k_rho_f32");
     }
     rbe_status st = check_launch(ctx, "k_rho");
@@ -889,7 +907,7 @@ rbe_status launch_evaluate_staged(rbe_ctx ctx, int64_t N, const double* h_pos, c
         err = launch_pdl(rho_kernel(ctx->rho_accum, pl[g].kf), dim3(pl[g].ktiles, pl[g].nchunks),
                          dim3(pl[g].kthreads), 0, s,
                          (const double*)(d_pos + 3 * a), (const double*)(d_q + a), n, ks, (const int4*)d.m, K,
-                         pl[g].chunk_len, nchunks, part32 + coff[g], d.status, 0);
+                         pl[g].chunk_len, nchunks, part32 + coff[g], d.status, 0, pl[g].ksub);
         if (err != cudaSuccess) return cuda_fail(ctx, err, "staged: k_rho_f32");
     }
     err = launch_pdl(k_reduce_f32, dim3(K + 1), dim3(kReduceThreads), 0, s, (const float4*)part32, nchunks, K,

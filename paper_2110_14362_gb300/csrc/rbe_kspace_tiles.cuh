@@ -11,7 +11,7 @@
 
 namespace rbe {
 
-constexpr int kTableThreads = 1024;   // k_tables block
+constexpr int kTableThreads = 1024;   // k_tables block (tables_body runs with any block of >= 160 threads)
 constexpr int kMaxRhoThreads = 256;   // threads of a rho block with one frequency per thread
 constexpr int kRhoThreadsF = 128;     // threads of a rho block with 2 or 4 frequencies per thread
 constexpr int kReduceThreads = 256;
@@ -57,7 +57,8 @@ __device__ __forceinline__ void tables_body(double bx, double by, double bz, con
 {
     __shared__ int sM[3], sSh[3];
     __shared__ double sc[3], sL[3];
-    __shared__ unsigned long long wsum[kTableThreads / 32];
+    __shared__ unsigned long long wsum[32];
+    const int nthr = blockDim.x;  // a multiple of 32, at least 160 (the box-constant threads)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid < 3) {
         const double ell = box_dev ? box_dev[tid] : (tid == 0 ? bx : (tid == 1 ? by : bz));
@@ -75,7 +76,7 @@ __device__ __forceinline__ void tables_body(double bx, double by, double bz, con
     // entries of the three rows are spread over all threads
     {
         const int n0 = sM[0] + 1, n1 = sM[1] + 1, n2 = sM[2] + 1;
-        for (int e = tid; e < n0 + n1 + n2; e += kTableThreads) {
+        for (int e = tid; e < n0 + n1 + n2; e += nthr) {
             const int t = e < n0 ? 0 : (e < n0 + n1 ? 1 : 2);
             const int a = e - (t == 0 ? 0 : (t == 1 ? n0 : n0 + n1));
             const int M = sM[t];
@@ -91,7 +92,7 @@ __device__ __forceinline__ void tables_body(double bx, double by, double bz, con
     for (int t = 0; t < 3; ++t) {
         const int n = 2 * sM[t] + 1;
         unsigned long long* row = cum + (size_t)t * cap;
-        const int per = (n + kTableThreads - 1) / kTableThreads;
+        const int per = (n + nthr - 1) / nthr;
         const int j0 = min(n, tid * per), j1 = min(n, j0 + per);
         unsigned long long local = 0;
         for (int j = j0; j < j1; ++j) local += row[j];
@@ -104,7 +105,7 @@ __device__ __forceinline__ void tables_body(double bx, double by, double bz, con
         if (lane == 31) wsum[warp] = incl;
         __syncthreads();
         if (warp == 0) {
-            unsigned long long v = wsum[lane];
+            unsigned long long v = lane < (nthr >> 5) ? wsum[lane] : 0ull;
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
                 const unsigned long long o = __shfl_up_sync(0xffffffffu, v, off);
@@ -306,13 +307,15 @@ __device__ __forceinline__ uint4 load_record(const void* __restrict__ pos, const
 }
 
 // =================================================================================
-// rho pass, FP32-phase path.  Block (kt, c) has blockDim.x threads (whole warps) and covers
-// the frequency tile of blockDim.x * F frequencies: thread j owns frequencies
-// kt * blockDim.x * F + f * blockDim.x + j (f < F), and runs over the particles
+// rho pass, FP32-phase path.  Block (kt, c) has blockDim.x = T S threads (whole warps): S
+// particle sub-streams of T frequency lanes.  It covers the frequency tile of T F frequencies:
+// thread j of sub-stream s owns frequencies kt T F + f T + j (f < F), and runs over its
+// contiguous share (kRhoStage / S particles) of every tile of the chunk's particles
 // [c * chunk_len, (c + 1) * chunk_len), staged in shared memory kRhoStage at a time as 32-bit
 // fixed-point (s_x, s_y, s_z) plus q as float and read as broadcasts: one shared-memory load
-// feeds F pairs.  No FP64 instruction runs per particle or per pair: sums across staged tiles
-// are float-float.
+// feeds F pairs.  The sub-streams let a small frequency tile fill a block of several warps;
+// their sums are added in sub-stream order at the end.  No FP64 instruction runs per particle
+// or per pair: sums across staged tiles are float-float.
 // ACC: RBE_RHO_COMP32 (compensated FP32: four-term partial sums added with Kahan's
 //      compensation, an error bound that does not grow with the particle count),
 //      RBE_RHO_FP32 (plain FP32 within a tile), RBE_RHO_FP64 (FP64 per pair; slow on GB300).
@@ -326,59 +329,62 @@ template <int ACC, int F, bool XYZQ = false>
 __device__ __forceinline__ void rho_f32_tile(int kt, int c, const void* __restrict__ pos,
                                              const double* __restrict__ q, int64_t N, const KState* __restrict__ ks,
           const int4* __restrict__ m, int K, int64_t chunk_len, int nchunks, float4* __restrict__ partials,
-          unsigned* __restrict__ status)
+          unsigned* __restrict__ status, int S = 1)
 {
     __shared__ uint4 sp[kRhoStage];
     __shared__ float red[2][32];
     __shared__ unsigned bad;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int lbase = kt * nt * F + tid;
+    const int T = nt / S, j = tid % T, ss = tid / T;  // frequency lane, particle sub-stream
+    const int lbase = kt * T * F + j;
+    const int share = kRhoStage / S, p0 = ss * share;  // the sub-stream's particles of a tile
     const FixScale scx = fs(ks->sc[0]), scy = fs(ks->sc[1]), scz = fs(ks->sc[2]);
     // the float-float sums across staged tiles, (Re hi, Re lo, Im hi, Im lo) per frequency, live
     // in shared memory: they change once per tile, and registers go to the pair loop
     __shared__ float4 acc_s[(F == 1 ? kMaxRhoThreads : kRhoThreadsF) * F];
 #pragma unroll
-    for (int f = 0; f < F; ++f) acc_s[f * nt + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int f = 0; f < F; ++f) acc_s[(ss * F + f) * T + j] = make_float4(0.f, 0.f, 0.f, 0.f);
     float q2h = 0.f, q2l = 0.f;
     const int64_t start = (int64_t)c * chunk_len;
     const int64_t end = min(N, start + chunk_len);
     if (tid == 0) bad = 0u;
     __syncthreads();
     // the first tile is staged before waiting for the sampler (inputs only)
-    for (int j = tid; j < kRhoStage; j += nt) {
-        const int64_t i = start + j;
+    for (int u = tid; u < kRhoStage; u += nt) {
+        const int64_t i = start + u;
         uint4 rec = make_uint4(0u, 0u, 0u, 0u);
         if (i < end) {
             rec = load_record<XYZQ>(pos, q, i, scx, scy, scz, &bad);
             const float qf = __uint_as_float(rec.w);
             ff_add(q2h, q2l, qf * qf);
         }
-        sp[j] = rec;
+        sp[u] = rec;
     }
     pdl_wait();
     pdl_trigger();
     int4 mv[F];
 #pragma unroll
     for (int f = 0; f < F; ++f) {
-        const int l = lbase + f * nt;
+        const int l = lbase + f * T;
         mv[f] = l < K ? m[l] : make_int4(0, 0, 0, 0);
     }
     for (int64_t base = start; base < end; base += kRhoStage) {
         if (base != start) {
             __syncthreads();  // every thread is done with the previous tile
-            for (int j = tid; j < kRhoStage; j += nt) {
-                const int64_t i = base + j;
+            for (int u = tid; u < kRhoStage; u += nt) {
+                const int64_t i = base + u;
                 uint4 rec = make_uint4(0u, 0u, 0u, 0u);
                 if (i < end) {
                     rec = load_record<XYZQ>(pos, q, i, scx, scy, scz, status);
                     const float qf = __uint_as_float(rec.w);
                     ff_add(q2h, q2l, qf * qf);
                 }
-                sp[j] = rec;
+                sp[u] = rec;
             }
         }
         __syncthreads();
-        const int n_here = (int)min((int64_t)kRhoStage, end - base);
+        // this sub-stream's particles of the tile: [p0, p0 + n_here)
+        const int n_here = (int)max((int64_t)0, min((int64_t)share, end - base - p0));
         float re[F], im[F], cre[F], cim[F];
         double are[F], aim[F];
 #pragma unroll
@@ -394,9 +400,8 @@ __device__ __forceinline__ void rho_f32_tile(int kt, int c, const void* __restri
             // four-term partials, 2 eps from the compensated additions).  Records past the end
             // of the chunk are staged as zeros (q = 0), so the last group of four is padded.
             const int n4 = (n_here + 3) & ~3;
-            for (int p = 0; p < n4; p += 4) {
+            for (int p = p0; p < p0 + n4; p += 4) {
                 const uint4 r0 = sp[p], r1 = sp[p + 1], r2 = sp[p + 2], r3 = sp[p + 3];
-#pragma unroll
                 const float2 q0 = make_float2(__uint_as_float(r0.w), __uint_as_float(r0.w));
                 const float2 q1 = make_float2(__uint_as_float(r1.w), __uint_as_float(r1.w));
                 const float2 q2 = make_float2(__uint_as_float(r2.w), __uint_as_float(r2.w));
@@ -427,7 +432,7 @@ __device__ __forceinline__ void rho_f32_tile(int kt, int c, const void* __restri
             }
         } else {
 #pragma unroll 2
-            for (int p = 0; p < n_here; ++p) {
+            for (int p = p0; p < p0 + n_here; ++p) {
                 const uint4 r = sp[p];
                 const float qp = __uint_as_float(r.w);
 #pragma unroll
@@ -447,7 +452,7 @@ __device__ __forceinline__ void rho_f32_tile(int kt, int c, const void* __restri
         }
 #pragma unroll
         for (int f = 0; f < F; ++f) {
-            float4 a = acc_s[f * nt + tid];
+            float4 a = acc_s[(ss * F + f) * T + j];
             if (ACC == RBE_RHO_FP64) {
                 const float ah = (float)are[f], bh = (float)aim[f];
                 ff_add2(a.x, a.y, ah, (float)(are[f] - (double)ah));
@@ -458,14 +463,23 @@ __device__ __forceinline__ void rho_f32_tile(int kt, int c, const void* __restri
                 ff_add(a.z, a.w, im[f]);
                 a.w -= cim[f];
             }
-            acc_s[f * nt + tid] = a;
+            acc_s[(ss * F + f) * T + j] = a;
         }
     }
     if (tid == 0 && bad) atomicOr(status, kStatusNonFinite);  // flagged while staging the first tile
+    if (S > 1) __syncthreads();  // every sub-stream's sums are in shared memory
+    if (ss == 0) {
 #pragma unroll
-    for (int f = 0; f < F; ++f) {
-        const int l = lbase + f * nt;
-        if (l < K) partials[(size_t)l * nchunks + c] = acc_s[f * nt + tid];
+        for (int f = 0; f < F; ++f) {
+            const int l = lbase + f * T;
+            float4 a = acc_s[f * T + j];
+            for (int u = 1; u < S; ++u) {  // sub-streams in order
+                const float4 b = acc_s[(u * F + f) * T + j];
+                ff_add2(a.x, a.y, b.x, b.y);
+                ff_add2(a.z, a.w, b.z, b.w);
+            }
+            if (l < K) partials[(size_t)l * nchunks + c] = a;
+        }
     }
     if (kt == 0) {
         block_sum_ff(q2h, q2l, red);  // sum of q^2 over the chunk, for E_self
@@ -564,6 +578,45 @@ __device__ __forceinline__ void reduce_f32_row(int l, const float4* __restrict__
     if (!isfinite(re) || !isfinite(im)) atomicOr(status, kStatusNonFinite);
 }
 
+// The same reduction of row l by one warp (lane-strided float-float sums over the chunks, then
+// a fixed shuffle tree): the batched kernel runs eight rows per block at a time.  The per-
+// frequency terms and coefficients are the block version's formulas.
+__device__ __forceinline__ void reduce_f32_row_warp(int l, const float4* __restrict__ partials, int nchunks, int K,
+                                                    const int4* __restrict__ m, const double* __restrict__ w,
+                                                    const KState* __restrict__ ks, double2* __restrict__ rho,
+                                                    double* __restrict__ terms, int4* __restrict__ coef_m,
+                                                    float4* __restrict__ coef_f, unsigned* __restrict__ status)
+{
+    const int lane = threadIdx.x & 31;
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    const float4* row = partials + (size_t)l * nchunks;
+    for (int j = lane; j < nchunks; j += 32) {
+        const float4 v = row[j];
+        ff_add2(rh, rl, v.x, v.y);
+        ff_add2(ih, il, v.z, v.w);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float a = __shfl_xor_sync(0xffffffffu, rh, off), b = __shfl_xor_sync(0xffffffffu, rl, off);
+        const float c = __shfl_xor_sync(0xffffffffu, ih, off), d = __shfl_xor_sync(0xffffffffu, il, off);
+        ff_add2(rh, rl, a, b);
+        ff_add2(ih, il, c, d);
+    }
+    if (lane != 0) return;
+    double* t = terms + (size_t)l * 8;
+    const double re = ff_to_double(rh, rl), im = ff_to_double(ih, il);
+    if (l == K) {
+        t[0] = re;  // sum of q^2
+        return;
+    }
+    const int4 mi = m[l];
+    const double wd = w[l];
+    freq_terms_f64(mi, wd, re, im, ks, t);
+    force_coef(mi, wd, re, im, ks, coef_m + l, coef_f + l);
+    rho[l] = make_double2(re, im);
+    if (!isfinite(re) || !isfinite(im)) atomicOr(status, kStatusNonFinite);
+}
+
 // Energy and virial: fixed-order FP64 sums of the per-frequency terms over l, by one block
 // of kForceThreads threads; E_self = -sqrt(alpha/pi) sum q^2 in FP64.
 __device__ __forceinline__ void final_sums(const double* __restrict__ terms, int K, const KState* __restrict__ ks,
@@ -621,7 +674,7 @@ __device__ __forceinline__ void final_sums(const double* __restrict__ terms, int
 //   F_i,theta = q_i (2 pi / l_theta) sum_l R_l m_l,theta sin(theta_il - arg rho_l)
 // (one sine per pair) is formed in FP32 and widened to double exactly.  The launch carries one extra block
 // that computes the energy and virial sums (final_sums_f32) meanwhile.
-template <bool XYZQ = false>
+template <bool XYZQ = false, int LU = kForceLUnroll>
 __device__ __forceinline__ void force_f32_block(int64_t blk, const void* __restrict__ pos,
                                                 const double* __restrict__ q, int64_t N, int64_t per_block,
                                                 const KState* __restrict__ ks, const int4* __restrict__ coef_m,
@@ -677,7 +730,7 @@ __device__ __forceinline__ void force_f32_block(int64_t blk, const void* __restr
 #pragma unroll
                 for (int p = 0; p < kForcePPT; ++p) pr[p] = sp[(r0 + 32 * p + lane) % kForceThreads];
                 const int l0 = (warp * nk) / kForceWarps, l1 = ((warp + 1) * nk) / kForceWarps;
-#pragma unroll kForceLUnroll
+#pragma unroll LU
                 for (int l = l0; l < l1; ++l) {
                     const int4 a = sm[l];
                     const float4 b = sf[l];

@@ -180,3 +180,88 @@ def test_batch_argument_errors():
             b.evaluate(arr)
         b.evaluate(items)  # still usable
         b.sync()
+
+
+def test_persistent_launch_equals_one_launch_per_pass():
+    """The persistent form (one cooperative launch whose resident blocks run the five passes
+    with grid barriers between them) and one launch per pass run the same tile bodies on the same
+    work lists: every output is the same bits."""
+    systems = _systems([5, 1000, 4001, 20000], seed0=31)
+    a = _dev(systems)
+    c = _dev(systems)
+    with rbe.Batch(ALPHA, 100, 4, 100.0) as b:
+        b.set_tiles(128, 512, 512)
+        b.evaluate(a)
+        b.set_persistent(False)
+        b.evaluate(c)
+        b.sync()
+    for x, y in zip(a, c):
+        for u, v in zip(_out(x), _out(y)):
+            assert np.array_equal(u, v)
+
+
+def test_device_resident_box_and_step():
+    """Items whose box and batch index live in device memory (box_dev, step_dev: an NPT
+    replica's cell block) give the bits of items that pass the same values from the host, and a
+    graph captured once follows new device values at replay."""
+    import torch
+    dev = cuda_device()
+    systems = _systems([800, 6000], seed0=41)
+    host_items = _dev(systems)
+    dev_items = _dev(systems)
+    for it in dev_items:
+        it["box_dev"] = torch.as_tensor(np.asarray(it["box"], dtype=np.float64)).to(dev)
+        it["step_dev"] = torch.tensor([it["step"]], dtype=torch.int64, device=dev)
+        it["box"] = [99.0, 99.0, 99.0]  # the host box only bounds the table size check now
+        it["step"] = 7777
+    s = torch.cuda.Stream()
+    with rbe.Batch(ALPHA, 100, 2, 100.0, stream=s.cuda_stream) as b:
+        b.evaluate(host_items)
+        arr = b.items(dev_items)
+        b.evaluate(arr)
+        b.sync()
+        for x, y in zip(host_items, dev_items):
+            for u, v in zip(_out(x), _out(y)):
+                assert np.array_equal(u, v)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+            b.evaluate(arr)
+        # new boxes and indices on the device; the replay reads them
+        new_box = [np.asarray(sy["box"]) * 1.03 for sy in systems]
+        for it, nb in zip(dev_items, new_box):
+            it["box_dev"].copy_(torch.as_tensor(nb))
+            it["step_dev"].add_(5)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        b.sync()
+    for sy, it, nb in zip(systems, dev_items, new_box):
+        moved = dict(sy, box=nb, step=sy["step"] + 5)
+        _check_vs_oracle(*_out(it), _oracle(moved, 100))
+
+
+def test_persistent_barrier_timeout_is_reported_and_recovered():
+    """The failure path of the persistent launch, without a fault: the test hook makes every
+    grid barrier wait for one block more than the grid has, so each wait runs out after its
+    one-second limit, the blocks leave the kernel and rbe_batch_sync reports RBE_ETIMEOUT; with
+    the hook off the next evaluation on the same batch is complete and equals the one before."""
+    import time
+    systems = _systems([900, 5000], seed0=51)
+    ref = _dev(systems)
+    cur = _dev(systems)
+    with rbe.Batch(ALPHA, 100, 2, 100.0) as b:
+        b.evaluate(ref)
+        b.sync()
+        b.test_barrier_timeout(True)
+        t0 = time.monotonic()
+        b.evaluate(cur)
+        with pytest.raises(rbe.RBEError) as e:
+            b.sync()
+        assert e.value.status == rbe.RBE_ETIMEOUT
+        assert time.monotonic() - t0 < 30.0
+        b.test_barrier_timeout(False)
+        b.evaluate(cur)
+        b.sync()
+    for x, y in zip(ref, cur):
+        for u, v in zip(_out(x), _out(y)):
+            assert np.array_equal(u, v)
