@@ -517,6 +517,9 @@ typedef struct {
                                   box[], which then only bounds the table size check */
     const uint64_t* step_dev;  /* NULL, or the item's batch index in device memory (read by every
                                   evaluation instead of step) */
+    uint32_t* status_dev;      /* NULL, or a device word (4-byte aligned) where this item's device
+                                  errors are latched (the bits of a context's status word) instead of
+                                  the batch's own, so that a failing item is told apart */
 } rbe_batch_item;
 
 /* A batch for up to max_items items with boxes no longer than max_box on any axis (sizes the
@@ -587,7 +590,18 @@ typedef struct {
                             rounded up to 32), plus 128 (P + ptilde) + 16 reuse (P + ptilde) for the
                             frequency buffers (the reuse term when reuse > 1) */
     int32_t use_graphs;  /* 1: replay a captured graph per chunk; 0: launch the steps directly */
-    int32_t pad;
+    int32_t batched;     /* 0: every replica runs its own chunks (its own stream and graph).  1: the
+                            resident replicas advance in lockstep chunks; each step's k-space of all
+                            of them is one persistent batched launch (rbe_batch, the tiles autotuned
+                            on the group), their cell updates, drifts, real space and finishing
+                            kernels run on their own streams around it, and a group that stays the
+                            same for a second chunk is captured as one CUDA graph and replayed.
+                            The batch runs its default tile shapes (1), or (2) the shapes
+                            rbe_batch_autotune picks on the first group captured, kept for the
+                            server's life.  FP32-phase only; requests with the exact sampler, no
+                            pressure batch and no sample reuse, the k-space on.  Requests join and
+                            leave at chunk boundaries.  A replica's result depends on its own data
+                            and the tile shapes only, not on the other replicas of its group. */
 } rbe_server_config;
 
 typedef struct {

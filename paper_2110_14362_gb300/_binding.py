@@ -104,13 +104,13 @@ class BatchItem(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("pos", ctypes.c_void_p), ("charge", ctypes.c_void_p),
                 ("forces", ctypes.c_void_p), ("virial", ctypes.c_void_p), ("energy", ctypes.c_void_p),
                 ("box", ctypes.c_double * 3), ("seed", ctypes.c_uint64), ("step", ctypes.c_uint64),
-                ("box_dev", ctypes.c_void_p), ("step_dev", ctypes.c_void_p)]
+                ("box_dev", ctypes.c_void_p), ("step_dev", ctypes.c_void_p), ("status_dev", ctypes.c_void_p)]
 
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("P", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("max_slots", ctypes.c_int32), ("chunk_steps", ctypes.c_int32), ("mem_budget", ctypes.c_int64),
-                ("use_graphs", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("use_graphs", ctypes.c_int32), ("batched", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -590,10 +590,12 @@ class Server:
     done, read results and chunk-latency statistics."""
 
     def __init__(self, alpha, P, precision=RBE_FP32_PHASE, max_slots=32, chunk_steps=10,
-                 mem_budget=8 << 30, use_graphs=True):
+                 mem_budget=8 << 30, use_graphs=True, batched=0):
+        """batched: 0 every replica on its own chunks; 1 lockstep groups with the batched k-space
+        (default tiles); 2 the same with tiles autotuned on the first captured group."""
         cfg = ServerConfig(alpha=float(alpha), P=int(P), precision=int(precision), max_slots=int(max_slots),
                            chunk_steps=int(chunk_steps), mem_budget=int(mem_budget),
-                           use_graphs=int(bool(use_graphs)), pad=0)
+                           use_graphs=int(bool(use_graphs)), batched=int(batched))
         self.h = ctypes.c_void_p()
         lib = load()
         st = lib.rbe_server_create(ctypes.byref(cfg), ctypes.byref(self.h))

@@ -41,6 +41,7 @@ struct BItem {
     double* E;
     const double* box_dev;                // the item's box in device memory (read every evaluation), or NULL
     const unsigned long long* step_dev;   // the item's batch index in device memory, or NULL: `step`
+    unsigned* status;                     // where the item's device errors are latched
     int64_t N;
     uint64_t seed, step;
     int64_t chunk_len, per_block;
@@ -161,7 +162,7 @@ __device__ __forceinline__ void pass_tables(const BArgs& a)
         const int r = a.which[w];
         const double* b = a.boxes + 3 * (size_t)r;
         tables_body(b[0], b[1], b[2], a.items[r].box_dev, a.alpha, a.P, a.cum + (size_t)r * 3 * a.cap, a.cap, a.ks + r,
-                    a.status);
+                    a.items[r].status);
         __syncthreads();
     }
 }
@@ -172,7 +173,7 @@ __device__ __forceinline__ void pass_sample(const BArgs& a)
         const int r = u / a.bpi, lb = (u % a.bpi) * kSampleBlock;
         const BItem& it = a.items[r];
         sample_body(lb, it.seed, it.step, it.step_dev, a.P, a.P, a.cum + (size_t)r * 3 * a.cap, a.cap, a.smem_cap,
-                    a.ks + r, a.m + (size_t)r * a.P, a.w + (size_t)r * a.P, a.status);
+                    a.ks + r, a.m + (size_t)r * a.P, a.w + (size_t)r * a.P, it.status);
         __syncthreads();
     }
 }
@@ -183,7 +184,7 @@ __device__ __forceinline__ void pass_rho(const BArgs& a)
         const int4 tl = a.rtiles[t];
         const BItem& it = a.items[tl.x];
         rho_f32_tile<RBE_RHO_COMP32, 1>(tl.y, tl.z, it.pos, it.q, it.N, a.ks + tl.x, a.m + (size_t)tl.x * a.P, a.P,
-                                        it.chunk_len, it.nchunks, a.part + it.part_off, a.status, a.S);
+                                        it.chunk_len, it.nchunks, a.part + it.part_off, it.status, a.S);
         __syncthreads();
     }
 }
@@ -197,7 +198,7 @@ __device__ __forceinline__ void pass_reduce(const BArgs& a)
         const BItem& it = a.items[r];
         const size_t o = (size_t)r * a.P;
         reduce_f32_row_warp(l, a.part + it.part_off, it.nchunks, a.P, a.m + o, a.w + o, a.ks + r, a.rho + o,
-                            a.terms + (size_t)r * (a.P + 1) * 8, a.coef_m + o, a.coef_f + o, a.status);
+                            a.terms + (size_t)r * (a.P + 1) * 8, a.coef_m + o, a.coef_f + o, it.status);
     }
 }
 
@@ -211,11 +212,11 @@ __device__ __forceinline__ void pass_force(const BArgs& a)
             const BItem& it = a.items[tl.x];
             const size_t o = (size_t)tl.x * a.P;
             force_f32_block<false, kBatchForceUnroll>((int64_t)tl.y, it.pos, it.q, it.N, it.per_block, a.ks + tl.x, a.coef_m + o,
-                                   a.coef_f + o, a.P, it.F, a.status);
+                                   a.coef_f + o, a.P, it.F, it.status);
         } else {
             const int r = t - a.nft;
             const BItem& it = a.items[r];
-            final_sums(a.terms + (size_t)r * (a.P + 1) * 8, a.P, a.ks + r, it.W, it.E, a.status);
+            final_sums(a.terms + (size_t)r * (a.P + 1) * 8, a.P, a.ks + r, it.W, it.E, it.status);
         }
         __syncthreads();
     }
@@ -404,8 +405,9 @@ rbe_status validate_items(rbe_batch b, const rbe_batch_item* items, int n)
             if (2 * host_axis_M(b->alpha, l) + 1 > b->cap)
                 return bfail(b, RBE_EINVAL, "item box beyond the batch's table capacity (rbe_batch_create max_box)");
         }
-        if ((reinterpret_cast<uintptr_t>(it.box_dev) | reinterpret_cast<uintptr_t>(it.step_dev)) % 8)
-            return bfail(b, RBE_EINVAL, "item box_dev and step_dev must be 8-byte aligned");
+        if ((reinterpret_cast<uintptr_t>(it.box_dev) | reinterpret_cast<uintptr_t>(it.step_dev)) % 8 ||
+            reinterpret_cast<uintptr_t>(it.status_dev) % 4)
+            return bfail(b, RBE_EINVAL, "item box_dev and step_dev must be 8-byte, status_dev 4-byte aligned");
     }
     return RBE_OK;
 }
@@ -472,6 +474,7 @@ rbe_status plan(rbe_batch b, const rbe_batch_item* items, int n)
         it.step = items[r].step;
         it.box_dev = items[r].box_dev;
         it.step_dev = reinterpret_cast<const unsigned long long*>(items[r].step_dev);
+        it.status = items[r].status_dev ? reinterpret_cast<unsigned*>(items[r].status_dev) : b->d_status;
     }
     return RBE_OK;
 }

@@ -194,6 +194,11 @@ rbe_status launch_sample_device_box(rbe_ctx ctx, uint64_t step, int P, const uns
 rbe_status launch_tables_sample_device(rbe_ctx ctx, int P, const double* box_dev, const unsigned long long* step_dev);
 rbe_status npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch);
 rbe_status npt_run(rbe_ctx ctx, rbe_system* sys, int32_t nsteps);
+// One NPT step in phases, for a caller that evaluates the step's k-space itself into npt.Fk
+// and npt.WEk (between kNptPhaseMove and kNptPhaseFinish; the real space may run beside it):
+// the cell update and drift; the real space; the finishing kernel, which advances the step.
+constexpr int kNptPhaseMove = 0, kNptPhaseReal = 1, kNptPhaseFinish = 2;
+rbe_status npt_step_phase(rbe_ctx ctx, rbe_system* sys, int phase);
 // Shared with the flexible-cell step (rbe_npt.cu): scratch for N particles and cells of edges up
 // to twice `box` (plus a list with skin > 0), the pair kernel's grid, the cell list of the
 // constants in npt.cellc (nls: the neighbour-list state or NULL).

@@ -1345,8 +1345,10 @@ rbe_status launch_cell_list(rbe_ctx ctx, int64_t N, const double* pos, const dou
 }
 
 // Forces, virial and energies at the current state (k-space batch `batch`), then the
-// finishing kernel (with or without the R^p/2 and V^p/2 of the step's end).
-static rbe_status npt_forces(rbe_ctx ctx, rbe_system* sys, uint64_t batch, int do_kick)
+// finishing kernel (with or without the R^p/2 and V^p/2 of the step's end).  `parts` selects
+// the k-space (1), the real space (2) and the finishing kernel (4): a caller that evaluates
+// the k-space itself (into npt.Fk and npt.WEk) runs 2 and 4 only.
+static rbe_status npt_forces(rbe_ctx ctx, rbe_system* sys, uint64_t batch, int do_kick, int parts = 7)
 {
     NptBuffers& b = ctx->npt;
     const rbe_npt_params& prm = sys->params;
@@ -1355,7 +1357,7 @@ static rbe_status npt_forces(rbe_ctx ctx, rbe_system* sys, uint64_t batch, int d
     const int nb = (int)((N + kNptThreads - 1) / kNptThreads);
     const int nbp = pair_blocks(ctx, N, ctx->precision == RBE_FP64);
     rbe_status st;
-    if (prm.kspace) {
+    if (prm.kspace && (parts & 1)) {
         // tables from the device box and the sampler (one launch), then the evaluation
         (void)batch;  // the batch index is the device-resident step index (set by the caller)
         if ((st = launch_tables_sample_device(ctx, ctx->P, sys->cell,
@@ -1366,7 +1368,7 @@ static rbe_status npt_forces(rbe_ctx ctx, rbe_system* sys, uint64_t batch, int d
         if ((st = launch_rbe(ctx, N, sys->pos, sys->charge, ctx->P, b.Fk, b.WEk, b.WEk + 9)) != RBE_OK)
             return st;
     }
-    if (prm.real && N > 0) {
+    if (prm.real && N > 0 && (parts & 2)) {
         const bool fp64 = ctx->precision == RBE_FP64;
         if (fp64 && b.n64 < N) return fail(ctx, RBE_ESTATE, "precision changed to FP64 after rbe_npt_init: call it again");
         const bool list = prm.skin > 0.0;
@@ -1417,6 +1419,7 @@ static rbe_status npt_forces(rbe_ctx ctx, rbe_system* sys, uint64_t batch, int d
         }
         if ((st = npt_check(ctx, "real-space kernels")) != RBE_OK) return st;
     }
+    if (!(parts & 4)) return RBE_OK;
     if (prm.barostat >= 2)
         k_npt_finish<true><<<std::max(1, nb), kNptThreads, 0, s>>>(
             N, sys->mom, sys->force, b.mprop, b.Fk, b.Fr, b.WEk, reinterpret_cast<const NptCoef*>(b.coef), b.partials,
@@ -1526,39 +1529,56 @@ rbe_status npt_init(rbe_ctx ctx, rbe_system* sys, uint64_t batch)
     return npt_check(ctx, "k_npt_set_step");
 }
 
+// The first part of a step: the cell update (V^p/2, V/2, O^p, V/2) and the particles' drift
+// (R^p/2, R/2, O, R/2).
+static rbe_status npt_move(rbe_ctx ctx, rbe_system* sys)
+{
+    cudaStream_t s = ctx->stream;
+    const int64_t N = sys->N;
+    const int nb = (int)((N + kNptThreads - 1) / kNptThreads);
+    NptCoef* cf = reinterpret_cast<NptCoef*>(ctx->npt.coef);
+    const NptBuffers& b = ctx->npt;
+    if (sys->params.barostat >= 2)
+        k_npt_cell_rect<<<1, kRectWarps * 32, 0, s>>>(sys->cell, cf, sys->params, ctx->seed, b.cellcap,
+                                                      static_cast<CellConsts*>(b.cellc));
+    else
+        k_npt_cell_a<<<1, kCellWarps * 32, 0, s>>>(sys->cell, cf, sys->params, ctx->seed, b.cellcap,
+                                                   static_cast<CellConsts*>(b.cellc));
+    const bool rect = sys->params.barostat >= 2;
+    auto drift = [&](auto f32_tag, auto rect_tag) {
+        k_npt_drift<decltype(f32_tag)::value, decltype(rect_tag)::value><<<nb, kNptThreads, 0, s>>>(
+            N, sys->pos, sys->mom, sys->force, b.mprop, cf, ctx->seed, sys->cell);
+    };
+    using T = std::true_type;
+    using F = std::false_type;
+    if (ctx->precision == RBE_FP64) rect ? drift(F{}, T{}) : drift(F{}, F{});
+    else rect ? drift(T{}, T{}) : drift(T{}, F{});
+    return npt_check(ctx, "k_npt_cell_a/k_npt_drift");
+}
+
 rbe_status npt_run(rbe_ctx ctx, rbe_system* sys, int32_t nsteps)
 {
     if (nsteps < 1) return fail(ctx, RBE_EINVAL, "nsteps must be >= 1");
     rbe_status st = npt_validate(ctx, sys);
     if (st != RBE_OK) return st;
     if (ctx->npt_ready_N != sys->N) return fail(ctx, RBE_ESTATE, "call rbe_npt_init for this system first");
-    cudaStream_t s = ctx->stream;
-    const int64_t N = sys->N;
-    const int nb = (int)((N + kNptThreads - 1) / kNptThreads);
-    NptCoef* cf = reinterpret_cast<NptCoef*>(ctx->npt.coef);
-    const NptBuffers& b = ctx->npt;
     for (int32_t k = 0; k < nsteps; ++k) {
         const uint64_t step = sys->step;
-        if (sys->params.barostat >= 2)
-            k_npt_cell_rect<<<1, kRectWarps * 32, 0, s>>>(sys->cell, cf, sys->params, ctx->seed, b.cellcap,
-                                                          static_cast<CellConsts*>(b.cellc));
-        else
-            k_npt_cell_a<<<1, kCellWarps * 32, 0, s>>>(sys->cell, cf, sys->params, ctx->seed, b.cellcap,
-                                                       static_cast<CellConsts*>(b.cellc));
-        const bool rect = sys->params.barostat >= 2;
-        auto drift = [&](auto f32_tag, auto rect_tag) {
-            k_npt_drift<decltype(f32_tag)::value, decltype(rect_tag)::value><<<nb, kNptThreads, 0, s>>>(
-                N, sys->pos, sys->mom, sys->force, b.mprop, cf, ctx->seed, sys->cell);
-        };
-        using T = std::true_type;
-        using F = std::false_type;
-        if (ctx->precision == RBE_FP64) rect ? drift(F{}, T{}) : drift(F{}, F{});
-        else rect ? drift(T{}, T{}) : drift(T{}, F{});
-        if ((st = npt_check(ctx, "k_npt_cell_a/k_npt_drift")) != RBE_OK) return st;
+        if ((st = npt_move(ctx, sys)) != RBE_OK) return st;
         if ((st = npt_forces(ctx, sys, step, 1)) != RBE_OK) return st;
         sys->step = step + 1;
     }
     return RBE_OK;
+}
+
+rbe_status npt_step_phase(rbe_ctx ctx, rbe_system* sys, int phase)
+{
+    if (ctx->npt_ready_N != sys->N) return fail(ctx, RBE_ESTATE, "call rbe_npt_init for this system first");
+    if (phase == kNptPhaseMove) return npt_move(ctx, sys);
+    if (phase == kNptPhaseReal) return npt_forces(ctx, sys, sys->step, 1, 2);
+    rbe_status st = npt_forces(ctx, sys, sys->step, 1, 4);
+    if (st == RBE_OK) sys->step += 1;
+    return st;
 }
 
 }  // namespace rbe

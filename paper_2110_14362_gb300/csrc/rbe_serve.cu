@@ -77,6 +77,21 @@ struct rbe_server_s {
     double t_first_admit = -1.0, t_last_done = 0.0;
     std::string last_error;
     int device = 0;
+    // lockstep groups (cfg.batched): the group's stream, the batched k-space, the chunk in flight
+    rbe_batch batch = nullptr;
+    double batch_box = 0.0;             // the batch's max_box
+    bool tuned = false;                 // cfg.batched == 2: tiles chosen (once)
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gfork = nullptr, gk = nullptr, gdone = nullptr;
+    std::vector<cudaEvent_t> ev_a, ev_b;  // per slot: after its move, after its finish
+    std::vector<int> members;           // slots of the chunk in flight (slot order)
+    std::vector<rbe_batch_item> items;
+    bool group_in_flight = false;
+    int32_t group_steps = 0;
+    double group_t_launch = 0.0;
+    std::vector<int64_t> last_key, graph_key;  // request ids of the last group and of the captured one
+    cudaGraphExec_t ggraph = nullptr;
+    int32_t ggraph_steps = 0;
 };
 
 namespace rbe {
@@ -204,7 +219,7 @@ static rbe_status admit(rbe_server_s* s, Slot& sl, int64_t id)
         sl.graph = nullptr;
     }
     sl.graph_steps = 0;
-    if (s->cfg.use_graphs && rq.r.nsteps >= s->cfg.chunk_steps) {
+    if (s->cfg.use_graphs && !s->cfg.batched && rq.r.nsteps >= s->cfg.chunk_steps) {
         // one chunk of launches, captured; the device step index makes it replayable
         cudaGraph_t g = nullptr;
         rbe_system probe = sl.sys;
@@ -299,6 +314,180 @@ static void evict(rbe_server_s* s, Slot& sl, int state, rbe_status st, const std
     release_slot(s, sl);
 }
 
+// ---------------------------------------------------------------------------------
+// Lockstep groups (cfg.batched): every resident replica advances by the same chunk; per step
+// the group stream forks to the replicas' streams (cell update and drift), joins them for one
+// persistent batched k-space launch over the group (each item reads its box and step index
+// from its replica's cell block and writes into its context's k-space buffers and status
+// word), and the replicas run their real space beside it and their finishing kernels after it.
+
+static rbe_status ensure_group_batch(rbe_server_s* s, int m)
+{
+    double need = 0.0;
+    for (int k : s->members) {
+        const Request& rq = *s->reqs[s->slots[k].req];
+        for (int t = 0; t < 3; ++t) need = std::max(need, 2.05 * rq.r.box[t]);  // the NPT range: twice the box
+    }
+    if (s->batch && need <= s->batch_box && m <= s->cfg.max_slots) return RBE_OK;
+    int32_t tk = 0, tc = 0, tf = 0;
+    if (s->batch) {
+        rbe_batch_get_tiles(s->batch, &tk, &tc, &tf);
+        rbe_batch_destroy(s->batch);
+        s->batch = nullptr;
+    }
+    need = std::max(need, 2.0 * s->batch_box);  // grow geometrically
+    rbe_status st = rbe_batch_create(s->cfg.alpha, s->cfg.P, s->cfg.max_slots, need, &s->batch);
+    if (st != RBE_OK) return sfail(s, st, std::string("group batch: ") + rbe_last_error(nullptr));
+    s->batch_box = need;
+    if ((st = rbe_batch_set_stream(s->batch, s->gstream)) != RBE_OK) return sfail(s, st, "group batch stream");
+    if (tk) rbe_batch_set_tiles(s->batch, tk, tc, tf);  // keep the tuned shapes
+    if (s->ggraph) {
+        cudaGraphExecDestroy(s->ggraph);  // it launched the old batch
+        s->ggraph = nullptr;
+        s->graph_key.clear();
+    }
+    return RBE_OK;
+}
+
+// The launches of `n` lockstep steps of the members (captured or direct).
+static rbe_status enqueue_group_steps(rbe_server_s* s, int32_t n)
+{
+    const int m = (int)s->members.size();
+    cudaError_t e = cudaSuccess;
+    rbe_status st = RBE_OK;
+    for (int32_t k = 0; k < n; ++k) {
+        if ((e = cudaEventRecord(s->gfork, s->gstream)) != cudaSuccess) break;
+        for (int j = 0; j < m && e == cudaSuccess; ++j) {
+            Slot& sl = s->slots[s->members[j]];
+            if ((e = cudaStreamWaitEvent(sl.stream, s->gfork, 0)) != cudaSuccess) break;
+            if ((st = npt_step_phase(sl.ctx, &sl.sys, kNptPhaseMove)) != RBE_OK) return sfail(s, st, rbe_last_error(sl.ctx));
+            if ((e = cudaEventRecord(s->ev_a[s->members[j]], sl.stream)) != cudaSuccess) break;
+        }
+        for (int j = 0; j < m && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(s->gstream, s->ev_a[s->members[j]], 0);
+        if (e != cudaSuccess) break;
+        if ((st = rbe_kspace_forces_virial_batched(s->batch, s->items.data(), m)) != RBE_OK)
+            return sfail(s, st, std::string("group k-space: ") + rbe_batch_last_error(s->batch));
+        if ((e = cudaEventRecord(s->gk, s->gstream)) != cudaSuccess) break;
+        for (int j = 0; j < m && e == cudaSuccess; ++j) {
+            Slot& sl = s->slots[s->members[j]];
+            if ((st = npt_step_phase(sl.ctx, &sl.sys, kNptPhaseReal)) != RBE_OK) return sfail(s, st, rbe_last_error(sl.ctx));
+            if ((e = cudaStreamWaitEvent(sl.stream, s->gk, 0)) != cudaSuccess) break;
+            if ((st = npt_step_phase(sl.ctx, &sl.sys, kNptPhaseFinish)) != RBE_OK)
+                return sfail(s, st, rbe_last_error(sl.ctx));
+            e = cudaEventRecord(s->ev_b[s->members[j]], sl.stream);
+        }
+        for (int j = 0; j < m && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(s->gstream, s->ev_b[s->members[j]], 0);
+        if (e != cudaSuccess) break;
+    }
+    if (e != cudaSuccess) return sfail(s, RBE_ECUDA, std::string("group chunk: ") + cudaGetErrorString(e));
+    return RBE_OK;
+}
+
+// Launch the next lockstep chunk of every resident replica: replayed from the group's graph
+// when the group is the one captured, captured when the same group comes a second time,
+// launched directly otherwise.
+static rbe_status launch_group_chunk(rbe_server_s* s)
+{
+    s->members.clear();
+    std::vector<int64_t> key;
+    int32_t n = s->cfg.chunk_steps;
+    for (int k = 0; k < (int)s->slots.size(); ++k)
+        if (s->slots[k].busy && s->slots[k].steps_left > 0) {
+            s->members.push_back(k);
+            key.push_back(s->slots[k].req);
+            n = std::min(n, s->slots[k].steps_left);
+        }
+    const int m = (int)s->members.size();
+    if (m == 0) return RBE_OK;
+    rbe_status st = ensure_group_batch(s, m);
+    if (st != RBE_OK) return st;
+    s->items.assign(m, rbe_batch_item{});
+    for (int j = 0; j < m; ++j) {
+        Slot& sl = s->slots[s->members[j]];
+        const Request& rq = *s->reqs[sl.req];
+        rbe_batch_item& it = s->items[j];
+        it.N = rq.r.N;
+        it.pos = sl.pos;
+        it.charge = sl.charge;
+        it.forces = sl.ctx->npt.Fk;
+        it.virial = sl.ctx->npt.WEk;
+        it.energy = sl.ctx->npt.WEk + 9;
+        for (int t = 0; t < 3; ++t) it.box[t] = rq.r.box[t];
+        it.seed = rq.r.seed;
+        it.step = 0;
+        it.box_dev = sl.cell;
+        it.step_dev = reinterpret_cast<const uint64_t*>(sl.cell + 11);
+        it.status_dev = sl.ctx->d.status;
+    }
+    cudaError_t e = cudaSuccess;
+    const bool replay = s->cfg.use_graphs && s->ggraph && key == s->graph_key && n == s->ggraph_steps;
+    if (!replay && s->ggraph) {
+        // the captured graph reads the batch's descriptors as they were at capture: once another
+        // group has run, it may not be replayed
+        cudaGraphExecDestroy(s->ggraph);
+        s->ggraph = nullptr;
+        s->graph_key.clear();
+    }
+    if (replay) {
+        if ((e = cudaGraphLaunch(s->ggraph, s->gstream)) != cudaSuccess)
+            return sfail(s, RBE_ECUDA, std::string("group graph launch: ") + cudaGetErrorString(e));
+        for (int k : s->members) s->slots[k].sys.step += (uint64_t)n;
+    } else if (s->cfg.use_graphs && key == s->last_key && n == s->cfg.chunk_steps) {
+        if (s->cfg.batched == 2 && !s->tuned) {
+            // the tile shapes of the group, once; the items' k-space buffers are scratch between steps
+            if ((st = rbe_batch_autotune(s->batch, s->items.data(), m, 2, nullptr)) != RBE_OK)
+                return sfail(s, st, std::string("group autotune: ") + rbe_batch_last_error(s->batch));
+            s->tuned = true;
+        }
+        // the batch plans its work lists outside capture: one direct chunk of these items first
+        // has done that (the same group ran the chunk before)
+        std::vector<rbe_system> saved;
+        for (int k : s->members) saved.push_back(s->slots[k].sys);
+        cudaGraph_t g = nullptr;
+        if ((e = cudaStreamBeginCapture(s->gstream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return sfail(s, RBE_ECUDA, std::string("group capture: ") + cudaGetErrorString(e));
+        st = enqueue_group_steps(s, n);
+        e = cudaStreamEndCapture(s->gstream, &g);
+        for (int j = 0; j < m; ++j) s->slots[s->members[j]].sys = saved[j];  // the capture ran nothing
+        if (st != RBE_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&s->ggraph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e == cudaSuccess) e = cudaGraphLaunch(s->ggraph, s->gstream);
+        if (e != cudaSuccess) return sfail(s, RBE_ECUDA, std::string("group graph: ") + cudaGetErrorString(e));
+        s->graph_key = key;
+        s->ggraph_steps = n;
+        for (int k : s->members) s->slots[k].sys.step += (uint64_t)n;
+    } else {
+        if ((st = enqueue_group_steps(s, n)) != RBE_OK) return st;
+    }
+    s->last_key = key;
+    // every member's latched device errors, read once the chunk is complete
+    for (int k : s->members) {
+        Slot& sl = s->slots[k];
+        if ((e = cudaMemcpyAsync(sl.h_status, sl.ctx->d.status, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                 s->gstream)) != cudaSuccess)
+            return sfail(s, RBE_ECUDA, std::string("group status: ") + cudaGetErrorString(e));
+        sl.in_flight = true;
+        sl.chunk_in_flight = n;
+    }
+    if ((e = cudaEventRecord(s->gdone, s->gstream)) != cudaSuccess)
+        return sfail(s, RBE_ECUDA, std::string("group event: ") + cudaGetErrorString(e));
+    s->group_in_flight = true;
+    s->group_steps = n;
+    s->group_t_launch = now_s(s);
+    return RBE_OK;
+}
+
+// Whether a request can run in a lockstep group (the batched k-space samples exactly, without a
+// pressure batch or reuse, on the FP32-phase path).
+static bool group_eligible(const rbe_request& r)
+{
+    return r.sampler == RBE_SAMPLER_EXACT && r.ptilde == 0 && r.reuse <= 1 && r.params.kspace == 1;
+}
+
 }  // namespace rbe
 
 using namespace rbe;
@@ -310,14 +499,32 @@ rbe_status rbe_server_create(const rbe_server_config* cfg, rbe_server* out)
     if (!cfg || !out) return fail(nullptr, RBE_EINVAL, "cfg and out must not be NULL");
     if (!(cfg->alpha > 0.0) || cfg->P < 1 || cfg->P > 65536 || cfg->max_slots < 1 || cfg->max_slots > 4096 ||
         cfg->chunk_steps < 1 || cfg->mem_budget <= 0 ||
-        (cfg->precision != RBE_FP64 && cfg->precision != RBE_FP32_PHASE))
+        (cfg->precision != RBE_FP64 && cfg->precision != RBE_FP32_PHASE) || cfg->batched < 0 || cfg->batched > 2)
         return fail(nullptr, RBE_EINVAL, "invalid server configuration");
+    if (cfg->batched && cfg->precision != RBE_FP32_PHASE)
+        return fail(nullptr, RBE_EINVAL, "lockstep groups run the batched FP32-phase k-space: precision RBE_FP32_PHASE");
     rbe_server s = new (std::nothrow) rbe_server_s();
     if (!s) return fail(nullptr, RBE_ENOMEM, "host allocation failed");
     s->cfg = *cfg;
     s->slots.resize(cfg->max_slots);
     s->t0 = Clock::now();
     cudaGetDevice(&s->device);
+    if (cfg->batched) {
+        cudaError_t e = cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->gfork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->gk, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->gdone, cudaEventDisableTiming);
+        s->ev_a.assign(cfg->max_slots, nullptr);
+        s->ev_b.assign(cfg->max_slots, nullptr);
+        for (int k = 0; k < cfg->max_slots && e == cudaSuccess; ++k) {
+            e = cudaEventCreateWithFlags(&s->ev_a[k], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_b[k], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) {
+            rbe_server_destroy(s);
+            return fail(nullptr, RBE_ECUDA, std::string("server group stream: ") + cudaGetErrorString(e));
+        }
+    }
     *out = s;
     return RBE_OK;
 }
@@ -328,6 +535,15 @@ rbe_status rbe_server_destroy(rbe_server s)
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != s->device) cudaSetDevice(s->device);
+    if (s->gstream) cudaStreamSynchronize(s->gstream);
+    if (s->ggraph) cudaGraphExecDestroy(s->ggraph);
+    if (s->batch) rbe_batch_destroy(s->batch);
+    for (cudaEvent_t ev : {s->gfork, s->gk, s->gdone})
+        if (ev) cudaEventDestroy(ev);
+    for (auto* v : {&s->ev_a, &s->ev_b})
+        for (cudaEvent_t ev : *v)
+            if (ev) cudaEventDestroy(ev);
+    if (s->gstream) cudaStreamDestroy(s->gstream);
     for (Slot& sl : s->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
         if (sl.graph) cudaGraphExecDestroy(sl.graph);
@@ -358,6 +574,9 @@ rbe_status rbe_server_submit(rbe_server s, const rbe_request* req, int64_t* id)
         return sfail(s, RBE_EINVAL, "invalid sampler, pressure batch or reuse");
     if (req->sampler == 2 && req->reuse > 1)
         return sfail(s, RBE_EINVAL, "sample reuse and the Metropolis-Hastings chain exclude each other");
+    if (s->cfg.batched && !group_eligible(*req))
+        return sfail(s, RBE_EINVAL, "lockstep groups serve requests with the exact sampler, no pressure batch, no "
+                                    "sample reuse and the k-space on");
     if (replica_bytes(*req, s->cfg.P) > s->cfg.mem_budget)
         return sfail(s, RBE_ENOMEM, "request larger than the whole memory budget");
     auto rq = std::make_unique<Request>();
@@ -385,9 +604,35 @@ rbe_status rbe_server_progress(rbe_server s, int32_t wait, int32_t* n_queued, in
     if (cur != s->device) cudaSetDevice(s->device);
     bool any_done = false;
     for (;;) {
-        // 1. observe finished chunks
+        // 1. observe finished chunks (a lockstep group's chunk completes for all members at once)
+        if (s->cfg.batched && s->group_in_flight) {
+            const cudaError_t q = cudaEventQuery(s->gdone);
+            if (q != cudaErrorNotReady) {
+                if (q != cudaSuccess) return sfail(s, RBE_ECUDA, std::string("cudaEventQuery: ") + cudaGetErrorString(q));
+                const double now = now_s(s);
+                s->group_in_flight = false;
+                any_done = true;
+                for (int k : s->members) {
+                    Slot& sl = s->slots[k];
+                    s->latencies.push_back(now - s->group_t_launch);
+                    sl.in_flight = false;
+                    sl.steps_left -= sl.chunk_in_flight;
+                    s->steps_done += sl.chunk_in_flight;
+                    const unsigned bits = *sl.h_status;
+                    if (bits) {
+                        const rbe_status st = status_from_bits(sl.ctx, bits);
+                        evict(s, sl, 3, st, std::string("evicted after step ") + std::to_string(sl.sys.step) + ": " +
+                                                rbe_last_error(sl.ctx));
+                    } else if (sl.cancel) {
+                        evict(s, sl, 4, RBE_ESTATE, "request cancelled");
+                    } else if (sl.steps_left <= 0) {
+                        retire(s, sl);
+                    }
+                }
+            }
+        }
         for (Slot& sl : s->slots) {
-            if (!sl.busy || !sl.in_flight) continue;
+            if (s->cfg.batched || !sl.busy || !sl.in_flight) continue;
             const cudaError_t q = cudaEventQuery(sl.done);
             if (q == cudaErrorNotReady) continue;
             if (q != cudaSuccess) return sfail(s, RBE_ECUDA, std::string("cudaEventQuery: ") + cudaGetErrorString(q));
@@ -407,8 +652,9 @@ rbe_status rbe_server_progress(rbe_server s, int32_t wait, int32_t* n_queued, in
                 retire(s, sl);
             }
         }
-        // 2. admit while a slot is free and the budget allows (first come, first served)
-        while (!s->queue.empty()) {
+        // 2. admit while a slot is free and the budget allows (first come, first served); lockstep
+        //    groups admit between chunks
+        while (!s->queue.empty() && !(s->cfg.batched && s->group_in_flight)) {
             const int64_t id = s->queue.front();
             const int64_t need = replica_bytes(s->reqs[id]->r, s->cfg.P);
             if (s->mem_used + need > s->cfg.mem_budget) break;
@@ -429,12 +675,19 @@ rbe_status rbe_server_progress(rbe_server s, int32_t wait, int32_t* n_queued, in
                 return st;
             }
         }
-        // 3. next chunk of every resident replica that is idle
-        for (Slot& sl : s->slots)
-            if (sl.busy && !sl.in_flight && sl.steps_left > 0) {
-                const rbe_status st = launch_chunk(s, sl);
+        // 3. next chunk of every resident replica that is idle (lockstep: of the whole group)
+        if (s->cfg.batched) {
+            if (!s->group_in_flight) {
+                const rbe_status st = launch_group_chunk(s);
                 if (st != RBE_OK) return st;
             }
+        } else {
+            for (Slot& sl : s->slots)
+                if (sl.busy && !sl.in_flight && sl.steps_left > 0) {
+                    const rbe_status st = launch_chunk(s, sl);
+                    if (st != RBE_OK) return st;
+                }
+        }
         bool active = false;
         for (const Slot& sl : s->slots) active = active || sl.busy;
         if (!wait || any_done || (!active && s->queue.empty())) break;

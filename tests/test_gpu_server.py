@@ -288,3 +288,78 @@ def test_cancel_queued_and_resident_requests():
         _same(srv.result(d), _direct(REQS[2], precision))
     finally:
         srv.close()
+
+
+def _serve_lockstep(idx, max_slots, chunk_steps=4, nan_in=None, batched=1):
+    """Run requests REQS[idx] through a server of lockstep groups (the batched k-space); returns
+    {i: result or the RBEError}, the chunk count and the steps done."""
+    cuda_device()
+    srv = rbe.Server(ALPHA, P, rbe.RBE_FP32_PHASE, max_slots=max_slots, chunk_steps=chunk_steps,
+                     mem_budget=8 << 30, batched=batched)
+    try:
+        ids = {}
+        for i in idx:
+            n_side, sseed, pseed, nsteps = REQS[i]
+            pos, mom, q, m, box = _system(n_side, sseed)
+            if i == nan_in:
+                pos = pos.copy()
+                pos[3, 0] = np.nan
+            ids[i] = srv.submit(pos, mom, q, m, box, _dev_params(box), pseed, nsteps)
+        _run_until_done(srv, len(ids), time.monotonic() + DEADLINE_S)
+        out = {}
+        for i, rid in ids.items():
+            try:
+                out[i] = srv.result(rid)
+            except rbe.RBEError as e:
+                out[i] = e
+        lat, steps, _ = srv.stats()
+        return out, len(lat), steps
+    finally:
+        srv.close()
+
+
+def test_lockstep_group_alone_equals_in_the_group():
+    """Lockstep serving (every step's k-space of the resident replicas in one persistent
+    batched launch, the group captured as one CUDA graph once it is stable): each replica ends
+    bit for bit as when it is served alone, whatever the other members and the chunking they
+    impose; the steps are all done."""
+    mix, nchunks, steps = _serve_lockstep([0, 1, 2, 3], max_slots=4)
+    assert steps == sum(r[3] for r in REQS)
+    for i in range(4):
+        alone, _, _ = _serve_lockstep([i], max_slots=1)
+        _same(mix[i], alone[i])
+
+
+def test_lockstep_close_to_direct_steps():
+    """The batched k-space tiles its sums differently from the single-system path, so a
+    lockstep-served trajectory agrees with the replica's direct steps to FP32 rounding only:
+    positions within 1e-6 A, momenta within 1e-5 relative, the box within 1e-9 relative."""
+    out, _, _ = _serve_lockstep([0, 1], max_slots=2)
+    for i in range(2):
+        r, p, cell = out[i]
+        r0, p0, cell0 = _direct(REQS[i], rbe.RBE_FP32_PHASE)
+        assert np.max(np.abs(r - r0)) < 1e-6
+        assert np.max(np.abs(p - p0)) <= 1e-5 * np.max(np.abs(p0))
+        assert np.allclose(cell[:3], cell0[:3], rtol=1e-9, atol=0)
+
+
+def test_lockstep_nonfinite_member_is_evicted():
+    """A NaN in one member's positions is latched in that replica's own status word (the
+    batched k-space writes each item's errors to its context), so only that replica fails
+    (RBE_ENONFINITE) while the others end bit for bit as when served alone."""
+    out, _, _ = _serve_lockstep([0, 1, 2, 3], max_slots=4, nan_in=1)
+    assert isinstance(out[1], rbe.RBEError) and out[1].status == rbe.RBE_ENONFINITE
+    for i in (0, 2, 3):
+        alone, _, _ = _serve_lockstep([i], max_slots=1)
+        _same(out[i], alone[i])
+
+
+def test_lockstep_autotuned_tiles():
+    """With the tiles autotuned on the first captured group (batched = 2) every request still
+    completes and stays within FP32 rounding of its direct steps."""
+    out, _, steps = _serve_lockstep([0, 1, 2, 3], max_slots=4, batched=2)
+    assert steps == sum(r[3] for r in REQS)
+    for i in range(4):
+        r, p, cell = out[i]
+        r0, p0, cell0 = _direct(REQS[i], rbe.RBE_FP32_PHASE)
+        assert np.max(np.abs(r - r0)) < 1e-6

@@ -12,7 +12,7 @@ from paper_2110_14362_gb300 import _binding as b
 
 def _cfg(**kw):
     base = dict(alpha=0.2, P=100, precision=rbe.RBE_FP32_PHASE, max_slots=4, chunk_steps=10,
-                mem_budget=1 << 30, use_graphs=1, pad=0)
+                mem_budget=1 << 30, use_graphs=1, batched=0)
     base.update(kw)
     return b.ServerConfig(**base)
 
@@ -24,7 +24,8 @@ def _create(cfg):
 
 
 @pytest.mark.parametrize("bad", [dict(alpha=0.0), dict(P=0), dict(max_slots=0), dict(max_slots=5000),
-                                 dict(chunk_steps=0), dict(mem_budget=0), dict(precision=7)])
+                                 dict(chunk_steps=0), dict(mem_budget=0), dict(precision=7),
+                                 dict(batched=3), dict(batched=1, precision=rbe.RBE_FP64)])
 def test_config_rejected(bad):
     st, h = _create(_cfg(**bad))
     assert st == rbe.RBE_EINVAL
