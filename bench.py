@@ -372,11 +372,13 @@ def serve_params(rbe, box, barostat=1):
 
 
 def serve(rbe, reqs, states, precision, max_slots, chunk, nsteps, use_graphs=True, open_loop=False,
-          budget=32 << 30, deadline_s=600.0):
+          budget=32 << 30, deadline_s=600.0, batched=0):
     """Drive the C++ serving loop: submit every request at t = 0 (closed loop) or at its
-    Poisson arrival time (open loop), poll until all are done.  Returns the metrics."""
+    Poisson arrival time (open loop), poll until all are done.  batched: 0 replicas on their own
+    chunks, 2 lockstep groups with the persistent batched k-space (tiles autotuned once).
+    Returns the metrics."""
     srv = rbe.Server(SERVE_ALPHA, SERVE_P, precision, max_slots=max_slots, chunk_steps=chunk,
-                     mem_budget=budget, use_graphs=use_graphs)
+                     mem_budget=budget, use_graphs=use_graphs, batched=batched)
     try:
         t0 = time.perf_counter()
         nxt = 0
@@ -760,6 +762,15 @@ def run_serving(args, world, rank):
     if not args.skip_open_loop:
         out["open_loop_20_per_s"] = serve(rbe, reqs, states, rbe.RBE_FP32_PHASE, args.serve_slots, chunk, steps,
                                           open_loop=True)
+    # lockstep groups: every step's k-space of the resident replicas in one persistent batched
+    # launch, a stable group replayed as one captured graph
+    serve(rbe, reqs[:4], states[:4], rbe.RBE_FP32_PHASE, args.serve_slots, chunk, chunk, batched=2)
+    lock = serve(rbe, reqs, states, rbe.RBE_FP32_PHASE, args.serve_slots, chunk, steps, batched=2)
+    lock["replica_steps_per_s_all_ranks"] = world * lock["replica_steps"] / max_over_ranks(world, lock["wall_s"])
+    out["lockstep_batched_closed_loop"] = lock
+    if not args.skip_open_loop:
+        out["lockstep_batched_open_loop_20_per_s"] = serve(rbe, reqs, states, rbe.RBE_FP32_PHASE, args.serve_slots,
+                                                           chunk, steps, open_loop=True, batched=2)
     k = min(args.serve_fp64_sample, len(reqs))
     if k > 0:
         fp64 = serve(rbe, reqs[:k], states[:k], rbe.RBE_FP64, 1, chunk, steps, use_graphs=False)
@@ -873,6 +884,7 @@ def main():
     ap.add_argument("--ptilde", type=int, default=0, help="with --profile-npt: a separate pressure batch")
     ap.add_argument("--reuse", type=int, default=1, help="with --profile-npt: samples drawn every M steps")
     ap.add_argument("--profile-batched", action="store_true", help="time only the batched k-space evaluation")
+    ap.add_argument("--profile-serving", action="store_true", help="run only the serving measurements")
     ap.add_argument("--profile-water", action="store_true",
                     help="run only the rigid-water NPT run (3000 molecules, FP64, --steps steps)")
     ap.add_argument("--water-alpha", type=float, default=None, help="with --profile-water: another alpha")
@@ -952,6 +964,11 @@ def main():
         torch.cuda.set_device(local)
         print(json.dumps({"metric": "general-cell k-space", "general": run_general(rbe, steps=args.steps)}),
               flush=True)
+        return
+    if args.profile_serving:
+        import torch
+        torch.cuda.set_device(local)
+        print(json.dumps({"metric": "serving", "serving": run_serving(args, world, rank)}), flush=True)
         return
     if args.profile_batched:
         # profiling aid: only the batched-versus-loop k-space measurement

@@ -33,6 +33,10 @@ struct KState {
     FixScaleH sc[3];    // 1/l as a 64-bit mantissa and a power of two (FP32-phase path)
     float cx, cy, cz;   // 2 pi / l
     int P;
+    double ce;          // 2 pi / V
+    double cb;          // 4 pi / V
+    double inv4a;       // 1 / (4 alpha)
+    double cself;       // -sqrt(alpha / pi)
 };
 
 // Frequency tiling of the rho pass (rho_shape in rbe_kspace.cu).

@@ -28,16 +28,22 @@
 
 namespace rbe {
 
-// Rho-pass planning constants (compile-time): particle sub-streams per block at most, and the
-// fewest particles per chunk.
+// Rho-pass planning constants (compile-time): particle sub-streams per block at most, the
+// fewest particles per chunk, and the most pairs N K of the latency-bound regime (one short
+// wave: one frequency per thread and no sub-streams run it fastest).  RBE_RHO_FORCE_F, when
+// defined, fixes the frequencies per thread (1, 2 or 4) for tuning.
 #ifndef RBE_RHO_MAXSUB
 #define RBE_RHO_MAXSUB 4
 #endif
 #ifndef RBE_RHO_MINCHUNK
 #define RBE_RHO_MINCHUNK 64
 #endif
+#ifndef RBE_RHO_LATENCY_PAIRS
+#define RBE_RHO_LATENCY_PAIRS 2.0e7
+#endif
 constexpr int kRhoMaxSub = RBE_RHO_MAXSUB;
 constexpr int kRhoMinChunk = RBE_RHO_MINCHUNK;
+constexpr double kRhoLatencyPairs = RBE_RHO_LATENCY_PAIRS;
 
 constexpr int kT = 128;               // threads per block of the FP64 force pass
 constexpr int kForceKT = 256;         // frequencies staged per tile in the FP64 force pass
@@ -679,6 +685,18 @@ static cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
     return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
+// The reduction's block: the fewest whole warps (up to kReduceThreads) that leave each thread at
+// most four partials of its row, so that short rows take small blocks (more of them resident
+// per SM, and the rows' FP64 work spread over the SMs).
+static cudaError_t launch_reduce_f32(cudaStream_t s, const float4* part32, int nchunks, int K, const int4* m,
+                                     const double* w, const KState* ks, const DeviceBuffers& d)
+{
+    int threads = 32;
+    while (threads < kReduceThreads && threads * 4 < nchunks) threads *= 2;
+    return launch_pdl(k_reduce_f32, dim3(K + 1), dim3(threads), 0, s, part32, nchunks, K, m, w, ks, d.rho,
+                      d.terms, d.coef_m, d.coef_f, d.status);
+}
+
 // Launch plan and partials capacity of one evaluation of N particles and K frequencies.
 struct EvalShape {
     Plan p;
@@ -687,32 +705,27 @@ struct EvalShape {
 };
 
 // Frequency tiling of the FP32-phase rho pass: kf frequencies per thread (1, 2 or 4) and
-// kthreads threads per block (whole warps).  The choice minimises a per-pair instruction
-// estimate: the pair's own work (base), one broadcast load per kf pairs, the particle
-// conversion spread over the tile's frequencies, divided by the fraction of lanes that hold a
-// frequency.
-// A tile narrower than the block's warps is given particle sub-streams (S = block threads / T,
-// a power of two), so that every block runs kRhoThreadsF threads or more.
-static RhoShape rho_shape(int K, int accum)
+// kthreads threads per block (whole warps).  Up to kRhoLatencyPairs pairs the pass is one short
+// wave bound by latency, not by issue: one frequency per thread, tiles of up to kMaxRhoThreads.
+// Above it, two frequencies per thread (one broadcast particle record feeds two pairs), tiles
+// of up to kRhoThreadsF threads.  Measured on GB300 from N K = 1e5 to 8e9, four frequencies per
+// thread never ran faster than two: equal where the tile is full, slower where a narrow tile
+// needs particle sub-streams.  A tile narrower than kRhoThreadsF threads is given particle
+// sub-streams (S = block threads / T, a power of two, at most kRhoMaxSub).
+static RhoShape rho_shape(int64_t N, int K)
 {
-    const double base = accum == RBE_RHO_COMP32 ? 12.0 : (accum == RBE_RHO_FP64 ? 14.0 : 10.0);
-    RhoShape best{1, 1, 32, 1};
-    double best_cost = 1e30;
-    for (int F : {4, 2, 1}) {
-        const int tmax = F == 1 ? kMaxRhoThreads : kRhoThreadsF;
-        const int ktiles = (K + tmax * F - 1) / (tmax * F);
-        const int per = (K + ktiles - 1) / ktiles;             // frequencies per tile
-        const int T = std::min(tmax, 32 * ((per + F * 32 - 1) / (F * 32)));
-        const double eff = (double)K / ((double)ktiles * T * F);
-        const double cost = (base + 1.0 / F + 55.0 / (T * F)) / eff;
-        if (cost < best_cost - 1e-9) {
-            best_cost = cost;
-            int S = 1;
-            while (T * S * 2 <= kRhoThreadsF && S * 2 <= kRhoMaxSub) S *= 2;
-            best = RhoShape{F, ktiles, T * S, S};
-        }
-    }
-    return best;
+#ifdef RBE_RHO_FORCE_F
+    const int F = RBE_RHO_FORCE_F;
+#else
+    const int F = (double)N * (double)K <= kRhoLatencyPairs ? 1 : 2;
+#endif
+    const int tmax = F == 1 ? kMaxRhoThreads : kRhoThreadsF;
+    const int ktiles = (K + tmax * F - 1) / (tmax * F);
+    const int per = (K + ktiles - 1) / ktiles;  // frequencies per tile
+    const int T = std::min(tmax, 32 * ((per + F * 32 - 1) / (F * 32)));
+    int S = 1;
+    while (T * S * 2 <= kRhoThreadsF && S * 2 <= kRhoMaxSub) S *= 2;
+    return RhoShape{F, ktiles, T * S, S};
 }
 
 static rbe_status evaluate_shape(rbe_ctx ctx, int64_t N, int K, EvalShape* out)
@@ -744,7 +757,7 @@ static rbe_status evaluate_shape(rbe_ctx ctx, int64_t N, int K, EvalShape* out)
         rs.ksub = 1;
         rho_bps = std::max(1, std::min(32, rho64_threads / rs.kthreads));
     } else {
-        rs = rho_shape(K, ctx->rho_accum);
+        rs = rho_shape(N, K);
         const int a = ctx->rho_accum < 0 || ctx->rho_accum > 2 ? 1 : ctx->rho_accum;
         const int fi = rs.kf == 4 ? 2 : (rs.kf == 2 ? 1 : 0);
         int& bps = rho32_bps[a][fi];
@@ -804,9 +817,7 @@ static rbe_status launch_evaluate_range(rbe_ctx ctx, int64_t N, const void* pos,
         k_reduce<<<K + 1, kReduceThreads, 0, s>>>(part64, p.nchunks, K, m_in, w_in, ks, d.rho, d.terms, d.coef_d,
                                                    d.counter, d.status, W, E);
     } else {
-        cudaError_t err = launch_pdl(k_reduce_f32, dim3(K + 1), dim3(kReduceThreads), 0, s, (const float4*)part32,
-                                     p.nchunks, K, m_in, w_in, ks, d.rho,
-                                     d.terms, d.coef_m, d.coef_f, d.status);
+        cudaError_t err = launch_reduce_f32(s, (const float4*)part32, p.nchunks, K, m_in, w_in, ks, d);
         if (err != cudaSuccess) return cuda_fail(ctx, err, "launch k_reduce_f32");
     }
     st = check_launch(ctx, "k_reduce");
@@ -910,9 +921,7 @@ rbe_status launch_evaluate_staged(rbe_ctx ctx, int64_t N, const double* h_pos, c
                          pl[g].chunk_len, nchunks, part32 + coff[g], d.status, 0, pl[g].ksub);
         if (err != cudaSuccess) return cuda_fail(ctx, err, "staged: k_rho_f32");
     }
-    err = launch_pdl(k_reduce_f32, dim3(K + 1), dim3(kReduceThreads), 0, s, (const float4*)part32, nchunks, K,
-                     (const int4*)d.m, (const double*)d.w, ks, d.rho, d.terms, d.coef_m,
-                     d.coef_f, d.status);
+    err = launch_reduce_f32(s, (const float4*)part32, nchunks, K, (const int4*)d.m, (const double*)d.w, ks, d);
     if (err != cudaSuccess) return cuda_fail(ctx, err, "staged: k_reduce_f32");
     for (int g = 0; g < pieces; ++g) {
         const int64_t a = i0[g], n = i0[g + 1] - i0[g];

@@ -146,10 +146,17 @@ __device__ __forceinline__ void tables_body(double bx, double by, double bz, con
         else if (t == 1) ks->cy = c;
         else ks->cz = c;
     } else if (tid == 96) {
-        ks->V = sL[0] * sL[1] * sL[2];
+        const double V = sL[0] * sL[1] * sL[2];
+        ks->V = V;
+        ks->ce = 2.0 * kPi / V;
+    } else if (tid == 97) {
+        ks->cb = 4.0 * kPi / (sL[0] * sL[1] * sL[2]);
     } else if (tid == 128) {
         ks->alpha = alpha;
         ks->P = P;
+        ks->inv4a = 0.25 / alpha;
+    } else if (tid == 129) {
+        ks->cself = -sqrt(alpha / kPi);
     }
     __syncthreads();
     if (tid == 0) {
@@ -260,6 +267,41 @@ __device__ __forceinline__ void block_sum_ff(float& hi, float& lo, float (*scrat
             const float oh = __shfl_xor_sync(0xffffffffu, hi, off);
             const float ol = __shfl_xor_sync(0xffffffffu, lo, off);
             ff_add2(hi, lo, oh, ol);
+        }
+    }
+}
+
+// Fixed-order block sums of two float-float values per thread (one shared-memory round for
+// both); valid in thread 0.
+__device__ __forceinline__ void block_sum_ff2(float& ah, float& al, float& bh, float& bl, float (*scratch)[32])
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float oah = __shfl_xor_sync(0xffffffffu, ah, off), oal = __shfl_xor_sync(0xffffffffu, al, off);
+        const float obh = __shfl_xor_sync(0xffffffffu, bh, off), obl = __shfl_xor_sync(0xffffffffu, bl, off);
+        ff_add2(ah, al, oah, oal);
+        ff_add2(bh, bl, obh, obl);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        scratch[0][warp] = ah;
+        scratch[1][warp] = al;
+        scratch[2][warp] = bh;
+        scratch[3][warp] = bl;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const bool on = lane < (int)(blockDim.x >> 5);
+        ah = on ? scratch[0][lane] : 0.f;
+        al = on ? scratch[1][lane] : 0.f;
+        bh = on ? scratch[2][lane] : 0.f;
+        bl = on ? scratch[3][lane] : 0.f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float oah = __shfl_xor_sync(0xffffffffu, ah, off), oal = __shfl_xor_sync(0xffffffffu, al, off);
+            const float obh = __shfl_xor_sync(0xffffffffu, bh, off), obl = __shfl_xor_sync(0xffffffffu, bl, off);
+            ff_add2(ah, al, oah, oal);
+            ff_add2(bh, bl, obh, obl);
         }
     }
 }
@@ -488,51 +530,61 @@ __device__ __forceinline__ void rho_f32_tile(int kt, int c, const void* __restri
 }
 
 // =================================================================================
-// Reduction for the FP32-phase path.  Block l (of K + 1) sums row l of the partials over
-// the chunks as float-float in a fixed order; thread 0 then widens rho_l to FP64 and forms
+// Reduction for the FP32-phase path.  Block l (of K + 1; whole warps, at most kReduceThreads)
+// sums row l of the partials over the chunks as float-float in a fixed order; thread 0 then widens rho_l to FP64 and forms
 // the per-frequency energy and virial terms in FP64 (App. C Eq. (pressuretensorflexible):
 // |rho|^2 of a float-float rho, the importance weight, 1/|k|^2 and the k k products), and the
 // force pass's FP32 coefficients.  Row K carries the sum of q^2.  The sums over l run in the
 // force launch (k_force_f32's extra block, final_sums), concurrently with the force pass.
+//
+// GB300 runs FP64 at a low rate and long latency, so the FP64 work of a frequency is split:
+// everything that does not depend on rho_l (1/|k|^2 and the tensor factors, freq_pre) is
+// formed before the reduction, while the partial sums are still being written, and only a few
+// multiplications follow it (freq_post).
 __device__ __forceinline__ double ff_to_double(float hi, float lo)
 {
     return __longlong_as_double((long long)float_to_double_bits(__float_as_uint(hi))) +
            __longlong_as_double((long long)float_to_double_bits(__float_as_uint(lo)));
 }
 
-// Energy and virial terms of one frequency in FP64: e = (2 pi / V) w |rho|^2 / |k|^2 and
-// e [delta - 2 (1/|k|^2 + 1/4a) k k] (xx, yy, zz, xy, xz, yz) into t[0..6].
-__device__ __forceinline__ void freq_terms_f64(int4 mi, double wd, double re, double im, const KState* __restrict__ ks,
-                                               double* __restrict__ t)
+// The rho-independent factors of frequency m with weight w:
+//   c[0] = (2 pi / V) w / |k|^2                 (e = c[0] |rho|^2)
+//   c[1..3] = 1 - b k_a^2, c[4..6] = -b k_x k_y, -b k_x k_z, -b k_y k_z,  b = 2 (1/|k|^2 + 1/4a)
+//   c[7] = (4 pi / V) w / |k|^2                 (the force amplitude R = c[7] |rho|)
+__device__ __forceinline__ void freq_pre(int4 mi, double wd, const KState* __restrict__ ks, double* __restrict__ c)
 {
     const double kx = 2.0 * kPi * (double)mi.x * ks->inv[0];
     const double ky = 2.0 * kPi * (double)mi.y * ks->inv[1];
     const double kz = 2.0 * kPi * (double)mi.z * ks->inv[2];
     const double kk = kx * kx + ky * ky + kz * kz;
     const double ikk = 1.0 / kk;
-    const double e = (2.0 * kPi / ks->V) * wd * (re * re + im * im) * ikk;
-    const double b = 2.0 * (ikk + 0.25 / ks->alpha);
-    t[0] = e;
-    t[1] = e * (1.0 - b * kx * kx);
-    t[2] = e * (1.0 - b * ky * ky);
-    t[3] = e * (1.0 - b * kz * kz);
-    t[4] = -e * b * kx * ky;
-    t[5] = -e * b * kx * kz;
-    t[6] = -e * b * ky * kz;
-    t[7] = 0.0;
+    const double wk = wd * ikk;
+    const double b = 2.0 * (ikk + ks->inv4a);
+    c[0] = ks->ce * wk;
+    c[1] = 1.0 - b * kx * kx;
+    c[2] = 1.0 - b * ky * ky;
+    c[3] = 1.0 - b * kz * kz;
+    c[4] = -b * kx * ky;
+    c[5] = -b * kx * kz;
+    c[6] = -b * ky * kz;
+    c[7] = ks->cb * wk;
 }
 
-// The force pass's data of one frequency: Im(e^{-ik.r} rho) = |rho| sin(arg rho - theta), so
-// the pass takes one sine per pair of the phase shifted by arg rho (harmonic addition), its
-// amplitude R = beta |rho| (beta = w 4 pi / (V |k|^2), FP64) folded into the FP32 coefficients,
-// and arg rho as a 32-bit fixed-point offset of the phase.
-__device__ __forceinline__ void force_coef(int4 mi, double wd, double re, double im, const KState* __restrict__ ks,
-                                           int4* __restrict__ cm, float4* __restrict__ cf)
+// Energy and virial terms of one frequency in FP64 into t[0..6] (e = c[0] |rho|^2 and
+// e [delta - 2 (1/|k|^2 + 1/4a) k k] as xx, yy, zz, xy, xz, yz), and the force pass's data:
+// Im(e^{-ik.r} rho) = |rho| sin(arg rho - theta), so the pass takes one sine per pair of the
+// phase shifted by arg rho (harmonic addition), its amplitude R = c[7] |rho| folded into the
+// FP32 coefficients, and arg rho as a 32-bit fixed-point offset of the phase.
+__device__ __forceinline__ void freq_post(int4 mi, const double* __restrict__ c, double re, double im,
+                                          double* __restrict__ t, int4* __restrict__ cm, float4* __restrict__ cf)
 {
-    const double kx = (double)mi.x * ks->inv[0], ky = (double)mi.y * ks->inv[1], kz = (double)mi.z * ks->inv[2];
-    const double kk = 4.0 * kPi * kPi * (kx * kx + ky * ky + kz * kz);
-    const double R = wd * (4.0 * kPi / ks->V) / kk * sqrt(re * re + im * im);
-    const float Rf = (float)R;
+    const double rho2 = re * re + im * im;
+    const double e = c[0] * rho2;
+    t[0] = e;
+#pragma unroll
+    for (int a = 1; a < 7; ++a) t[a] = e * c[a];
+    t[7] = 0.0;
+    const float Rf = (float)c[7] * sqrtf((float)rho2);
     const double phi = (double)atan2f((float)im, (float)re) * 683565275.57643158978;  // revolutions x 2^32
     const uint32_t off = 0x80000100u - (uint32_t)(unsigned long long)__double2ll_rn(phi);
     *cm = make_int4(mi.x, mi.y, mi.z, (int)off);
@@ -545,26 +597,25 @@ __device__ __forceinline__ void reduce_f32_row(int l, const float4* __restrict__
              double* __restrict__ terms, int4* __restrict__ coef_m, float4* __restrict__ coef_f,
              unsigned* __restrict__ status)
 {
-    __shared__ float red[2][32];
+    __shared__ float red[4][32];
     // the sampler completed before the rho pass passed its wait, and the rho pass lets this
     // launch start only after that wait: m, w and ks are final here
     int4 mi = make_int4(0, 0, 0, 0);
-    double wd = 0.0;
+    double c[8];
     if (threadIdx.x == 0 && l < K) {
         mi = m[l];
-        wd = w[l];
+        freq_pre(mi, w[l], ks, c);
     }
     pdl_wait();
     pdl_trigger();
     float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
     const float4* row = partials + (size_t)l * nchunks;
-    for (int j = threadIdx.x; j < nchunks; j += kReduceThreads) {
+    for (int j = threadIdx.x; j < nchunks; j += blockDim.x) {
         const float4 v = row[j];
         ff_add2(rh, rl, v.x, v.y);
         ff_add2(ih, il, v.z, v.w);
     }
-    block_sum_ff(rh, rl, red);
-    block_sum_ff(ih, il, red);
+    block_sum_ff2(rh, rl, ih, il, red);
     if (threadIdx.x != 0) return;
     double* t = terms + (size_t)l * 8;
     const double re = ff_to_double(rh, rl), im = ff_to_double(ih, il);
@@ -572,8 +623,7 @@ __device__ __forceinline__ void reduce_f32_row(int l, const float4* __restrict__
         t[0] = re;  // sum of q^2
         return;
     }
-    freq_terms_f64(mi, wd, re, im, ks, t);
-    force_coef(mi, wd, re, im, ks, coef_m + l, coef_f + l);
+    freq_post(mi, c, re, im, t, coef_m + l, coef_f + l);
     rho[l] = make_double2(re, im);
     if (!isfinite(re) || !isfinite(im)) atomicOr(status, kStatusNonFinite);
 }
@@ -588,6 +638,12 @@ __device__ __forceinline__ void reduce_f32_row_warp(int l, const float4* __restr
                                                     float4* __restrict__ coef_f, unsigned* __restrict__ status)
 {
     const int lane = threadIdx.x & 31;
+    int4 mi = make_int4(0, 0, 0, 0);
+    double c[8];
+    if (lane == 0 && l < K) {
+        mi = m[l];
+        freq_pre(mi, w[l], ks, c);
+    }
     float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
     const float4* row = partials + (size_t)l * nchunks;
     for (int j = lane; j < nchunks; j += 32) {
@@ -598,9 +654,9 @@ __device__ __forceinline__ void reduce_f32_row_warp(int l, const float4* __restr
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         const float a = __shfl_xor_sync(0xffffffffu, rh, off), b = __shfl_xor_sync(0xffffffffu, rl, off);
-        const float c = __shfl_xor_sync(0xffffffffu, ih, off), d = __shfl_xor_sync(0xffffffffu, il, off);
+        const float cc = __shfl_xor_sync(0xffffffffu, ih, off), d = __shfl_xor_sync(0xffffffffu, il, off);
         ff_add2(rh, rl, a, b);
-        ff_add2(ih, il, c, d);
+        ff_add2(ih, il, cc, d);
     }
     if (lane != 0) return;
     double* t = terms + (size_t)l * 8;
@@ -609,44 +665,36 @@ __device__ __forceinline__ void reduce_f32_row_warp(int l, const float4* __restr
         t[0] = re;  // sum of q^2
         return;
     }
-    const int4 mi = m[l];
-    const double wd = w[l];
-    freq_terms_f64(mi, wd, re, im, ks, t);
-    force_coef(mi, wd, re, im, ks, coef_m + l, coef_f + l);
+    freq_post(mi, c, re, im, t, coef_m + l, coef_f + l);
     rho[l] = make_double2(re, im);
     if (!isfinite(re) || !isfinite(im)) atomicOr(status, kStatusNonFinite);
 }
 
-// Energy and virial: fixed-order FP64 sums of the per-frequency terms over l, by one block
-// of kForceThreads threads; E_self = -sqrt(alpha/pi) sum q^2 in FP64.
+// Energy and virial: fixed-order FP64 sums of the per-frequency terms over l by one block of
+// kForceWarps warps; E_self = cself sum q^2 in FP64.  Lane (part p = lane / 8, term a = lane
+// % 8) of warp v sums term a of rows l = 4 (v + kForceWarps i) + p, i = 0, 1, ... in order
+// (one FP64 add per row and lane: a warp instruction covers four rows of all seven terms);
+// the four parts are then combined by a fixed shuffle pair and the warps in order.
 __device__ __forceinline__ void final_sums(const double* __restrict__ terms, int K, const KState* __restrict__ ks,
                                            double* __restrict__ W_out, double* __restrict__ E_out,
                                            unsigned* __restrict__ status)
 {
-    __shared__ double fin[kForceWarps][7];
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int j = threadIdx.x; j < K; j += blockDim.x) {
-        const double* t = terms + (size_t)j * 8;
-#pragma unroll
-        for (int a = 0; a < 7; ++a) acc[a] += t[a];
-    }
+    __shared__ double fin[kForceWarps][8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-    for (int a = 0; a < 7; ++a) {
-        double v = acc[a];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (lane == 0) fin[warp][a] = v;
-    }
+    const int p = lane >> 3, a = lane & 7;
+    double acc = 0.0;
+    for (int l = 4 * warp + p; l < K; l += 4 * kForceWarps) acc += terms[(size_t)l * 8 + a];
+    acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+    if (lane < 8) fin[warp][lane] = acc;
     __syncthreads();
     // thread a (< 7) finishes term a; thread 7 the self energy
     if (threadIdx.x < 8) {
-        const int a = threadIdx.x;
         double v = 0.0;
         if (a < 7) {
-            for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) v += fin[wv][a];
+            for (int wv = 0; wv < kForceWarps; ++wv) v += fin[wv][a];
         } else {
-            v = -sqrt(ks->alpha / kPi) * terms[(size_t)K * 8];
+            v = ks->cself * terms[(size_t)K * 8];
         }
         if (!isfinite(v)) atomicOr(status, kStatusNonFinite);
         if (a == 0 && E_out) E_out[0] = v;

@@ -9,8 +9,10 @@
 // concurrently on the GPU and new requests are admitted while others run.  Latency of a
 // chunk = host time from its launch to the observation of its completion event.
 //
-// Failures stay with their request: after every chunk the slot's device status word is copied
-// into pinned host memory on the slot's stream, before the completion event, so a replica that
+// Failures stay with their request: every chunk ends with a one-thread kernel that stores the
+// slot's device status word into mapped pinned host memory (inside the chunk's graph; a store
+// over the host link instead of a copy-engine transfer per chunk, which the copy engines shared
+// by all slots' streams would serialise), before the completion event, so a replica that
 // latched an error (non-finite values, a box outside its prepared range, a full neighbour
 // list) is evicted at the end of that chunk with the error as its result, and its slot serves
 // the next request; the other replicas run on untouched.  A request can also be cancelled,
@@ -58,9 +60,27 @@ struct Slot {
     cudaGraphExec_t graph = nullptr;
     int32_t graph_steps = 0;
     int64_t bytes = 0;
-    unsigned* h_status = nullptr;  // pinned: the context's device status word after the last chunk
+    unsigned* h_status = nullptr;  // pinned, mapped: the context's device status word after the last chunk
+    unsigned* h_status_dev = nullptr;  // the same word's device address
     bool cancel = false;           // leave at the end of the chunk in flight
 };
+
+// Stores up to kPublishMax device status words into their mapped host words (thread i: pair i).
+constexpr int kPublishMax = 64;
+struct StatusPairs {
+    const unsigned* dev[kPublishMax];
+    unsigned* host[kPublishMax];
+    int n;
+};
+
+__global__ void k_publish_status(StatusPairs p)
+{
+    const int i = threadIdx.x;
+    if (i < p.n) {
+        *reinterpret_cast<volatile unsigned*>(p.host[i]) = *reinterpret_cast<const volatile unsigned*>(p.dev[i]);
+        __threadfence_system();
+    }
+}
 
 }  // namespace
 
@@ -147,12 +167,31 @@ static void release_slot(rbe_server_s* s, Slot& sl)
     sl.cancel = false;
 }
 
+// Publishes the status words of `n` slots on `stream` (kernel launches, capturable).
+static cudaError_t publish_status(cudaStream_t stream, const Slot* const* sl, int n)
+{
+    for (int b = 0; b < n; b += kPublishMax) {
+        StatusPairs p{};
+        p.n = std::min(kPublishMax, n - b);
+        for (int i = 0; i < p.n; ++i) {
+            p.dev[i] = sl[b + i]->ctx->d.status;
+            p.host[i] = sl[b + i]->h_status_dev;
+        }
+        k_publish_status<<<1, kPublishMax, 0, stream>>>(p);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 static rbe_status ensure_slot_buffers(rbe_server_s* s, Slot& sl, int64_t N)
 {
     if (!sl.stream) {
         cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&sl.h_status), sizeof(unsigned));
+        if (e == cudaSuccess)
+            e = cudaHostAlloc(reinterpret_cast<void**>(&sl.h_status), sizeof(unsigned), cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&sl.h_status_dev), sl.h_status, 0);
         if (e != cudaSuccess) return sfail(s, RBE_ECUDA, std::string("slot stream: ") + cudaGetErrorString(e));
         *sl.h_status = 0u;
     }
@@ -226,7 +265,10 @@ static rbe_status admit(rbe_server_s* s, Slot& sl, int64_t id)
         e = cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             st = rbe_npt_step(sl.ctx, &probe, s->cfg.chunk_steps);
+            const Slot* one = &sl;
+            const cudaError_t ep = st == RBE_OK ? publish_status(sl.stream, &one, 1) : cudaSuccess;
             e = cudaStreamEndCapture(sl.stream, &g);
+            if (e == cudaSuccess) e = ep;
             if (st != RBE_OK) {
                 if (g) cudaGraphDestroy(g);
                 return sfail(s, st, std::string("capture: ") + rbe_last_error(sl.ctx));
@@ -260,11 +302,13 @@ static rbe_status launch_chunk(rbe_server_s* s, Slot& sl)
     } else {
         st = rbe_npt_step(sl.ctx, &sl.sys, n);
         if (st != RBE_OK) return sfail(s, st, rbe_last_error(sl.ctx));
+        // the replica's latched device errors, read by progress() once the chunk is complete (the
+        // captured chunk publishes them itself)
+        const Slot* one = &sl;
+        const cudaError_t ep = publish_status(sl.stream, &one, 1);
+        if (ep != cudaSuccess) return sfail(s, RBE_ECUDA, std::string("chunk status: ") + cudaGetErrorString(ep));
     }
-    // the replica's latched device errors, read by progress() once the chunk is complete
-    cudaError_t e = cudaMemcpyAsync(sl.h_status, sl.ctx->d.status, sizeof(unsigned), cudaMemcpyDeviceToHost,
-                                    sl.stream);
-    if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
+    cudaError_t e = cudaEventRecord(sl.done, sl.stream);
     if (e != cudaSuccess) return sfail(s, RBE_ECUDA, std::string("chunk status: ") + cudaGetErrorString(e));
     sl.in_flight = true;
     sl.chunk_in_flight = n;
@@ -465,14 +509,15 @@ static rbe_status launch_group_chunk(rbe_server_s* s)
     }
     s->last_key = key;
     // every member's latched device errors, read once the chunk is complete
+    std::vector<const Slot*> pub;
     for (int k : s->members) {
         Slot& sl = s->slots[k];
-        if ((e = cudaMemcpyAsync(sl.h_status, sl.ctx->d.status, sizeof(unsigned), cudaMemcpyDeviceToHost,
-                                 s->gstream)) != cudaSuccess)
-            return sfail(s, RBE_ECUDA, std::string("group status: ") + cudaGetErrorString(e));
+        pub.push_back(&sl);
         sl.in_flight = true;
         sl.chunk_in_flight = n;
     }
+    if ((e = publish_status(s->gstream, pub.data(), (int)pub.size())) != cudaSuccess)
+        return sfail(s, RBE_ECUDA, std::string("group status: ") + cudaGetErrorString(e));
     if ((e = cudaEventRecord(s->gdone, s->gstream)) != cudaSuccess)
         return sfail(s, RBE_ECUDA, std::string("group event: ") + cudaGetErrorString(e));
     s->group_in_flight = true;
@@ -618,7 +663,7 @@ rbe_status rbe_server_progress(rbe_server s, int32_t wait, int32_t* n_queued, in
                     sl.in_flight = false;
                     sl.steps_left -= sl.chunk_in_flight;
                     s->steps_done += sl.chunk_in_flight;
-                    const unsigned bits = *sl.h_status;
+                    const unsigned bits = *static_cast<volatile unsigned*>(sl.h_status);
                     if (bits) {
                         const rbe_status st = status_from_bits(sl.ctx, bits);
                         evict(s, sl, 3, st, std::string("evicted after step ") + std::to_string(sl.sys.step) + ": " +
@@ -641,7 +686,7 @@ rbe_status rbe_server_progress(rbe_server s, int32_t wait, int32_t* n_queued, in
             sl.steps_left -= sl.chunk_in_flight;
             s->steps_done += sl.chunk_in_flight;
             any_done = true;
-            const unsigned bits = *sl.h_status;
+            const unsigned bits = *static_cast<volatile unsigned*>(sl.h_status);
             if (bits) {
                 const rbe_status st = status_from_bits(sl.ctx, bits);
                 evict(s, sl, 3, st, std::string("evicted after step ") + std::to_string(sl.sys.step) + ": " +
