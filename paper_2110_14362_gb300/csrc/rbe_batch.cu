@@ -10,14 +10,18 @@
 //   sample   units of 256 frequencies per item                                   (H2)
 //   rho      the work list of (item, frequency tile, particle chunk) tiles: partial rho(k)
 //            per chunk                                                           (H4)
-//   reduce   one unit per (item, frequency): rho(k), terms, force coefficients   (H3, H6)
+//   reduce   groups of 32 (item, frequency) rows: rho(k), terms, force coefficients
+//                                                                                (H3, H6)
 //   force    the work list of (item, particle block) tiles, then one final-sum unit per item:
 //            forces, virial, energies                                            (H5, H6)
 // The tiles run the single-system kernels' bodies (rbe_kspace_tiles.cuh).  Tile shapes
 // (frequencies per rho tile, particles per rho chunk, particles per force block) are the
 // batch's, set by hand or by rbe_batch_autotune, which times the candidate shapes on the
 // caller's items pass by pass.  An item's result depends only on its own inputs and the tile
-// shapes, never on the other items (fixed-order sums inside the item's tiles).
+// shapes, never on the other items (fixed-order sums inside the item's tiles).  With
+// persistence off the five passes are five launches of kernels compiled one per pass (the
+// same bodies, so the same results bit for bit): each needs fewer registers than the fused
+// kernel, so more of its blocks stay resident.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -189,16 +193,49 @@ __device__ __forceinline__ void pass_rho(const BArgs& a)
     }
 }
 
-// one (item, frequency) row per warp
+// (item, frequency) rows u = r (P + 1) + l in groups of 32 per block: each warp sums four rows
+// (warp_row_sum), then the lanes of warp 0 form the 32 rows' FP64 terms and coefficients at
+// once (GB300 issues a warp's FP64 instruction at about two lanes per clock, so one FP64 chain
+// per row and warp would queue on the FP64 unit).
+constexpr int kReduceRowsPerWarp = 4;
+constexpr int kReduceGroup = kReduceRowsPerWarp * kBThreads / 32;
+static_assert(kReduceGroup == 32, "one row per lane of the finishing warp");
+
 __device__ __forceinline__ void pass_reduce(const BArgs& a)
 {
-    const int wpb = kBThreads / 32, warp = threadIdx.x >> 5;
-    for (int u = blockIdx.x * wpb + warp; u < a.n * (a.P + 1); u += gridDim.x * wpb) {
-        const int r = u / (a.P + 1), l = u % (a.P + 1);
-        const BItem& it = a.items[r];
-        const size_t o = (size_t)r * a.P;
-        reduce_f32_row_warp(l, a.part + it.part_off, it.nchunks, a.P, a.m + o, a.w + o, a.ks + r, a.rho + o,
-                            a.terms + (size_t)r * (a.P + 1) * 8, a.coef_m + o, a.coef_f + o, it.status);
+    __shared__ double2 srho[kReduceGroup];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rows = a.n * (a.P + 1);
+    for (int base = blockIdx.x * kReduceGroup; base < rows; base += gridDim.x * kReduceGroup) {
+        // warp 0's lanes: the factors of their rows that do not depend on rho, meanwhile
+        int4 mi = make_int4(0, 0, 0, 0);
+        double c[8];
+        const int uf = base + lane;
+        if (warp == 0 && uf < rows) {
+            const int r = uf / (a.P + 1), l = uf % (a.P + 1);
+            if (l < a.P) {
+                const size_t o = (size_t)r * a.P;
+                mi = a.m[o + l];
+                freq_pre(mi, a.w[o + l], a.ks + r, c);
+            }
+        }
+#pragma unroll 1
+        for (int i = 0; i < kReduceRowsPerWarp; ++i) {
+            const int j = warp * kReduceRowsPerWarp + i, u = base + j;
+            if (u >= rows) break;
+            const int r = u / (a.P + 1), l = u % (a.P + 1);
+            const BItem& it = a.items[r];
+            const double2 v = warp_row_sum(a.part + it.part_off + (size_t)l * it.nchunks, it.nchunks);
+            if (lane == 0) srho[j] = v;
+        }
+        __syncthreads();
+        if (warp == 0 && uf < rows) {
+            const int r = uf / (a.P + 1), l = uf % (a.P + 1);
+            const size_t o = (size_t)r * a.P;
+            row_finish(l, a.P, srho[lane].x, srho[lane].y, mi, c, a.rho + o, a.terms + (size_t)r * (a.P + 1) * 8,
+                       a.coef_m + o, a.coef_f + o, a.items[r].status);
+        }
+        __syncthreads();
     }
 }
 
@@ -222,30 +259,41 @@ __device__ __forceinline__ void pass_force(const BArgs& a)
     }
 }
 
-// The batched evaluation: the passes in `mask` (1 tables, 2 sample, 4 rho, 8 reduce, 16
-// force).  All five in one launch is the persistent form: a cooperative launch whose blocks
-// all stay resident, with a grid barrier between consecutive passes; a single pass runs as an
-// ordinary launch (the tuner times passes one by one).
+// The batched evaluation in one launch, the persistent form: a cooperative launch whose blocks
+// all stay resident and run the five passes with a grid barrier between consecutive passes.
+// Written as straight-line code (not a loop over the passes), the fused kernel fits three
+// blocks of 256 threads per SM without spilling.
 #ifndef RBE_BATCH_MINB
-#define RBE_BATCH_MINB 2
+#define RBE_BATCH_MINB 3
 #endif
-__global__ void __launch_bounds__(kBThreads, RBE_BATCH_MINB) k_batch(BArgs a, int mask)
+__global__ void __launch_bounds__(kBThreads, RBE_BATCH_MINB) k_batch(BArgs a)
 {
-    bool first = true;
-    const int passes[5] = {1, 2, 4, 8, 16};
-    for (int k = 0; k < 5; ++k) {
-        if (!(mask & passes[k])) continue;
-        if (!first && !grid_sync(a.bar, gridDim.x + (unsigned)a.bar_extra, a.status)) return;
-        first = false;
-        switch (k) {
-        case 0: pass_tables(a); break;
-        case 1: pass_sample(a); break;
-        case 2: pass_rho(a); break;
-        case 3: pass_reduce(a); break;
-        default: pass_force(a); break;
-        }
-    }
+    const unsigned nb = gridDim.x + (unsigned)a.bar_extra;
+    pass_tables(a);
+    if (!grid_sync(a.bar, nb, a.status)) return;
+    pass_sample(a);
+    if (!grid_sync(a.bar, nb, a.status)) return;
+    pass_rho(a);
+    if (!grid_sync(a.bar, nb, a.status)) return;
+    pass_reduce(a);
+    if (!grid_sync(a.bar, nb, a.status)) return;
+    pass_force(a);
 }
+
+// The same passes as launches of their own (persistence off): each pass compiled alone needs 60
+// to 86 registers (tables 86), not the fused kernel's 128, so four blocks of 256 threads stay
+// resident per SM instead of two.
+#ifndef RBE_BATCH_PASS_MINB
+#define RBE_BATCH_PASS_MINB 4
+#endif
+__global__ void __launch_bounds__(kBThreads, 2) k_btables(BArgs a) { pass_tables(a); }
+__global__ void __launch_bounds__(kBThreads, RBE_BATCH_PASS_MINB) k_bsample(BArgs a) { pass_sample(a); }
+__global__ void __launch_bounds__(kBThreads, RBE_BATCH_PASS_MINB) k_brho(BArgs a) { pass_rho(a); }
+__global__ void __launch_bounds__(kBThreads, RBE_BATCH_PASS_MINB) k_breduce(BArgs a) { pass_reduce(a); }
+__global__ void __launch_bounds__(kBThreads, RBE_BATCH_PASS_MINB) k_bforce(BArgs a) { pass_force(a); }
+
+using PassKernel = void (*)(BArgs);
+static const PassKernel kPassKernels[5] = {k_btables, k_bsample, k_brho, k_breduce, k_bforce};
 
 template <typename Kern>
 static int resident_blocks(Kern kern, int threads, size_t dyn_smem)
@@ -302,6 +350,8 @@ struct rbe_batch_s {
     std::vector<int4> h_rtiles;
     std::vector<int2> h_ftiles;
     int grid_per_sm = 1;      // resident blocks of k_batch per SM (the persistent grid)
+    int pass_per_sm[5] = {1, 1, 1, 1, 1};  // resident blocks per SM of each pass kernel
+    size_t pass_smem[5] = {0, 0, 0, 0, 0};  // their dynamic shared memory
     GridBar* d_bar = nullptr;  // the grid barrier of the persistent launch
     bool persistent = true;    // one cooperative launch per evaluation (else one launch per pass)
     int bar_extra = 0;         // test hook of the barriers' timeout (rbe_batch_test_barrier_timeout)
@@ -543,9 +593,11 @@ rbe_status launch(rbe_batch b, int n, int mask)
     a.bar_extra = b->bar_extra;
     const size_t smem = std::max(a.smem_cap ? table_smem : 0, (size_t)kForceSmemPerK * std::min(P, kForceStageK));
     const int resident = std::max(1, b->num_sms * b->grid_per_sm);
-    auto run = [&](int m, int units, bool coop) -> cudaError_t {
+    if (mask == 31 && b->persistent) {
+        // the barrier words start at zero for every launch (a launch that timed out leaves them set)
+        if ((e = cudaMemsetAsync(b->d_bar, 0, sizeof(GridBar), s)) != cudaSuccess) return bcuda(b, e, "barrier reset");
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(coop ? resident : std::max(1, std::min(units, resident)));
+        cfg.gridDim = dim3(resident);
         cfg.blockDim = dim3(kBThreads);
         cfg.dynamicSmemBytes = smem;
         cfg.stream = s;
@@ -553,19 +605,17 @@ rbe_status launch(rbe_batch b, int n, int mask)
         attr[0].id = cudaLaunchAttributeCooperative;
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
-        cfg.numAttrs = coop ? 1 : 0;
-        return cudaLaunchKernelEx(&cfg, k_batch, a, m);
-    };
-    if (mask == 31 && b->persistent) {
-        // the barrier words start at zero for every launch (a launch that timed out leaves them set)
-        if ((e = cudaMemsetAsync(b->d_bar, 0, sizeof(GridBar), s)) != cudaSuccess) return bcuda(b, e, "barrier reset");
-        if ((e = run(31, 0, true)) != cudaSuccess) return bcuda(b, e, "persistent batched k-space launch");
+        cfg.numAttrs = 1;
+        if ((e = cudaLaunchKernelEx(&cfg, k_batch, a)) != cudaSuccess)
+            return bcuda(b, e, "persistent batched k-space launch");
         return RBE_OK;
     }
-    const int units[5] = {nw, n * a.bpi, a.nrt, (n * (P + 1) + kBThreads / 32 - 1) / (kBThreads / 32), a.nft + n};
+    const int units[5] = {nw, n * a.bpi, a.nrt, (n * (P + 1) + kReduceGroup - 1) / kReduceGroup, a.nft + n};
     for (int k = 0; k < 5; ++k) {
         if (!(mask & (1 << k)) || units[k] == 0) continue;
-        if ((e = run(1 << k, units[k], false)) != cudaSuccess) return bcuda(b, e, "batched k-space pass");
+        const int grid = std::max(1, std::min(units[k], b->num_sms * b->pass_per_sm[k]));
+        kPassKernels[k]<<<grid, kBThreads, b->pass_smem[k], s>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return bcuda(b, e, "batched k-space pass");
     }
     return RBE_OK;
 }
@@ -653,6 +703,15 @@ rbe_status rbe_batch_create(double alpha, int32_t P, int32_t max_items, double m
         const size_t smem = std::max(tsm <= 48 * 1024 ? tsm : 0, (size_t)kForceSmemPerK * std::min(P, kForceStageK));
         cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         b->grid_per_sm = resident_blocks(k_batch, kBThreads, smem);
+        // the pass kernels: the tables and the sampler take the tables' shared memory, the force
+        // pass its staged frequencies
+        const size_t ts = tsm <= 48 * 1024 ? tsm : 0;
+        const size_t psm[5] = {ts, ts, 0, 0, (size_t)kForceSmemPerK * std::min(P, kForceStageK)};
+        for (int k = 0; k < 5; ++k) {
+            b->pass_smem[k] = psm[k];
+            cudaFuncSetAttribute(kPassKernels[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm[k]);
+            b->pass_per_sm[k] = resident_blocks(kPassKernels[k], kBThreads, psm[k]);
+        }
         e = cudaDeviceSynchronize();
     }
     if (e != cudaSuccess) {

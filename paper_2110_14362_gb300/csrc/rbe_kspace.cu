@@ -707,25 +707,42 @@ struct EvalShape {
 // Frequency tiling of the FP32-phase rho pass: kf frequencies per thread (1, 2 or 4) and
 // kthreads threads per block (whole warps).  Up to kRhoLatencyPairs pairs the pass is one short
 // wave bound by latency, not by issue: one frequency per thread, tiles of up to kMaxRhoThreads.
-// Above it, two frequencies per thread (one broadcast particle record feeds two pairs), tiles
-// of up to kRhoThreadsF threads.  Measured on GB300 from N K = 1e5 to 8e9, four frequencies per
-// thread never ran faster than two: equal where the tile is full, slower where a narrow tile
-// needs particle sub-streams.  A tile narrower than kRhoThreadsF threads is given particle
-// sub-streams (S = block threads / T, a power of two, at most kRhoMaxSub).
-static RhoShape rho_shape(int64_t N, int K)
+// Above it, one or two frequencies per thread (two: one broadcast particle record feeds two
+// pairs, tiles of up to kRhoThreadsF threads), whichever minimises a per-pair instruction
+// estimate: the pair's own work (base), one broadcast load per kf pairs, the particle
+// conversion spread over the tile's frequencies, divided by the fraction of lanes that hold a
+// frequency.  Measured on GB300 from N K = 1e5 to 8e9, four frequencies per thread never ran
+// faster than two (equal where the tile is full, slower where a narrow tile needs particle
+// sub-streams), so they are left to tuning (RBE_RHO_FORCE_F).  A tile narrower than
+// kRhoThreadsF threads is given particle sub-streams (S = block threads / T, a power of two, at
+// most kRhoMaxSub).
+static RhoShape rho_shape(int64_t N, int K, int accum)
 {
+    const double base = accum == RBE_RHO_COMP32 ? 12.0 : (accum == RBE_RHO_FP64 ? 14.0 : 10.0);
+    const bool latency = (double)N * (double)K <= kRhoLatencyPairs;
+    RhoShape best{1, 1, 32, 1};
+    double best_cost = 1e30;
 #ifdef RBE_RHO_FORCE_F
-    const int F = RBE_RHO_FORCE_F;
+    (void)latency;
+    for (int F : {RBE_RHO_FORCE_F}) {
 #else
-    const int F = (double)N * (double)K <= kRhoLatencyPairs ? 1 : 2;
+    for (int F : {2, 1}) {
+        if (latency && F != 1) continue;
 #endif
-    const int tmax = F == 1 ? kMaxRhoThreads : kRhoThreadsF;
-    const int ktiles = (K + tmax * F - 1) / (tmax * F);
-    const int per = (K + ktiles - 1) / ktiles;  // frequencies per tile
-    const int T = std::min(tmax, 32 * ((per + F * 32 - 1) / (F * 32)));
-    int S = 1;
-    while (T * S * 2 <= kRhoThreadsF && S * 2 <= kRhoMaxSub) S *= 2;
-    return RhoShape{F, ktiles, T * S, S};
+        const int tmax = F == 1 ? kMaxRhoThreads : kRhoThreadsF;
+        const int ktiles = (K + tmax * F - 1) / (tmax * F);
+        const int per = (K + ktiles - 1) / ktiles;  // frequencies per tile
+        const int T = std::min(tmax, 32 * ((per + F * 32 - 1) / (F * 32)));
+        const double eff = (double)K / ((double)ktiles * T * F);
+        const double cost = (base + 1.0 / F + 55.0 / (T * F)) / eff;
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            int S = 1;
+            while (T * S * 2 <= kRhoThreadsF && S * 2 <= kRhoMaxSub) S *= 2;
+            best = RhoShape{F, ktiles, T * S, S};
+        }
+    }
+    return best;
 }
 
 static rbe_status evaluate_shape(rbe_ctx ctx, int64_t N, int K, EvalShape* out)
@@ -757,7 +774,7 @@ static rbe_status evaluate_shape(rbe_ctx ctx, int64_t N, int K, EvalShape* out)
         rs.ksub = 1;
         rho_bps = std::max(1, std::min(32, rho64_threads / rs.kthreads));
     } else {
-        rs = rho_shape(N, K);
+        rs = rho_shape(N, K, ctx->rho_accum);
         const int a = ctx->rho_accum < 0 || ctx->rho_accum > 2 ? 1 : ctx->rho_accum;
         const int fi = rs.kf == 4 ? 2 : (rs.kf == 2 ? 1 : 0);
         int& bps = rho32_bps[a][fi];

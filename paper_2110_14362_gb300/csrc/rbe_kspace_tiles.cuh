@@ -591,6 +591,46 @@ __device__ __forceinline__ void freq_post(int4 mi, const double* __restrict__ c,
     *cf = make_float4(Rf, Rf * (float)mi.x, Rf * (float)mi.y, Rf * (float)mi.z);
 }
 
+// Row sums by one warp (lane-strided float-float sums over the chunks, then a fixed shuffle
+// tree; every lane ends with the total), and the outputs of row l from its sum: the batched
+// kernel sums four rows per warp and finishes 32 rows at once on the lanes of one warp, so
+// that a row's FP64 work is one lane of a warp instruction, not a warp instruction of its own.
+__device__ __forceinline__ double2 warp_row_sum(const float4* __restrict__ row, int nchunks)
+{
+    const int lane = threadIdx.x & 31;
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    for (int j = lane; j < nchunks; j += 32) {
+        const float4 v = row[j];
+        ff_add2(rh, rl, v.x, v.y);
+        ff_add2(ih, il, v.z, v.w);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float a = __shfl_xor_sync(0xffffffffu, rh, off), b = __shfl_xor_sync(0xffffffffu, rl, off);
+        const float c = __shfl_xor_sync(0xffffffffu, ih, off), d = __shfl_xor_sync(0xffffffffu, il, off);
+        ff_add2(rh, rl, a, b);
+        ff_add2(ih, il, c, d);
+    }
+    return make_double2(ff_to_double(rh, rl), ff_to_double(ih, il));
+}
+
+// Row l's outputs from its sum (re, im) and its factors c (freq_pre; unused for l == K, the
+// row of the sum of q^2).
+__device__ __forceinline__ void row_finish(int l, int K, double re, double im, int4 mi, const double* __restrict__ c,
+                                           double2* __restrict__ rho, double* __restrict__ terms,
+                                           int4* __restrict__ coef_m, float4* __restrict__ coef_f,
+                                           unsigned* __restrict__ status)
+{
+    double* t = terms + (size_t)l * 8;
+    if (l == K) {
+        t[0] = re;  // sum of q^2
+        return;
+    }
+    freq_post(mi, c, re, im, t, coef_m + l, coef_f + l);
+    rho[l] = make_double2(re, im);
+    if (!isfinite(re) || !isfinite(im)) atomicOr(status, kStatusNonFinite);
+}
+
 __device__ __forceinline__ void reduce_f32_row(int l, const float4* __restrict__ partials, int nchunks, int K,
                                                const int4* __restrict__ m,
              const double* __restrict__ w, const KState* __restrict__ ks, double2* __restrict__ rho,
@@ -617,57 +657,7 @@ __device__ __forceinline__ void reduce_f32_row(int l, const float4* __restrict__
     }
     block_sum_ff2(rh, rl, ih, il, red);
     if (threadIdx.x != 0) return;
-    double* t = terms + (size_t)l * 8;
-    const double re = ff_to_double(rh, rl), im = ff_to_double(ih, il);
-    if (l == K) {
-        t[0] = re;  // sum of q^2
-        return;
-    }
-    freq_post(mi, c, re, im, t, coef_m + l, coef_f + l);
-    rho[l] = make_double2(re, im);
-    if (!isfinite(re) || !isfinite(im)) atomicOr(status, kStatusNonFinite);
-}
-
-// The same reduction of row l by one warp (lane-strided float-float sums over the chunks, then
-// a fixed shuffle tree): the batched kernel runs eight rows per block at a time.  The per-
-// frequency terms and coefficients are the block version's formulas.
-__device__ __forceinline__ void reduce_f32_row_warp(int l, const float4* __restrict__ partials, int nchunks, int K,
-                                                    const int4* __restrict__ m, const double* __restrict__ w,
-                                                    const KState* __restrict__ ks, double2* __restrict__ rho,
-                                                    double* __restrict__ terms, int4* __restrict__ coef_m,
-                                                    float4* __restrict__ coef_f, unsigned* __restrict__ status)
-{
-    const int lane = threadIdx.x & 31;
-    int4 mi = make_int4(0, 0, 0, 0);
-    double c[8];
-    if (lane == 0 && l < K) {
-        mi = m[l];
-        freq_pre(mi, w[l], ks, c);
-    }
-    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-    const float4* row = partials + (size_t)l * nchunks;
-    for (int j = lane; j < nchunks; j += 32) {
-        const float4 v = row[j];
-        ff_add2(rh, rl, v.x, v.y);
-        ff_add2(ih, il, v.z, v.w);
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const float a = __shfl_xor_sync(0xffffffffu, rh, off), b = __shfl_xor_sync(0xffffffffu, rl, off);
-        const float cc = __shfl_xor_sync(0xffffffffu, ih, off), d = __shfl_xor_sync(0xffffffffu, il, off);
-        ff_add2(rh, rl, a, b);
-        ff_add2(ih, il, cc, d);
-    }
-    if (lane != 0) return;
-    double* t = terms + (size_t)l * 8;
-    const double re = ff_to_double(rh, rl), im = ff_to_double(ih, il);
-    if (l == K) {
-        t[0] = re;  // sum of q^2
-        return;
-    }
-    freq_post(mi, c, re, im, t, coef_m + l, coef_f + l);
-    rho[l] = make_double2(re, im);
-    if (!isfinite(re) || !isfinite(im)) atomicOr(status, kStatusNonFinite);
+    row_finish(l, K, ff_to_double(rh, rl), ff_to_double(ih, il), mi, c, rho, terms, coef_m, coef_f, status);
 }
 
 // Energy and virial: fixed-order FP64 sums of the per-frequency terms over l by one block of
