@@ -117,6 +117,24 @@ __device__ __forceinline__ uint32_t fixed_frac(double r, double inv_l)
 // (t >> 9) | 0x3f800000 in one funnel shift: the 64-bit word (0x7f : t) shifted right by 9.
 __device__ __forceinline__ uint32_t phase_bits(uint32_t t) { return __funnelshift_r(t, 0x7fu, 9); }
 
+// Sine and cosine by the MUFU approximations with subnormal inputs flushed (sin.approx.ftz,
+// cos.approx.ftz).  The phases of fixed_phase are (b - 3/2) 2 pi for b in [1, 2) with a 23-bit
+// mantissa: zero or at least 2 pi 2^-23 in magnitude, never subnormal, so the flush changes no
+// result, and the instruction needs no subnormal handling around the MUFU operation.
+__device__ __forceinline__ float mufu_sin(float x)
+{
+    float y;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float mufu_cos(float x)
+{
+    float y;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ float fixed_phase(int mx, int my, int mz, uint32_t sx, uint32_t sy, uint32_t sz)
 {
     uint32_t t = (uint32_t)mx * sx + 0x80000100u;

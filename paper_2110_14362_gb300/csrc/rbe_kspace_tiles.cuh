@@ -452,10 +452,14 @@ __device__ __forceinline__ void rho_f32_tile(int kt, int c, const void* __restri
 #pragma unroll
                 for (int f = 0; f < F; ++f) {
                     float2 e0, e1, e2, e3;  // (cos, sin) of the four phases
-                    __sincosf(fixed_phase(mv[f].x, mv[f].y, mv[f].z, r0.x, r0.y, r0.z), &e0.y, &e0.x);
-                    __sincosf(fixed_phase(mv[f].x, mv[f].y, mv[f].z, r1.x, r1.y, r1.z), &e1.y, &e1.x);
-                    __sincosf(fixed_phase(mv[f].x, mv[f].y, mv[f].z, r2.x, r2.y, r2.z), &e2.y, &e2.x);
-                    __sincosf(fixed_phase(mv[f].x, mv[f].y, mv[f].z, r3.x, r3.y, r3.z), &e3.y, &e3.x);
+                    const float th0 = fixed_phase(mv[f].x, mv[f].y, mv[f].z, r0.x, r0.y, r0.z);
+                    e0 = make_float2(mufu_cos(th0), mufu_sin(th0));
+                    const float th1 = fixed_phase(mv[f].x, mv[f].y, mv[f].z, r1.x, r1.y, r1.z);
+                    e1 = make_float2(mufu_cos(th1), mufu_sin(th1));
+                    const float th2 = fixed_phase(mv[f].x, mv[f].y, mv[f].z, r2.x, r2.y, r2.z);
+                    e2 = make_float2(mufu_cos(th2), mufu_sin(th2));
+                    const float th3 = fixed_phase(mv[f].x, mv[f].y, mv[f].z, r3.x, r3.y, r3.z);
+                    e3 = make_float2(mufu_cos(th3), mufu_sin(th3));
                     // (Re, Im) as packed pairs: each FP32x2 operation is the scalar one per lane
                     // (x - c is fma(c, -1, x), rounded once like the subtraction)
                     float2 x = __fmul2_rn(q0, e0);
@@ -480,8 +484,7 @@ __device__ __forceinline__ void rho_f32_tile(int kt, int c, const void* __restri
 #pragma unroll
                 for (int f = 0; f < F; ++f) {
                     const float th = fixed_phase(mv[f].x, mv[f].y, mv[f].z, r.x, r.y, r.z);
-                    float sn, cs;
-                    __sincosf(th, &sn, &cs);
+                    const float sn = mufu_sin(th), cs = mufu_cos(th);
                     if (ACC == RBE_RHO_FP32) {
                         re[f] = fmaf(qp, cs, re[f]);
                         im[f] = fmaf(qp, sn, im[f]);
@@ -775,7 +778,7 @@ __device__ __forceinline__ void force_f32_block(int64_t blk, const void* __restr
 #pragma unroll
                     for (int p = 0; p < kForcePPT; ++p) {
                         // g = R sin(theta - arg rho) = beta (Re rho sin theta - Im rho cos theta)
-                        const float g = __sinf(fixed_phase_off(a.x, a.y, a.z, pr[p].x, pr[p].y, pr[p].z,
+                        const float g = mufu_sin(fixed_phase_off(a.x, a.y, a.z, pr[p].x, pr[p].y, pr[p].z,
                                                                (uint32_t)a.w));
                         gx[p] = fmaf(g, b.y, gx[p]);
                         gy[p] = fmaf(g, b.z, gy[p]);
