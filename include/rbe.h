@@ -550,8 +550,9 @@ rbe_status rbe_kspace_forces_virial_batched(rbe_batch b, const rbe_batch_item* i
  * the chosen shapes.  Synchronous. */
 rbe_status rbe_batch_autotune(rbe_batch b, const rbe_batch_item* items, int32_t n, int32_t reps, double* best_ms);
 
-/* 1 (default): one persistent cooperative launch per evaluation; 0: one launch per pass (the same
- * tile bodies and results, bit for bit).  RBE_EINVAL for other values. */
+/* 1 (default): one persistent cooperative launch per evaluation; 0: one launch per pass, each of
+ * a kernel compiled for that pass alone (fewer registers, more resident blocks; the same tile
+ * bodies and results, bit for bit).  RBE_EINVAL for other values. */
 rbe_status rbe_batch_set_persistent(rbe_batch b, int32_t enable);
 
 /* Test of the failure path of the persistent launch (no counterpart in the paper): with

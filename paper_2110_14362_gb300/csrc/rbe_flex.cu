@@ -730,7 +730,9 @@ k_flex_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, co
                 }
                 const R inv_r2 = inv_r * inv_r;
                 const R coul = qk * qi * qj * inv_r;
-                const R er = erfc(sa * r);
+                R er;
+                if constexpr (kF64) er = erfc(sa * r);
+                else er = erfc_nr(sa * r);
                 ec += coul * er;
                 R f = coul * (er + two_sa_pi * r * ex) * inv_r2;
                 if (lj) {

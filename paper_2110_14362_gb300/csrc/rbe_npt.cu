@@ -662,7 +662,8 @@ k_cl_sort(const CellConsts* __restrict__ cc, const int* __restrict__ cnt, const 
 //   Evaluation: every 32 buffered candidates, one per lane; the FP64 path recomputes the
 //   distance from the FP64 positions and applies the exact cutoff.
 //   f = -(dU/dr)/r for U = qqr2e q_i q_j erfc(sqrt(a) r)/r + 4 eps ((s/r)^12 - (s/r)^6); the
-//   lane sums go through a fixed shuffle tree, so the result does not depend on timing.
+//   lane sums go through a fixed shuffle tree, so the result does not depend on timing.  The
+//   FP32 path evaluates erfc by a published Chebyshev fit (erfc_nr).
 // Each pair is visited from both ends: energies and the virial take half.  The warps stride
 // over the slots (grid-stride); per-block partials {W_r, E_coul, E_lj} at slots 1..3, or with
 // kDiag (rectangular cells) {W_xx, W_yy, W_zz, E_coul, E_lj} at slots 3..7 (W_jj = sum f d_j^2).  A box that
@@ -849,7 +850,9 @@ k_pair(int64_t N, const CellConsts* __restrict__ cc, const PairConst pc, const i
                 }
                 const R inv_r2 = inv_r * inv_r;
                 const R coul = qk * qi * qj * inv_r;  // qqr2e q_i q_j / r
-                const R er = erfc(sa * r);
+                R er;
+                if constexpr (kF64) er = erfc(sa * r);
+                else er = erfc_nr(sa * r);
                 ec += coul * er;
                 R f = coul * (er + two_sa_pi * r * ex) * inv_r2;
                 if (lj) {

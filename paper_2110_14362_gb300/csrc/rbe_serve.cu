@@ -359,11 +359,13 @@ static void evict(rbe_server_s* s, Slot& sl, int state, rbe_status st, const std
 }
 
 // ---------------------------------------------------------------------------------
-// Lockstep groups (cfg.batched): every resident replica advances by the same chunk; per step
-// the group stream forks to the replicas' streams (cell update and drift), joins them for one
-// persistent batched k-space launch over the group (each item reads its box and step index
-// from its replica's cell block and writes into its context's k-space buffers and status
-// word), and the replicas run their real space beside it and their finishing kernels after it.
+// Lockstep groups (cfg.batched): every resident replica advances by the same chunk.  The group
+// stream forks to the replicas' streams once per chunk; per step each replica moves (cell
+// update and drift), the group stream joins the moves for one persistent batched k-space
+// launch over the group (each item reads its box and step index from its replica's cell block
+// and writes into its context's k-space buffers and status word), and the replicas run their
+// real space beside it and their finishing kernels after it; the group stream joins them at
+// the end of the chunk.
 
 static rbe_status ensure_group_batch(rbe_server_s* s, int m)
 {
@@ -399,13 +401,17 @@ static rbe_status enqueue_group_steps(rbe_server_s* s, int32_t n)
     const int m = (int)s->members.size();
     cudaError_t e = cudaSuccess;
     rbe_status st = RBE_OK;
-    for (int32_t k = 0; k < n; ++k) {
-        if ((e = cudaEventRecord(s->gfork, s->gstream)) != cudaSuccess) break;
+    // fork once per chunk: a replica's next move follows its own finishing pass in stream order,
+    // and that pass waited for the group's k-space, so the steps need no join of their own
+    // beyond the k-space's (which needs every replica's moved positions and cell)
+    if ((e = cudaEventRecord(s->gfork, s->gstream)) == cudaSuccess)
+        for (int j = 0; j < m && e == cudaSuccess; ++j)
+            e = cudaStreamWaitEvent(s->slots[s->members[j]].stream, s->gfork, 0);
+    for (int32_t k = 0; k < n && e == cudaSuccess; ++k) {
         for (int j = 0; j < m && e == cudaSuccess; ++j) {
             Slot& sl = s->slots[s->members[j]];
-            if ((e = cudaStreamWaitEvent(sl.stream, s->gfork, 0)) != cudaSuccess) break;
             if ((st = npt_step_phase(sl.ctx, &sl.sys, kNptPhaseMove)) != RBE_OK) return sfail(s, st, rbe_last_error(sl.ctx));
-            if ((e = cudaEventRecord(s->ev_a[s->members[j]], sl.stream)) != cudaSuccess) break;
+            e = cudaEventRecord(s->ev_a[s->members[j]], sl.stream);
         }
         for (int j = 0; j < m && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(s->gstream, s->ev_a[s->members[j]], 0);
         if (e != cudaSuccess) break;
@@ -414,14 +420,17 @@ static rbe_status enqueue_group_steps(rbe_server_s* s, int32_t n)
         if ((e = cudaEventRecord(s->gk, s->gstream)) != cudaSuccess) break;
         for (int j = 0; j < m && e == cudaSuccess; ++j) {
             Slot& sl = s->slots[s->members[j]];
+            // the real space needs only this replica's moved positions: it runs beside the k-space
             if ((st = npt_step_phase(sl.ctx, &sl.sys, kNptPhaseReal)) != RBE_OK) return sfail(s, st, rbe_last_error(sl.ctx));
             if ((e = cudaStreamWaitEvent(sl.stream, s->gk, 0)) != cudaSuccess) break;
             if ((st = npt_step_phase(sl.ctx, &sl.sys, kNptPhaseFinish)) != RBE_OK)
                 return sfail(s, st, rbe_last_error(sl.ctx));
-            e = cudaEventRecord(s->ev_b[s->members[j]], sl.stream);
         }
-        for (int j = 0; j < m && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(s->gstream, s->ev_b[s->members[j]], 0);
-        if (e != cudaSuccess) break;
+    }
+    // join once per chunk
+    for (int j = 0; j < m && e == cudaSuccess; ++j) {
+        if ((e = cudaEventRecord(s->ev_b[s->members[j]], s->slots[s->members[j]].stream)) != cudaSuccess) break;
+        e = cudaStreamWaitEvent(s->gstream, s->ev_b[s->members[j]], 0);
     }
     if (e != cudaSuccess) return sfail(s, RBE_ECUDA, std::string("group chunk: ") + cudaGetErrorString(e));
     return RBE_OK;
