@@ -528,10 +528,11 @@ rbe_status rbe_batch_create(double alpha, int32_t P, int32_t max_items, double m
 rbe_status rbe_batch_destroy(rbe_batch b);
 /* Stream of later evaluations (a cudaStream_t; NULL = legacy default); synchronises the old one. */
 rbe_status rbe_batch_set_stream(rbe_batch b, void* stream);
-/* Tile shapes: rho_k frequencies per rho tile (32, 64, 128 or 256; a block of 256 threads runs
- * 256 / rho_k particle sub-streams of the tile), rho_chunk particles per rho chunk (>= 32),
- * force_block particles per force tile (a positive multiple of 128).  All three 0 restores the
- * defaults. */
+/* Tile shapes: rho_k frequencies per rho tile (16 to 256; a block of 256 threads runs
+ * floor(256 / rho_k) particle sub-streams of the tile, the threads beyond them idle), rho_chunk
+ * particles per rho chunk (>= 32), force_block particles per force tile (a positive multiple of
+ * 128).  All three 0 restores the defaults (the rho tile that keeps the most lanes busy for this
+ * P, chunks of 256, force tiles of 256). */
 rbe_status rbe_batch_set_tiles(rbe_batch b, int32_t rho_k, int32_t rho_chunk, int32_t force_block);
 rbe_status rbe_batch_get_tiles(rbe_batch b, int32_t* rho_k, int32_t* rho_chunk, int32_t* force_block);
 

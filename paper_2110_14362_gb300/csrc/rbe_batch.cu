@@ -57,6 +57,8 @@ struct BItem {
 // frequencies of one item.
 constexpr int kBThreads = kForceThreads;
 constexpr int kSampleBlock = kBThreads;
+constexpr int kMinRhoK = 16;        // fewest frequency lanes of a rho tile (at most 16 sub-streams)
+constexpr int kRhoKCandidates = 6;  // frequency-tile shapes the autotuner times
 // Bounded wait of the grid barrier: one second by the GPU's global timer (and at most
 // kBarrierSpins polls), then the block gives up and the evaluation reports RBE_ETIMEOUT.
 constexpr unsigned long long kBarrierNs = 1000000000ull;
@@ -89,7 +91,8 @@ struct BArgs {
     int4* m;
     double* w;
     const int4* rtiles;         // (item, frequency tile, chunk)
-    int nrt, S;                 // rho tiles; particle sub-streams of a rho block (kBThreads / rho_k)
+    int nrt, S, T;              // rho tiles; particle sub-streams of a rho block (kBThreads / rho_k) and
+                                // frequency lanes of each (rho_k)
     float4* part;
     double2* rho;
     double* terms;
@@ -188,7 +191,7 @@ __device__ __forceinline__ void pass_rho(const BArgs& a)
         const int4 tl = a.rtiles[t];
         const BItem& it = a.items[tl.x];
         rho_f32_tile<RBE_RHO_COMP32, 1>(tl.y, tl.z, it.pos, it.q, it.N, a.ks + tl.x, a.m + (size_t)tl.x * a.P, a.P,
-                                        it.chunk_len, it.nchunks, a.part + it.part_off, it.status, a.S);
+                                        it.chunk_len, it.nchunks, a.part + it.part_off, it.status, a.S, a.T);
         __syncthreads();
     }
 }
@@ -414,21 +417,53 @@ bool capturing(cudaStream_t s)
 bool valid_tiles(int P, int rho_k, int rho_chunk, int force_block)
 {
     // a rho tile of rho_k frequencies fills a block of kBThreads threads with kBThreads / rho_k
-    // particle sub-streams
-    return (rho_k == 32 || rho_k == 64 || rho_k == 128 || rho_k == 256) && rho_chunk >= 32 &&
-           rho_chunk <= (1 << 24) && force_block >= kForceRound && force_block % kForceRound == 0 &&
-           force_block <= (1 << 24) && P >= 1;
+    // particle sub-streams (the threads beyond them idle)
+    return rho_k >= kMinRhoK && rho_k <= kBThreads && rho_chunk >= 32 && rho_chunk <= (1 << 24) &&
+           force_block >= kForceRound && force_block % kForceRound == 0 && force_block <= (1 << 24) && P >= 1;
 }
 
-// The tile shapes the planner uses when none were set: frequency tiles of the smallest power
-// of two (32 to 256) that covers P in the fewest tiles, chunks of 256 particles.
+// Busy fraction of a rho block's lanes with frequency tiles of k lanes: the tiles' share of real
+// frequencies times the share of the block's threads in whole sub-streams.
+static double rho_lane_efficiency(int P, int k)
+{
+    const int ktiles = (P + k - 1) / k;
+    const int S = kBThreads / k;
+    return (double)P / ((double)ktiles * k) * (double)(S * k) / kBThreads;
+}
+
+// Frequency-tile candidates for the autotuner: P split evenly into 1 to 16 tiles (lane counts
+// that need not be powers of two: P = 100 as two tiles of 50 lanes in five sub-streams keeps
+// 250 of 256 threads on real frequencies) and the powers of two 32 to 256; at most
+// kRhoKCandidates of them, ranked by lane efficiency less 0.01 per frequency tile (every tile
+// stages and converts the particles again).  The pass is bound by instruction issue, so the
+// busier lanes pay for the extra re-staging and sub-streams rather than run faster (measured
+// at P = 100: 50-lane and 128-lane tiles equal); the timing decides.
+static double rho_k_score(int P, int k) { return rho_lane_efficiency(P, k) - 0.01 * ((P + k - 1) / k); }
+
+static std::vector<int> rho_k_candidates(int P)
+{
+    std::vector<int> ks;
+    for (int kt = 1; kt <= 16; ++kt) {
+        const int k = (P + kt - 1) / kt;
+        if (k >= kMinRhoK && k <= kBThreads) ks.push_back(k);
+    }
+    for (int k : {32, 64, 128, 256}) ks.push_back(k);
+    std::sort(ks.begin(), ks.end());
+    ks.erase(std::unique(ks.begin(), ks.end()), ks.end());
+    std::stable_sort(ks.begin(), ks.end(), [P](int x, int y) {
+        const double sx = rho_k_score(P, x), sy = rho_k_score(P, y);
+        if (sx != sy) return sx > sy;
+        return x > y;
+    });
+    if ((int)ks.size() > kRhoKCandidates) ks.resize(kRhoKCandidates);
+    return ks;
+}
+
+// The tile shapes the planner uses when none were set: the frequency tile of the best lane
+// efficiency, chunks of 256 particles.
 void default_tiles(rbe_batch b)
 {
-    const int ktiles = (b->P + kBThreads - 1) / kBThreads;
-    const int per = (b->P + ktiles - 1) / ktiles;
-    int k = 32;
-    while (k < per) k *= 2;
-    b->rho_k = k;
+    b->rho_k = rho_k_candidates(b->P).front();
     b->rho_chunk = 256;
     b->force_block = 2 * kForceRound;
 }
@@ -581,6 +616,7 @@ rbe_status launch(rbe_batch b, int n, int mask)
     a.rtiles = b->d_rtiles;
     a.nrt = b->n_rtiles;
     a.S = kBThreads / b->rho_k;
+    a.T = b->rho_k;
     a.part = b->d_part;
     a.rho = b->d_rho;
     a.terms = b->d_terms;
@@ -751,7 +787,7 @@ rbe_status rbe_batch_set_tiles(rbe_batch b, int32_t rho_k, int32_t rho_chunk, in
         return RBE_OK;
     }
     if (!valid_tiles(b->P, rho_k, rho_chunk, force_block))
-        return bfail(b, RBE_EINVAL, "tiles: rho_k a multiple of 32 in [32, 256], rho_chunk >= 32, "
+        return bfail(b, RBE_EINVAL, "tiles: rho_k in [16, 256], rho_chunk >= 32, "
                                     "force_block a positive multiple of 128");
     b->rho_k = rho_k;
     b->rho_chunk = rho_chunk;
@@ -816,7 +852,7 @@ rbe_status rbe_batch_autotune(rbe_batch b, const rbe_batch_item* items, int32_t 
         *ms /= (float)reps;
         return RBE_OK;
     };
-    const int rho_ks[] = {32, 64, 128, 256};
+    const std::vector<int> rho_ks = rho_k_candidates(b->P);
     const int chunks[] = {64, 128, 256, 512, 1024, 2048};
     const int fblocks[] = {128, 256, 512, 1024, 2048};
     rbe_status st = RBE_OK;
@@ -828,8 +864,6 @@ rbe_status rbe_batch_autotune(rbe_batch b, const rbe_batch_item* items, int32_t 
     if (st == RBE_OK) st = launch(b, n, 31);
     for (int k : rho_ks) {
         if (st != RBE_OK) break;
-        const int ktiles = (b->P + k - 1) / k;
-        if (ktiles > 1 && k < 32 * ((((b->P + ktiles - 1) / ktiles) + 31) / 32)) continue;
         for (int c : chunks) {
             b->rho_k = k;
             b->rho_chunk = c;

@@ -371,28 +371,36 @@ template <int ACC, int F, bool XYZQ = false>
 __device__ __forceinline__ void rho_f32_tile(int kt, int c, const void* __restrict__ pos,
                                              const double* __restrict__ q, int64_t N, const KState* __restrict__ ks,
           const int4* __restrict__ m, int K, int64_t chunk_len, int nchunks, float4* __restrict__ partials,
-          unsigned* __restrict__ status, int S = 1)
+          unsigned* __restrict__ status, int S = 1, int T_lanes = 0)
 {
     __shared__ uint4 sp[kRhoStage];
     __shared__ float red[2][32];
     __shared__ unsigned bad;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int T = nt / S, j = tid % T, ss = tid / T;  // frequency lane, particle sub-stream
+    // T frequency lanes per sub-stream (by default the block divided evenly; any T with S T <= the
+    // block's threads otherwise, the threads beyond S T idle), S particle sub-streams
+    const int T = T_lanes > 0 ? T_lanes : nt / S, j = tid % T, ss = tid / T;
+    const bool act = ss < S;
     const int lbase = kt * T * F + j;
-    const int share = kRhoStage / S, p0 = ss * share;  // the sub-stream's particles of a tile
+    // each sub-stream's share of a staged tile is a multiple of four particles (the compensated
+    // sums take them four at a time), so that no group reaches into the next share
+    const int share = 4 * (kRhoStage / (4 * S)), p0 = ss * share;
+    const int stage = S * share;  // particles staged per tile (kRhoStage for S = 1, 2, 4)
     const FixScale scx = fs(ks->sc[0]), scy = fs(ks->sc[1]), scz = fs(ks->sc[2]);
     // the float-float sums across staged tiles, (Re hi, Re lo, Im hi, Im lo) per frequency, live
     // in shared memory: they change once per tile, and registers go to the pair loop
     __shared__ float4 acc_s[(F == 1 ? kMaxRhoThreads : kRhoThreadsF) * F];
+    if (act) {
 #pragma unroll
-    for (int f = 0; f < F; ++f) acc_s[(ss * F + f) * T + j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int f = 0; f < F; ++f) acc_s[(ss * F + f) * T + j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     float q2h = 0.f, q2l = 0.f;
     const int64_t start = (int64_t)c * chunk_len;
     const int64_t end = min(N, start + chunk_len);
     if (tid == 0) bad = 0u;
     __syncthreads();
     // the first tile is staged before waiting for the sampler (inputs only)
-    for (int u = tid; u < kRhoStage; u += nt) {
+    for (int u = tid; u < stage; u += nt) {
         const int64_t i = start + u;
         uint4 rec = make_uint4(0u, 0u, 0u, 0u);
         if (i < end) {
@@ -410,10 +418,10 @@ __device__ __forceinline__ void rho_f32_tile(int kt, int c, const void* __restri
         const int l = lbase + f * T;
         mv[f] = l < K ? m[l] : make_int4(0, 0, 0, 0);
     }
-    for (int64_t base = start; base < end; base += kRhoStage) {
+    for (int64_t base = start; base < end; base += stage) {
         if (base != start) {
             __syncthreads();  // every thread is done with the previous tile
-            for (int u = tid; u < kRhoStage; u += nt) {
+            for (int u = tid; u < stage; u += nt) {
                 const int64_t i = base + u;
                 uint4 rec = make_uint4(0u, 0u, 0u, 0u);
                 if (i < end) {
@@ -425,6 +433,7 @@ __device__ __forceinline__ void rho_f32_tile(int kt, int c, const void* __restri
             }
         }
         __syncthreads();
+        if (!act) continue;  // idle threads only stage
         // this sub-stream's particles of the tile: [p0, p0 + n_here)
         const int n_here = (int)max((int64_t)0, min((int64_t)share, end - base - p0));
         float re[F], im[F], cre[F], cim[F];

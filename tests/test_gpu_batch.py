@@ -102,7 +102,8 @@ def test_item_alone_equals_in_mix():
         assert np.array_equal(a, c)
 
 
-@pytest.mark.parametrize("tiles", [(32, 64, 128), (64, 100, 384), (128, 2048, 1024), (256, 33, 128)])
+@pytest.mark.parametrize("tiles", [(32, 64, 128), (64, 100, 384), (128, 2048, 1024), (256, 33, 128),
+                                   (50, 64, 128), (75, 256, 256), (16, 100, 128), (150, 1000, 512)])
 def test_tile_shapes(tiles):
     systems = _systems([1, 999, 5000], seed0=11)
     ref = _dev(systems)
@@ -128,7 +129,7 @@ def test_autotune_then_evaluate():
         ms = b.autotune(items, reps=2)
         assert ms > 0
         k, c, f = b.tiles()
-        assert k % 32 == 0 and 32 <= k <= 256 and c >= 32 and f % 128 == 0
+        assert 16 <= k <= 256 and c >= 32 and f % 128 == 0
         b.evaluate(items)
         b.sync()
     for sy, it in zip(systems, items):
@@ -164,9 +165,10 @@ def test_batch_argument_errors():
     systems = _systems([10, 20])
     items = _dev(systems)
     with rbe.Batch(ALPHA, 64, 2, 50.0) as b:
-        with pytest.raises(rbe.RBEError) as e:
-            b.set_tiles(48, 64, 128)
-        assert e.value.status == rbe.RBE_EINVAL
+        for bad in ((8, 64, 128), (257, 64, 128), (64, 16, 128), (64, 64, 100)):
+            with pytest.raises(rbe.RBEError) as e:
+                b.set_tiles(*bad)
+            assert e.value.status == rbe.RBE_EINVAL
         arr = b.items(items)
         arr[0].N = 0
         with pytest.raises(rbe.RBEError):
