@@ -63,9 +63,10 @@ typedef enum {
 typedef enum {
     RBE_RHO_FP64 = 0,    /* FP32-phase path: rho accumulated per pair in FP64 */
     RBE_RHO_COMP32 = 1,  /* FP32-phase path: compensated FP32 summation within a staged tile (FP32
-                            partial sums of four consecutive particles added with Kahan's
+                            partial sums of 16 consecutive particles added with Kahan's
                             compensation: a rounding error that does not grow with the particle
-                            count), float-float (about 48 bits) across tiles (default) */
+                            count, to first order at most 17 eps sum |q| per tile), float-float
+                            (about 48 bits) across tiles (default) */
     RBE_RHO_FP32 = 2     /* FP32-phase path: plain FP32 within a staged tile, float-float across (faster;
                             outside the compensated-or-FP64 rule of the default) */
 } rbe_rho_accum;

@@ -358,7 +358,7 @@ __device__ __forceinline__ uint4 load_record(const void* __restrict__ pos, const
 // feeds F pairs.  The sub-streams let a small frequency tile fill a block of several warps;
 // their sums are added in sub-stream order at the end.  No FP64 instruction runs per particle
 // or per pair: sums across staged tiles are float-float.
-// ACC: RBE_RHO_COMP32 (compensated FP32: four-term partial sums added with Kahan's
+// ACC: RBE_RHO_COMP32 (compensated FP32: 16-term partial sums added with Kahan's
 //      compensation, an error bound that does not grow with the particle count),
 //      RBE_RHO_FP32 (plain FP32 within a tile), RBE_RHO_FP64 (FP64 per pair; slow on GB300).
 // Partials: float4 (Re hi, Re lo, Im hi, Im lo) at [l * nchunks + c]; row K holds the
@@ -366,6 +366,13 @@ __device__ __forceinline__ uint4 load_record(const void* __restrict__ pos, const
 // kernel that wrote them (k_tables) runs before the sampler, which is this launch's
 // predecessor, and the sampler starts only after k_tables has completed.
 constexpr int kRhoStage = 256;  // particles staged per tile
+// Particles per FP32 partial sum of the compensated path: 16 (one compensated addition per 16
+// pairs; groups of 4 and 8 measured 7 % and 3 % slower at N = 4e6, P = 2000).
+#ifndef RBE_RHO_GROUP
+#define RBE_RHO_GROUP 16
+#endif
+constexpr int kRhoGroup = RBE_RHO_GROUP;
+static_assert(kRhoGroup == 4 || kRhoGroup == 8 || kRhoGroup == 16, "groups of 4, 8 or 16 particles");
 
 template <int ACC, int F, bool XYZQ = false>
 __device__ __forceinline__ void rho_f32_tile(int kt, int c, const void* __restrict__ pos,
@@ -382,10 +389,10 @@ __device__ __forceinline__ void rho_f32_tile(int kt, int c, const void* __restri
     const int T = T_lanes > 0 ? T_lanes : nt / S, j = tid % T, ss = tid / T;
     const bool act = ss < S;
     const int lbase = kt * T * F + j;
-    // each sub-stream's share of a staged tile is a multiple of four particles (the compensated
-    // sums take them four at a time), so that no group reaches into the next share
-    const int share = 4 * (kRhoStage / (4 * S)), p0 = ss * share;
-    const int stage = S * share;  // particles staged per tile (kRhoStage for S = 1, 2, 4)
+    // each sub-stream's share of a staged tile is a multiple of kRhoGroup particles (the
+    // compensated sums take them a group at a time), so that no group reaches into the next share
+    const int share = kRhoGroup * (kRhoStage / (kRhoGroup * S)), p0 = ss * share;
+    const int stage = S * share;  // particles staged per tile (kRhoStage for S = 1, 2, 4, 8, 16)
     const FixScale scx = fs(ks->sc[0]), scy = fs(ks->sc[1]), scz = fs(ks->sc[2]);
     // the float-float sums across staged tiles, (Re hi, Re lo, Im hi, Im lo) per frequency, live
     // in shared memory: they change once per tile, and registers go to the pair loop
@@ -444,39 +451,49 @@ __device__ __forceinline__ void rho_f32_tile(int kt, int c, const void* __restri
             are[f] = aim[f] = 0.0;
         }
         if (ACC == RBE_RHO_COMP32) {
-            // Compensated summation: the terms of four consecutive particles form an FP32 partial
-            // sum, and the partial sums are added with Kahan's compensation (the rounding error
-            // of each addition carried into the next), so the error does not grow with the
-            // number of particles: to first order at most 5 eps sum_i |q_i| (3 eps from the
-            // four-term partials, 2 eps from the compensated additions).  Records past the end
-            // of the chunk are staged as zeros (q = 0), so the last group of four is padded.
-            const int n4 = (n_here + 3) & ~3;
-            for (int p = p0; p < p0 + n4; p += 4) {
-                const uint4 r0 = sp[p], r1 = sp[p + 1], r2 = sp[p + 2], r3 = sp[p + 3];
-                const float2 q0 = make_float2(__uint_as_float(r0.w), __uint_as_float(r0.w));
-                const float2 q1 = make_float2(__uint_as_float(r1.w), __uint_as_float(r1.w));
-                const float2 q2 = make_float2(__uint_as_float(r2.w), __uint_as_float(r2.w));
-                const float2 q3 = make_float2(__uint_as_float(r3.w), __uint_as_float(r3.w));
+            // Compensated summation: the terms of kRhoGroup consecutive particles form an FP32
+            // partial sum (four at a time from the staged records), and the partial sums are
+            // added with Kahan's compensation (the rounding error of each addition carried into
+            // the next), so the error does not grow with the number of particles: to first
+            // order at most (kRhoGroup + 1) eps sum_i |q_i| (kRhoGroup - 1 eps from the
+            // partials, 2 eps from the compensated additions; 17 eps for groups of 16).
+            // Records past the end of the chunk are staged as zeros (q = 0), so the last group
+            // is padded.
+            const int ng = (n_here + kRhoGroup - 1) & ~(kRhoGroup - 1);
+            for (int p = p0; p < p0 + ng; p += kRhoGroup) {
+                float2 x[F];
+#pragma unroll
+                for (int h = 0; h < kRhoGroup; h += 4) {
+                    const uint4 r0 = sp[p + h], r1 = sp[p + h + 1], r2 = sp[p + h + 2], r3 = sp[p + h + 3];
+                    const float2 q0 = make_float2(__uint_as_float(r0.w), __uint_as_float(r0.w));
+                    const float2 q1 = make_float2(__uint_as_float(r1.w), __uint_as_float(r1.w));
+                    const float2 q2 = make_float2(__uint_as_float(r2.w), __uint_as_float(r2.w));
+                    const float2 q3 = make_float2(__uint_as_float(r3.w), __uint_as_float(r3.w));
+#pragma unroll
+                    for (int f = 0; f < F; ++f) {
+                        float2 e0, e1, e2, e3;  // (cos, sin) of the four phases
+                        const float th0 = fixed_phase(mv[f].x, mv[f].y, mv[f].z, r0.x, r0.y, r0.z);
+                        e0 = make_float2(mufu_cos(th0), mufu_sin(th0));
+                        const float th1 = fixed_phase(mv[f].x, mv[f].y, mv[f].z, r1.x, r1.y, r1.z);
+                        e1 = make_float2(mufu_cos(th1), mufu_sin(th1));
+                        const float th2 = fixed_phase(mv[f].x, mv[f].y, mv[f].z, r2.x, r2.y, r2.z);
+                        e2 = make_float2(mufu_cos(th2), mufu_sin(th2));
+                        const float th3 = fixed_phase(mv[f].x, mv[f].y, mv[f].z, r3.x, r3.y, r3.z);
+                        e3 = make_float2(mufu_cos(th3), mufu_sin(th3));
+                        // (Re, Im) as packed pairs: each FP32x2 operation is the scalar one per lane
+                        x[f] = h == 0 ? __fmul2_rn(q0, e0) : __ffma2_rn(q0, e0, x[f]);
+                        x[f] = __ffma2_rn(q1, e1, x[f]);
+                        x[f] = __ffma2_rn(q2, e2, x[f]);
+                        x[f] = __ffma2_rn(q3, e3, x[f]);
+                    }
+                }
                 const float2 m1 = make_float2(-1.f, -1.f);
 #pragma unroll
                 for (int f = 0; f < F; ++f) {
-                    float2 e0, e1, e2, e3;  // (cos, sin) of the four phases
-                    const float th0 = fixed_phase(mv[f].x, mv[f].y, mv[f].z, r0.x, r0.y, r0.z);
-                    e0 = make_float2(mufu_cos(th0), mufu_sin(th0));
-                    const float th1 = fixed_phase(mv[f].x, mv[f].y, mv[f].z, r1.x, r1.y, r1.z);
-                    e1 = make_float2(mufu_cos(th1), mufu_sin(th1));
-                    const float th2 = fixed_phase(mv[f].x, mv[f].y, mv[f].z, r2.x, r2.y, r2.z);
-                    e2 = make_float2(mufu_cos(th2), mufu_sin(th2));
-                    const float th3 = fixed_phase(mv[f].x, mv[f].y, mv[f].z, r3.x, r3.y, r3.z);
-                    e3 = make_float2(mufu_cos(th3), mufu_sin(th3));
-                    // (Re, Im) as packed pairs: each FP32x2 operation is the scalar one per lane
-                    // (x - c is fma(c, -1, x), rounded once like the subtraction)
-                    float2 x = __fmul2_rn(q0, e0);
-                    x = __ffma2_rn(q1, e1, x);
-                    x = __ffma2_rn(q2, e2, x);
-                    x = __ffma2_rn(q3, e3, x);
+                    // the group's partial sum added with compensation (x - c is fma(c, -1, x),
+                    // rounded once like the subtraction)
                     const float2 acc = make_float2(re[f], im[f]), cmp = make_float2(cre[f], cim[f]);
-                    const float2 y = __ffma2_rn(cmp, m1, x);
+                    const float2 y = __ffma2_rn(cmp, m1, x[f]);
                     const float2 t = __fadd2_rn(acc, y);
                     const float2 c = __ffma2_rn(y, m1, __ffma2_rn(acc, m1, t));
                     re[f] = t.x;
