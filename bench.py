@@ -99,24 +99,30 @@ def max_over_ranks(world, x: float) -> float:
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms while running, each sample
+    time-stamped, so that the summary can keep the samples of the timed region only."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
+        self.window = None  # (t0, t1) in time.time() seconds: the timed region
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
         return self
+
+    def mark(self, t0: float, t1: float):
+        """The timed region, as time.time() values."""
+        self.window = (t0, t1)
 
     def __exit__(self, *exc):
         self.lines = []
@@ -129,25 +135,46 @@ class ClockSampler:
                 out, _ = self.proc.communicate()
             self.lines = [ln for ln in out.splitlines() if ln.strip()]
 
+    @staticmethod
+    def _epoch(stamp: str):
+        # nvidia-smi writes local time as "YYYY/MM/DD HH:MM:SS.mmm"
+        try:
+            base, _, frac = stamp.partition(".")
+            return time.mktime(time.strptime(base, "%Y/%m/%d %H:%M:%S")) + (float("0." + frac) if frac else 0.0)
+        except ValueError:
+            return None
+
     def summary(self):
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for ln in getattr(self, "lines", []):
             parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                rows.append((self._epoch(parts[0]), float(parts[2]), float(parts[3]), parts[6:10]))
             except ValueError:
                 continue
-            for name, flag in zip(names, parts[5:9]):
+        label = "whole measurement"
+        if self.window is not None:
+            # the samples inside the timed region (the sampler's clock and time.time() agree to
+            # well under the 50 ms period); a region shorter than the period falls back to the
+            # samples within 0.25 s of it
+            t0, t1 = self.window
+            for pad, name in ((0.05, "timed region"), (0.25, "within 0.25 s of the timed region")):
+                inside = [r for r in rows if r[0] is not None and t0 - pad <= r[0] <= t1 + pad]
+                if inside:
+                    rows, label = inside, name
+                    break
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for name, flag in zip(names, r[3]):
                 if flag.lower() in ("active", "1"):
                     reasons.add(name)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median([r[1] for r in rows]), "sm_max_mhz": max(r[2] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows), "window": label}
 
 
 ACCUM_NAMES = {0: "fp64 per pair", 1: "compensated fp32 (Kahan) per tile, float-float across tiles",
@@ -182,6 +209,7 @@ def measure_kspace(rbe, s, args, world, rank, local, precision, accum, with_fp64
         barrier(world)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        e0 = time.time()
         for k in range(steps):
             flush.fill_(float(k))
             evs[k][0].record(stream)
@@ -190,12 +218,15 @@ def measure_kspace(rbe, s, args, world, rank, local, precision, accum, with_fp64
         torch.cuda.synchronize()
         barrier(world)
         wall = time.perf_counter() - t0
+        window = (e0, time.time())
         ctx.sync()
-        return [a.elapsed_time(b) for a, b in evs], wall
+        return [a.elapsed_time(b) for a, b in evs], wall, window
 
     ctx = rbe.Context(s.box, s.alpha, s.P, seed, precision, accum)
     with ClockSampler(local) as clk:
-        ms, wall = timed_loop(ctx, args.steps, args.warmup, 0)
+        time.sleep(0.3)  # the sampler's first samples before the warm-up
+        ms, wall, window = timed_loop(ctx, args.steps, args.warmup, 0)
+        clk.mark(*window)
     clocks = clk.summary()
     dev_s_max = max_over_ranks(world, sum(ms) / 1e3)
     value = world * args.steps * pairs / dev_s_max
@@ -233,7 +264,7 @@ def measure_kspace(rbe, s, args, world, rank, local, precision, accum, with_fp64
     if with_fp64 and precision == rbe.RBE_FP32_PHASE:
         ctx64 = rbe.Context(s.box, s.alpha, s.P, seed, rbe.RBE_FP64)
         n64 = 2 if pairs > 1e9 else max(2, min(args.steps, 5))
-        ms64, _ = timed_loop(ctx64, n64, 1 if pairs > 1e9 else 2, 50_000)
+        ms64, _, _ = timed_loop(ctx64, n64, 1 if pairs > 1e9 else 2, 50_000)
         other = {"precision": "fp64", "value": pairs / (sum(ms64) / len(ms64) / 1e3), "unit": UNIT,
                  "ms_per_step": sum(ms64) / len(ms64), "steps": n64}
         # accuracy of the timed FP32-phase path against the FP64 path on the same frequencies

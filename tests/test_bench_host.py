@@ -65,3 +65,32 @@ def test_reference_arm_other_ranks_print_nothing(capsys):
     args = argparse.Namespace(workload="snapshot", steps=1, warmup=3)
     bench.run_reference(args, world=2, rank=1)
     assert capsys.readouterr().out == ""
+
+
+def test_clock_sampler_keeps_the_timed_region():
+    """The clock summary takes the samples inside the timed region (time-stamped nvidia-smi
+    lines), falls back to those within 0.25 s of a region shorter than the sampling period, and
+    reports the throttle reasons of the samples it kept."""
+    import time as _time
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    clk = bench.ClockSampler(0)
+
+    def line(t, mhz, thermal="Not Active"):
+        stamp = _time.strftime("%Y/%m/%d %H:%M:%S", _time.localtime(int(t))) + ".%03d" % int(round((t % 1) * 1000))
+        return f"{stamp}, 0, {mhz}, 2070, 900.0, 0x0, Not Active, {thermal}, Not Active, Not Active"
+
+    base = float(int(_time.time())) + 0.5
+    clk.lines = [line(base - 1.0, 345, "Active"), line(base + 0.10, 2070), line(base + 0.15, 2055),
+                 line(base + 0.20, 2070), line(base + 2.0, 600)]
+    clk.mark(base + 0.09, base + 0.21)
+    s = clk.summary()
+    assert s["samples"] == 3 and s["sm_mhz"] == 2070.0 and s["reasons"] == [] and s["window"] == "timed region"
+    clk.mark(base + 0.30, base + 0.31)  # shorter than the period: the neighbours within 0.25 s
+    s = clk.summary()
+    assert s["samples"] == 3 and s["window"].startswith("within")
+    clk.window = None
+    s = clk.summary()
+    assert s["samples"] == 5 and "hw_thermal_slowdown" in s["reasons"] and s["window"] == "whole measurement"

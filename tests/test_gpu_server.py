@@ -333,14 +333,17 @@ def test_lockstep_group_alone_equals_in_the_group():
 def test_lockstep_close_to_direct_steps():
     """The batched k-space tiles its sums differently from the single-system path, so a
     lockstep-served trajectory agrees with the replica's direct steps to FP32 rounding only:
-    positions within 1e-6 A, momenta within 1e-5 relative, the box within 1e-9 relative."""
+    positions within 1e-6 A, momenta within 1e-5 relative.  The box moves by the integrated
+    virial, which each FP32-phase evaluation gives within 1e-5 relative, so the two boxes'
+    displacements from the common initial box agree within 2e-5 of the displacement."""
     out, _, _ = _serve_lockstep([0, 1], max_slots=2)
     for i in range(2):
         r, p, cell = out[i]
         r0, p0, cell0 = _direct(REQS[i], rbe.RBE_FP32_PHASE)
+        box_init = _system(REQS[i][0], REQS[i][1])[4]
         assert np.max(np.abs(r - r0)) < 1e-6
         assert np.max(np.abs(p - p0)) <= 1e-5 * np.max(np.abs(p0))
-        assert np.allclose(cell[:3], cell0[:3], rtol=1e-9, atol=0)
+        assert np.all(np.abs(cell[:3] - cell0[:3]) <= 2e-5 * np.abs(cell0[:3] - box_init) + 1e-12 * cell0[:3])
 
 
 def test_lockstep_nonfinite_member_is_evicted():
