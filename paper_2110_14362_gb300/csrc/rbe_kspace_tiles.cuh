@@ -24,7 +24,7 @@ constexpr int kForceThreads = 32 * kForceWarps;
 #define RBE_FORCE_PPT 4
 #endif
 #ifndef RBE_FORCE_LUNROLL
-#define RBE_FORCE_LUNROLL 4
+#define RBE_FORCE_LUNROLL 8
 #endif
 #ifndef RBE_FORCE_MINB
 #define RBE_FORCE_MINB 4
