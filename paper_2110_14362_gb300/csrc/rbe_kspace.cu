@@ -148,7 +148,10 @@ __device__ __forceinline__ double block_sum(double v, double* scratch32)
 // threads for F = 2 and 4.
 // XYZQ: positions and charges as one float4 (x, y, z, q) per particle in pos (q unused).
 template <int ACC, int F, bool XYZQ>
-__global__ void __launch_bounds__(F == 1 ? kMaxRhoThreads : kRhoThreadsF, F == 1 ? 6 : 8)
+#ifndef RBE_RHO_MINB_F
+#define RBE_RHO_MINB_F 8
+#endif
+__global__ void __launch_bounds__(F == 1 ? kMaxRhoThreads : kRhoThreadsF, F == 1 ? 6 : RBE_RHO_MINB_F)
 k_rho_f32(const void* __restrict__ pos, const double* __restrict__ q, int64_t N, const KState* __restrict__ ks,
           const int4* __restrict__ m, int K, int64_t chunk_len, int nchunks, float4* __restrict__ partials,
           unsigned* __restrict__ status, int c_off, int S)

@@ -365,7 +365,10 @@ __device__ __forceinline__ uint4 load_record(const void* __restrict__ pos, const
 // chunk's sum of q^2 (hi, lo).  The box constants are read from ks before pdl_wait: the
 // kernel that wrote them (k_tables) runs before the sampler, which is this launch's
 // predecessor, and the sampler starts only after k_tables has completed.
-constexpr int kRhoStage = 256;  // particles staged per tile
+#ifndef RBE_RHO_STAGE
+#define RBE_RHO_STAGE 512
+#endif
+constexpr int kRhoStage = RBE_RHO_STAGE;  // particles staged per tile
 // Particles per FP32 partial sum of the compensated path: 16 (one compensated addition per 16
 // pairs; groups of 4 and 8 measured 7 % and 3 % slower at N = 4e6, P = 2000).
 #ifndef RBE_RHO_GROUP
