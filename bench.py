@@ -635,7 +635,8 @@ def run_batched(rbe, n_items=64, P=100, iters=20):
     with rbe.Batch(SERVE_ALPHA, P, n_items, max_box, stream=stream.cuda_stream) as b:
         arr = b.items(items)
         out["autotune_ms"] = b.autotune(arr, reps=3)
-        out["tiles"] = {"rho_k": b.tiles()[0], "rho_chunk": b.tiles()[1], "force_block": b.tiles()[2]}
+        out["tiles"] = {"rho_k": b.tiles()[0], "rho_f": b.rho_f(), "rho_chunk": b.tiles()[1],
+                        "force_block": b.tiles()[2]}
 
         def timed(fn):
             for _ in range(3):

@@ -529,13 +529,19 @@ rbe_status rbe_batch_create(double alpha, int32_t P, int32_t max_items, double m
 rbe_status rbe_batch_destroy(rbe_batch b);
 /* Stream of later evaluations (a cudaStream_t; NULL = legacy default); synchronises the old one. */
 rbe_status rbe_batch_set_stream(rbe_batch b, void* stream);
-/* Tile shapes: rho_k frequencies per rho tile (16 to 256; a block of 256 threads runs
+/* Tile shapes: rho_k frequency lanes per rho tile (16 to 256; a block of 256 threads runs
  * floor(256 / rho_k) particle sub-streams of the tile, the threads beyond them idle), rho_chunk
  * particles per rho chunk (>= 32), force_block particles per force tile (a positive multiple of
  * 128).  All three 0 restores the defaults (the rho tile that keeps the most lanes busy for this
  * P, chunks of 256, force tiles of 256). */
 rbe_status rbe_batch_set_tiles(rbe_batch b, int32_t rho_k, int32_t rho_chunk, int32_t force_block);
 rbe_status rbe_batch_get_tiles(rbe_batch b, int32_t* rho_k, int32_t* rho_chunk, int32_t* force_block);
+/* Frequencies per lane of a rho tile: 1 (default) or 2.  With 2 each of the tile's rho_k lanes
+ * holds two frequencies (the tile covers 2 rho_k), so that one staged particle record feeds two
+ * (particle, frequency) pairs.  Kept by rbe_batch_set_tiles; reset to 1 by its all-zero
+ * defaults; chosen with the other shapes by rbe_batch_autotune.  RBE_EINVAL for other values. */
+rbe_status rbe_batch_set_rho_f(rbe_batch b, int32_t rho_f);
+rbe_status rbe_batch_get_rho_f(rbe_batch b, int32_t* rho_f);
 
 /* Evaluate items[0..n) (host array of descriptors, read during the call).  Asynchronous on the
  * batch's stream; validation errors (RBE_EINVAL) leave no side effects.  The work lists are

@@ -159,6 +159,8 @@ SIGNATURES = [
     ("rbe_batch_destroy", ctypes.c_int, [_vp]),
     ("rbe_batch_set_stream", ctypes.c_int, [_vp, _vp]),
     ("rbe_batch_set_tiles", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    ("rbe_batch_set_rho_f", ctypes.c_int, [_vp, ctypes.c_int32]),
+    ("rbe_batch_get_rho_f", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32)]),
     ("rbe_batch_set_persistent", ctypes.c_int, [_vp, ctypes.c_int32]),
     ("rbe_batch_test_barrier_timeout", ctypes.c_int, [_vp, ctypes.c_int32]),
     ("rbe_batch_get_tiles", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
@@ -553,6 +555,14 @@ class Batch:
         a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         self._check(load().rbe_batch_get_tiles(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return a.value, b.value, c.value
+
+    def set_rho_f(self, rho_f: int):
+        self._check(load().rbe_batch_set_rho_f(self.h, int(rho_f)))
+
+    def rho_f(self) -> int:
+        f = ctypes.c_int32()
+        self._check(load().rbe_batch_get_rho_f(self.h, ctypes.byref(f)))
+        return f.value
 
     def set_stream(self, stream_handle: int):
         self._check(load().rbe_batch_set_stream(self.h, stream_handle))

@@ -91,8 +91,8 @@ struct BArgs {
     int4* m;
     double* w;
     const int4* rtiles;         // (item, frequency tile, chunk)
-    int nrt, S, T;              // rho tiles; particle sub-streams of a rho block (kBThreads / rho_k) and
-                                // frequency lanes of each (rho_k)
+    int nrt, S, T, F;           // rho tiles; particle sub-streams of a rho block (kBThreads / T),
+                                // frequency lanes of each (T = rho_k / F) and frequencies per lane
     float4* part;
     double2* rho;
     double* terms;
@@ -185,15 +185,26 @@ __device__ __forceinline__ void pass_sample(const BArgs& a)
     }
 }
 
-__device__ __forceinline__ void pass_rho(const BArgs& a)
+// F frequencies per lane (a.F): with two, one broadcast particle record feeds two pairs
+template <int F>
+__device__ __forceinline__ void pass_rho_f(const BArgs& a)
 {
     for (int t = blockIdx.x; t < a.nrt; t += gridDim.x) {
         const int4 tl = a.rtiles[t];
         const BItem& it = a.items[tl.x];
-        rho_f32_tile<RBE_RHO_COMP32, 1>(tl.y, tl.z, it.pos, it.q, it.N, a.ks + tl.x, a.m + (size_t)tl.x * a.P, a.P,
-                                        it.chunk_len, it.nchunks, a.part + it.part_off, it.status, a.S, a.T);
+        rho_f32_tile<RBE_RHO_COMP32, F, false, kBThreads>(tl.y, tl.z, it.pos, it.q, it.N, a.ks + tl.x,
+                                                          a.m + (size_t)tl.x * a.P, a.P, it.chunk_len, it.nchunks,
+                                                          a.part + it.part_off, it.status, a.S, a.T);
         __syncthreads();
     }
+}
+
+__device__ __forceinline__ void pass_rho(const BArgs& a)
+{
+    if (a.F == 2)  // the same for every block
+        pass_rho_f<2>(a);
+    else
+        pass_rho_f<1>(a);
 }
 
 // (item, frequency) rows u = r (P + 1) + l in groups of 32 per block: each warp sums four rows
@@ -291,12 +302,14 @@ __global__ void __launch_bounds__(kBThreads, RBE_BATCH_MINB) k_batch(BArgs a)
 #endif
 __global__ void __launch_bounds__(kBThreads, 2) k_btables(BArgs a) { pass_tables(a); }
 __global__ void __launch_bounds__(kBThreads, RBE_BATCH_PASS_MINB) k_bsample(BArgs a) { pass_sample(a); }
-__global__ void __launch_bounds__(kBThreads, RBE_BATCH_PASS_MINB) k_brho(BArgs a) { pass_rho(a); }
+__global__ void __launch_bounds__(kBThreads, RBE_BATCH_PASS_MINB) k_brho(BArgs a) { pass_rho_f<1>(a); }
+__global__ void __launch_bounds__(kBThreads, RBE_BATCH_PASS_MINB) k_brho2(BArgs a) { pass_rho_f<2>(a); }
 __global__ void __launch_bounds__(kBThreads, RBE_BATCH_PASS_MINB) k_breduce(BArgs a) { pass_reduce(a); }
 __global__ void __launch_bounds__(kBThreads, RBE_BATCH_PASS_MINB) k_bforce(BArgs a) { pass_force(a); }
 
 using PassKernel = void (*)(BArgs);
-static const PassKernel kPassKernels[5] = {k_btables, k_bsample, k_brho, k_breduce, k_bforce};
+// the five passes in order, then the rho pass with two frequencies per lane
+static const PassKernel kPassKernels[6] = {k_btables, k_bsample, k_brho, k_breduce, k_bforce, k_brho2};
 
 template <typename Kern>
 static int resident_blocks(Kern kern, int threads, size_t dyn_smem)
@@ -321,8 +334,8 @@ struct rbe_batch_s {
     int P = 0;
     int max_items = 0;
     int cap = 0;  // table entries per axis
-    // tile shapes
-    int rho_k = 0, rho_chunk = 0, force_block = 0;
+    // tile shapes (rho_k frequency lanes of rho_f frequencies each per rho tile)
+    int rho_k = 0, rho_f = 1, rho_chunk = 0, force_block = 0;
     // device buffers
     BItem* d_items = nullptr;
     double* d_boxes = nullptr;
@@ -348,13 +361,13 @@ struct rbe_batch_s {
     int* h_which = nullptr;
     std::vector<double> last_boxes;
     std::vector<int64_t> plan_N;
-    int plan_k = -1, plan_chunk = -1, plan_fb = -1;
+    int plan_k = -1, plan_f = -1, plan_chunk = -1, plan_fb = -1;
     int n_rtiles = 0, n_ftiles = 0;
     std::vector<int4> h_rtiles;
     std::vector<int2> h_ftiles;
     int grid_per_sm = 1;      // resident blocks of k_batch per SM (the persistent grid)
-    int pass_per_sm[5] = {1, 1, 1, 1, 1};  // resident blocks per SM of each pass kernel
-    size_t pass_smem[5] = {0, 0, 0, 0, 0};  // their dynamic shared memory
+    int pass_per_sm[6] = {1, 1, 1, 1, 1, 1};  // resident blocks per SM of each pass kernel
+    size_t pass_smem[6] = {0, 0, 0, 0, 0, 0};  // their dynamic shared memory
     GridBar* d_bar = nullptr;  // the grid barrier of the persistent launch
     bool persistent = true;    // one cooperative launch per evaluation (else one launch per pass)
     int bar_extra = 0;         // test hook of the barriers' timeout (rbe_batch_test_barrier_timeout)
@@ -422,13 +435,13 @@ bool valid_tiles(int P, int rho_k, int rho_chunk, int force_block)
            force_block >= kForceRound && force_block % kForceRound == 0 && force_block <= (1 << 24) && P >= 1;
 }
 
-// Busy fraction of a rho block's lanes with frequency tiles of k lanes: the tiles' share of real
-// frequencies times the share of the block's threads in whole sub-streams.
-static double rho_lane_efficiency(int P, int k)
+// Busy fraction of a rho block's lanes with frequency tiles of k lanes of f frequencies: the
+// tiles' share of real frequencies times the share of the block's threads in whole sub-streams.
+static double rho_lane_efficiency(int P, int k, int f)
 {
-    const int ktiles = (P + k - 1) / k;
+    const int ktiles = (P + k * f - 1) / (k * f);
     const int S = kBThreads / k;
-    return (double)P / ((double)ktiles * k) * (double)(S * k) / kBThreads;
+    return (double)P / ((double)ktiles * k * f) * (double)(S * k) / kBThreads;
 }
 
 // Frequency-tile candidates for the autotuner: P split evenly into 1 to 16 tiles (lane counts
@@ -438,20 +451,24 @@ static double rho_lane_efficiency(int P, int k)
 // stages and converts the particles again).  The pass is bound by instruction issue, so the
 // busier lanes pay for the extra re-staging and sub-streams rather than run faster (measured
 // at P = 100: 50-lane and 128-lane tiles equal); the timing decides.
-static double rho_k_score(int P, int k) { return rho_lane_efficiency(P, k) - 0.01 * ((P + k - 1) / k); }
+static double rho_k_score(int P, int k, int f)
+{
+    return rho_lane_efficiency(P, k, f) - 0.01 * ((P + k * f - 1) / (k * f));
+}
 
-static std::vector<int> rho_k_candidates(int P)
+// Lane counts for tiles of f frequencies per lane (a tile covers k f frequencies).
+static std::vector<int> rho_k_candidates(int P, int f = 1)
 {
     std::vector<int> ks;
     for (int kt = 1; kt <= 16; ++kt) {
-        const int k = (P + kt - 1) / kt;
+        const int k = (P + kt * f - 1) / (kt * f);
         if (k >= kMinRhoK && k <= kBThreads) ks.push_back(k);
     }
     for (int k : {32, 64, 128, 256}) ks.push_back(k);
     std::sort(ks.begin(), ks.end());
     ks.erase(std::unique(ks.begin(), ks.end()), ks.end());
-    std::stable_sort(ks.begin(), ks.end(), [P](int x, int y) {
-        const double sx = rho_k_score(P, x), sy = rho_k_score(P, y);
+    std::stable_sort(ks.begin(), ks.end(), [P, f](int x, int y) {
+        const double sx = rho_k_score(P, x, f), sy = rho_k_score(P, y, f);
         if (sx != sy) return sx > sy;
         return x > y;
     });
@@ -463,7 +480,8 @@ static std::vector<int> rho_k_candidates(int P)
 // efficiency, chunks of 256 particles.
 void default_tiles(rbe_batch b)
 {
-    b->rho_k = rho_k_candidates(b->P).front();
+    b->rho_f = 1;
+    b->rho_k = rho_k_candidates(b->P, b->rho_f).front();
     b->rho_chunk = 256;
     b->force_block = 2 * kForceRound;
 }
@@ -501,8 +519,8 @@ rbe_status validate_items(rbe_batch b, const rbe_batch_item* items, int n)
 // the N of some item or a tile shape changed).
 rbe_status plan(rbe_batch b, const rbe_batch_item* items, int n)
 {
-    bool same = (int)b->plan_N.size() == n && b->plan_k == b->rho_k && b->plan_chunk == b->rho_chunk &&
-                b->plan_fb == b->force_block;
+    bool same = (int)b->plan_N.size() == n && b->plan_k == b->rho_k && b->plan_f == b->rho_f &&
+                b->plan_chunk == b->rho_chunk && b->plan_fb == b->force_block;
     for (int r = 0; same && r < n; ++r) same = b->plan_N[r] == items[r].N;
     if (!same) {
         if (capturing(b->stream))
@@ -511,7 +529,7 @@ rbe_status plan(rbe_batch b, const rbe_batch_item* items, int n)
         b->h_rtiles.clear();
         b->h_ftiles.clear();
         b->plan_N.assign(n, 0);
-        const int ktiles = (b->P + b->rho_k - 1) / b->rho_k;
+        const int ktiles = (b->P + b->rho_k * b->rho_f - 1) / (b->rho_k * b->rho_f);
         int64_t part = 0;
         for (int r = 0; r < n; ++r) {
             const int64_t N = items[r].N;
@@ -544,6 +562,7 @@ rbe_status plan(rbe_batch b, const rbe_batch_item* items, int n)
         b->n_rtiles = (int)b->h_rtiles.size();
         b->n_ftiles = (int)b->h_ftiles.size();
         b->plan_k = b->rho_k;
+        b->plan_f = b->rho_f;
         b->plan_chunk = b->rho_chunk;
         b->plan_fb = b->force_block;
     }
@@ -617,6 +636,7 @@ rbe_status launch(rbe_batch b, int n, int mask)
     a.nrt = b->n_rtiles;
     a.S = kBThreads / b->rho_k;
     a.T = b->rho_k;
+    a.F = b->rho_f;
     a.part = b->d_part;
     a.rho = b->d_rho;
     a.terms = b->d_terms;
@@ -649,8 +669,9 @@ rbe_status launch(rbe_batch b, int n, int mask)
     const int units[5] = {nw, n * a.bpi, a.nrt, (n * (P + 1) + kReduceGroup - 1) / kReduceGroup, a.nft + n};
     for (int k = 0; k < 5; ++k) {
         if (!(mask & (1 << k)) || units[k] == 0) continue;
-        const int grid = std::max(1, std::min(units[k], b->num_sms * b->pass_per_sm[k]));
-        kPassKernels[k]<<<grid, kBThreads, b->pass_smem[k], s>>>(a);
+        const int kk = k == 2 && a.F == 2 ? 5 : k;
+        const int grid = std::max(1, std::min(units[k], b->num_sms * b->pass_per_sm[kk]));
+        kPassKernels[kk]<<<grid, kBThreads, b->pass_smem[kk], s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return bcuda(b, e, "batched k-space pass");
     }
     return RBE_OK;
@@ -742,8 +763,8 @@ rbe_status rbe_batch_create(double alpha, int32_t P, int32_t max_items, double m
         // the pass kernels: the tables and the sampler take the tables' shared memory, the force
         // pass its staged frequencies
         const size_t ts = tsm <= 48 * 1024 ? tsm : 0;
-        const size_t psm[5] = {ts, ts, 0, 0, (size_t)kForceSmemPerK * std::min(P, kForceStageK)};
-        for (int k = 0; k < 5; ++k) {
+        const size_t psm[6] = {ts, ts, 0, 0, (size_t)kForceSmemPerK * std::min(P, kForceStageK), 0};
+        for (int k = 0; k < 6; ++k) {
             b->pass_smem[k] = psm[k];
             cudaFuncSetAttribute(kPassKernels[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm[k]);
             b->pass_per_sm[k] = resident_blocks(kPassKernels[k], kBThreads, psm[k]);
@@ -811,6 +832,21 @@ rbe_status rbe_batch_test_barrier_timeout(rbe_batch b, int32_t enable)
     return RBE_OK;
 }
 
+rbe_status rbe_batch_set_rho_f(rbe_batch b, int32_t rho_f)
+{
+    if (!b) return RBE_EINVAL;
+    if (rho_f != 1 && rho_f != 2) return bfail(b, RBE_EINVAL, "rho_f must be 1 or 2");
+    b->rho_f = rho_f;
+    return RBE_OK;
+}
+
+rbe_status rbe_batch_get_rho_f(rbe_batch b, int32_t* rho_f)
+{
+    if (!b || !rho_f) return RBE_EINVAL;
+    *rho_f = b->rho_f;
+    return RBE_OK;
+}
+
 rbe_status rbe_batch_get_tiles(rbe_batch b, int32_t* rho_k, int32_t* rho_chunk, int32_t* force_block)
 {
     if (!b) return RBE_EINVAL;
@@ -852,34 +888,38 @@ rbe_status rbe_batch_autotune(rbe_batch b, const rbe_batch_item* items, int32_t 
         *ms /= (float)reps;
         return RBE_OK;
     };
-    const std::vector<int> rho_ks = rho_k_candidates(b->P);
     const int chunks[] = {64, 128, 256, 512, 1024, 2048};
     const int fblocks[] = {128, 256, 512, 1024, 2048};
     rbe_status st = RBE_OK;
     float best_rho = 1e30f, best_force = 1e30f;
-    int bk = b->rho_k, bc = b->rho_chunk, bf = b->force_block;
+    int bk = b->rho_k, bff = b->rho_f, bc = b->rho_chunk, bf = b->force_block;
     // a full evaluation with the current shapes gives the frequencies and coefficients the
     // timed passes read
     st = prepare(b, items, n);
     if (st == RBE_OK) st = launch(b, n, 31);
-    for (int k : rho_ks) {
-        if (st != RBE_OK) break;
-        for (int c : chunks) {
-            b->rho_k = k;
-            b->rho_chunk = c;
-            b->force_block = bf;
-            float ms = 0.f;
-            if ((st = prepare(b, items, n)) != RBE_OK || (st = time_pass(4, &ms)) != RBE_OK) break;
-            if (ms < best_rho) {
-                best_rho = ms;
-                bk = k;
-                bc = c;
+    for (int rf = 1; rf <= 2; ++rf) {
+        for (int k : rho_k_candidates(b->P, rf)) {
+            if (st != RBE_OK) break;
+            for (int c : chunks) {
+                b->rho_k = k;
+                b->rho_f = rf;
+                b->rho_chunk = c;
+                b->force_block = bf;
+                float ms = 0.f;
+                if ((st = prepare(b, items, n)) != RBE_OK || (st = time_pass(4, &ms)) != RBE_OK) break;
+                if (ms < best_rho) {
+                    best_rho = ms;
+                    bk = k;
+                    bff = rf;
+                    bc = c;
+                }
             }
         }
     }
     for (int f : fblocks) {
         if (st != RBE_OK) break;
         b->rho_k = bk;
+        b->rho_f = bff;
         b->rho_chunk = bc;
         b->force_block = f;
         float ms = 0.f;
@@ -890,6 +930,7 @@ rbe_status rbe_batch_autotune(rbe_batch b, const rbe_batch_item* items, int32_t 
         }
     }
     b->rho_k = bk;
+    b->rho_f = bff;
     b->rho_chunk = bc;
     b->force_block = bf;
     float full = 0.f;

@@ -377,7 +377,8 @@ constexpr int kRhoStage = RBE_RHO_STAGE;  // particles staged per tile
 constexpr int kRhoGroup = RBE_RHO_GROUP;
 static_assert(kRhoGroup == 4 || kRhoGroup == 8 || kRhoGroup == 16, "groups of 4, 8 or 16 particles");
 
-template <int ACC, int F, bool XYZQ = false>
+// NT: the most threads a block of this tile has (the size of its shared float-float sums).
+template <int ACC, int F, bool XYZQ = false, int NT = (F == 1 ? kMaxRhoThreads : kRhoThreadsF)>
 __device__ __forceinline__ void rho_f32_tile(int kt, int c, const void* __restrict__ pos,
                                              const double* __restrict__ q, int64_t N, const KState* __restrict__ ks,
           const int4* __restrict__ m, int K, int64_t chunk_len, int nchunks, float4* __restrict__ partials,
@@ -399,7 +400,7 @@ __device__ __forceinline__ void rho_f32_tile(int kt, int c, const void* __restri
     const FixScale scx = fs(ks->sc[0]), scy = fs(ks->sc[1]), scz = fs(ks->sc[2]);
     // the float-float sums across staged tiles, (Re hi, Re lo, Im hi, Im lo) per frequency, live
     // in shared memory: they change once per tile, and registers go to the pair loop
-    __shared__ float4 acc_s[(F == 1 ? kMaxRhoThreads : kRhoThreadsF) * F];
+    __shared__ float4 acc_s[NT * F];
     if (act) {
 #pragma unroll
         for (int f = 0; f < F; ++f) acc_s[(ss * F + f) * T + j] = make_float4(0.f, 0.f, 0.f, 0.f);

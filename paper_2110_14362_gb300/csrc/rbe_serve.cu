@@ -375,9 +375,10 @@ static rbe_status ensure_group_batch(rbe_server_s* s, int m)
         for (int t = 0; t < 3; ++t) need = std::max(need, 2.05 * rq.r.box[t]);  // the NPT range: twice the box
     }
     if (s->batch && need <= s->batch_box && m <= s->cfg.max_slots) return RBE_OK;
-    int32_t tk = 0, tc = 0, tf = 0;
+    int32_t tk = 0, tc = 0, tf = 0, trf = 1;
     if (s->batch) {
         rbe_batch_get_tiles(s->batch, &tk, &tc, &tf);
+        rbe_batch_get_rho_f(s->batch, &trf);
         rbe_batch_destroy(s->batch);
         s->batch = nullptr;
     }
@@ -386,7 +387,10 @@ static rbe_status ensure_group_batch(rbe_server_s* s, int m)
     if (st != RBE_OK) return sfail(s, st, std::string("group batch: ") + rbe_last_error(nullptr));
     s->batch_box = need;
     if ((st = rbe_batch_set_stream(s->batch, s->gstream)) != RBE_OK) return sfail(s, st, "group batch stream");
-    if (tk) rbe_batch_set_tiles(s->batch, tk, tc, tf);  // keep the tuned shapes
+    if (tk) {  // keep the tuned shapes
+        rbe_batch_set_tiles(s->batch, tk, tc, tf);
+        rbe_batch_set_rho_f(s->batch, trf);
+    }
     if (s->ggraph) {
         cudaGraphExecDestroy(s->ggraph);  // it launched the old batch
         s->ggraph = nullptr;

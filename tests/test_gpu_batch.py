@@ -122,6 +122,37 @@ def test_tile_shapes(tiles):
         _check_vs_oracle(F1, W1, E1, _oracle(sy, 150))
 
 
+@pytest.mark.parametrize("tiles", [(50, 64, 128), (64, 256, 256), (16, 100, 128), (38, 512, 384), (128, 33, 128)])
+def test_two_frequencies_per_lane(tiles):
+    """Rho tiles whose lanes hold two frequencies each (a tile of rho_k lanes covers 2 rho_k
+    frequencies; P = 150 leaves ragged tiles) agree with the one-frequency tiles and the oracle,
+    and an item's result is the same alone and in a mix."""
+    systems = _systems([1, 999, 5000, 20000], seed0=13)
+    ref = _dev(systems)
+    cur = _dev(systems)
+    alone = _dev([systems[2]])
+    with rbe.Batch(ALPHA, 150, 4, 100.0) as b:
+        b.evaluate(ref)
+        b.set_tiles(*tiles)
+        b.set_rho_f(2)
+        assert b.rho_f() == 2 and b.tiles() == tiles
+        b.evaluate(cur)
+        b.evaluate(alone)
+        b.set_persistent(False)
+        per_pass = _dev([systems[2]])
+        b.evaluate(per_pass)
+        b.sync()
+    for a, c, d in zip(_out(alone[0]), _out(cur[2]), _out(per_pass[0])):
+        assert np.array_equal(a, c)
+        assert np.array_equal(a, d)
+    for sy, r, c in zip(systems, ref, cur):
+        F0, W0, _ = _out(r)
+        F1, W1, E1 = _out(c)
+        if np.abs(F0).max() > 0:
+            assert rel_rms_force(F1, F0) < 2e-6
+        _check_vs_oracle(F1, W1, E1, _oracle(sy, 150))
+
+
 def test_autotune_then_evaluate():
     systems = _systems([1000, 2000, 8000, 30000], seed0=5)
     items = _dev(systems)
@@ -169,6 +200,13 @@ def test_batch_argument_errors():
             with pytest.raises(rbe.RBEError) as e:
                 b.set_tiles(*bad)
             assert e.value.status == rbe.RBE_EINVAL
+        for bad in (0, 3, -1):
+            with pytest.raises(rbe.RBEError) as e:
+                b.set_rho_f(bad)
+            assert e.value.status == rbe.RBE_EINVAL
+        b.set_rho_f(2)
+        b.set_tiles(0, 0, 0)  # the defaults: one frequency per lane
+        assert b.rho_f() == 1
         arr = b.items(items)
         arr[0].N = 0
         with pytest.raises(rbe.RBEError):
