@@ -533,7 +533,7 @@ rbe_status rbe_batch_set_stream(rbe_batch b, void* stream);
  * floor(256 / rho_k) particle sub-streams of the tile, the threads beyond them idle), rho_chunk
  * particles per rho chunk (>= 32), force_block particles per force tile (a positive multiple of
  * 128).  All three 0 restores the defaults (the rho tile that keeps the most lanes busy for this
- * P, chunks of 256, force tiles of 256). */
+ * P, chunks of 256, force tiles of 512). */
 rbe_status rbe_batch_set_tiles(rbe_batch b, int32_t rho_k, int32_t rho_chunk, int32_t force_block);
 rbe_status rbe_batch_get_tiles(rbe_batch b, int32_t* rho_k, int32_t* rho_chunk, int32_t* force_block);
 /* Frequencies per lane of a rho tile: 1 (default) or 2.  With 2 each of the tile's rho_k lanes

@@ -56,6 +56,7 @@ struct BItem {
 // Every batched kernel runs blocks of kBThreads threads; a sampling unit covers kSampleBlock
 // frequencies of one item.
 constexpr int kBThreads = kForceThreads;
+constexpr int kForceTileUnit = 128;  // force tiles are multiples of this many particles
 constexpr int kSampleBlock = kBThreads;
 constexpr int kMinRhoK = 16;        // fewest frequency lanes of a rho tile (at most 16 sub-streams)
 constexpr int kRhoKCandidates = 6;  // frequency-tile shapes the autotuner times
@@ -262,8 +263,8 @@ __device__ __forceinline__ void pass_force(const BArgs& a)
             const int2 tl = a.ftiles[t];
             const BItem& it = a.items[tl.x];
             const size_t o = (size_t)tl.x * a.P;
-            force_f32_block<false, kBatchForceUnroll>((int64_t)tl.y, it.pos, it.q, it.N, it.per_block, a.ks + tl.x, a.coef_m + o,
-                                   a.coef_f + o, a.P, it.F, it.status);
+            force_f32_block<false, kBatchForceUnroll>((int64_t)tl.y, it.pos, it.q, it.N, it.per_block, a.ks + tl.x,
+                                                      a.coef_m + o, a.coef_f + o, a.P, it.F, it.status);
         } else {
             const int r = t - a.nft;
             const BItem& it = a.items[r];
@@ -432,7 +433,7 @@ bool valid_tiles(int P, int rho_k, int rho_chunk, int force_block)
     // a rho tile of rho_k frequencies fills a block of kBThreads threads with kBThreads / rho_k
     // particle sub-streams (the threads beyond them idle)
     return rho_k >= kMinRhoK && rho_k <= kBThreads && rho_chunk >= 32 && rho_chunk <= (1 << 24) &&
-           force_block >= kForceRound && force_block % kForceRound == 0 && force_block <= (1 << 24) && P >= 1;
+           force_block >= kForceTileUnit && force_block % kForceTileUnit == 0 && force_block <= (1 << 24) && P >= 1;
 }
 
 // Busy fraction of a rho block's lanes with frequency tiles of k lanes of f frequencies: the
@@ -483,7 +484,7 @@ void default_tiles(rbe_batch b)
     b->rho_f = 1;
     b->rho_k = rho_k_candidates(b->P, b->rho_f).front();
     b->rho_chunk = 256;
-    b->force_block = 2 * kForceRound;
+    b->force_block = 4 * kForceTileUnit;  // a round of kForceRound particles for each of the block's warps
 }
 
 rbe_status validate_items(rbe_batch b, const rbe_batch_item* items, int n)

@@ -41,6 +41,13 @@ namespace rbe {
 #ifndef RBE_RHO_LATENCY_PAIRS
 #define RBE_RHO_LATENCY_PAIRS 2.0e7
 #endif
+// Fewest particle rounds per block of the FP32 force pass: below four, a block's warps mostly
+// idle at small N and hold resident slots that concurrent replicas' kernels could use (the
+// serving loop, 256 replicas of 1e3-1e5 charges: 21.3k replica-steps/s at one round per block,
+// 22.0k at four, 22.2k at eight, which slows a lone replica at N = 1e3 by 2 %).
+#ifndef RBE_FORCE_MIN_ROUNDS
+#define RBE_FORCE_MIN_ROUNDS 4
+#endif
 constexpr int kRhoMaxSub = RBE_RHO_MAXSUB;
 constexpr int kRhoMinChunk = RBE_RHO_MINCHUNK;
 constexpr double kRhoLatencyPairs = RBE_RHO_LATENCY_PAIRS;
@@ -648,7 +655,8 @@ static int blocks_per_sm(Kern kern, int threads, size_t dyn_smem = 0)
 // thread), particle chunks so that the grid is one full wave of resident blocks with equal
 // particle counts.  Force pass: whole rounds of force_unit particles per block, at most one
 // resident wave.
-static Plan make_plan(rbe_ctx ctx, int64_t N, int K, const RhoShape& rs, int rho_bps, int force_bps, int force_unit)
+static Plan make_plan(rbe_ctx ctx, int64_t N, int K, const RhoShape& rs, int rho_bps, int force_bps, int force_unit,
+                      int min_rounds)
 {
     Plan p{};
     p.kf = rs.kf;
@@ -664,7 +672,8 @@ static Plan make_plan(rbe_ctx ctx, int64_t N, int K, const RhoShape& rs, int rho
     p.ppt = kForcePPT;
     const int64_t resident = std::max<int64_t>(1, (int64_t)ctx->num_sms * force_bps);
     const int64_t rounds = (N + force_unit - 1) / force_unit;
-    const int64_t per = rounds > 0 ? (rounds + resident - 1) / resident : 0;  // rounds per block
+    int64_t per = rounds > 0 ? (rounds + resident - 1) / resident : 0;  // rounds per block
+    if (per > 0) per = std::max<int64_t>(per, min_rounds);
     p.per_block = per * force_unit;
     p.fblocks = per > 0 ? (int)((rounds + per - 1) / per) : 0;
     return p;
@@ -787,7 +796,8 @@ static rbe_status evaluate_shape(rbe_ctx ctx, int64_t N, int K, EvalShape* out)
         }
         rho_bps = std::max(1, std::min(32, bps / rs.kthreads));
     }
-    const Plan p = make_plan(ctx, N, K, rs, rho_bps, bps_force, fp64 ? kT * 2 : kForceRound);
+    const Plan p = make_plan(ctx, N, K, rs, rho_bps, bps_force,
+                             fp64 ? kT * 2 : kForceRound, fp64 ? 1 : RBE_FORCE_MIN_ROUNDS);
     const size_t need = (size_t)(K + 1) * p.nchunks;
     if (need > d.part_cap) {
         ctx_free(ctx, d.partials);

@@ -21,7 +21,7 @@ constexpr int kForceThreads = 32 * kForceWarps;
 // particles per lane, unroll of the frequency loop, resident blocks per SM the registers are
 // sized for.
 #ifndef RBE_FORCE_PPT
-#define RBE_FORCE_PPT 4
+#define RBE_FORCE_PPT 2
 #endif
 #ifndef RBE_FORCE_LUNROLL
 #define RBE_FORCE_LUNROLL 8
@@ -734,17 +734,19 @@ __device__ __forceinline__ void final_sums(const double* __restrict__ terms, int
 }
 
 // =================================================================================
-// Force pass, FP32-phase path.  Blocks of kForceWarps warps; block b owns particles
-// [b * per_block, (b+1) * per_block).  The frequencies are staged in shared memory (as
-// (mx, my, mz, off_l) and (R_l, R_l mx, R_l my, R_l mz), R_l = beta_l |rho_l| and off_l the
-// fixed-point phase offset of arg rho_l) and split into kForceWarps contiguous slices, one
-// per warp.  Particles are converted once per block into shared memory, kForceThreads at
-// a time; each round of kForceRound particles is processed by every warp against its
-// slice (kForcePPT particles per lane), and the warps' partial forces are summed in
-// shared memory in a fixed order.  No FP64 instruction runs:
+// Force pass, FP32-phase path (Eq. (appforce)).  Block b owns particles [b * per_block,
+// (b+1) * per_block); its warps take whole rounds of kForceRound particles (kForcePPT per lane,
+// read from global memory straight into registers as fixed-point records) over all K
+// frequencies, warp w the rounds w, w + warps, ... of the block, so that no partial force
+// crosses warps (no shared-memory sums, no block barrier per round).  The frequencies are
+// staged in shared memory as (mx, my, mz, off_l) and (R_l, R_l mx, R_l my, R_l mz), R_l =
+// beta_l |rho_l| and off_l the fixed-point phase offset of arg rho_l: once per block when K <=
+// kForceStageK, else kForceStageK at a time for every round (the warps then run the same number
+// of rounds, idle ones included, around the staging barriers).  No FP64 instruction runs:
 //   F_i,theta = q_i (2 pi / l_theta) sum_l R_l m_l,theta sin(theta_il - arg rho_l)
-// (one sine per pair) is formed in FP32 and widened to double exactly.  The launch carries one extra block
-// that computes the energy and virial sums (final_sums_f32) meanwhile.
+// (one sine per pair) is one FP32 sum over l = 0 .. K - 1 in order, widened to double exactly.
+// The launch carries one extra block that computes the energy and virial sums (final_sums)
+// meanwhile.
 template <bool XYZQ = false, int LU = kForceLUnroll>
 __device__ __forceinline__ void force_f32_block(int64_t blk, const void* __restrict__ pos,
                                                 const double* __restrict__ q, int64_t N, int64_t per_block,
@@ -753,10 +755,8 @@ __device__ __forceinline__ void force_f32_block(int64_t blk, const void* __restr
                                                 unsigned* __restrict__ status)
 {
     extern __shared__ int4 s_dyn[];
-    __shared__ uint4 sp[kForceThreads];
-    __shared__ float part[kForceWarps][3][kForceRound];
     __shared__ unsigned bad;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = (int)(blockDim.x >> 5);
     const int kstage = min(K, kForceStageK);
     int4* sm = s_dyn;
     float4* sf = reinterpret_cast<float4*>(s_dyn + kstage);
@@ -765,49 +765,56 @@ __device__ __forceinline__ void force_f32_block(int64_t blk, const void* __restr
     const float cx = ks->cx, cy = ks->cy, cz = ks->cz;
     const int64_t b0 = blk * per_block;
     const int64_t b1 = min(N, b0 + per_block);
-    const bool multi = K > kstage;  // frequency tiles must be restaged for every round
-    bool staged = false;
-    // the first particle tile is converted before waiting for the reduction (inputs only)
+    const bool multi = K > kstage;
+    const int64_t nround = b1 > b0 ? (b1 - b0 + kForceRound - 1) / kForceRound : 0;
+    const int64_t rlim = multi ? (nround + nwarps - 1) / nwarps * nwarps : nround;
     if (tid == 0) bad = 0u;
     __syncthreads();
-    const uint4 first =
-        b0 + tid < b1 ? load_record<XYZQ>(pos, q, b0 + tid, scx, scy, scz, &bad) : make_uint4(0u, 0u, 0u, 0u);
-    pdl_wait();
-    for (int64_t sbase = b0; sbase < b1; sbase += kForceThreads) {
-        // convert up to kForceThreads particles into shared memory
-        const int64_t i = sbase + tid;
-        __syncthreads();
-        sp[tid] = sbase == b0 ? first
-                              : (i < b1 ? load_record<XYZQ>(pos, q, i, scx, scy, scz, status)
-                                        : make_uint4(0u, 0u, 0u, 0u));
-        if (sbase == b0 && tid == 0 && bad) atomicOr(status, kStatusNonFinite);
-        const int nstaged = (int)min((int64_t)kForceThreads, b1 - sbase);
-        for (int r0 = 0; r0 < nstaged; r0 += kForceRound) {
-            float gx[kForcePPT], gy[kForcePPT], gz[kForcePPT];
+    uint4 pr[kForcePPT];
+    // the first round's records are read before waiting for the reduction (inputs only)
 #pragma unroll
-            for (int p = 0; p < kForcePPT; ++p) gx[p] = gy[p] = gz[p] = 0.f;
-            for (int k0 = 0; k0 < K; k0 += kstage) {
-                const int nk = min(kstage, K - k0);
-                if (multi || !staged) {
-                    __syncthreads();
-                    for (int j = tid; j < nk; j += kForceThreads) {
-                        sm[j] = coef_m[k0 + j];
-                        sf[j] = coef_f[k0 + j];
-                    }
-                    staged = true;
+    for (int p = 0; p < kForcePPT; ++p) {
+        const int64_t i = b0 + (int64_t)warp * kForceRound + 32 * p + lane;
+        pr[p] = i < b1 ? load_record<XYZQ>(pos, q, i, scx, scy, scz, &bad) : make_uint4(0u, 0u, 0u, 0u);
+    }
+    pdl_wait();
+    if (!multi) {
+        for (int j = tid; j < K; j += blockDim.x) {
+            sm[j] = coef_m[j];
+            sf[j] = coef_f[j];
+        }
+    }
+    __syncthreads();  // the frequencies staged; every first-round flag raised
+    if (tid == 0 && bad) atomicOr(status, kStatusNonFinite);
+    for (int64_t r = warp; r < rlim; r += nwarps) {
+        const int64_t base = b0 + r * kForceRound;
+        if (r != warp) {
+#pragma unroll
+            for (int p = 0; p < kForcePPT; ++p) {
+                const int64_t i = base + 32 * p + lane;
+                pr[p] = i < b1 ? load_record<XYZQ>(pos, q, i, scx, scy, scz, status) : make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+        float gx[kForcePPT], gy[kForcePPT], gz[kForcePPT];
+#pragma unroll
+        for (int p = 0; p < kForcePPT; ++p) gx[p] = gy[p] = gz[p] = 0.f;
+        for (int k0 = 0; k0 < K; k0 += kstage) {
+            const int nk = min(kstage, K - k0);
+            if (multi) {
+                __syncthreads();
+                for (int j = tid; j < nk; j += blockDim.x) {
+                    sm[j] = coef_m[k0 + j];
+                    sf[j] = coef_f[k0 + j];
                 }
                 __syncthreads();
-                uint4 pr[kForcePPT];
-#pragma unroll
-                for (int p = 0; p < kForcePPT; ++p) pr[p] = sp[(r0 + 32 * p + lane) % kForceThreads];
-                const int l0 = (warp * nk) / kForceWarps, l1 = ((warp + 1) * nk) / kForceWarps;
+            }
+            if (r < nround) {
 #pragma unroll LU
-                for (int l = l0; l < l1; ++l) {
+                for (int l = 0; l < nk; ++l) {
                     const int4 a = sm[l];
                     const float4 b = sf[l];
 #pragma unroll
                     for (int p = 0; p < kForcePPT; ++p) {
-                        // g = R sin(theta - arg rho) = beta (Re rho sin theta - Im rho cos theta)
                         const float g = mufu_sin(fixed_phase_off(a.x, a.y, a.z, pr[p].x, pr[p].y, pr[p].z,
                                                                (uint32_t)a.w));
                         gx[p] = fmaf(g, b.y, gx[p]);
@@ -816,22 +823,16 @@ __device__ __forceinline__ void force_f32_block(int64_t blk, const void* __restr
                     }
                 }
             }
+        }
+        if (r < nround) {
 #pragma unroll
             for (int p = 0; p < kForcePPT; ++p) {
-                part[warp][0][32 * p + lane] = gx[p];
-                part[warp][1][32 * p + lane] = gy[p];
-                part[warp][2][32 * p + lane] = gz[p];
-            }
-            __syncthreads();
-            for (int t = tid; t < 3 * kForceRound; t += kForceThreads) {
-                const int c = t / kForceRound, j = t % kForceRound;
-                if (r0 + j < nstaged) {
-                    float acc = part[0][c][j];
-#pragma unroll
-                    for (int wv = 1; wv < kForceWarps; ++wv) acc += part[wv][c][j];
-                    const float qf = __uint_as_float(sp[r0 + j].w);
-                    const float sc = c == 0 ? cx : (c == 1 ? cy : cz);
-                    Fb[3 * (sbase + r0 + j) + c] = float_to_double_bits(__float_as_uint(qf * sc * acc));
+                const int64_t i = base + 32 * p + lane;
+                if (i < b1) {
+                    const float qf = __uint_as_float(pr[p].w);
+                    Fb[3 * i] = float_to_double_bits(__float_as_uint(qf * cx * gx[p]));
+                    Fb[3 * i + 1] = float_to_double_bits(__float_as_uint(qf * cy * gy[p]));
+                    Fb[3 * i + 2] = float_to_double_bits(__float_as_uint(qf * cz * gz[p]));
                 }
             }
         }
