@@ -45,6 +45,7 @@ struct RhoShape {
     int ktiles;         // frequency tiles
     int kthreads;       // threads per block: whole warps (ksub sub-streams of kthreads / ksub lanes)
     int ksub;           // particle sub-streams per block
+    int klanes;         // frequency lanes per sub-stream of a two-frequency wide tile (0: kthreads / ksub)
 };
 
 // Launch plan of the N x K pair kernels (chosen by make_plan in rbe_kspace.cu).
@@ -53,6 +54,7 @@ struct Plan {
     int ktiles;         // frequency tiles in the rho pass (kthreads x kf frequencies each)
     int kthreads;       // threads per rho block: whole warps, <= 256
     int ksub;           // particle sub-streams per rho block
+    int klanes;         // lanes per sub-stream of a wide two-frequency tile (0: kthreads / ksub)
     int nchunks;        // particle chunks in the rho pass
     int64_t chunk_len;  // particles per chunk
     int ppt;            // particles per thread in the force pass

@@ -49,6 +49,7 @@ namespace rbe {
 #define RBE_FORCE_MIN_ROUNDS 4
 #endif
 constexpr int kRhoMaxSub = RBE_RHO_MAXSUB;
+constexpr int kRhoWideMaxSub = 8;  // particle sub-streams of a wide two-frequency tile at most
 constexpr int kRhoMinChunk = RBE_RHO_MINCHUNK;
 constexpr double kRhoLatencyPairs = RBE_RHO_LATENCY_PAIRS;
 
@@ -167,8 +168,27 @@ k_rho_f32(const void* __restrict__ pos, const double* __restrict__ q, int64_t N,
                                partials, status, S);
 }
 
+// Two frequencies per thread in blocks of up to kMaxRhoThreads threads with any lane count T
+// (a tile of 2 T frequencies, S = threads / T particle sub-streams, the threads beyond S T idle):
+// small K, where the kRhoThreadsF-thread tiles of k_rho_f32<ACC, 2> would leave lanes without a
+// frequency (K = 200: one tile of 100 lanes in two sub-streams).
+#ifndef RBE_RHO_WIDE_MINB
+#define RBE_RHO_WIDE_MINB 4
+#endif
+template <int ACC, bool XYZQ>
+__global__ void __launch_bounds__(kMaxRhoThreads, RBE_RHO_WIDE_MINB)
+k_rho_f32_wide(const void* __restrict__ pos, const double* __restrict__ q, int64_t N, const KState* __restrict__ ks,
+               const int4* __restrict__ m, int K, int64_t chunk_len, int nchunks, float4* __restrict__ partials,
+               unsigned* __restrict__ status, int c_off, int S, int T)
+{
+    rho_f32_tile<ACC, 2, XYZQ, kMaxRhoThreads>((int)blockIdx.x, c_off + (int)blockIdx.y, pos, q, N, ks, m, K,
+                                               chunk_len, nchunks, partials, status, S, T);
+}
+
 using RhoKernel = void (*)(const void*, const double*, int64_t, const KState*, const int4*, int, int64_t, int,
                            float4*, unsigned*, int, int);
+using RhoWideKernel = void (*)(const void*, const double*, int64_t, const KState*, const int4*, int, int64_t, int,
+                               float4*, unsigned*, int, int, int);
 
 template <int ACC, bool XYZQ>
 static RhoKernel rho_kernel_f(int F)
@@ -188,6 +208,20 @@ static RhoKernel rho_kernel(int accum, int F, bool xyzq = false)
 {
     return xyzq ? rho_kernel_x<true>(accum, F) : rho_kernel_x<false>(accum, F);
 }
+
+template <bool XYZQ>
+static RhoWideKernel rho_wide_kernel_x(int accum)
+{
+    return accum == RBE_RHO_FP64     ? k_rho_f32_wide<RBE_RHO_FP64, XYZQ>
+           : accum == RBE_RHO_COMP32 ? k_rho_f32_wide<RBE_RHO_COMP32, XYZQ>
+                                     : k_rho_f32_wide<RBE_RHO_FP32, XYZQ>;
+}
+
+static RhoWideKernel rho_wide_kernel(int accum, bool xyzq = false)
+{
+    return xyzq ? rho_wide_kernel_x<true>(accum) : rho_wide_kernel_x<false>(accum);
+}
+
 
 // rho pass, FP64 path: s = r / l wrapped to [0, 1); t = m.s - rint(m.s); sincospi(2t).
 __global__ void __launch_bounds__(kMaxRhoThreads)
@@ -663,6 +697,7 @@ static Plan make_plan(rbe_ctx ctx, int64_t N, int K, const RhoShape& rs, int rho
     p.ktiles = rs.ktiles;
     p.kthreads = rs.kthreads;
     p.ksub = rs.ksub;
+    p.klanes = rs.klanes;
     const int64_t want = std::max<int64_t>(1, (int64_t)ctx->num_sms * rho_bps / p.ktiles);
     // at least one staged tile of particles per chunk (fewer leave the block's fixed costs unpaid)
     const int64_t max_chunks = std::max<int64_t>(1, (N + kRhoMinChunk - 1) / kRhoMinChunk);
@@ -695,6 +730,18 @@ static cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+// The FP32-phase rho pass of plan p on stream s (the wide two-frequency kernel when p.klanes > 0).
+static cudaError_t launch_rho_f32(int accum, bool xyzq, const Plan& p, dim3 grid, cudaStream_t s, const void* pos,
+                                  const double* q, int64_t N, const KState* ks, const int4* m, int K, int nchunks,
+                                  float4* part, unsigned* status)
+{
+    if (p.klanes > 0)
+        return launch_pdl(rho_wide_kernel(accum, xyzq), grid, dim3(p.kthreads), 0, s, pos, q, N, ks, m, K, p.chunk_len,
+                          nchunks, part, status, 0, p.ksub, p.klanes);
+    return launch_pdl(rho_kernel(accum, p.kf, xyzq), grid, dim3(p.kthreads), 0, s, pos, q, N, ks, m, K, p.chunk_len,
+                      nchunks, part, status, 0, p.ksub);
 }
 
 // The reduction's block: the fewest whole warps (up to kReduceThreads) that leave each thread at
@@ -732,8 +779,8 @@ static RhoShape rho_shape(int64_t N, int K, int accum)
 {
     const double base = accum == RBE_RHO_COMP32 ? 12.0 : (accum == RBE_RHO_FP64 ? 14.0 : 10.0);
     const bool latency = (double)N * (double)K <= kRhoLatencyPairs;
-    RhoShape best{1, 1, 32, 1};
-    double best_cost = 1e30;
+    RhoShape best{1, 1, 32, 1, 0};
+    double best_cost = 1e30, best_eff = 0.0;
 #ifdef RBE_RHO_FORCE_F
     (void)latency;
     for (int F : {RBE_RHO_FORCE_F}) {
@@ -749,11 +796,30 @@ static RhoShape rho_shape(int64_t N, int K, int accum)
         const double cost = (base + 1.0 / F + 55.0 / (T * F)) / eff;
         if (cost < best_cost - 1e-9) {
             best_cost = cost;
+            best_eff = eff;
             int S = 1;
             while (T * S * 2 <= kRhoThreadsF && S * 2 <= kRhoMaxSub) S *= 2;
-            best = RhoShape{F, ktiles, T * S, S};
+            best = RhoShape{F, ktiles, T * S, S, 0};
         }
     }
+#ifndef RBE_RHO_FORCE_F
+    // the wide two-frequency tiles, where the tiles above leave more than 5 % of the lanes without
+    // a frequency: the frequencies split evenly into kt tiles of 2 T, T lanes of any count, as
+    // many whole sub-streams as fit kMaxRhoThreads (at most kRhoWideMaxSub)
+    for (int kt = 1; !latency && best_eff < 0.95 && kt <= 8; ++kt) {
+        const int per = (K + kt - 1) / kt;
+        const int T = (per + 1) / 2;
+        if (T < 16 || T > kMaxRhoThreads || (kt > 1 && (K + 2 * T - 1) / (2 * T) != kt)) continue;
+        const int S = std::min(kRhoWideMaxSub, kMaxRhoThreads / T);
+        const int threads = 32 * ((S * T + 31) / 32);
+        const double eff = (double)K / ((double)kt * 2 * T) * (double)(S * T) / threads;
+        const double cost = (base + 0.5 + 55.0 / (2 * T)) / eff;
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best = RhoShape{2, kt, threads, S, T};
+        }
+    }
+#endif
     return best;
 }
 
@@ -762,7 +828,7 @@ static rbe_status evaluate_shape(rbe_ctx ctx, int64_t N, int K, EvalShape* out)
     DeviceBuffers& d = ctx->d;
     const bool fp64 = ctx->precision == RBE_FP64;
     static int rho64_threads = 0, bps_f64 = 0;
-    static int rho32_bps[3][3] = {{0}};  // [accum][F index] resident blocks per SM at the F's block size
+    static int rho32_bps[3][4] = {{0}};  // [accum][F index, 3: wide] resident threads per SM
     if (!rho64_threads) {
         rho64_threads = blocks_per_sm(k_rho_f64, kMaxRhoThreads) * kMaxRhoThreads;
         bps_f64 = blocks_per_sm(k_force_f64<2>, kT);
@@ -784,15 +850,18 @@ static rbe_status evaluate_shape(rbe_ctx ctx, int64_t N, int K, EvalShape* out)
         rs.ktiles = (K + kMaxRhoThreads - 1) / kMaxRhoThreads;
         rs.kthreads = std::min(kMaxRhoThreads, 32 * (((K + rs.ktiles - 1) / rs.ktiles + 31) / 32));
         rs.ksub = 1;
+        rs.klanes = 0;
         rho_bps = std::max(1, std::min(32, rho64_threads / rs.kthreads));
     } else {
         rs = rho_shape(N, K, ctx->rho_accum);
         const int a = ctx->rho_accum < 0 || ctx->rho_accum > 2 ? 1 : ctx->rho_accum;
-        const int fi = rs.kf == 4 ? 2 : (rs.kf == 2 ? 1 : 0);
+        const bool wide = rs.klanes > 0;
+        const int fi = wide ? 3 : (rs.kf == 4 ? 2 : (rs.kf == 2 ? 1 : 0));
         int& bps = rho32_bps[a][fi];
         if (!bps) {
-            const int tmax = rs.kf == 1 ? kMaxRhoThreads : kRhoThreadsF;
-            bps = std::max(1, blocks_per_sm(rho_kernel(a, rs.kf), tmax) * tmax);  // resident threads per SM
+            const int tmax = rs.kf == 1 || wide ? kMaxRhoThreads : kRhoThreadsF;
+            bps = std::max(1, (wide ? blocks_per_sm(rho_wide_kernel(a), tmax) : blocks_per_sm(rho_kernel(a, rs.kf), tmax)) *
+                                  tmax);  // resident threads per SM
         }
         rho_bps = std::max(1, std::min(32, bps / rs.kthreads));
     }
@@ -835,9 +904,8 @@ static rbe_status launch_evaluate_range(rbe_ctx ctx, int64_t N, const void* pos,
         k_rho_f64<<<grid, p.kthreads, 0, s>>>(static_cast<const double*>(pos), q, N, ks, m_in, K, p.chunk_len,
                                               p.nchunks, part64, d.status);
     } else {
-        const RhoKernel kern = rho_kernel(ctx->rho_accum, p.kf, xyzq);
-        cudaError_t err = launch_pdl(kern, grid, dim3(p.kthreads), 0, s, pos, q, N, ks, m_in, K,
-                                     p.chunk_len, p.nchunks, part32, d.status, 0, p.ksub);
+        cudaError_t err = launch_rho_f32(ctx->rho_accum, xyzq, p, grid, s, pos, q, N, ks, m_in, K, p.nchunks, part32,
+                                         d.status);
         if (err != cudaSuccess) return cuda_fail(ctx, err, "launch k_rho_f32");
     }
     rbe_status st = check_launch(ctx, "k_rho");
@@ -945,10 +1013,9 @@ rbe_status launch_evaluate_staged(rbe_ctx ctx, int64_t N, const double* h_pos, c
             (err = cudaStreamWaitEvent(s, ctx->pev[1 + g], 0)) != cudaSuccess)
             return cuda_fail(ctx, err, "staged: input event");
         // group g: rows of stride nchunks, its columns from coff[g]
-        err = launch_pdl(rho_kernel(ctx->rho_accum, pl[g].kf), dim3(pl[g].ktiles, pl[g].nchunks),
-                         dim3(pl[g].kthreads), 0, s,
-                         (const double*)(d_pos + 3 * a), (const double*)(d_q + a), n, ks, (const int4*)d.m, K,
-                         pl[g].chunk_len, nchunks, part32 + coff[g], d.status, 0, pl[g].ksub);
+        err = launch_rho_f32(ctx->rho_accum, false, pl[g], dim3(pl[g].ktiles, pl[g].nchunks), s,
+                             (const double*)(d_pos + 3 * a), (const double*)(d_q + a), n, ks, (const int4*)d.m, K,
+                             nchunks, part32 + coff[g], d.status);
         if (err != cudaSuccess) return cuda_fail(ctx, err, "staged: k_rho_f32");
     }
     err = launch_reduce_f32(s, (const float4*)part32, nchunks, K, (const int4*)d.m, (const double*)d.w, ks, d);
