@@ -42,7 +42,7 @@ MUFU_OPS_PER_PAIR = {"k_rho": 2.0, "k_force": 1.0}
 # DRAM bytes per launch of the dominant kernel measured by ncu on this workload
 # (dram__bytes_read.sum + dram__bytes_write.sum), or None when not captured for the
 # current kernel version.  Source: profiles/ summaries.
-NCU_TRAFFIC = {("k_rho", "uniform-N4000000-P2000"): 128080128 + 3214592}
+NCU_TRAFFIC = {("k_rho", "uniform-N4000000-P2000"): 128080384 + 3272448}
 
 # launches of the library's own kernels per evaluation at a fixed box: the sampler, the rho
 # pass, the rho reduction and the force pass
@@ -610,7 +610,7 @@ def run_general(rbe, steps=20, warmup=3):
     return out
 
 
-def run_batched(rbe, n_items=64, P=100, iters=20):
+def run_batched(rbe, n_items=64, P=100, iters=20, tiles=None):
     """Batched k-space (one evaluation of n_items uneven systems in one persistent launch,
     autotuned tiles; also timed as one launch per pass) against a loop of single-system
     evaluations of the same systems on one stream:
@@ -634,7 +634,12 @@ def run_batched(rbe, n_items=64, P=100, iters=20):
            "N_range": [int(min(r.N for r in reqs)), int(max(r.N for r in reqs))]}
     with rbe.Batch(SERVE_ALPHA, P, n_items, max_box, stream=stream.cuda_stream) as b:
         arr = b.items(items)
-        out["autotune_ms"] = b.autotune(arr, reps=3)
+        if tiles:  # pinned shapes (rho lanes, frequencies per lane, rho chunk, force block)
+            b.set_tiles(tiles[0], tiles[2], tiles[3])
+            b.set_rho_f(tiles[1])
+            out["autotune_ms"] = None
+        else:
+            out["autotune_ms"] = b.autotune(arr, reps=3)
         out["tiles"] = {"rho_k": b.tiles()[0], "rho_f": b.rho_f(), "rho_chunk": b.tiles()[1],
                         "force_block": b.tiles()[2]}
 
@@ -916,6 +921,8 @@ def main():
     ap.add_argument("--ptilde", type=int, default=0, help="with --profile-npt: a separate pressure batch")
     ap.add_argument("--reuse", type=int, default=1, help="with --profile-npt: samples drawn every M steps")
     ap.add_argument("--profile-batched", action="store_true", help="time only the batched k-space evaluation")
+    ap.add_argument("--batched-tiles", default=None,
+                    help="with --profile-batched: pin the tiles 'lanes,freqs_per_lane,chunk,force_block' (no autotune)")
     ap.add_argument("--profile-serving", action="store_true", help="run only the serving measurements")
     ap.add_argument("--profile-water", action="store_true",
                     help="run only the rigid-water NPT run (3000 molecules, FP64, --steps steps)")
@@ -1007,7 +1014,8 @@ def main():
         import torch
         import paper_2110_14362_gb300 as rbe
         torch.cuda.set_device(local)
-        print(json.dumps({"metric": "batched k-space", "batched_kspace": run_batched(rbe, iters=args.steps)}),
+        tiles = [int(x) for x in args.batched_tiles.split(",")] if args.batched_tiles else None
+        print(json.dumps({"metric": "batched k-space", "batched_kspace": run_batched(rbe, iters=args.steps, tiles=tiles)}),
               flush=True)
         return
     if args.impl == "reference":

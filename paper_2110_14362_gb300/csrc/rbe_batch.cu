@@ -216,6 +216,9 @@ constexpr int kReduceRowsPerWarp = 4;
 constexpr int kReduceGroup = kReduceRowsPerWarp * kBThreads / 32;
 static_assert(kReduceGroup == 32, "one row per lane of the finishing warp");
 
+// JOINT: a warp's rows summed together (the per-pass kernel, given the registers for it) or one
+// after the other (the persistent kernel, whose registers all five passes share); the same bits.
+template <bool JOINT>
 __device__ __forceinline__ void pass_reduce(const BArgs& a)
 {
     __shared__ double2 srho[kReduceGroup];
@@ -234,14 +237,64 @@ __device__ __forceinline__ void pass_reduce(const BArgs& a)
                 freq_pre(mi, a.w[o + l], a.ks + r, c);
             }
         }
+        // the warp's rows summed together, so that the loads of all of them are in flight at
+        // once; each row's own order is warp_row_sum's (lane-strided float-float sums over the
+        // chunks, then the same shuffle tree), so a row's sum does not depend on its neighbours
+        if (!JOINT) {
 #pragma unroll 1
-        for (int i = 0; i < kReduceRowsPerWarp; ++i) {
-            const int j = warp * kReduceRowsPerWarp + i, u = base + j;
-            if (u >= rows) break;
-            const int r = u / (a.P + 1), l = u % (a.P + 1);
-            const BItem& it = a.items[r];
-            const double2 v = warp_row_sum(a.part + it.part_off + (size_t)l * it.nchunks, it.nchunks);
-            if (lane == 0) srho[j] = v;
+            for (int i = 0; i < kReduceRowsPerWarp; ++i) {
+                const int j = warp * kReduceRowsPerWarp + i, u = base + j;
+                if (u >= rows) break;
+                const int r = u / (a.P + 1), l = u % (a.P + 1);
+                const BItem& it = a.items[r];
+                const double2 v = warp_row_sum(a.part + it.part_off + (size_t)l * it.nchunks, it.nchunks);
+                if (lane == 0) srho[j] = v;
+            }
+        } else {
+            const float4* rowp[kReduceRowsPerWarp];
+            int nch[kReduceRowsPerWarp], nmax = 0;
+            float rh[kReduceRowsPerWarp], rl[kReduceRowsPerWarp], ih[kReduceRowsPerWarp], il[kReduceRowsPerWarp];
+#pragma unroll
+            for (int i = 0; i < kReduceRowsPerWarp; ++i) {
+                const int u = base + warp * kReduceRowsPerWarp + i;
+                rowp[i] = a.part;
+                nch[i] = 0;
+                if (u < rows) {
+                    const int r = u / (a.P + 1), l = u % (a.P + 1);
+                    const BItem& it = a.items[r];
+                    rowp[i] = a.part + it.part_off + (size_t)l * it.nchunks;
+                    nch[i] = it.nchunks;
+                }
+                nmax = max(nmax, nch[i]);
+                rh[i] = rl[i] = ih[i] = il[i] = 0.f;
+            }
+            for (int j = lane; j < nmax; j += 32) {
+#pragma unroll
+                for (int i = 0; i < kReduceRowsPerWarp; ++i) {
+                    if (j < nch[i]) {
+                        const float4 v = rowp[i][j];
+                        ff_add2(rh[i], rl[i], v.x, v.y);
+                        ff_add2(ih[i], il[i], v.z, v.w);
+                    }
+                }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+                for (int i = 0; i < kReduceRowsPerWarp; ++i) {
+                    const float x0 = __shfl_xor_sync(0xffffffffu, rh[i], off), x1 = __shfl_xor_sync(0xffffffffu, rl[i], off);
+                    const float x2 = __shfl_xor_sync(0xffffffffu, ih[i], off), x3 = __shfl_xor_sync(0xffffffffu, il[i], off);
+                    ff_add2(rh[i], rl[i], x0, x1);
+                    ff_add2(ih[i], il[i], x2, x3);
+                }
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int i = 0; i < kReduceRowsPerWarp; ++i)
+                    if (nch[i] > 0)
+                        srho[warp * kReduceRowsPerWarp + i] =
+                            make_double2(ff_to_double(rh[i], rl[i]), ff_to_double(ih[i], il[i]));
+            }
         }
         __syncthreads();
         if (warp == 0 && uf < rows) {
@@ -256,6 +309,9 @@ __device__ __forceinline__ void pass_reduce(const BArgs& a)
 
 // tiles [0, nft) are (item, particle block); tiles [nft, nft + n) the per-item energy and
 // virial sums
+// LU: unroll of the frequency loop (the per-pass kernel takes the single-system unroll; the
+// persistent kernel, whose registers all five passes share, a shorter one)
+template <int LU>
 __device__ __forceinline__ void pass_force(const BArgs& a)
 {
     for (int t = blockIdx.x; t < a.nft + a.n; t += gridDim.x) {
@@ -263,7 +319,7 @@ __device__ __forceinline__ void pass_force(const BArgs& a)
             const int2 tl = a.ftiles[t];
             const BItem& it = a.items[tl.x];
             const size_t o = (size_t)tl.x * a.P;
-            force_f32_block<false, kBatchForceUnroll>((int64_t)tl.y, it.pos, it.q, it.N, it.per_block, a.ks + tl.x,
+            force_f32_block<false, LU>((int64_t)tl.y, it.pos, it.q, it.N, it.per_block, a.ks + tl.x,
                                                       a.coef_m + o, a.coef_f + o, a.P, it.F, it.status);
         } else {
             const int r = t - a.nft;
@@ -290,9 +346,9 @@ __global__ void __launch_bounds__(kBThreads, RBE_BATCH_MINB) k_batch(BArgs a)
     if (!grid_sync(a.bar, nb, a.status)) return;
     pass_rho(a);
     if (!grid_sync(a.bar, nb, a.status)) return;
-    pass_reduce(a);
+    pass_reduce<false>(a);
     if (!grid_sync(a.bar, nb, a.status)) return;
-    pass_force(a);
+    pass_force<kBatchForceUnroll>(a);
 }
 
 // The same passes as launches of their own (persistence off): each pass compiled alone needs 60
@@ -305,8 +361,8 @@ __global__ void __launch_bounds__(kBThreads, 2) k_btables(BArgs a) { pass_tables
 __global__ void __launch_bounds__(kBThreads, RBE_BATCH_PASS_MINB) k_bsample(BArgs a) { pass_sample(a); }
 __global__ void __launch_bounds__(kBThreads, RBE_BATCH_PASS_MINB) k_brho(BArgs a) { pass_rho_f<1>(a); }
 __global__ void __launch_bounds__(kBThreads, RBE_BATCH_PASS_MINB) k_brho2(BArgs a) { pass_rho_f<2>(a); }
-__global__ void __launch_bounds__(kBThreads, RBE_BATCH_PASS_MINB) k_breduce(BArgs a) { pass_reduce(a); }
-__global__ void __launch_bounds__(kBThreads, RBE_BATCH_PASS_MINB) k_bforce(BArgs a) { pass_force(a); }
+__global__ void __launch_bounds__(kBThreads, 2) k_breduce(BArgs a) { pass_reduce<true>(a); }
+__global__ void __launch_bounds__(kBThreads, RBE_BATCH_PASS_MINB) k_bforce(BArgs a) { pass_force<kForceLUnroll>(a); }
 
 using PassKernel = void (*)(BArgs);
 // the five passes in order, then the rho pass with two frequencies per lane
@@ -901,7 +957,15 @@ rbe_status rbe_batch_autotune(rbe_batch b, const rbe_batch_item* items, int32_t 
     for (int rf = 1; rf <= 2; ++rf) {
         for (int k : rho_k_candidates(b->P, rf)) {
             if (st != RBE_OK) break;
-            for (int c : chunks) {
+            // the chunk lengths, and whole multiples of the tile's staged particles (S sub-streams of
+            // kRhoGroup-multiple shares of kRhoStage), whose chunks end on a full staged tile
+            const int S = kBThreads / k, stage = S * (kRhoGroup * (kRhoStage / (kRhoGroup * S)));
+            std::vector<int> cands(std::begin(chunks), std::end(chunks));
+            for (int mlt : {1, 2, 4})
+                if (stage * mlt >= 32 && stage * mlt <= 2048) cands.push_back(stage * mlt);
+            std::sort(cands.begin(), cands.end());
+            cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
+            for (int c : cands) {
                 b->rho_k = k;
                 b->rho_f = rf;
                 b->rho_chunk = c;
