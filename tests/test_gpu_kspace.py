@@ -327,11 +327,12 @@ def _xyzq(pos, q):
     return to_dev(np.concatenate([pos, q[:, None]], axis=1).astype(np.float32))
 
 
-@pytest.mark.parametrize("N,P", [(20000, 200), (5003, 517), (1, 64)])
+@pytest.mark.parametrize("N,P", [(20000, 200), (5003, 517), (1, 64), (300000, 100)])
 def test_xyzq_input(N, P):
     """float4 (x, y, z, q) input: bit for bit the evaluation of the float-rounded positions given
     as doubles, and within 1e-5 of the oracle fed the same float-rounded positions (the compute
-    error); the rounding of the input itself is a separate, larger error."""
+    error); the rounding of the input itself is a separate, larger error.  (300000, 100) runs
+    the wide two-frequency rho tiles on the float4 records."""
     import torch
     s = inputs.uniform_density(N, P=P)
     pos32, q32 = s.pos.astype(np.float32), s.q.astype(np.float32)
