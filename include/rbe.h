@@ -552,9 +552,10 @@ rbe_status rbe_batch_get_rho_f(rbe_batch b, int32_t* rho_f);
  * redraws, non-finite values) are reported by rbe_batch_sync. */
 rbe_status rbe_kspace_forces_virial_batched(rbe_batch b, const rbe_batch_item* items, int32_t n);
 
-/* Times candidate tile shapes on these items (frequencies per rho tile x particles per chunk,
- * then particles per force tile; reps evaluations of each pass) and keeps the fastest; the
- * items' outputs are overwritten.  *best_ms (may be NULL): mean time of one evaluation with
+/* Times candidate tile shapes on these items (rho lanes x frequencies per lane x particles per
+ * chunk, then particles per force tile; reps evaluations of each pass; with the persistent launch
+ * on, the force tiles on reps whole evaluations) and keeps the fastest; the items' outputs are
+ * overwritten.  *best_ms (may be NULL): mean time of one evaluation with
  * the chosen shapes.  Synchronous. */
 rbe_status rbe_batch_autotune(rbe_batch b, const rbe_batch_item* items, int32_t n, int32_t reps, double* best_ms);
 

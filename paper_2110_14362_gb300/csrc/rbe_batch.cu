@@ -994,6 +994,26 @@ rbe_status rbe_batch_autotune(rbe_batch b, const rbe_batch_item* items, int32_t 
             bf = f;
         }
     }
+    if (b->persistent) {
+        // the persistent launch runs every pass on its fewer resident blocks, where the force
+        // tiles' count against the grid decides the balance: choose them on whole evaluations
+        float best_full = 1e30f;
+        const int bf_pass = bf;
+        for (int f : fblocks) {
+            if (st != RBE_OK) break;
+            b->rho_k = bk;
+            b->rho_f = bff;
+            b->rho_chunk = bc;
+            b->force_block = f;
+            float ms = 0.f;
+            if ((st = prepare(b, items, n)) != RBE_OK || (st = time_pass(31, &ms)) != RBE_OK) break;
+            if (ms < best_full) {
+                best_full = ms;
+                bf = f;
+            }
+        }
+        if (st != RBE_OK) bf = bf_pass;
+    }
     b->rho_k = bk;
     b->rho_f = bff;
     b->rho_chunk = bc;
