@@ -50,6 +50,9 @@ namespace rbe {
 #endif
 constexpr int kRhoMaxSub = RBE_RHO_MAXSUB;
 constexpr int kRhoWideMaxSub = 8;  // particle sub-streams of a wide two-frequency tile at most
+#ifndef RBE_RHO_WIDE_MAXKT
+#define RBE_RHO_WIDE_MAXKT 1  // frequency tiles of a wide plan at most (slab: one tile 39.1 us, two 40.2 us)
+#endif
 constexpr int kRhoMinChunk = RBE_RHO_MINCHUNK;
 constexpr double kRhoLatencyPairs = RBE_RHO_LATENCY_PAIRS;
 
@@ -806,7 +809,7 @@ static RhoShape rho_shape(int64_t N, int K, int accum)
     // the wide two-frequency tiles, where the tiles above leave more than 5 % of the lanes without
     // a frequency: the frequencies split evenly into kt tiles of 2 T, T lanes of any count, as
     // many whole sub-streams as fit kMaxRhoThreads (at most kRhoWideMaxSub)
-    for (int kt = 1; !latency && best_eff < 0.95 && kt <= 8; ++kt) {
+    for (int kt = 1; !latency && best_eff < 0.95 && kt <= RBE_RHO_WIDE_MAXKT; ++kt) {
         const int per = (K + kt - 1) / kt;
         const int T = (per + 1) / 2;
         if (T < 16 || T > kMaxRhoThreads || (kt > 1 && (K + 2 * T - 1) / (2 * T) != kt)) continue;

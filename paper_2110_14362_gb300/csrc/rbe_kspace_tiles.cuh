@@ -24,7 +24,7 @@ constexpr int kForceThreads = 32 * kForceWarps;
 #define RBE_FORCE_PPT 2
 #endif
 #ifndef RBE_FORCE_LUNROLL
-#define RBE_FORCE_LUNROLL 8
+#define RBE_FORCE_LUNROLL 16
 #endif
 #ifndef RBE_FORCE_MINB
 #define RBE_FORCE_MINB 4
