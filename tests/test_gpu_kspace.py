@@ -156,8 +156,10 @@ def test_fp32_phase_parity_small(accum):
     assert abs(E[0] - Ek0) <= 1e-5 * abs(Ek0)
 
 
-@pytest.mark.parametrize("N,P", [(20000, 200), (5003, 517), (64, 4096)])
+@pytest.mark.parametrize("N,P", [(20000, 200), (5003, 517), (64, 4096), (100000, 300), (100003, 450)])
 def test_fp32_phase_parity_mid(N, P):
+    """FP32-phase path against the oracle; (100000, 300) and (100003, 450) run the wide
+    two-frequency rho tiles with one particle sub-stream (150 and 225 lanes)."""
     s = inputs.uniform_density(N, P=P)
     F, W, E, _ = _run(s, P, 11, rbe.RBE_FP32_PHASE)
     F0, W0, Ek0, Es0, _, _ = oracle.rbe_snapshot(s.pos, s.q, s.box, s.alpha, P, SEED, 11)
