@@ -42,7 +42,7 @@ MUFU_OPS_PER_PAIR = {"k_rho": 2.0, "k_force": 1.0}
 # DRAM bytes per launch of the dominant kernel measured by ncu on this workload
 # (dram__bytes_read.sum + dram__bytes_write.sum), or None when not captured for the
 # current kernel version.  Source: profiles/ summaries.
-NCU_TRAFFIC = {("k_rho", "uniform-N4000000-P2000"): 128080384 + 3272448}
+NCU_TRAFFIC = {("k_rho", "uniform-N4000000-P2000"): 128415488 + 3578368}
 
 # launches of the library's own kernels per evaluation at a fixed box: the sampler, the rho
 # pass, the rho reduction and the force pass
