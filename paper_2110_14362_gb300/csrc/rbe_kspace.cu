@@ -984,7 +984,10 @@ rbe_status launch_evaluate_staged(rbe_ctx ctx, int64_t N, const double* h_pos, c
     int64_t i0[kMaxPieces + 1];
     int coff[kMaxPieces + 1];
     coff[0] = 0;
-    for (int g = 0; g <= pieces; ++g) i0[g] = N * g / pieces;
+    // four groups: a small first and last one (an eighth each), so that the copy in before the
+    // first pass and the copy out after the last are short; else equal groups
+    static const int kEighths4[5] = {0, 1, 4, 7, 8};
+    for (int g = 0; g <= pieces; ++g) i0[g] = pieces == 4 ? N * kEighths4[g] / 8 : N * g / pieces;
     for (int g = 0; g < pieces; ++g) {
         EvalShape sg;
         if ((st = evaluate_shape(ctx, i0[g + 1] - i0[g], K, &sg)) != RBE_OK) return st;

@@ -244,6 +244,38 @@ def test_host_api_pipelined(pinned):
         assert abs(Wh[a, a] - Wo[a, a]) <= 1e-5 * np.abs(np.diag(Wo)).max()
 
 
+def test_host_api_four_groups():
+    """The host-buffer call from 2^19 particles pipelines four groups of uneven size (an eighth,
+    three eighths, three eighths, an eighth): N = 600000, P = 100 with page-locked buffers, against
+    the device API to FP32 rounding, the oracle within 1e-5, and the same bits on a second call."""
+    import torch
+    s = inputs.uniform_density(600000, P=100)
+    F, W, E, _ = _run(s, 100, 7, rbe.RBE_FP32_PHASE)
+    pos = torch.empty((s.N, 3), dtype=torch.float64, pin_memory=True)
+    q = torch.empty((s.N,), dtype=torch.float64, pin_memory=True)
+    pos.copy_(torch.as_tensor(s.pos))
+    q.copy_(torch.as_tensor(s.q))
+    Fout = torch.zeros((s.N, 3), dtype=torch.float64, pin_memory=True).numpy()
+    outs = []
+    with rbe.Context(s.box, s.alpha, 100, SEED, rbe.RBE_FP32_PHASE) as ctx:
+        for _ in range(2):
+            Fout[:] = np.nan
+            Fh, Wh, Eh = rbe.rbe_kspace_forces_virial_host(ctx.h, pos.numpy(), q.numpy(), 7, Fout)
+            outs.append((Fh.copy(), Wh.copy(), Eh.copy()))
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+    Fh, Wh, Eh = outs[0]
+    assert rel_rms_force(Fh, F) < 2e-6
+    assert rel_frob(Wh, W) < 2e-6
+    assert abs(Eh[0] - E[0]) < 2e-6 * abs(E[0])
+    m, S = oracle.sample_k(s.box, s.alpha, 100, SEED, 7)
+    Fo, Wo, Eko, Eso, _ = oracle.rbe_kspace(s.pos, s.q, s.box, s.alpha, m, S / 100)
+    assert rel_rms_force(Fh, Fo) < 1e-5
+    for a in range(3):
+        assert abs(Wh[a, a] - Wo[a, a]) <= 1e-5 * np.abs(np.diag(Wo)).max()
+    assert abs(Eh[0] - Eko) <= 1e-5 * abs(Eko)
+
+
 @pytest.mark.parametrize("precision", [rbe.RBE_FP64, rbe.RBE_FP32_PHASE])
 def test_bitwise_reproducible(precision):
     s = inputs.uniform_density(30000, P=300)
