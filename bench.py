@@ -780,6 +780,32 @@ def run_sweep(rbe, steps=3):
             "mufu_peak_measured": peak, "points": out}
 
 
+# Warp instructions of one NPT step per particle (FP32-phase, P = 100, neighbour list, at the
+# serving stream's mean size N = 2e4; all kernels of 24 evaluations summed and divided by
+# 24 N: ncu smsp__inst_executed.sum of every launch, 80 % of them the real-space list evaluation).
+NPT_WARP_INSTR_PER_PARTICLE_STEP = 644.7e6 / (24 * 20000)
+
+
+def served_roofline(rbe, closed):
+    """The served form against its binding resources: the NPT step is bound by instruction issue
+    (the real-space list evaluation, about 80 % of its instructions), so the served particle-steps
+    per second times the warp instructions of a particle-step (measured) is set against the GPU's
+    issue rate (one warp instruction per clock per scheduler, four per SM); the k-space part
+    against the measured MUFU rate at 3 MUFU operations per pair."""
+    import torch
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sm_hz = 2.07e9  # the maximum SM clock, which the clock samples of the timed regions show under load
+    issue_peak = props.multi_processor_count * 4 * sm_hz
+    particle_steps = closed["pair_evals_per_s"] / SERVE_P
+    achieved = particle_steps * NPT_WARP_INSTR_PER_PARTICLE_STEP
+    mufu = rbe.rbe_measure_pipe(0, 4096)
+    return {"bound": "issue", "unit": "warp-instructions/s", "achieved": achieved, "peak": issue_peak,
+            "frac": achieved / issue_peak, "particle_steps_per_s": particle_steps,
+            "warp_instructions_per_particle_step": NPT_WARP_INSTR_PER_PARTICLE_STEP,
+            "kspace_mufu_frac": 3.0 * closed["pair_evals_per_s"] / mufu,
+            "source": "profiles/npt_replica_N20000_fp32_instruction_counts.md (ncu, N = 2e4)"}
+
+
 def run_serving(args, world, rank):
     """Requests of Poisson arrivals at 20/s, N log-uniform in [1e3, 1e5] at 0.1 per A^3,
     P = 100, 100 NPT steps each, chunks of 10 steps: closed-loop capacity and open-loop
@@ -795,7 +821,7 @@ def run_serving(args, world, rank):
     closed["replica_steps_per_s_all_ranks"] = world * closed["replica_steps"] / wall
     out = {"workload": f"{len(reqs)} NPT replica requests, Poisson 20/s, N log-uniform [1e3, 1e5] at 0.1/A^3, "
                        f"P={SERVE_P}, {steps} steps, chunk {chunk} steps, FP32-phase",
-           "slots": args.serve_slots, "closed_loop": closed}
+           "slots": args.serve_slots, "closed_loop": closed, "roofline": served_roofline(rbe, closed)}
     if not args.skip_open_loop:
         out["open_loop_20_per_s"] = serve(rbe, reqs, states, rbe.RBE_FP32_PHASE, args.serve_slots, chunk, steps,
                                           open_loop=True)
