@@ -93,7 +93,7 @@ struct BArgs {
     double* w;
     const int4* rtiles;         // (item, frequency tile, chunk)
     int nrt, S, T, F;           // rho tiles; particle sub-streams of a rho block (kBThreads / T),
-                                // frequency lanes of each (T = rho_k / F) and frequencies per lane
+                                // frequency lanes of each (T = rho_k) and frequencies per lane (rho_f)
     float4* part;
     double2* rho;
     double* terms;
@@ -237,10 +237,7 @@ __device__ __forceinline__ void pass_reduce(const BArgs& a)
                 freq_pre(mi, a.w[o + l], a.ks + r, c);
             }
         }
-        // the warp's rows summed together, so that the loads of all of them are in flight at
-        // once; each row's own order is warp_row_sum's (lane-strided float-float sums over the
-        // chunks, then the same shuffle tree), so a row's sum does not depend on its neighbours
-        if (!JOINT) {
+        if (!JOINT) {  // the warp's rows one after the other
 #pragma unroll 1
             for (int i = 0; i < kReduceRowsPerWarp; ++i) {
                 const int j = warp * kReduceRowsPerWarp + i, u = base + j;
@@ -251,6 +248,9 @@ __device__ __forceinline__ void pass_reduce(const BArgs& a)
                 if (lane == 0) srho[j] = v;
             }
         } else {
+            // the warp's rows summed together, so that the loads of all of them are in flight at
+            // once; each row's own order is warp_row_sum's (lane-strided float-float sums over the
+            // chunks, then the same shuffle tree), so a row's sum does not depend on its neighbours
             const float4* rowp[kReduceRowsPerWarp];
             int nch[kReduceRowsPerWarp], nmax = 0;
             float rh[kReduceRowsPerWarp], rl[kReduceRowsPerWarp], ih[kReduceRowsPerWarp], il[kReduceRowsPerWarp];
