@@ -4,7 +4,8 @@
 // the batch's alpha and P, on the FP32-phase path with compensated FP32 accumulation inside
 // a staged tile (RBE_RHO_COMP32) and FP64 energy and virial terms.  One evaluation is one
 // cooperative launch of k_batch whose blocks stay resident and run five passes, with a grid
-// barrier (bounded wait) between consecutive passes:
+// barrier (bounded wait) between consecutive passes (after the tables pass only when it has
+// tables to rebuild):
 //   tables   one unit per item whose box changed (or lives on the device): tables and box
 //            constants                                                           (H1)
 //   sample   units of 256 frequencies per item                                   (H2)
@@ -340,8 +341,10 @@ __device__ __forceinline__ void pass_force(const BArgs& a)
 __global__ void __launch_bounds__(kBThreads, RBE_BATCH_MINB) k_batch(BArgs a)
 {
     const unsigned nb = gridDim.x + (unsigned)a.bar_extra;
-    pass_tables(a);
-    if (!grid_sync(a.bar, nb, a.status)) return;
+    if (a.nw > 0) {  // tables to rebuild (the same for every block): the sampler waits for them
+        pass_tables(a);
+        if (!grid_sync(a.bar, nb, a.status)) return;
+    }
     pass_sample(a);
     if (!grid_sync(a.bar, nb, a.status)) return;
     pass_rho(a);
