@@ -61,6 +61,11 @@ def test_argument_validation_without_gpu():
     assert lib.rbe_water_init(None, None, None, 0) == rbe.RBE_EINVAL
     assert lib.rbe_water_step(None, None, None, 1) == rbe.RBE_EINVAL
     assert lib.rbe_flex_step(None, None, 1) == rbe.RBE_EINVAL
+    # the batch's tile setters refuse a NULL batch (or a NULL output) before any device work
+    f = ctypes.c_int32()
+    assert lib.rbe_batch_set_rho_f(None, 2) == rbe.RBE_EINVAL
+    assert lib.rbe_batch_get_rho_f(None, ctypes.byref(f)) == rbe.RBE_EINVAL
+    assert lib.rbe_batch_set_tiles(None, 64, 256, 512) == rbe.RBE_EINVAL
 
 
 def test_python_binding_raises_without_fallback():
