@@ -678,6 +678,12 @@ def run_batched(rbe, n_items=64, P=100, iters=20, tiles=None):
     out["pair_evals_per_s_loop"] = pairs / (out["loop_ms"] * 1e-3)
     out["batched_over_loop"] = out["loop_ms"] / out["batched_ms"]
     out["launches"] = {"batched": 1, "batched_one_launch_per_pass": 5, "loop": 4 * n_items}
+    # against the measured MUFU rate at 3 MUFU operations per pair (a sine and a cosine in the
+    # rho pass, one sine in the force pass), like the single-system evaluation
+    peak = rbe.rbe_measure_pipe(0, 4096)
+    out["mufu_frac"] = {"persistent": 3.0 * pairs / (out["batched_ms"] * 1e-3) / peak,
+                        "one_launch_per_pass": 3.0 * pairs / (out["batched_one_launch_per_pass_ms"] * 1e-3) / peak,
+                        "peak": peak}
     return out
 
 
