@@ -684,6 +684,16 @@ def run_batched(rbe, n_items=64, P=100, iters=20, tiles=None):
     out["mufu_frac"] = {"persistent": 3.0 * pairs / (out["batched_ms"] * 1e-3) / peak,
                         "one_launch_per_pass": 3.0 * pairs / (out["batched_one_launch_per_pass_ms"] * 1e-3) / peak,
                         "peak": peak}
+    # and against instruction issue, which binds both pair passes at P = 100: the warp instructions
+    # of one evaluation of these 64 systems (ncu, profiles/batched_kspace_64systems_P100.md: the
+    # rho, reduction and force passes one launch each, 132.7 M; the persistent kernel 139.1 M)
+    # over 152 SMs x 4 schedulers x 2.07 GHz
+    if n_items == 64 and P == 100:
+        import torch
+        issue = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count * 4 * 2.07e9
+        out["issue_frac"] = {"persistent": 139.1e6 / (out["batched_ms"] * 1e-3) / issue,
+                             "one_launch_per_pass": 132.7e6 / (out["batched_one_launch_per_pass_ms"] * 1e-3) / issue,
+                             "peak_warp_instructions_per_s": issue}
     return out
 
 
