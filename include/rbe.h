@@ -201,8 +201,9 @@ rbe_status rbe_kspace_forces_virial_xyzq(rbe_ctx ctx, int64_t N, const float* xy
  * device buffers, evaluates, copies forces, virial and energy back, synchronises the
  * stream and returns any latched device error.  forces_out may be NULL.  On the FP32-phase
  * path with N >= 2^17 the copies are pipelined with the passes: the particles go in two
- * groups, each evaluated by full-GPU passes of its own, so that a group's copy in overlaps the
- * previous group's rho pass and its forces' copy out overlaps the next group's force pass.
+ * groups (four from N >= 2^19: an eighth, three eighths, three eighths and an eighth), each
+ * evaluated by full-GPU passes of its own, so that a group's copy in overlaps the previous
+ * group's rho pass and its forces' copy out overlaps the next group's force pass.
  * The sums then run over a different chunk partition: the results agree with
  * rbe_kspace_forces_virial to FP32 rounding and are reproducible run to run.  Page-locked
  * host buffers let the copies overlap fully. */
