@@ -207,8 +207,24 @@ __device__ __forceinline__ void sample_body(int lbase, uint64_t seed, uint64_t s
     const unsigned long long* tx = cum;
     const unsigned long long* ty = cum + cap;
     const unsigned long long* tz = cum + 2 * (size_t)cap;
-    if (smem_cap > 0)  // smem_cap == cap: copy the three rows whole, without waiting for M
-        for (int j = threadIdx.x; j < 3 * smem_cap; j += blockDim.x) s_cum[j] = cum[j];
+    if (smem_cap > 0) {  // smem_cap == cap: copy the three rows whole, without waiting for M
+        // eight loads per thread issued before their stores, so that the copy takes one round
+        // trip to L2 per eight entries instead of one per entry
+        const int n = 3 * smem_cap;
+        for (int j0 = threadIdx.x; j0 < n; j0 += 8 * (int)blockDim.x) {
+            unsigned long long v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + u * (int)blockDim.x;
+                v[u] = j < n ? cum[j] : 0ull;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + u * (int)blockDim.x;
+                if (j < n) s_cum[j] = v[u];
+            }
+        }
+    }
     const int Mx = ks->M[0], My = ks->M[1], Mz = ks->M[2];
     if (smem_cap > 0) {
         __syncthreads();
